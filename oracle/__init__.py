@@ -1,0 +1,193 @@
+"""FP64 CPU oracle for the CREDIT reduction-reuse row ops.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product library
+(``paper_2609_01864_gb300``) never imports it, and it never imports the product
+library: the two share no code and meet only at the seeded input bytes.
+
+Contents
+--------
+* ``credit_oracle.c`` -- the plain double-precision definitions of softmax,
+  log-sum-exp, LayerNorm and RMSNorm (Eq. 1 of the paper, one row at a time),
+  exact decoding of BF16 / FP8-E4M3 inputs and round-to-nearest-even encoding
+  of BF16 / E4M3 outputs, written from the formats' definitions.
+* ``cost_model`` -- the analytic profitability model (Eq. 3, 4, 6-9).
+* ``mlp`` -- FP64 forward / backward / Adam of the latency MLP.
+
+The C part is compiled with gcc on first use (or by ``build()``) into
+``oracle/_build/liboracle.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "credit_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+F32, BF16, E4M3 = 0, 1, 2
+SOFTMAX, LOGSUMEXP, LAYERNORM, RMSNORM = 0, 1, 2, 3
+DTYPE_SIZE = {F32: 4, BF16: 2, E4M3: 1}
+E4M3_MAX = 448.0
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (gcc, -O2, OpenMP, no fast-math)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            so = build()
+            L = ctypes.CDLL(so)
+            d, i64, vp, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+            L.oracle_bf16_to_double.restype = d
+            L.oracle_bf16_to_double.argtypes = [ctypes.c_uint16]
+            L.oracle_e4m3_to_double.restype = d
+            L.oracle_e4m3_to_double.argtypes = [ctypes.c_uint8]
+            L.oracle_double_to_bf16.restype = ctypes.c_uint16
+            L.oracle_double_to_bf16.argtypes = [d]
+            L.oracle_double_to_e4m3_sat.restype = ctypes.c_uint8
+            L.oracle_double_to_e4m3_sat.argtypes = [d]
+            L.oracle_softmax_row.argtypes = [vp, i64, vp]
+            L.oracle_lse_row.restype = d
+            L.oracle_lse_row.argtypes = [vp, i64]
+            L.oracle_layernorm_row.argtypes = [vp, i64, vp, vp, d, vp]
+            L.oracle_rmsnorm_row.argtypes = [vp, i64, vp, d, vp]
+            L.oracle_decode.argtypes = [i32, vp, vp, i64, i64, i64, vp]
+            L.oracle_run.restype = i32
+            L.oracle_run.argtypes = [i32, i32, i32, vp, vp, i64, i64, i64, vp, vp, d,
+                                     vp, vp, i64, vp, i32]
+            L.oracle_max_threads.restype = i32
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------- formats
+def bf16_to_double(codes: np.ndarray) -> np.ndarray:
+    L = lib()
+    c = np.asarray(codes, dtype=np.uint16).ravel()
+    return np.array([L.oracle_bf16_to_double(int(v)) for v in c]).reshape(np.shape(codes))
+
+
+def e4m3_to_double(codes: np.ndarray) -> np.ndarray:
+    L = lib()
+    c = np.asarray(codes, dtype=np.uint8).ravel()
+    return np.array([L.oracle_e4m3_to_double(int(v)) for v in c]).reshape(np.shape(codes))
+
+
+def double_to_bf16(v: np.ndarray) -> np.ndarray:
+    L = lib()
+    a = np.asarray(v, dtype=np.float64).ravel()
+    return np.array([L.oracle_double_to_bf16(float(x)) for x in a], dtype=np.uint16).reshape(np.shape(v))
+
+
+def double_to_e4m3(v: np.ndarray) -> np.ndarray:
+    L = lib()
+    a = np.asarray(v, dtype=np.float64).ravel()
+    return np.array([L.oracle_double_to_e4m3_sat(float(x)) for x in a], dtype=np.uint8).reshape(np.shape(v))
+
+
+# ---------------------------------------------------------------- row ops
+def softmax(x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    for r in range(x.shape[0]):
+        lib().oracle_softmax_row(_ptr(x[r]), x.shape[1], _ptr(y[r]))
+    return y
+
+
+def logsumexp(x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return np.array([lib().oracle_lse_row(_ptr(x[r]), x.shape[1]) for r in range(x.shape[0])])
+
+
+def layernorm(x, gamma=None, beta=None, eps=1e-5):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = None if gamma is None else np.ascontiguousarray(gamma, dtype=np.float64)
+    b = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
+    y = np.empty_like(x)
+    for r in range(x.shape[0]):
+        lib().oracle_layernorm_row(_ptr(x[r]), x.shape[1], _ptr(g), _ptr(b), eps, _ptr(y[r]))
+    return y
+
+
+def rmsnorm(x, gamma=None, eps=1e-6):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = None if gamma is None else np.ascontiguousarray(gamma, dtype=np.float64)
+    y = np.empty_like(x)
+    for r in range(x.shape[0]):
+        lib().oracle_rmsnorm_row(_ptr(x[r]), x.shape[1], _ptr(g), eps, _ptr(y[r]))
+    return y
+
+
+def decode(dtype: int, raw: np.ndarray, rows: int, cols: int, ld: int = 0, in_scale=None) -> np.ndarray:
+    """Exact FP64 values of `rows` x `cols` stored elements (raw: bytes/words)."""
+    raw = np.ascontiguousarray(raw)
+    sc = None if in_scale is None else np.ascontiguousarray(in_scale, dtype=np.float32)
+    x = np.empty((rows, cols), dtype=np.float64)
+    lib().oracle_decode(dtype, _ptr(raw), _ptr(sc), rows, cols, ld or cols, _ptr(x))
+    return x
+
+
+DEFAULT_EPS = {SOFTMAX: 0.0, LOGSUMEXP: 0.0, LAYERNORM: 1e-5, RMSNORM: 1e-6}
+
+
+def run(op: int, in_dtype: int, raw: np.ndarray, rows: int, cols: int, *, out_dtype=None,
+        in_scale=None, gamma=None, beta=None, eps=None, ld_in: int = 0,
+        want_exact: bool = True, want_encoded: bool = False, nthreads: int = 0):
+    """Batch oracle.  Returns (y64 or None, encoded or None, out_scale or None).
+
+    raw holds the stored input elements (float32 / uint16 bf16 codes / uint8
+    e4m3 codes).  y64 is (rows, cols) or (rows,) for log-sum-exp.
+    """
+    out_dtype = in_dtype if out_dtype is None else out_dtype
+    if op == LOGSUMEXP:
+        out_dtype = F32
+    eps = DEFAULT_EPS[op] if eps is None else eps
+    raw = np.ascontiguousarray(raw)
+    sc = None if in_scale is None else np.ascontiguousarray(in_scale, dtype=np.float32)
+    g = None if gamma is None else np.ascontiguousarray(gamma, dtype=np.float32)
+    b = None if beta is None else np.ascontiguousarray(beta, dtype=np.float32)
+    shape = (rows,) if op == LOGSUMEXP else (rows, cols)
+    y64 = np.empty(shape, dtype=np.float64) if want_exact else None
+    enc = None
+    osc = None
+    if want_encoded:
+        npdt = {F32: np.float32, BF16: np.uint16, E4M3: np.uint8}[out_dtype]
+        enc = np.empty(shape, dtype=npdt)
+        if out_dtype == E4M3:
+            osc = np.empty(rows, dtype=np.float32)
+    rc = lib().oracle_run(op, in_dtype, out_dtype, _ptr(raw), _ptr(sc), rows, cols, ld_in,
+                          _ptr(g), _ptr(b), float(eps), _ptr(y64), _ptr(enc),
+                          0 if op == LOGSUMEXP else cols, _ptr(osc), nthreads)
+    if rc != 0:
+        raise ValueError("oracle_run rejected its arguments")
+    return y64, enc, osc
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())

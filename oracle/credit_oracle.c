@@ -1,0 +1,296 @@
+/*
+ * credit_oracle.c -- plain FP64 CPU oracle for the reduction-reuse row ops.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path links, loads or
+ * calls this file: only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark do.  It shares no code, header or constant table with the
+ * CUDA library; the two meet only at the seeded input bytes.
+ *
+ * What it computes (CREDIT, Sec. III-B, Eq. 1): every op reduces a row of N
+ * elements to a few statistics and then applies an elementwise function h to
+ * every element of the same row.  Because the cluster split of Eq. 2 is only a
+ * re-association of the same reductions, the oracle is the plain definition of
+ * each op, one row at a time, in double precision, with no blocking, slicing
+ * or reordering:
+ *
+ *   softmax   m = max_i x_i,  S = sum_i exp(x_i - m),  y_i = exp(x_i - m) / S
+ *   logsumexp m + ln S                                (one value per row)
+ *   layernorm mu = sum x / N, var = sum (x - mu)^2 / N  (biased, two passes),
+ *             y_i = (x_i - mu) / sqrt(var + eps) * gamma_i + beta_i
+ *   rmsnorm   y_i = x_i / sqrt(sum x^2 / N + eps) * gamma_i
+ *
+ * Sums use Neumaier compensation so that the oracle's own rounding stays far
+ * below every tolerance the GPU path is held to.
+ *
+ * Inputs are decoded EXACTLY to double: BF16 widens exactly; an FP8-E4M3 code
+ * times its FP32 per-row scale is exact in double (4 + 24 significant bits).
+ * Output rounding (BF16 round-to-nearest-even, E4M3 round-to-nearest-even with
+ * saturation to +-448) is written here from the two formats' definitions.
+ *
+ * FP8 output uses a per-row scale s = amax_i |y_i| / 448, codes q_i =
+ * RNE_sat(y_i / s); a row whose outputs are all zero gets s = 1 and q = 0.
+ *
+ * Build: gcc -O2 -fopenmp -fPIC -shared -ffp-contract=off (no fast-math).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+#include <float.h>
+#include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { OR_F32 = 0, OR_BF16 = 1, OR_E4M3 = 2 };
+enum { OR_SOFTMAX = 0, OR_LOGSUMEXP = 1, OR_LAYERNORM = 2, OR_RMSNORM = 3 };
+
+/* ------------------------------------------------------------------ */
+/* Compensated (Neumaier) summation                                    */
+/* ------------------------------------------------------------------ */
+typedef struct { double s, c; } nsum_t;
+
+static inline void nsum_add(nsum_t *a, double v) {
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+    else                       a->c += (v - t) + a->s;
+    a->s = t;
+}
+static inline double nsum_get(const nsum_t *a) { return a->s + a->c; }
+
+/* ------------------------------------------------------------------ */
+/* Number formats, from their definitions                              */
+/* ------------------------------------------------------------------ */
+
+/* bfloat16: 1 sign, 8 exponent (bias 127), 7 fraction bits; the upper half
+ * of an IEEE binary32. */
+double oracle_bf16_to_double(uint16_t b) {
+    int sign = (b >> 15) & 1;
+    int e = (b >> 7) & 0xFF;
+    int f = b & 0x7F;
+    double v;
+    if (e == 0xFF) v = f ? NAN : INFINITY;
+    else if (e == 0) v = ldexp((double)f, -126 - 7);          /* subnormal */
+    else v = ldexp(1.0 + (double)f / 128.0, e - 127);
+    return sign ? -v : v;
+}
+
+/* FP8 E4M3 ("fn" variant): 1 sign, 4 exponent (bias 7), 3 fraction bits; no
+ * infinities; S.1111.111 is NaN; largest finite magnitude 1.75 * 2^8 = 448. */
+double oracle_e4m3_to_double(uint8_t b) {
+    int sign = (b >> 7) & 1;
+    int e = (b >> 3) & 0xF;
+    int f = b & 0x7;
+    double v;
+    if (e == 0xF && f == 0x7) return NAN;
+    if (e == 0) v = ldexp((double)f, -6 - 3);                 /* subnormal */
+    else v = ldexp(1.0 + (double)f / 8.0, e - 7);
+    return sign ? -v : v;
+}
+
+/* Round v to a multiple of 2^k, ties to even (exact for the magnitudes used:
+ * v / 2^k is an exact power-of-two scaling). */
+static double round_to_quantum(double v, int k) {
+    double t = ldexp(v, -k);
+    double r = nearbyint(t);           /* default rounding mode: ties to even */
+    return ldexp(r, k);
+}
+
+uint16_t oracle_double_to_bf16(double v) {
+    if (isnan(v)) return 0x7FC0;
+    uint16_t sign = signbit(v) ? 0x8000 : 0;
+    double a = fabs(v);
+    if (a == 0.0) return sign;
+    int e;
+    frexp(a, &e);                      /* a = m * 2^e, m in [0.5, 1) */
+    int ex = e - 1;                    /* a in [2^ex, 2^(ex+1)) */
+    if (ex < -126) ex = -126;          /* subnormal quantum 2^-133 */
+    double q = round_to_quantum(a, ex - 7);
+    /* largest finite bf16 = (2 - 2^-7) * 2^127; overflow rounds to inf */
+    if (q >= ldexp(2.0, 127)) return sign | 0x7F80;
+    if (q == 0.0) return sign;
+    int qe;
+    frexp(q, &qe);
+    int qx = qe - 1;
+    if (qx < -126) {                   /* subnormal encoding */
+        int f = (int)ldexp(q, 133);
+        return sign | (uint16_t)f;
+    }
+    int f = (int)(ldexp(q, -qx) * 128.0 - 128.0 + 0.5);
+    return sign | (uint16_t)((qx + 127) << 7) | (uint16_t)f;
+}
+
+uint8_t oracle_double_to_e4m3_sat(double v) {
+    if (isnan(v)) return 0x7F;
+    uint8_t sign = signbit(v) ? 0x80 : 0;
+    double a = fabs(v);
+    if (a == 0.0) return sign;
+    int e;
+    frexp(a, &e);
+    int ex = e - 1;
+    if (ex < -6) ex = -6;              /* subnormal quantum 2^-9 */
+    double q = round_to_quantum(a, ex - 3);
+    if (q > 448.0) q = 448.0;          /* saturate (satfinite) */
+    if (q == 0.0) return sign;
+    int qe;
+    frexp(q, &qe);
+    int qx = qe - 1;
+    if (qx < -6) {
+        int f = (int)ldexp(q, 9);
+        return sign | (uint8_t)f;
+    }
+    int f = (int)(ldexp(q, -qx) * 8.0 - 8.0 + 0.5);
+    return sign | (uint8_t)((qx + 7) << 3) | (uint8_t)f;
+}
+
+/* ------------------------------------------------------------------ */
+/* The four ops on one row of doubles (Eq. 1, plain definitions)        */
+/* ------------------------------------------------------------------ */
+
+void oracle_softmax_row(const double *x, int64_t n, double *y) {
+    double m = -INFINITY;
+    for (int64_t i = 0; i < n; ++i) m = x[i] > m ? x[i] : m;
+    nsum_t S = {0, 0};
+    for (int64_t i = 0; i < n; ++i) nsum_add(&S, exp(x[i] - m));
+    double s = nsum_get(&S);
+    for (int64_t i = 0; i < n; ++i) y[i] = exp(x[i] - m) / s;
+}
+
+double oracle_lse_row(const double *x, int64_t n) {
+    double m = -INFINITY;
+    for (int64_t i = 0; i < n; ++i) m = x[i] > m ? x[i] : m;
+    nsum_t S = {0, 0};
+    for (int64_t i = 0; i < n; ++i) nsum_add(&S, exp(x[i] - m));
+    return m + log(nsum_get(&S));
+}
+
+void oracle_layernorm_row(const double *x, int64_t n, const double *gamma,
+                          const double *beta, double eps, double *y) {
+    nsum_t S = {0, 0};
+    for (int64_t i = 0; i < n; ++i) nsum_add(&S, x[i]);
+    double mu = nsum_get(&S) / (double)n;
+    nsum_t V = {0, 0};
+    for (int64_t i = 0; i < n; ++i) { double d = x[i] - mu; nsum_add(&V, d * d); }
+    double var = nsum_get(&V) / (double)n;
+    double r = 1.0 / sqrt(var + eps);
+    for (int64_t i = 0; i < n; ++i) {
+        double g = gamma ? gamma[i] : 1.0;
+        double b = beta ? beta[i] : 0.0;
+        y[i] = (x[i] - mu) * r * g + b;
+    }
+}
+
+void oracle_rmsnorm_row(const double *x, int64_t n, const double *gamma,
+                        double eps, double *y) {
+    nsum_t S = {0, 0};
+    for (int64_t i = 0; i < n; ++i) nsum_add(&S, x[i] * x[i]);
+    double r = 1.0 / sqrt(nsum_get(&S) / (double)n + eps);
+    for (int64_t i = 0; i < n; ++i) {
+        double g = gamma ? gamma[i] : 1.0;
+        y[i] = x[i] * r * g;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Batch driver: decode -> op -> (exact doubles, encoded output)        */
+/* ------------------------------------------------------------------ */
+
+static double decode_one(const void *base, int dtype, int64_t idx) {
+    switch (dtype) {
+    case OR_F32:  return (double)((const float *)base)[idx];
+    case OR_BF16: return oracle_bf16_to_double(((const uint16_t *)base)[idx]);
+    default:      return oracle_e4m3_to_double(((const uint8_t *)base)[idx]);
+    }
+}
+
+static void *malloc_row(int64_t n) { return malloc((size_t)n * sizeof(double)); }
+static void free_row(void *p) { free(p); }
+
+static int dtype_size(int dtype) { return dtype == OR_F32 ? 4 : (dtype == OR_BF16 ? 2 : 1); }
+
+/* Decode `rows` rows of `cols` elements (row stride ld elements) to doubles.
+ * For E4M3 input the per-row FP32 scale multiplies the decoded code. */
+void oracle_decode(int dtype, const void *in, const float *in_scale, int64_t rows,
+                   int64_t cols, int64_t ld, double *x) {
+    for (int64_t r = 0; r < rows; ++r) {
+        const char *row = (const char *)in + r * ld * dtype_size(dtype);
+        double sc = (dtype == OR_E4M3 && in_scale) ? (double)in_scale[r] : 1.0;
+        for (int64_t i = 0; i < cols; ++i) x[r * cols + i] = decode_one(row, dtype, i) * sc;
+    }
+}
+
+/*
+ * Full batch.  y64 (may be NULL) receives the exact result: rows*cols doubles,
+ * or `rows` doubles for logsumexp.  out (may be NULL) receives the result
+ * rounded to out_dtype with row stride ld_out; for E4M3 output out_scale gets
+ * the per-row scale (amax/448, or 1 for an all-zero row).  Logsumexp always
+ * writes FP32.  nthreads <= 0 uses the OpenMP default.  Returns 0, or -1 on a
+ * bad argument.
+ */
+int oracle_run(int op, int in_dtype, int out_dtype, const void *in,
+               const float *in_scale, int64_t rows, int64_t cols, int64_t ld_in,
+               const float *gamma, const float *beta, double eps, double *y64,
+               void *out, int64_t ld_out, float *out_scale, int nthreads) {
+    if (rows < 0 || cols <= 0 || !in) return -1;
+    if (op < 0 || op > 3 || in_dtype < 0 || in_dtype > 2 || out_dtype < 0 || out_dtype > 2) return -1;
+    if (ld_in <= 0) ld_in = cols;
+    if (ld_out <= 0) ld_out = cols;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    int bad = 0;
+#pragma omp parallel
+    {
+        double *x = (double *)malloc_row(cols);
+        double *y = (double *)malloc_row(cols);
+        double *g = gamma ? (double *)malloc_row(cols) : NULL;
+        double *b = beta ? (double *)malloc_row(cols) : NULL;
+        if (!x || !y || (gamma && !g) || (beta && !b)) {
+#pragma omp atomic write
+            bad = 1;
+        } else {
+            if (g) for (int64_t i = 0; i < cols; ++i) g[i] = (double)gamma[i];
+            if (b) for (int64_t i = 0; i < cols; ++i) b[i] = (double)beta[i];
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t r = 0; r < rows; ++r) {
+                const char *row = (const char *)in + r * ld_in * dtype_size(in_dtype);
+                double sc = (in_dtype == OR_E4M3 && in_scale) ? (double)in_scale[r] : 1.0;
+                for (int64_t i = 0; i < cols; ++i) x[i] = decode_one(row, in_dtype, i) * sc;
+                if (op == OR_LOGSUMEXP) {
+                    double v = oracle_lse_row(x, cols);
+                    if (y64) y64[r] = v;
+                    if (out) ((float *)out)[r] = (float)v;
+                    continue;
+                }
+                if (op == OR_SOFTMAX) oracle_softmax_row(x, cols, y);
+                else if (op == OR_LAYERNORM) oracle_layernorm_row(x, cols, g, b, eps, y);
+                else oracle_rmsnorm_row(x, cols, g, eps, y);
+                if (y64) memcpy(y64 + r * cols, y, (size_t)cols * sizeof(double));
+                if (!out) continue;
+                char *orow = (char *)out + r * ld_out * dtype_size(out_dtype);
+                if (out_dtype == OR_F32) {
+                    for (int64_t i = 0; i < cols; ++i) ((float *)orow)[i] = (float)y[i];
+                } else if (out_dtype == OR_BF16) {
+                    for (int64_t i = 0; i < cols; ++i) ((uint16_t *)orow)[i] = oracle_double_to_bf16(y[i]);
+                } else {
+                    double amax = 0.0;
+                    for (int64_t i = 0; i < cols; ++i) amax = fabs(y[i]) > amax ? fabs(y[i]) : amax;
+                    double s = amax > 0.0 ? amax / 448.0 : 1.0;
+                    if (out_scale) out_scale[r] = (float)s;
+                    for (int64_t i = 0; i < cols; ++i) ((uint8_t *)orow)[i] = oracle_double_to_e4m3_sat(y[i] / s);
+                }
+            }
+        }
+        free_row(x); free_row(y); free_row(g); free_row(b);
+    }
+    return bad ? -1 : 0;
+}
+
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
