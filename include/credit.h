@@ -1,0 +1,209 @@
+/*
+ * credit.h -- C ABI of the GB300 (sm_103a) reduction-reuse row library.
+ *
+ * The library computes wide "reduction-reuse" row ops (CREDIT, Sec. III-B,
+ * Eq. 1): every row of N elements is reduced to a few scalar statistics and
+ * the statistics are then applied to every element of the same row.  Three
+ * execution paths exist:
+ *
+ *   CLUSTER   the row is split over the P CTAs of a thread-block cluster
+ *             (Eq. 2); each CTA stages its slice once in shared memory with
+ *             bulk-async copies, pushes its partial statistics into every
+ *             peer's shared memory over DSMEM (Eq. 5), and writes its output
+ *             segment from shared memory (no second HBM read, Eq. 4).
+ *   ONE_CTA   the whole row is staged in one CTA's shared memory (the
+ *             local-SMEM-staged non-DSMEM baseline of Sec. IV-A).
+ *   TWO_PASS  the global-reread non-DSMEM baseline of Sec. IV-A: a statistics
+ *             sweep over HBM, then a second sweep that rereads the row and
+ *             writes the output; with ctas_per_row > 1 the row is split over
+ *             several CTAs whose partials go through a device workspace and
+ *             a second kernel launch.
+ *
+ * A planner (Sec. III-D, Eq. 3 and 7-9; optionally a learned latency model)
+ * picks a path and cluster size per shape.
+ *
+ * Conventions shared by every entry point:
+ *  - Device pointers are plain device addresses owned by the caller.  The
+ *    library owns only a per-device workspace that credit_init() allocates.
+ *  - All work is enqueued asynchronously on `stream` (0 = legacy default
+ *    stream).  The return value reports argument and launch errors; faults
+ *    found on the device (a bounded wait that gave up) are reported later by
+ *    credit_device_error().
+ *  - Rows are row-major.  Element i of row r lives at base + (r*ld + i)
+ *    elements; ld = 0 means ld = cols.  Any element alignment is accepted;
+ *    16-byte-aligned rows take the vectorised fast path automatically.
+ *  - rows == 0 is a no-op that returns CREDIT_OK.  cols <= 0, a NULL data
+ *    pointer, or FP8 data without scales return CREDIT_ERR_INVALID_ARG.
+ *  - in == out is allowed for every op except logsumexp; partial overlap of
+ *    input and output is undefined.
+ *  - Statistics are computed in FP32 from inputs decoded to FP32; outputs are
+ *    rounded to nearest even (FP8 saturates to +-448).
+ */
+#ifndef CREDIT_H_
+#define CREDIT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CREDIT_F32 = 0,
+    CREDIT_BF16 = 1,
+    CREDIT_FP8_E4M3 = 2  /* e4m3 "fn": +-448 max, per-row FP32 scale */
+} credit_dtype;
+
+typedef enum {
+    CREDIT_OP_SOFTMAX = 0,    /* y_i = exp(x_i - m) / sum_j exp(x_j - m)            */
+    CREDIT_OP_LOGSUMEXP = 1,  /* out[r] = m + ln sum_j exp(x_j - m), FP32 per row    */
+    CREDIT_OP_LAYERNORM = 2,  /* y_i = (x_i - mu) / sqrt(var + eps) * g_i + b_i      */
+    CREDIT_OP_RMSNORM = 3     /* y_i = x_i / sqrt(mean(x^2) + eps) * g_i             */
+} credit_op;
+
+typedef enum {
+    CREDIT_PATH_AUTO = -1,
+    CREDIT_PATH_ONE_CTA = 0,
+    CREDIT_PATH_TWO_PASS = 1,
+    CREDIT_PATH_CLUSTER = 2
+} credit_path;
+
+typedef enum {
+    CREDIT_OK = 0,
+    CREDIT_ERR_INVALID_ARG = 1,
+    CREDIT_ERR_UNSUPPORTED = 2,      /* illegal cluster size (Eq. 3), dtype or shape   */
+    CREDIT_ERR_CUDA = 3,             /* a CUDA runtime call or launch failed           */
+    CREDIT_ERR_TIMEOUT = 4,          /* a bounded device wait gave up                  */
+    CREDIT_ERR_NOT_INITIALIZED = 5,  /* credit_init() has not run on this device       */
+    CREDIT_ERR_CAPTURE = 6,          /* the call would allocate during stream capture  */
+    CREDIT_ERR_IO = 7                /* a calibration / model file could not be used   */
+} credit_status;
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char *credit_status_string(credit_status s);
+
+/* Version of this library as MAJOR*10000 + MINOR*100 + PATCH. */
+int credit_version(void);
+
+/*
+ * credit_init -- prepare `device` (sets it current on the calling thread):
+ * reads device limits (SM count, opt-in shared memory per block, clock),
+ * raises the dynamic-shared-memory and non-portable-cluster attributes of the
+ * kernels, and allocates the per-device workspace used by the split-row
+ * two-pass path (and the device error word).  Idempotent and thread-safe.
+ * The simple entry points call it on first use; call it yourself before any
+ * stream capture, because it allocates.
+ */
+credit_status credit_init(int device);
+
+/*
+ * Simple entry points (BASELINE interface).  dtype is both the input and the
+ * output type; FP8 needs per-row scales and is only reachable through
+ * credit_run_ex (these return CREDIT_ERR_INVALID_ARG for FP8).  LayerNorm
+ * uses gamma = 1, beta = 0, eps = 1e-5; RMSNorm gamma = 1, eps = 1e-6.
+ * The path is chosen by credit_plan().  Sec. III-B/C; Eq. 1-2, 5.
+ *   in   device pointer, rows x cols elements of dtype, contiguous rows
+ *   out  device pointer, rows x cols of dtype (logsumexp: rows FP32 values)
+ */
+credit_status credit_softmax(const void *in, void *out, int64_t rows, int64_t cols,
+                             credit_dtype dtype, cudaStream_t stream);
+credit_status credit_logsumexp(const void *in, void *out, int64_t rows, int64_t cols,
+                               credit_dtype dtype, cudaStream_t stream);
+credit_status credit_layernorm(const void *in, void *out, int64_t rows, int64_t cols,
+                               credit_dtype dtype, cudaStream_t stream);
+credit_status credit_rmsnorm(const void *in, void *out, int64_t rows, int64_t cols,
+                             credit_dtype dtype, cudaStream_t stream);
+
+/*
+ * Execution plan.  path / cluster_size / ctas_per_row / threads fully decide
+ * the launch; the rest is informational.
+ *   cluster_size  P of Eq. 2 for CREDIT_PATH_CLUSTER (2..16); 1 otherwise
+ *   ctas_per_row  CTAs that share one row: P for CLUSTER, 1 for ONE_CTA,
+ *                 G >= 1 for TWO_PASS (G > 1 uses the workspace)
+ *   threads       threads per CTA (multiple of 32, 64..1024; 0 = default)
+ *   smem_bytes    dynamic shared memory per CTA (S_CTA of Eq. 3)
+ *   predicted_us  model latency for the whole call (0 when not modelled)
+ *   source        0 analytic model, 1 learned model, 2 forced by caller or
+ *                 environment, 3 built-in heuristic (no calibration loaded)
+ */
+typedef struct {
+    int32_t path;          /* credit_path */
+    int32_t cluster_size;
+    int32_t ctas_per_row;
+    int32_t threads;
+    int64_t smem_bytes;
+    float predicted_us;
+    int32_t source;
+} credit_plan_t;
+
+/*
+ * credit_plan -- choose a plan for (op, rows, cols, in dtype -> out dtype)
+ * (Sec. III-D).  Enumerates the legal candidates (Eq. 3 capacity, cluster
+ * occupancy > 0), scores them with the loaded calibration (Eq. 7-9) or the
+ * learned model, and returns the best one in *out.  Pure host code apart from
+ * one-time occupancy queries; deterministic; thread-safe.
+ * Environment overrides: CREDIT_FORCE_PATH=one_cta|two_pass|cluster,
+ * CREDIT_FORCE_P=<P>, CREDIT_MODEL=analytic|learned.
+ */
+credit_status credit_plan(credit_op op, int64_t rows, int64_t cols, credit_dtype dtype,
+                          credit_plan_t *out);
+credit_status credit_plan_ex(credit_op op, int64_t rows, int64_t cols, credit_dtype in_dtype,
+                             credit_dtype out_dtype, credit_plan_t *out);
+
+/*
+ * Full argument set.
+ *   in, out      device pointers (see conventions); out of logsumexp = rows FP32
+ *   ld_in/ld_out row strides in elements (0 = cols)
+ *   in_scale     FP8 input: rows FP32 scales (x = code * scale); else NULL
+ *   out_scale    FP8 output: rows FP32 scales written by the call; else NULL
+ *   gamma, beta  LayerNorm / RMSNorm affine, cols FP32 each, NULL = 1 / 0
+ *   eps          LayerNorm / RMSNorm epsilon; negative = default (1e-5 / 1e-6)
+ */
+typedef struct {
+    int32_t op;            /* credit_op */
+    const void *in;
+    void *out;
+    int64_t rows, cols, ld_in, ld_out;
+    int32_t in_dtype, out_dtype;  /* credit_dtype; logsumexp output is FP32 */
+    const float *in_scale;
+    float *out_scale;
+    const float *gamma;
+    const float *beta;
+    float eps;
+} credit_args;
+
+/*
+ * credit_run_ex -- run one op with an explicit plan (NULL = credit_plan's
+ * choice).  Returns CREDIT_ERR_UNSUPPORTED for a plan that breaks Eq. 3 or
+ * cannot be scheduled on this device, without launching anything.
+ */
+credit_status credit_run_ex(const credit_args *args, const credit_plan_t *plan,
+                            cudaStream_t stream);
+
+/*
+ * credit_device_error -- synchronise `stream`, then read and clear the
+ * device error word of the current device.  Returns CREDIT_ERR_TIMEOUT if a
+ * kernel's bounded wait gave up since the last call, CREDIT_OK otherwise.
+ */
+credit_status credit_device_error(cudaStream_t stream);
+
+/*
+ * Capacity of one CTA for a staged slice (Eq. 3): the largest slice, in
+ * elements of dtype, that fits the opt-in shared memory of the current device
+ * next to the fixed scratch.  0 before credit_init.
+ */
+int64_t credit_slice_capacity(credit_dtype dtype);
+
+/*
+ * Number of kernels this library has launched in this process, all devices
+ * (monotonic).  The difference across a region counts the launches in it.
+ */
+long long credit_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CREDIT_H_ */

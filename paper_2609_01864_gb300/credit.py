@@ -1,0 +1,221 @@
+"""Thin ctypes binding of libcredit.so (include/credit.h).
+
+Argument marshalling only: every step of every op runs in the library's CUDA
+kernels.  Tensors are torch CUDA tensors (PyTorch supplies device memory and
+streams); raw device addresses are accepted where a tensor is.  If the
+library is not built the first call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libcredit.so")
+
+# enums of credit.h
+F32, BF16, FP8_E4M3 = 0, 1, 2
+SOFTMAX, LOGSUMEXP, LAYERNORM, RMSNORM = 0, 1, 2, 3
+PATH_AUTO, PATH_ONE_CTA, PATH_TWO_PASS, PATH_CLUSTER = -1, 0, 1, 2
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_INITIALIZED, ERR_CAPTURE, ERR_IO = range(8)
+OP_NAMES = {SOFTMAX: "softmax", LOGSUMEXP: "logsumexp", LAYERNORM: "layernorm", RMSNORM: "rmsnorm"}
+PATH_NAMES = {PATH_ONE_CTA: "one_cta", PATH_TWO_PASS: "two_pass", PATH_CLUSTER: "cluster"}
+
+TORCH_DTYPE = {F32: torch.float32, BF16: torch.bfloat16, FP8_E4M3: torch.float8_e4m3fn}
+DTYPE_OF = {torch.float32: F32, torch.bfloat16: BF16, torch.float8_e4m3fn: FP8_E4M3}
+
+
+class CreditError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)}" if what else status_string(status))
+
+
+class PlanT(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("ctas_per_row", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int64), ("predicted_us", ctypes.c_float),
+                ("source", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+    def __repr__(self):
+        return f"PlanT({self.as_dict()})"
+
+
+class ArgsT(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("ld_in", ctypes.c_int64),
+                ("ld_out", ctypes.c_int64), ("in_dtype", ctypes.c_int32), ("out_dtype", ctypes.c_int32),
+                ("in_scale", ctypes.c_void_p), ("out_scale", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
+                ("beta", ctypes.c_void_p), ("eps", ctypes.c_float)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcredit.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libcredit.so is not built ({LIB_PATH}); run "
+                                   "paper_2609_01864_gb300.build.build() -- there is no fallback path")
+            L = ctypes.CDLL(LIB_PATH)
+            i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+            L.credit_status_string.restype = ctypes.c_char_p
+            L.credit_status_string.argtypes = [i32]
+            L.credit_version.restype = i32
+            L.credit_init.restype = i32
+            L.credit_init.argtypes = [i32]
+            for name in ("credit_softmax", "credit_logsumexp", "credit_layernorm", "credit_rmsnorm"):
+                f = getattr(L, name)
+                f.restype = i32
+                f.argtypes = [vp, vp, i64, i64, i32, vp]
+            L.credit_plan.restype = i32
+            L.credit_plan.argtypes = [i32, i64, i64, i32, ctypes.POINTER(PlanT)]
+            L.credit_plan_ex.restype = i32
+            L.credit_plan_ex.argtypes = [i32, i64, i64, i32, i32, ctypes.POINTER(PlanT)]
+            L.credit_run_ex.restype = i32
+            L.credit_run_ex.argtypes = [ctypes.POINTER(ArgsT), ctypes.POINTER(PlanT), vp]
+            L.credit_device_error.restype = i32
+            L.credit_device_error.argtypes = [vp]
+            L.credit_slice_capacity.restype = i64
+            L.credit_slice_capacity.argtypes = [i32]
+            L.credit_launch_count.restype = ctypes.c_longlong
+            L.credit_launch_count.argtypes = []
+            _extra_prototypes(L)
+            _lib = L
+    return _lib
+
+
+def _extra_prototypes(L):
+    """Prototypes of the optional subsystems (profiling, model, ragged, MLP)."""
+    return L
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().credit_status_string(int(s)).decode()
+    except Exception:  # library not loadable: still give a readable message
+        return f"status {s}"
+
+
+def _check(st: int, what: str):
+    if st != OK:
+        raise CreditError(st, what)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def init(device: int | None = None):
+    dev = torch.cuda.current_device() if device is None else int(device)
+    _check(lib().credit_init(dev), "credit_init")
+
+
+def _simple(fn_name, op, x, out, stream):
+    if x.dim() != 2 or not x.is_contiguous():
+        raise ValueError("expected a contiguous 2-D tensor")
+    dt = DTYPE_OF[x.dtype]
+    rows, cols = x.shape
+    if out is None:
+        out = torch.empty(rows, device=x.device, dtype=torch.float32) if op == LOGSUMEXP else torch.empty_like(x)
+    _check(getattr(lib(), fn_name)(_ptr(x), _ptr(out), rows, cols, dt, _stream(stream)), fn_name)
+    return out
+
+
+def softmax(x, out=None, stream=None):
+    return _simple("credit_softmax", SOFTMAX, x, out, stream)
+
+
+def logsumexp(x, out=None, stream=None):
+    return _simple("credit_logsumexp", LOGSUMEXP, x, out, stream)
+
+
+def layernorm(x, out=None, stream=None):
+    return _simple("credit_layernorm", LAYERNORM, x, out, stream)
+
+
+def rmsnorm(x, out=None, stream=None):
+    return _simple("credit_rmsnorm", RMSNORM, x, out, stream)
+
+
+def make_plan(path: int, cluster_size: int = 1, ctas_per_row: int = 1, threads: int = 0) -> PlanT:
+    p = PlanT()
+    p.path = path
+    p.cluster_size = cluster_size
+    p.ctas_per_row = ctas_per_row if path != PATH_CLUSTER else cluster_size
+    p.threads = threads
+    return p
+
+
+def plan(op: int, rows: int, cols: int, in_dtype: int, out_dtype: int | None = None) -> PlanT:
+    p = PlanT()
+    if out_dtype is None:
+        out_dtype = F32 if op == LOGSUMEXP else in_dtype
+    _check(lib().credit_plan_ex(op, rows, cols, in_dtype, out_dtype, ctypes.byref(p)), "credit_plan_ex")
+    return p
+
+
+def run_ex(op: int, x, out, *, rows: int | None = None, cols: int | None = None, in_dtype: int | None = None,
+           out_dtype: int | None = None, ld_in: int = 0, ld_out: int = 0, in_scale=None, out_scale=None,
+           gamma=None, beta=None, eps: float = -1.0, plan: PlanT | None = None, stream=None) -> int:
+    """credit_run_ex.  x / out: tensors or raw device addresses.  Returns the
+    status (raises CreditError on a non-OK status)."""
+    a = ArgsT()
+    a.op = op
+    a.in_ = _ptr(x)
+    a.out = _ptr(out)
+    if rows is None or cols is None:
+        rows, cols = x.shape[0], x.shape[-1]
+    a.rows, a.cols, a.ld_in, a.ld_out = rows, cols, ld_in, ld_out
+    if in_dtype is None:
+        in_dtype = DTYPE_OF[x.dtype]
+    if out_dtype is None:
+        out_dtype = F32 if op == LOGSUMEXP else (DTYPE_OF[out.dtype] if hasattr(out, "dtype") else in_dtype)
+    a.in_dtype, a.out_dtype = in_dtype, out_dtype
+    a.in_scale, a.out_scale = _ptr(in_scale), _ptr(out_scale)
+    a.gamma, a.beta = _ptr(gamma), _ptr(beta)
+    a.eps = eps
+    st = lib().credit_run_ex(ctypes.byref(a), ctypes.byref(plan) if plan is not None else None, _stream(stream))
+    _check(st, "credit_run_ex")
+    return st
+
+
+def run_ex_status(*args, **kw) -> int:
+    """Like run_ex but returns the status instead of raising."""
+    try:
+        return run_ex(*args, **kw)
+    except CreditError as e:
+        return e.status
+
+
+def device_error(stream=None) -> int:
+    return lib().credit_device_error(_stream(stream))
+
+
+def slice_capacity(dtype: int) -> int:
+    return int(lib().credit_slice_capacity(dtype))
+
+
+def launch_count() -> int:
+    return int(lib().credit_launch_count())

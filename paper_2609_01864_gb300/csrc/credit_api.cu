@@ -1,0 +1,500 @@
+// credit_api.cu -- host side of the C ABI declared in include/credit.h.
+//
+// Argument validation, per-device state (limits, workspace, error word),
+// plan legality (Eq. 3 capacity, cluster occupancy), and the launches of the
+// three paths.  Planning itself lives in credit_plan.cpp.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "../../include/credit.h"
+#include "credit_host.h"
+#include "credit_rows.cuh"
+
+namespace credit {
+bool kernels_tin0(int op, int tout, KernelSet *ks);
+bool kernels_tin1(int op, int tout, KernelSet *ks);
+bool kernels_tin2(int op, int tout, KernelSet *ks);
+}  // namespace credit
+
+using namespace credit;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr size_t kWorkspaceFloats = size_t(16) << 20;  // 64 MiB of two-pass partials
+
+struct DeviceState {
+    std::mutex mu;
+    std::atomic<bool> ready{false};
+    DeviceInfo info{};
+    float *ws = nullptr;
+    unsigned *err = nullptr;
+    std::map<const void *, bool> attr_done;
+    std::map<std::tuple<const void *, int, int, long long>, int> clusters;  // max active clusters
+};
+DeviceState g_dev[kMaxDevices];
+
+bool kernel_set(int op, int tin, int tout, KernelSet *ks) {
+    std::memset(ks, 0, sizeof(*ks));
+    if (op == OP_LSE) tout = DT_F32;
+    switch (tin) {
+    case DT_F32: return kernels_tin0(op, tout, ks);
+    case DT_BF16: return kernels_tin1(op, tout, ks);
+    case DT_E4M3: return kernels_tin2(op, tout, ks);
+    default: return false;
+    }
+}
+
+credit_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return CREDIT_OK;
+    if (std::getenv("CREDIT_LOG")) std::fprintf(stderr, "credit: CUDA error %s\n", cudaGetErrorString(e));
+    return CREDIT_ERR_CUDA;
+}
+
+bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+// Raise per-kernel attributes once per (device, kernel).
+credit_status prepare_kernel(DeviceState &d, const void *fn, bool staged) {
+    std::lock_guard<std::mutex> lk(d.mu);
+    if (d.attr_done.count(fn)) return CREDIT_OK;
+    if (staged) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(d.info.smem_optin));
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    d.attr_done[fn] = true;
+    return CREDIT_OK;
+}
+
+int default_staged_threads(long long groups_per_cta) {
+    long long t = (groups_per_cta + 7) / 8;
+    t = (t + 31) / 32 * 32;
+    if (t < 64) t = 64;
+    if (t > 1024) t = 1024;
+    return static_cast<int>(t);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host helpers
+namespace credit {
+
+int dtype_size(int dt) { return dt == DT_F32 ? 4 : (dt == DT_BF16 ? 2 : 1); }
+
+// S_CTA of Eq. 3 for a slice of a row of N elements of isz bytes over P CTAs.
+long long staged_smem_bytes(long long N, int isz, int P) {
+    const long long groups = (N * isz) / 16;           // full 16-byte groups (upper bound)
+    const long long per = (groups + P - 1) / P;
+    return kCtrlBytes + kEdgeBytes + per * 16;
+}
+
+long long staged_groups_per_cta(long long N, int isz, int P) {
+    const long long groups = (N * isz) / 16;
+    return (groups + P - 1) / P;
+}
+
+const DeviceInfo *device_info(int device) {
+    if (device < 0 || device >= kMaxDevices || !g_dev[device].ready.load()) return nullptr;
+    return &g_dev[device].info;
+}
+
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    return dev;
+}
+
+// Max active clusters of the staged kernel for (op, dtypes, P, threads, smem);
+// 0 if it cannot be scheduled.  Cached.
+int staged_max_clusters(int device, int op, int tin, int tout, int P, int threads, long long smem) {
+    if (device < 0 || device >= kMaxDevices) return 0;
+    DeviceState &d = g_dev[device];
+    KernelSet ks;
+    if (!kernel_set(op, tin, tout, &ks)) return 0;
+    if (smem > d.info.smem_optin) return 0;
+    if (prepare_kernel(d, ks.staged, true) != CREDIT_OK) return 0;
+    const auto key = std::make_tuple(ks.staged, P, threads, smem);
+    {
+        std::lock_guard<std::mutex> lk(d.mu);
+        auto it = d.clusters.find(key);
+        if (it != d.clusters.end()) return it->second;
+    }
+    int n = 0;
+    if (P <= 1) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.staged, threads, static_cast<size_t>(smem)) ==
+            cudaSuccess)
+            n = per_sm * d.info.sm_count;
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = P;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(P * 64);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaOccupancyMaxActiveClusters(&n, ks.staged, &cfg) != cudaSuccess) {
+            n = 0;
+            (void)cudaGetLastError();
+        }
+    }
+    std::lock_guard<std::mutex> lk(d.mu);
+    d.clusters[key] = n;
+    return n;
+}
+
+}  // namespace credit
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char *credit_status_string(credit_status s) {
+    switch (s) {
+    case CREDIT_OK: return "CREDIT_OK";
+    case CREDIT_ERR_INVALID_ARG: return "CREDIT_ERR_INVALID_ARG";
+    case CREDIT_ERR_UNSUPPORTED: return "CREDIT_ERR_UNSUPPORTED";
+    case CREDIT_ERR_CUDA: return "CREDIT_ERR_CUDA";
+    case CREDIT_ERR_TIMEOUT: return "CREDIT_ERR_TIMEOUT";
+    case CREDIT_ERR_NOT_INITIALIZED: return "CREDIT_ERR_NOT_INITIALIZED";
+    case CREDIT_ERR_CAPTURE: return "CREDIT_ERR_CAPTURE";
+    case CREDIT_ERR_IO: return "CREDIT_ERR_IO";
+    default: return "CREDIT_ERR_UNKNOWN";
+    }
+}
+
+int credit_version(void) { return 10000; }
+
+credit_status credit_init(int device) {
+    if (device < 0 || device >= kMaxDevices) return CREDIT_ERR_INVALID_ARG;
+    DeviceState &d = g_dev[device];
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (d.ready.load()) return CREDIT_OK;
+    std::lock_guard<std::mutex> lk(d.mu);
+    if (d.ready.load()) return CREDIT_OK;
+    DeviceInfo info{};
+    int v = 0;
+    if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return cuda_status(e);
+    info.sm_count = v;
+    if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) != cudaSuccess)
+        return cuda_status(e);
+    info.smem_optin = v;
+    if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device)) != cudaSuccess)
+        return cuda_status(e);
+    info.smem_per_sm = v;
+    if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMajor, device)) != cudaSuccess)
+        return cuda_status(e);
+    info.cc_major = v;
+    if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMinor, device)) != cudaSuccess)
+        return cuda_status(e);
+    info.cc_minor = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrClockRate, device) == cudaSuccess) info.clock_khz = v;
+    if (info.cc_major < 10) return CREDIT_ERR_UNSUPPORTED;  // needs Blackwell (sm_103a build)
+    if ((e = cudaMalloc(&d.ws, kWorkspaceFloats * sizeof(float))) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMalloc(&d.err, 64)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemset(d.err, 0, 64)) != cudaSuccess) return cuda_status(e);
+    info.ws_floats = kWorkspaceFloats;
+    d.info = info;
+    d.ready.store(true);
+    return CREDIT_OK;
+}
+
+int64_t credit_slice_capacity(credit_dtype dtype) {
+    const DeviceInfo *di = device_info(current_device());
+    if (!di || dtype < 0 || dtype > 2) return 0;
+    const long long bytes = di->smem_optin - kCtrlBytes - kEdgeBytes;
+    return bytes / dtype_size(dtype);
+}
+
+credit_status credit_device_error(cudaStream_t stream) {
+    const int dev = current_device();
+    if (dev < 0 || !g_dev[dev].ready.load()) return CREDIT_ERR_NOT_INITIALIZED;
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    unsigned w = 0;
+    if ((e = cudaMemcpy(&w, g_dev[dev].err, sizeof(w), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_status(e);
+    if (w != 0 && (e = cudaMemset(g_dev[dev].err, 0, sizeof(w))) != cudaSuccess) return cuda_status(e);
+    return w ? CREDIT_ERR_TIMEOUT : CREDIT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ launching
+namespace credit {
+
+credit_status validate_args(const credit_args *a) {
+    if (!a) return CREDIT_ERR_INVALID_ARG;
+    if (a->op < 0 || a->op > 3) return CREDIT_ERR_INVALID_ARG;
+    if (a->in_dtype < 0 || a->in_dtype > 2 || a->out_dtype < 0 || a->out_dtype > 2) return CREDIT_ERR_INVALID_ARG;
+    if (a->rows < 0 || a->cols <= 0) return CREDIT_ERR_INVALID_ARG;
+    if (a->rows == 0) return CREDIT_OK;
+    if (!a->in || !a->out) return CREDIT_ERR_INVALID_ARG;
+    const long long ld_in = a->ld_in ? a->ld_in : a->cols;
+    const long long ld_out = a->ld_out ? a->ld_out : a->cols;
+    if (ld_in < a->cols || (a->op != OP_LSE && ld_out < a->cols)) return CREDIT_ERR_INVALID_ARG;
+    if (a->in_dtype == DT_E4M3 && !a->in_scale) return CREDIT_ERR_INVALID_ARG;
+    const int tout = a->op == OP_LSE ? DT_F32 : a->out_dtype;
+    if (a->op != OP_LSE && tout == DT_E4M3 && !a->out_scale) return CREDIT_ERR_INVALID_ARG;
+    const uintptr_t ip = reinterpret_cast<uintptr_t>(a->in), op = reinterpret_cast<uintptr_t>(a->out);
+    if (ip % dtype_size(a->in_dtype) || op % dtype_size(tout)) return CREDIT_ERR_INVALID_ARG;
+    if ((a->gamma && reinterpret_cast<uintptr_t>(a->gamma) % 4) ||
+        (a->beta && reinterpret_cast<uintptr_t>(a->beta) % 4))
+        return CREDIT_ERR_INVALID_ARG;
+    if (a->op == OP_LSE && a->in == a->out) return CREDIT_ERR_INVALID_ARG;
+    return CREDIT_OK;
+}
+
+// Is `p` legal for the arguments on this device (Eq. 3 and scheduling)?
+credit_status check_plan(int device, const credit_args *a, const credit_plan_t *p) {
+    const DeviceInfo *di = device_info(device);
+    if (!di) return CREDIT_ERR_NOT_INITIALIZED;
+    const int isz = dtype_size(a->in_dtype);
+    const int tout = a->op == OP_LSE ? DT_F32 : a->out_dtype;
+    const int threads = p->threads;
+    if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32)) return CREDIT_ERR_UNSUPPORTED;
+    switch (p->path) {
+    case CREDIT_PATH_ONE_CTA:
+    case CREDIT_PATH_CLUSTER: {
+        const int P = p->path == CREDIT_PATH_ONE_CTA ? 1 : p->cluster_size;
+        if (P < 1 || P > kMaxCluster) return CREDIT_ERR_UNSUPPORTED;
+        if (p->path == CREDIT_PATH_CLUSTER && P < 2) return CREDIT_ERR_UNSUPPORTED;
+        const long long smem = staged_smem_bytes(a->cols, isz, P);
+        if (smem > di->smem_optin) return CREDIT_ERR_UNSUPPORTED;  // Eq. 3
+        const long long body = smem - kCtrlBytes - kEdgeBytes;
+        if (body > static_cast<long long>(kMaxChunks) * kChunkBytes) return CREDIT_ERR_UNSUPPORTED;
+        const int t = threads ? threads : default_staged_threads(staged_groups_per_cta(a->cols, isz, P));
+        if (staged_max_clusters(device, a->op, a->in_dtype, tout, P, t, smem) <= 0) return CREDIT_ERR_UNSUPPORTED;
+        return CREDIT_OK;
+    }
+    case CREDIT_PATH_TWO_PASS: {
+        const int G = p->ctas_per_row;
+        if (G < 1 || G > 4096) return CREDIT_ERR_UNSUPPORTED;
+        if (G > 1 && static_cast<size_t>(G) * 4 > di->ws_floats) return CREDIT_ERR_UNSUPPORTED;
+        return CREDIT_OK;
+    }
+    default: return CREDIT_ERR_UNSUPPORTED;
+    }
+}
+
+static RowArgs make_row_args(const credit_args *a, unsigned *err, float *ws) {
+    RowArgs r;
+    r.in = static_cast<const unsigned char *>(a->in);
+    r.out = static_cast<unsigned char *>(a->out);
+    r.rows = a->rows;
+    r.cols = a->cols;
+    r.ld_in = a->ld_in ? a->ld_in : a->cols;
+    r.ld_out = a->ld_out ? a->ld_out : a->cols;
+    r.in_scale = a->in_scale;
+    r.out_scale = a->out_scale;
+    r.gamma = a->gamma;
+    r.beta = a->beta;
+    const float dflt = a->op == OP_RMS ? 1e-6f : 1e-5f;
+    r.eps = a->eps < 0.0f ? dflt : a->eps;
+    r.err = err;
+    r.ws = ws;
+    r.G = 1;
+    r.row0 = 0;
+    return r;
+}
+
+// Shift the row pointers of `r` by `r0` rows (chunked launches).
+static RowArgs rows_from(const RowArgs &base, long long r0, long long n, int isz, int osz, bool lse) {
+    RowArgs r = base;
+    r.in = base.in + r0 * base.ld_in * isz;
+    r.out = lse ? base.out + r0 * 4 : base.out + r0 * base.ld_out * osz;
+    if (base.in_scale) r.in_scale = base.in_scale + r0;
+    if (base.out_scale) r.out_scale = base.out_scale + r0;
+    r.rows = n;
+    return r;
+}
+
+static cudaError_t launch(const void *fn, dim3 grid, dim3 block, size_t smem, int cluster, cudaStream_t s,
+                          void **args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    if (cluster > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+std::atomic<long long> g_launch_count{0};
+
+credit_status run_with_plan(int device, const credit_args *a, const credit_plan_t *p, cudaStream_t s) {
+    DeviceState &d = g_dev[device];
+    const int tin = a->in_dtype;
+    const int tout = a->op == OP_LSE ? DT_F32 : a->out_dtype;
+    const int isz = dtype_size(tin), osz = dtype_size(tout);
+    const bool lse = a->op == OP_LSE;
+    KernelSet ks;
+    if (!kernel_set(a->op, tin, tout, &ks)) return CREDIT_ERR_UNSUPPORTED;
+    const RowArgs base = make_row_args(a, d.err, d.ws);
+    const long long rows = a->rows;
+
+    if (p->path == CREDIT_PATH_ONE_CTA || p->path == CREDIT_PATH_CLUSTER) {
+        const int P = p->path == CREDIT_PATH_ONE_CTA ? 1 : p->cluster_size;
+        const long long smem = staged_smem_bytes(a->cols, isz, P);
+        const int threads = p->threads ? p->threads : default_staged_threads(staged_groups_per_cta(a->cols, isz, P));
+        credit_status st = prepare_kernel(d, ks.staged, true);
+        if (st != CREDIT_OK) return st;
+        const long long max_rows = (0x7FFFFFFFLL / P);
+        for (long long r0 = 0; r0 < rows; r0 += max_rows) {
+            const long long n = rows - r0 < max_rows ? rows - r0 : max_rows;
+            RowArgs r = rows_from(base, r0, n, isz, osz, lse);
+            void *args[] = {&r};
+            cudaError_t e = launch(ks.staged, dim3(static_cast<unsigned>(P * n)), dim3(threads),
+                                   static_cast<size_t>(smem), P, s, args);
+            if (e != cudaSuccess) return cuda_status(e);
+            g_launch_count.fetch_add(1);
+        }
+        return CREDIT_OK;
+    }
+
+    // TWO_PASS
+    const int G = p->ctas_per_row;
+    const int threads = p->threads ? p->threads : 512;
+    if (G == 1) {
+        credit_status st = prepare_kernel(d, ks.tp_fused, false);
+        if (st != CREDIT_OK) return st;
+        const long long max_rows = 0x7FFFFFFFLL;
+        for (long long r0 = 0; r0 < rows; r0 += max_rows) {
+            const long long n = rows - r0 < max_rows ? rows - r0 : max_rows;
+            RowArgs r = rows_from(base, r0, n, isz, osz, lse);
+            void *args[] = {&r};
+            cudaError_t e = launch(ks.tp_fused, dim3(static_cast<unsigned>(n)), dim3(threads), 0, 1, s, args);
+            if (e != cudaSuccess) return cuda_status(e);
+            g_launch_count.fetch_add(1);
+        }
+        return CREDIT_OK;
+    }
+    const long long cap_rows = static_cast<long long>(d.info.ws_floats / (static_cast<size_t>(G) * 4));
+    const long long max_rows = cap_rows < 0x7FFFFFFFLL / G ? cap_rows : 0x7FFFFFFFLL / G;
+    const bool fp8_stage = (a->op == OP_LN || a->op == OP_RMS) && tout == DT_E4M3;
+    for (long long r0 = 0; r0 < rows; r0 += max_rows) {
+        const long long n = rows - r0 < max_rows ? rows - r0 : max_rows;
+        RowArgs r = rows_from(base, r0, n, isz, osz, lse);
+        r.G = G;
+        void *args[] = {&r};
+        const dim3 grid(static_cast<unsigned>(G * n));
+        cudaError_t e = launch(ks.tp_stats, grid, dim3(threads), 0, 1, s, args);
+        if (e != cudaSuccess) return cuda_status(e);
+        g_launch_count.fetch_add(1);
+        if (lse) {
+            long long nn = n;
+            void *args2[] = {&r, &nn};
+            e = launch(ks.tp_lse_final, dim3(static_cast<unsigned>((n + 255) / 256)), dim3(256), 0, 1, s, args2);
+            if (e != cudaSuccess) return cuda_status(e);
+            g_launch_count.fetch_add(1);
+            continue;
+        }
+        if (fp8_stage) {
+            e = launch(ks.tp_amax, grid, dim3(threads), 0, 1, s, args);
+            if (e != cudaSuccess) return cuda_status(e);
+            g_launch_count.fetch_add(1);
+        }
+        e = launch(ks.tp_apply, grid, dim3(threads), 0, 1, s, args);
+        if (e != cudaSuccess) return cuda_status(e);
+        g_launch_count.fetch_add(1);
+    }
+    return CREDIT_OK;
+}
+
+credit_status ensure_init(int *device_out, cudaStream_t s) {
+    const int dev = current_device();
+    if (dev < 0 || dev >= kMaxDevices) return CREDIT_ERR_CUDA;
+    *device_out = dev;
+    if (g_dev[dev].ready.load()) return CREDIT_OK;
+    if (stream_capturing(s)) return CREDIT_ERR_CAPTURE;  // init allocates
+    return credit_init(dev);
+}
+
+}  // namespace credit
+
+extern "C" {
+
+credit_status credit_run_ex(const credit_args *args, const credit_plan_t *plan, cudaStream_t stream) {
+    credit_status st = validate_args(args);
+    if (st != CREDIT_OK) return st;
+    if (args->rows == 0) return CREDIT_OK;
+    int dev = 0;
+    if ((st = ensure_init(&dev, stream)) != CREDIT_OK) return st;
+    credit_plan_t chosen;
+    if (plan) {
+        chosen = *plan;
+    } else {
+        st = credit_plan_ex(static_cast<credit_op>(args->op), args->rows, args->cols,
+                            static_cast<credit_dtype>(args->in_dtype),
+                            static_cast<credit_dtype>(args->op == OP_LSE ? DT_F32 : args->out_dtype), &chosen);
+        if (st != CREDIT_OK) return st;
+    }
+    if ((st = check_plan(dev, args, &chosen)) != CREDIT_OK) return st;
+    return run_with_plan(dev, args, &chosen, stream);
+}
+
+static credit_status simple(credit_op op, const void *in, void *out, int64_t rows, int64_t cols, credit_dtype dtype,
+                            cudaStream_t stream) {
+    if (dtype == CREDIT_FP8_E4M3) return CREDIT_ERR_INVALID_ARG;  // scales need credit_run_ex
+    credit_args a;
+    std::memset(&a, 0, sizeof(a));
+    a.op = op;
+    a.in = in;
+    a.out = out;
+    a.rows = rows;
+    a.cols = cols;
+    a.in_dtype = dtype;
+    a.out_dtype = op == CREDIT_OP_LOGSUMEXP ? CREDIT_F32 : dtype;
+    a.eps = -1.0f;
+    return credit_run_ex(&a, nullptr, stream);
+}
+
+credit_status credit_softmax(const void *in, void *out, int64_t rows, int64_t cols, credit_dtype dtype,
+                             cudaStream_t stream) {
+    return simple(CREDIT_OP_SOFTMAX, in, out, rows, cols, dtype, stream);
+}
+credit_status credit_logsumexp(const void *in, void *out, int64_t rows, int64_t cols, credit_dtype dtype,
+                               cudaStream_t stream) {
+    return simple(CREDIT_OP_LOGSUMEXP, in, out, rows, cols, dtype, stream);
+}
+credit_status credit_layernorm(const void *in, void *out, int64_t rows, int64_t cols, credit_dtype dtype,
+                               cudaStream_t stream) {
+    return simple(CREDIT_OP_LAYERNORM, in, out, rows, cols, dtype, stream);
+}
+credit_status credit_rmsnorm(const void *in, void *out, int64_t rows, int64_t cols, credit_dtype dtype,
+                             cudaStream_t stream) {
+    return simple(CREDIT_OP_RMSNORM, in, out, rows, cols, dtype, stream);
+}
+
+// Number of kernel launches this library has issued in this process (all
+// devices).  Lets a caller count the launches inside a timed region.
+long long credit_launch_count(void) { return g_launch_count.load(); }
+
+}  // extern "C"

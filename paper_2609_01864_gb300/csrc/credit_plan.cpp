@@ -1,0 +1,126 @@
+// credit_plan.cpp -- plan selection (CREDIT Sec. III-D).
+//
+// Candidates for a shape: the one-CTA staged path (P = 1), the cluster path
+// for every P in {2, 4, 8, 16} that passes the capacity check of Eq. 3 and
+// can be scheduled (max active clusters > 0), and the two-pass global-reread
+// path.  Without calibration data the built-in heuristic below is used; the
+// analytic model of Eq. 7-9 and the learned model plug in through
+// credit_model.cpp.
+#include <cstdlib>
+#include <initializer_list>
+#include <cstring>
+
+#include "credit_host.h"
+#include "credit_model.h"
+
+namespace credit {
+
+static bool env_force(credit_plan_t *p, int op, long long rows, long long cols, int tin) {
+    const char *fp = std::getenv("CREDIT_FORCE_PATH");
+    if (!fp || !*fp) return false;
+    std::memset(p, 0, sizeof(*p));
+    const char *fP = std::getenv("CREDIT_FORCE_P");
+    const char *fG = std::getenv("CREDIT_FORCE_G");
+    const char *fT = std::getenv("CREDIT_FORCE_THREADS");
+    p->threads = fT ? std::atoi(fT) : 0;
+    p->source = 2;
+    const int isz = dtype_size(tin);
+    if (!std::strcmp(fp, "one_cta")) {
+        p->path = CREDIT_PATH_ONE_CTA;
+        p->cluster_size = 1;
+        p->ctas_per_row = 1;
+        p->smem_bytes = staged_smem_bytes(cols, isz, 1);
+    } else if (!std::strcmp(fp, "cluster")) {
+        p->path = CREDIT_PATH_CLUSTER;
+        p->cluster_size = fP ? std::atoi(fP) : 4;
+        p->ctas_per_row = p->cluster_size;
+        p->smem_bytes = staged_smem_bytes(cols, isz, p->cluster_size);
+    } else if (!std::strcmp(fp, "two_pass")) {
+        p->path = CREDIT_PATH_TWO_PASS;
+        p->cluster_size = 1;
+        p->ctas_per_row = fG ? std::atoi(fG) : 1;
+    } else {
+        return false;
+    }
+    (void)op;
+    (void)rows;
+    return true;
+}
+
+// Split factor for the two-pass path: enough CTAs to cover the GPU several
+// times over, but no CTA with fewer than ~1024 16-byte groups.
+int two_pass_split(int sm_count, long long rows, long long cols, int isz) {
+    const long long target = 4LL * sm_count;
+    if (rows >= target) return 1;
+    long long G = (target + rows - 1) / rows;
+    const long long groups = (cols * isz) / 16;
+    long long gmax = groups / 1024;
+    if (gmax < 1) gmax = 1;
+    if (G > gmax) G = gmax;
+    if (G > 1024) G = 1024;
+    return static_cast<int>(G < 1 ? 1 : G);
+}
+
+void heuristic_plan(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin, int tout,
+                    credit_plan_t *p) {
+    std::memset(p, 0, sizeof(*p));
+    p->source = 3;
+    const int isz = dtype_size(tin);
+    if (op != 1) {
+        // Smallest P whose slice is <= 64 KiB, else the smallest P that fits.
+        int pick = 0;
+        for (int pass = 0; pass < 2 && !pick; ++pass) {
+            for (int P : {1, 2, 4, 8, 16}) {
+                const long long smem = staged_smem_bytes(cols, isz, P);
+                if (smem > di.smem_optin) continue;
+                if (pass == 0 && smem > 65536 + 1056) continue;
+                const long long gpc = staged_groups_per_cta(cols, isz, P);
+                long long t = (gpc + 7) / 8;
+                t = (t + 31) / 32 * 32;
+                t = t < 64 ? 64 : (t > 1024 ? 1024 : t);
+                if (staged_max_clusters(device, op, tin, tout, P, static_cast<int>(t), smem) <= 0) continue;
+                pick = P;
+                break;
+            }
+        }
+        if (pick) {
+            p->path = pick == 1 ? CREDIT_PATH_ONE_CTA : CREDIT_PATH_CLUSTER;
+            p->cluster_size = pick;
+            p->ctas_per_row = pick;
+            p->smem_bytes = staged_smem_bytes(cols, isz, pick);
+            return;
+        }
+    }
+    p->path = CREDIT_PATH_TWO_PASS;
+    p->cluster_size = 1;
+    p->ctas_per_row = two_pass_split(di.sm_count, rows, cols, isz);
+}
+
+}  // namespace credit
+
+using namespace credit;
+
+extern "C" {
+
+credit_status credit_plan_ex(credit_op op, int64_t rows, int64_t cols, credit_dtype in_dtype, credit_dtype out_dtype,
+                             credit_plan_t *out) {
+    if (!out || op < 0 || op > 3 || in_dtype < 0 || in_dtype > 2 || out_dtype < 0 || out_dtype > 2)
+        return CREDIT_ERR_INVALID_ARG;
+    if (rows < 0 || cols <= 0) return CREDIT_ERR_INVALID_ARG;
+    const int tout = op == CREDIT_OP_LOGSUMEXP ? 0 : out_dtype;
+    if (env_force(out, op, rows, cols, in_dtype)) return CREDIT_OK;
+    int dev = 0;
+    credit_status st = ensure_init(&dev, nullptr);
+    if (st != CREDIT_OK) return st;
+    const DeviceInfo *di = device_info(dev);
+    if (!di) return CREDIT_ERR_NOT_INITIALIZED;
+    if (model_plan(*di, dev, op, rows, cols, in_dtype, tout, out)) return CREDIT_OK;
+    heuristic_plan(*di, dev, op, rows, cols, in_dtype, tout, out);
+    return CREDIT_OK;
+}
+
+credit_status credit_plan(credit_op op, int64_t rows, int64_t cols, credit_dtype dtype, credit_plan_t *out) {
+    return credit_plan_ex(op, rows, cols, dtype, op == CREDIT_OP_LOGSUMEXP ? CREDIT_F32 : dtype, out);
+}
+
+}  // extern "C"

@@ -1,0 +1,299 @@
+// credit_prim.cuh -- sm_103a device primitives used by the row kernels.
+//
+// Inline-PTX wrappers for the pieces of the cluster protocol (CREDIT
+// Sec. III-C): bulk-async global->shared copies completed on an mbarrier
+// (each CTA stages only its own slice, never a multicast), DSMEM address
+// mapping (mapa) and remote stores (st.shared::cluster), and the split
+// cluster barrier (barrier.cluster.arrive / wait).  Every spin on an mbarrier
+// is bounded by a wall-clock limit; a wait that gives up sets a bit in the
+// caller-supplied device error word and returns, so a fault never hangs the
+// GPU.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+namespace credit {
+
+enum DType : int { DT_F32 = 0, DT_BF16 = 1, DT_E4M3 = 2 };
+enum Op : int { OP_SOFTMAX = 0, OP_LSE = 1, OP_LN = 2, OP_RMS = 3 };
+
+// Error-word bits (read back by credit_device_error).
+enum : unsigned { ERR_TMA_TIMEOUT = 1u, ERR_BAD_LAUNCH = 2u };
+
+// Wall-clock limit of any bounded wait, in nanoseconds (2 s).
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------------ mbarrier
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for phase `parity` of `bar`.  Returns false (and flags the
+// error word) if the phase did not complete within kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_timer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
+            if (err) atomicOr(err, ERR_TMA_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// ------------------------------------------------------------ bulk async copy
+// Global -> this CTA's shared memory, completion counted in bytes on `bar`.
+// dst and src must be 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ------------------------------------------------------------ cluster / DSMEM
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_nctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// Address of the same shared-memory offset inside CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_v2f32(uint32_t addr, float a, float b) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
+}
+__device__ __forceinline__ float ld_cluster_f32(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+// Split cluster barrier.  All threads of every CTA execute these.
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------ math
+// 2^x on the SFU (ex2.approx, subnormal results kept).  exp(x) = 2^(x*log2 e).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float kLog2e = 1.4426950408889634f;
+__device__ __forceinline__ float exp_fast(float x) { return ex2_approx(x * kLog2e); }
+
+// ------------------------------------------------------------ element formats
+template <int DT> struct Fmt;
+template <> struct Fmt<DT_F32> {
+    static constexpr int size = 4;
+    static constexpr int V = 4;   // elements per 16-byte group
+};
+template <> struct Fmt<DT_BF16> {
+    static constexpr int size = 2;
+    static constexpr int V = 8;
+};
+template <> struct Fmt<DT_E4M3> {
+    static constexpr int size = 1;
+    static constexpr int V = 16;
+};
+
+// Decode one 16-byte group (already loaded as uint4) into floats.
+template <int DT>
+__device__ __forceinline__ void decode_group(const uint4 &w, float (&f)[Fmt<DT>::V], float scale) {
+    if constexpr (DT == DT_F32) {
+        f[0] = __uint_as_float(w.x);
+        f[1] = __uint_as_float(w.y);
+        f[2] = __uint_as_float(w.z);
+        f[3] = __uint_as_float(w.w);
+    } else if constexpr (DT == DT_BF16) {
+        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            f[2 * k] = __uint_as_float(u[k] << 16);
+            f[2 * k + 1] = __uint_as_float(u[k] & 0xFFFF0000u);
+        }
+    } else {
+        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                __nv_fp8x2_storage_t pair = static_cast<__nv_fp8x2_storage_t>((u[k] >> (16 * h)) & 0xFFFFu);
+                __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
+                float2 ff = __half22float2(*reinterpret_cast<__half2 *>(&hr));
+                f[4 * k + 2 * h] = ff.x * scale;
+                f[4 * k + 2 * h + 1] = ff.y * scale;
+            }
+        }
+    }
+}
+
+// Decode a single element from raw storage.
+template <int DT>
+__device__ __forceinline__ float decode_one(const unsigned char *p, float scale) {
+    if constexpr (DT == DT_F32) {
+        return *reinterpret_cast<const float *>(p);
+    } else if constexpr (DT == DT_BF16) {
+        return __uint_as_float(static_cast<uint32_t>(*reinterpret_cast<const uint16_t *>(p)) << 16);
+    } else {
+        __half_raw hr = __nv_cvt_fp8_to_halfraw(static_cast<__nv_fp8_storage_t>(*p), __NV_E4M3);
+        return __half2float(*reinterpret_cast<__half *>(&hr)) * scale;
+    }
+}
+
+// Encode / store one element.
+template <int DT>
+__device__ __forceinline__ void store_one(unsigned char *p, float v) {
+    if constexpr (DT == DT_F32) {
+        *reinterpret_cast<float *>(p) = v;
+    } else if constexpr (DT == DT_BF16) {
+        __nv_bfloat16 b = __float2bfloat16_rn(v);
+        *reinterpret_cast<__nv_bfloat16 *>(p) = b;
+    } else {
+        *p = static_cast<unsigned char>(__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3));
+    }
+}
+
+// Pack V floats into the storage bytes of DT (V * size bytes, V*size % 4 == 0).
+template <int DT, int V>
+__device__ __forceinline__ void pack_words(const float (&y)[V], uint32_t (&w)[(V * Fmt<DT>::size) / 4]) {
+    if constexpr (DT == DT_F32) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) w[k] = __float_as_uint(y[k]);
+    } else if constexpr (DT == DT_BF16) {
+#pragma unroll
+        for (int k = 0; k < V / 2; ++k) {
+            __nv_bfloat162 b = __floats2bfloat162_rn(y[2 * k], y[2 * k + 1]);
+            w[k] = *reinterpret_cast<uint32_t *>(&b);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < V / 4; ++k) {
+            uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(y[4 * k], y[4 * k + 1]), __NV_SATFINITE, __NV_E4M3);
+            uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(y[4 * k + 2], y[4 * k + 3]), __NV_SATFINITE, __NV_E4M3);
+            w[k] = (lo & 0xFFFFu) | (hi << 16);
+        }
+    }
+}
+
+// Store V outputs at p.  vec: p is aligned to min(16, V*size) bytes.
+template <int DT, int V>
+__device__ __forceinline__ void store_group(unsigned char *p, const float (&y)[V], bool vec) {
+    constexpr int bytes = V * Fmt<DT>::size;
+    if (vec) {
+        uint32_t w[bytes / 4];
+        pack_words<DT, V>(y, w);
+        if constexpr (bytes >= 16) {
+#pragma unroll
+            for (int k = 0; k < bytes / 16; ++k)
+                *reinterpret_cast<uint4 *>(p + 16 * k) = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+        } else if constexpr (bytes == 8) {
+            *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+        } else {
+            *reinterpret_cast<uint32_t *>(p) = w[0];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) store_one<DT>(p + k * Fmt<DT>::size, y[k]);
+    }
+}
+
+// ------------------------------------------------------------ global loads
+__device__ __forceinline__ uint4 ld_global_v4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint4 ld_global_stream_v4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// ------------------------------------------------------------ warp/block reductions
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Deterministic block all-reduce (sum or max) through `red` (>= 33 floats).
+// Every thread returns the same value.  Contains two __syncthreads.
+template <bool MAX>
+__device__ __forceinline__ float block_allreduce(float v, float *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = MAX ? warp_max(v) : warp_sum(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        float t = lane < nw ? red[lane] : (MAX ? -INFINITY : 0.0f);
+        t = MAX ? warp_max(t) : warp_sum(t);
+        if (lane == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+}  // namespace credit

@@ -1,0 +1,806 @@
+// credit_rows.cuh -- row kernels of the reduction-reuse ops (CREDIT Sec. III).
+//
+// Op model (Eq. 1): a row of N elements is reduced to q scalar statistics per
+// stage, then every element is mapped through h.
+//   softmax    stage 1: q = 2, (m, s): m = max x, s = sum exp(x - m)
+//              h(x) = exp(x - m) / s
+//   logsumexp  the softmax statistics; the row's output is m + ln s (no h)
+//   layernorm  stage 1: q = 2, (mean, M2) merged with Chan's formula
+//              h(x) = (x - mean) * rsqrt(M2 / N + eps) * gamma + beta
+//   rmsnorm    stage 1: q = 1, sum x^2;  h(x) = x * rsqrt(sum/N + eps) * gamma
+//   FP8 output of layernorm / rmsnorm adds stage 2: q = 1, amax |h(x)|, and
+//   writes codes h(x) * 448 / amax with the row scale amax / 448.  Softmax
+//   needs no extra stage: its amax is 1 / s in closed form.
+//
+// Slicing (Eq. 2).  A row is cut on the 16-byte grid of its own address: the
+// elements before the first 16-byte boundary (the "head", < 16 bytes) belong
+// to CTA 0, the elements after the last full 16-byte group (the "tail") to CTA
+// P-1, and the G full groups in between are split evenly, CTA c taking groups
+// [G*c/P, G*(c+1)/P).  The same rule with P -> ctas_per_row slices rows in
+// the split-row two-pass path.
+//
+// Kernels
+//   k_staged     one row per cluster of P CTAs (P = 1: the one-CTA path).
+//                Each CTA stages its slice into its own shared memory with
+//                cp.async.bulk (16 KiB chunks, one mbarrier each, so the
+//                first reduction sweep overlaps the copy), reduces locally
+//                (threads -> warp shuffles -> shared memory), pushes its
+//                partials into every peer's slot array over DSMEM (Eq. 5:
+//                one of the first P threads per destination), crosses one
+//                split cluster barrier, combines the P local slots in fixed
+//                order c = 0..P-1 (so every CTA holds bit-identical
+//                statistics), and writes its output segment from shared
+//                memory (Sec. III-C, "reuse").
+//   k_tp_fused   the global-reread baseline with one CTA per row: a
+//                statistics sweep over HBM, then a sweep that rereads the row
+//                (Sec. IV-A; Eq. 4 with b_reread = input bytes).
+//   k_tp_stats / k_tp_amax / k_tp_apply / k_tp_lse_final
+//                the same baseline with G CTAs per row: partials go to a
+//                device workspace and the next launch is the barrier; no
+//                kernel ever waits on another CTA.
+#pragma once
+
+#include "credit_prim.cuh"
+
+namespace credit {
+
+struct RowArgs {
+    const unsigned char *in;
+    unsigned char *out;
+    long long rows, cols, ld_in, ld_out;  // strides in elements
+    const float *in_scale;                // FP8 input: per-row scale
+    float *out_scale;                     // FP8 output: per-row scale
+    const float *gamma, *beta;
+    float eps;
+    unsigned *err;                        // device error word
+    float *ws;                            // two-pass partials [row - row0][G][4]
+    int G;                                // CTAs per row of the two-pass path
+    long long row0;                       // first row of this launch
+};
+
+constexpr int kMaxCluster = 16;
+constexpr int kMaxChunks = 16;
+constexpr int kChunkBytes = 16384;
+// Shared-memory control area of k_staged:
+//   [0, 128)     mbarriers, one per staged chunk
+//   [128, 640)   DSMEM slots [2 stages][16 sources][4 floats]
+//   [640, 1024)  block-reduction scratch
+constexpr int kCtrlBytes = 1024;
+constexpr int kEdgeBytes = 32;  // 16-byte head slot + 16-byte tail slot of the image
+
+struct RowSlice {
+    long long h0;          // head elements (rank 0)
+    long long G;           // full 16-byte groups after the head
+    long long t0;          // tail elements (rank P-1)
+    long long g_lo, g_hi;  // this CTA's groups
+};
+
+__host__ __device__ __forceinline__ RowSlice make_slice(uintptr_t row_addr, long long N, int isz, int P, int c) {
+    const int V = 16 / isz;
+    const long long mis = static_cast<long long>(row_addr & 15u);
+    long long h0 = mis ? (16 - mis) / isz : 0;
+    if (h0 > N) h0 = N;
+    const long long rest = N - h0;
+    RowSlice s;
+    s.h0 = h0;
+    s.G = rest / V;
+    s.t0 = rest - s.G * V;
+    s.g_lo = s.G * c / P;
+    s.g_hi = s.G * (c + 1) / P;
+    return s;
+}
+
+// Elements owned by CTA c (of P) for a row with h0 / G / t0.
+__host__ __device__ __forceinline__ long long slice_count(const RowSlice &s, int V, int P, int c) {
+    const long long lo = s.G * c / P, hi = s.G * (c + 1) / P;
+    return (hi - lo) * V + (c == 0 ? s.h0 : 0) + (c == P - 1 ? s.t0 : 0);
+}
+
+// ------------------------------------------------------------------ stats
+// Per-CTA partials are two floats for every op:
+//   softmax / lse: (m_c, s_c)   layernorm: (mean_c, M2_c)   rmsnorm: (ss_c, 0)
+// Row statistics after the combine:
+//   softmax / lse: (M, S)       layernorm: (mean, rstd)     rmsnorm: (rstd, 0)
+struct Stats {
+    float a, b;
+};
+
+// Combine partials p[c*stride + 0/1], c = 0..P-1, in fixed order.
+template <int OP>
+__device__ __forceinline__ Stats combine_partials(const float *p, int stride, int P, const RowSlice &s, int V,
+                                                  long long N, float eps) {
+    Stats st;
+    if constexpr (OP == OP_SOFTMAX || OP == OP_LSE) {
+        float M = -INFINITY;
+        for (int c = 0; c < P; ++c) M = fmaxf(M, p[c * stride]);
+        float S = 0.0f;
+        for (int c = 0; c < P; ++c) {
+            const float sc = p[c * stride + 1];
+            if (sc > 0.0f) S += sc * exp_fast(p[c * stride] - M);
+        }
+        st.a = M;
+        st.b = S;
+    } else if constexpr (OP == OP_LN) {
+        float n = 0.0f, mu = 0.0f, m2 = 0.0f;
+        for (int c = 0; c < P; ++c) {
+            const float nb = static_cast<float>(slice_count(s, V, P, c));
+            if (nb == 0.0f) continue;
+            const float nn = n + nb;
+            const float d = p[c * stride] - mu;
+            mu += d * (nb / nn);
+            m2 += p[c * stride + 1] + d * d * (n * nb / nn);
+            n = nn;
+        }
+        st.a = mu;
+        st.b = rsqrtf(m2 / static_cast<float>(N) + eps);
+    } else {
+        float ss = 0.0f;
+        for (int c = 0; c < P; ++c) ss += p[c * stride];
+        st.a = rsqrtf(ss / static_cast<float>(N) + eps);
+        st.b = 0.0f;
+    }
+    return st;
+}
+
+// h(x) for LayerNorm / RMSNorm.
+template <int OP>
+__device__ __forceinline__ float norm_h(float x, const Stats &st, float g, float b) {
+    if constexpr (OP == OP_LN) return (x - st.a) * st.b * g + b;
+    else return x * st.a * g;
+}
+
+template <int V>
+__device__ __forceinline__ void load_affine(const float *p, long long i0, bool vec, float dflt, float (&v)[V]) {
+    if (p == nullptr) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) v[k] = dflt;
+    } else if (vec) {
+#pragma unroll
+        for (int k = 0; k < V / 4; ++k) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(p + i0) + k);
+            v[4 * k] = t.x;
+            v[4 * k + 1] = t.y;
+            v[4 * k + 2] = t.z;
+            v[4 * k + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) v[k] = __ldg(p + i0 + k);
+    }
+}
+
+__device__ __forceinline__ void copy_raw(unsigned char *dst, const unsigned char *src, int isz) {
+    if (isz == 4) *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(src);
+    else if (isz == 2) *reinterpret_cast<uint16_t *>(dst) = *reinterpret_cast<const uint16_t *>(src);
+    else *dst = *src;
+}
+
+// ======================================================================
+// Staged kernel: cluster path (P > 1) and one-CTA path (P == 1).
+// Grid: 1-D, P * rows CTAs; cluster dims (P, 1, 1); row = blockIdx.x / P.
+// ======================================================================
+template <int OP, int TIN, int TOUT>
+__global__ void __launch_bounds__(1024, 1) k_staged(const RowArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    float *slots = reinterpret_cast<float *>(smem + 128);
+    float *red = reinterpret_cast<float *>(smem + 640);
+    unsigned char *img = smem + kCtrlBytes;
+
+    constexpr int isz = Fmt<TIN>::size, V = Fmt<TIN>::V;
+    constexpr int osz = Fmt<TOUT>::size;
+    constexpr bool kFp8Stage = (TOUT == DT_E4M3) && (OP == OP_LN || OP == OP_RMS);
+    constexpr bool kCacheExp = (OP == OP_SOFTMAX) && (TIN == DT_F32);
+
+    const int P = static_cast<int>(cluster_nctarank());
+    const int c = P > 1 ? static_cast<int>(cluster_ctarank()) : 0;
+    const long long row = blockIdx.x / P;
+    // Start barrier, split: arrive now, wait just before the first remote
+    // store, so that every peer is known to be running when it is written.
+    if (P > 1) cluster_arrive_relaxed();
+
+    const int tid = threadIdx.x, T = blockDim.x;
+    const long long N = a.cols;
+    const unsigned char *in_row = a.in + row * a.ld_in * isz;
+    const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), N, isz, P, c);
+    const float in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
+    const long long ng = s.g_hi - s.g_lo;
+    const uint32_t body = static_cast<uint32_t>(ng * 16);
+    const int nchunks = static_cast<int>((body + kChunkBytes - 1) / kChunkBytes);
+    const bool own_head = (c == 0), own_tail = (c == P - 1);
+    const long long tail_i0 = s.h0 + s.G * V;  // element index of the first tail element
+    unsigned char *img_body = img + 16;
+
+    if (tid == 0) {
+        for (int k = 0; k < nchunks; ++k) mbar_init(&mbar[k], 1);
+        fence_mbar_init();
+    }
+    // Edges (< 16 bytes each) are copied with plain loads.
+    if (own_head && tid < s.h0) copy_raw(img + 16 - (s.h0 - tid) * isz, in_row + tid * isz, isz);
+    if (own_tail && tid >= 32 && tid - 32 < s.t0)
+        copy_raw(img_body + body + (tid - 32) * isz, in_row + (tail_i0 + tid - 32) * isz, isz);
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned char *src = in_row + s.h0 * isz + s.g_lo * 16;
+        for (int k = 0; k < nchunks; ++k) {
+            const uint32_t off = static_cast<uint32_t>(k) * kChunkBytes;
+            const uint32_t bytes = min(static_cast<uint32_t>(kChunkBytes), body - off);
+            mbar_arrive_expect_tx(&mbar[k], bytes);
+            bulk_g2s(img_body + off, src + off, bytes, &mbar[k]);
+        }
+    }
+
+    // Visit the edge elements owned by this CTA: head by thread 0, tail by
+    // thread T-1 (fixed owners keep the reduction order deterministic).
+    auto edge_ptr = [&](int which, long long k) -> unsigned char * {
+        return which == 0 ? img + 16 - (s.h0 - k) * isz : img_body + body + k * isz;
+    };
+    const long long n_head = (own_head && tid == 0) ? s.h0 : 0;
+    const long long n_tail = (own_tail && tid == T - 1) ? s.t0 : 0;
+
+    // ---------------- stage 1, first local sweep (overlaps the bulk copy)
+    float acc0 = (OP == OP_SOFTMAX || OP == OP_LSE) ? -INFINITY : 0.0f;
+    for (int k = 0; k < nchunks; ++k) {
+        mbar_wait_bounded(&mbar[k], 0, a.err);
+        const long long gb = static_cast<long long>(k) * (kChunkBytes / 16);
+        const long long ge = min(ng, gb + kChunkBytes / 16);
+        for (long long g = gb + tid; g < ge; g += T) {
+            const uint4 w = *reinterpret_cast<const uint4 *>(img_body + g * 16);
+            float f[V];
+            decode_group<TIN>(w, f, in_sc);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                if constexpr (OP == OP_SOFTMAX || OP == OP_LSE) acc0 = fmaxf(acc0, f[j]);
+                else if constexpr (OP == OP_LN) acc0 += f[j];
+                else acc0 = fmaf(f[j], f[j], acc0);
+            }
+        }
+    }
+    for (int e = 0; e < 2; ++e) {
+        const long long cnt = e == 0 ? n_head : n_tail;
+        for (long long k = 0; k < cnt; ++k) {
+            const float x = decode_one<TIN>(edge_ptr(e, k), in_sc);
+            if constexpr (OP == OP_SOFTMAX || OP == OP_LSE) acc0 = fmaxf(acc0, x);
+            else if constexpr (OP == OP_LN) acc0 += x;
+            else acc0 = fmaf(x, x, acc0);
+        }
+    }
+    const long long n_c = slice_count(s, V, P, c);
+    float part0, part1 = 0.0f;
+    if constexpr (OP == OP_SOFTMAX || OP == OP_LSE || OP == OP_LN) {
+        const float r0 = (OP == OP_LN) ? block_allreduce<false>(acc0, red) : block_allreduce<true>(acc0, red);
+        const float center = (OP == OP_LN) ? (n_c > 0 ? r0 / static_cast<float>(n_c) : 0.0f) : r0;
+        // ------------- stage 1, second local sweep over shared memory
+        float acc1 = 0.0f;
+        // A slice whose maximum is -inf contributes exp(...) = 0 everywhere.
+        const bool dead = (OP != OP_LN) && center == -INFINITY;
+        if (!dead || kCacheExp) {
+            for (long long g = tid; g < ng; g += T) {
+                uint4 *pw = reinterpret_cast<uint4 *>(img_body + g * 16);
+                float f[V];
+                decode_group<TIN>(*pw, f, in_sc);
+                if constexpr (OP == OP_LN) {
+#pragma unroll
+                    for (int j = 0; j < V; ++j) {
+                        const float d = f[j] - center;
+                        acc1 = fmaf(d, d, acc1);
+                    }
+                } else {
+                    float e4[V];
+#pragma unroll
+                    for (int j = 0; j < V; ++j) {
+                        e4[j] = dead ? 0.0f : exp_fast(f[j] - center);
+                        acc1 += e4[j];
+                    }
+                    if constexpr (kCacheExp)
+                        *pw = make_uint4(__float_as_uint(e4[0]), __float_as_uint(e4[1]), __float_as_uint(e4[2]),
+                                         __float_as_uint(e4[3]));
+                }
+            }
+            for (int e = 0; e < 2; ++e) {
+                const long long cnt = e == 0 ? n_head : n_tail;
+                for (long long k = 0; k < cnt; ++k) {
+                    unsigned char *pe = edge_ptr(e, k);
+                    const float x = decode_one<TIN>(pe, in_sc);
+                    if constexpr (OP == OP_LN) {
+                        const float d = x - center;
+                        acc1 = fmaf(d, d, acc1);
+                    } else {
+                        const float ev = dead ? 0.0f : exp_fast(x - center);
+                        acc1 += ev;
+                        if constexpr (kCacheExp) *reinterpret_cast<float *>(pe) = ev;
+                    }
+                }
+            }
+        }
+        part0 = center;
+        part1 = block_allreduce<false>(acc1, red);
+    } else {
+        part0 = block_allreduce<false>(acc0, red);
+    }
+
+    // ---------------- DSMEM push all-gather (Eq. 5) and combine
+    Stats st;
+    if (P > 1) {
+        cluster_wait_acquire();  // start barrier: all peers are running
+        if (tid < P) {
+            const uint32_t dst = mapa_shared(smem_addr(&slots[c * 4]), static_cast<uint32_t>(tid));
+            if constexpr (OP == OP_RMS) st_cluster_f32(dst, part0);
+            else st_cluster_v2f32(dst, part0, part1);
+        }
+        cluster_arrive_release();
+        cluster_wait_acquire();
+        st = combine_partials<OP>(slots, 4, P, s, V, N, a.eps);
+    } else {
+        float p1[2] = {part0, part1};
+        st = combine_partials<OP>(p1, 2, 1, s, V, N, a.eps);
+    }
+
+    if constexpr (OP == OP_LSE) {
+        if (c == 0 && tid == 0) reinterpret_cast<float *>(a.out)[row] = st.a + logf(st.b);
+        return;
+    } else {
+        unsigned char *out_row = a.out + row * a.ld_out * osz;
+        const long long i_base = s.h0 + s.g_lo * V;  // element index of this CTA's first group
+        constexpr int vec_bytes = (V * osz) < 16 ? (V * osz) : 16;
+        const bool out_vec = ((reinterpret_cast<uintptr_t>(out_row) + s.h0 * osz) % vec_bytes) == 0;
+        const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + s.h0) & 15u) == 0);
+        const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + s.h0) & 15u) == 0);
+
+        // ------------- stage 2 (FP8 output of the norms): amax |h(x)|
+        float qmul = 1.0f;  // multiplier from y to the stored value
+        if constexpr (kFp8Stage) {
+            float am = 0.0f;
+            for (long long g = tid; g < ng; g += T) {
+                float f[V], gg[V], bb[V];
+                decode_group<TIN>(*reinterpret_cast<const uint4 *>(img_body + g * 16), f, in_sc);
+                load_affine<V>(a.gamma, i_base + g * V, g_vec, 1.0f, gg);
+                load_affine<V>(a.beta, i_base + g * V, b_vec, 0.0f, bb);
+#pragma unroll
+                for (int j = 0; j < V; ++j) am = fmaxf(am, fabsf(norm_h<OP>(f[j], st, gg[j], bb[j])));
+            }
+            for (int e = 0; e < 2; ++e) {
+                const long long cnt = e == 0 ? n_head : n_tail;
+                for (long long k = 0; k < cnt; ++k) {
+                    const long long i = e == 0 ? k : tail_i0 + k;
+                    const float x = decode_one<TIN>(edge_ptr(e, k), in_sc);
+                    const float gg = a.gamma ? a.gamma[i] : 1.0f, bb = a.beta ? a.beta[i] : 0.0f;
+                    am = fmaxf(am, fabsf(norm_h<OP>(x, st, gg, bb)));
+                }
+            }
+            am = block_allreduce<true>(am, red);
+            if (P > 1) {
+                float *slots2 = slots + 64;
+                if (tid < P) st_cluster_f32(mapa_shared(smem_addr(&slots2[c * 4]), static_cast<uint32_t>(tid)), am);
+                cluster_arrive_release();
+                cluster_wait_acquire();
+                am = 0.0f;
+                for (int k = 0; k < P; ++k) am = fmaxf(am, slots2[k * 4]);
+            }
+            qmul = am > 0.0f ? 448.0f / am : 1.0f;
+            if (c == 0 && tid == 0) a.out_scale[row] = am > 0.0f ? am / 448.0f : 1.0f;
+        }
+
+        // ------------- reuse pass: h over the retained slice, write out
+        if constexpr (OP == OP_SOFTMAX) {
+            const float inv = 1.0f / st.b;
+            // y = exp(x - M) / S;  FP8 codes are y / (1 / (448 S)) = 448 exp(x - M)
+            const float mul = (TOUT == DT_E4M3) ? 448.0f : inv;
+            const float cmul = (kCacheExp && part0 != -INFINITY) ? exp_fast(part0 - st.a) * mul : 0.0f;
+            if (TOUT == DT_E4M3 && c == 0 && tid == 0) a.out_scale[row] = inv * (1.0f / 448.0f);
+            for (long long g = tid; g < ng; g += T) {
+                float f[V], y[V];
+                decode_group<TIN>(*reinterpret_cast<const uint4 *>(img_body + g * 16), f, in_sc);
+#pragma unroll
+                for (int j = 0; j < V; ++j) y[j] = kCacheExp ? f[j] * cmul : exp_fast(f[j] - st.a) * mul;
+                store_group<TOUT, V>(out_row + (i_base + g * V) * osz, y, out_vec);
+            }
+            for (int e = 0; e < 2; ++e) {
+                const long long cnt = e == 0 ? n_head : n_tail;
+                for (long long k = 0; k < cnt; ++k) {
+                    const long long i = e == 0 ? k : tail_i0 + k;
+                    const unsigned char *pe = edge_ptr(e, k);
+                    const float y = kCacheExp ? *reinterpret_cast<const float *>(pe) * cmul
+                                              : exp_fast(decode_one<TIN>(pe, in_sc) - st.a) * mul;
+                    store_one<TOUT>(out_row + i * osz, y);
+                }
+            }
+        } else {
+            for (long long g = tid; g < ng; g += T) {
+                float f[V], gg[V], bb[V], y[V];
+                decode_group<TIN>(*reinterpret_cast<const uint4 *>(img_body + g * 16), f, in_sc);
+                load_affine<V>(a.gamma, i_base + g * V, g_vec, 1.0f, gg);
+                if constexpr (OP == OP_LN) load_affine<V>(a.beta, i_base + g * V, b_vec, 0.0f, bb);
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    const float bj = (OP == OP_LN) ? bb[j] : 0.0f;
+                    y[j] = norm_h<OP>(f[j], st, gg[j], bj) * qmul;
+                }
+                store_group<TOUT, V>(out_row + (i_base + g * V) * osz, y, out_vec);
+            }
+            for (int e = 0; e < 2; ++e) {
+                const long long cnt = e == 0 ? n_head : n_tail;
+                for (long long k = 0; k < cnt; ++k) {
+                    const long long i = e == 0 ? k : tail_i0 + k;
+                    const float x = decode_one<TIN>(edge_ptr(e, k), in_sc);
+                    const float gg = a.gamma ? a.gamma[i] : 1.0f;
+                    const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
+                    store_one<TOUT>(out_row + i * osz, norm_h<OP>(x, st, gg, bb) * qmul);
+                }
+            }
+        }
+    }
+}
+
+// ======================================================================
+// Streaming statistics over global memory (two-pass path)
+// ======================================================================
+template <int OP> struct Stream;
+
+template <> struct Stream<OP_SOFTMAX> {  // online (max, sum exp)
+    float m = -INFINITY, s = 0.0f;
+    template <int V> __device__ __forceinline__ void add(const float (&f)[V]) {
+        float mv = f[0];
+#pragma unroll
+        for (int j = 1; j < V; ++j) mv = fmaxf(mv, f[j]);
+        if (mv == -INFINITY) return;
+        if (mv > m) {
+            s *= exp_fast(m - mv);
+            m = mv;
+        }
+#pragma unroll
+        for (int j = 0; j < V; ++j) s += exp_fast(f[j] - m);
+    }
+    __device__ __forceinline__ void add1(float x) {
+        float f[1] = {x};
+        add<1>(f);
+    }
+    __device__ __forceinline__ void merge(float m2, float s2) {
+        if (s2 == 0.0f) return;
+        if (s == 0.0f) {
+            m = m2;
+            s = s2;
+            return;
+        }
+        const float M = fmaxf(m, m2);
+        s = s * exp_fast(m - M) + s2 * exp_fast(m2 - M);
+        m = M;
+    }
+    __device__ __forceinline__ float p0() const { return m; }
+    __device__ __forceinline__ float p1() const { return s; }
+};
+template <> struct Stream<OP_LSE> : Stream<OP_SOFTMAX> {};
+
+template <> struct Stream<OP_LN> {  // Welford / Chan, merged per 16-byte group
+    float n = 0.0f, mu = 0.0f, m2 = 0.0f;
+    __device__ __forceinline__ void merge3(float nb, float mb, float m2b) {
+        if (nb == 0.0f) return;
+        const float nn = n + nb;
+        const float d = mb - mu;
+        mu += d * (nb / nn);
+        m2 += m2b + d * d * (n * nb / nn);
+        n = nn;
+    }
+    template <int V> __device__ __forceinline__ void add(const float (&f)[V]) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int j = 0; j < V; ++j) sum += f[j];
+        const float mb = sum * (1.0f / V);
+        float q = 0.0f;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const float d = f[j] - mb;
+            q = fmaf(d, d, q);
+        }
+        merge3(static_cast<float>(V), mb, q);
+    }
+    __device__ __forceinline__ void add1(float x) { merge3(1.0f, x, 0.0f); }
+};
+
+template <> struct Stream<OP_RMS> {
+    float ss = 0.0f;
+    template <int V> __device__ __forceinline__ void add(const float (&f)[V]) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) ss = fmaf(f[j], f[j], ss);
+    }
+    __device__ __forceinline__ void add1(float x) { ss = fmaf(x, x, ss); }
+};
+
+// Deterministic block reduction of a Stream state; returns the CTA partial
+// (p0, p1) in the same format as the staged kernel's partials.
+template <int OP>
+__device__ __forceinline__ float2 block_reduce_stream(Stream<OP> st, float *red, long long n_c) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if constexpr (OP == OP_RMS) {
+        return make_float2(block_allreduce<false>(st.ss, red), 0.0f);
+    } else if constexpr (OP == OP_LN) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float nb = __shfl_xor_sync(0xffffffffu, st.n, o);
+            const float mb = __shfl_xor_sync(0xffffffffu, st.mu, o);
+            const float qb = __shfl_xor_sync(0xffffffffu, st.m2, o);
+            if (lane & o) {  // make the merge order independent of which side holds what
+                Stream<OP_LN> t;
+                t.n = nb; t.mu = mb; t.m2 = qb;
+                t.merge3(st.n, st.mu, st.m2);
+                st = t;
+            } else {
+                st.merge3(nb, mb, qb);
+            }
+        }
+        if (lane == 0) {
+            red[3 * wid] = st.n;
+            red[3 * wid + 1] = st.mu;
+            red[3 * wid + 2] = st.m2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Stream<OP_LN> t;
+            for (int w = 0; w < nw; ++w) t.merge3(red[3 * w], red[3 * w + 1], red[3 * w + 2]);
+            red[96] = t.mu;
+            red[97] = t.m2;
+        }
+        __syncthreads();
+        (void)n_c;
+        const float2 r = make_float2(red[96], red[97]);
+        __syncthreads();
+        return r;
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float m2 = __shfl_xor_sync(0xffffffffu, st.m, o);
+            const float s2 = __shfl_xor_sync(0xffffffffu, st.s, o);
+            if (lane & o) {
+                Stream<OP> t;
+                t.m = m2; t.s = s2;
+                t.merge(st.m, st.s);
+                st = t;
+            } else {
+                st.merge(m2, s2);
+            }
+        }
+        if (lane == 0) {
+            red[2 * wid] = st.m;
+            red[2 * wid + 1] = st.s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Stream<OP> t;
+            for (int w = 0; w < nw; ++w) t.merge(red[2 * w], red[2 * w + 1]);
+            red[96] = t.m;
+            red[97] = t.s;
+        }
+        __syncthreads();
+        const float2 r = make_float2(red[96], red[97]);
+        __syncthreads();
+        return r;
+    }
+}
+
+// Visit this CTA's part of a row in global memory, 4 groups in flight per thread.
+template <int TIN, class F>
+__device__ __forceinline__ void sweep_global(const unsigned char *in_row, const RowSlice &s, int P, int c,
+                                             float in_sc, F &&fn /* fn(long long elem_index, float(&)[V]) */) {
+    constexpr int V = Fmt<TIN>::V, isz = Fmt<TIN>::size;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const unsigned char *body = in_row + s.h0 * isz;
+    for (long long g0 = s.g_lo + tid; g0 < s.g_hi; g0 += 4LL * T) {
+        uint4 w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long g = g0 + static_cast<long long>(u) * T;
+            if (g < s.g_hi) w[u] = ld_global_v4(body + g * 16);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long g = g0 + static_cast<long long>(u) * T;
+            if (g < s.g_hi) {
+                float f[V];
+                decode_group<TIN>(w[u], f, in_sc);
+                fn(s.h0 + g * V, f);
+            }
+        }
+    }
+    (void)P;
+    (void)c;
+}
+
+// Edge elements of this CTA (head by thread 0 of CTA 0, tail by the last
+// thread of CTA P-1).
+template <int TIN, class F>
+__device__ __forceinline__ void sweep_edges(const unsigned char *in_row, const RowSlice &s, int P, int c, float in_sc,
+                                            F &&fn /* fn(long long i, float x) */) {
+    constexpr int V = Fmt<TIN>::V, isz = Fmt<TIN>::size;
+    if (c == 0 && threadIdx.x == 0)
+        for (long long k = 0; k < s.h0; ++k) fn(k, decode_one<TIN>(in_row + k * isz, in_sc));
+    if (c == P - 1 && threadIdx.x == blockDim.x - 1) {
+        const long long t = s.h0 + s.G * V;
+        for (long long k = 0; k < s.t0; ++k) fn(t + k, decode_one<TIN>(in_row + (t + k) * isz, in_sc));
+    }
+}
+
+template <int OP, int TIN>
+__device__ __forceinline__ float2 stats_sweep(const RowArgs &a, const unsigned char *in_row, const RowSlice &s, int P,
+                                              int c, float in_sc, float *red) {
+    Stream<OP> st;
+    sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long, const float(&f)[Fmt<TIN>::V]) { st.add(f); });
+    sweep_edges<TIN>(in_row, s, P, c, in_sc, [&](long long, float x) { st.add1(x); });
+    return block_reduce_stream<OP>(st, red, slice_count(s, Fmt<TIN>::V, P, c));
+}
+
+template <int OP, int TIN>
+__device__ __forceinline__ float amax_sweep(const RowArgs &a, const unsigned char *in_row, const RowSlice &s, int P,
+                                            int c, float in_sc, const Stats &st, float *red) {
+    constexpr int V = Fmt<TIN>::V;
+    const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + s.h0) & 15u) == 0);
+    const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + s.h0) & 15u) == 0);
+    float am = 0.0f;
+    sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
+        float gg[V], bb[V];
+        load_affine<V>(a.gamma, i0, g_vec, 1.0f, gg);
+        load_affine<V>(a.beta, i0, b_vec, 0.0f, bb);
+#pragma unroll
+        for (int j = 0; j < V; ++j) am = fmaxf(am, fabsf(norm_h<OP>(f[j], st, gg[j], OP == OP_LN ? bb[j] : 0.0f)));
+    });
+    sweep_edges<TIN>(in_row, s, P, c, in_sc, [&](long long i, float x) {
+        const float gg = a.gamma ? a.gamma[i] : 1.0f, bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
+        am = fmaxf(am, fabsf(norm_h<OP>(x, st, gg, bb)));
+    });
+    return block_allreduce<true>(am, red);
+}
+
+template <int OP, int TIN, int TOUT>
+__device__ __forceinline__ void apply_sweep(const RowArgs &a, long long row, const unsigned char *in_row,
+                                            const RowSlice &s, int P, int c, float in_sc, const Stats &st,
+                                            float qmul) {
+    constexpr int V = Fmt<TIN>::V, osz = Fmt<TOUT>::size;
+    unsigned char *out_row = a.out + row * a.ld_out * osz;
+    constexpr int vec_bytes = (V * osz) < 16 ? (V * osz) : 16;
+    const bool out_vec = ((reinterpret_cast<uintptr_t>(out_row) + s.h0 * osz) % vec_bytes) == 0;
+    const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + s.h0) & 15u) == 0);
+    const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + s.h0) & 15u) == 0);
+    if constexpr (OP == OP_SOFTMAX) {
+        const float inv = 1.0f / st.b;
+        const float mul = (TOUT == DT_E4M3) ? 448.0f : inv;
+        sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
+            float y[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) y[j] = exp_fast(f[j] - st.a) * mul;
+            store_group<TOUT, V>(out_row + i0 * osz, y, out_vec);
+        });
+        sweep_edges<TIN>(in_row, s, P, c, in_sc,
+                         [&](long long i, float x) { store_one<TOUT>(out_row + i * osz, exp_fast(x - st.a) * mul); });
+    } else {
+        sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
+            float gg[V], bb[V], y[V];
+            load_affine<V>(a.gamma, i0, g_vec, 1.0f, gg);
+            if constexpr (OP == OP_LN) load_affine<V>(a.beta, i0, b_vec, 0.0f, bb);
+#pragma unroll
+            for (int j = 0; j < V; ++j) y[j] = norm_h<OP>(f[j], st, gg[j], OP == OP_LN ? bb[j] : 0.0f) * qmul;
+            store_group<TOUT, V>(out_row + i0 * osz, y, out_vec);
+        });
+        sweep_edges<TIN>(in_row, s, P, c, in_sc, [&](long long i, float x) {
+            const float gg = a.gamma ? a.gamma[i] : 1.0f, bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
+            store_one<TOUT>(out_row + i * osz, norm_h<OP>(x, st, gg, bb) * qmul);
+        });
+    }
+}
+
+// ----------------------------------------------------------------------
+// Two-pass path, one CTA per row (single launch, the row is read twice).
+// ----------------------------------------------------------------------
+template <int OP, int TIN, int TOUT>
+__global__ void __launch_bounds__(1024) k_tp_fused(const RowArgs a) {
+    __shared__ float red[128];
+    constexpr int isz = Fmt<TIN>::size, V = Fmt<TIN>::V;
+    const long long row = blockIdx.x + a.row0;
+    const unsigned char *in_row = a.in + row * a.ld_in * isz;
+    const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), a.cols, isz, 1, 0);
+    const float in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
+    const float2 p = stats_sweep<OP, TIN>(a, in_row, s, 1, 0, in_sc, red);
+    const float pp[2] = {p.x, p.y};
+    const Stats st = combine_partials<OP>(pp, 2, 1, s, V, a.cols, a.eps);
+    if constexpr (OP == OP_LSE) {
+        if (threadIdx.x == 0) reinterpret_cast<float *>(a.out)[row] = st.a + logf(st.b);
+    } else {
+        float qmul = 1.0f;
+        if constexpr (TOUT == DT_E4M3 && (OP == OP_LN || OP == OP_RMS)) {
+            const float am = amax_sweep<OP, TIN>(a, in_row, s, 1, 0, in_sc, st, red);
+            qmul = am > 0.0f ? 448.0f / am : 1.0f;
+            if (threadIdx.x == 0) a.out_scale[row] = am > 0.0f ? am / 448.0f : 1.0f;
+        }
+        if constexpr (TOUT == DT_E4M3 && OP == OP_SOFTMAX) {
+            if (threadIdx.x == 0) a.out_scale[row] = (1.0f / st.b) * (1.0f / 448.0f);
+        }
+        apply_sweep<OP, TIN, TOUT>(a, row, in_row, s, 1, 0, in_sc, st, qmul);
+    }
+}
+
+// ----------------------------------------------------------------------
+// Two-pass path, G CTAs per row (workspace partials, launches as barriers).
+// Grid: G * rows_in_launch; CTA (r, g) = blockIdx.x / G, blockIdx.x % G.
+// ws layout: [(row - row0) * G + g] * 4 floats: stats partial in [0, 2),
+// amax partial in [2].
+// ----------------------------------------------------------------------
+template <int OP, int TIN>
+__global__ void __launch_bounds__(1024) k_tp_stats(const RowArgs a) {
+    __shared__ float red[128];
+    constexpr int isz = Fmt<TIN>::size;
+    const int G = a.G, g = blockIdx.x % G;
+    const long long lr = blockIdx.x / G, row = lr + a.row0;
+    const unsigned char *in_row = a.in + row * a.ld_in * isz;
+    const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), a.cols, isz, G, g);
+    const float in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
+    const float2 p = stats_sweep<OP, TIN>(a, in_row, s, G, g, in_sc, red);
+    if (threadIdx.x == 0) {
+        float *w = a.ws + (lr * G + g) * 4;
+        w[0] = p.x;
+        w[1] = p.y;
+    }
+}
+
+template <int OP, int TIN>
+__device__ __forceinline__ Stats tp_row_stats(const RowArgs &a, long long lr, const RowSlice &s) {
+    return combine_partials<OP>(a.ws + lr * a.G * 4, 4, a.G, s, Fmt<TIN>::V, a.cols, a.eps);
+}
+
+template <int OP, int TIN>
+__global__ void __launch_bounds__(1024) k_tp_amax(const RowArgs a) {
+    __shared__ float red[128];
+    constexpr int isz = Fmt<TIN>::size;
+    const int G = a.G, g = blockIdx.x % G;
+    const long long lr = blockIdx.x / G, row = lr + a.row0;
+    const unsigned char *in_row = a.in + row * a.ld_in * isz;
+    const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), a.cols, isz, G, g);
+    const float in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
+    const Stats st = tp_row_stats<OP, TIN>(a, lr, s);
+    const float am = amax_sweep<OP, TIN>(a, in_row, s, G, g, in_sc, st, red);
+    if (threadIdx.x == 0) a.ws[(lr * G + g) * 4 + 2] = am;
+}
+
+template <int OP, int TIN, int TOUT>
+__global__ void __launch_bounds__(1024) k_tp_apply(const RowArgs a) {
+    constexpr int isz = Fmt<TIN>::size;
+    const int G = a.G, g = blockIdx.x % G;
+    const long long lr = blockIdx.x / G, row = lr + a.row0;
+    const unsigned char *in_row = a.in + row * a.ld_in * isz;
+    const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), a.cols, isz, G, g);
+    const float in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
+    const Stats st = tp_row_stats<OP, TIN>(a, lr, s);
+    float qmul = 1.0f;
+    if constexpr (TOUT == DT_E4M3 && (OP == OP_LN || OP == OP_RMS)) {
+        float am = 0.0f;
+        for (int k = 0; k < G; ++k) am = fmaxf(am, a.ws[(lr * G + k) * 4 + 2]);
+        qmul = am > 0.0f ? 448.0f / am : 1.0f;
+        if (g == 0 && threadIdx.x == 0) a.out_scale[row] = am > 0.0f ? am / 448.0f : 1.0f;
+    }
+    if constexpr (TOUT == DT_E4M3 && OP == OP_SOFTMAX) {
+        if (g == 0 && threadIdx.x == 0) a.out_scale[row] = (1.0f / st.b) * (1.0f / 448.0f);
+    }
+    apply_sweep<OP, TIN, TOUT>(a, row, in_row, s, G, g, in_sc, st, qmul);
+}
+
+// One thread per row: combine the G log-sum-exp partials.
+template <int TIN>
+__global__ void k_tp_lse_final(const RowArgs a, long long nrows) {
+    const long long lr = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (lr >= nrows) return;
+    const long long row = lr + a.row0;
+    const RowSlice s = make_slice(0, a.cols, Fmt<TIN>::size, a.G, 0);
+    const Stats st = combine_partials<OP_LSE>(a.ws + lr * a.G * 4, 4, a.G, s, Fmt<TIN>::V, a.cols, a.eps);
+    reinterpret_cast<float *>(a.out)[row] = st.a + logf(st.b);
+}
+
+// ----------------------------------------------------------------------
+// Kernel table of one (input dtype) translation unit.
+// ----------------------------------------------------------------------
+struct KernelSet {
+    const void *staged;
+    const void *tp_fused;
+    const void *tp_stats;
+    const void *tp_amax;
+    const void *tp_apply;
+    const void *tp_lse_final;
+};
+
+}  // namespace credit

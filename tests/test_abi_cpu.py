@@ -1,0 +1,81 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+entry point declared in include/*.h, and argument validation rejects bad
+calls before anything touches a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2609_01864_gb300 import build as B
+from paper_2609_01864_gb300 import credit as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return C.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(credit_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_core_entry_points():
+    names = declared_functions()
+    for n in ("credit_softmax", "credit_logsumexp", "credit_layernorm", "credit_rmsnorm", "credit_plan",
+              "credit_run_ex", "credit_init"):
+        assert n in names
+
+
+def test_every_declared_function_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version(lib):
+    assert C.status_string(C.OK) == "CREDIT_OK"
+    assert C.status_string(C.ERR_INVALID_ARG) == "CREDIT_ERR_INVALID_ARG"
+    assert C.status_string(99) == "CREDIT_ERR_UNKNOWN"
+    assert lib.credit_version() >= 10000
+
+
+def test_validation_rejects_bad_calls_without_touching_the_gpu(lib):
+    # NULL argument block
+    assert lib.credit_run_ex(None, None, None) == C.ERR_INVALID_ARG
+    a = C.ArgsT()
+    a.op, a.in_, a.out, a.rows, a.cols = C.SOFTMAX, 0x1000, 0x2000, 4, 0   # cols == 0
+    assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.ERR_INVALID_ARG
+    a.cols, a.op = 16, 7                                                   # unknown op
+    assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.ERR_INVALID_ARG
+    a.op, a.in_dtype = C.SOFTMAX, C.FP8_E4M3                                # FP8 without scales
+    assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.ERR_INVALID_ARG
+    a.in_dtype, a.in_ = C.F32, 0x1002                                      # misaligned FP32 pointer
+    assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.ERR_INVALID_ARG
+    a.in_, a.op, a.out = 0x1000, C.LOGSUMEXP, 0x1000                       # in == out for logsumexp
+    assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.ERR_INVALID_ARG
+    a.op, a.out, a.in_ = C.SOFTMAX, 0x2000, None                            # NULL input
+    assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.ERR_INVALID_ARG
+    a.in_, a.rows = 0x1000, 0                                              # rows == 0 is a no-op
+    assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.OK
+    # simple entry points: FP8 needs credit_run_ex (scales)
+    assert lib.credit_softmax(0x1000, 0x2000, 4, 16, C.FP8_E4M3, None) == C.ERR_INVALID_ARG
+    p = C.PlanT()
+    assert lib.credit_plan_ex(9, 4, 16, 0, 0, ctypes.byref(p)) == C.ERR_INVALID_ARG
+    assert lib.credit_plan_ex(0, 4, 0, 0, 0, ctypes.byref(p)) == C.ERR_INVALID_ARG
+    assert lib.credit_plan_ex(0, 4, 16, 0, 0, None) == C.ERR_INVALID_ARG
+
+
+def test_struct_layouts_match_the_header():
+    assert ctypes.sizeof(C.PlanT) == 32
+    assert ctypes.sizeof(C.ArgsT) == 104
+    assert C.ArgsT.eps.offset == 96 and C.ArgsT.in_scale.offset == 64
