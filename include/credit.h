@@ -117,13 +117,19 @@ credit_status credit_rmsnorm(const void *in, void *out, int64_t rows, int64_t co
                              credit_dtype dtype, cudaStream_t stream);
 
 /*
- * Execution plan.  path / cluster_size / ctas_per_row / threads fully decide
- * the launch; the rest is informational.
+ * Execution plan.  path / cluster_size / ctas_per_row / threads /
+ * ring_chunks / chunk_bytes fully decide the launch; the rest is
+ * informational.
  *   cluster_size  P of Eq. 2 for CREDIT_PATH_CLUSTER (2..16); 1 otherwise
  *   ctas_per_row  CTAs that share one row: P for CLUSTER, 1 for ONE_CTA,
  *                 G >= 1 for TWO_PASS (G > 1 uses the workspace)
- *   threads       threads per CTA (multiple of 32, 64..1024; 0 = default)
- *   smem_bytes    dynamic shared memory per CTA (S_CTA of Eq. 3)
+ *   threads       threads per CTA (multiple of 32; 0 = default).  Staged
+ *                 paths: consumer threads + one producer warp (96..1024);
+ *                 two-pass: 64..1024
+ *   ring_chunks   staged paths: chunk slots of the shared-memory ring
+ *                 (>= chunks of one slice; 0 = default)
+ *   chunk_bytes   staged paths: bytes per chunk (multiple of 16; 0 = default)
+ *   smem_bytes    dynamic shared memory per CTA (S_CTA of Eq. 3), output
  *   predicted_us  model latency for the whole call (0 when not modelled)
  *   source        0 analytic model, 1 learned model, 2 forced by caller or
  *                 environment, 3 built-in heuristic (no calibration loaded)
@@ -133,6 +139,8 @@ typedef struct {
     int32_t cluster_size;
     int32_t ctas_per_row;
     int32_t threads;
+    int32_t ring_chunks;
+    int32_t chunk_bytes;
     int64_t smem_bytes;
     float predicted_us;
     int32_t source;
@@ -181,6 +189,13 @@ typedef struct {
  */
 credit_status credit_run_ex(const credit_args *args, const credit_plan_t *plan,
                             cudaStream_t stream);
+
+/*
+ * credit_plan_check -- CREDIT_OK if `plan` is legal for `args` on the current
+ * device (Eq. 3 capacity, cluster size, scheduling), CREDIT_ERR_UNSUPPORTED
+ * if not, CREDIT_ERR_INVALID_ARG for bad arguments.  Launches nothing.
+ */
+credit_status credit_plan_check(const credit_args *args, const credit_plan_t *plan);
 
 /*
  * credit_device_error -- synchronise `stream`, then read and clear the

@@ -36,8 +36,8 @@ class CreditError(RuntimeError):
 
 class PlanT(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("ctas_per_row", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int64), ("predicted_us", ctypes.c_float),
-                ("source", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("ring_chunks", ctypes.c_int32), ("chunk_bytes", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int64), ("predicted_us", ctypes.c_float), ("source", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,6 +83,8 @@ def lib() -> ctypes.CDLL:
             L.credit_plan_ex.argtypes = [i32, i64, i64, i32, i32, ctypes.POINTER(PlanT)]
             L.credit_run_ex.restype = i32
             L.credit_run_ex.argtypes = [ctypes.POINTER(ArgsT), ctypes.POINTER(PlanT), vp]
+            L.credit_plan_check.restype = i32
+            L.credit_plan_check.argtypes = [ctypes.POINTER(ArgsT), ctypes.POINTER(PlanT)]
             L.credit_device_error.restype = i32
             L.credit_device_error.argtypes = [vp]
             L.credit_slice_capacity.restype = i64
@@ -159,12 +161,15 @@ def rmsnorm(x, out=None, stream=None):
     return _simple("credit_rmsnorm", RMSNORM, x, out, stream)
 
 
-def make_plan(path: int, cluster_size: int = 1, ctas_per_row: int = 1, threads: int = 0) -> PlanT:
+def make_plan(path: int, cluster_size: int = 1, ctas_per_row: int = 1, threads: int = 0, ring_chunks: int = 0,
+              chunk_bytes: int = 0) -> PlanT:
     p = PlanT()
     p.path = path
     p.cluster_size = cluster_size
     p.ctas_per_row = ctas_per_row if path != PATH_CLUSTER else cluster_size
     p.threads = threads
+    p.ring_chunks = ring_chunks
+    p.chunk_bytes = chunk_bytes
     return p
 
 
@@ -176,11 +181,9 @@ def plan(op: int, rows: int, cols: int, in_dtype: int, out_dtype: int | None = N
     return p
 
 
-def run_ex(op: int, x, out, *, rows: int | None = None, cols: int | None = None, in_dtype: int | None = None,
-           out_dtype: int | None = None, ld_in: int = 0, ld_out: int = 0, in_scale=None, out_scale=None,
-           gamma=None, beta=None, eps: float = -1.0, plan: PlanT | None = None, stream=None) -> int:
-    """credit_run_ex.  x / out: tensors or raw device addresses.  Returns the
-    status (raises CreditError on a non-OK status)."""
+def make_args(op: int, x, out, *, rows: int | None = None, cols: int | None = None, in_dtype: int | None = None,
+              out_dtype: int | None = None, ld_in: int = 0, ld_out: int = 0, in_scale=None, out_scale=None,
+              gamma=None, beta=None, eps: float = -1.0) -> ArgsT:
     a = ArgsT()
     a.op = op
     a.in_ = _ptr(x)
@@ -196,6 +199,20 @@ def run_ex(op: int, x, out, *, rows: int | None = None, cols: int | None = None,
     a.in_scale, a.out_scale = _ptr(in_scale), _ptr(out_scale)
     a.gamma, a.beta = _ptr(gamma), _ptr(beta)
     a.eps = eps
+    return a
+
+
+def plan_check(op: int, x, out, plan: PlanT, **kw) -> int:
+    """credit_plan_check: OK if `plan` is legal for these arguments."""
+    a = make_args(op, x, out, **kw)
+    return lib().credit_plan_check(ctypes.byref(a), ctypes.byref(plan))
+
+
+def run_ex(op: int, x, out, *, plan: PlanT | None = None, stream=None, **kw) -> int:
+    """credit_run_ex.  x / out: tensors or raw device addresses; keyword
+    arguments as make_args.  Returns the status (raises CreditError on a
+    non-OK status)."""
+    a = make_args(op, x, out, **kw)
     st = lib().credit_run_ex(ctypes.byref(a), ctypes.byref(plan) if plan is not None else None, _stream(stream))
     _check(st, "credit_run_ex")
     return st

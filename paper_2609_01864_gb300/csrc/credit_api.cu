@@ -82,14 +82,6 @@ credit_status prepare_kernel(DeviceState &d, const void *fn, bool staged) {
     return CREDIT_OK;
 }
 
-int default_staged_threads(long long groups_per_cta) {
-    long long t = (groups_per_cta + 7) / 8;
-    t = (t + 31) / 32 * 32;
-    if (t < 64) t = 64;
-    if (t > 1024) t = 1024;
-    return static_cast<int>(t);
-}
-
 }  // namespace
 
 // ------------------------------------------------------------------ host helpers
@@ -97,16 +89,52 @@ namespace credit {
 
 int dtype_size(int dt) { return dt == DT_F32 ? 4 : (dt == DT_BF16 ? 2 : 1); }
 
-// S_CTA of Eq. 3 for a slice of a row of N elements of isz bytes over P CTAs.
-long long staged_smem_bytes(long long N, int isz, int P) {
-    const long long groups = (N * isz) / 16;           // full 16-byte groups (upper bound)
-    const long long per = (groups + P - 1) / P;
-    return kCtrlBytes + kEdgeBytes + per * 16;
-}
-
-long long staged_groups_per_cta(long long N, int isz, int P) {
+// Geometry of the staged (ring) paths for rows of N elements of isz bytes
+// over P CTAs.  The body of a CTA's slice is at most ceil(G / P) 16-byte
+// groups, G = floor(N * isz / 16).  Eq. 3: the slice must fit the ring, i.e.
+// kRingCtrl + ceil(body / chunk) * chunk <= the opt-in shared memory.
+bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring, int req_chunk, int req_threads,
+                 RingCfg *out) {
+    if (P < 1 || P > kMaxCluster || N <= 0) return false;
     const long long groups = (N * isz) / 16;
-    return (groups + P - 1) / P;
+    const long long per = (groups + P - 1) / P;
+    RingCfg r{};
+    r.P = P;
+    r.body_max = per * 16;
+    if (req_chunk > 0) {
+        if (req_chunk % 16) return false;
+        r.chunk = req_chunk;
+    } else if (r.body_max == 0) {
+        r.chunk = 16;
+    } else {
+        const long long n = (r.body_max + kMaxChunkBytes - 1) / kMaxChunkBytes;
+        r.chunk = static_cast<int>(((r.body_max + n - 1) / n + 15) / 16 * 16);
+    }
+    r.nch_max = static_cast<int>((r.body_max + r.chunk - 1) / r.chunk);
+    const long long fit = (di.smem_optin - kRingCtrl) / r.chunk;
+    if (req_ring > 0) {
+        r.ring = req_ring;
+    } else {
+        long long k = 2LL * r.nch_max;
+        if (k < 2) k = 2;
+        if (k > kMaxRing) k = kMaxRing;
+        if (k > fit) k = fit;
+        r.ring = static_cast<int>(k);
+    }
+    if (r.ring < r.nch_max || r.ring < 1 || r.ring > kMaxRing) return false;
+    r.smem = kRingCtrl + static_cast<long long>(r.ring) * r.chunk;
+    if (r.smem > di.smem_optin) return false;  // Eq. 3
+    if (req_threads > 0) {
+        if (req_threads % 32 || req_threads < 96 || req_threads > 1024) return false;
+        r.threads = req_threads;
+    } else {
+        long long tc = (r.chunk / 16 / 4 + 31) / 32 * 32;
+        if (tc < 64) tc = 64;
+        if (tc > 512) tc = 512;
+        r.threads = static_cast<int>(tc) + 32;
+    }
+    *out = r;
+    return true;
 }
 
 const DeviceInfo *device_info(int device) {
@@ -120,16 +148,16 @@ int current_device() {
     return dev;
 }
 
-// Max active clusters of the staged kernel for (op, dtypes, P, threads, smem);
+// Max active clusters of the ring kernel for (op, dtypes, P, threads, smem);
 // 0 if it cannot be scheduled.  Cached.
-int staged_max_clusters(int device, int op, int tin, int tout, int P, int threads, long long smem) {
+int ring_max_clusters(int device, int op, int tin, int tout, int P, int threads, long long smem) {
     if (device < 0 || device >= kMaxDevices) return 0;
     DeviceState &d = g_dev[device];
     KernelSet ks;
     if (!kernel_set(op, tin, tout, &ks)) return 0;
     if (smem > d.info.smem_optin) return 0;
-    if (prepare_kernel(d, ks.staged, true) != CREDIT_OK) return 0;
-    const auto key = std::make_tuple(ks.staged, P, threads, smem);
+    if (prepare_kernel(d, ks.ring, true) != CREDIT_OK) return 0;
+    const auto key = std::make_tuple(ks.ring, P, threads, smem);
     {
         std::lock_guard<std::mutex> lk(d.mu);
         auto it = d.clusters.find(key);
@@ -138,9 +166,11 @@ int staged_max_clusters(int device, int op, int tin, int tout, int P, int thread
     int n = 0;
     if (P <= 1) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.staged, threads, static_cast<size_t>(smem)) ==
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.ring, threads, static_cast<size_t>(smem)) ==
             cudaSuccess)
             n = per_sm * d.info.sm_count;
+        else
+            (void)cudaGetLastError();
     } else {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -153,7 +183,7 @@ int staged_max_clusters(int device, int op, int tin, int tout, int P, int thread
         cfg.dynamicSmemBytes = static_cast<size_t>(smem);
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if (cudaOccupancyMaxActiveClusters(&n, ks.staged, &cfg) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveClusters(&n, ks.ring, &cfg) != cudaSuccess) {
             n = 0;
             (void)cudaGetLastError();
         }
@@ -222,8 +252,8 @@ credit_status credit_init(int device) {
 int64_t credit_slice_capacity(credit_dtype dtype) {
     const DeviceInfo *di = device_info(current_device());
     if (!di || dtype < 0 || dtype > 2) return 0;
-    const long long bytes = di->smem_optin - kCtrlBytes - kEdgeBytes;
-    return bytes / dtype_size(dtype);
+    const long long bytes = di->smem_optin - kRingCtrl;
+    return bytes / 16 * 16 / dtype_size(dtype);
 }
 
 credit_status credit_device_error(cudaStream_t stream) {
@@ -272,18 +302,18 @@ credit_status check_plan(int device, const credit_args *a, const credit_plan_t *
     const int tout = a->op == OP_LSE ? DT_F32 : a->out_dtype;
     const int threads = p->threads;
     if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32)) return CREDIT_ERR_UNSUPPORTED;
+    (void)threads;
     switch (p->path) {
     case CREDIT_PATH_ONE_CTA:
     case CREDIT_PATH_CLUSTER: {
         const int P = p->path == CREDIT_PATH_ONE_CTA ? 1 : p->cluster_size;
         if (P < 1 || P > kMaxCluster) return CREDIT_ERR_UNSUPPORTED;
         if (p->path == CREDIT_PATH_CLUSTER && P < 2) return CREDIT_ERR_UNSUPPORTED;
-        const long long smem = staged_smem_bytes(a->cols, isz, P);
-        if (smem > di->smem_optin) return CREDIT_ERR_UNSUPPORTED;  // Eq. 3
-        const long long body = smem - kCtrlBytes - kEdgeBytes;
-        if (body > static_cast<long long>(kMaxChunks) * kChunkBytes) return CREDIT_ERR_UNSUPPORTED;
-        const int t = threads ? threads : default_staged_threads(staged_groups_per_cta(a->cols, isz, P));
-        if (staged_max_clusters(device, a->op, a->in_dtype, tout, P, t, smem) <= 0) return CREDIT_ERR_UNSUPPORTED;
+        RingCfg rc;
+        if (!ring_config(*di, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, p->threads, &rc))
+            return CREDIT_ERR_UNSUPPORTED;  // Eq. 3
+        if (ring_max_clusters(device, a->op, a->in_dtype, tout, P, rc.threads, rc.smem) <= 0)
+            return CREDIT_ERR_UNSUPPORTED;
         return CREDIT_OK;
     }
     case CREDIT_PATH_TWO_PASS: {
@@ -313,6 +343,8 @@ static RowArgs make_row_args(const credit_args *a, unsigned *err, float *ws) {
     r.err = err;
     r.ws = ws;
     r.G = 1;
+    r.chunk_bytes = 0;
+    r.ring = 0;
     r.row0 = 0;
     return r;
 }
@@ -362,20 +394,25 @@ credit_status run_with_plan(int device, const credit_args *a, const credit_plan_
 
     if (p->path == CREDIT_PATH_ONE_CTA || p->path == CREDIT_PATH_CLUSTER) {
         const int P = p->path == CREDIT_PATH_ONE_CTA ? 1 : p->cluster_size;
-        const long long smem = staged_smem_bytes(a->cols, isz, P);
-        const int threads = p->threads ? p->threads : default_staged_threads(staged_groups_per_cta(a->cols, isz, P));
-        credit_status st = prepare_kernel(d, ks.staged, true);
+        RingCfg rc;
+        if (!ring_config(d.info, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, p->threads, &rc))
+            return CREDIT_ERR_UNSUPPORTED;
+        credit_status st = prepare_kernel(d, ks.ring, true);
         if (st != CREDIT_OK) return st;
-        const long long max_rows = (0x7FFFFFFFLL / P);
-        for (long long r0 = 0; r0 < rows; r0 += max_rows) {
-            const long long n = rows - r0 < max_rows ? rows - r0 : max_rows;
-            RowArgs r = rows_from(base, r0, n, isz, osz, lse);
-            void *args[] = {&r};
-            cudaError_t e = launch(ks.staged, dim3(static_cast<unsigned>(P * n)), dim3(threads),
-                                   static_cast<size_t>(smem), P, s, args);
-            if (e != cudaSuccess) return cuda_status(e);
-            g_launch_count.fetch_add(1);
-        }
+        const int maxc = ring_max_clusters(device, a->op, tin, tout, P, rc.threads, rc.smem);
+        if (maxc <= 0) return CREDIT_ERR_UNSUPPORTED;
+        const long long ncl = rows < maxc ? rows : maxc;
+        if (std::getenv("CREDIT_LOG"))
+            std::fprintf(stderr, "credit: ring op=%d P=%d clusters=%lld (max %d) threads=%d chunk=%d ring=%d smem=%lld\n",
+                         a->op, P, ncl, maxc, rc.threads, rc.chunk, rc.ring, rc.smem);
+        RowArgs r = base;
+        r.chunk_bytes = rc.chunk;
+        r.ring = rc.ring;
+        void *args[] = {&r};
+        cudaError_t e = launch(ks.ring, dim3(static_cast<unsigned>(P * ncl)), dim3(rc.threads),
+                               static_cast<size_t>(rc.smem), P, s, args);
+        if (e != cudaSuccess) return cuda_status(e);
+        g_launch_count.fetch_add(1);
         return CREDIT_OK;
     }
 
@@ -458,6 +495,15 @@ credit_status credit_run_ex(const credit_args *args, const credit_plan_t *plan, 
     }
     if ((st = check_plan(dev, args, &chosen)) != CREDIT_OK) return st;
     return run_with_plan(dev, args, &chosen, stream);
+}
+
+credit_status credit_plan_check(const credit_args *args, const credit_plan_t *plan) {
+    credit_status st = validate_args(args);
+    if (st != CREDIT_OK) return st;
+    if (!plan) return CREDIT_ERR_INVALID_ARG;
+    int dev = 0;
+    if ((st = ensure_init(&dev, nullptr)) != CREDIT_OK) return st;
+    return check_plan(dev, args, plan);
 }
 
 static credit_status simple(credit_op op, const void *in, void *out, int64_t rows, int64_t cols, credit_dtype dtype,

@@ -17,7 +17,7 @@ namespace credit {
 
 template <int OP, int TIN, int TOUT>
 static void fill_set(KernelSet *ks) {
-    ks->staged = reinterpret_cast<const void *>(&k_staged<OP, TIN, TOUT>);
+    ks->ring = reinterpret_cast<const void *>(&k_ring<OP, TIN, TOUT>);
     ks->tp_fused = reinterpret_cast<const void *>(&k_tp_fused<OP, TIN, TOUT>);
     ks->tp_stats = reinterpret_cast<const void *>(&k_tp_stats<OP, TIN>);
     ks->tp_amax = nullptr;

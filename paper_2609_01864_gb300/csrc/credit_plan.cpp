@@ -15,26 +15,28 @@
 
 namespace credit {
 
-static bool env_force(credit_plan_t *p, int op, long long rows, long long cols, int tin) {
+static bool env_force(const DeviceInfo *di, credit_plan_t *p, long long cols, int tin) {
     const char *fp = std::getenv("CREDIT_FORCE_PATH");
     if (!fp || !*fp) return false;
     std::memset(p, 0, sizeof(*p));
     const char *fP = std::getenv("CREDIT_FORCE_P");
     const char *fG = std::getenv("CREDIT_FORCE_G");
     const char *fT = std::getenv("CREDIT_FORCE_THREADS");
+    const char *fR = std::getenv("CREDIT_FORCE_RING");
+    const char *fC = std::getenv("CREDIT_FORCE_CHUNK");
     p->threads = fT ? std::atoi(fT) : 0;
+    p->ring_chunks = fR ? std::atoi(fR) : 0;
+    p->chunk_bytes = fC ? std::atoi(fC) : 0;
     p->source = 2;
-    const int isz = dtype_size(tin);
-    if (!std::strcmp(fp, "one_cta")) {
-        p->path = CREDIT_PATH_ONE_CTA;
-        p->cluster_size = 1;
-        p->ctas_per_row = 1;
-        p->smem_bytes = staged_smem_bytes(cols, isz, 1);
-    } else if (!std::strcmp(fp, "cluster")) {
-        p->path = CREDIT_PATH_CLUSTER;
-        p->cluster_size = fP ? std::atoi(fP) : 4;
+    if (!std::strcmp(fp, "one_cta") || !std::strcmp(fp, "cluster")) {
+        const bool one = !std::strcmp(fp, "one_cta");
+        p->path = one ? CREDIT_PATH_ONE_CTA : CREDIT_PATH_CLUSTER;
+        p->cluster_size = one ? 1 : (fP ? std::atoi(fP) : 4);
         p->ctas_per_row = p->cluster_size;
-        p->smem_bytes = staged_smem_bytes(cols, isz, p->cluster_size);
+        RingCfg rc;
+        if (di && ring_config(*di, cols, dtype_size(tin), p->cluster_size, p->ring_chunks, p->chunk_bytes,
+                              p->threads, &rc))
+            p->smem_bytes = rc.smem;
     } else if (!std::strcmp(fp, "two_pass")) {
         p->path = CREDIT_PATH_TWO_PASS;
         p->cluster_size = 1;
@@ -42,8 +44,6 @@ static bool env_force(credit_plan_t *p, int op, long long rows, long long cols, 
     } else {
         return false;
     }
-    (void)op;
-    (void)rows;
     return true;
 }
 
@@ -69,17 +69,15 @@ void heuristic_plan(const DeviceInfo &di, int device, int op, long long rows, lo
     if (op != 1) {
         // Smallest P whose slice is <= 64 KiB, else the smallest P that fits.
         int pick = 0;
+        RingCfg best{};
         for (int pass = 0; pass < 2 && !pick; ++pass) {
             for (int P : {1, 2, 4, 8, 16}) {
-                const long long smem = staged_smem_bytes(cols, isz, P);
-                if (smem > di.smem_optin) continue;
-                if (pass == 0 && smem > 65536 + 1056) continue;
-                const long long gpc = staged_groups_per_cta(cols, isz, P);
-                long long t = (gpc + 7) / 8;
-                t = (t + 31) / 32 * 32;
-                t = t < 64 ? 64 : (t > 1024 ? 1024 : t);
-                if (staged_max_clusters(device, op, tin, tout, P, static_cast<int>(t), smem) <= 0) continue;
+                RingCfg rc;
+                if (!ring_config(di, cols, isz, P, 0, 0, 0, &rc)) continue;
+                if (pass == 0 && rc.body_max > 65536) continue;
+                if (ring_max_clusters(device, op, tin, tout, P, rc.threads, rc.smem) <= 0) continue;
                 pick = P;
+                best = rc;
                 break;
             }
         }
@@ -87,7 +85,7 @@ void heuristic_plan(const DeviceInfo &di, int device, int op, long long rows, lo
             p->path = pick == 1 ? CREDIT_PATH_ONE_CTA : CREDIT_PATH_CLUSTER;
             p->cluster_size = pick;
             p->ctas_per_row = pick;
-            p->smem_bytes = staged_smem_bytes(cols, isz, pick);
+            p->smem_bytes = best.smem;
             return;
         }
     }
@@ -108,12 +106,12 @@ credit_status credit_plan_ex(credit_op op, int64_t rows, int64_t cols, credit_dt
         return CREDIT_ERR_INVALID_ARG;
     if (rows < 0 || cols <= 0) return CREDIT_ERR_INVALID_ARG;
     const int tout = op == CREDIT_OP_LOGSUMEXP ? 0 : out_dtype;
-    if (env_force(out, op, rows, cols, in_dtype)) return CREDIT_OK;
     int dev = 0;
     credit_status st = ensure_init(&dev, nullptr);
     if (st != CREDIT_OK) return st;
     const DeviceInfo *di = device_info(dev);
     if (!di) return CREDIT_ERR_NOT_INITIALIZED;
+    if (env_force(di, out, cols, in_dtype)) return CREDIT_OK;
     if (model_plan(*di, dev, op, rows, cols, in_dtype, tout, out)) return CREDIT_OK;
     heuristic_plan(*di, dev, op, rows, cols, in_dtype, tout, out);
     return CREDIT_OK;

@@ -20,17 +20,17 @@
 // the split-row two-pass path.
 //
 // Kernels
-//   k_staged     one row per cluster of P CTAs (P = 1: the one-CTA path).
-//                Each CTA stages its slice into its own shared memory with
-//                cp.async.bulk (16 KiB chunks, one mbarrier each, so the
-//                first reduction sweep overlaps the copy), reduces locally
-//                (threads -> warp shuffles -> shared memory), pushes its
-//                partials into every peer's slot array over DSMEM (Eq. 5:
-//                one of the first P threads per destination), crosses one
-//                split cluster barrier, combines the P local slots in fixed
-//                order c = 0..P-1 (so every CTA holds bit-identical
-//                statistics), and writes its output segment from shared
-//                memory (Sec. III-C, "reuse").
+//   k_ring       a cluster of P CTAs per row (P = 1: the one-CTA path),
+//                persistent over rows.  Each CTA stages its slice into its
+//                own shared memory with cp.async.bulk through a ring of
+//                chunks (the first reduction sweep overlaps the copy, the
+//                next row's copy overlaps this row's writes), reduces
+//                locally (threads -> warp shuffles -> shared memory), pushes
+//                its partials into every peer's slot array over DSMEM (Eq. 5:
+//                one of the first P threads per destination), combines the P
+//                local slots in fixed order c = 0..P-1 (so every CTA holds
+//                bit-identical statistics), and writes its output segment
+//                from shared memory (Sec. III-C, "reuse").
 //   k_tp_fused   the global-reread baseline with one CTA per row: a
 //                statistics sweep over HBM, then a sweep that rereads the row
 //                (Sec. IV-A; Eq. 4 with b_reread = input bytes).
@@ -55,18 +55,13 @@ struct RowArgs {
     unsigned *err;                        // device error word
     float *ws;                            // two-pass partials [row - row0][G][4]
     int G;                                // CTAs per row of the two-pass path
+    int chunk_bytes;                      // ring kernel: bytes per staged chunk
+    int ring;                             // ring kernel: chunk slots
     long long row0;                       // first row of this launch
 };
 
 constexpr int kMaxCluster = 16;
-constexpr int kMaxChunks = 16;
-constexpr int kChunkBytes = 16384;
-// Shared-memory control area of k_staged:
-//   [0, 128)     mbarriers, one per staged chunk
-//   [128, 640)   DSMEM slots [2 stages][16 sources][4 floats]
-//   [640, 1024)  block-reduction scratch
-constexpr int kCtrlBytes = 1024;
-constexpr int kEdgeBytes = 32;  // 16-byte head slot + 16-byte tail slot of the image
+constexpr int kMaxChunkBytes = 16384;  // default (and largest) staged chunk
 
 struct RowSlice {
     long long h0;          // head elements (rank 0)
@@ -176,259 +171,349 @@ __device__ __forceinline__ void copy_raw(unsigned char *dst, const unsigned char
 }
 
 // ======================================================================
-// Staged kernel: cluster path (P > 1) and one-CTA path (P == 1).
-// Grid: 1-D, P * rows CTAs; cluster dims (P, 1, 1); row = blockIdx.x / P.
+// Ring kernel: the cluster path (P > 1) and the one-CTA path (P == 1).
+//
+// Persistent: grid = nclusters * P CTAs with cluster dims (P, 1, 1); cluster
+// k handles rows k, k + nclusters, ...  The last warp is the producer (its
+// lane 0 issues the bulk copies); the other W warps consume.  Shared memory
+// holds a control area and a ring of `ring` chunk slots of `chunk_bytes`.
+// The slices of successive rows form one chunk sequence j = 0, 1, ...;
+// chunk j lives in slot j % ring.  full[s] completes when a chunk has landed
+// (transaction bytes), empty[s] when every consumer warp has finished the
+// reuse pass over it, so the next rows' slices stream in while the current
+// row is being written.  A slice needs ceil(body / chunk_bytes) <= ring slots
+// (Eq. 3).
+//
+// Exchange (Eq. 5): thread t < P of each CTA pushes the CTA's partials into
+// slot [c] of peer t with st.async, which completes on the peer's exchange
+// mbarrier; each CTA waits (bounded) on its own exchange mbarrier for the
+// P - 1 remote pushes, then combines its P local slots in fixed order.  The
+// slot arrays and exchange mbarriers are double-buffered by row parity, so a
+// peer can run one row ahead without overwriting partials still being read.
+// One cluster barrier at the start (every CTA's mbarriers are initialised
+// before any remote push) and one at the end (no CTA exits while a peer may
+// still push into it) are the only cluster-wide barriers.
 // ======================================================================
+constexpr int kRingCtrl = 2048;
+constexpr int kMaxRing = 32;
+// Control area layout:
+//   [0, 256)      full[32] mbarriers
+//   [256, 512)    empty[32] mbarriers
+//   [512, 544)    exchange mbarriers [stage][parity]
+//   [544, 1024)   reduction scratch (120 floats)
+//   [1024, 2048)  DSMEM slots [stage][parity][16 sources][4 floats]
+
+__device__ __forceinline__ float *slot_ptr(float *slots, int stage, int par, int c) {
+    return slots + ((stage * 2 + par) * 16 + c) * 4;
+}
+
+// All-reduce over the Tc consumer threads (named barrier 1).
+template <bool MAX>
+__device__ __forceinline__ float cons_allreduce(float v, float *red, int Tc) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = Tc >> 5;
+    v = MAX ? warp_max(v) : warp_sum(v);
+    if (lane == 0) red[wid] = v;
+    named_bar_sync(1, Tc);
+    if (wid == 0) {
+        float t = lane < nw ? red[lane] : (MAX ? -INFINITY : 0.0f);
+        t = MAX ? warp_max(t) : warp_sum(t);
+        if (lane == 0) red[32] = t;
+    }
+    named_bar_sync(1, Tc);
+    return red[32];
+}
+
+// Replicated push all-gather of NQ floats per CTA (consumer threads only).
+template <int NQ>
+__device__ __forceinline__ const float *exchange_push(float p0, float p1, float *slots, uint64_t *xbar, int stage,
+                                                      int par, uint32_t phase, int P, int c, int Tc, unsigned *err) {
+    const int tid = threadIdx.x;
+    float *mine = slot_ptr(slots, stage, par, c);
+    uint64_t *bar = &xbar[stage * 2 + par];
+    if (tid < P) {
+        if (tid == c) {
+            mine[0] = p0;
+            if (NQ == 2) mine[1] = p1;
+        } else {
+            // order this CTA's earlier reads of the slots before the peer's next writes
+            fence_acq_rel_cluster();
+            const uint32_t raddr = mapa_shared(smem_addr(mine), static_cast<uint32_t>(tid));
+            const uint32_t rbar = mapa_shared(smem_addr(bar), static_cast<uint32_t>(tid));
+            if (NQ == 2) st_async_v2f32(raddr, p0, p1, rbar);
+            else st_async_f32(raddr, p0, rbar);
+        }
+    }
+    if (tid == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>((P - 1) * NQ * 4));
+    named_bar_sync(1, Tc);
+    mbar_wait_bounded(bar, phase, err);
+    return slot_ptr(slots, stage, par, 0);
+}
+
 template <int OP, int TIN, int TOUT>
-__global__ void __launch_bounds__(1024, 1) k_staged(const RowArgs a) {
+__global__ void __launch_bounds__(1024, 1) k_ring(const RowArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
-    float *slots = reinterpret_cast<float *>(smem + 128);
-    float *red = reinterpret_cast<float *>(smem + 640);
-    unsigned char *img = smem + kCtrlBytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + 32;
+    uint64_t *xbar = full + 64;
+    float *red = reinterpret_cast<float *>(smem + 544);
+    float *slots = reinterpret_cast<float *>(smem + 1024);
+    unsigned char *ring = smem + kRingCtrl;
 
     constexpr int isz = Fmt<TIN>::size, V = Fmt<TIN>::V;
     constexpr int osz = Fmt<TOUT>::size;
     constexpr bool kFp8Stage = (TOUT == DT_E4M3) && (OP == OP_LN || OP == OP_RMS);
-    constexpr bool kCacheExp = (OP == OP_SOFTMAX) && (TIN == DT_F32);
+    constexpr bool kTwoSweep = (OP == OP_SOFTMAX || OP == OP_LSE || OP == OP_LN);
 
+    const int CH = a.chunk_bytes, K = a.ring, gpc = CH / 16;
     const int P = static_cast<int>(cluster_nctarank());
     const int c = P > 1 ? static_cast<int>(cluster_ctarank()) : 0;
-    const long long row = blockIdx.x / P;
-    // Start barrier, split: arrive now, wait just before the first remote
-    // store, so that every peer is known to be running when it is written.
-    if (P > 1) cluster_arrive_relaxed();
-
-    const int tid = threadIdx.x, T = blockDim.x;
+    const long long ncl = gridDim.x / P, cl = blockIdx.x / P;
+    const int tid = threadIdx.x, Tc = static_cast<int>(blockDim.x) - 32, W = Tc >> 5;
     const long long N = a.cols;
-    const unsigned char *in_row = a.in + row * a.ld_in * isz;
-    const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), N, isz, P, c);
-    const float in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
-    const long long ng = s.g_hi - s.g_lo;
-    const uint32_t body = static_cast<uint32_t>(ng * 16);
-    const int nchunks = static_cast<int>((body + kChunkBytes - 1) / kChunkBytes);
-    const bool own_head = (c == 0), own_tail = (c == P - 1);
-    const long long tail_i0 = s.h0 + s.G * V;  // element index of the first tail element
-    unsigned char *img_body = img + 16;
 
     if (tid == 0) {
-        for (int k = 0; k < nchunks; ++k) mbar_init(&mbar[k], 1);
+        for (int k = 0; k < K; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], static_cast<uint32_t>(W));
+        }
+        for (int k = 0; k < 4; ++k) mbar_init(&xbar[k], 1);
         fence_mbar_init();
     }
-    // Edges (< 16 bytes each) are copied with plain loads.
-    if (own_head && tid < s.h0) copy_raw(img + 16 - (s.h0 - tid) * isz, in_row + tid * isz, isz);
-    if (own_tail && tid >= 32 && tid - 32 < s.t0)
-        copy_raw(img_body + body + (tid - 32) * isz, in_row + (tail_i0 + tid - 32) * isz, isz);
     __syncthreads();
-    if (tid == 0) {
-        const unsigned char *src = in_row + s.h0 * isz + s.g_lo * 16;
-        for (int k = 0; k < nchunks; ++k) {
-            const uint32_t off = static_cast<uint32_t>(k) * kChunkBytes;
-            const uint32_t bytes = min(static_cast<uint32_t>(kChunkBytes), body - off);
-            mbar_arrive_expect_tx(&mbar[k], bytes);
-            bulk_g2s(img_body + off, src + off, bytes, &mbar[k]);
-        }
-    }
+    if (P > 1) cluster_arrive_release();  // start barrier, split
+    bool waited_start = false;
 
-    // Visit the edge elements owned by this CTA: head by thread 0, tail by
-    // thread T-1 (fixed owners keep the reduction order deterministic).
-    auto edge_ptr = [&](int which, long long k) -> unsigned char * {
-        return which == 0 ? img + 16 - (s.h0 - k) * isz : img_body + body + k * isz;
-    };
-    const long long n_head = (own_head && tid == 0) ? s.h0 : 0;
-    const long long n_tail = (own_tail && tid == T - 1) ? s.t0 : 0;
-
-    // ---------------- stage 1, first local sweep (overlaps the bulk copy)
-    float acc0 = (OP == OP_SOFTMAX || OP == OP_LSE) ? -INFINITY : 0.0f;
-    for (int k = 0; k < nchunks; ++k) {
-        mbar_wait_bounded(&mbar[k], 0, a.err);
-        const long long gb = static_cast<long long>(k) * (kChunkBytes / 16);
-        const long long ge = min(ng, gb + kChunkBytes / 16);
-        for (long long g = gb + tid; g < ge; g += T) {
-            const uint4 w = *reinterpret_cast<const uint4 *>(img_body + g * 16);
-            float f[V];
-            decode_group<TIN>(w, f, in_sc);
-#pragma unroll
-            for (int j = 0; j < V; ++j) {
-                if constexpr (OP == OP_SOFTMAX || OP == OP_LSE) acc0 = fmaxf(acc0, f[j]);
-                else if constexpr (OP == OP_LN) acc0 += f[j];
-                else acc0 = fmaf(f[j], f[j], acc0);
+    if (tid >= Tc) {
+        // ------------------------------------------------------ producer warp
+        if (tid == Tc) {
+            long long j = 0;
+            for (long long row = cl; row < a.rows; row += ncl) {
+                const unsigned char *in_row = a.in + row * a.ld_in * isz;
+                const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), N, isz, P, c);
+                const long long body = (s.g_hi - s.g_lo) * 16;
+                const unsigned char *src = in_row + s.h0 * isz + s.g_lo * 16;
+                for (long long off = 0; off < body; off += CH, ++j) {
+                    const int slot = static_cast<int>(j % K);
+                    if (j >= K) mbar_wait_bounded(&empty[slot], static_cast<uint32_t>(((j / K) - 1) & 1), a.err);
+                    const uint32_t bytes = static_cast<uint32_t>(body - off < CH ? body - off : CH);
+                    mbar_arrive_expect_tx(&full[slot], bytes);
+                    bulk_g2s(ring + static_cast<size_t>(slot) * CH, src + off, bytes, &full[slot]);
+                }
             }
         }
-    }
-    for (int e = 0; e < 2; ++e) {
-        const long long cnt = e == 0 ? n_head : n_tail;
-        for (long long k = 0; k < cnt; ++k) {
-            const float x = decode_one<TIN>(edge_ptr(e, k), in_sc);
-            if constexpr (OP == OP_SOFTMAX || OP == OP_LSE) acc0 = fmaxf(acc0, x);
-            else if constexpr (OP == OP_LN) acc0 += x;
-            else acc0 = fmaf(x, x, acc0);
-        }
-    }
-    const long long n_c = slice_count(s, V, P, c);
-    float part0, part1 = 0.0f;
-    if constexpr (OP == OP_SOFTMAX || OP == OP_LSE || OP == OP_LN) {
-        const float r0 = (OP == OP_LN) ? block_allreduce<false>(acc0, red) : block_allreduce<true>(acc0, red);
-        const float center = (OP == OP_LN) ? (n_c > 0 ? r0 / static_cast<float>(n_c) : 0.0f) : r0;
-        // ------------- stage 1, second local sweep over shared memory
-        float acc1 = 0.0f;
-        // A slice whose maximum is -inf contributes exp(...) = 0 everywhere.
-        const bool dead = (OP != OP_LN) && center == -INFINITY;
-        if (!dead || kCacheExp) {
-            for (long long g = tid; g < ng; g += T) {
-                uint4 *pw = reinterpret_cast<uint4 *>(img_body + g * 16);
-                float f[V];
-                decode_group<TIN>(*pw, f, in_sc);
-                if constexpr (OP == OP_LN) {
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------ consumer warps
+        long long j = 0;
+        int rr = 0;
+        for (long long row = cl; row < a.rows; row += ncl, ++rr) {
+            const unsigned char *in_row = a.in + row * a.ld_in * isz;
+            const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), N, isz, P, c);
+            const long long ng = s.g_hi - s.g_lo;
+            const int nch = static_cast<int>((ng * 16 + CH - 1) / CH);
+            const float in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
+            const long long n_head = (c == 0 && tid == 0) ? s.h0 : 0;
+            const long long n_tail = (c == P - 1 && tid == Tc - 1) ? s.t0 : 0;
+            const long long tail_i0 = s.h0 + s.G * V;
+            const int par = rr & 1;
+            const uint32_t xphase = static_cast<uint32_t>((rr >> 1) & 1);
+            auto chunk = [&](int k) -> const unsigned char * {
+                return ring + static_cast<size_t>((j + k) % K) * CH;
+            };
+            auto chunk_groups = [&](int k) -> int {
+                const long long r = ng - static_cast<long long>(k) * gpc;
+                return static_cast<int>(r < gpc ? r : gpc);
+            };
+            auto edge_x = [&](int e, long long k) -> float {
+                const long long i = e == 0 ? k : tail_i0 + k;
+                return decode_one<TIN>(in_row + i * isz, in_sc);
+            };
+
+            // ---------- stage 1, first local sweep (waits for each chunk)
+            float acc0 = (OP == OP_SOFTMAX || OP == OP_LSE) ? -INFINITY : 0.0f;
+            for (int k = 0; k < nch; ++k) {
+                const long long jk = j + k;
+                mbar_wait_bounded(&full[jk % K], static_cast<uint32_t>((jk / K) & 1), a.err);
+                const unsigned char *cb = chunk(k);
+                const int gn = chunk_groups(k);
+                for (int g = tid; g < gn; g += Tc) {
+                    float f[V];
+                    decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, in_sc);
 #pragma unroll
-                    for (int j = 0; j < V; ++j) {
-                        const float d = f[j] - center;
-                        acc1 = fmaf(d, d, acc1);
+                    for (int q = 0; q < V; ++q) {
+                        if constexpr (OP == OP_SOFTMAX || OP == OP_LSE) acc0 = fmaxf(acc0, f[q]);
+                        else if constexpr (OP == OP_LN) acc0 += f[q];
+                        else acc0 = fmaf(f[q], f[q], acc0);
                     }
-                } else {
-                    float e4[V];
-#pragma unroll
-                    for (int j = 0; j < V; ++j) {
-                        e4[j] = dead ? 0.0f : exp_fast(f[j] - center);
-                        acc1 += e4[j];
-                    }
-                    if constexpr (kCacheExp)
-                        *pw = make_uint4(__float_as_uint(e4[0]), __float_as_uint(e4[1]), __float_as_uint(e4[2]),
-                                         __float_as_uint(e4[3]));
                 }
             }
             for (int e = 0; e < 2; ++e) {
                 const long long cnt = e == 0 ? n_head : n_tail;
                 for (long long k = 0; k < cnt; ++k) {
-                    unsigned char *pe = edge_ptr(e, k);
-                    const float x = decode_one<TIN>(pe, in_sc);
-                    if constexpr (OP == OP_LN) {
-                        const float d = x - center;
-                        acc1 = fmaf(d, d, acc1);
-                    } else {
-                        const float ev = dead ? 0.0f : exp_fast(x - center);
-                        acc1 += ev;
-                        if constexpr (kCacheExp) *reinterpret_cast<float *>(pe) = ev;
+                    const float x = edge_x(e, k);
+                    if constexpr (OP == OP_SOFTMAX || OP == OP_LSE) acc0 = fmaxf(acc0, x);
+                    else if constexpr (OP == OP_LN) acc0 += x;
+                    else acc0 = fmaf(x, x, acc0);
+                }
+            }
+            const long long n_c = slice_count(s, V, P, c);
+            float part0, part1 = 0.0f;
+            if constexpr (kTwoSweep) {
+                const float r0 = (OP == OP_LN) ? cons_allreduce<false>(acc0, red, Tc) : cons_allreduce<true>(acc0, red, Tc);
+                const float center = (OP == OP_LN) ? (n_c > 0 ? r0 / static_cast<float>(n_c) : 0.0f) : r0;
+                const bool dead = (OP != OP_LN) && center == -INFINITY;
+                float acc1 = 0.0f;
+                if (!dead) {
+                    // ------ stage 1, second local sweep over shared memory
+                    for (int k = 0; k < nch; ++k) {
+                        const unsigned char *cb = chunk(k);
+                        const int gn = chunk_groups(k);
+                        for (int g = tid; g < gn; g += Tc) {
+                            float f[V];
+                            decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, in_sc);
+#pragma unroll
+                            for (int q = 0; q < V; ++q) {
+                                if constexpr (OP == OP_LN) {
+                                    const float d = f[q] - center;
+                                    acc1 = fmaf(d, d, acc1);
+                                } else {
+                                    acc1 += exp_fast(f[q] - center);
+                                }
+                            }
+                        }
+                    }
+                    for (int e = 0; e < 2; ++e) {
+                        const long long cnt = e == 0 ? n_head : n_tail;
+                        for (long long k = 0; k < cnt; ++k) {
+                            const float x = edge_x(e, k);
+                            if constexpr (OP == OP_LN) {
+                                const float d = x - center;
+                                acc1 = fmaf(d, d, acc1);
+                            } else {
+                                acc1 += exp_fast(x - center);
+                            }
+                        }
                     }
                 }
+                part0 = center;
+                part1 = cons_allreduce<false>(acc1, red, Tc);
+            } else {
+                part0 = cons_allreduce<false>(acc0, red, Tc);
             }
-        }
-        part0 = center;
-        part1 = block_allreduce<false>(acc1, red);
-    } else {
-        part0 = block_allreduce<false>(acc0, red);
-    }
-
-    // ---------------- DSMEM push all-gather (Eq. 5) and combine
-    Stats st;
-    if (P > 1) {
-        cluster_wait_acquire();  // start barrier: all peers are running
-        if (tid < P) {
-            const uint32_t dst = mapa_shared(smem_addr(&slots[c * 4]), static_cast<uint32_t>(tid));
-            if constexpr (OP == OP_RMS) st_cluster_f32(dst, part0);
-            else st_cluster_v2f32(dst, part0, part1);
-        }
-        cluster_arrive_release();
-        cluster_wait_acquire();
-        st = combine_partials<OP>(slots, 4, P, s, V, N, a.eps);
-    } else {
-        float p1[2] = {part0, part1};
-        st = combine_partials<OP>(p1, 2, 1, s, V, N, a.eps);
-    }
-
-    if constexpr (OP == OP_LSE) {
-        if (c == 0 && tid == 0) reinterpret_cast<float *>(a.out)[row] = st.a + logf(st.b);
-        return;
-    } else {
-        unsigned char *out_row = a.out + row * a.ld_out * osz;
-        const long long i_base = s.h0 + s.g_lo * V;  // element index of this CTA's first group
-        constexpr int vec_bytes = (V * osz) < 16 ? (V * osz) : 16;
-        const bool out_vec = ((reinterpret_cast<uintptr_t>(out_row) + s.h0 * osz) % vec_bytes) == 0;
-        const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + s.h0) & 15u) == 0);
-        const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + s.h0) & 15u) == 0);
-
-        // ------------- stage 2 (FP8 output of the norms): amax |h(x)|
-        float qmul = 1.0f;  // multiplier from y to the stored value
-        if constexpr (kFp8Stage) {
-            float am = 0.0f;
-            for (long long g = tid; g < ng; g += T) {
-                float f[V], gg[V], bb[V];
-                decode_group<TIN>(*reinterpret_cast<const uint4 *>(img_body + g * 16), f, in_sc);
-                load_affine<V>(a.gamma, i_base + g * V, g_vec, 1.0f, gg);
-                load_affine<V>(a.beta, i_base + g * V, b_vec, 0.0f, bb);
-#pragma unroll
-                for (int j = 0; j < V; ++j) am = fmaxf(am, fabsf(norm_h<OP>(f[j], st, gg[j], bb[j])));
-            }
-            for (int e = 0; e < 2; ++e) {
-                const long long cnt = e == 0 ? n_head : n_tail;
-                for (long long k = 0; k < cnt; ++k) {
-                    const long long i = e == 0 ? k : tail_i0 + k;
-                    const float x = decode_one<TIN>(edge_ptr(e, k), in_sc);
-                    const float gg = a.gamma ? a.gamma[i] : 1.0f, bb = a.beta ? a.beta[i] : 0.0f;
-                    am = fmaxf(am, fabsf(norm_h<OP>(x, st, gg, bb)));
+            if constexpr (OP == OP_LSE) {
+                // no reuse pass: release the slice now
+                for (int k = 0; k < nch; ++k) {
+                    __syncwarp();
+                    if ((tid & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
                 }
             }
-            am = block_allreduce<true>(am, red);
+
+            // ---------- DSMEM push all-gather (Eq. 5) and fixed-order combine
+            Stats st;
             if (P > 1) {
-                float *slots2 = slots + 64;
-                if (tid < P) st_cluster_f32(mapa_shared(smem_addr(&slots2[c * 4]), static_cast<uint32_t>(tid)), am);
-                cluster_arrive_release();
-                cluster_wait_acquire();
-                am = 0.0f;
-                for (int k = 0; k < P; ++k) am = fmaxf(am, slots2[k * 4]);
+                if (!waited_start) {
+                    cluster_wait_acquire();
+                    waited_start = true;
+                }
+                const float *sl = exchange_push<(OP == OP_RMS) ? 1 : 2>(part0, part1, slots, xbar, 0, par, xphase, P,
+                                                                         c, Tc, a.err);
+                st = combine_partials<OP>(sl, 4, P, s, V, N, a.eps);
+            } else {
+                const float p1[2] = {part0, part1};
+                st = combine_partials<OP>(p1, 2, 1, s, V, N, a.eps);
             }
-            qmul = am > 0.0f ? 448.0f / am : 1.0f;
-            if (c == 0 && tid == 0) a.out_scale[row] = am > 0.0f ? am / 448.0f : 1.0f;
-        }
 
-        // ------------- reuse pass: h over the retained slice, write out
-        if constexpr (OP == OP_SOFTMAX) {
-            const float inv = 1.0f / st.b;
-            // y = exp(x - M) / S;  FP8 codes are y / (1 / (448 S)) = 448 exp(x - M)
-            const float mul = (TOUT == DT_E4M3) ? 448.0f : inv;
-            const float cmul = (kCacheExp && part0 != -INFINITY) ? exp_fast(part0 - st.a) * mul : 0.0f;
-            if (TOUT == DT_E4M3 && c == 0 && tid == 0) a.out_scale[row] = inv * (1.0f / 448.0f);
-            for (long long g = tid; g < ng; g += T) {
-                float f[V], y[V];
-                decode_group<TIN>(*reinterpret_cast<const uint4 *>(img_body + g * 16), f, in_sc);
+            if constexpr (OP == OP_LSE) {
+                if (c == 0 && tid == 0) reinterpret_cast<float *>(a.out)[row] = st.a + logf(st.b);
+            } else {
+                unsigned char *out_row = a.out + row * a.ld_out * osz;
+                const long long i_base = s.h0 + s.g_lo * V;
+                constexpr int vec_bytes = (V * osz) < 16 ? (V * osz) : 16;
+                const bool out_vec = ((reinterpret_cast<uintptr_t>(out_row) + s.h0 * osz) % vec_bytes) == 0;
+                const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + s.h0) & 15u) == 0);
+                const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + s.h0) & 15u) == 0);
+
+                // ------ stage 2 (FP8 output of the norms): amax |h(x)|
+                float qmul = 1.0f;
+                if constexpr (kFp8Stage) {
+                    float am = 0.0f;
+                    for (int k = 0; k < nch; ++k) {
+                        const unsigned char *cb = chunk(k);
+                        const int gn = chunk_groups(k);
+                        for (int g = tid; g < gn; g += Tc) {
+                            float f[V], gg[V], bb[V];
+                            const long long i0 = i_base + (static_cast<long long>(k) * gpc + g) * V;
+                            decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, in_sc);
+                            load_affine<V>(a.gamma, i0, g_vec, 1.0f, gg);
+                            load_affine<V>(a.beta, i0, b_vec, 0.0f, bb);
 #pragma unroll
-                for (int j = 0; j < V; ++j) y[j] = kCacheExp ? f[j] * cmul : exp_fast(f[j] - st.a) * mul;
-                store_group<TOUT, V>(out_row + (i_base + g * V) * osz, y, out_vec);
-            }
-            for (int e = 0; e < 2; ++e) {
-                const long long cnt = e == 0 ? n_head : n_tail;
-                for (long long k = 0; k < cnt; ++k) {
-                    const long long i = e == 0 ? k : tail_i0 + k;
-                    const unsigned char *pe = edge_ptr(e, k);
-                    const float y = kCacheExp ? *reinterpret_cast<const float *>(pe) * cmul
-                                              : exp_fast(decode_one<TIN>(pe, in_sc) - st.a) * mul;
-                    store_one<TOUT>(out_row + i * osz, y);
+                            for (int q = 0; q < V; ++q)
+                                am = fmaxf(am, fabsf(norm_h<OP>(f[q], st, gg[q], OP == OP_LN ? bb[q] : 0.0f)));
+                        }
+                    }
+                    for (int e = 0; e < 2; ++e) {
+                        const long long cnt = e == 0 ? n_head : n_tail;
+                        for (long long k = 0; k < cnt; ++k) {
+                            const long long i = e == 0 ? k : tail_i0 + k;
+                            const float gg = a.gamma ? a.gamma[i] : 1.0f;
+                            const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
+                            am = fmaxf(am, fabsf(norm_h<OP>(edge_x(e, k), st, gg, bb)));
+                        }
+                    }
+                    am = cons_allreduce<true>(am, red, Tc);
+                    if (P > 1) {
+                        const float *sl = exchange_push<1>(am, 0.0f, slots, xbar, 1, par, xphase, P, c, Tc, a.err);
+                        am = 0.0f;
+                        for (int q = 0; q < P; ++q) am = fmaxf(am, sl[q * 4]);
+                    }
+                    qmul = am > 0.0f ? 448.0f / am : 1.0f;
+                    if (c == 0 && tid == 0) a.out_scale[row] = am > 0.0f ? am / 448.0f : 1.0f;
                 }
-            }
-        } else {
-            for (long long g = tid; g < ng; g += T) {
-                float f[V], gg[V], bb[V], y[V];
-                decode_group<TIN>(*reinterpret_cast<const uint4 *>(img_body + g * 16), f, in_sc);
-                load_affine<V>(a.gamma, i_base + g * V, g_vec, 1.0f, gg);
-                if constexpr (OP == OP_LN) load_affine<V>(a.beta, i_base + g * V, b_vec, 0.0f, bb);
+                const float inv = (OP == OP_SOFTMAX) ? 1.0f / st.b : 0.0f;
+                const float smul = (TOUT == DT_E4M3) ? 448.0f : inv;  // softmax: y (or its FP8 code) = exp(x - M) * smul
+                if constexpr (OP == OP_SOFTMAX && TOUT == DT_E4M3) {
+                    if (c == 0 && tid == 0) a.out_scale[row] = inv * (1.0f / 448.0f);
+                }
+                auto h = [&](float x, float g, float b) -> float {
+                    if constexpr (OP == OP_SOFTMAX) return exp_fast(x - st.a) * smul;
+                    else return norm_h<OP>(x, st, g, b) * qmul;
+                };
+
+                // ------ reuse pass: h over the retained slice, chunk by chunk
+                for (int k = 0; k < nch; ++k) {
+                    const unsigned char *cb = chunk(k);
+                    const int gn = chunk_groups(k);
+                    for (int g = tid; g < gn; g += Tc) {
+                        float f[V], gg[V], bb[V], y[V];
+                        const long long i0 = i_base + (static_cast<long long>(k) * gpc + g) * V;
+                        decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, in_sc);
+                        if constexpr (OP != OP_SOFTMAX) load_affine<V>(a.gamma, i0, g_vec, 1.0f, gg);
+                        if constexpr (OP == OP_LN) load_affine<V>(a.beta, i0, b_vec, 0.0f, bb);
 #pragma unroll
-                for (int j = 0; j < V; ++j) {
-                    const float bj = (OP == OP_LN) ? bb[j] : 0.0f;
-                    y[j] = norm_h<OP>(f[j], st, gg[j], bj) * qmul;
+                        for (int q = 0; q < V; ++q)
+                            y[q] = h(f[q], OP != OP_SOFTMAX ? gg[q] : 1.0f, OP == OP_LN ? bb[q] : 0.0f);
+                        store_group<TOUT, V>(out_row + i0 * osz, y, out_vec);
+                    }
+                    __syncwarp();
+                    if ((tid & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
                 }
-                store_group<TOUT, V>(out_row + (i_base + g * V) * osz, y, out_vec);
-            }
-            for (int e = 0; e < 2; ++e) {
-                const long long cnt = e == 0 ? n_head : n_tail;
-                for (long long k = 0; k < cnt; ++k) {
-                    const long long i = e == 0 ? k : tail_i0 + k;
-                    const float x = decode_one<TIN>(edge_ptr(e, k), in_sc);
-                    const float gg = a.gamma ? a.gamma[i] : 1.0f;
-                    const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
-                    store_one<TOUT>(out_row + i * osz, norm_h<OP>(x, st, gg, bb) * qmul);
+                for (int e = 0; e < 2; ++e) {
+                    const long long cnt = e == 0 ? n_head : n_tail;
+                    for (long long k = 0; k < cnt; ++k) {
+                        const long long i = e == 0 ? k : tail_i0 + k;
+                        const float gg = (OP != OP_SOFTMAX && a.gamma) ? a.gamma[i] : 1.0f;
+                        const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
+                        store_one<TOUT>(out_row + i * osz, h(edge_x(e, k), gg, bb));
+                    }
                 }
             }
+            j += nch;
         }
+    }
+    if (P > 1) {
+        if (!waited_start) cluster_wait_acquire();
+        cluster_arrive_release();  // end barrier: nobody exits while a peer may push into it
+        cluster_wait_acquire();
     }
 }
 
@@ -795,7 +880,7 @@ __global__ void k_tp_lse_final(const RowArgs a, long long nrows) {
 // Kernel table of one (input dtype) translation unit.
 // ----------------------------------------------------------------------
 struct KernelSet {
-    const void *staged;
+    const void *ring;
     const void *tp_fused;
     const void *tp_stats;
     const void *tp_amax;

@@ -101,8 +101,20 @@ def run_gpu(op, x_cpu, scale, *, out_dtype=None, plan=None, gamma=None, beta=Non
     sc = None if scale is None else scale.to(device)
     g = None if gamma is None else gamma.to(device)
     b = None if beta is None else beta.to(device)
-    C.run_ex(op, x, out, in_dtype=in_dtype, out_dtype=out_dtype, in_scale=sc, out_scale=osc, gamma=g, beta=b,
-             eps=eps, plan=plan)
+    kw = dict(in_dtype=in_dtype, out_dtype=out_dtype, in_scale=sc, out_scale=osc, gamma=g, beta=b, eps=eps)
+    if plan is not None and C.plan_check(op, x, out, plan, **kw) == C.ERR_UNSUPPORTED:
+        # Only a staged slice too large for one CTA's shared memory (Eq. 3)
+        # may be refused; the call must then refuse too, launching nothing.
+        assert plan.path in (C.PATH_ONE_CTA, C.PATH_CLUSTER), "two-pass plan refused"
+        P = 1 if plan.path == C.PATH_ONE_CTA else plan.cluster_size
+        isz = x.element_size()
+        body = -(-((cols * isz) // 16) // P) * 16
+        assert body > C.slice_capacity(C.FP8_E4M3) - 16 * 16, "legal slice refused"
+        n0 = C.launch_count()
+        assert C.run_ex_status(op, x, out, plan=plan, **kw) == C.ERR_UNSUPPORTED
+        assert C.launch_count() == n0
+        return None, None
+    C.run_ex(op, x, out, plan=plan, **kw)
     return out, osc
 
 
@@ -112,6 +124,8 @@ def check_against_oracle(op, x_cpu, scale, *, out_dtype=None, plan=None, gamma=N
     if out_dtype is None:
         out_dtype = C.F32 if op == C.LOGSUMEXP else in_dtype
     out, osc = run_gpu(op, x_cpu, scale, out_dtype=out_dtype, plan=plan, gamma=gamma, beta=beta, eps=eps)
+    if out is None:
+        return None, None
     torch.cuda.synchronize()
     assert C.device_error() == C.OK
     ref = reference(op, in_dtype, x_cpu, scale, gamma, beta, None if eps < 0 else eps)
