@@ -3,8 +3,12 @@
 Error bounds (the readings are listed in the design doc):
   FP32 output   softmax: max_i |y - y*| / |y*| <= 1e-5
                 logsumexp, layernorm, rmsnorm: max_i |y - y*| / max(|y*|, 1) <= 1e-5
-  BF16 output   |y - y*| <= one BF16 ulp of y*, ulp = 2^(floor(log2|y*|) - 7)
-                (2^-133 below the normal range)
+  BF16 output   |y - y*| <= ulp(y*) + e32(y*): one BF16 ulp of y*, ulp =
+                2^(floor(log2|y*|) - 7) (2^-133 below the normal range), on
+                top of the FP32 bound e32 (1e-5 |y*| for softmax, 1e-5
+                max(|y*|, 1) otherwise).  Without e32 the bound cannot be met
+                with FP32 statistics where the normalised output cancels to
+                |y*| << 1 (LayerNorm with beta).
   FP8 output    |q * s - y*| <= 2^(max(floor(log2(|y*| / s)), -6) - 3) * s, one
                 E4M3 quantum at the scaled value, and s within 1e-5 (relative)
                 of amax|y*| / 448
@@ -73,7 +77,8 @@ def error_metric(op: int, out_dtype: int, y: np.ndarray, ref: np.ndarray, out_sc
         a = np.abs(ref)
         e = np.floor(np.log2(np.where(a > 0, a, 1.0)))
         ulp = np.where(a >= 2.0 ** -126, np.exp2(e - 7), 2.0 ** -133)
-        return float(np.max(np.abs(y - ref) / ulp)) if y.size else 0.0
+        e32 = F32_TOL * (a if op == C.SOFTMAX else np.maximum(a, 1.0))
+        return float(np.max(np.abs(y - ref) / (ulp + e32))) if y.size else 0.0
     # FP8: y holds decoded codes (not yet scaled)
     s = np.asarray(out_scale, dtype=np.float64).reshape(-1, 1)
     t = np.abs(ref) / s
