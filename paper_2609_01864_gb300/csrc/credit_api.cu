@@ -125,12 +125,12 @@ bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring
     r.smem = kRingCtrl + static_cast<long long>(r.ring) * r.chunk;
     if (r.smem > di.smem_optin) return false;  // Eq. 3
     if (req_threads > 0) {
-        if (req_threads % 32 || req_threads < 96 || req_threads > 1024) return false;
+        if (req_threads % 32 || req_threads < 96 || req_threads > 288) return false;
         r.threads = req_threads;
     } else {
         long long tc = (r.chunk / 16 / 4 + 31) / 32 * 32;
         if (tc < 64) tc = 64;
-        if (tc > 512) tc = 512;
+        if (tc > 256) tc = 256;
         r.threads = static_cast<int>(tc) + 32;
     }
     *out = r;

@@ -171,354 +171,7 @@ __device__ __forceinline__ void copy_raw(unsigned char *dst, const unsigned char
 }
 
 // ======================================================================
-// Ring kernel: the cluster path (P > 1) and the one-CTA path (P == 1).
-//
-// Persistent: grid = nclusters * P CTAs with cluster dims (P, 1, 1); cluster
-// k handles rows k, k + nclusters, ...  The last warp is the producer (its
-// lane 0 issues the bulk copies); the other W warps consume.  Shared memory
-// holds a control area and a ring of `ring` chunk slots of `chunk_bytes`.
-// The slices of successive rows form one chunk sequence j = 0, 1, ...;
-// chunk j lives in slot j % ring.  full[s] completes when a chunk has landed
-// (transaction bytes), empty[s] when every consumer warp has finished the
-// reuse pass over it, so the next rows' slices stream in while the current
-// row is being written.  A slice needs ceil(body / chunk_bytes) <= ring slots
-// (Eq. 3).
-//
-// Exchange (Eq. 5): thread t < P of each CTA pushes the CTA's partials into
-// slot [c] of peer t with st.async, which completes on the peer's exchange
-// mbarrier; each CTA waits (bounded) on its own exchange mbarrier for the
-// P - 1 remote pushes, then combines its P local slots in fixed order.  The
-// slot arrays and exchange mbarriers are double-buffered by row parity, so a
-// peer can run one row ahead without overwriting partials still being read.
-// One cluster barrier at the start (every CTA's mbarriers are initialised
-// before any remote push) and one at the end (no CTA exits while a peer may
-// still push into it) are the only cluster-wide barriers.
-// ======================================================================
-constexpr int kRingCtrl = 2048;
-constexpr int kMaxRing = 32;
-// Control area layout:
-//   [0, 256)      full[32] mbarriers
-//   [256, 512)    empty[32] mbarriers
-//   [512, 544)    exchange mbarriers [stage][parity]
-//   [544, 1024)   reduction scratch (120 floats)
-//   [1024, 2048)  DSMEM slots [stage][parity][16 sources][4 floats]
-
-__device__ __forceinline__ float *slot_ptr(float *slots, int stage, int par, int c) {
-    return slots + ((stage * 2 + par) * 16 + c) * 4;
-}
-
-// All-reduce over the Tc consumer threads (named barrier 1).
-template <bool MAX>
-__device__ __forceinline__ float cons_allreduce(float v, float *red, int Tc) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = Tc >> 5;
-    v = MAX ? warp_max(v) : warp_sum(v);
-    if (lane == 0) red[wid] = v;
-    named_bar_sync(1, Tc);
-    if (wid == 0) {
-        float t = lane < nw ? red[lane] : (MAX ? -INFINITY : 0.0f);
-        t = MAX ? warp_max(t) : warp_sum(t);
-        if (lane == 0) red[32] = t;
-    }
-    named_bar_sync(1, Tc);
-    return red[32];
-}
-
-// Replicated push all-gather of NQ floats per CTA (consumer threads only).
-template <int NQ>
-__device__ __forceinline__ const float *exchange_push(float p0, float p1, float *slots, uint64_t *xbar, int stage,
-                                                      int par, uint32_t phase, int P, int c, int Tc, unsigned *err) {
-    const int tid = threadIdx.x;
-    float *mine = slot_ptr(slots, stage, par, c);
-    uint64_t *bar = &xbar[stage * 2 + par];
-    if (tid < P) {
-        if (tid == c) {
-            mine[0] = p0;
-            if (NQ == 2) mine[1] = p1;
-        } else {
-            // order this CTA's earlier reads of the slots before the peer's next writes
-            fence_acq_rel_cluster();
-            const uint32_t raddr = mapa_shared(smem_addr(mine), static_cast<uint32_t>(tid));
-            const uint32_t rbar = mapa_shared(smem_addr(bar), static_cast<uint32_t>(tid));
-            if (NQ == 2) st_async_v2f32(raddr, p0, p1, rbar);
-            else st_async_f32(raddr, p0, rbar);
-        }
-    }
-    if (tid == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>((P - 1) * NQ * 4));
-    named_bar_sync(1, Tc);
-    mbar_wait_bounded(bar, phase, err);
-    return slot_ptr(slots, stage, par, 0);
-}
-
-template <int OP, int TIN, int TOUT>
-__global__ void __launch_bounds__(1024, 1) k_ring(const RowArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *empty = full + 32;
-    uint64_t *xbar = full + 64;
-    float *red = reinterpret_cast<float *>(smem + 544);
-    float *slots = reinterpret_cast<float *>(smem + 1024);
-    unsigned char *ring = smem + kRingCtrl;
-
-    constexpr int isz = Fmt<TIN>::size, V = Fmt<TIN>::V;
-    constexpr int osz = Fmt<TOUT>::size;
-    constexpr bool kFp8Stage = (TOUT == DT_E4M3) && (OP == OP_LN || OP == OP_RMS);
-    constexpr bool kTwoSweep = (OP == OP_SOFTMAX || OP == OP_LSE || OP == OP_LN);
-
-    const int CH = a.chunk_bytes, K = a.ring, gpc = CH / 16;
-    const int P = static_cast<int>(cluster_nctarank());
-    const int c = P > 1 ? static_cast<int>(cluster_ctarank()) : 0;
-    const long long ncl = gridDim.x / P, cl = blockIdx.x / P;
-    const int tid = threadIdx.x, Tc = static_cast<int>(blockDim.x) - 32, W = Tc >> 5;
-    const long long N = a.cols;
-
-    if (tid == 0) {
-        for (int k = 0; k < K; ++k) {
-            mbar_init(&full[k], 1);
-            mbar_init(&empty[k], static_cast<uint32_t>(W));
-        }
-        for (int k = 0; k < 4; ++k) mbar_init(&xbar[k], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (P > 1) cluster_arrive_release();  // start barrier, split
-    bool waited_start = false;
-
-    if (tid >= Tc) {
-        // ------------------------------------------------------ producer warp
-        if (tid == Tc) {
-            long long j = 0;
-            for (long long row = cl; row < a.rows; row += ncl) {
-                const unsigned char *in_row = a.in + row * a.ld_in * isz;
-                const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), N, isz, P, c);
-                const long long body = (s.g_hi - s.g_lo) * 16;
-                const unsigned char *src = in_row + s.h0 * isz + s.g_lo * 16;
-                for (long long off = 0; off < body; off += CH, ++j) {
-                    const int slot = static_cast<int>(j % K);
-                    if (j >= K) mbar_wait_bounded(&empty[slot], static_cast<uint32_t>(((j / K) - 1) & 1), a.err);
-                    const uint32_t bytes = static_cast<uint32_t>(body - off < CH ? body - off : CH);
-                    mbar_arrive_expect_tx(&full[slot], bytes);
-                    bulk_g2s(ring + static_cast<size_t>(slot) * CH, src + off, bytes, &full[slot]);
-                }
-            }
-        }
-        __syncwarp();
-    } else {
-        // ------------------------------------------------------ consumer warps
-        long long j = 0;
-        int rr = 0;
-        for (long long row = cl; row < a.rows; row += ncl, ++rr) {
-            const unsigned char *in_row = a.in + row * a.ld_in * isz;
-            const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), N, isz, P, c);
-            const long long ng = s.g_hi - s.g_lo;
-            const int nch = static_cast<int>((ng * 16 + CH - 1) / CH);
-            const float in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
-            const long long n_head = (c == 0 && tid == 0) ? s.h0 : 0;
-            const long long n_tail = (c == P - 1 && tid == Tc - 1) ? s.t0 : 0;
-            const long long tail_i0 = s.h0 + s.G * V;
-            const int par = rr & 1;
-            const uint32_t xphase = static_cast<uint32_t>((rr >> 1) & 1);
-            auto chunk = [&](int k) -> const unsigned char * {
-                return ring + static_cast<size_t>((j + k) % K) * CH;
-            };
-            auto chunk_groups = [&](int k) -> int {
-                const long long r = ng - static_cast<long long>(k) * gpc;
-                return static_cast<int>(r < gpc ? r : gpc);
-            };
-            auto edge_x = [&](int e, long long k) -> float {
-                const long long i = e == 0 ? k : tail_i0 + k;
-                return decode_one<TIN>(in_row + i * isz, in_sc);
-            };
-
-            // ---------- stage 1, first local sweep (waits for each chunk)
-            float acc0 = (OP == OP_SOFTMAX || OP == OP_LSE) ? -INFINITY : 0.0f;
-            for (int k = 0; k < nch; ++k) {
-                const long long jk = j + k;
-                mbar_wait_bounded(&full[jk % K], static_cast<uint32_t>((jk / K) & 1), a.err);
-                const unsigned char *cb = chunk(k);
-                const int gn = chunk_groups(k);
-                for (int g = tid; g < gn; g += Tc) {
-                    float f[V];
-                    decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, in_sc);
-#pragma unroll
-                    for (int q = 0; q < V; ++q) {
-                        if constexpr (OP == OP_SOFTMAX || OP == OP_LSE) acc0 = fmaxf(acc0, f[q]);
-                        else if constexpr (OP == OP_LN) acc0 += f[q];
-                        else acc0 = fmaf(f[q], f[q], acc0);
-                    }
-                }
-            }
-            for (int e = 0; e < 2; ++e) {
-                const long long cnt = e == 0 ? n_head : n_tail;
-                for (long long k = 0; k < cnt; ++k) {
-                    const float x = edge_x(e, k);
-                    if constexpr (OP == OP_SOFTMAX || OP == OP_LSE) acc0 = fmaxf(acc0, x);
-                    else if constexpr (OP == OP_LN) acc0 += x;
-                    else acc0 = fmaf(x, x, acc0);
-                }
-            }
-            const long long n_c = slice_count(s, V, P, c);
-            float part0, part1 = 0.0f;
-            if constexpr (kTwoSweep) {
-                const float r0 = (OP == OP_LN) ? cons_allreduce<false>(acc0, red, Tc) : cons_allreduce<true>(acc0, red, Tc);
-                const float center = (OP == OP_LN) ? (n_c > 0 ? r0 / static_cast<float>(n_c) : 0.0f) : r0;
-                const bool dead = (OP != OP_LN) && center == -INFINITY;
-                float acc1 = 0.0f;
-                if (!dead) {
-                    // ------ stage 1, second local sweep over shared memory
-                    for (int k = 0; k < nch; ++k) {
-                        const unsigned char *cb = chunk(k);
-                        const int gn = chunk_groups(k);
-                        for (int g = tid; g < gn; g += Tc) {
-                            float f[V];
-                            decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, in_sc);
-#pragma unroll
-                            for (int q = 0; q < V; ++q) {
-                                if constexpr (OP == OP_LN) {
-                                    const float d = f[q] - center;
-                                    acc1 = fmaf(d, d, acc1);
-                                } else {
-                                    acc1 += exp_fast(f[q] - center);
-                                }
-                            }
-                        }
-                    }
-                    for (int e = 0; e < 2; ++e) {
-                        const long long cnt = e == 0 ? n_head : n_tail;
-                        for (long long k = 0; k < cnt; ++k) {
-                            const float x = edge_x(e, k);
-                            if constexpr (OP == OP_LN) {
-                                const float d = x - center;
-                                acc1 = fmaf(d, d, acc1);
-                            } else {
-                                acc1 += exp_fast(x - center);
-                            }
-                        }
-                    }
-                }
-                part0 = center;
-                part1 = cons_allreduce<false>(acc1, red, Tc);
-            } else {
-                part0 = cons_allreduce<false>(acc0, red, Tc);
-            }
-            if constexpr (OP == OP_LSE) {
-                // no reuse pass: release the slice now
-                for (int k = 0; k < nch; ++k) {
-                    __syncwarp();
-                    if ((tid & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
-                }
-            }
-
-            // ---------- DSMEM push all-gather (Eq. 5) and fixed-order combine
-            Stats st;
-            if (P > 1) {
-                if (!waited_start) {
-                    cluster_wait_acquire();
-                    waited_start = true;
-                }
-                const float *sl = exchange_push<(OP == OP_RMS) ? 1 : 2>(part0, part1, slots, xbar, 0, par, xphase, P,
-                                                                         c, Tc, a.err);
-                st = combine_partials<OP>(sl, 4, P, s, V, N, a.eps);
-            } else {
-                const float p1[2] = {part0, part1};
-                st = combine_partials<OP>(p1, 2, 1, s, V, N, a.eps);
-            }
-
-            if constexpr (OP == OP_LSE) {
-                if (c == 0 && tid == 0) reinterpret_cast<float *>(a.out)[row] = st.a + logf(st.b);
-            } else {
-                unsigned char *out_row = a.out + row * a.ld_out * osz;
-                const long long i_base = s.h0 + s.g_lo * V;
-                constexpr int vec_bytes = (V * osz) < 16 ? (V * osz) : 16;
-                const bool out_vec = ((reinterpret_cast<uintptr_t>(out_row) + s.h0 * osz) % vec_bytes) == 0;
-                const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + s.h0) & 15u) == 0);
-                const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + s.h0) & 15u) == 0);
-
-                // ------ stage 2 (FP8 output of the norms): amax |h(x)|
-                float qmul = 1.0f;
-                if constexpr (kFp8Stage) {
-                    float am = 0.0f;
-                    for (int k = 0; k < nch; ++k) {
-                        const unsigned char *cb = chunk(k);
-                        const int gn = chunk_groups(k);
-                        for (int g = tid; g < gn; g += Tc) {
-                            float f[V], gg[V], bb[V];
-                            const long long i0 = i_base + (static_cast<long long>(k) * gpc + g) * V;
-                            decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, in_sc);
-                            load_affine<V>(a.gamma, i0, g_vec, 1.0f, gg);
-                            load_affine<V>(a.beta, i0, b_vec, 0.0f, bb);
-#pragma unroll
-                            for (int q = 0; q < V; ++q)
-                                am = fmaxf(am, fabsf(norm_h<OP>(f[q], st, gg[q], OP == OP_LN ? bb[q] : 0.0f)));
-                        }
-                    }
-                    for (int e = 0; e < 2; ++e) {
-                        const long long cnt = e == 0 ? n_head : n_tail;
-                        for (long long k = 0; k < cnt; ++k) {
-                            const long long i = e == 0 ? k : tail_i0 + k;
-                            const float gg = a.gamma ? a.gamma[i] : 1.0f;
-                            const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
-                            am = fmaxf(am, fabsf(norm_h<OP>(edge_x(e, k), st, gg, bb)));
-                        }
-                    }
-                    am = cons_allreduce<true>(am, red, Tc);
-                    if (P > 1) {
-                        const float *sl = exchange_push<1>(am, 0.0f, slots, xbar, 1, par, xphase, P, c, Tc, a.err);
-                        am = 0.0f;
-                        for (int q = 0; q < P; ++q) am = fmaxf(am, sl[q * 4]);
-                    }
-                    qmul = am > 0.0f ? 448.0f / am : 1.0f;
-                    if (c == 0 && tid == 0) a.out_scale[row] = am > 0.0f ? am / 448.0f : 1.0f;
-                }
-                const float inv = (OP == OP_SOFTMAX) ? 1.0f / st.b : 0.0f;
-                const float smul = (TOUT == DT_E4M3) ? 448.0f : inv;  // softmax: y (or its FP8 code) = exp(x - M) * smul
-                if constexpr (OP == OP_SOFTMAX && TOUT == DT_E4M3) {
-                    if (c == 0 && tid == 0) a.out_scale[row] = inv * (1.0f / 448.0f);
-                }
-                auto h = [&](float x, float g, float b) -> float {
-                    if constexpr (OP == OP_SOFTMAX) return exp_fast(x - st.a) * smul;
-                    else return norm_h<OP>(x, st, g, b) * qmul;
-                };
-
-                // ------ reuse pass: h over the retained slice, chunk by chunk
-                for (int k = 0; k < nch; ++k) {
-                    const unsigned char *cb = chunk(k);
-                    const int gn = chunk_groups(k);
-                    for (int g = tid; g < gn; g += Tc) {
-                        float f[V], gg[V], bb[V], y[V];
-                        const long long i0 = i_base + (static_cast<long long>(k) * gpc + g) * V;
-                        decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, in_sc);
-                        if constexpr (OP != OP_SOFTMAX) load_affine<V>(a.gamma, i0, g_vec, 1.0f, gg);
-                        if constexpr (OP == OP_LN) load_affine<V>(a.beta, i0, b_vec, 0.0f, bb);
-#pragma unroll
-                        for (int q = 0; q < V; ++q)
-                            y[q] = h(f[q], OP != OP_SOFTMAX ? gg[q] : 1.0f, OP == OP_LN ? bb[q] : 0.0f);
-                        store_group<TOUT, V>(out_row + i0 * osz, y, out_vec);
-                    }
-                    __syncwarp();
-                    if ((tid & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
-                }
-                for (int e = 0; e < 2; ++e) {
-                    const long long cnt = e == 0 ? n_head : n_tail;
-                    for (long long k = 0; k < cnt; ++k) {
-                        const long long i = e == 0 ? k : tail_i0 + k;
-                        const float gg = (OP != OP_SOFTMAX && a.gamma) ? a.gamma[i] : 1.0f;
-                        const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
-                        store_one<TOUT>(out_row + i * osz, h(edge_x(e, k), gg, bb));
-                    }
-                }
-            }
-            j += nch;
-        }
-    }
-    if (P > 1) {
-        if (!waited_start) cluster_wait_acquire();
-        cluster_arrive_release();  // end barrier: nobody exits while a peer may push into it
-        cluster_wait_acquire();
-    }
-}
-
-// ======================================================================
-// Streaming statistics over global memory (two-pass path)
+// Per-thread streaming statistics (one sweep; used by every path)
 // ======================================================================
 template <int OP> struct Stream;
 
@@ -591,13 +244,77 @@ template <> struct Stream<OP_RMS> {
     __device__ __forceinline__ void add1(float x) { ss = fmaf(x, x, ss); }
 };
 
+// ======================================================================
+// Ring kernel: the cluster path (P > 1) and the one-CTA path (P == 1).
+//
+// Persistent: grid = nclusters * P CTAs with cluster dims (P, 1, 1); cluster
+// k handles rows k, k + nclusters, ...  The last warp is the producer (its
+// lane 0 issues the bulk copies); the other W warps consume.  Shared memory
+// holds a control area and a ring of `ring` chunk slots of `chunk_bytes`.
+// The slices of successive rows form one chunk sequence j = 0, 1, ...;
+// chunk j lives in slot j % ring.  full[s] completes when a chunk has landed
+// (transaction bytes), empty[s] when every consumer warp has finished the
+// reuse pass over it, so the next rows' slices stream in while the current
+// row is being written.  A slice needs ceil(body / chunk_bytes) <= ring slots
+// (Eq. 3).
+//
+// Exchange (Eq. 5): thread t < P of each CTA pushes the CTA's partials into
+// slot [c] of peer t with st.async, which completes on the peer's exchange
+// mbarrier; each CTA waits (bounded) on its own exchange mbarrier for the
+// P - 1 remote pushes, then combines its P local slots in fixed order.  The
+// slot arrays and exchange mbarriers are double-buffered by row parity, so a
+// peer can run one row ahead without overwriting partials still being read.
+// One cluster barrier at the start (every CTA's mbarriers are initialised
+// before any remote push) and one at the end (no CTA exits while a peer may
+// still push into it) are the only cluster-wide barriers.
+// ======================================================================
+constexpr int kRingCtrl = 2048;
+constexpr int kMaxRing = 32;
+// Control area layout:
+//   [0, 256)      full[32] mbarriers
+//   [256, 512)    empty[32] mbarriers
+//   [512, 544)    exchange mbarriers [stage][parity]
+//   [544, 1024)   reduction scratch (120 floats)
+//   [1024, 2048)  DSMEM slots [stage][parity][16 sources][4 floats]
+
+__device__ __forceinline__ float *slot_ptr(float *slots, int stage, int par, int c) {
+    return slots + ((stage * 2 + par) * 16 + c) * 4;
+}
+
+// All-reduce over the Tc consumer threads (named barrier 1).
+template <bool MAX>
+__device__ __forceinline__ float cons_allreduce(float v, float *red, int Tc) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = Tc >> 5;
+    v = MAX ? warp_max(v) : warp_sum(v);
+    if (lane == 0) red[wid] = v;
+    named_bar_sync(1, Tc);
+    if (wid == 0) {
+        float t = lane < nw ? red[lane] : (MAX ? -INFINITY : 0.0f);
+        t = MAX ? warp_max(t) : warp_sum(t);
+        if (lane == 0) red[32] = t;
+    }
+    named_bar_sync(1, Tc);
+    return red[32];
+}
+
 // Deterministic block reduction of a Stream state; returns the CTA partial
 // (p0, p1) in the same format as the staged kernel's partials.
+// Tc threads take part (the first Tc of the block); bar_id 0 is
+// __syncthreads-equivalent for the whole block, 1 is the consumer barrier.
+__device__ __forceinline__ void sync_group(int bar_id, int Tc) {
+    if (bar_id == 0) __syncthreads();
+    else named_bar_sync(bar_id, Tc);
+}
+
 template <int OP>
-__device__ __forceinline__ float2 block_reduce_stream(Stream<OP> st, float *red, long long n_c) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ __forceinline__ float2 block_reduce_stream(Stream<OP> st, float *red, long long n_c, int bar_id = 0,
+                                                      int Tc = 0) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (Tc == 0) Tc = blockDim.x;
+    const int nw = Tc >> 5;
     if constexpr (OP == OP_RMS) {
-        return make_float2(block_allreduce<false>(st.ss, red), 0.0f);
+        if (bar_id == 0) return make_float2(block_allreduce<false>(st.ss, red), 0.0f);
+        return make_float2(cons_allreduce<false>(st.ss, red, Tc), 0.0f);
     } else if constexpr (OP == OP_LN) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -618,17 +335,17 @@ __device__ __forceinline__ float2 block_reduce_stream(Stream<OP> st, float *red,
             red[3 * wid + 1] = st.mu;
             red[3 * wid + 2] = st.m2;
         }
-        __syncthreads();
+        sync_group(bar_id, Tc);
         if (threadIdx.x == 0) {
             Stream<OP_LN> t;
             for (int w = 0; w < nw; ++w) t.merge3(red[3 * w], red[3 * w + 1], red[3 * w + 2]);
             red[96] = t.mu;
             red[97] = t.m2;
         }
-        __syncthreads();
+        sync_group(bar_id, Tc);
         (void)n_c;
         const float2 r = make_float2(red[96], red[97]);
-        __syncthreads();
+        sync_group(bar_id, Tc);
         return r;
     } else {
 #pragma unroll
@@ -648,17 +365,281 @@ __device__ __forceinline__ float2 block_reduce_stream(Stream<OP> st, float *red,
             red[2 * wid] = st.m;
             red[2 * wid + 1] = st.s;
         }
-        __syncthreads();
+        sync_group(bar_id, Tc);
         if (threadIdx.x == 0) {
             Stream<OP> t;
             for (int w = 0; w < nw; ++w) t.merge(red[2 * w], red[2 * w + 1]);
             red[96] = t.m;
             red[97] = t.s;
         }
-        __syncthreads();
+        sync_group(bar_id, Tc);
         const float2 r = make_float2(red[96], red[97]);
-        __syncthreads();
+        sync_group(bar_id, Tc);
         return r;
+    }
+}
+
+// Replicated push all-gather of NQ floats per CTA (consumer threads only).
+template <int NQ>
+__device__ __forceinline__ const float *exchange_push(float p0, float p1, float *slots, uint64_t *xbar, int stage,
+                                                      int par, uint32_t phase, int P, int c, int Tc, unsigned *err) {
+    const int tid = threadIdx.x;
+    float *mine = slot_ptr(slots, stage, par, c);
+    uint64_t *bar = &xbar[stage * 2 + par];
+    if (tid < P) {
+        if (tid == c) {
+            mine[0] = p0;
+            if (NQ == 2) mine[1] = p1;
+        } else {
+            // order this CTA's earlier reads of the slots before the peer's next writes
+            fence_acq_rel_cluster();
+            const uint32_t raddr = mapa_shared(smem_addr(mine), static_cast<uint32_t>(tid));
+            const uint32_t rbar = mapa_shared(smem_addr(bar), static_cast<uint32_t>(tid));
+            if (NQ == 2) st_async_v2f32(raddr, p0, p1, rbar);
+            else st_async_f32(raddr, p0, rbar);
+        }
+    }
+    if (tid == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>((P - 1) * NQ * 4));
+    named_bar_sync(1, Tc);
+    mbar_wait_bounded(bar, phase, err);
+    return slot_ptr(slots, stage, par, 0);
+}
+
+// Visit the gn 16-byte groups of one staged chunk, groups tid, tid + Tc, ...
+// U shared-memory loads are issued before any of them is used.
+template <int TIN, class F>
+__device__ __forceinline__ void visit_chunk(const unsigned char *cb, int gn, int tid, int Tc, float in_sc, F &&fn) {
+    constexpr int V = Fmt<TIN>::V;
+    constexpr int U = (V == 16) ? 2 : 4;
+    int g = tid;
+    for (; g + (U - 1) * Tc < gn; g += U * Tc) {
+        uint4 w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) w[u] = *reinterpret_cast<const uint4 *>(cb + (g + u * Tc) * 16);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            float f[V];
+            decode_group<TIN>(w[u], f, in_sc);
+            fn(g + u * Tc, f);
+        }
+    }
+    for (; g < gn; g += Tc) {
+        float f[V];
+        decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, in_sc);
+        fn(g, f);
+    }
+}
+
+template <int OP, int TIN, int TOUT>
+__global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + 32;
+    uint64_t *xbar = full + 64;
+    float *red = reinterpret_cast<float *>(smem + 544);
+    float *slots = reinterpret_cast<float *>(smem + 1024);
+    unsigned char *ring = smem + kRingCtrl;
+
+    constexpr int isz = Fmt<TIN>::size, V = Fmt<TIN>::V;
+    constexpr int SV = V < 8 ? V : 8;  // outputs produced per step of the reuse pass
+    constexpr int osz = Fmt<TOUT>::size;
+    constexpr bool kFp8Stage = (TOUT == DT_E4M3) && (OP == OP_LN || OP == OP_RMS);
+
+    const int CH = a.chunk_bytes, K = a.ring, gpc = CH / 16;
+    const int P = static_cast<int>(cluster_nctarank());
+    const int c = P > 1 ? static_cast<int>(cluster_ctarank()) : 0;
+    const long long ncl = gridDim.x / P, cl = blockIdx.x / P;
+    const int tid = threadIdx.x, Tc = static_cast<int>(blockDim.x) - 32, W = Tc >> 5;
+    const long long N = a.cols;
+
+    if (tid == 0) {
+        for (int k = 0; k < K; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], static_cast<uint32_t>(W));
+        }
+        for (int k = 0; k < 4; ++k) mbar_init(&xbar[k], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (P > 1) cluster_arrive_release();  // start barrier, split
+    bool waited_start = false;
+
+    if (tid >= Tc) {
+        // ------------------------------------------------------ producer warp
+        if (tid == Tc) {
+            long long j = 0;
+            for (long long row = cl; row < a.rows; row += ncl) {
+                const unsigned char *in_row = a.in + row * a.ld_in * isz;
+                const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), N, isz, P, c);
+                const long long body = (s.g_hi - s.g_lo) * 16;
+                const unsigned char *src = in_row + s.h0 * isz + s.g_lo * 16;
+                for (long long off = 0; off < body; off += CH, ++j) {
+                    const int slot = static_cast<int>(j % K);
+                    if (j >= K) mbar_wait_bounded(&empty[slot], static_cast<uint32_t>(((j / K) - 1) & 1), a.err);
+                    const uint32_t bytes = static_cast<uint32_t>(body - off < CH ? body - off : CH);
+                    mbar_arrive_expect_tx(&full[slot], bytes);
+                    bulk_g2s(ring + static_cast<size_t>(slot) * CH, src + off, bytes, &full[slot]);
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------ consumer warps
+        long long j = 0;
+        int rr = 0;
+        for (long long row = cl; row < a.rows; row += ncl, ++rr) {
+            const unsigned char *in_row = a.in + row * a.ld_in * isz;
+            const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), N, isz, P, c);
+            const long long ng = s.g_hi - s.g_lo;
+            const int nch = static_cast<int>((ng * 16 + CH - 1) / CH);
+            const float in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
+            const long long n_head = (c == 0 && tid == 0) ? s.h0 : 0;
+            const long long n_tail = (c == P - 1 && tid == Tc - 1) ? s.t0 : 0;
+            const long long tail_i0 = s.h0 + s.G * V;
+            const int par = rr & 1;
+            const uint32_t xphase = static_cast<uint32_t>((rr >> 1) & 1);
+            auto chunk = [&](int k) -> const unsigned char * {
+                return ring + static_cast<size_t>((j + k) % K) * CH;
+            };
+            auto chunk_groups = [&](int k) -> int {
+                const long long r = ng - static_cast<long long>(k) * gpc;
+                return static_cast<int>(r < gpc ? r : gpc);
+            };
+            auto edge_x = [&](int e, long long k) -> float {
+                const long long i = e == 0 ? k : tail_i0 + k;
+                return decode_one<TIN>(in_row + i * isz, in_sc);
+            };
+
+            // ---------- stage 1: one local sweep (waits for each chunk as it lands)
+            Stream<OP> acc;
+            for (int k = 0; k < nch; ++k) {
+                const long long jk = j + k;
+                mbar_wait_bounded(&full[jk % K], static_cast<uint32_t>((jk / K) & 1), a.err);
+                visit_chunk<TIN>(chunk(k), chunk_groups(k), tid, Tc, in_sc,
+                                 [&](int, const float(&f)[V]) { acc.add(f); });
+            }
+            for (int e = 0; e < 2; ++e) {
+                const long long cnt = e == 0 ? n_head : n_tail;
+                for (long long k = 0; k < cnt; ++k) acc.add1(edge_x(e, k));
+            }
+            const float2 part = block_reduce_stream<OP>(acc, red, slice_count(s, V, P, c), 1, Tc);
+            const float part0 = part.x, part1 = part.y;
+            if constexpr (OP == OP_LSE) {
+                // no reuse pass: release the slice now
+                for (int k = 0; k < nch; ++k) {
+                    __syncwarp();
+                    if ((tid & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
+                }
+            }
+
+            // ---------- DSMEM push all-gather (Eq. 5) and fixed-order combine
+            Stats st;
+            if (P > 1) {
+                if (!waited_start) {
+                    cluster_wait_acquire();
+                    waited_start = true;
+                }
+                const float *sl = exchange_push<(OP == OP_RMS) ? 1 : 2>(part0, part1, slots, xbar, 0, par, xphase, P,
+                                                                         c, Tc, a.err);
+                st = combine_partials<OP>(sl, 4, P, s, V, N, a.eps);
+            } else {
+                const float p1[2] = {part0, part1};
+                st = combine_partials<OP>(p1, 2, 1, s, V, N, a.eps);
+            }
+
+            if constexpr (OP == OP_LSE) {
+                if (c == 0 && tid == 0) reinterpret_cast<float *>(a.out)[row] = st.a + logf(st.b);
+            } else {
+                unsigned char *out_row = a.out + row * a.ld_out * osz;
+                const long long i_base = s.h0 + s.g_lo * V;
+                constexpr int vec_bytes = (SV * osz) < 16 ? (SV * osz) : 16;
+                const bool out_vec = ((reinterpret_cast<uintptr_t>(out_row) + s.h0 * osz) % vec_bytes) == 0;
+                const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + s.h0) & 15u) == 0);
+                const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + s.h0) & 15u) == 0);
+
+                // ------ stage 2 (FP8 output of the norms): amax |h(x)|
+                float qmul = 1.0f;
+                if constexpr (kFp8Stage) {
+                    float am = 0.0f;
+                    for (int k = 0; k < nch; ++k) {
+                        const long long kg = static_cast<long long>(k) * gpc;
+                        visit_chunk<TIN>(chunk(k), chunk_groups(k), tid, Tc, in_sc, [&](int g, const float(&f)[V]) {
+#pragma unroll
+                            for (int hv = 0; hv < V; hv += SV) {
+                                float gg[SV], bb[SV];
+                                const long long i0 = i_base + (kg + g) * V + hv;
+                                load_affine<SV>(a.gamma, i0, g_vec, 1.0f, gg);
+                                load_affine<SV>(a.beta, i0, b_vec, 0.0f, bb);
+#pragma unroll
+                                for (int q = 0; q < SV; ++q)
+                                    am = fmaxf(am, fabsf(norm_h<OP>(f[hv + q], st, gg[q], OP == OP_LN ? bb[q] : 0.0f)));
+                            }
+                        });
+                    }
+                    for (int e = 0; e < 2; ++e) {
+                        const long long cnt = e == 0 ? n_head : n_tail;
+                        for (long long k = 0; k < cnt; ++k) {
+                            const long long i = e == 0 ? k : tail_i0 + k;
+                            const float gg = a.gamma ? a.gamma[i] : 1.0f;
+                            const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
+                            am = fmaxf(am, fabsf(norm_h<OP>(edge_x(e, k), st, gg, bb)));
+                        }
+                    }
+                    am = cons_allreduce<true>(am, red, Tc);
+                    if (P > 1) {
+                        const float *sl = exchange_push<1>(am, 0.0f, slots, xbar, 1, par, xphase, P, c, Tc, a.err);
+                        am = 0.0f;
+                        for (int q = 0; q < P; ++q) am = fmaxf(am, sl[q * 4]);
+                    }
+                    qmul = am > 0.0f ? 448.0f / am : 1.0f;
+                    if (c == 0 && tid == 0) a.out_scale[row] = am > 0.0f ? am / 448.0f : 1.0f;
+                }
+                const float inv = (OP == OP_SOFTMAX) ? 1.0f / st.b : 0.0f;
+                const float smul = (TOUT == DT_E4M3) ? 448.0f : inv;  // softmax: y (or its FP8 code) = exp(x - M) * smul
+                if constexpr (OP == OP_SOFTMAX && TOUT == DT_E4M3) {
+                    if (c == 0 && tid == 0) a.out_scale[row] = inv * (1.0f / 448.0f);
+                }
+                auto h = [&](float x, float g, float b) -> float {
+                    if constexpr (OP == OP_SOFTMAX) return exp_fast(x - st.a) * smul;
+                    else return norm_h<OP>(x, st, g, b) * qmul;
+                };
+
+                // ------ reuse pass: h over the retained slice, chunk by chunk
+                for (int k = 0; k < nch; ++k) {
+                    const long long kg = static_cast<long long>(k) * gpc;
+                    visit_chunk<TIN>(chunk(k), chunk_groups(k), tid, Tc, in_sc, [&](int g, const float(&f)[V]) {
+#pragma unroll
+                        for (int hv = 0; hv < V; hv += SV) {
+                            float gg[SV], bb[SV], y[SV];
+                            const long long i0 = i_base + (kg + g) * V + hv;
+                            if constexpr (OP != OP_SOFTMAX) load_affine<SV>(a.gamma, i0, g_vec, 1.0f, gg);
+                            if constexpr (OP == OP_LN) load_affine<SV>(a.beta, i0, b_vec, 0.0f, bb);
+#pragma unroll
+                            for (int q = 0; q < SV; ++q)
+                                y[q] = h(f[hv + q], OP != OP_SOFTMAX ? gg[q] : 1.0f, OP == OP_LN ? bb[q] : 0.0f);
+                            store_group<TOUT, SV>(out_row + i0 * osz, y, out_vec);
+                        }
+                    });
+                    __syncwarp();
+                    if ((tid & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
+                }
+                for (int e = 0; e < 2; ++e) {
+                    const long long cnt = e == 0 ? n_head : n_tail;
+                    for (long long k = 0; k < cnt; ++k) {
+                        const long long i = e == 0 ? k : tail_i0 + k;
+                        const float gg = (OP != OP_SOFTMAX && a.gamma) ? a.gamma[i] : 1.0f;
+                        const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
+                        store_one<TOUT>(out_row + i * osz, h(edge_x(e, k), gg, bb));
+                    }
+                }
+            }
+            j += nch;
+        }
+    }
+    if (P > 1) {
+        if (!waited_start) cluster_wait_acquire();
+        cluster_arrive_release();  // end barrier: nobody exits while a peer may push into it
+        cluster_wait_acquire();
     }
 }
 
