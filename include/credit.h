@@ -124,8 +124,11 @@ credit_status credit_rmsnorm(const void *in, void *out, int64_t rows, int64_t co
  *   ctas_per_row  CTAs that share one row: P for CLUSTER, 1 for ONE_CTA,
  *                 G >= 1 for TWO_PASS (G > 1 uses the workspace)
  *   threads       threads per CTA (multiple of 32; 0 = default).  Staged
- *                 paths: consumer threads + one producer warp (96..1024);
- *                 two-pass: 64..1024
+ *                 paths: reducer + writer threads + one producer warp
+ *                 (96..288); two-pass: 64..1024
+ *   reducer_threads  staged paths: threads that reduce and exchange (the rest
+ *                 of the non-producer threads write); multiple of 32, 0 =
+ *                 default (half)
  *   ring_chunks   staged paths: chunk slots of the shared-memory ring
  *                 (>= chunks of one slice; 0 = default)
  *   chunk_bytes   staged paths: bytes per chunk (multiple of 16; 0 = default)
@@ -141,6 +144,7 @@ typedef struct {
     int32_t threads;
     int32_t ring_chunks;
     int32_t chunk_bytes;
+    int32_t reducer_threads;
     int64_t smem_bytes;
     float predicted_us;
     int32_t source;
@@ -196,6 +200,18 @@ credit_status credit_run_ex(const credit_args *args, const credit_plan_t *plan,
  * if not, CREDIT_ERR_INVALID_ARG for bad arguments.  Launches nothing.
  */
 credit_status credit_plan_check(const credit_args *args, const credit_plan_t *plan);
+
+/*
+ * credit_set_trace -- phase tracing of the staged (ring) kernel.  While a
+ * buffer is set, the first 32 CTAs of every staged launch write global-timer
+ * stamps (ns) for their first R = bytes / (32 * 8 * 8) rows into it, as
+ * uint64 [cta][row][8]: 0 row start, 1 stage-1 sweep done, 2 CTA reduction
+ * done, 3 DSMEM exchange done, 4 reuse pass done, 5 producer issued the row's
+ * last chunk (6, 7 unused).  device_buf: caller-owned device memory, 8-byte
+ * aligned; NULL turns tracing off.  Not thread-safe against concurrent
+ * launches; a debugging aid, off by default.
+ */
+credit_status credit_set_trace(void *device_buf, int64_t bytes);
 
 /*
  * credit_device_error -- synchronise `stream`, then read and clear the

@@ -37,7 +37,7 @@ class CreditError(RuntimeError):
 class PlanT(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("ctas_per_row", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("ring_chunks", ctypes.c_int32), ("chunk_bytes", ctypes.c_int32),
-                ("smem_bytes", ctypes.c_int64), ("predicted_us", ctypes.c_float), ("source", ctypes.c_int32)]
+                ("reducer_threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int64), ("predicted_us", ctypes.c_float), ("source", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,6 +83,8 @@ def lib() -> ctypes.CDLL:
             L.credit_plan_ex.argtypes = [i32, i64, i64, i32, i32, ctypes.POINTER(PlanT)]
             L.credit_run_ex.restype = i32
             L.credit_run_ex.argtypes = [ctypes.POINTER(ArgsT), ctypes.POINTER(PlanT), vp]
+            L.credit_set_trace.restype = i32
+            L.credit_set_trace.argtypes = [vp, i64]
             L.credit_plan_check.restype = i32
             L.credit_plan_check.argtypes = [ctypes.POINTER(ArgsT), ctypes.POINTER(PlanT)]
             L.credit_device_error.restype = i32
@@ -162,7 +164,7 @@ def rmsnorm(x, out=None, stream=None):
 
 
 def make_plan(path: int, cluster_size: int = 1, ctas_per_row: int = 1, threads: int = 0, ring_chunks: int = 0,
-              chunk_bytes: int = 0) -> PlanT:
+              chunk_bytes: int = 0, reducer_threads: int = 0) -> PlanT:
     p = PlanT()
     p.path = path
     p.cluster_size = cluster_size
@@ -170,6 +172,7 @@ def make_plan(path: int, cluster_size: int = 1, ctas_per_row: int = 1, threads: 
     p.threads = threads
     p.ring_chunks = ring_chunks
     p.chunk_bytes = chunk_bytes
+    p.reducer_threads = reducer_threads
     return p
 
 
@@ -224,6 +227,14 @@ def run_ex_status(*args, **kw) -> int:
         return run_ex(*args, **kw)
     except CreditError as e:
         return e.status
+
+
+def set_trace(buf=None) -> None:
+    """credit_set_trace: buf is a uint64 CUDA tensor (or None to stop)."""
+    if buf is None:
+        _check(lib().credit_set_trace(None, 0), "credit_set_trace")
+    else:
+        _check(lib().credit_set_trace(_ptr(buf), buf.numel() * buf.element_size()), "credit_set_trace")
 
 
 def device_error(stream=None) -> int:

@@ -94,7 +94,7 @@ int dtype_size(int dt) { return dt == DT_F32 ? 4 : (dt == DT_BF16 ? 2 : 1); }
 // groups, G = floor(N * isz / 16).  Eq. 3: the slice must fit the ring, i.e.
 // kRingCtrl + ceil(body / chunk) * chunk <= the opt-in shared memory.
 bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring, int req_chunk, int req_threads,
-                 RingCfg *out) {
+                 int req_reducers, RingCfg *out) {
     if (P < 1 || P > kMaxCluster || N <= 0) return false;
     const long long groups = (N * isz) / 16;
     const long long per = (groups + P - 1) / P;
@@ -129,10 +129,19 @@ bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring
         r.threads = req_threads;
     } else {
         long long tc = (r.chunk / 16 / 4 + 31) / 32 * 32;
-        if (tc < 64) tc = 64;
+        if (tc < 128) tc = 128;
         if (tc > 256) tc = 256;
         r.threads = static_cast<int>(tc) + 32;
     }
+    const int tp = r.threads - 32;
+    if (req_reducers > 0) {
+        if (req_reducers % 32 || req_reducers >= tp) return false;
+        r.reducers = req_reducers;
+    } else {
+        r.reducers = (tp / 2) / 32 * 32;
+        if (r.reducers < 32) r.reducers = 32;
+    }
+    if (tp - r.reducers < 32) return false;
     *out = r;
     return true;
 }
@@ -310,7 +319,7 @@ credit_status check_plan(int device, const credit_args *a, const credit_plan_t *
         if (P < 1 || P > kMaxCluster) return CREDIT_ERR_UNSUPPORTED;
         if (p->path == CREDIT_PATH_CLUSTER && P < 2) return CREDIT_ERR_UNSUPPORTED;
         RingCfg rc;
-        if (!ring_config(*di, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, p->threads, &rc))
+        if (!ring_config(*di, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, p->threads, p->reducer_threads, &rc))
             return CREDIT_ERR_UNSUPPORTED;  // Eq. 3
         if (ring_max_clusters(device, a->op, a->in_dtype, tout, P, rc.threads, rc.smem) <= 0)
             return CREDIT_ERR_UNSUPPORTED;
@@ -325,6 +334,9 @@ credit_status check_plan(int device, const credit_args *a, const credit_plan_t *
     default: return CREDIT_ERR_UNSUPPORTED;
     }
 }
+
+static unsigned long long *g_trace_buf = nullptr;
+static int g_trace_rows = 0;
 
 static RowArgs make_row_args(const credit_args *a, unsigned *err, float *ws) {
     RowArgs r;
@@ -345,6 +357,9 @@ static RowArgs make_row_args(const credit_args *a, unsigned *err, float *ws) {
     r.G = 1;
     r.chunk_bytes = 0;
     r.ring = 0;
+    r.reducers = 0;
+    r.trace = g_trace_buf;
+    r.trace_rows = g_trace_rows;
     r.row0 = 0;
     return r;
 }
@@ -395,7 +410,7 @@ credit_status run_with_plan(int device, const credit_args *a, const credit_plan_
     if (p->path == CREDIT_PATH_ONE_CTA || p->path == CREDIT_PATH_CLUSTER) {
         const int P = p->path == CREDIT_PATH_ONE_CTA ? 1 : p->cluster_size;
         RingCfg rc;
-        if (!ring_config(d.info, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, p->threads, &rc))
+        if (!ring_config(d.info, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, p->threads, p->reducer_threads, &rc))
             return CREDIT_ERR_UNSUPPORTED;
         credit_status st = prepare_kernel(d, ks.ring, true);
         if (st != CREDIT_OK) return st;
@@ -403,11 +418,14 @@ credit_status run_with_plan(int device, const credit_args *a, const credit_plan_
         if (maxc <= 0) return CREDIT_ERR_UNSUPPORTED;
         const long long ncl = rows < maxc ? rows : maxc;
         if (std::getenv("CREDIT_LOG"))
-            std::fprintf(stderr, "credit: ring op=%d P=%d clusters=%lld (max %d) threads=%d chunk=%d ring=%d smem=%lld\n",
-                         a->op, P, ncl, maxc, rc.threads, rc.chunk, rc.ring, rc.smem);
+            std::fprintf(stderr,
+                         "credit: ring op=%d P=%d clusters=%lld (max %d) threads=%d reducers=%d chunk=%d ring=%d "
+                         "smem=%lld\n",
+                         a->op, P, ncl, maxc, rc.threads, rc.reducers, rc.chunk, rc.ring, rc.smem);
         RowArgs r = base;
         r.chunk_bytes = rc.chunk;
         r.ring = rc.ring;
+        r.reducers = rc.reducers;
         void *args[] = {&r};
         cudaError_t e = launch(ks.ring, dim3(static_cast<unsigned>(P * ncl)), dim3(rc.threads),
                                static_cast<size_t>(rc.smem), P, s, args);
@@ -495,6 +513,19 @@ credit_status credit_run_ex(const credit_args *args, const credit_plan_t *plan, 
     }
     if ((st = check_plan(dev, args, &chosen)) != CREDIT_OK) return st;
     return run_with_plan(dev, args, &chosen, stream);
+}
+
+credit_status credit_set_trace(void *device_buf, int64_t bytes) {
+    if (device_buf == nullptr || bytes <= 0) {
+        g_trace_buf = nullptr;
+        g_trace_rows = 0;
+        return CREDIT_OK;
+    }
+    const int64_t per_row = static_cast<int64_t>(kTraceCtas) * kTraceFields * 8;
+    if (reinterpret_cast<uintptr_t>(device_buf) % 8 || bytes < per_row) return CREDIT_ERR_INVALID_ARG;
+    g_trace_buf = static_cast<unsigned long long *>(device_buf);
+    g_trace_rows = static_cast<int>(bytes / per_row);
+    return CREDIT_OK;
 }
 
 credit_status credit_plan_check(const credit_args *args, const credit_plan_t *plan) {

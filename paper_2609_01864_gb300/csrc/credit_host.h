@@ -25,13 +25,14 @@ struct RingCfg {
     int P;
     int chunk;           // bytes per chunk
     int ring;            // chunk slots
-    int threads;         // consumer threads + one producer warp
+    int threads;         // reducer + writer threads + one producer warp
+    int reducers;        // reducer threads
     long long smem;      // dynamic shared memory per CTA
     long long body_max;  // largest slice body (bytes) of any CTA
     int nch_max;         // chunks of the largest slice
 };
 bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring, int req_chunk, int req_threads,
-                 RingCfg *out);
+                 int req_reducers, RingCfg *out);
 int ring_max_clusters(int device, int op, int tin, int tout, int P, int threads, long long smem);
 credit_status validate_args(const credit_args *a);
 credit_status check_plan(int device, const credit_args *a, const credit_plan_t *p);

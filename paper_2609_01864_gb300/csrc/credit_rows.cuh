@@ -57,6 +57,9 @@ struct RowArgs {
     int G;                                // CTAs per row of the two-pass path
     int chunk_bytes;                      // ring kernel: bytes per staged chunk
     int ring;                             // ring kernel: chunk slots
+    int reducers;                         // ring kernel: reducer threads (multiple of 32)
+    unsigned long long *trace;            // optional phase timestamps (see credit_set_trace)
+    int trace_rows;                       // rows recorded per traced CTA
     long long row0;                       // first row of this launch
 };
 
@@ -248,34 +251,47 @@ template <> struct Stream<OP_RMS> {
 // Ring kernel: the cluster path (P > 1) and the one-CTA path (P == 1).
 //
 // Persistent: grid = nclusters * P CTAs with cluster dims (P, 1, 1); cluster
-// k handles rows k, k + nclusters, ...  The last warp is the producer (its
-// lane 0 issues the bulk copies); the other W warps consume.  Shared memory
-// holds a control area and a ring of `ring` chunk slots of `chunk_bytes`.
-// The slices of successive rows form one chunk sequence j = 0, 1, ...;
-// chunk j lives in slot j % ring.  full[s] completes when a chunk has landed
-// (transaction bytes), empty[s] when every consumer warp has finished the
-// reuse pass over it, so the next rows' slices stream in while the current
-// row is being written.  A slice needs ceil(body / chunk_bytes) <= ring slots
+// k handles rows k, k + nclusters, ...  Three warp roles per CTA:
+//   producer (last warp; lane 0)  streams row slices into a ring of `ring`
+//            chunk slots of `chunk_bytes` with cp.async.bulk.  The slices of
+//            successive rows form one chunk sequence j = 0, 1, ...; chunk j
+//            lives in slot j % ring; full[s] completes when it has landed
+//            (transaction bytes), empty[s] when every writer warp is done
+//            with it.
+//   reducers (first `reducers` threads)  sweep each slice as its chunks land,
+//            reduce within the CTA (warp shuffles, then shared memory),
+//            exchange partials with the cluster (Eq. 5), combine them, and
+//            publish the row statistics in a double-buffered stats slot.
+//   writers  (the threads in between)  wait for a row's statistics, apply h
+//            to the retained slice (the reuse pass) and store the output
+//            segment, releasing each chunk to the producer.
+// So row r is written while row r+1 is being reduced and exchanged and
+// row r+2 is streaming in: the cluster exchange and the reductions leave the
+// output stream busy.  A slice needs ceil(body / chunk_bytes) <= ring slots
 // (Eq. 3).
 //
-// Exchange (Eq. 5): thread t < P of each CTA pushes the CTA's partials into
-// slot [c] of peer t with st.async, which completes on the peer's exchange
+// Exchange (Eq. 5): reducer thread t < P pushes the CTA's partials into slot
+// [c] of peer t with st.async, which completes on the peer's exchange
 // mbarrier; each CTA waits (bounded) on its own exchange mbarrier for the
-// P - 1 remote pushes, then combines its P local slots in fixed order.  The
-// slot arrays and exchange mbarriers are double-buffered by row parity, so a
-// peer can run one row ahead without overwriting partials still being read.
-// One cluster barrier at the start (every CTA's mbarriers are initialised
-// before any remote push) and one at the end (no CTA exits while a peer may
-// still push into it) are the only cluster-wide barriers.
+// P - 1 remote pushes, then combines its P local slots in fixed order
+// c = 0..P-1, so every CTA holds bit-identical statistics.  Slot arrays and
+// exchange mbarriers are double-buffered by row parity, so a peer can run one
+// row ahead without overwriting partials still being read.  One cluster
+// barrier at the start (every CTA's mbarriers are initialised before any
+// remote push) and one at the end (no CTA exits while a peer may still push
+// into it) are the only cluster-wide barriers.
 // ======================================================================
-constexpr int kRingCtrl = 2048;
+constexpr int kRingCtrl = 2304;
 constexpr int kMaxRing = 32;
 // Control area layout:
-//   [0, 256)      full[32] mbarriers
-//   [256, 512)    empty[32] mbarriers
-//   [512, 544)    exchange mbarriers [stage][parity]
-//   [544, 1024)   reduction scratch (120 floats)
-//   [1024, 2048)  DSMEM slots [stage][parity][16 sources][4 floats]
+//   [0, 256)       full[32] mbarriers
+//   [256, 512)     empty[32] mbarriers
+//   [512, 544)     exchange mbarriers [stage][parity]
+//   [544, 560)     stats_full[parity] mbarriers
+//   [560, 576)     stats_empty[parity] mbarriers
+//   [576, 640)     published row statistics [parity][8 floats]
+//   [640, 1152)    reduction scratch (128 floats)
+//   [1152, 2176)   DSMEM slots [stage][parity][16 sources][4 floats]
 
 __device__ __forceinline__ float *slot_ptr(float *slots, int stage, int par, int c) {
     return slots + ((stage * 2 + par) * 16 + c) * 4;
@@ -430,14 +446,28 @@ __device__ __forceinline__ void visit_chunk(const unsigned char *cb, int gn, int
     }
 }
 
+// Phase timestamps (global timer, ns) of the first kTraceCtas CTAs, for the
+// first trace_rows rows each: [0] row start, [1] stage-1 sweep done (all
+// chunks waited), [2] CTA reduction done, [3] exchange done, [4] reuse pass
+// done, [5] producer issued the row's last chunk.
+constexpr int kTraceCtas = 32;
+constexpr int kTraceFields = 8;
+__device__ __forceinline__ void trace_stamp(const RowArgs &a, int rr, int field) {
+    if (a.trace != nullptr && blockIdx.x < kTraceCtas && rr < a.trace_rows)
+        a.trace[(static_cast<size_t>(blockIdx.x) * a.trace_rows + rr) * kTraceFields + field] = global_timer_ns();
+}
+
 template <int OP, int TIN, int TOUT>
 __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + 32;
     uint64_t *xbar = full + 64;
-    float *red = reinterpret_cast<float *>(smem + 544);
-    float *slots = reinterpret_cast<float *>(smem + 1024);
+    uint64_t *stats_full = full + 68;
+    uint64_t *stats_empty = full + 70;
+    float *pub = reinterpret_cast<float *>(smem + 576);
+    float *red = reinterpret_cast<float *>(smem + 640);
+    float *slots = reinterpret_cast<float *>(smem + 1152);
     unsigned char *ring = smem + kRingCtrl;
 
     constexpr int isz = Fmt<TIN>::size, V = Fmt<TIN>::V;
@@ -449,30 +479,64 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
     const int P = static_cast<int>(cluster_nctarank());
     const int c = P > 1 ? static_cast<int>(cluster_ctarank()) : 0;
     const long long ncl = gridDim.x / P, cl = blockIdx.x / P;
-    const int tid = threadIdx.x, Tc = static_cast<int>(blockDim.x) - 32, W = Tc >> 5;
+    const int tid = threadIdx.x;
+    const int Tr = a.reducers, Tp = static_cast<int>(blockDim.x) - 32, Tw = Tp - Tr, Ww = Tw >> 5;
     const long long N = a.cols;
 
     if (tid == 0) {
         for (int k = 0; k < K; ++k) {
             mbar_init(&full[k], 1);
-            mbar_init(&empty[k], static_cast<uint32_t>(W));
+            mbar_init(&empty[k], static_cast<uint32_t>(Ww));
         }
         for (int k = 0; k < 4; ++k) mbar_init(&xbar[k], 1);
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&stats_full[k], 1);
+            mbar_init(&stats_empty[k], static_cast<uint32_t>(Ww));
+        }
         fence_mbar_init();
     }
     __syncthreads();
     if (P > 1) cluster_arrive_release();  // start barrier, split
     bool waited_start = false;
 
-    if (tid >= Tc) {
-        // ------------------------------------------------------ producer warp
-        if (tid == Tc) {
+    // Geometry of this CTA's slice of `row`.
+    struct RowGeo {
+        const unsigned char *in_row;
+        RowSlice s;
+        long long ng;
+        int nch;
+        float in_sc;
+    };
+    auto geo = [&](long long row) {
+        RowGeo g;
+        g.in_row = a.in + row * a.ld_in * isz;
+        g.s = make_slice(reinterpret_cast<uintptr_t>(g.in_row), N, isz, P, c);
+        g.ng = g.s.g_hi - g.s.g_lo;
+        g.nch = static_cast<int>((g.ng * 16 + CH - 1) / CH);
+        g.in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
+        return g;
+    };
+    auto chunk_ptr = [&](long long j, int k) -> const unsigned char * {
+        return ring + static_cast<size_t>((j + k) % K) * CH;
+    };
+    auto chunk_groups = [&](const RowGeo &g, int k) -> int {
+        const long long r = g.ng - static_cast<long long>(k) * gpc;
+        return static_cast<int>(r < gpc ? r : gpc);
+    };
+    auto edge_x = [&](const RowGeo &g, int e, long long k) -> float {
+        const long long i = e == 0 ? k : g.s.h0 + g.s.G * V + k;
+        return decode_one<TIN>(g.in_row + i * isz, g.in_sc);
+    };
+
+    if (tid >= Tp) {
+        // ========================================================== producer
+        if (tid == Tp) {
             long long j = 0;
+            int prr = 0;
             for (long long row = cl; row < a.rows; row += ncl) {
-                const unsigned char *in_row = a.in + row * a.ld_in * isz;
-                const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), N, isz, P, c);
-                const long long body = (s.g_hi - s.g_lo) * 16;
-                const unsigned char *src = in_row + s.h0 * isz + s.g_lo * 16;
+                const RowGeo g = geo(row);
+                const long long body = g.ng * 16;
+                const unsigned char *src = g.in_row + g.s.h0 * isz + g.s.g_lo * 16;
                 for (long long off = 0; off < body; off += CH, ++j) {
                     const int slot = static_cast<int>(j % K);
                     if (j >= K) mbar_wait_bounded(&empty[slot], static_cast<uint32_t>(((j / K) - 1) & 1), a.err);
@@ -480,57 +544,75 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                     mbar_arrive_expect_tx(&full[slot], bytes);
                     bulk_g2s(ring + static_cast<size_t>(slot) * CH, src + off, bytes, &full[slot]);
                 }
+                trace_stamp(a, prr++, 5);
             }
         }
         __syncwarp();
-    } else {
-        // ------------------------------------------------------ consumer warps
+    } else if (tid < Tr) {
+        // ========================================================== reducers
         long long j = 0;
         int rr = 0;
         for (long long row = cl; row < a.rows; row += ncl, ++rr) {
-            const unsigned char *in_row = a.in + row * a.ld_in * isz;
-            const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), N, isz, P, c);
-            const long long ng = s.g_hi - s.g_lo;
-            const int nch = static_cast<int>((ng * 16 + CH - 1) / CH);
-            const float in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
-            const long long n_head = (c == 0 && tid == 0) ? s.h0 : 0;
-            const long long n_tail = (c == P - 1 && tid == Tc - 1) ? s.t0 : 0;
-            const long long tail_i0 = s.h0 + s.G * V;
+            const RowGeo g = geo(row);
+            const long long n_head = (c == 0 && tid == 0) ? g.s.h0 : 0;
+            const long long n_tail = (c == P - 1 && tid == Tr - 1) ? g.s.t0 : 0;
             const int par = rr & 1;
             const uint32_t xphase = static_cast<uint32_t>((rr >> 1) & 1);
-            auto chunk = [&](int k) -> const unsigned char * {
-                return ring + static_cast<size_t>((j + k) % K) * CH;
-            };
-            auto chunk_groups = [&](int k) -> int {
-                const long long r = ng - static_cast<long long>(k) * gpc;
-                return static_cast<int>(r < gpc ? r : gpc);
-            };
-            auto edge_x = [&](int e, long long k) -> float {
-                const long long i = e == 0 ? k : tail_i0 + k;
-                return decode_one<TIN>(in_row + i * isz, in_sc);
-            };
+            if (tid == 0) trace_stamp(a, rr, 0);
 
-            // ---------- stage 1: one local sweep (waits for each chunk as it lands)
-            Stream<OP> acc;
-            for (int k = 0; k < nch; ++k) {
-                const long long jk = j + k;
-                mbar_wait_bounded(&full[jk % K], static_cast<uint32_t>((jk / K) & 1), a.err);
-                visit_chunk<TIN>(chunk(k), chunk_groups(k), tid, Tc, in_sc,
-                                 [&](int, const float(&f)[V]) { acc.add(f); });
-            }
-            for (int e = 0; e < 2; ++e) {
-                const long long cnt = e == 0 ? n_head : n_tail;
-                for (long long k = 0; k < cnt; ++k) acc.add1(edge_x(e, k));
-            }
-            const float2 part = block_reduce_stream<OP>(acc, red, slice_count(s, V, P, c), 1, Tc);
-            const float part0 = part.x, part1 = part.y;
-            if constexpr (OP == OP_LSE) {
-                // no reuse pass: release the slice now
-                for (int k = 0; k < nch; ++k) {
-                    __syncwarp();
-                    if ((tid & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
+            // ---------- stage 1 (sweeps wait for each chunk as it lands)
+            float part0, part1 = 0.0f;
+            const long long n_c = slice_count(g.s, V, P, c);
+            if constexpr (OP == OP_LN) {
+                // exact two sweeps: the slice mean, then squared deviations
+                float sum = 0.0f;
+                for (int k = 0; k < g.nch; ++k) {
+                    const long long jk = j + k;
+                    mbar_wait_bounded(&full[jk % K], static_cast<uint32_t>((jk / K) & 1), a.err);
+                    visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), tid, Tr, g.in_sc,
+                                     [&](int, const float(&f)[V]) {
+#pragma unroll
+                                         for (int q = 0; q < V; ++q) sum += f[q];
+                                     });
                 }
+                for (int e = 0; e < 2; ++e)
+                    for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) sum += edge_x(g, e, k);
+                if (tid == 0) trace_stamp(a, rr, 1);
+                sum = cons_allreduce<false>(sum, red, Tr);
+                const float mean = n_c > 0 ? sum / static_cast<float>(n_c) : 0.0f;
+                float m2 = 0.0f;
+                for (int k = 0; k < g.nch; ++k)
+                    visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), tid, Tr, g.in_sc,
+                                     [&](int, const float(&f)[V]) {
+#pragma unroll
+                                         for (int q = 0; q < V; ++q) {
+                                             const float d = f[q] - mean;
+                                             m2 = fmaf(d, d, m2);
+                                         }
+                                     });
+                for (int e = 0; e < 2; ++e)
+                    for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) {
+                        const float d = edge_x(g, e, k) - mean;
+                        m2 = fmaf(d, d, m2);
+                    }
+                part0 = mean;
+                part1 = cons_allreduce<false>(m2, red, Tr);
+            } else {
+                Stream<OP> acc;
+                for (int k = 0; k < g.nch; ++k) {
+                    const long long jk = j + k;
+                    mbar_wait_bounded(&full[jk % K], static_cast<uint32_t>((jk / K) & 1), a.err);
+                    visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), tid, Tr, g.in_sc,
+                                     [&](int, const float(&f)[V]) { acc.add(f); });
+                }
+                for (int e = 0; e < 2; ++e)
+                    for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) acc.add1(edge_x(g, e, k));
+                if (tid == 0) trace_stamp(a, rr, 1);
+                const float2 part = block_reduce_stream<OP>(acc, red, n_c, 1, Tr);
+                part0 = part.x;
+                part1 = part.y;
             }
+            if (tid == 0) trace_stamp(a, rr, 2);
 
             // ---------- DSMEM push all-gather (Eq. 5) and fixed-order combine
             Stats st;
@@ -540,100 +622,137 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                     waited_start = true;
                 }
                 const float *sl = exchange_push<(OP == OP_RMS) ? 1 : 2>(part0, part1, slots, xbar, 0, par, xphase, P,
-                                                                         c, Tc, a.err);
-                st = combine_partials<OP>(sl, 4, P, s, V, N, a.eps);
+                                                                         c, Tr, a.err);
+                st = combine_partials<OP>(sl, 4, P, g.s, V, N, a.eps);
             } else {
                 const float p1[2] = {part0, part1};
-                st = combine_partials<OP>(p1, 2, 1, s, V, N, a.eps);
+                st = combine_partials<OP>(p1, 2, 1, g.s, V, N, a.eps);
             }
+            if (tid == 0) trace_stamp(a, rr, 3);
 
+            // ---------- stage 2 (FP8 output of the norms): amax |h(x)|
+            float qmul = 1.0f;
+            if constexpr (kFp8Stage) {
+                const long long i_base = g.s.h0 + g.s.g_lo * V;
+                const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + g.s.h0) & 15u) == 0);
+                const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + g.s.h0) & 15u) == 0);
+                float am = 0.0f;
+                for (int k = 0; k < g.nch; ++k) {
+                    const long long kg = static_cast<long long>(k) * gpc;
+                    visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), tid, Tr, g.in_sc,
+                                     [&](int gi, const float(&f)[V]) {
+#pragma unroll
+                                         for (int hv = 0; hv < V; hv += SV) {
+                                             float gg[SV], bb[SV];
+                                             const long long i0 = i_base + (kg + gi) * V + hv;
+                                             load_affine<SV>(a.gamma, i0, g_vec, 1.0f, gg);
+                                             load_affine<SV>(a.beta, i0, b_vec, 0.0f, bb);
+#pragma unroll
+                                             for (int q = 0; q < SV; ++q)
+                                                 am = fmaxf(am, fabsf(norm_h<OP>(f[hv + q], st, gg[q],
+                                                                                 OP == OP_LN ? bb[q] : 0.0f)));
+                                         }
+                                     });
+                }
+                for (int e = 0; e < 2; ++e)
+                    for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) {
+                        const long long i = e == 0 ? k : g.s.h0 + g.s.G * V + k;
+                        const float gg = a.gamma ? a.gamma[i] : 1.0f;
+                        const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
+                        am = fmaxf(am, fabsf(norm_h<OP>(edge_x(g, e, k), st, gg, bb)));
+                    }
+                am = cons_allreduce<true>(am, red, Tr);
+                if (P > 1) {
+                    const float *sl = exchange_push<1>(am, 0.0f, slots, xbar, 1, par, xphase, P, c, Tr, a.err);
+                    am = 0.0f;
+                    for (int q = 0; q < P; ++q) am = fmaxf(am, sl[q * 4]);
+                }
+                qmul = am > 0.0f ? 448.0f / am : 1.0f;
+                if (c == 0 && tid == 0) a.out_scale[row] = am > 0.0f ? am / 448.0f : 1.0f;
+            }
+            if constexpr (OP == OP_SOFTMAX && TOUT == DT_E4M3) {
+                if (c == 0 && tid == 0) a.out_scale[row] = (1.0f / st.b) * (1.0f / 448.0f);
+            }
             if constexpr (OP == OP_LSE) {
                 if (c == 0 && tid == 0) reinterpret_cast<float *>(a.out)[row] = st.a + logf(st.b);
+            }
+
+            // ---------- publish the row statistics to the writers
+            if (tid == 0) {
+                if (rr >= 2) mbar_wait_bounded(&stats_empty[par], static_cast<uint32_t>(((rr >> 1) - 1) & 1), a.err);
+                pub[par * 8 + 0] = st.a;
+                pub[par * 8 + 1] = st.b;
+                pub[par * 8 + 2] = qmul;
+                mbar_arrive(&stats_full[par]);
+            }
+            j += g.nch;
+        }
+    } else {
+        // ========================================================== writers
+        const int wt = tid - Tr;
+        long long j = 0;
+        int rr = 0;
+        for (long long row = cl; row < a.rows; row += ncl, ++rr) {
+            const RowGeo g = geo(row);
+            const int par = rr & 1;
+            mbar_wait_bounded(&stats_full[par], static_cast<uint32_t>((rr >> 1) & 1), a.err);
+            Stats st;
+            st.a = pub[par * 8 + 0];
+            st.b = pub[par * 8 + 1];
+            const float qmul = pub[par * 8 + 2];
+            __syncwarp();
+            if ((wt & 31) == 0) mbar_arrive(&stats_empty[par]);
+
+            if constexpr (OP == OP_LSE) {
+                for (int k = 0; k < g.nch; ++k) {
+                    __syncwarp();
+                    if ((wt & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
+                }
             } else {
                 unsigned char *out_row = a.out + row * a.ld_out * osz;
-                const long long i_base = s.h0 + s.g_lo * V;
+                const long long i_base = g.s.h0 + g.s.g_lo * V;
                 constexpr int vec_bytes = (SV * osz) < 16 ? (SV * osz) : 16;
-                const bool out_vec = ((reinterpret_cast<uintptr_t>(out_row) + s.h0 * osz) % vec_bytes) == 0;
-                const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + s.h0) & 15u) == 0);
-                const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + s.h0) & 15u) == 0);
-
-                // ------ stage 2 (FP8 output of the norms): amax |h(x)|
-                float qmul = 1.0f;
-                if constexpr (kFp8Stage) {
-                    float am = 0.0f;
-                    for (int k = 0; k < nch; ++k) {
-                        const long long kg = static_cast<long long>(k) * gpc;
-                        visit_chunk<TIN>(chunk(k), chunk_groups(k), tid, Tc, in_sc, [&](int g, const float(&f)[V]) {
-#pragma unroll
-                            for (int hv = 0; hv < V; hv += SV) {
-                                float gg[SV], bb[SV];
-                                const long long i0 = i_base + (kg + g) * V + hv;
-                                load_affine<SV>(a.gamma, i0, g_vec, 1.0f, gg);
-                                load_affine<SV>(a.beta, i0, b_vec, 0.0f, bb);
-#pragma unroll
-                                for (int q = 0; q < SV; ++q)
-                                    am = fmaxf(am, fabsf(norm_h<OP>(f[hv + q], st, gg[q], OP == OP_LN ? bb[q] : 0.0f)));
-                            }
-                        });
-                    }
-                    for (int e = 0; e < 2; ++e) {
-                        const long long cnt = e == 0 ? n_head : n_tail;
-                        for (long long k = 0; k < cnt; ++k) {
-                            const long long i = e == 0 ? k : tail_i0 + k;
-                            const float gg = a.gamma ? a.gamma[i] : 1.0f;
-                            const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
-                            am = fmaxf(am, fabsf(norm_h<OP>(edge_x(e, k), st, gg, bb)));
-                        }
-                    }
-                    am = cons_allreduce<true>(am, red, Tc);
-                    if (P > 1) {
-                        const float *sl = exchange_push<1>(am, 0.0f, slots, xbar, 1, par, xphase, P, c, Tc, a.err);
-                        am = 0.0f;
-                        for (int q = 0; q < P; ++q) am = fmaxf(am, sl[q * 4]);
-                    }
-                    qmul = am > 0.0f ? 448.0f / am : 1.0f;
-                    if (c == 0 && tid == 0) a.out_scale[row] = am > 0.0f ? am / 448.0f : 1.0f;
-                }
+                const bool out_vec = ((reinterpret_cast<uintptr_t>(out_row) + g.s.h0 * osz) % vec_bytes) == 0;
+                const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + g.s.h0) & 15u) == 0);
+                const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + g.s.h0) & 15u) == 0);
                 const float inv = (OP == OP_SOFTMAX) ? 1.0f / st.b : 0.0f;
-                const float smul = (TOUT == DT_E4M3) ? 448.0f : inv;  // softmax: y (or its FP8 code) = exp(x - M) * smul
-                if constexpr (OP == OP_SOFTMAX && TOUT == DT_E4M3) {
-                    if (c == 0 && tid == 0) a.out_scale[row] = inv * (1.0f / 448.0f);
-                }
-                auto h = [&](float x, float g, float b) -> float {
+                const float smul = (TOUT == DT_E4M3) ? 448.0f : inv;  // softmax: y (or its code) = exp(x - M) * smul
+                auto h = [&](float x, float gm, float bt) -> float {
                     if constexpr (OP == OP_SOFTMAX) return exp_fast(x - st.a) * smul;
-                    else return norm_h<OP>(x, st, g, b) * qmul;
+                    else return norm_h<OP>(x, st, gm, bt) * qmul;
                 };
-
-                // ------ reuse pass: h over the retained slice, chunk by chunk
-                for (int k = 0; k < nch; ++k) {
+                for (int k = 0; k < g.nch; ++k) {
                     const long long kg = static_cast<long long>(k) * gpc;
-                    visit_chunk<TIN>(chunk(k), chunk_groups(k), tid, Tc, in_sc, [&](int g, const float(&f)[V]) {
+                    visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), wt, Tw, g.in_sc,
+                                     [&](int gi, const float(&f)[V]) {
 #pragma unroll
-                        for (int hv = 0; hv < V; hv += SV) {
-                            float gg[SV], bb[SV], y[SV];
-                            const long long i0 = i_base + (kg + g) * V + hv;
-                            if constexpr (OP != OP_SOFTMAX) load_affine<SV>(a.gamma, i0, g_vec, 1.0f, gg);
-                            if constexpr (OP == OP_LN) load_affine<SV>(a.beta, i0, b_vec, 0.0f, bb);
+                                         for (int hv = 0; hv < V; hv += SV) {
+                                             float gg[SV], bb[SV], y[SV];
+                                             const long long i0 = i_base + (kg + gi) * V + hv;
+                                             if constexpr (OP != OP_SOFTMAX) load_affine<SV>(a.gamma, i0, g_vec, 1.0f, gg);
+                                             if constexpr (OP == OP_LN) load_affine<SV>(a.beta, i0, b_vec, 0.0f, bb);
 #pragma unroll
-                            for (int q = 0; q < SV; ++q)
-                                y[q] = h(f[hv + q], OP != OP_SOFTMAX ? gg[q] : 1.0f, OP == OP_LN ? bb[q] : 0.0f);
-                            store_group<TOUT, SV>(out_row + i0 * osz, y, out_vec);
-                        }
-                    });
+                                             for (int q = 0; q < SV; ++q)
+                                                 y[q] = h(f[hv + q], OP != OP_SOFTMAX ? gg[q] : 1.0f,
+                                                          OP == OP_LN ? bb[q] : 0.0f);
+                                             store_group<TOUT, SV>(out_row + i0 * osz, y, out_vec);
+                                         }
+                                     });
                     __syncwarp();
-                    if ((tid & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
+                    if ((wt & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
                 }
-                for (int e = 0; e < 2; ++e) {
-                    const long long cnt = e == 0 ? n_head : n_tail;
-                    for (long long k = 0; k < cnt; ++k) {
-                        const long long i = e == 0 ? k : tail_i0 + k;
-                        const float gg = (OP != OP_SOFTMAX && a.gamma) ? a.gamma[i] : 1.0f;
-                        const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
-                        store_one<TOUT>(out_row + i * osz, h(edge_x(e, k), gg, bb));
+                const long long n_head = (c == 0 && wt == 0) ? g.s.h0 : 0;
+                const long long n_tail = (c == P - 1 && wt == Tw - 1) ? g.s.t0 : 0;
+                for (int e = 0; e < 2; ++e)
+                    for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) {
+                        const long long i = e == 0 ? k : g.s.h0 + g.s.G * V + k;
+                        const float gm = (OP != OP_SOFTMAX && a.gamma) ? a.gamma[i] : 1.0f;
+                        const float bt = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
+                        store_one<TOUT>(out_row + i * osz, h(edge_x(g, e, k), gm, bt));
                     }
-                }
             }
-            j += nch;
+            if (wt == 0) trace_stamp(a, rr, 4);
+            j += g.nch;
         }
     }
     if (P > 1) {
