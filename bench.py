@@ -1,0 +1,485 @@
+"""Benchmark of the reduction-reuse row ops on GB300 (one JSON line on stdout).
+
+Workload (a "step"): LayerNorm (gamma ~ N(1, 0.1), beta ~ N(0, 0.1)) and
+RMSNorm (gamma) in FP32 over 4096 rows x cols in {16K, 64K, 128K, 256K, 512K},
+inputs N(0, 1) with 1% outliers at +-50, each shape run once through the
+public C ABI with the plan the cost model picks.  Every input tensor (>= 268
+MB) is larger than the 129 MB L2, so no flush is needed between steps.
+
+value      algorithmic HBM GB/s of the whole step (one read of every input
+           element, one write of every output element; gamma/beta excluded)
+           with inputs resident in HBM, timed with CUDA events, max over ranks
+e2e        the same metric end to end: pinned host inputs copied in, the ops
+           run, the outputs copied back, all inside the timed region
+roofline   the dominant kernel's achieved GB/s (its algorithmic bytes per
+           launch / its mean launch time, CUDA events on the launching stream)
+           against the measured HBM copy rate
+cpu_baseline  the FP64 oracle on a bounded sample of the same shapes, all
+           host cores
+
+Also reported: speedup of the chosen plans over the best non-DSMEM plan
+(one-CTA staging or two-pass reread) on the same shapes, and the cost model's
+pick accuracy on these shapes (pick within 5% of the measured best candidate).
+
+--impl reference  times the FP64 CPU oracle (the reference arm of this
+           project) on a bounded sample of the same workload.
+--case op:rows:cols:path:P  runs one small case a few times (for profilers).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WIDTHS = [16384, 65536, 131072, 262144, 524288]
+ROWS = 4096
+OPS = ("layernorm", "rmsnorm")
+METRIC = "HBM GB/s (% of roofline) & speedup vs best non-DSMEM path; cost-model pick accuracy"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.lines.append(line.strip())
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def algorithmic_bytes(rows, cols, op):
+    return rows * cols * 8  # FP32 in + FP32 out
+
+
+def kernel_name(plan, C):
+    if plan.path in (C.PATH_ONE_CTA, C.PATH_CLUSTER):
+        return "k_ring"
+    return "k_tp_fused" if plan.ctas_per_row == 1 else "k_tp_split"
+
+
+def traffic_record(kernel: str, op: str, cols: int):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
+    the kernel source as it is now (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            recs = json.load(f)
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2609_01864_gb300", "csrc", "credit_rows.cuh")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for r in recs.get("records", []):
+        if r.get("kernel") == kernel and r.get("op") == op and r.get("cols") == cols and r.get("source_sha") == h:
+            return r
+    return None
+
+
+def time_events(fn, reps, warm=1):
+    import torch
+    for _ in range(warm):
+        fn()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in evs:
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def candidates(C, op, x, y, g, b):
+    out = []
+    for P in (1, 2, 4, 8, 16):
+        p = C.make_plan(C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P)
+        if C.plan_check(op, x, y, p, gamma=g, beta=b) == C.OK:
+            out.append((f"{'one_cta' if P == 1 else 'cluster'}{'' if P == 1 else P}", p))
+    for G in (1, 4):
+        p = C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)
+        out.append((f"two_pass_g{G}", p))
+    return out
+
+
+# ---------------------------------------------------------------- reference arm
+def cpu_oracle_sample(seconds: float = 10.0, threads: int = 0):
+    """Time the FP64 oracle on a bounded sample of the workload (rows of each
+    shape, both ops), repeating until `seconds` have elapsed."""
+    import numpy as np
+    import oracle as O
+    from paper_2609_01864_gb300 import synth
+    O.build()
+    rows_per = 8
+    data = []
+    for cols in WIDTHS:
+        x = synth.outliers(rows_per, cols, seed=synth.SEED_DATA).numpy()
+        g, bt = synth.gamma_beta(cols)
+        data.append((cols, x, g.numpy(), bt.numpy()))
+    nbytes = 0
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        for cols, x, g, bt in data:
+            for op in (O.LAYERNORM, O.RMSNORM):
+                O.run(op, O.F32, x, rows_per, cols, gamma=g, beta=bt if op == O.LAYERNORM else None,
+                      want_exact=False, want_encoded=True, nthreads=threads)
+                nbytes += rows_per * cols * 8
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    cores = threads if threads > 0 else O.max_threads()
+    return {"value": round(nbytes / el / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"{rows_per} rows x each of cols {WIDTHS}, LayerNorm+RMSNorm, FP32 in/out, "
+                      f"{reps} repetitions in {el:.1f} s ({nbytes / 1e9:.2f} GB algorithmic)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step = min(per_step, 10.0)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(seconds=min(2.0, per_step))
+    vals = []
+    last = None
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        last = cpu_oracle_sample(seconds=per_step)
+        vals.append(last["value"])
+    el = time.perf_counter() - t0
+    v = statistics.median(vals)
+    line = {"metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(el * 1e3 / max(1, args.steps), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "LayerNorm+RMSNorm FP32, 4096 x {16K,64K,128K,256K,512K} (bounded CPU sample)"},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_case(spec: str):
+    import torch
+    from paper_2609_01864_gb300 import build as B
+    from paper_2609_01864_gb300 import credit as C
+    from paper_2609_01864_gb300 import synth
+    B.build()
+    op, rows, cols, path, P = [int(v) for v in spec.split(":")]
+    C.init(torch.cuda.current_device())
+    x = synth.outliers(rows, cols, seed=synth.SEED_DATA, device="cuda")
+    y = torch.empty_like(x)
+    g, b = synth.gamma_beta(cols, device="cuda")
+    plan = None if path < 0 else C.make_plan(path, P, ctas_per_row=P if path == C.PATH_TWO_PASS else 1)
+    kw = dict(gamma=g if op in (C.LAYERNORM, C.RMSNORM) else None, beta=b if op == C.LAYERNORM else None)
+    for _ in range(3):
+        C.run_ex(op, x, y, plan=plan, **kw)
+    torch.cuda.synchronize()
+    assert C.device_error() == C.OK
+    print(json.dumps({"case": spec, "launches": C.launch_count()}))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2609_01864_gb300 import build as B
+    from paper_2609_01864_gb300 import credit as C
+    from paper_2609_01864_gb300 import synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    C.init(local)
+    dev = torch.device("cuda", local)
+    widths = WIDTHS if not args.widths else [int(w) for w in args.widths.split(",")]
+
+    # ---- inputs (seeded, resident in HBM)
+    shapes = []
+    for cols in widths:
+        x = synth.outliers(ROWS, cols, seed=synth.SEED_DATA + rank, device=dev)
+        g, b = synth.gamma_beta(cols, device=dev)
+        shapes.append({"cols": cols, "x": x, "y": torch.empty_like(x), "g": g, "b": b})
+    jobs = []
+    for sh in shapes:
+        for name in OPS:
+            op = C.LAYERNORM if name == "layernorm" else C.RMSNORM
+            plan = C.plan(op, ROWS, sh["cols"], C.F32)
+            kw = dict(gamma=sh["g"], beta=sh["b"] if op == C.LAYERNORM else None)
+            jobs.append({"op": op, "name": name, "cols": sh["cols"], "x": sh["x"], "y": sh["y"], "kw": kw,
+                         "plan": plan, "kernel": kernel_name(plan, C),
+                         "bytes": algorithmic_bytes(ROWS, sh["cols"], op)})
+    step_bytes = sum(j["bytes"] for j in jobs)
+    stream = torch.cuda.current_stream()
+
+    def step(record=None):
+        for k, j in enumerate(jobs):
+            if record is not None:
+                record[k][0].record(stream)
+            C.run_ex(j["op"], j["x"], j["y"], plan=j["plan"], **j["kw"])
+            if record is not None:
+                record[k][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    per = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in jobs]
+           for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    n0 = C.launch_count()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(per[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = C.launch_count() - n0
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = step_bytes * world / (ms_step * 1e-3) / 1e9
+    assert C.device_error() == C.OK
+
+    # ---- per-kernel launch times (roofline of the dominant kernel)
+    per_kernel = {}
+    for s in range(args.steps):
+        for k, j in enumerate(jobs):
+            ms = per[s][k][0].elapsed_time(per[s][k][1])
+            d = per_kernel.setdefault(j["kernel"], {"ms": 0.0, "launches": 0, "bytes": 0, "jobs": {}})
+            d["ms"] += ms
+            d["launches"] += 1
+            d["bytes"] += j["bytes"]
+            jd = d["jobs"].setdefault((j["name"], j["cols"]), {"ms": [], "bytes": j["bytes"]})
+            jd["ms"].append(ms)
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    dk = per_kernel[dom]
+    peak, peak_kind = measured_peak()
+    achieved = dk["bytes"] / (dk["ms"] * 1e-3) / 1e9
+    # traffic of the dominant kernel's largest job (per launch), if a current capture exists
+    big = max(dk["jobs"], key=lambda k: dk["jobs"][k]["bytes"])
+    tr = traffic_record(dom, big[0], big[1])
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None if tr is None else tr["dram_bytes"],
+                "peak_source": f"{peak_kind} hbm_gbs (copy)", "kernel": dom,
+                "kernel_share": round(dk["ms"] / sum(v["ms"] for v in per_kernel.values()), 3),
+                "traffic_job": None if tr is None else f"{big[0]} cols={big[1]}",
+                "traffic_algorithmic_bytes": None if tr is None else tr.get("algorithmic_bytes")}
+    per_job = []
+    for k, j in enumerate(jobs):
+        ms = statistics.median(per[s][k][0].elapsed_time(per[s][k][1]) for s in range(args.steps))
+        per_job.append({"op": j["name"], "cols": j["cols"], "plan": C.PATH_NAMES[j["plan"].path],
+                        "P": j["plan"].cluster_size, "G": j["plan"].ctas_per_row, "source": j["plan"].source,
+                        "ms": round(ms, 4), "GBps": round(j["bytes"] / ms / 1e6, 1)})
+
+    # ---- speedup vs best non-DSMEM path and pick accuracy (every candidate timed)
+    speed_num = speed_den = 0.0
+    hits = 0
+    pick_rows = []
+    if not args.no_picks:
+        for k, j in enumerate(jobs):
+            times = {}
+            for name, p in candidates(C, j["op"], j["x"], j["y"], j["kw"]["gamma"], j["kw"]["beta"]):
+                ts = time_events(lambda: C.run_ex(j["op"], j["x"], j["y"], plan=p, **j["kw"]), 5)
+                times[name] = statistics.median(ts)
+            best_non = min(v for n, v in times.items() if not n.startswith("cluster"))
+            best_all = min(times.values())
+            chosen = per_job[k]["ms"]
+            speed_num += best_non
+            speed_den += chosen
+            hit = chosen <= 1.05 * best_all
+            hits += int(hit)
+            pick_rows.append({"op": j["name"], "cols": j["cols"], "chosen_ms": chosen,
+                              "best": min(times, key=times.get), "best_ms": round(best_all, 4),
+                              "best_non_dsmem_ms": round(best_non, 4), "hit": hit,
+                              "candidates": {n: round(v, 4) for n, v in times.items()}})
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(C, torch, dev, jobs, shapes, stream, args)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_oracle_sample(seconds=args.cpu_seconds)
+
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "LayerNorm(gamma,beta)+RMSNorm(gamma) FP32, 4096 rows x cols "
+                               "{16K,64K,128K,256K,512K}, N(0,1) with 1% +-50 outliers, planner-chosen path",
+                   "rows": ROWS, "cols": widths, "ops": list(OPS),
+                   "l2": "every input > L2 (>= 268 MB), no flush", "parallelism": f"rows per GPU x {world}"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "speedup_vs_best_non_dsmem": round(speed_num / speed_den, 4) if speed_den else None,
+        "pick_accuracy": round(hits / len(jobs), 4) if pick_rows else None,
+        "pick_rule": "chosen plan within 5% of the fastest measured candidate (median of 5)",
+        "per_job": per_job,
+        "picks": pick_rows,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_e2e(C, torch, dev, jobs, shapes, stream, args):
+    host_x = {}
+    for sh in shapes:
+        hx = torch.empty(sh["x"].shape, dtype=sh["x"].dtype, pin_memory=True)
+        hx.copy_(sh["x"])
+        host_x[sh["cols"]] = hx
+    big = max(sh["x"].numel() for sh in shapes)
+    host_y = torch.empty(big, dtype=torch.float32, pin_memory=True)
+    dev_x = {sh["cols"]: sh["x"] for sh in shapes}
+    h2d = sum(host_x[c].numel() * 4 for c in host_x)
+    d2h = sum(j["y"].numel() * 4 for j in jobs)
+
+    def step():
+        for sh in shapes:
+            dev_x[sh["cols"]].copy_(host_x[sh["cols"]], non_blocking=True)
+        for j in jobs:
+            C.run_ex(j["op"], j["x"], j["y"], plan=j["plan"], **j["kw"])
+            host_y[: j["y"].numel()].view(j["y"].shape).copy_(j["y"], non_blocking=True)
+
+    steps = max(1, min(args.steps, args.e2e_steps))
+    step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    step_bytes = sum(j["bytes"] for j in jobs)
+    return {"value": round(step_bytes / (ms * 1e-3) / 1e9, 1), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3), "steps": steps}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--widths", default="")
+    ap.add_argument("--no-picks", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--case", default="")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not args.case:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.case:
+        return run_case(args.case)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
