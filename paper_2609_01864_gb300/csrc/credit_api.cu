@@ -94,24 +94,34 @@ int dtype_size(int dt) { return dt == DT_F32 ? 4 : (dt == DT_BF16 ? 2 : 1); }
 // groups, G = floor(N * isz / 16).  Eq. 3: the slice must fit the ring, i.e.
 // kRingCtrl + ceil(body / chunk) * chunk <= the opt-in shared memory.
 bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring, int req_chunk, int req_threads,
-                 int req_reducers, RingCfg *out) {
+                 int req_reducers, int nab, RingCfg *out) {
     if (P < 1 || P > kMaxCluster || N <= 0) return false;
     const long long groups = (N * isz) / 16;
     const long long per = (groups + P - 1) / P;
     RingCfg r{};
     r.P = P;
     r.body_max = per * 16;
+    // gamma / beta bytes staged per data byte
+    const int abytes_per16 = nab * (16 / isz) * 4;
+    long long max_chunk = kMaxChunkBytes;
+    if (nab > 0) {
+        const long long cap = (32768LL * 16 / abytes_per16) / 16 * 16;  // affine slot <= 32 KiB
+        if (cap < max_chunk) max_chunk = cap;
+    }
     if (req_chunk > 0) {
         if (req_chunk % 16) return false;
         r.chunk = req_chunk;
     } else if (r.body_max == 0) {
         r.chunk = 16;
     } else {
-        const long long n = (r.body_max + kMaxChunkBytes - 1) / kMaxChunkBytes;
+        const long long n = (r.body_max + max_chunk - 1) / max_chunk;
         r.chunk = static_cast<int>(((r.body_max + n - 1) / n + 15) / 16 * 16);
     }
     r.nch_max = static_cast<int>((r.body_max + r.chunk - 1) / r.chunk);
-    const long long fit = (di.smem_optin - kRingCtrl) / r.chunk;
+    r.affine = nab > 0 ? 2 : 0;
+    r.aslot = static_cast<long long>(r.chunk / 16) * abytes_per16;
+    const long long budget = di.smem_optin - kRingCtrl - r.affine * r.aslot;
+    const long long fit = budget > 0 ? budget / r.chunk : 0;
     if (req_ring > 0) {
         r.ring = req_ring;
     } else {
@@ -122,7 +132,7 @@ bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring
         r.ring = static_cast<int>(k);
     }
     if (r.ring < r.nch_max || r.ring < 1 || r.ring > kMaxRing) return false;
-    r.smem = kRingCtrl + static_cast<long long>(r.ring) * r.chunk;
+    r.smem = kRingCtrl + static_cast<long long>(r.ring) * r.chunk + r.affine * r.aslot;
     if (r.smem > di.smem_optin) return false;  // Eq. 3
     if (req_threads > 0) {
         if (req_threads % 32 || req_threads < 96 || req_threads > 288) return false;
@@ -144,6 +154,27 @@ bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring
     if (tp - r.reducers < 32) return false;
     *out = r;
     return true;
+}
+
+// Number of gamma / beta arrays the ring kernel can stream through its affine
+// ring for these arguments (0 = the reuse pass loads them directly): norms
+// only, every row starting at the same 16-byte phase, and the gamma / beta
+// segments of the slices 16-byte aligned.
+int affine_arrays(const credit_args *a) {
+    if (a->op != OP_LN && a->op != OP_RMS) return 0;
+    if (std::getenv("CREDIT_NO_AFFINE")) return 0;
+    const int isz = dtype_size(a->in_dtype);
+    const long long ld = a->ld_in ? a->ld_in : a->cols;
+    if ((ld * isz) % 16) return 0;
+    const uintptr_t ip = reinterpret_cast<uintptr_t>(a->in);
+    const long long mis = static_cast<long long>(ip & 15u);
+    long long h0 = mis ? (16 - mis) / isz : 0;
+    if (h0 > a->cols) h0 = a->cols;
+    const float *gm = a->gamma;
+    const float *bt = a->op == OP_LN ? a->beta : nullptr;
+    if (gm && (reinterpret_cast<uintptr_t>(gm + h0) & 15u)) return 0;
+    if (bt && (reinterpret_cast<uintptr_t>(bt + h0) & 15u)) return 0;
+    return (gm ? 1 : 0) + (bt ? 1 : 0);
 }
 
 const DeviceInfo *device_info(int device) {
@@ -281,6 +312,17 @@ credit_status credit_device_error(cudaStream_t stream) {
 // ------------------------------------------------------------------ launching
 namespace credit {
 
+// Ring geometry for a call: with the gamma / beta affine ring when it fits,
+// else with direct gamma / beta loads (same legality as without them).
+static bool ring_config_for(const DeviceInfo &di, const credit_args *a, int isz, int P, const credit_plan_t *p,
+                            RingCfg *rc) {
+    const int nab = affine_arrays(a);
+    if (nab > 0 &&
+        ring_config(di, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, p->threads, p->reducer_threads, nab, rc))
+        return true;
+    return ring_config(di, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, p->threads, p->reducer_threads, 0, rc);
+}
+
 credit_status validate_args(const credit_args *a) {
     if (!a) return CREDIT_ERR_INVALID_ARG;
     if (a->op < 0 || a->op > 3) return CREDIT_ERR_INVALID_ARG;
@@ -319,7 +361,7 @@ credit_status check_plan(int device, const credit_args *a, const credit_plan_t *
         if (P < 1 || P > kMaxCluster) return CREDIT_ERR_UNSUPPORTED;
         if (p->path == CREDIT_PATH_CLUSTER && P < 2) return CREDIT_ERR_UNSUPPORTED;
         RingCfg rc;
-        if (!ring_config(*di, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, p->threads, p->reducer_threads, &rc))
+        if (!ring_config_for(*di, a, isz, P, p, &rc))
             return CREDIT_ERR_UNSUPPORTED;  // Eq. 3
         if (ring_max_clusters(device, a->op, a->in_dtype, tout, P, rc.threads, rc.smem) <= 0)
             return CREDIT_ERR_UNSUPPORTED;
@@ -358,6 +400,7 @@ static RowArgs make_row_args(const credit_args *a, unsigned *err, float *ws) {
     r.chunk_bytes = 0;
     r.ring = 0;
     r.reducers = 0;
+    r.affine = 0;
     r.trace = g_trace_buf;
     r.trace_rows = g_trace_rows;
     r.row0 = 0;
@@ -410,7 +453,7 @@ credit_status run_with_plan(int device, const credit_args *a, const credit_plan_
     if (p->path == CREDIT_PATH_ONE_CTA || p->path == CREDIT_PATH_CLUSTER) {
         const int P = p->path == CREDIT_PATH_ONE_CTA ? 1 : p->cluster_size;
         RingCfg rc;
-        if (!ring_config(d.info, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, p->threads, p->reducer_threads, &rc))
+        if (!ring_config_for(d.info, a, isz, P, p, &rc))
             return CREDIT_ERR_UNSUPPORTED;
         credit_status st = prepare_kernel(d, ks.ring, true);
         if (st != CREDIT_OK) return st;
@@ -420,12 +463,13 @@ credit_status run_with_plan(int device, const credit_args *a, const credit_plan_
         if (std::getenv("CREDIT_LOG"))
             std::fprintf(stderr,
                          "credit: ring op=%d P=%d clusters=%lld (max %d) threads=%d reducers=%d chunk=%d ring=%d "
-                         "smem=%lld\n",
-                         a->op, P, ncl, maxc, rc.threads, rc.reducers, rc.chunk, rc.ring, rc.smem);
+                         "affine=%d smem=%lld\n",
+                         a->op, P, ncl, maxc, rc.threads, rc.reducers, rc.chunk, rc.ring, rc.affine, rc.smem);
         RowArgs r = base;
         r.chunk_bytes = rc.chunk;
         r.ring = rc.ring;
         r.reducers = rc.reducers;
+        r.affine = rc.affine;
         void *args[] = {&r};
         cudaError_t e = launch(ks.ring, dim3(static_cast<unsigned>(P * ncl)), dim3(rc.threads),
                                static_cast<size_t>(rc.smem), P, s, args);

@@ -27,13 +27,17 @@ struct RingCfg {
     int ring;            // chunk slots
     int threads;         // reducer + writer threads + one producer warp
     int reducers;        // reducer threads
+    int affine;          // gamma/beta ring slots (0: direct loads)
+    long long aslot;     // bytes per affine slot
     long long smem;      // dynamic shared memory per CTA
     long long body_max;  // largest slice body (bytes) of any CTA
     int nch_max;         // chunks of the largest slice
 };
+// nab: gamma/beta arrays streamed through the affine ring (0, 1 or 2).
 bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring, int req_chunk, int req_threads,
-                 int req_reducers, RingCfg *out);
+                 int req_reducers, int nab, RingCfg *out);
 int ring_max_clusters(int device, int op, int tin, int tout, int P, int threads, long long smem);
+int affine_arrays(const credit_args *a);
 credit_status validate_args(const credit_args *a);
 credit_status check_plan(int device, const credit_args *a, const credit_plan_t *p);
 credit_status ensure_init(int *device_out, cudaStream_t s);

@@ -37,7 +37,7 @@ static bool env_force(const DeviceInfo *di, credit_plan_t *p, long long cols, in
         p->ctas_per_row = p->cluster_size;
         RingCfg rc;
         if (di && ring_config(*di, cols, dtype_size(tin), p->cluster_size, p->ring_chunks, p->chunk_bytes,
-                              p->threads, p->reducer_threads, &rc))
+                              p->threads, p->reducer_threads, 0, &rc))
             p->smem_bytes = rc.smem;
     } else if (!std::strcmp(fp, "two_pass")) {
         p->path = CREDIT_PATH_TWO_PASS;
@@ -75,7 +75,7 @@ void heuristic_plan(const DeviceInfo &di, int device, int op, long long rows, lo
         for (int pass = 0; pass < 2 && !pick; ++pass) {
             for (int P : {1, 2, 4, 8, 16}) {
                 RingCfg rc;
-                if (!ring_config(di, cols, isz, P, 0, 0, 0, 0, &rc)) continue;
+                if (!ring_config(di, cols, isz, P, 0, 0, 0, 0, 0, &rc)) continue;
                 if (pass == 0 && rc.body_max > 65536) continue;
                 if (ring_max_clusters(device, op, tin, tout, P, rc.threads, rc.smem) <= 0) continue;
                 pick = P;

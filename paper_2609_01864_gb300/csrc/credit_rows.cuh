@@ -58,6 +58,7 @@ struct RowArgs {
     int chunk_bytes;                      // ring kernel: bytes per staged chunk
     int ring;                             // ring kernel: chunk slots
     int reducers;                         // ring kernel: reducer threads (multiple of 32)
+    int affine;                           // ring kernel: gamma/beta ring slots (0 = direct loads)
     unsigned long long *trace;            // optional phase timestamps (see credit_set_trace)
     int trace_rows;                       // rows recorded per traced CTA
     long long row0;                       // first row of this launch
@@ -167,6 +168,22 @@ __device__ __forceinline__ void load_affine(const float *p, long long i0, bool v
     }
 }
 
+// SV affine values from the shared-memory affine ring (p == nullptr: dflt).
+template <int SV>
+__device__ __forceinline__ void load_affine_smem(const float *p, int off, float dflt, float (&v)[SV]) {
+    if (p == nullptr) {
+#pragma unroll
+        for (int k = 0; k < SV; ++k) v[k] = dflt;
+    } else {
+        const uint32_t base = smem_addr(p + off);
+#pragma unroll
+        for (int k = 0; k < SV / 4; ++k)
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(v[4 * k]), "=f"(v[4 * k + 1]), "=f"(v[4 * k + 2]), "=f"(v[4 * k + 3])
+                         : "r"(base + 16 * k));
+    }
+}
+
 __device__ __forceinline__ void copy_raw(unsigned char *dst, const unsigned char *src, int isz) {
     if (isz == 4) *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(src);
     else if (isz == 2) *reinterpret_cast<uint16_t *>(dst) = *reinterpret_cast<const uint16_t *>(src);
@@ -265,6 +282,10 @@ template <> struct Stream<OP_RMS> {
 //   writers  (the threads in between)  wait for a row's statistics, apply h
 //            to the retained slice (the reuse pass) and store the output
 //            segment, releasing each chunk to the producer.
+//   For LayerNorm / RMSNorm with gamma / beta, producer lane 1 streams the
+//   gamma / beta segment of each chunk into a small affine ring just ahead of
+//   the writers (the same columns for every row, served from L2), so the
+//   reuse pass reads only shared memory.
 // So row r is written while row r+1 is being reduced and exchanged and
 // row r+2 is streaming in: the cluster exchange and the reductions leave the
 // output stream busy.  A slice needs ceil(body / chunk_bytes) <= ring slots
@@ -292,6 +313,10 @@ constexpr int kMaxRing = 32;
 //   [576, 640)     published row statistics [parity][8 floats]
 //   [640, 1152)    reduction scratch (128 floats)
 //   [1152, 2176)   DSMEM slots [stage][parity][16 sources][4 floats]
+//   [2176, 2208)   affine_full[4] mbarriers
+//   [2208, 2240)   affine_empty[4] mbarriers
+// The chunk ring follows the control area; the affine ring (gamma and beta
+// segments of the chunk the writers are on, `affine` slots) follows the ring.
 
 __device__ __forceinline__ float *slot_ptr(float *slots, int stage, int par, int c) {
     return slots + ((stage * 2 + par) * 16 + c) * 4;
@@ -468,6 +493,8 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
     float *pub = reinterpret_cast<float *>(smem + 576);
     float *red = reinterpret_cast<float *>(smem + 640);
     float *slots = reinterpret_cast<float *>(smem + 1152);
+    uint64_t *affine_full = reinterpret_cast<uint64_t *>(smem + 2176);
+    uint64_t *affine_empty = reinterpret_cast<uint64_t *>(smem + 2208);
     unsigned char *ring = smem + kRingCtrl;
 
     constexpr int isz = Fmt<TIN>::size, V = Fmt<TIN>::V;
@@ -476,6 +503,12 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
     constexpr bool kFp8Stage = (TOUT == DT_E4M3) && (OP == OP_LN || OP == OP_RMS);
 
     const int CH = a.chunk_bytes, K = a.ring, gpc = CH / 16;
+    // affine ring: per slot, gamma (gpc*V floats) then beta (gpc*V floats)
+    const int A = a.affine;
+    const bool has_g = a.gamma != nullptr, has_b = (OP == OP_LN) && a.beta != nullptr;
+    const int aseg = gpc * V * 4;  // bytes of one gamma or beta segment
+    const int aslot = aseg * ((has_g ? 1 : 0) + (has_b ? 1 : 0));
+    unsigned char *aring = ring + static_cast<size_t>(K) * CH;
     const int P = static_cast<int>(cluster_nctarank());
     const int c = P > 1 ? static_cast<int>(cluster_ctarank()) : 0;
     const long long ncl = gridDim.x / P, cl = blockIdx.x / P;
@@ -492,6 +525,10 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
         for (int k = 0; k < 2; ++k) {
             mbar_init(&stats_full[k], 1);
             mbar_init(&stats_empty[k], static_cast<uint32_t>(Ww));
+        }
+        for (int k = 0; k < A; ++k) {
+            mbar_init(&affine_full[k], 1);
+            mbar_init(&affine_empty[k], static_cast<uint32_t>(Ww));
         }
         fence_mbar_init();
     }
@@ -545,6 +582,24 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                     bulk_g2s(ring + static_cast<size_t>(slot) * CH, src + off, bytes, &full[slot]);
                 }
                 trace_stamp(a, prr++, 5);
+            }
+        } else if (tid == Tp + 1 && A > 0) {
+            // gamma / beta segments of every chunk, in the writers' order
+            long long aj = 0;
+            for (long long row = cl; row < a.rows; row += ncl) {
+                const RowGeo g = geo(row);
+                const long long i_base = g.s.h0 + g.s.g_lo * V;
+                for (int k = 0; k < g.nch; ++k, ++aj) {
+                    const int slot = static_cast<int>(aj % A);
+                    if (aj >= A)
+                        mbar_wait_bounded(&affine_empty[slot], static_cast<uint32_t>(((aj / A) - 1) & 1), a.err);
+                    const uint32_t bytes = static_cast<uint32_t>(chunk_groups(g, k)) * V * 4;
+                    const long long e0 = i_base + static_cast<long long>(k) * gpc * V;
+                    unsigned char *dst = aring + static_cast<size_t>(slot) * aslot;
+                    mbar_arrive_expect_tx(&affine_full[slot], bytes * ((has_g ? 1u : 0u) + (has_b ? 1u : 0u)));
+                    if (has_g) bulk_g2s(dst, a.gamma + e0, bytes, &affine_full[slot]);
+                    if (has_b) bulk_g2s(dst + (has_g ? aseg : 0), a.beta + e0, bytes, &affine_full[slot]);
+                }
             }
         }
         __syncwarp();
@@ -690,7 +745,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
     } else {
         // ========================================================== writers
         const int wt = tid - Tr;
-        long long j = 0;
+        long long j = 0, aj_w = 0;
         int rr = 0;
         for (long long row = cl; row < a.rows; row += ncl, ++rr) {
             const RowGeo g = geo(row);
@@ -723,14 +778,25 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                 };
                 for (int k = 0; k < g.nch; ++k) {
                     const long long kg = static_cast<long long>(k) * gpc;
+                    const int aslot_k = A > 0 ? static_cast<int>((aj_w + k) % A) : 0;
+                    const float *ag = reinterpret_cast<const float *>(aring + static_cast<size_t>(aslot_k) * aslot);
+                    const float *ab = ag + (has_g ? gpc * V : 0);
+                    if (A > 0)
+                        mbar_wait_bounded(&affine_full[aslot_k], static_cast<uint32_t>(((aj_w + k) / A) & 1), a.err);
                     visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), wt, Tw, g.in_sc,
                                      [&](int gi, const float(&f)[V]) {
 #pragma unroll
                                          for (int hv = 0; hv < V; hv += SV) {
                                              float gg[SV], bb[SV], y[SV];
                                              const long long i0 = i_base + (kg + gi) * V + hv;
-                                             if constexpr (OP != OP_SOFTMAX) load_affine<SV>(a.gamma, i0, g_vec, 1.0f, gg);
-                                             if constexpr (OP == OP_LN) load_affine<SV>(a.beta, i0, b_vec, 0.0f, bb);
+                                             if constexpr (OP != OP_SOFTMAX) {
+                                                 if (A > 0) load_affine_smem<SV>(has_g ? ag : nullptr, gi * V + hv, 1.0f, gg);
+                                                 else load_affine<SV>(a.gamma, i0, g_vec, 1.0f, gg);
+                                             }
+                                             if constexpr (OP == OP_LN) {
+                                                 if (A > 0) load_affine_smem<SV>(has_b ? ab : nullptr, gi * V + hv, 0.0f, bb);
+                                                 else load_affine<SV>(a.beta, i0, b_vec, 0.0f, bb);
+                                             }
 #pragma unroll
                                              for (int q = 0; q < SV; ++q)
                                                  y[q] = h(f[hv + q], OP != OP_SOFTMAX ? gg[q] : 1.0f,
@@ -739,8 +805,12 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                                          }
                                      });
                     __syncwarp();
-                    if ((wt & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
+                    if ((wt & 31) == 0) {
+                        mbar_arrive(&empty[(j + k) % K]);
+                        if (A > 0) mbar_arrive(&affine_empty[aslot_k]);
+                    }
                 }
+                aj_w += g.nch;
                 const long long n_head = (c == 0 && wt == 0) ? g.s.h0 : 0;
                 const long long n_tail = (c == P - 1 && wt == Tw - 1) ? g.s.t0 : 0;
                 for (int e = 0; e < 2; ++e)
