@@ -118,8 +118,21 @@ bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring
         r.chunk = static_cast<int>(((r.body_max + n - 1) / n + 15) / 16 * 16);
     }
     r.nch_max = static_cast<int>((r.body_max + r.chunk - 1) / r.chunk);
-    r.affine = nab > 0 ? 2 : 0;
     r.aslot = static_cast<long long>(r.chunk / 16) * abytes_per16;
+    r.affine = 0;
+    r.affine_resident = 0;
+    if (nab > 0) {
+        // resident gamma / beta (one slot per chunk of the slice, loaded once)
+        // when that leaves room for one slice in the ring, else 2 streaming slots
+        const long long res = static_cast<long long>(r.nch_max) * r.aslot;
+        if (r.nch_max <= kMaxAffine &&
+            kRingCtrl + res + static_cast<long long>(r.nch_max) * r.chunk <= di.smem_optin) {
+            r.affine = r.nch_max < 1 ? 1 : r.nch_max;
+            r.affine_resident = 1;
+        } else {
+            r.affine = 2;
+        }
+    }
     const long long budget = di.smem_optin - kRingCtrl - r.affine * r.aslot;
     const long long fit = budget > 0 ? budget / r.chunk : 0;
     if (req_ring > 0) {
@@ -401,6 +414,7 @@ static RowArgs make_row_args(const credit_args *a, unsigned *err, float *ws) {
     r.ring = 0;
     r.reducers = 0;
     r.affine = 0;
+    r.affine_resident = 0;
     r.trace = g_trace_buf;
     r.trace_rows = g_trace_rows;
     r.row0 = 0;
@@ -463,13 +477,15 @@ credit_status run_with_plan(int device, const credit_args *a, const credit_plan_
         if (std::getenv("CREDIT_LOG"))
             std::fprintf(stderr,
                          "credit: ring op=%d P=%d clusters=%lld (max %d) threads=%d reducers=%d chunk=%d ring=%d "
-                         "affine=%d smem=%lld\n",
-                         a->op, P, ncl, maxc, rc.threads, rc.reducers, rc.chunk, rc.ring, rc.affine, rc.smem);
+                         "affine=%d%s smem=%lld\n",
+                         a->op, P, ncl, maxc, rc.threads, rc.reducers, rc.chunk, rc.ring, rc.affine,
+                         rc.affine_resident ? "(resident)" : "", rc.smem);
         RowArgs r = base;
         r.chunk_bytes = rc.chunk;
         r.ring = rc.ring;
         r.reducers = rc.reducers;
         r.affine = rc.affine;
+        r.affine_resident = rc.affine_resident;
         void *args[] = {&r};
         cudaError_t e = launch(ks.ring, dim3(static_cast<unsigned>(P * ncl)), dim3(rc.threads),
                                static_cast<size_t>(rc.smem), P, s, args);

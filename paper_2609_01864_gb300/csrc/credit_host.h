@@ -28,6 +28,7 @@ struct RingCfg {
     int threads;         // reducer + writer threads + one producer warp
     int reducers;        // reducer threads
     int affine;          // gamma/beta ring slots (0: direct loads)
+    int affine_resident; // slots hold the whole slice's gamma/beta
     long long aslot;     // bytes per affine slot
     long long smem;      // dynamic shared memory per CTA
     long long body_max;  // largest slice body (bytes) of any CTA

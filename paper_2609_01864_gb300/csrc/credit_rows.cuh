@@ -59,6 +59,7 @@ struct RowArgs {
     int ring;                             // ring kernel: chunk slots
     int reducers;                         // ring kernel: reducer threads (multiple of 32)
     int affine;                           // ring kernel: gamma/beta ring slots (0 = direct loads)
+    int affine_resident;                  // 1: the slots hold the whole slice's gamma/beta, loaded once
     unsigned long long *trace;            // optional phase timestamps (see credit_set_trace)
     int trace_rows;                       // rows recorded per traced CTA
     long long row0;                       // first row of this launch
@@ -282,10 +283,12 @@ template <> struct Stream<OP_RMS> {
 //   writers  (the threads in between)  wait for a row's statistics, apply h
 //            to the retained slice (the reuse pass) and store the output
 //            segment, releasing each chunk to the producer.
-//   For LayerNorm / RMSNorm with gamma / beta, producer lane 1 streams the
-//   gamma / beta segment of each chunk into a small affine ring just ahead of
-//   the writers (the same columns for every row, served from L2), so the
-//   reuse pass reads only shared memory.
+//   For LayerNorm / RMSNorm with gamma / beta, producer lane 1 stages the
+//   gamma / beta segment of each chunk in an affine ring, so the reuse pass
+//   reads only shared memory.  A persistent CTA handles the same columns for
+//   every row, so when the ring has one slot per chunk of the slice the
+//   segments are loaded once per launch and stay resident; otherwise they
+//   stream just ahead of the writers (served from L2).
 // So row r is written while row r+1 is being reduced and exchanged and
 // row r+2 is streaming in: the cluster exchange and the reductions leave the
 // output stream busy.  A slice needs ceil(body / chunk_bytes) <= ring slots
@@ -304,6 +307,7 @@ template <> struct Stream<OP_RMS> {
 // ======================================================================
 constexpr int kRingCtrl = 2304;
 constexpr int kMaxRing = 32;
+constexpr int kMaxAffine = 8;  // affine slots (resident mode: chunks per slice)
 // Control area layout:
 //   [0, 256)       full[32] mbarriers
 //   [256, 512)     empty[32] mbarriers
@@ -313,8 +317,8 @@ constexpr int kMaxRing = 32;
 //   [576, 640)     published row statistics [parity][8 floats]
 //   [640, 1152)    reduction scratch (128 floats)
 //   [1152, 2176)   DSMEM slots [stage][parity][16 sources][4 floats]
-//   [2176, 2208)   affine_full[4] mbarriers
-//   [2208, 2240)   affine_empty[4] mbarriers
+//   [2176, 2240)   affine_full[8] mbarriers
+//   [2240, 2304)   affine_empty[8] mbarriers
 // The chunk ring follows the control area; the affine ring (gamma and beta
 // segments of the chunk the writers are on, `affine` slots) follows the ring.
 
@@ -494,7 +498,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
     float *red = reinterpret_cast<float *>(smem + 640);
     float *slots = reinterpret_cast<float *>(smem + 1152);
     uint64_t *affine_full = reinterpret_cast<uint64_t *>(smem + 2176);
-    uint64_t *affine_empty = reinterpret_cast<uint64_t *>(smem + 2208);
+    uint64_t *affine_empty = reinterpret_cast<uint64_t *>(smem + 2240);
     unsigned char *ring = smem + kRingCtrl;
 
     constexpr int isz = Fmt<TIN>::size, V = Fmt<TIN>::V;
@@ -585,13 +589,14 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
             }
         } else if (tid == Tp + 1 && A > 0) {
             // gamma / beta segments of every chunk, in the writers' order
+            // (resident: the first row's chunks only, one slot each)
             long long aj = 0;
-            for (long long row = cl; row < a.rows; row += ncl) {
+            for (long long row = cl; row < a.rows && !(a.affine_resident && row > cl); row += ncl) {
                 const RowGeo g = geo(row);
                 const long long i_base = g.s.h0 + g.s.g_lo * V;
                 for (int k = 0; k < g.nch; ++k, ++aj) {
                     const int slot = static_cast<int>(aj % A);
-                    if (aj >= A)
+                    if (aj >= A && !a.affine_resident)
                         mbar_wait_bounded(&affine_empty[slot], static_cast<uint32_t>(((aj / A) - 1) & 1), a.err);
                     const uint32_t bytes = static_cast<uint32_t>(chunk_groups(g, k)) * V * 4;
                     const long long e0 = i_base + static_cast<long long>(k) * gpc * V;
@@ -778,11 +783,12 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                 };
                 for (int k = 0; k < g.nch; ++k) {
                     const long long kg = static_cast<long long>(k) * gpc;
-                    const int aslot_k = A > 0 ? static_cast<int>((aj_w + k) % A) : 0;
+                    const int aslot_k = A > 0 ? (a.affine_resident ? k : static_cast<int>((aj_w + k) % A)) : 0;
                     const float *ag = reinterpret_cast<const float *>(aring + static_cast<size_t>(aslot_k) * aslot);
                     const float *ab = ag + (has_g ? gpc * V : 0);
-                    if (A > 0)
-                        mbar_wait_bounded(&affine_full[aslot_k], static_cast<uint32_t>(((aj_w + k) / A) & 1), a.err);
+                    if (A > 0 && (!a.affine_resident || rr == 0))
+                        mbar_wait_bounded(&affine_full[aslot_k],
+                                          a.affine_resident ? 0u : static_cast<uint32_t>(((aj_w + k) / A) & 1), a.err);
                     visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), wt, Tw, g.in_sc,
                                      [&](int gi, const float(&f)[V]) {
 #pragma unroll
@@ -807,7 +813,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                     __syncwarp();
                     if ((wt & 31) == 0) {
                         mbar_arrive(&empty[(j + k) % K]);
-                        if (A > 0) mbar_arrive(&affine_empty[aslot_k]);
+                        if (A > 0 && !a.affine_resident) mbar_arrive(&affine_empty[aslot_k]);
                     }
                 }
                 aj_w += g.nch;

@@ -159,3 +159,18 @@ def test_simple_entry_points_use_the_planner():
     torch.cuda.synchronize()
     ref = U.reference(C.SOFTMAX, C.BF16, xb.cpu())
     assert U.error_metric(C.SOFTMAX, C.BF16, U.to64(yb), ref) <= 1.0
+
+
+# --------------------------------------------------------------- gamma/beta staging modes
+# 16-byte-aligned rows with gamma/beta: the ring kernel stages gamma/beta in
+# shared memory, resident for small slices and streamed for wide ones; more
+# rows than persistent clusters make every CTA recycle its rings.
+@pytest.mark.parametrize("op", [C.LAYERNORM, C.RMSNORM])
+@pytest.mark.parametrize("dt,cols,P", [(C.F32, 4096, 1), (C.F32, 16384, 2), (C.F32, 40000, 1), (C.F32, 65536, 4),
+                                       (C.BF16, 8192, 1), (C.BF16, 40000, 2), (C.FP8_E4M3, 65536, 1)])
+def test_affine_staging_modes(op, dt, cols, P):
+    rows = 400
+    x, s = U.make_input(dt, rows, cols, kind="outliers", seed=cols + P)
+    g, b = _affine(op, cols, seed=7)
+    plan = C.make_plan(C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P)
+    U.check_against_oracle(op, x, s, plan=plan, gamma=g, beta=b)
