@@ -175,7 +175,10 @@ bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring
 // segments of the slices 16-byte aligned.
 int affine_arrays(const credit_args *a) {
     if (a->op != OP_LN && a->op != OP_RMS) return 0;
-    if (std::getenv("CREDIT_NO_AFFINE")) return 0;
+    // gamma / beta staging in shared memory is opt-in (CREDIT_AFFINE_STAGE=1):
+    // it costs ring capacity, and the writers' batched L2 loads measure faster
+    const char *stage = std::getenv("CREDIT_AFFINE_STAGE");
+    if (!stage || std::atoi(stage) == 0) return 0;
     const int isz = dtype_size(a->in_dtype);
     const long long ld = a->ld_in ? a->ld_in : a->cols;
     if ((ld * isz) % 16) return 0;

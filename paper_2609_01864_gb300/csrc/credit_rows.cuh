@@ -475,6 +475,60 @@ __device__ __forceinline__ void visit_chunk(const unsigned char *cb, int gn, int
     }
 }
 
+// Reuse pass of the norms over one staged chunk with gamma / beta read from
+// global memory (L2): for each batch of U groups every gamma / beta load is
+// issued before the batch's shared-memory reads and stores, so their latency
+// overlaps instead of following each store.
+template <int OP, int TIN, int TOUT, class H>
+__device__ __forceinline__ void write_chunk_direct(const unsigned char *cb, int gn, int wt, int Tw, float in_sc,
+                                                   const float *gamma, const float *beta, long long i0c,
+                                                   unsigned char *out_row, bool out_vec, H &&h) {
+    constexpr int V = Fmt<TIN>::V, osz = Fmt<TOUT>::size;
+    constexpr int U = (V == 4) ? 4 : (V == 8 ? 2 : 1);
+    constexpr int NV = V / 4;  // float4 per group
+    for (int g0 = wt; g0 < gn; g0 += U * Tw) {
+        float4 gv[U][NV], bv[U][NV];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int g = g0 + u * Tw;
+            const long long i0 = i0c + static_cast<long long>(g) * V;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                if (g < gn && gamma) gv[u][k] = __ldg(reinterpret_cast<const float4 *>(gamma + i0) + k);
+                else gv[u][k] = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+                if (g < gn && beta) bv[u][k] = __ldg(reinterpret_cast<const float4 *>(beta + i0) + k);
+                else bv[u][k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+        }
+        uint4 w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int g = g0 + u * Tw;
+            if (g < gn) w[u] = *reinterpret_cast<const uint4 *>(cb + g * 16);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int g = g0 + u * Tw;
+            if (g >= gn) continue;
+            float f[V], y[V];
+            decode_group<TIN>(w[u], f, in_sc);
+            const float *gf = reinterpret_cast<const float *>(&gv[u][0]);
+            const float *bf = reinterpret_cast<const float *>(&bv[u][0]);
+#pragma unroll
+            for (int q = 0; q < V; ++q) y[q] = h(f[q], gf[q], bf[q]);
+            const long long i0 = i0c + static_cast<long long>(g) * V;
+#pragma unroll
+            for (int hv = 0; hv < V; hv += (V < 8 ? V : 8)) {
+                constexpr int SV = V < 8 ? V : 8;
+                float ys[SV];
+#pragma unroll
+                for (int q = 0; q < SV; ++q) ys[q] = y[hv + q];
+                store_group<TOUT, SV>(out_row + (i0 + hv) * osz, ys, out_vec);
+            }
+        }
+    }
+}
+
 // Phase timestamps (global timer, ns) of the first kTraceCtas CTAs, for the
 // first trace_rows rows each: [0] row start, [1] stage-1 sweep done (all
 // chunks waited), [2] CTA reduction done, [3] exchange done, [4] reuse pass
@@ -789,6 +843,16 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                     if (A > 0 && (!a.affine_resident || rr == 0))
                         mbar_wait_bounded(&affine_full[aslot_k],
                                           a.affine_resident ? 0u : static_cast<uint32_t>(((aj_w + k) / A) & 1), a.err);
+                    if constexpr (OP == OP_LN || OP == OP_RMS) {
+                        if (A == 0 && g_vec && b_vec && (has_g || has_b)) {
+                            write_chunk_direct<OP, TIN, TOUT>(chunk_ptr(j, k), chunk_groups(g, k), wt, Tw, g.in_sc,
+                                                              has_g ? a.gamma : nullptr, has_b ? a.beta : nullptr,
+                                                              i_base + kg * V, out_row, out_vec, h);
+                            __syncwarp();
+                            if ((wt & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
+                            continue;
+                        }
+                    }
                     visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), wt, Tw, g.in_sc,
                                      [&](int gi, const float(&f)[V]) {
 #pragma unroll
