@@ -214,6 +214,30 @@ credit_status credit_plan_check(const credit_args *args, const credit_plan_t *pl
 credit_status credit_set_trace(void *device_buf, int64_t bytes);
 
 /*
+ * credit_run_two_pass_noalloc -- the split-row two-pass path (ctas_per_row
+ * CTAs per row, partials exchanged through device memory between two kernel
+ * launches) for callers that cannot allocate device memory: frameworks whose
+ * caching allocator owns the device heap and pass a library only finished
+ * buffers, or code recording a CUDA graph in global capture mode, where
+ * cudaMalloc is a prohibited call.  The paper has no counterpart; it is an
+ * interface variant of the non-DSMEM baseline.
+ *   args          as credit_run_ex (caller-owned device buffers)
+ *   ctas_per_row  CTAs per row, 2..4096; outside that: CREDIT_ERR_UNSUPPORTED
+ * Allocates nothing and never calls credit_init(): the partials live in a
+ * fixed 4 MiB array in the library's device image (on every GPU that loads
+ * the library, until the process exits), 262144 (row, CTA) partial sets, so
+ * one launch covers floor(262144 / ctas_per_row) rows and longer calls are
+ * split into several launches on `stream`.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  The array keeps the last call's partials; each
+ * call writes every partial it reads, so nothing needs clearing.  All calls
+ * share the one array: calls that can overlap on the GPU (different streams,
+ * no ordering between them) race and corrupt each other's results.
+ */
+credit_status credit_run_two_pass_noalloc(const credit_args *args, int32_t ctas_per_row,
+                                          cudaStream_t stream);
+
+/*
  * credit_device_error -- synchronise `stream`, then read and clear the
  * device error word of the current device.  Returns CREDIT_ERR_TIMEOUT if a
  * kernel's bounded wait gave up since the last call, CREDIT_OK otherwise.

@@ -83,6 +83,8 @@ def lib() -> ctypes.CDLL:
             L.credit_plan_ex.argtypes = [i32, i64, i64, i32, i32, ctypes.POINTER(PlanT)]
             L.credit_run_ex.restype = i32
             L.credit_run_ex.argtypes = [ctypes.POINTER(ArgsT), ctypes.POINTER(PlanT), vp]
+            L.credit_run_two_pass_noalloc.restype = i32
+            L.credit_run_two_pass_noalloc.argtypes = [ctypes.POINTER(ArgsT), i32, vp]
             L.credit_set_trace.restype = i32
             L.credit_set_trace.argtypes = [vp, i64]
             L.credit_plan_check.restype = i32
@@ -219,6 +221,13 @@ def run_ex(op: int, x, out, *, plan: PlanT | None = None, stream=None, **kw) -> 
     st = lib().credit_run_ex(ctypes.byref(a), ctypes.byref(plan) if plan is not None else None, _stream(stream))
     _check(st, "credit_run_ex")
     return st
+
+
+def run_two_pass_noalloc(op: int, x, out, ctas_per_row: int, *, stream=None, **kw) -> int:
+    """credit_run_two_pass_noalloc: the split-row two-pass path with the
+    library's fixed device scratch (no allocation).  Returns the status."""
+    a = make_args(op, x, out, **kw)
+    return lib().credit_run_two_pass_noalloc(ctypes.byref(a), int(ctas_per_row), _stream(stream))
 
 
 def run_ex_status(*args, **kw) -> int:
