@@ -201,6 +201,85 @@ credit_status credit_run_ex(const credit_args *args, const credit_plan_t *plan,
  */
 credit_status credit_plan_check(const credit_args *args, const credit_plan_t *plan);
 
+/* ------------------------------------------------------------------ profiling
+ * Primitive characterisation (Sec. III-A, Table II) on the current device.
+ * Latencies in cycles per dependent load; rates in bytes per cycle per SM;
+ * index k of the per-P arrays is P = 2, 4, 8, 16.  The two CTAs of the
+ * latency and throughput clusters run on different SMs (distinct_sms = 1
+ * when confirmed with %smid).  Every figure is the median of `runs`
+ * (<= 0: 15) launches.  Allocates a small device buffer.
+ */
+typedef struct {
+    double lat_local_cycles, lat_remote_cycles;
+    double sync_cycles[4];
+    double rate_local_read, rate_local_store, rate_remote_read;
+    double rate_remote_store[4];
+    double sm_clock_mhz;
+    int32_t distinct_sms;
+} credit_microbench_t;
+credit_status credit_microbench(credit_microbench_t *out, int runs);
+
+/*
+ * credit_control_time -- median time (us, of `reps` launches) of the
+ * work-free control kernel (Sec. III-D): the staged kernel's launch shape
+ * (persistent clusters of P CTAs, threads, dynamic shared memory) and its
+ * per-row DSMEM push all-gather, with no data work.  T_ctrl(M, N, P) of
+ * Eq. 9 = control(P) - control(1).  Allocates a small device buffer.
+ */
+credit_status credit_control_time(credit_op op, int64_t rows, int64_t cols, credit_dtype dtype, int32_t P,
+                                  int32_t reps, float *us_out);
+
+/* ------------------------------------------------------------------ cost model
+ * One evaluation of the profitability model for one (M, N, P) (Sec. III-D):
+ *   B_eff   = M N b_B / T_B                                   (Eq. 7)
+ *   T_save  = T_B b_reread / b_B
+ *   W       = ceil(M / active_clusters)                       (Eq. 8; the
+ *             paper's floor(S/P) replaced by the queried count)
+ *   T_replay = W ceil(N/P) b_keep / (f B_smem_read)
+ *   T_DSM   = s W (P-1) q_sum / (f B_dsm_store)
+ *   T_deposit = max(0, W ceil(N/P) b_keep / (f B_smem_store) - M N b_in / B_eff)
+ *   dT      = T_save - T_ctrl - T_replay - T_deposit - T_DSM    (Eq. 9)
+ * ablation = 1 evaluates the "peak bandwidth + serialized staging" model of
+ * Table IV instead: T_save = M N b_reread / B_peak and T_deposit = the full
+ * staging time.  Times in us, f in MHz, rates in bytes per cycle, B_peak in
+ * GB/s.  Pure host arithmetic; no device needed.
+ */
+typedef struct {
+    double M, N, P;
+    double T_B_us, T_ctrl_us;
+    double b_B, b_reread, b_keep, b_in;
+    double s_bytes, q_sum;
+    double active_clusters;
+    double f_mhz;
+    double B_smem_read, B_smem_store, B_dsm_store;
+    double B_peak_gbs;
+    int32_t ablation;
+} credit_model_inputs;
+typedef struct {
+    double W, B_eff_gbs, T_save_us, T_replay_us, T_dsm_us, T_deposit_us, T_smem_w_us, T_input_us, dT_us;
+} credit_model_terms;
+credit_status credit_model_eval(const credit_model_inputs *in, credit_model_terms *out);
+
+/*
+ * credit_calibrate -- profile the current device and write a calibration
+ * file: microbenchmarks, the selected non-DSMEM baseline's time T_B over a
+ * (rows, cols) grid per op and dtype, and the control kernel's T_ctrl over a
+ * (rows, cols, P) grid (Sec. III-D).  Loads the result for planning too.
+ * Slow (seconds to a minute); allocates up to `max_bytes` (<= 0: 4 GiB) of
+ * device memory for the timing buffers.  CREDIT_ERR_IO if the file cannot
+ * be written.
+ */
+credit_status credit_calibrate(const char *path, int64_t max_bytes);
+
+/*
+ * credit_load_model -- load a calibration file (and, if it names one, the
+ * learned model's weights) for the current device.  From then on
+ * credit_plan scores candidates with the analytic model (Eq. 7-9), or with
+ * the learned model when CREDIT_MODEL=learned and weights are loaded.
+ * CREDIT_ERR_IO for a missing or malformed file.
+ */
+credit_status credit_load_model(const char *path);
+
 /*
  * credit_set_trace -- phase tracing of the staged (ring) kernel.  While a
  * buffer is set, the first 32 CTAs of every staged launch write global-timer

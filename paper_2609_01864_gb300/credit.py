@@ -100,8 +100,48 @@ def lib() -> ctypes.CDLL:
     return _lib
 
 
+class MicrobenchT(ctypes.Structure):
+    _fields_ = [("lat_local_cycles", ctypes.c_double), ("lat_remote_cycles", ctypes.c_double),
+                ("sync_cycles", ctypes.c_double * 4), ("rate_local_read", ctypes.c_double),
+                ("rate_local_store", ctypes.c_double), ("rate_remote_read", ctypes.c_double),
+                ("rate_remote_store", ctypes.c_double * 4), ("sm_clock_mhz", ctypes.c_double),
+                ("distinct_sms", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if hasattr(v, "__len__") else v
+        return d
+
+
+MODEL_IN_FIELDS = ["M", "N", "P", "T_B_us", "T_ctrl_us", "b_B", "b_reread", "b_keep", "b_in", "s_bytes", "q_sum",
+                   "active_clusters", "f_mhz", "B_smem_read", "B_smem_store", "B_dsm_store", "B_peak_gbs"]
+MODEL_OUT_FIELDS = ["W", "B_eff_gbs", "T_save_us", "T_replay_us", "T_dsm_us", "T_deposit_us", "T_smem_w_us",
+                    "T_input_us", "dT_us"]
+
+
+class ModelInT(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in MODEL_IN_FIELDS] + [("ablation", ctypes.c_int32)]
+
+
+class ModelOutT(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in MODEL_OUT_FIELDS]
+
+
 def _extra_prototypes(L):
     """Prototypes of the optional subsystems (profiling, model, ragged, MLP)."""
+    i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    L.credit_microbench.restype = i32
+    L.credit_microbench.argtypes = [ctypes.POINTER(MicrobenchT), i32]
+    L.credit_control_time.restype = i32
+    L.credit_control_time.argtypes = [i32, i64, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_float)]
+    L.credit_model_eval.restype = i32
+    L.credit_model_eval.argtypes = [ctypes.POINTER(ModelInT), ctypes.POINTER(ModelOutT)]
+    L.credit_calibrate.restype = i32
+    L.credit_calibrate.argtypes = [ctypes.c_char_p, i64]
+    L.credit_load_model.restype = i32
+    L.credit_load_model.argtypes = [ctypes.c_char_p]
     return L
 
 
@@ -244,6 +284,36 @@ def set_trace(buf=None) -> None:
         _check(lib().credit_set_trace(None, 0), "credit_set_trace")
     else:
         _check(lib().credit_set_trace(_ptr(buf), buf.numel() * buf.element_size()), "credit_set_trace")
+
+
+def microbench(runs: int = 15) -> dict:
+    m = MicrobenchT()
+    _check(lib().credit_microbench(ctypes.byref(m), runs), "credit_microbench")
+    return m.as_dict()
+
+
+def control_time(op: int, rows: int, cols: int, dtype: int, P: int, reps: int = 15) -> float:
+    us = ctypes.c_float()
+    _check(lib().credit_control_time(op, rows, cols, dtype, P, reps, ctypes.byref(us)), "credit_control_time")
+    return us.value
+
+
+def model_eval(**kw) -> dict:
+    """credit_model_eval: the Eq. 7-9 terms for explicit inputs (host only)."""
+    i = ModelInT()
+    for k, v in kw.items():
+        setattr(i, k, v)
+    o = ModelOutT()
+    _check(lib().credit_model_eval(ctypes.byref(i), ctypes.byref(o)), "credit_model_eval")
+    return {k: getattr(o, k) for k in MODEL_OUT_FIELDS}
+
+
+def calibrate(path: str, max_bytes: int = 0) -> None:
+    _check(lib().credit_calibrate(path.encode(), max_bytes), "credit_calibrate")
+
+
+def load_model(path: str) -> None:
+    _check(lib().credit_load_model(path.encode()), "credit_load_model")
 
 
 def device_error(stream=None) -> int:

@@ -5,9 +5,23 @@
 
 namespace credit {
 
-// Fill *p from the loaded calibration / learned model.  Returns false when no
-// model is loaded (the caller then uses the built-in heuristic).
+// Fill *p from the loaded calibration (analytic model, or the learned model
+// when CREDIT_MODEL=learned).  Returns false when no calibration is loaded
+// (the caller then uses the built-in heuristic).
 bool model_plan(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin, int tout,
                 credit_plan_t *p);
 
+// Analytic model (Eq. 7-9; ablation = 1: Table IV's peak-bandwidth +
+// serialized-staging model).  best_dT receives the winning dT (us).
+bool analytic_plan(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin, int tout,
+                   int ablation, credit_plan_t *p, double *best_dT);
+
+// Learned model: argmin of the predicted latency over the legal candidates.
+bool learned_plan(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin, int tout,
+                  credit_plan_t *p);
+
+int two_pass_split(int sm_count, long long rows, long long cols, int isz);
+
 }  // namespace credit
+
+extern "C" credit_status credit_mlp_load(const char *path);
