@@ -270,6 +270,9 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     C.init(local)
+    calib = os.path.join(ROOT, "paper_2609_01864_gb300", "data", "gb300.calib")
+    if os.path.exists(calib) and not args.no_model:
+        C.load_model(calib)
     dev = torch.device("cuda", local)
     widths = WIDTHS if not args.widths else [int(w) for w in args.widths.split(",")]
 
@@ -466,6 +469,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--widths", default="")
     ap.add_argument("--no-picks", action="store_true")
+    ap.add_argument("--no-model", action="store_true", help="plan with the built-in heuristic")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
