@@ -280,6 +280,37 @@ credit_status credit_calibrate(const char *path, int64_t max_bytes);
  */
 credit_status credit_load_model(const char *path);
 
+/* ------------------------------------------------------------------ learned model
+ * A 3 x 64 ReLU MLP predicting log2 of a candidate plan's latency (us) from
+ * 16 features (credit_mlp_features), trained on the GPU by the library's own
+ * FP32 kernels (forward, backward, Adam; no tensor cores).  With
+ * CREDIT_MODEL=learned, credit_plan picks the legal candidate with the
+ * smallest predicted latency; the analytic model stays the fallback.  The
+ * paper has no learned model; this is the project's addition.
+ */
+#define CREDIT_MLP_FEATURES 16
+int64_t credit_mlp_num_params(void);
+/* Features of candidate (path, P, G) for (op, dtypes, rows, cols) into out[16]:
+ * log2 rows, log2 cols, input dtype one-hot, op one-hot, path one-hot
+ * (one-CTA, two-pass, cluster), log2 P, log2 G, log2 algorithmic bytes,
+ * output bytes per element. */
+credit_status credit_mlp_features(int32_t op, int32_t in_dtype, int32_t out_dtype, int64_t rows, int64_t cols,
+                                  int32_t path, int32_t P, int32_t G, float *out);
+/* Train from scratch on n host samples (X n x 16, y = log2 us): minibatch
+ * Adam on the MSE of standardised targets; He-initialised from `seed`.
+ * loss_curve (NULL or `epochs` floats) gets the mean training loss per epoch. */
+credit_status credit_mlp_train(const float *X, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,
+                               uint64_t seed, float *loss_curve);
+/* Batched GPU inference: out[i] = predicted log2 us of feature row i. */
+credit_status credit_mlp_predict(const float *X, int64_t n, float *out);
+/* One GPU forward + backward with explicit parameters on raw inputs: MSE loss
+ * and its gradient (host arrays; params and grad have credit_mlp_num_params()
+ * floats).  For checking the kernels. */
+credit_status credit_mlp_grad(const float *params, const float *X, const float *t, int64_t n, float *grad,
+                              float *loss);
+credit_status credit_mlp_save(const char *path);
+credit_status credit_mlp_load(const char *path);
+
 /*
  * credit_set_trace -- phase tracing of the staged (ring) kernel.  While a
  * buffer is set, the first 32 CTAs of every staged launch write global-timer

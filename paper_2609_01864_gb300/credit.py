@@ -142,6 +142,20 @@ def _extra_prototypes(L):
     L.credit_calibrate.argtypes = [ctypes.c_char_p, i64]
     L.credit_load_model.restype = i32
     L.credit_load_model.argtypes = [ctypes.c_char_p]
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.credit_mlp_num_params.restype = i64
+    L.credit_mlp_features.restype = i32
+    L.credit_mlp_features.argtypes = [i32, i32, i32, i64, i64, i32, i32, i32, fp]
+    L.credit_mlp_train.restype = i32
+    L.credit_mlp_train.argtypes = [fp, fp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64, fp]
+    L.credit_mlp_predict.restype = i32
+    L.credit_mlp_predict.argtypes = [fp, i64, fp]
+    L.credit_mlp_grad.restype = i32
+    L.credit_mlp_grad.argtypes = [fp, fp, fp, i64, fp, fp]
+    L.credit_mlp_save.restype = i32
+    L.credit_mlp_save.argtypes = [ctypes.c_char_p]
+    L.credit_mlp_load.restype = i32
+    L.credit_mlp_load.argtypes = [ctypes.c_char_p]
     return L
 
 
@@ -314,6 +328,65 @@ def calibrate(path: str, max_bytes: int = 0) -> None:
 
 def load_model(path: str) -> None:
     _check(lib().credit_load_model(path.encode()), "credit_load_model")
+
+
+MLP_FEATURES = 16
+
+
+def _fptr(a):
+    import numpy as np
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def mlp_num_params() -> int:
+    return int(lib().credit_mlp_num_params())
+
+
+def mlp_features(op, in_dtype, out_dtype, rows, cols, path, P, G):
+    import numpy as np
+    f = np.zeros(MLP_FEATURES, dtype=np.float32)
+    _check(lib().credit_mlp_features(op, in_dtype, out_dtype, rows, cols, path, P, G, _fptr(f)),
+           "credit_mlp_features")
+    return f
+
+
+def mlp_train(X, y, *, epochs=200, batch=256, lr=2e-3, seed=0):
+    import numpy as np
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    curve = np.zeros(epochs, dtype=np.float32)
+    _check(lib().credit_mlp_train(_fptr(X), _fptr(y), X.shape[0], epochs, batch, lr, seed, _fptr(curve)),
+           "credit_mlp_train")
+    return curve
+
+
+def mlp_predict(X):
+    import numpy as np
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    out = np.zeros(X.shape[0], dtype=np.float32)
+    _check(lib().credit_mlp_predict(_fptr(X), X.shape[0], _fptr(out)), "credit_mlp_predict")
+    return out
+
+
+def mlp_grad(params, X, t):
+    import numpy as np
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    g = np.zeros(mlp_num_params(), dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    _check(lib().credit_mlp_grad(_fptr(params), _fptr(X), _fptr(t), X.shape[0], _fptr(g), _fptr(loss)),
+           "credit_mlp_grad")
+    return float(loss[0]), g
+
+
+def mlp_save(path: str):
+    _check(lib().credit_mlp_save(path.encode()), "credit_mlp_save")
+
+
+def mlp_load(path: str):
+    _check(lib().credit_mlp_load(path.encode()), "credit_mlp_load")
 
 
 def device_error(stream=None) -> int:

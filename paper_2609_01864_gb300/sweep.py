@@ -1,0 +1,209 @@
+"""Profiling sweep, learned-model training and pick-accuracy evaluation.
+
+Times every legal candidate plan (one-CTA, cluster P in {2, 4, 8, 16},
+two-pass G = 1 and the split factor) of a seeded set of shapes (rows
+2^U(6,16), cols 2^U(10,20), dtype and op uniform, I/O <= a byte cap;
+median of `reps` CUDA-event timings), splits the shapes 80/20, trains the
+latency MLP on the GPU with the library's kernels, and reports, on the
+held-out shapes, how often each planner's pick is within 5% of the measured
+best candidate: the learned model, the analytic model (Eq. 7-9), and the
+ablation model of Table IV.
+
+    python -m paper_2609_01864_gb300.sweep --shapes 2000 --out DIR
+
+writes DIR/gb300_mlp.txt (weights), DIR/sweep_gb300.csv (timings) and
+DIR/sweep_gb300_summary.json.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import sys
+import time
+
+import numpy as np
+import torch
+
+from . import credit as C
+from . import synth
+
+DT_TORCH = {0: torch.float32, 1: torch.bfloat16, 2: torch.float8_e4m3fn}
+
+
+def candidates(op, rows, cols, dtype, x, y, sc, osc, gamma, beta):
+    out = []
+    kw = dict(rows=rows, cols=cols, in_dtype=dtype, out_dtype=C.F32 if op == C.LOGSUMEXP else dtype,
+              in_scale=sc, out_scale=osc, gamma=gamma, beta=beta)
+    for P in (1, 2, 4, 8, 16):
+        p = C.make_plan(C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P)
+        if C.plan_check(op, x, y, p, **kw) == C.OK:
+            out.append((C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P, P, p))
+    Gs = [1]
+    auto = C.plan(op, rows, cols, dtype)  # any plan; the split factor comes from the two-pass rule
+    g_auto = two_pass_split(rows, cols, dtype)
+    if g_auto > 1:
+        Gs.append(g_auto)
+    for G in Gs:
+        out.append((C.PATH_TWO_PASS, 1, G, C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)))
+    del auto
+    return out, kw
+
+
+def two_pass_split(rows, cols, dtype, sm_count=None):
+    """Mirror of the library's split rule (enough CTAs for 4 waves, >= 1024
+    16-byte groups per CTA)."""
+    if sm_count is None:
+        sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    isz = {0: 4, 1: 2, 2: 1}[dtype]
+    target = 4 * sm_count
+    if rows >= target:
+        return 1
+    G = -(-target // rows)
+    gmax = max(1, (cols * isz // 16) // 1024)
+    return int(max(1, min(G, gmax, 1024)))
+
+
+def time_plan(fn, reps):
+    for _ in range(2):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) * 1e3 for a, b in ev)
+
+
+def run_sweep(shapes, reps, cap_bytes, log=None):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    buf_in = torch.empty(cap_bytes, dtype=torch.uint8, device=dev)
+    buf_out = torch.empty(cap_bytes, dtype=torch.uint8, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(synth.SEED_SWEEP)
+    # inputs: N(0, 1) floats written through each dtype's view of the same buffer
+    max_cols = max(s[3] for s in shapes)
+    max_rows = max(s[2] for s in shapes)
+    gamma, beta = synth.gamma_beta(max_cols, device=dev)
+    scales = torch.ones(max_rows, device=dev)
+    oscales = torch.empty(max_rows, device=dev)
+    rows_out = []
+    t0 = time.time()
+    for si, (op, dt, rows, cols) in enumerate(shapes):
+        isz = {0: 4, 1: 2, 2: 1}[dt]
+        x = buf_in[: rows * cols * isz].view(DT_TORCH[dt]).view(rows, cols)
+        src = torch.randn(rows, cols, device=dev, generator=g) if rows * cols * 4 <= 2 ** 31 else None
+        if src is not None:
+            x.copy_(src.clamp_(-8, 8).to(DT_TORCH[dt]))
+            del src
+        else:
+            x.view(torch.uint8).fill_(0x3c)
+        y = buf_out[: rows * cols * 4].view(torch.float32)
+        cands, kw = candidates(op, rows, cols, dt, x, y, scales[:rows], oscales[:rows],
+                               gamma[:cols] if op in (2, 3) else None, beta[:cols] if op == 2 else None)
+        times = []
+        for path, P, G, plan in cands:
+            us = time_plan(lambda: C.run_ex(op, x, y, plan=plan, **kw), reps)
+            times.append((path, P, G, us))
+        for path, P, G, us in times:
+            rows_out.append(dict(shape=si, op=op, dtype=dt, rows=rows, cols=cols, path=path, P=P, G=G, us=us))
+        if log and si % 100 == 0:
+            print(f"shape {si}/{len(shapes)} {time.time() - t0:.0f}s", file=log, flush=True)
+    assert C.device_error() == C.OK
+    return rows_out
+
+
+def features_of(r):
+    out_dt = C.F32 if r["op"] == C.LOGSUMEXP else r["dtype"]
+    return C.mlp_features(r["op"], r["dtype"], out_dt, r["rows"], r["cols"], r["path"], r["P"], r["G"])
+
+
+def evaluate(rows, test_shapes):
+    by_shape = {}
+    for r in rows:
+        by_shape.setdefault(r["shape"], []).append(r)
+    res = {"learned": 0, "analytic": 0, "ablation": 0, "always_two_pass": 0, "always_best_non_dsmem": 0}
+    n = 0
+    feats, owners = [], []
+    for s in test_shapes:
+        for r in by_shape.get(s, []):
+            feats.append(features_of(r))
+            owners.append(r)
+    pred = C.mlp_predict(np.stack(feats)) if feats else []
+    for r, pr in zip(owners, pred):
+        r["pred_log2us"] = float(pr)
+    for s in test_shapes:
+        cand = by_shape.get(s)
+        if not cand:
+            continue
+        n += 1
+        best = min(c["us"] for c in cand)
+        ok = lambda c: c["us"] <= 1.05 * best  # noqa: E731
+        learned = min(cand, key=lambda c: c["pred_log2us"])
+        res["learned"] += ok(learned)
+        r0 = cand[0]
+        for name, env in (("analytic", None), ("ablation", "ablation")):
+            if env:
+                os.environ["CREDIT_MODEL"] = env
+            else:
+                os.environ.pop("CREDIT_MODEL", None)
+            p = C.plan(r0["op"], r0["rows"], r0["cols"], r0["dtype"])
+            os.environ.pop("CREDIT_MODEL", None)
+            match = [c for c in cand if c["path"] == p.path and (c["P"] == p.cluster_size if p.path != C.PATH_TWO_PASS
+                                                                  else c["G"] == p.ctas_per_row)]
+            res[name] += ok(match[0]) if match else 0
+        tp = [c for c in cand if c["path"] == C.PATH_TWO_PASS and c["G"] == 1]
+        res["always_two_pass"] += ok(tp[0]) if tp else 0
+        nd = [c for c in cand if c["path"] != C.PATH_CLUSTER]
+        res["always_best_non_dsmem"] += ok(min(nd, key=lambda c: c["us"])) if nd else 0
+    return {k: v / max(1, n) for k, v in res.items()}, n
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--shapes", type=int, default=2000)
+    ap.add_argument("--reps", type=int, default=15)
+    ap.add_argument("--cap-gib", type=float, default=8.0)
+    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data"))
+    ap.add_argument("--calib", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
+                                                    "gb300.calib"))
+    args = ap.parse_args(argv)
+    from . import build as B
+    B.build()
+    C.init()
+    C.load_model(args.calib)
+    cap = int(args.cap_gib * 2 ** 30)
+    shapes = synth.sweep_shapes(args.shapes, cap_bytes=cap)
+    t0 = time.time()
+    rows = run_sweep(shapes, args.reps, cap, log=sys.stderr)
+    t_sweep = time.time() - t0
+    train, test = synth.split_by_shape(len(shapes))
+    train_set = set(train)
+    Xtr = np.stack([features_of(r) for r in rows if r["shape"] in train_set])
+    ytr = np.array([np.log2(r["us"]) for r in rows if r["shape"] in train_set], dtype=np.float32)
+    t1 = time.time()
+    curve = C.mlp_train(Xtr, ytr, epochs=args.epochs, batch=256, lr=2e-3, seed=0)
+    t_train = time.time() - t1
+    acc, n_test = evaluate(rows, test)
+    os.makedirs(args.out, exist_ok=True)
+    C.mlp_save(os.path.join(args.out, "gb300_mlp.txt"))
+    with open(os.path.join(args.out, "sweep_gb300.csv"), "w") as f:
+        f.write("shape,op,dtype,rows,cols,path,P,G,us\n")
+        for r in rows:
+            f.write(f"{r['shape']},{r['op']},{r['dtype']},{r['rows']},{r['cols']},{r['path']},{r['P']},{r['G']},"
+                    f"{r['us']:.3f}\n")
+    summary = {"shapes": len(shapes), "timings": len(rows), "train_shapes": len(train), "test_shapes": n_test,
+               "pick_rule": "pick within 5% of the measured best candidate", "pick_accuracy": acc,
+               "train_loss_first_last": [float(curve[0]), float(curve[-1])], "sweep_s": round(t_sweep, 1),
+               "train_s": round(t_train, 1), "reps": args.reps, "cap_gib": args.cap_gib}
+    with open(os.path.join(args.out, "sweep_gb300_summary.json"), "w") as f:
+        json.dump(summary, f, indent=1)
+    print(json.dumps(summary))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
