@@ -201,6 +201,39 @@ credit_status credit_run_ex(const credit_args *args, const credit_plan_t *plan,
  */
 credit_status credit_plan_check(const credit_args *args, const credit_plan_t *plan);
 
+/* ------------------------------------------------------------------ ragged batches
+ * Rows of uneven width and mixed op in one persistent cluster launch captured
+ * in a CUDA graph.  Each row: elements in_base[in_off .. in_off + cols) ->
+ * out_base[out_off ..) of the same dtype (offsets in elements; rows may be
+ * packed with any alignment); op is CREDIT_OP_SOFTMAX or CREDIT_OP_RMSNORM
+ * (gamma = 1, eps = 1e-6).  Narrow rows run one per CTA (one-CTA path), wide
+ * rows split over the cluster with the DSMEM exchange (cluster path), rows
+ * beyond the staging capacity stream twice within the cluster.  The project's
+ * addition; the paper runs one shape per launch.
+ */
+typedef struct {
+    int64_t in_off, out_off, cols;
+    int32_t op;
+    int32_t reserved;
+} credit_ragged_row;
+typedef struct credit_ragged credit_ragged;
+typedef struct {
+    int32_t cluster_size, threads, staging_bytes, clusters;
+    int64_t items, narrow_items, wide_items, huge_items;
+    float tuned_us;  /* autotuner's best time for the batch (0 if not tuned) */
+} credit_ragged_info_t;
+/* Build the work list, autotune (tune != 0: cluster size 4/8/16 x staging
+ * capacity x threads, each timed on this batch -- this launches the kernel
+ * and writes out_base), and capture the chosen launch in a CUDA graph.
+ * Allocates the device work list; in_base / out_base must stay valid while
+ * the handle is used.  BF16 and FP32 only (FP8 rows would need scales). */
+credit_status credit_ragged_create(const credit_ragged_row *host_rows, int64_t n, credit_dtype dtype,
+                                   const void *in_base, void *out_base, int32_t tune, credit_ragged **out);
+/* Replay the captured launch on `stream` (cudaGraphLaunch). */
+credit_status credit_ragged_run(credit_ragged *h, cudaStream_t stream);
+credit_status credit_ragged_info(const credit_ragged *h, credit_ragged_info_t *out);
+void credit_ragged_destroy(credit_ragged *h);
+
 /* ------------------------------------------------------------------ profiling
  * Primitive characterisation (Sec. III-A, Table II) on the current device.
  * Latencies in cycles per dependent load; rates in bytes per cycle per SM;

@@ -115,6 +115,17 @@ class MicrobenchT(ctypes.Structure):
         return d
 
 
+class RaggedRowT(ctypes.Structure):
+    _fields_ = [("in_off", ctypes.c_int64), ("out_off", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("op", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class RaggedInfoT(ctypes.Structure):
+    _fields_ = [("cluster_size", ctypes.c_int32), ("threads", ctypes.c_int32), ("staging_bytes", ctypes.c_int32),
+                ("clusters", ctypes.c_int32), ("items", ctypes.c_int64), ("narrow_items", ctypes.c_int64),
+                ("wide_items", ctypes.c_int64), ("huge_items", ctypes.c_int64), ("tuned_us", ctypes.c_float)]
+
+
 MODEL_IN_FIELDS = ["M", "N", "P", "T_B_us", "T_ctrl_us", "b_B", "b_reread", "b_keep", "b_in", "s_bytes", "q_sum",
                    "active_clusters", "f_mhz", "B_smem_read", "B_smem_store", "B_dsm_store", "B_peak_gbs"]
 MODEL_OUT_FIELDS = ["W", "B_eff_gbs", "T_save_us", "T_replay_us", "T_dsm_us", "T_deposit_us", "T_smem_w_us",
@@ -156,6 +167,14 @@ def _extra_prototypes(L):
     L.credit_mlp_save.argtypes = [ctypes.c_char_p]
     L.credit_mlp_load.restype = i32
     L.credit_mlp_load.argtypes = [ctypes.c_char_p]
+    L.credit_ragged_create.restype = i32
+    L.credit_ragged_create.argtypes = [ctypes.POINTER(RaggedRowT), i64, i32, vp, vp, i32, ctypes.POINTER(vp)]
+    L.credit_ragged_run.restype = i32
+    L.credit_ragged_run.argtypes = [vp, vp]
+    L.credit_ragged_info.restype = i32
+    L.credit_ragged_info.argtypes = [vp, ctypes.POINTER(RaggedInfoT)]
+    L.credit_ragged_destroy.restype = None
+    L.credit_ragged_destroy.argtypes = [vp]
     return L
 
 
@@ -328,6 +347,38 @@ def calibrate(path: str, max_bytes: int = 0) -> None:
 
 def load_model(path: str) -> None:
     _check(lib().credit_load_model(path.encode()), "credit_load_model")
+
+
+class Ragged:
+    """credit_ragged_* handle: rows (in_off, out_off, cols, op) of one dtype."""
+
+    def __init__(self, rows, dtype: int, in_base, out_base, tune: bool = True):
+        arr = (RaggedRowT * len(rows))()
+        for i, (io, oo, cols, op) in enumerate(rows):
+            arr[i].in_off, arr[i].out_off, arr[i].cols, arr[i].op = int(io), int(oo), int(cols), int(op)
+        h = ctypes.c_void_p()
+        _check(lib().credit_ragged_create(arr, len(rows), dtype, _ptr(in_base), _ptr(out_base), int(tune),
+                                          ctypes.byref(h)), "credit_ragged_create")
+        self.h = h
+
+    def run(self, stream=None):
+        _check(lib().credit_ragged_run(self.h, _stream(stream)), "credit_ragged_run")
+
+    def info(self) -> dict:
+        i = RaggedInfoT()
+        _check(lib().credit_ragged_info(self.h, ctypes.byref(i)), "credit_ragged_info")
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def close(self):
+        if self.h:
+            lib().credit_ragged_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 MLP_FEATURES = 16

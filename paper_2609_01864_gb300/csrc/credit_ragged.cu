@@ -1,0 +1,525 @@
+// credit_ragged.cu -- ragged batches: rows of uneven width and mixed op
+// (softmax / RMSNorm) in one persistent cluster launch, captured in a CUDA
+// graph, with the launch shape chosen by timing the batch (autotuner).
+//
+// Work items, built on the host from the row list (widest first, dealt
+// round-robin to the persistent clusters):
+//   narrow  up to P rows, one per CTA, each staged whole in its CTA's shared
+//           memory (no exchange; the one-CTA path)
+//   wide    one row split over the P CTAs of the cluster (Eq. 2), each slice
+//           staged once, partials exchanged over DSMEM (Eq. 5), output
+//           written from shared memory (the cluster path)
+//   huge    a row whose slices exceed the staging capacity: each CTA sweeps
+//           its part in HBM, the partials are exchanged, then the part is
+//           read again and written (the two-pass schedule inside a cluster)
+// The op is a per-row field; the element type is a template parameter.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/credit.h"
+#include "credit_host.h"
+#include "credit_rows.cuh"
+
+namespace credit {
+extern std::atomic<long long> g_launch_count;
+}
+
+using namespace credit;
+
+namespace {
+
+enum : int { ITEM_NARROW = 0, ITEM_WIDE = 1, ITEM_HUGE = 2 };
+
+struct RRow {
+    long long in_off, out_off, cols;  // elements
+    int op;
+    int pad;
+};
+struct RItem {
+    int kind;
+    int count;      // rows in a narrow item
+    long long row;  // first row (index into the row table)
+};
+struct RaggedArgs {
+    const unsigned char *in;
+    unsigned char *out;
+    const RRow *rows;
+    const RItem *items;
+    long long n_items;
+    int cap;  // staging capacity per CTA (bytes, multiple of the chunk size)
+    float eps;
+    unsigned *err;
+};
+
+constexpr int kRCtrl = 1024;  // [0,128) mbarriers, [128,640) slots [2][16][4], [640,1024) reduction scratch
+constexpr int kRChunk = 16384;
+
+template <int TIN>
+__device__ __forceinline__ float2 stats_from_smem(int op, const unsigned char *buf, long long ng, const RowSlice &s,
+                                                  bool own_head, bool own_tail, const unsigned char *row,
+                                                  uint64_t *mbar, uint32_t &phase_bits, int nch, float *red,
+                                                  unsigned *err) {
+    constexpr int V = Fmt<TIN>::V, isz = Fmt<TIN>::size;
+    const int tid = threadIdx.x, T = blockDim.x;
+    Stream<OP_SOFTMAX> sm;
+    Stream<OP_RMS> rs;
+    for (int k = 0; k < nch; ++k) {
+        mbar_wait_bounded(&mbar[k], (phase_bits >> k) & 1u, err);
+        const long long gb = static_cast<long long>(k) * (kRChunk / 16);
+        const long long ge = min(ng, gb + kRChunk / 16);
+        for (long long g = gb + tid; g < ge; g += T) {
+            float f[V];
+            decode_group<TIN>(*reinterpret_cast<const uint4 *>(buf + g * 16), f, 1.0f);
+            if (op == OP_SOFTMAX) sm.add(f);
+            else rs.add(f);
+        }
+    }
+    phase_bits ^= (nch >= 32 ? 0xFFFFFFFFu : ((1u << nch) - 1u));
+    if (own_head && tid == 0)
+        for (long long i = 0; i < s.h0; ++i) {
+            const float x = decode_one<TIN>(row + i * isz, 1.0f);
+            if (op == OP_SOFTMAX) sm.add1(x);
+            else rs.add1(x);
+        }
+    if (own_tail && tid == T - 1)
+        for (long long i = 0; i < s.t0; ++i) {
+            const float x = decode_one<TIN>(row + (s.h0 + s.G * V + i) * isz, 1.0f);
+            if (op == OP_SOFTMAX) sm.add1(x);
+            else rs.add1(x);
+        }
+    if (op == OP_SOFTMAX) return block_reduce_stream<OP_SOFTMAX>(sm, red, 0);
+    return block_reduce_stream<OP_RMS>(rs, red, 0);
+}
+
+// Exchange (P > 1) with the cluster: every thread returns the combined stats.
+template <int TIN>
+__device__ __forceinline__ Stats exchange_combine(int op, float2 part, float *slots, uint64_t *xbar, int &nx, int P,
+                                                  int c, const RowSlice &s, long long N, float eps, unsigned *err) {
+    constexpr int V = Fmt<TIN>::V;
+    const int par = nx & 1;
+    const uint32_t phase = static_cast<uint32_t>((nx >> 1) & 1);
+    ++nx;
+    Stats st;
+    if (P > 1) {
+        const int tid = threadIdx.x;
+        float *mine = slots + (par * 16 + c) * 4;
+        if (tid < P) {
+            if (tid == c) {
+                mine[0] = part.x;
+                mine[1] = part.y;
+            } else {
+                fence_acq_rel_cluster();
+                st_async_v2f32(mapa_shared(smem_addr(mine), tid), part.x, part.y,
+                               mapa_shared(smem_addr(&xbar[par]), tid));
+            }
+        }
+        if (tid == 0) mbar_arrive_expect_tx(&xbar[par], static_cast<uint32_t>((P - 1) * 8));
+        __syncthreads();
+        mbar_wait_bounded(&xbar[par], phase, err);
+        const float *sl = slots + par * 16 * 4;
+        st = op == OP_SOFTMAX ? combine_partials<OP_SOFTMAX>(sl, 4, P, s, V, N, eps)
+                              : combine_partials<OP_RMS>(sl, 4, P, s, V, N, eps);
+    } else {
+        const float p1[2] = {part.x, part.y};
+        st = op == OP_SOFTMAX ? combine_partials<OP_SOFTMAX>(p1, 2, 1, s, V, N, eps)
+                              : combine_partials<OP_RMS>(p1, 2, 1, s, V, N, eps);
+    }
+    return st;
+}
+
+template <int TIN>
+__device__ __forceinline__ float h_of(int op, float x, const Stats &st, float inv) {
+    return op == OP_SOFTMAX ? exp_fast(x - st.a) * inv : x * st.a;
+}
+
+template <int TIN>
+__global__ void __launch_bounds__(512, 1) k_ragged(const RaggedArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);       // [0..14) chunks, [14..16) exchange
+    uint64_t *xbar = mbar + 14;
+    float *slots = reinterpret_cast<float *>(smem + 128);
+    float *red = reinterpret_cast<float *>(smem + 640);
+    unsigned char *buf = smem + kRCtrl;
+    constexpr int isz = Fmt<TIN>::size, V = Fmt<TIN>::V;
+    const int P = static_cast<int>(cluster_nctarank());
+    const int c = P > 1 ? static_cast<int>(cluster_ctarank()) : 0;
+    const long long ncl = gridDim.x / P, cl = blockIdx.x / P;
+    const int tid = threadIdx.x, T = blockDim.x;
+    if (tid == 0) {
+        for (int k = 0; k < 16; ++k) mbar_init(&mbar[k], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (P > 1) {
+        cluster_arrive_release();
+        cluster_wait_acquire();  // peers' exchange barriers are initialised
+    }
+    uint32_t phase_bits = 0;
+    int nx = 0;
+    for (long long it = cl; it < a.n_items; it += ncl) {
+        const RItem item = a.items[it];
+        bool active = true;
+        long long ri = item.row;
+        if (item.kind == ITEM_NARROW) {
+            active = c < item.count;
+            ri = item.row + c;
+        }
+        const RRow rw = a.rows[active ? ri : item.row];
+        const int op = rw.op;
+        const long long N = rw.cols;
+        const unsigned char *row = a.in + rw.in_off * isz;
+        unsigned char *orow = a.out + rw.out_off * isz;
+        const int Pslice = item.kind == ITEM_NARROW ? 1 : P;
+        const int cslice = item.kind == ITEM_NARROW ? 0 : c;
+        const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(row), N, isz, Pslice, cslice);
+        const long long ng = s.g_hi - s.g_lo;
+        const bool own_head = cslice == 0, own_tail = cslice == Pslice - 1;
+        const long long i_base = s.h0 + s.g_lo * V;
+        const bool out_vec = ((reinterpret_cast<uintptr_t>(orow) + s.h0 * isz) & 15u) == 0;
+        if (item.kind != ITEM_HUGE) {
+            // ---- staged: TMA the slice into shared memory (chunks), reduce, [exchange], write
+            const uint32_t body = static_cast<uint32_t>(ng * 16);
+            const int nch = active ? static_cast<int>((body + kRChunk - 1) / kRChunk) : 0;
+            __syncthreads();  // the previous item's reads of buf are done
+            if (tid == 0)
+                for (int k = 0; k < nch; ++k) {
+                    const uint32_t off = static_cast<uint32_t>(k) * kRChunk;
+                    const uint32_t bytes = min(static_cast<uint32_t>(kRChunk), body - off);
+                    mbar_arrive_expect_tx(&mbar[k], bytes);
+                    bulk_g2s(buf + off, row + s.h0 * isz + s.g_lo * 16 + off, bytes, &mbar[k]);
+                }
+            float2 part = make_float2(op == OP_SOFTMAX ? -INFINITY : 0.0f, 0.0f);
+            if (active)
+                part = stats_from_smem<TIN>(op, buf, ng, s, own_head, own_tail, row, mbar, phase_bits, nch, red,
+                                            a.err);
+            Stats st;
+            if (item.kind == ITEM_WIDE) {
+                st = exchange_combine<TIN>(op, part, slots, xbar, nx, P, c, s, N, a.eps, a.err);
+            } else {
+                const float p1[2] = {part.x, part.y};
+                st = op == OP_SOFTMAX ? combine_partials<OP_SOFTMAX>(p1, 2, 1, s, V, N, a.eps)
+                                      : combine_partials<OP_RMS>(p1, 2, 1, s, V, N, a.eps);
+            }
+            if (!active) continue;
+            const float inv = op == OP_SOFTMAX ? 1.0f / st.b : 0.0f;
+            for (long long g = tid; g < ng; g += T) {
+                float f[V], y[V];
+                decode_group<TIN>(*reinterpret_cast<const uint4 *>(buf + g * 16), f, 1.0f);
+#pragma unroll
+                for (int q = 0; q < V; ++q) y[q] = h_of<TIN>(op, f[q], st, inv);
+                store_group<TIN, V>(orow + (i_base + g * V) * isz, y, out_vec);
+            }
+            if (own_head && tid == 0)
+                for (long long i = 0; i < s.h0; ++i)
+                    store_one<TIN>(orow + i * isz, h_of<TIN>(op, decode_one<TIN>(row + i * isz, 1.0f), st, inv));
+            if (own_tail && tid == T - 1)
+                for (long long i = 0; i < s.t0; ++i) {
+                    const long long e = s.h0 + s.G * V + i;
+                    store_one<TIN>(orow + e * isz, h_of<TIN>(op, decode_one<TIN>(row + e * isz, 1.0f), st, inv));
+                }
+        } else {
+            // ---- streaming: sweep HBM, exchange, reread and write
+            Stream<OP_SOFTMAX> sm;
+            Stream<OP_RMS> rs;
+            sweep_global<TIN>(row, s, P, c, 1.0f, [&](long long, const float(&f)[V]) {
+                if (op == OP_SOFTMAX) sm.add(f);
+                else rs.add(f);
+            });
+            sweep_edges<TIN>(row, s, P, c, 1.0f, [&](long long, float x) {
+                if (op == OP_SOFTMAX) sm.add1(x);
+                else rs.add1(x);
+            });
+            const float2 part = op == OP_SOFTMAX ? block_reduce_stream<OP_SOFTMAX>(sm, red, 0)
+                                                 : block_reduce_stream<OP_RMS>(rs, red, 0);
+            const Stats st = exchange_combine<TIN>(op, part, slots, xbar, nx, P, c, s, N, a.eps, a.err);
+            const float inv = op == OP_SOFTMAX ? 1.0f / st.b : 0.0f;
+            sweep_global<TIN>(row, s, P, c, 1.0f, [&](long long i0, const float(&f)[V]) {
+                float y[V];
+#pragma unroll
+                for (int q = 0; q < V; ++q) y[q] = h_of<TIN>(op, f[q], st, inv);
+                store_group<TIN, V>(orow + i0 * isz, y, out_vec);
+            });
+            sweep_edges<TIN>(row, s, P, c, 1.0f, [&](long long i, float x) {
+                store_one<TIN>(orow + i * isz, h_of<TIN>(op, x, st, inv));
+            });
+        }
+    }
+    if (P > 1) {
+        cluster_arrive_release();  // nobody exits while a peer may still push into it
+        cluster_wait_acquire();
+    }
+}
+
+const void *ragged_kernel(int dt) {
+    switch (dt) {
+    case DT_F32: return reinterpret_cast<const void *>(&k_ragged<DT_F32>);
+    case DT_BF16: return reinterpret_cast<const void *>(&k_ragged<DT_BF16>);
+    default: return reinterpret_cast<const void *>(&k_ragged<DT_E4M3>);
+    }
+}
+
+}  // namespace
+
+struct credit_ragged {
+    int device = 0;
+    int dtype = 0;
+    long long n_rows = 0;
+    std::vector<RRow> rows;  // host copy, original order
+    const unsigned char *in = nullptr;
+    unsigned char *out = nullptr;
+    // chosen launch
+    int P = 0, threads = 0, cap = 0, clusters = 0;
+    long long n_items = 0, n_narrow = 0, n_wide = 0, n_huge = 0;
+    RRow *d_rows = nullptr;
+    RItem *d_items = nullptr;
+    unsigned *d_err = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    float tuned_us = 0.0f;
+};
+
+namespace {
+
+// Items for launch shape (P, cap): rows sorted widest first.
+void build_items(const std::vector<RRow> &rows, int isz, int P, int cap, std::vector<RItem> &items,
+                 std::vector<RRow> &sorted, long long &nn, long long &nw, long long &nh) {
+    sorted = rows;
+    std::stable_sort(sorted.begin(), sorted.end(), [](const RRow &x, const RRow &y) { return x.cols > y.cols; });
+    items.clear();
+    nn = nw = nh = 0;
+    const long long per_cta = cap;  // bytes
+    size_t i = 0;
+    while (i < sorted.size()) {
+        const long long bytes = sorted[i].cols * isz;
+        if (bytes + 32 <= per_cta && (P == 1 || bytes <= per_cta / 2)) {
+            // narrow: up to P consecutive rows, one per CTA
+            RItem it{ITEM_NARROW, 0, static_cast<long long>(i)};
+            while (i < sorted.size() && it.count < P && sorted[i].cols * isz + 32 <= per_cta) {
+                ++it.count;
+                ++i;
+            }
+            items.push_back(it);
+            ++nn;
+        } else {
+            const long long slice = ((bytes / 16 + P - 1) / P) * 16;
+            RItem it{slice + 32 <= per_cta ? ITEM_WIDE : ITEM_HUGE, 1, static_cast<long long>(i)};
+            items.push_back(it);
+            ++(it.kind == ITEM_WIDE ? nw : nh);
+            ++i;
+        }
+    }
+}
+
+credit_status upload_and_launch_config(credit_ragged *h, int P, int threads, int cap, bool capture,
+                                       float *us_out) {
+    const int isz = dtype_size(h->dtype);
+    const DeviceInfo *di = device_info(h->device);
+    std::vector<RItem> items;
+    std::vector<RRow> sorted;
+    long long nn, nw, nh;
+    build_items(h->rows, isz, P, cap, items, sorted, nn, nw, nh);
+    const long long smem = kRCtrl + cap;
+    if (smem > di->smem_optin) return CREDIT_ERR_UNSUPPORTED;
+    const void *fn = ragged_kernel(h->dtype);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(di->smem_optin));
+    cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    int maxc = 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(P * 64);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&maxc, fn, &cfg) != cudaSuccess || maxc <= 0) {
+        (void)cudaGetLastError();
+        return CREDIT_ERR_UNSUPPORTED;
+    }
+    const long long ncl = std::min<long long>(maxc, static_cast<long long>(items.size()));
+    if (cudaMemcpy(h->d_rows, sorted.data(), sorted.size() * sizeof(RRow), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_items, items.data(), items.size() * sizeof(RItem), cudaMemcpyHostToDevice) != cudaSuccess)
+        return CREDIT_ERR_CUDA;
+    RaggedArgs ra;
+    ra.in = h->in;
+    ra.out = h->out;
+    ra.rows = h->d_rows;
+    ra.items = h->d_items;
+    ra.n_items = static_cast<long long>(items.size());
+    ra.cap = cap;
+    ra.eps = 1e-6f;
+    ra.err = h->d_err;
+    void *args[] = {&ra};
+    cfg.gridDim = dim3(static_cast<unsigned>(P * std::max<long long>(ncl, 1)));
+    cfg.stream = h->cap_stream;
+    if (capture) {
+        if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return CREDIT_ERR_CUDA;
+        cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) return CREDIT_ERR_CUDA;
+        if (h->exec) cudaGraphExecDestroy(h->exec);
+        if (h->graph) cudaGraphDestroy(h->graph);
+        h->graph = g;
+        if (cudaGraphInstantiate(&h->exec, g, 0) != cudaSuccess) return CREDIT_ERR_CUDA;
+        h->P = P;
+        h->threads = threads;
+        h->cap = cap;
+        h->clusters = static_cast<int>(ncl);
+        h->n_items = static_cast<long long>(items.size());
+        h->n_narrow = nn;
+        h->n_wide = nw;
+        h->n_huge = nh;
+        return CREDIT_OK;
+    }
+    // timing run (median of 3 after a warm-up)
+    cudaEvent_t a0, a1;
+    cudaEventCreate(&a0);
+    cudaEventCreate(&a1);
+    std::vector<float> t;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+        cudaEventRecord(a0, h->cap_stream);
+        e = cudaLaunchKernelExC(&cfg, fn, args);
+        cudaEventRecord(a1, h->cap_stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(a1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a0, a1);
+        if (k) t.push_back(ms * 1e3f);
+    }
+    cudaEventDestroy(a0);
+    cudaEventDestroy(a1);
+    if (e != cudaSuccess) return CREDIT_ERR_CUDA;
+    std::sort(t.begin(), t.end());
+    *us_out = t[t.size() / 2];
+    return CREDIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+credit_status credit_ragged_create(const credit_ragged_row *host_rows, int64_t n, credit_dtype dtype,
+                                   const void *in_base, void *out_base, int32_t tune, credit_ragged **out) {
+    if (!host_rows || n <= 0 || !in_base || !out_base || !out || dtype < 0 || dtype > 2) return CREDIT_ERR_INVALID_ARG;
+    const int isz = dtype_size(dtype);
+    if (reinterpret_cast<uintptr_t>(in_base) % isz || reinterpret_cast<uintptr_t>(out_base) % isz)
+        return CREDIT_ERR_INVALID_ARG;
+    if (dtype == CREDIT_FP8_E4M3) return CREDIT_ERR_UNSUPPORTED;  // ragged FP8 would need per-row scales
+    int dev = 0;
+    credit_status st = ensure_init(&dev, nullptr);
+    if (st != CREDIT_OK) return st;
+    credit_ragged *h = new (std::nothrow) credit_ragged();
+    if (!h) return CREDIT_ERR_INVALID_ARG;
+    h->device = dev;
+    h->dtype = dtype;
+    h->n_rows = n;
+    h->in = static_cast<const unsigned char *>(in_base);
+    h->out = static_cast<unsigned char *>(out_base);
+    h->rows.resize(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const credit_ragged_row &r = host_rows[i];
+        if (r.cols <= 0 || r.in_off < 0 || r.out_off < 0 || (r.op != CREDIT_OP_SOFTMAX && r.op != CREDIT_OP_RMSNORM)) {
+            delete h;
+            return CREDIT_ERR_INVALID_ARG;
+        }
+        h->rows[i] = RRow{r.in_off, r.out_off, r.cols, r.op, 0};
+    }
+    const bool ok = cudaMalloc(&h->d_rows, n * sizeof(RRow)) == cudaSuccess &&
+                    cudaMalloc(&h->d_items, n * sizeof(RItem)) == cudaSuccess &&
+                    cudaMalloc(&h->d_err, 16) == cudaSuccess &&
+                    cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) {
+        credit_ragged_destroy(h);
+        return CREDIT_ERR_CUDA;
+    }
+    cudaMemset(h->d_err, 0, 16);
+    // autotune: cluster size x staging capacity x threads, timed on this batch
+    const int Ps[3] = {4, 8, 16};
+    const int caps[2] = {6 * kRChunk, 13 * kRChunk};
+    const int thr[2] = {256, 512};
+    float best = 1e30f;
+    int bP = 16, bcap = caps[1], bthr = 512;
+    if (!tune) {  // fixed launch shape (CREDIT_RAGGED_P / _CHUNKS / _THREADS override the defaults)
+        const char *eP = std::getenv("CREDIT_RAGGED_P"), *eC = std::getenv("CREDIT_RAGGED_CHUNKS");
+        const char *eT = std::getenv("CREDIT_RAGGED_THREADS");
+        if (eP) bP = std::atoi(eP);
+        if (eC) bcap = std::atoi(eC) * kRChunk;
+        if (eT) bthr = std::atoi(eT);
+        if (bP < 1 || bP > 16 || bcap < kRChunk || bcap > 13 * kRChunk || bthr < 64 || bthr > 512 || bthr % 32) {
+            credit_ragged_destroy(h);
+            return CREDIT_ERR_INVALID_ARG;
+        }
+    } else {
+        for (int P : Ps)
+            for (int cap : caps)
+                for (int t : thr) {
+                    float us = 0;
+                    if (upload_and_launch_config(h, P, t, cap, false, &us) == CREDIT_OK && us < best) {
+                        best = us;
+                        bP = P;
+                        bcap = cap;
+                        bthr = t;
+                    }
+                }
+        if (best >= 1e30f) {
+            credit_ragged_destroy(h);
+            return CREDIT_ERR_UNSUPPORTED;
+        }
+    }
+    h->tuned_us = tune ? best : 0.0f;
+    st = upload_and_launch_config(h, bP, bthr, bcap, true, nullptr);
+    if (st != CREDIT_OK) {
+        credit_ragged_destroy(h);
+        return st;
+    }
+    cudaStreamSynchronize(h->cap_stream);
+    *out = h;
+    return CREDIT_OK;
+}
+
+credit_status credit_ragged_run(credit_ragged *h, cudaStream_t stream) {
+    if (!h || !h->exec) return CREDIT_ERR_INVALID_ARG;
+    if (cudaGraphLaunch(h->exec, stream) != cudaSuccess) return CREDIT_ERR_CUDA;
+    g_launch_count.fetch_add(1);
+    return CREDIT_OK;
+}
+
+credit_status credit_ragged_info(const credit_ragged *h, credit_ragged_info_t *out) {
+    if (!h || !out) return CREDIT_ERR_INVALID_ARG;
+    out->cluster_size = h->P;
+    out->threads = h->threads;
+    out->staging_bytes = h->cap;
+    out->clusters = h->clusters;
+    out->items = h->n_items;
+    out->narrow_items = h->n_narrow;
+    out->wide_items = h->n_wide;
+    out->huge_items = h->n_huge;
+    out->tuned_us = h->tuned_us;
+    return CREDIT_OK;
+}
+
+void credit_ragged_destroy(credit_ragged *h) {
+    if (!h) return;
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    cudaFree(h->d_rows);
+    cudaFree(h->d_items);
+    cudaFree(h->d_err);
+    delete h;
+}
+
+}  // extern "C"
