@@ -216,8 +216,21 @@ void mlp_features(int op, int tin, int tout, long long rows, long long cols, int
     f[15] = static_cast<float>(ob);
 }
 
+static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin,
+                              int tout, bool allow_cluster, credit_plan_t *p);
+
 bool learned_plan(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin, int tout,
                   credit_plan_t *p) {
+    return learned_plan_impl(di, device, op, rows, cols, tin, tout, true, p);
+}
+
+bool learned_plan_no_cluster(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin,
+                             int tout, credit_plan_t *p) {
+    return learned_plan_impl(di, device, op, rows, cols, tin, tout, false, p);
+}
+
+static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin,
+                              int tout, bool allow_cluster, credit_plan_t *p) {
     Model mdl;
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -244,6 +257,7 @@ bool learned_plan(const DeviceInfo &di, int device, int op, long long rows, long
     const int isz = dtype_size(tin);
     for (int P : {1, 2, 4, 8, 16}) {
         if (op == 1 && P == 1) continue;
+        if (P > 1 && !allow_cluster) continue;
         RingCfg rc;
         if (!ring_config(di, cols, isz, P, 0, 0, 0, 0, 0, &rc)) continue;
         if (ring_max_clusters(device, op, tin, tout, P, rc.threads, rc.smem) <= 0) continue;

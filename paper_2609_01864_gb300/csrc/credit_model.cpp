@@ -288,11 +288,22 @@ bool analytic_plan(const DeviceInfo &di, int device, int op, long long rows, lon
     return true;
 }
 
+// Planner selection: CREDIT_MODEL=analytic | ablation | learned; unset means
+// the learned model when its weights are loaded, else the analytic model.
+// The analytic model also judges the learned pick: a cluster plan for an op
+// whose structural screen rejects the cluster path (no reread to save:
+// scalar-output reductions, Sec. III-D) is replaced by the learned model's
+// best non-cluster candidate.
 bool model_plan(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin, int tout,
                 credit_plan_t *p) {
     const char *m = std::getenv("CREDIT_MODEL");
+    const bool analytic = m && !std::strcmp(m, "analytic");
     const int ablation = (m && !std::strcmp(m, "ablation")) ? 1 : 0;
-    if (m && !std::strcmp(m, "learned") && learned_plan(di, device, op, rows, cols, tin, tout, p)) return true;
+    if (!analytic && !ablation && learned_plan(di, device, op, rows, cols, tin, tout, p)) {
+        if (p->path == CREDIT_PATH_CLUSTER && static_bytes(op, tin, tout, false).b_reread == 0.0)
+            learned_plan_no_cluster(di, device, op, rows, cols, tin, tout, p);
+        return true;
+    }
     return analytic_plan(di, device, op, rows, cols, tin, tout, ablation, p, nullptr);
 }
 

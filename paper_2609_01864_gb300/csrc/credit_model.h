@@ -19,6 +19,9 @@ bool analytic_plan(const DeviceInfo &di, int device, int op, long long rows, lon
 // Learned model: argmin of the predicted latency over the legal candidates.
 bool learned_plan(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin, int tout,
                   credit_plan_t *p);
+// The same, restricted to the non-cluster candidates.
+bool learned_plan_no_cluster(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin,
+                             int tout, credit_plan_t *p);
 
 int two_pass_split(int sm_count, long long rows, long long cols, int isz);
 

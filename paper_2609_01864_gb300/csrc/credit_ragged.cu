@@ -58,7 +58,7 @@ struct RaggedArgs {
     unsigned *err;
 };
 
-constexpr int kRCtrl = 1024;  // [0,128) mbarriers, [128,640) slots [2][16][4], [640,1024) reduction scratch
+constexpr int kRCtrl = 1280;  // [0,128) mbarriers, [128,640) slots [2][16][4], [640,1152) reduction scratch (128 floats)
 constexpr int kRChunk = 16384;
 
 template <int TIN>

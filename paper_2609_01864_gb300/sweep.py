@@ -144,11 +144,8 @@ def evaluate(rows, test_shapes):
         learned = min(cand, key=lambda c: c["pred_log2us"])
         res["learned"] += ok(learned)
         r0 = cand[0]
-        for name, env in (("analytic", None), ("ablation", "ablation")):
-            if env:
-                os.environ["CREDIT_MODEL"] = env
-            else:
-                os.environ.pop("CREDIT_MODEL", None)
+        for name, env in (("analytic", "analytic"), ("ablation", "ablation")):
+            os.environ["CREDIT_MODEL"] = env
             p = C.plan(r0["op"], r0["rows"], r0["cols"], r0["dtype"])
             os.environ.pop("CREDIT_MODEL", None)
             match = [c for c in cand if c["path"] == p.path and (c["P"] == p.cluster_size if p.path != C.PATH_TWO_PASS

@@ -35,7 +35,8 @@ def test_control_kernel_times_and_excess():
     assert C.device_error() == C.OK
 
 
-def test_calibrate_load_and_plan(tmp_path):
+def test_calibrate_load_and_plan(tmp_path, monkeypatch):
+    monkeypatch.setenv("CREDIT_MODEL", "analytic")
     path = str(tmp_path / "gb300.calib")
     C.calibrate(path, max_bytes=1 << 28)
     text = open(path).read()
@@ -50,3 +51,16 @@ def test_calibrate_load_and_plan(tmp_path):
     C.run_ex(C.SOFTMAX, x, y)                           # the planner's plan runs
     torch.cuda.synchronize()
     assert torch.allclose(y.sum(dim=1), torch.ones(256, device="cuda"), atol=1e-4)
+
+
+def test_committed_calibration_and_learned_planner(monkeypatch):
+    data = os.path.join(os.path.dirname(C.__file__), "data", "gb300.calib")
+    monkeypatch.delenv("CREDIT_MODEL", raising=False)
+    C.load_model(data)                                    # loads the MLP weights it names
+    p = C.plan(C.LAYERNORM, 4096, 65536, C.F32)
+    assert p.source == 1 and p.predicted_us > 0           # learned model by default
+    for cols in (16384, 262144, 1 << 20):
+        q = C.plan(C.LOGSUMEXP, 4096, cols, C.F32)
+        assert q.path != C.PATH_CLUSTER                   # the analytic screen's veto (no reread to save)
+    monkeypatch.setenv("CREDIT_MODEL", "analytic")
+    assert C.plan(C.LAYERNORM, 4096, 65536, C.F32).source == 0
