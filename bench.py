@@ -162,7 +162,7 @@ def candidates(C, op, x, y, g, b):
         p = C.make_plan(C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P)
         if C.plan_check(op, x, y, p, gamma=g, beta=b) == C.OK:
             out.append((f"{'one_cta' if P == 1 else 'cluster'}{'' if P == 1 else P}", p))
-    for G in (1, 4):
+    for G in (1, 2, 4, 8):
         p = C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)
         out.append((f"two_pass_g{G}", p))
     return out

@@ -7,8 +7,8 @@
 // targets; features and targets are standardised with the training set's
 // mean / standard deviation, kept with the weights.
 // Planning: the argmin of the predicted latency over the legal candidates
-// (one-CTA, cluster P in {2, 4, 8, 16}, two-pass with G = 1 and the split
-// factor); single planning queries run the same network on the host, batched
+// (one-CTA, cluster P in {2, 4, 8, 16}, two-pass with G in {1, 2, 4, 8} and
+// the split factor); single planning queries run the same network on the host, batched
 // evaluation runs the inference kernel.
 #include <cuda_runtime.h>
 
@@ -263,9 +263,12 @@ static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long lon
         if (ring_max_clusters(device, op, tin, tout, P, rc.threads, rc.smem) <= 0) continue;
         consider(P == 1 ? CREDIT_PATH_ONE_CTA : CREDIT_PATH_CLUSTER, P, P, rc.smem);
     }
-    consider(CREDIT_PATH_TWO_PASS, 1, 1, 0);
-    const int G = two_pass_split(di.sm_count, rows, cols, isz);
-    if (G > 1) consider(CREDIT_PATH_TWO_PASS, 1, G, 0);
+    // two-pass: G in {1, 2, 4, 8} with >= 1024 16-byte groups per CTA, and the split rule's G
+    const long long groups = cols * isz / 16;
+    for (int G : {1, 2, 4, 8})
+        if (G == 1 || groups / G >= 1024) consider(CREDIT_PATH_TWO_PASS, 1, G, 0);
+    const int Gs = two_pass_split(di.sm_count, rows, cols, isz);
+    if (Gs > 1 && Gs != 2 && Gs != 4 && Gs != 8) consider(CREDIT_PATH_TWO_PASS, 1, Gs, 0);
     *p = bp;
     return true;
 }

@@ -230,8 +230,15 @@ template <> struct Stream<OP_SOFTMAX> {  // online (max, sum exp)
 };
 template <> struct Stream<OP_LSE> : Stream<OP_SOFTMAX> {};
 
-template <> struct Stream<OP_LN> {  // Welford / Chan, merged per 16-byte group
-    float n = 0.0f, mu = 0.0f, m2 = 0.0f;
+// LayerNorm statistics in one sweep: each thread accumulates sums about a
+// shift K (its first element), s1 = sum (x - K), s2 = sum (x - K)^2, and
+// converts them once to (n, mean, M2) = (n, K + s1/n, s2 - s1^2/n) before the
+// CTA merge (Chan's formula).  The shift is a sample of the thread's own
+// data, so the cancellation in s2 - s1^2/n stays small.
+template <> struct Stream<OP_LN> {
+    float n = 0.0f, mu = 0.0f, m2 = 0.0f;  // merged form (after finish())
+    float K = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    bool has = false;
     __device__ __forceinline__ void merge3(float nb, float mb, float m2b) {
         if (nb == 0.0f) return;
         const float nn = n + nb;
@@ -241,19 +248,30 @@ template <> struct Stream<OP_LN> {  // Welford / Chan, merged per 16-byte group
         n = nn;
     }
     template <int V> __device__ __forceinline__ void add(const float (&f)[V]) {
-        float sum = 0.0f;
-#pragma unroll
-        for (int j = 0; j < V; ++j) sum += f[j];
-        const float mb = sum * (1.0f / V);
-        float q = 0.0f;
+        if (!has) {
+            K = f[0];
+            has = true;
+        }
 #pragma unroll
         for (int j = 0; j < V; ++j) {
-            const float d = f[j] - mb;
-            q = fmaf(d, d, q);
+            const float d = f[j] - K;
+            s1 += d;
+            s2 = fmaf(d, d, s2);
         }
-        merge3(static_cast<float>(V), mb, q);
+        n += static_cast<float>(V);
     }
-    __device__ __forceinline__ void add1(float x) { merge3(1.0f, x, 0.0f); }
+    __device__ __forceinline__ void add1(float x) {
+        float f[1] = {x};
+        add<1>(f);
+    }
+    // (n, K, s1, s2) -> (n, mean, M2); call once before merging
+    __device__ __forceinline__ void finish() {
+        if (n > 0.0f) {
+            const float q = s1 / n;
+            mu = K + q;
+            m2 = fmaxf(s2 - s1 * q, 0.0f);
+        }
+    }
 };
 
 template <> struct Stream<OP_RMS> {
@@ -361,6 +379,7 @@ __device__ __forceinline__ float2 block_reduce_stream(Stream<OP> st, float *red,
         if (bar_id == 0) return make_float2(block_allreduce<false>(st.ss, red), 0.0f);
         return make_float2(cons_allreduce<false>(st.ss, red, Tc), 0.0f);
     } else if constexpr (OP == OP_LN) {
+        st.finish();
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const float nb = __shfl_xor_sync(0xffffffffu, st.n, o);
@@ -677,41 +696,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
             // ---------- stage 1 (sweeps wait for each chunk as it lands)
             float part0, part1 = 0.0f;
             const long long n_c = slice_count(g.s, V, P, c);
-            if constexpr (OP == OP_LN) {
-                // exact two sweeps: the slice mean, then squared deviations
-                float sum = 0.0f;
-                for (int k = 0; k < g.nch; ++k) {
-                    const long long jk = j + k;
-                    mbar_wait_bounded(&full[jk % K], static_cast<uint32_t>((jk / K) & 1), a.err);
-                    visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), tid, Tr, g.in_sc,
-                                     [&](int, const float(&f)[V]) {
-#pragma unroll
-                                         for (int q = 0; q < V; ++q) sum += f[q];
-                                     });
-                }
-                for (int e = 0; e < 2; ++e)
-                    for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) sum += edge_x(g, e, k);
-                if (tid == 0) trace_stamp(a, rr, 1);
-                sum = cons_allreduce<false>(sum, red, Tr);
-                const float mean = n_c > 0 ? sum / static_cast<float>(n_c) : 0.0f;
-                float m2 = 0.0f;
-                for (int k = 0; k < g.nch; ++k)
-                    visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), tid, Tr, g.in_sc,
-                                     [&](int, const float(&f)[V]) {
-#pragma unroll
-                                         for (int q = 0; q < V; ++q) {
-                                             const float d = f[q] - mean;
-                                             m2 = fmaf(d, d, m2);
-                                         }
-                                     });
-                for (int e = 0; e < 2; ++e)
-                    for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) {
-                        const float d = edge_x(g, e, k) - mean;
-                        m2 = fmaf(d, d, m2);
-                    }
-                part0 = mean;
-                part1 = cons_allreduce<false>(m2, red, Tr);
-            } else {
+            {
                 Stream<OP> acc;
                 for (int k = 0; k < g.nch; ++k) {
                     const long long jk = j + k;
@@ -909,15 +894,16 @@ __device__ __forceinline__ void sweep_global(const unsigned char *in_row, const 
     constexpr int V = Fmt<TIN>::V, isz = Fmt<TIN>::size;
     const int tid = threadIdx.x, T = blockDim.x;
     const unsigned char *body = in_row + s.h0 * isz;
-    for (long long g0 = s.g_lo + tid; g0 < s.g_hi; g0 += 4LL * T) {
-        uint4 w[4];
+    constexpr int U = 4;  // 16-byte loads in flight per thread (8 spills at 64 registers and measures slower)
+    for (long long g0 = s.g_lo + tid; g0 < s.g_hi; g0 += static_cast<long long>(U) * T) {
+        uint4 w[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             const long long g = g0 + static_cast<long long>(u) * T;
             if (g < s.g_hi) w[u] = ld_global_v4(body + g * 16);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             const long long g = g0 + static_cast<long long>(u) * T;
             if (g < s.g_hi) {
                 float f[V];

@@ -1,7 +1,7 @@
 """Profiling sweep, learned-model training and pick-accuracy evaluation.
 
 Times every legal candidate plan (one-CTA, cluster P in {2, 4, 8, 16},
-two-pass G = 1 and the split factor) of a seeded set of shapes (rows
+two-pass G in {1, 2, 4, 8} and the split factor) of a seeded set of shapes (rows
 2^U(6,16), cols 2^U(10,20), dtype and op uniform, I/O <= a byte cap;
 median of `reps` CUDA-event timings), splits the shapes 80/20, trains the
 latency MLP on the GPU with the library's kernels, and reports, on the
@@ -40,14 +40,14 @@ def candidates(op, rows, cols, dtype, x, y, sc, osc, gamma, beta):
         p = C.make_plan(C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P)
         if C.plan_check(op, x, y, p, **kw) == C.OK:
             out.append((C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P, P, p))
-    Gs = [1]
-    auto = C.plan(op, rows, cols, dtype)  # any plan; the split factor comes from the two-pass rule
+    isz = {0: 4, 1: 2, 2: 1}[dtype]
+    groups = cols * isz // 16
+    Gs = [G for G in (1, 2, 4, 8) if G == 1 or groups // G >= 1024]
     g_auto = two_pass_split(rows, cols, dtype)
-    if g_auto > 1:
+    if g_auto > 1 and g_auto not in Gs:
         Gs.append(g_auto)
     for G in Gs:
         out.append((C.PATH_TWO_PASS, 1, G, C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)))
-    del auto
     return out, kw
 
 
