@@ -315,21 +315,21 @@ credit_status credit_load_model(const char *path);
 
 /* ------------------------------------------------------------------ learned model
  * A 3 x 64 ReLU MLP predicting log2 of a candidate plan's latency (us) from
- * 16 features (credit_mlp_features), trained on the GPU by the library's own
+ * 18 features (credit_mlp_features), trained on the GPU by the library's own
  * FP32 kernels (forward, backward, Adam; no tensor cores).  With
  * CREDIT_MODEL=learned, credit_plan picks the legal candidate with the
  * smallest predicted latency; the analytic model stays the fallback.  The
  * paper has no learned model; this is the project's addition.
  */
-#define CREDIT_MLP_FEATURES 16
+#define CREDIT_MLP_FEATURES 18
 int64_t credit_mlp_num_params(void);
-/* Features of candidate (path, P, G) for (op, dtypes, rows, cols) into out[16]:
+/* Features of candidate (path, P, G) for (op, dtypes, rows, cols) into out[18]:
  * log2 rows, log2 cols, input dtype one-hot, op one-hot, path one-hot
  * (one-CTA, two-pass, cluster), log2 P, log2 G, log2 algorithmic bytes,
- * output bytes per element. */
+ * output bytes per element, log2 input bytes per CTA, log2 CTAs per SM. */
 credit_status credit_mlp_features(int32_t op, int32_t in_dtype, int32_t out_dtype, int64_t rows, int64_t cols,
                                   int32_t path, int32_t P, int32_t G, float *out);
-/* Train from scratch on n host samples (X n x 16, y = log2 us): minibatch
+/* Train from scratch on n host samples (X n x 18, y = log2 us): minibatch
  * Adam on the MSE of standardised targets; He-initialised from `seed`.
  * loss_curve (NULL or `epochs` floats) gets the mean training loss per epoch. */
 credit_status credit_mlp_train(const float *X, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,

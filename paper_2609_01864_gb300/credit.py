@@ -381,7 +381,7 @@ class Ragged:
             pass
 
 
-MLP_FEATURES = 16
+MLP_FEATURES = 18
 
 
 def _fptr(a):

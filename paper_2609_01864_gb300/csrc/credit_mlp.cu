@@ -1,7 +1,7 @@
 // credit_mlp.cu -- learned latency model: a 3 x 64 MLP trained on the GPU
 // with hand-written FP32 kernels (no tensor cores: the matrices are 64 wide).
 //
-// Input: 16 features of one (shape, dtype, op, candidate plan) (see
+// Input: 18 features of one (shape, dtype, op, candidate plan) (see
 // credit_mlp_features).  Output: predicted log2 of the latency in us.
 // Training: minibatch Adam on the mean squared error of standardised
 // targets; features and targets are standardised with the training set's
@@ -29,8 +29,8 @@ namespace credit {
 
 namespace {
 
-constexpr int kIn = 16, kH = 64;
-// flat layout: W1 (64x16), b1, W2 (64x64), b2, W3 (64x64), b3, W4 (1x64), b4
+constexpr int kIn = 18, kH = 64;
+// flat layout: W1 (64x18), b1, W2 (64x64), b2, W3 (64x64), b3, W4 (1x64), b4
 constexpr int kOffW[4] = {0, kH * kIn + kH, kH * kIn + kH + kH * kH + kH, kH * kIn + kH + 2 * (kH * kH + kH)};
 constexpr int kFanIn[4] = {kIn, kH, kH, kH};
 constexpr int kFanOut[4] = {kH, kH, kH, 1};
@@ -200,7 +200,8 @@ void host_forward(const Model &mdl, const float *xin, float *yout_log2us) {
 
 // Features of one candidate: log2 rows, log2 cols, input dtype one-hot (3),
 // op one-hot (4), path one-hot (one-CTA, two-pass, cluster), log2 P, log2 G,
-// log2 of the algorithmic bytes, output bytes per element.
+// log2 of the algorithmic bytes, output bytes per element, log2 of the input
+// bytes one CTA handles, log2 of the CTAs per SM (152 SMs) the rows need.
 void mlp_features(int op, int tin, int tout, long long rows, long long cols, int path, int P, int G, float *f) {
     std::memset(f, 0, kIn * sizeof(float));
     f[0] = std::log2(static_cast<float>(rows));
@@ -214,6 +215,9 @@ void mlp_features(int op, int tin, int tout, long long rows, long long cols, int
     const double bytes = static_cast<double>(rows) * cols * (dtype_size(tin) + ob) + (op == 1 ? rows * 4.0 : 0.0);
     f[14] = static_cast<float>(std::log2(bytes));
     f[15] = static_cast<float>(ob);
+    const int split = path == CREDIT_PATH_TWO_PASS ? (G < 1 ? 1 : G) : (P < 1 ? 1 : P);
+    f[16] = static_cast<float>(std::log2(static_cast<double>(cols) * dtype_size(tin) / split + 1.0));
+    f[17] = static_cast<float>(std::log2(static_cast<double>(rows) * split / 152.0));
 }
 
 static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin,

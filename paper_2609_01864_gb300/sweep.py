@@ -163,31 +163,62 @@ def main(argv=None):
     ap.add_argument("--shapes", type=int, default=2000)
     ap.add_argument("--reps", type=int, default=15)
     ap.add_argument("--cap-gib", type=float, default=8.0)
-    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--epoch-grid", type=int, nargs="+", default=[50, 100, 200, 400, 800])
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data"))
     ap.add_argument("--calib", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
                                                     "gb300.calib"))
+    ap.add_argument("--from-csv", default="", help="retrain and evaluate from an earlier sweep's timings")
     args = ap.parse_args(argv)
     from . import build as B
     B.build()
     C.init()
-    C.load_model(args.calib)
+    try:
+        C.load_model(args.calib)
+    except C.CreditError as e:  # the calibration loads before the weights it names; stale weights are replaced below
+        print(f"note: {e}", file=sys.stderr)
     cap = int(args.cap_gib * 2 ** 30)
     shapes = synth.sweep_shapes(args.shapes, cap_bytes=cap)
     t0 = time.time()
-    rows = run_sweep(shapes, args.reps, cap, log=sys.stderr)
+    if args.from_csv:
+        rows = []
+        with open(args.from_csv) as f:
+            next(f)
+            for line in f:
+                sh, op, dt, r, c, path, P, G, us = line.strip().split(",")
+                rows.append(dict(shape=int(sh), op=int(op), dtype=int(dt), rows=int(r), cols=int(c), path=int(path),
+                                 P=int(P), G=int(G), us=float(us)))
+        shapes = shapes[:1 + max(r["shape"] for r in rows)]
+    else:
+        rows = run_sweep(shapes, args.reps, cap, log=sys.stderr)
     t_sweep = time.time() - t0
     train, test = synth.split_by_shape(len(shapes))
-    train_set = set(train)
-    Xtr = np.stack([features_of(r) for r in rows if r["shape"] in train_set])
-    ytr = np.array([np.log2(r["us"]) for r in rows if r["shape"] in train_set], dtype=np.float32)
+
+    def xy(shape_set):
+        X = np.stack([features_of(r) for r in rows if r["shape"] in shape_set])
+        y = np.array([np.log2(r["us"]) for r in rows if r["shape"] in shape_set], dtype=np.float32)
+        return X, y
+
     t1 = time.time()
-    curve = C.mlp_train(Xtr, ytr, epochs=args.epochs, batch=256, lr=2e-3, seed=0)
+    # epochs chosen on a validation split of the training shapes (the held-out
+    # test shapes are used once, for the final report)
+    fit_idx, val_idx = synth.split_by_shape(len(train), seed=synth.SEED_SWEEP + 7, train_frac=0.85)
+    fit_set, val_set = {train[i] for i in fit_idx}, [train[i] for i in val_idx]
+    Xf, yf = xy(fit_set)
+    val_acc = {}
+    for ep in args.epoch_grid:
+        C.mlp_train(Xf, yf, epochs=ep, batch=256, lr=2e-3, seed=0)
+        val_acc[ep] = evaluate(rows, val_set)[0]["learned"]
+    epochs = max(args.epoch_grid, key=lambda e: (val_acc[e], -e))
+    Xtr, ytr = xy(set(train))
+    curve = C.mlp_train(Xtr, ytr, epochs=epochs, batch=256, lr=2e-3, seed=0)
     t_train = time.time() - t1
     acc, n_test = evaluate(rows, test)
     os.makedirs(args.out, exist_ok=True)
     C.mlp_save(os.path.join(args.out, "gb300_mlp.txt"))
-    with open(os.path.join(args.out, "sweep_gb300.csv"), "w") as f:
+    csv_out = os.path.join(args.out, "sweep_gb300.csv")
+    if args.from_csv and os.path.abspath(args.from_csv) == os.path.abspath(csv_out):
+        csv_out += ".new"
+    with open(csv_out, "w") as f:
         f.write("shape,op,dtype,rows,cols,path,P,G,us\n")
         for r in rows:
             f.write(f"{r['shape']},{r['op']},{r['dtype']},{r['rows']},{r['cols']},{r['path']},{r['P']},{r['G']},"
@@ -195,6 +226,7 @@ def main(argv=None):
     summary = {"shapes": len(shapes), "timings": len(rows), "train_shapes": len(train), "test_shapes": n_test,
                "pick_rule": "pick within 5% of the measured best candidate", "pick_accuracy": acc,
                "train_loss_first_last": [float(curve[0]), float(curve[-1])], "sweep_s": round(t_sweep, 1),
+               "epochs": epochs, "validation_accuracy_by_epochs": val_acc,
                "train_s": round(t_train, 1), "reps": args.reps, "cap_gib": args.cap_gib}
     with open(os.path.join(args.out, "sweep_gb300_summary.json"), "w") as f:
         json.dump(summary, f, indent=1)

@@ -18,7 +18,7 @@ def test_hand_built_network():
     layers[3][1][0] = 1.0
     y, _ = M.forward(p, np.array([[3.0, 5.0, -1.0], [-3.0, 9.0, 9.0], [0.5, 0.0, 0.0]]))
     assert np.allclose(y, [7.0, 1.0, 2.0], rtol=0, atol=1e-15)
-    assert M.n_params(16) == 16 * 64 + 64 + 2 * (64 * 64 + 64) + 64 + 1
+    assert M.n_params(18) == 18 * 64 + 64 + 2 * (64 * 64 + 64) + 64 + 1
 
 
 def test_backprop_matches_finite_differences():
