@@ -70,6 +70,22 @@ typedef enum {
     CREDIT_PATH_CLUSTER = 2
 } credit_path;
 
+/* Where the staged paths (ONE_CTA, CLUSTER) keep a row slice between its
+ * reduction and its reuse pass (Sec. III-C, "reuse"; the capacity of Eq. 3).
+ *   SMEM  the shared-memory chunk ring (slice <= the opt-in shared memory)
+ *   TMEM  tensor memory, two 128-KiB row buffers per SM; shared memory holds
+ *         only chunks in flight and gamma / beta.  Softmax, LayerNorm and
+ *         RMSNorm (not FP8-output norms, not logsumexp), slice <= 128 KiB of
+ *         input, one CTA per SM.  The project's addition; the paper stages
+ *         in shared memory only.
+ *   AUTO  TMEM where it applies, else SMEM (CREDIT_RETAIN=smem|tmem in the
+ *         environment overrides AUTO). */
+typedef enum {
+    CREDIT_RETAIN_AUTO = 0,
+    CREDIT_RETAIN_SMEM = 1,
+    CREDIT_RETAIN_TMEM = 2
+} credit_retain;
+
 typedef enum {
     CREDIT_OK = 0,
     CREDIT_ERR_INVALID_ARG = 1,
@@ -132,6 +148,7 @@ credit_status credit_rmsnorm(const void *in, void *out, int64_t rows, int64_t co
  *   ring_chunks   staged paths: chunk slots of the shared-memory ring
  *                 (>= chunks of one slice; 0 = default)
  *   chunk_bytes   staged paths: bytes per chunk (multiple of 16; 0 = default)
+ *   retain        staged paths: credit_retain (0 = AUTO)
  *   smem_bytes    dynamic shared memory per CTA (S_CTA of Eq. 3), output
  *   predicted_us  model latency for the whole call (0 when not modelled)
  *   source        0 analytic model, 1 learned model, 2 forced by caller or
@@ -145,6 +162,7 @@ typedef struct {
     int32_t ring_chunks;
     int32_t chunk_bytes;
     int32_t reducer_threads;
+    int32_t retain;        /* credit_retain: where the staged paths keep the slice */
     int64_t smem_bytes;
     float predicted_us;
     int32_t source;

@@ -23,6 +23,7 @@ PATH_AUTO, PATH_ONE_CTA, PATH_TWO_PASS, PATH_CLUSTER = -1, 0, 1, 2
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_INITIALIZED, ERR_CAPTURE, ERR_IO = range(8)
 OP_NAMES = {SOFTMAX: "softmax", LOGSUMEXP: "logsumexp", LAYERNORM: "layernorm", RMSNORM: "rmsnorm"}
 PATH_NAMES = {PATH_ONE_CTA: "one_cta", PATH_TWO_PASS: "two_pass", PATH_CLUSTER: "cluster"}
+RETAIN_AUTO, RETAIN_SMEM, RETAIN_TMEM = 0, 1, 2
 
 TORCH_DTYPE = {F32: torch.float32, BF16: torch.bfloat16, FP8_E4M3: torch.float8_e4m3fn}
 DTYPE_OF = {torch.float32: F32, torch.bfloat16: BF16, torch.float8_e4m3fn: FP8_E4M3}
@@ -37,7 +38,7 @@ class CreditError(RuntimeError):
 class PlanT(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("ctas_per_row", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("ring_chunks", ctypes.c_int32), ("chunk_bytes", ctypes.c_int32),
-                ("reducer_threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int64), ("predicted_us", ctypes.c_float), ("source", ctypes.c_int32)]
+                ("reducer_threads", ctypes.c_int32), ("retain", ctypes.c_int32), ("smem_bytes", ctypes.c_int64), ("predicted_us", ctypes.c_float), ("source", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -239,7 +240,7 @@ def rmsnorm(x, out=None, stream=None):
 
 
 def make_plan(path: int, cluster_size: int = 1, ctas_per_row: int = 1, threads: int = 0, ring_chunks: int = 0,
-              chunk_bytes: int = 0, reducer_threads: int = 0) -> PlanT:
+              chunk_bytes: int = 0, reducer_threads: int = 0, retain: int = 0) -> PlanT:
     p = PlanT()
     p.path = path
     p.cluster_size = cluster_size
@@ -248,6 +249,7 @@ def make_plan(path: int, cluster_size: int = 1, ctas_per_row: int = 1, threads: 
     p.ring_chunks = ring_chunks
     p.chunk_bytes = chunk_bytes
     p.reducer_threads = reducer_threads
+    p.retain = retain
     return p
 
 

@@ -15,7 +15,7 @@
 
 #include "../../include/credit.h"
 #include "credit_host.h"
-#include "credit_rows.cuh"
+#include "credit_ring_tm.cuh"
 
 namespace credit {
 bool kernels_tin0(int op, int tout, KernelSet *ks);
@@ -86,6 +86,9 @@ credit_status prepare_kernel(DeviceState &d, const void *fn, bool staged) {
 
 // ------------------------------------------------------------------ host helpers
 namespace credit {
+
+// AUTO retention policy: tensor memory where it applies.
+bool g_auto_retain_tmem = false;
 
 int dtype_size(int dt) { return dt == DT_F32 ? 4 : (dt == DT_BF16 ? 2 : 1); }
 
@@ -165,6 +168,80 @@ bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring
         if (r.reducers < 32) r.reducers = 32;
     }
     if (tp - r.reducers < 32) return false;
+    r.tmem = 0;
+    *out = r;
+    return true;
+}
+
+// Geometry of k_ring_tm.  The slice is retained in one of two TMEM buffers of
+// kTmMaxChunks chunks (capacity: kTmMaxChunks * kTmMaxChunkBytes bytes of
+// input per CTA); the shared-memory ring only holds chunks between landing and
+// sweep, and gamma / beta are resident in shared memory when they fit beside
+// a ring of at least kTmMinRing chunks, else streamed through as many slots as
+// fit beside a ring of kTmStreamRing chunks.  The
+// request is raised above half of the SM's shared memory so that one CTA runs
+// per SM (the kernel allocates all kTmCols columns).
+bool ring_config_tm(const DeviceInfo &di, long long N, int isz, int P, int req_ring, int req_chunk, int nab,
+                    RingCfg *out) {
+    constexpr int kTmMinRing = 4;     // chunks in flight: enough to cover the load latency
+    constexpr int kTmStreamRing = 5;  // ring beside streamed gamma / beta slots
+    if (P < 1 || P > kMaxCluster || N <= 0) return false;
+    const long long groups = (N * isz) / 16;
+    const long long per = (groups + P - 1) / P;
+    RingCfg r{};
+    r.P = P;
+    r.tmem = 1;
+    r.body_max = per * 16;
+    const int abytes_per16 = nab * (16 / isz) * 4;
+    const long long max_chunk = kTmMaxChunkBytes;
+    if (req_chunk > 0) {
+        if (req_chunk % 16 || req_chunk > kTmMaxChunkBytes) return false;
+        r.chunk = req_chunk;
+    } else if (r.body_max == 0) {
+        r.chunk = 16;
+    } else {
+        const long long n = (r.body_max + max_chunk - 1) / max_chunk;
+        r.chunk = static_cast<int>(((r.body_max + n - 1) / n + 15) / 16 * 16);
+    }
+    r.nch_max = static_cast<int>((r.body_max + r.chunk - 1) / r.chunk);
+    if (r.nch_max > kTmMaxChunks) return false;  // TMEM capacity
+    r.aslot = static_cast<long long>(r.chunk / 16) * abytes_per16;
+    const long long budget = di.smem_optin - kTmCtrl;
+    r.affine = 0;
+    r.affine_resident = 0;
+    if (nab > 0) {
+        const long long res = static_cast<long long>(r.nch_max < 1 ? 1 : r.nch_max) * r.aslot;
+        const char *mode = std::getenv("CREDIT_TM_AFFINE");
+        const bool force_stream = mode && std::strcmp(mode, "stream") == 0;
+        const bool force_direct = mode && std::strcmp(mode, "direct") == 0;
+        if (force_direct) {
+            r.affine = 0;
+        } else if (!force_stream && r.nch_max <= kMaxAffine && (budget - res) / r.chunk >= kTmMinRing) {
+            r.affine = r.nch_max < 1 ? 1 : r.nch_max;
+            r.affine_resident = 1;
+        } else {
+            // as many streaming slots as fit beside a ring of kTmStreamRing chunks
+            long long na = (budget - static_cast<long long>(kTmStreamRing) * r.chunk) / r.aslot;
+            if (na > kMaxAffine) na = kMaxAffine;
+            if (na < 0) na = 0;
+            r.affine = static_cast<int>(na);
+        }
+    }
+    const long long fit = (budget - r.affine * r.aslot) / r.chunk;
+    if (req_ring > 0) {
+        r.ring = req_ring;
+    } else {
+        long long k = fit < kMaxRing ? fit : kMaxRing;
+        r.ring = static_cast<int>(k);
+    }
+    if (r.ring < 2 || r.ring > kMaxRing) return false;
+    r.smem = kTmCtrl + static_cast<long long>(r.ring) * r.chunk + r.affine * r.aslot;
+    if (r.smem > di.smem_optin) return false;
+    const long long half = di.smem_per_sm / 2 + 1024;  // one CTA per SM
+    if (r.smem < half) r.smem = half;
+    if (r.smem > di.smem_optin) return false;
+    r.threads = kTmThreads;
+    r.reducers = kTmReducers;
     *out = r;
     return true;
 }
@@ -173,12 +250,8 @@ bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring
 // ring for these arguments (0 = the reuse pass loads them directly): norms
 // only, every row starting at the same 16-byte phase, and the gamma / beta
 // segments of the slices 16-byte aligned.
-int affine_arrays(const credit_args *a) {
+int affine_arrays_aligned(const credit_args *a) {
     if (a->op != OP_LN && a->op != OP_RMS) return 0;
-    // gamma / beta staging in shared memory is opt-in (CREDIT_AFFINE_STAGE=1):
-    // it costs ring capacity, and the writers' batched L2 loads measure faster
-    const char *stage = std::getenv("CREDIT_AFFINE_STAGE");
-    if (!stage || std::atoi(stage) == 0) return 0;
     const int isz = dtype_size(a->in_dtype);
     const long long ld = a->ld_in ? a->ld_in : a->cols;
     if ((ld * isz) % 16) return 0;
@@ -191,6 +264,15 @@ int affine_arrays(const credit_args *a) {
     if (gm && (reinterpret_cast<uintptr_t>(gm + h0) & 15u)) return 0;
     if (bt && (reinterpret_cast<uintptr_t>(bt + h0) & 15u)) return 0;
     return (gm ? 1 : 0) + (bt ? 1 : 0);
+}
+
+int affine_arrays(const credit_args *a) {
+    // gamma / beta staging in the shared-memory ring kernel is opt-in
+    // (CREDIT_AFFINE_STAGE=1): there it costs ring capacity, and the writers'
+    // batched L2 loads measure faster
+    const char *stage = std::getenv("CREDIT_AFFINE_STAGE");
+    if (!stage || std::atoi(stage) == 0) return 0;
+    return affine_arrays_aligned(a);
 }
 
 const DeviceInfo *device_info(int device) {
@@ -206,14 +288,16 @@ int current_device() {
 
 // Max active clusters of the ring kernel for (op, dtypes, P, threads, smem);
 // 0 if it cannot be scheduled.  Cached.
-int ring_max_clusters(int device, int op, int tin, int tout, int P, int threads, long long smem) {
+int ring_max_clusters(int device, int op, int tin, int tout, int P, int threads, long long smem, bool tm) {
     if (device < 0 || device >= kMaxDevices) return 0;
     DeviceState &d = g_dev[device];
     KernelSet ks;
     if (!kernel_set(op, tin, tout, &ks)) return 0;
+    const void *fn = tm ? ks.ring_tm : ks.ring;
+    if (fn == nullptr) return 0;
     if (smem > d.info.smem_optin) return 0;
-    if (prepare_kernel(d, ks.ring, true) != CREDIT_OK) return 0;
-    const auto key = std::make_tuple(ks.ring, P, threads, smem);
+    if (prepare_kernel(d, fn, true) != CREDIT_OK) return 0;
+    const auto key = std::make_tuple(fn, P, threads, smem);
     {
         std::lock_guard<std::mutex> lk(d.mu);
         auto it = d.clusters.find(key);
@@ -222,11 +306,12 @@ int ring_max_clusters(int device, int op, int tin, int tout, int P, int threads,
     int n = 0;
     if (P <= 1) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.ring, threads, static_cast<size_t>(smem)) ==
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, static_cast<size_t>(smem)) ==
             cudaSuccess)
             n = per_sm * d.info.sm_count;
         else
             (void)cudaGetLastError();
+        if (tm && per_sm > 1) n = 0;  // TMEM allocation assumes one CTA per SM
     } else {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -239,7 +324,7 @@ int ring_max_clusters(int device, int op, int tin, int tout, int P, int threads,
         cfg.dynamicSmemBytes = static_cast<size_t>(smem);
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if (cudaOccupancyMaxActiveClusters(&n, ks.ring, &cfg) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
             n = 0;
             (void)cudaGetLastError();
         }
@@ -328,10 +413,32 @@ credit_status credit_device_error(cudaStream_t stream) {
 // ------------------------------------------------------------------ launching
 namespace credit {
 
-// Ring geometry for a call: with the gamma / beta affine ring when it fits,
-// else with direct gamma / beta loads (same legality as without them).
+// Retention tier asked for by a plan: 0 shared memory, 1 tensor memory,
+// 2 tensor memory where it applies (AUTO; CREDIT_RETAIN=smem|tmem overrides).
+static int retain_request(const credit_plan_t *p) {
+    if (p->retain == CREDIT_RETAIN_SMEM) return 0;
+    if (p->retain == CREDIT_RETAIN_TMEM) return 1;
+    const char *e = std::getenv("CREDIT_RETAIN");
+    if (e && std::strcmp(e, "smem") == 0) return 0;
+    if (e && std::strcmp(e, "tmem") == 0) return 2;
+    return g_auto_retain_tmem ? 2 : 0;
+}
+
+// Ring geometry for a call.  Tensor-memory retention first when the plan asks
+// for it and the op has a reuse pass (not logsumexp, not the FP8-output norms,
+// whose amax stage rereads the slice); then the shared-memory ring, with the
+// gamma / beta affine ring when it fits, else with direct gamma / beta loads.
 static bool ring_config_for(const DeviceInfo &di, const credit_args *a, int isz, int P, const credit_plan_t *p,
                             RingCfg *rc) {
+    const int tout = a->op == OP_LSE ? DT_F32 : a->out_dtype;
+    const bool tm_op = a->op != OP_LSE && !(tout == DT_E4M3 && (a->op == OP_LN || a->op == OP_RMS));
+    const int want = retain_request(p);
+    const bool tuned_smem = p->threads != 0 || p->reducer_threads != 0;
+    if (want != 0 && tm_op && !(want == 2 && tuned_smem) &&
+        (p->threads == 0 || p->threads == kTmThreads) && (p->reducer_threads == 0 || p->reducer_threads == kTmReducers) &&
+        ring_config_tm(di, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, affine_arrays_aligned(a), rc))
+        return true;
+    if (want == 1) return false;  // tensor memory asked for but not applicable
     const int nab = affine_arrays(a);
     if (nab > 0 &&
         ring_config(di, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, p->threads, p->reducer_threads, nab, rc))
@@ -379,7 +486,7 @@ credit_status check_plan(int device, const credit_args *a, const credit_plan_t *
         RingCfg rc;
         if (!ring_config_for(*di, a, isz, P, p, &rc))
             return CREDIT_ERR_UNSUPPORTED;  // Eq. 3
-        if (ring_max_clusters(device, a->op, a->in_dtype, tout, P, rc.threads, rc.smem) <= 0)
+        if (ring_max_clusters(device, a->op, a->in_dtype, tout, P, rc.threads, rc.smem, rc.tmem != 0) <= 0)
             return CREDIT_ERR_UNSUPPORTED;
         return CREDIT_OK;
     }
@@ -472,17 +579,19 @@ credit_status run_with_plan(int device, const credit_args *a, const credit_plan_
         RingCfg rc;
         if (!ring_config_for(d.info, a, isz, P, p, &rc))
             return CREDIT_ERR_UNSUPPORTED;
-        credit_status st = prepare_kernel(d, ks.ring, true);
+        const void *fn = rc.tmem ? ks.ring_tm : ks.ring;
+        if (fn == nullptr) return CREDIT_ERR_UNSUPPORTED;
+        credit_status st = prepare_kernel(d, fn, true);
         if (st != CREDIT_OK) return st;
-        const int maxc = ring_max_clusters(device, a->op, tin, tout, P, rc.threads, rc.smem);
+        const int maxc = ring_max_clusters(device, a->op, tin, tout, P, rc.threads, rc.smem, rc.tmem != 0);
         if (maxc <= 0) return CREDIT_ERR_UNSUPPORTED;
         const long long ncl = rows < maxc ? rows : maxc;
         if (std::getenv("CREDIT_LOG"))
             std::fprintf(stderr,
-                         "credit: ring op=%d P=%d clusters=%lld (max %d) threads=%d reducers=%d chunk=%d ring=%d "
+                         "credit: ring%s op=%d P=%d clusters=%lld (max %d) threads=%d reducers=%d chunk=%d ring=%d "
                          "affine=%d%s smem=%lld\n",
-                         a->op, P, ncl, maxc, rc.threads, rc.reducers, rc.chunk, rc.ring, rc.affine,
-                         rc.affine_resident ? "(resident)" : "", rc.smem);
+                         rc.tmem ? "_tm" : "", a->op, P, ncl, maxc, rc.threads, rc.reducers, rc.chunk, rc.ring,
+                         rc.affine, rc.affine_resident ? "(resident)" : "", rc.smem);
         RowArgs r = base;
         r.chunk_bytes = rc.chunk;
         r.ring = rc.ring;
@@ -490,7 +599,7 @@ credit_status run_with_plan(int device, const credit_args *a, const credit_plan_
         r.affine = rc.affine;
         r.affine_resident = rc.affine_resident;
         void *args[] = {&r};
-        cudaError_t e = launch(ks.ring, dim3(static_cast<unsigned>(P * ncl)), dim3(rc.threads),
+        cudaError_t e = launch(fn, dim3(static_cast<unsigned>(P * ncl)), dim3(rc.threads),
                                static_cast<size_t>(rc.smem), P, s, args);
         if (e != cudaSuccess) return cuda_status(e);
         g_launch_count.fetch_add(1);

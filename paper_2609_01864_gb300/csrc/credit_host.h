@@ -33,12 +33,18 @@ struct RingCfg {
     long long smem;      // dynamic shared memory per CTA
     long long body_max;  // largest slice body (bytes) of any CTA
     int nch_max;         // chunks of the largest slice
+    int tmem;            // 1: the slice is retained in tensor memory (k_ring_tm)
 };
 // nab: gamma/beta arrays streamed through the affine ring (0, 1 or 2).
 bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring, int req_chunk, int req_threads,
                  int req_reducers, int nab, RingCfg *out);
-int ring_max_clusters(int device, int op, int tin, int tout, int P, int threads, long long smem);
+// Tensor-memory retention geometry (k_ring_tm); false where it does not apply.
+bool ring_config_tm(const DeviceInfo &di, long long N, int isz, int P, int req_ring, int req_chunk, int nab,
+                    RingCfg *out);
+int ring_max_clusters(int device, int op, int tin, int tout, int P, int threads, long long smem, bool tm = false);
 int affine_arrays(const credit_args *a);
+int affine_arrays_aligned(const credit_args *a);
+extern bool g_auto_retain_tmem;
 credit_status validate_args(const credit_args *a);
 credit_status check_plan(int device, const credit_args *a, const credit_plan_t *p);
 credit_status ensure_init(int *device_out, cudaStream_t s);

@@ -4,7 +4,7 @@
 // 1 (BF16) and 2 (FP8-E4M3) so that the three object files compile in
 // parallel.  Each exports credit::kernels_tin<N>(op, out_dtype, &set), which
 // fills the kernel table the host dispatcher launches from.
-#include "credit_rows.cuh"
+#include "credit_ring_tm.cuh"
 
 #ifndef CREDIT_TIN
 #error "CREDIT_TIN must be defined (0 = FP32, 1 = BF16, 2 = FP8-E4M3)"
@@ -18,6 +18,9 @@ namespace credit {
 template <int OP, int TIN, int TOUT>
 static void fill_set(KernelSet *ks) {
     ks->ring = reinterpret_cast<const void *>(&k_ring<OP, TIN, TOUT>);
+    ks->ring_tm = nullptr;
+    if constexpr (OP != OP_LSE && !(TOUT == DT_E4M3 && (OP == OP_LN || OP == OP_RMS)))
+        ks->ring_tm = reinterpret_cast<const void *>(&k_ring_tm<OP, TIN, TOUT>);
     ks->tp_fused = reinterpret_cast<const void *>(&k_tp_fused<OP, TIN, TOUT>);
     ks->tp_stats = reinterpret_cast<const void *>(&k_tp_stats<OP, TIN>);
     ks->tp_amax = nullptr;

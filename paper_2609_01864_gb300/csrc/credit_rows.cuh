@@ -75,6 +75,14 @@ struct RowSlice {
     long long g_lo, g_hi;  // this CTA's groups
 };
 
+// floor(G * k / P) for 0 <= k <= P <= 16: 32-bit unsigned arithmetic when the
+// product fits (the common case; exact, so identical to the 64-bit form).
+__host__ __device__ __forceinline__ long long group_split(long long G, int k, int P) {
+    if (G <= 0x0FFFFFFFLL) return static_cast<long long>(static_cast<uint32_t>(G) * static_cast<uint32_t>(k) /
+                                                         static_cast<uint32_t>(P));
+    return G * k / P;
+}
+
 __host__ __device__ __forceinline__ RowSlice make_slice(uintptr_t row_addr, long long N, int isz, int P, int c) {
     const int V = 16 / isz;
     const long long mis = static_cast<long long>(row_addr & 15u);
@@ -85,14 +93,14 @@ __host__ __device__ __forceinline__ RowSlice make_slice(uintptr_t row_addr, long
     s.h0 = h0;
     s.G = rest / V;
     s.t0 = rest - s.G * V;
-    s.g_lo = s.G * c / P;
-    s.g_hi = s.G * (c + 1) / P;
+    s.g_lo = group_split(s.G, c, P);
+    s.g_hi = group_split(s.G, c + 1, P);
     return s;
 }
 
 // Elements owned by CTA c (of P) for a row with h0 / G / t0.
 __host__ __device__ __forceinline__ long long slice_count(const RowSlice &s, int V, int P, int c) {
-    const long long lo = s.G * c / P, hi = s.G * (c + 1) / P;
+    const long long lo = group_split(s.G, c, P), hi = group_split(s.G, c + 1, P);
     return (hi - lo) * V + (c == 0 ? s.h0 : 0) + (c == P - 1 ? s.t0 : 0);
 }
 
@@ -239,12 +247,23 @@ template <> struct Stream<OP_LN> {
     float n = 0.0f, mu = 0.0f, m2 = 0.0f;  // merged form (after finish())
     float K = 0.0f, s1 = 0.0f, s2 = 0.0f;
     bool has = false;
+    // Chan's merge of (nb, mb, m2b) into this state.  The two quotients use
+    // one correctly rounded reciprocal of the merged count (<= 1.5 ulp each
+    // instead of two IEEE divisions on the reduction's critical path).
     __device__ __forceinline__ void merge3(float nb, float mb, float m2b) {
         if (nb == 0.0f) return;
+        if (n == 0.0f) {
+            n = nb;
+            mu = mb;
+            m2 = m2b;
+            return;
+        }
         const float nn = n + nb;
+        const float r = __frcp_rn(nn);
         const float d = mb - mu;
-        mu += d * (nb / nn);
-        m2 += m2b + d * d * (n * nb / nn);
+        const float wb = nb * r;
+        mu += d * wb;
+        m2 += m2b + d * d * (n * wb);
         n = nn;
     }
     template <int V> __device__ __forceinline__ void add(const float (&f)[V]) {
@@ -267,7 +286,7 @@ template <> struct Stream<OP_LN> {
     // (n, K, s1, s2) -> (n, mean, M2); call once before merging
     __device__ __forceinline__ void finish() {
         if (n > 0.0f) {
-            const float q = s1 / n;
+            const float q = s1 * __frcp_rn(n);
             mu = K + q;
             m2 = fmaxf(s2 - s1 * q, 0.0f);
         }
@@ -400,11 +419,31 @@ __device__ __forceinline__ float2 block_reduce_stream(Stream<OP> st, float *red,
             red[3 * wid + 2] = st.m2;
         }
         sync_group(bar_id, Tc);
-        if (threadIdx.x == 0) {
+        if (wid == 0) {  // the warps' states, merged by a shuffle tree in warp 0
             Stream<OP_LN> t;
-            for (int w = 0; w < nw; ++w) t.merge3(red[3 * w], red[3 * w + 1], red[3 * w + 2]);
-            red[96] = t.mu;
-            red[97] = t.m2;
+            if (lane < nw) {
+                t.n = red[3 * lane];
+                t.mu = red[3 * lane + 1];
+                t.m2 = red[3 * lane + 2];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float nb = __shfl_xor_sync(0xffffffffu, t.n, o);
+                const float mb = __shfl_xor_sync(0xffffffffu, t.mu, o);
+                const float qb = __shfl_xor_sync(0xffffffffu, t.m2, o);
+                if (lane & o) {
+                    Stream<OP_LN> u;
+                    u.n = nb; u.mu = mb; u.m2 = qb;
+                    u.merge3(t.n, t.mu, t.m2);
+                    t = u;
+                } else {
+                    t.merge3(nb, mb, qb);
+                }
+            }
+            if (lane == 0) {
+                red[96] = t.mu;
+                red[97] = t.m2;
+            }
         }
         sync_group(bar_id, Tc);
         (void)n_c;
@@ -1107,6 +1146,7 @@ __global__ void k_tp_lse_final(const RowArgs a, long long nrows) {
 // ----------------------------------------------------------------------
 struct KernelSet {
     const void *ring;
+    const void *ring_tm;  // TMEM retention variant (null where it does not apply)
     const void *tp_fused;
     const void *tp_stats;
     const void *tp_amax;
