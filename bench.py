@@ -120,10 +120,26 @@ def algorithmic_bytes(rows, cols, op):
     return rows * cols * 8  # FP32 in + FP32 out
 
 
-def kernel_name(plan, C):
+def kernel_name(plan, C, cols=0, isz=4):
     if plan.path in (C.PATH_ONE_CTA, C.PATH_CLUSTER):
+        if plan.retain == C.RETAIN_TMEM:
+            return "k_ring_tm"
+        if plan.retain == C.RETAIN_AUTO:  # the library's AUTO rule for the norms with FP32 output
+            P = max(1, plan.cluster_size)
+            body = -(-(cols * isz // 16) // P) * 16
+            if 32768 < body <= 8 * 16384 and os.environ.get("CREDIT_RETAIN", "") != "smem":
+                return "k_ring_tm"
         return "k_ring"
     return "k_tp_fused" if plan.ctas_per_row == 1 else "k_tp_split"
+
+
+def source_sha():
+    """Hash of the row-kernel sources a traffic capture was taken on."""
+    h = hashlib.sha256()
+    for name in ("credit_prim.cuh", "credit_rows.cuh", "credit_ring_tm.cuh"):
+        with open(os.path.join(ROOT, "paper_2609_01864_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def traffic_record(kernel: str, op: str, cols: int):
@@ -135,8 +151,7 @@ def traffic_record(kernel: str, op: str, cols: int):
             recs = json.load(f)
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_2609_01864_gb300", "csrc", "credit_rows.cuh")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = source_sha()
     for r in recs.get("records", []):
         if r.get("kernel") == kernel and r.get("op") == op and r.get("cols") == cols and r.get("source_sha") == h:
             return r
@@ -159,9 +174,10 @@ def time_events(fn, reps, warm=1):
 def candidates(C, op, x, y, g, b):
     out = []
     for P in (1, 2, 4, 8, 16):
-        p = C.make_plan(C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P)
-        if C.plan_check(op, x, y, p, gamma=g, beta=b) == C.OK:
-            out.append((f"{'one_cta' if P == 1 else 'cluster'}{'' if P == 1 else P}", p))
+        for retain, tag in ((C.RETAIN_SMEM, ""), (C.RETAIN_TMEM, "_tm")):
+            p = C.make_plan(C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P, retain=retain)
+            if C.plan_check(op, x, y, p, gamma=g, beta=b) == C.OK:
+                out.append((f"{'one_cta' if P == 1 else 'cluster'}{'' if P == 1 else P}{tag}", p))
     for G in (1, 2, 4, 8):
         p = C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)
         out.append((f"two_pass_g{G}", p))
@@ -237,12 +253,15 @@ def run_case(spec: str):
     from paper_2609_01864_gb300 import credit as C
     from paper_2609_01864_gb300 import synth
     B.build()
-    op, rows, cols, path, P = [int(v) for v in spec.split(":")]
+    v = [int(t) for t in spec.split(":")]
+    op, rows, cols, path, P = v[:5]
+    retain = v[5] if len(v) > 5 else 0
     C.init(torch.cuda.current_device())
     x = synth.outliers(rows, cols, seed=synth.SEED_DATA, device="cuda")
     y = torch.empty_like(x)
     g, b = synth.gamma_beta(cols, device="cuda")
-    plan = None if path < 0 else C.make_plan(path, P, ctas_per_row=P if path == C.PATH_TWO_PASS else 1)
+    plan = None if path < 0 else C.make_plan(path, P, ctas_per_row=P if path == C.PATH_TWO_PASS else 1,
+                                             retain=retain)
     kw = dict(gamma=g if op in (C.LAYERNORM, C.RMSNORM) else None, beta=b if op == C.LAYERNORM else None)
     for _ in range(3):
         C.run_ex(op, x, y, plan=plan, **kw)
@@ -289,7 +308,7 @@ def run_ours(args):
             plan = C.plan(op, ROWS, sh["cols"], C.F32)
             kw = dict(gamma=sh["g"], beta=sh["b"] if op == C.LAYERNORM else None)
             jobs.append({"op": op, "name": name, "cols": sh["cols"], "x": sh["x"], "y": sh["y"], "kw": kw,
-                         "plan": plan, "kernel": kernel_name(plan, C),
+                         "plan": plan, "kernel": kernel_name(plan, C, sh["cols"]),
                          "bytes": algorithmic_bytes(ROWS, sh["cols"], op)})
     step_bytes = sum(j["bytes"] for j in jobs)
     stream = torch.cuda.current_stream()
@@ -365,6 +384,7 @@ def run_ours(args):
         ms = statistics.median(per[s][k][0].elapsed_time(per[s][k][1]) for s in range(args.steps))
         per_job.append({"op": j["name"], "cols": j["cols"], "plan": C.PATH_NAMES[j["plan"].path],
                         "P": j["plan"].cluster_size, "G": j["plan"].ctas_per_row, "source": j["plan"].source,
+                        "kernel": j["kernel"],
                         "ms": round(ms, 4), "GBps": round(j["bytes"] / ms / 1e6, 1)})
 
     # ---- speedup vs best non-DSMEM path and pick accuracy (every candidate timed)
@@ -474,7 +494,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--case", default="")
+    ap.add_argument("--case", default="", help="op:rows:cols:path:P[:retain] -- one plan, 3 launches (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not args.case:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

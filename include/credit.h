@@ -78,8 +78,10 @@ typedef enum {
  *         RMSNorm (not FP8-output norms, not logsumexp), slice <= 128 KiB of
  *         input, one CTA per SM.  The project's addition; the paper stages
  *         in shared memory only.
- *   AUTO  TMEM where it applies, else SMEM (CREDIT_RETAIN=smem|tmem in the
- *         environment overrides AUTO). */
+ *   AUTO  TMEM where it applies and a slice exceeds 32 KiB, else SMEM
+ *         (CREDIT_RETAIN=smem in the environment makes AUTO mean SMEM,
+ *         CREDIT_RETAIN=tmem TMEM wherever it applies).  The planners set
+ *         SMEM or TMEM explicitly. */
 typedef enum {
     CREDIT_RETAIN_AUTO = 0,
     CREDIT_RETAIN_SMEM = 1,
@@ -333,21 +335,23 @@ credit_status credit_load_model(const char *path);
 
 /* ------------------------------------------------------------------ learned model
  * A 3 x 64 ReLU MLP predicting log2 of a candidate plan's latency (us) from
- * 18 features (credit_mlp_features), trained on the GPU by the library's own
+ * 19 features (credit_mlp_features), trained on the GPU by the library's own
  * FP32 kernels (forward, backward, Adam; no tensor cores).  With
  * CREDIT_MODEL=learned, credit_plan picks the legal candidate with the
  * smallest predicted latency; the analytic model stays the fallback.  The
  * paper has no learned model; this is the project's addition.
  */
-#define CREDIT_MLP_FEATURES 18
+#define CREDIT_MLP_FEATURES 19
 int64_t credit_mlp_num_params(void);
-/* Features of candidate (path, P, G) for (op, dtypes, rows, cols) into out[18]:
- * log2 rows, log2 cols, input dtype one-hot, op one-hot, path one-hot
+/* Features of candidate (path, P, G, retain) for (op, dtypes, rows, cols) into
+ * out[19]: log2 rows, log2 cols, input dtype one-hot, op one-hot, path one-hot
  * (one-CTA, two-pass, cluster), log2 P, log2 G, log2 algorithmic bytes,
- * output bytes per element, log2 input bytes per CTA, log2 CTAs per SM. */
+ * output bytes per element, log2 input bytes per CTA, log2 CTAs per SM, and
+ * 1 when a staged path retains the slice in tensor memory (retain =
+ * CREDIT_RETAIN_TMEM; AUTO and SMEM give 0). */
 credit_status credit_mlp_features(int32_t op, int32_t in_dtype, int32_t out_dtype, int64_t rows, int64_t cols,
-                                  int32_t path, int32_t P, int32_t G, float *out);
-/* Train from scratch on n host samples (X n x 18, y = log2 us): minibatch
+                                  int32_t path, int32_t P, int32_t G, int32_t retain, float *out);
+/* Train from scratch on n host samples (X n x 19, y = log2 us): minibatch
  * Adam on the MSE of standardised targets; He-initialised from `seed`.
  * loss_curve (NULL or `epochs` floats) gets the mean training loss per epoch. */
 credit_status credit_mlp_train(const float *X, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,

@@ -157,7 +157,7 @@ def _extra_prototypes(L):
     fp = ctypes.POINTER(ctypes.c_float)
     L.credit_mlp_num_params.restype = i64
     L.credit_mlp_features.restype = i32
-    L.credit_mlp_features.argtypes = [i32, i32, i32, i64, i64, i32, i32, i32, fp]
+    L.credit_mlp_features.argtypes = [i32, i32, i32, i64, i64, i32, i32, i32, i32, fp]
     L.credit_mlp_train.restype = i32
     L.credit_mlp_train.argtypes = [fp, fp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64, fp]
     L.credit_mlp_predict.restype = i32
@@ -383,7 +383,7 @@ class Ragged:
             pass
 
 
-MLP_FEATURES = 18
+MLP_FEATURES = 19
 
 
 def _fptr(a):
@@ -396,10 +396,10 @@ def mlp_num_params() -> int:
     return int(lib().credit_mlp_num_params())
 
 
-def mlp_features(op, in_dtype, out_dtype, rows, cols, path, P, G):
+def mlp_features(op, in_dtype, out_dtype, rows, cols, path, P, G, retain=0):
     import numpy as np
     f = np.zeros(MLP_FEATURES, dtype=np.float32)
-    _check(lib().credit_mlp_features(op, in_dtype, out_dtype, rows, cols, path, P, G, _fptr(f)),
+    _check(lib().credit_mlp_features(op, in_dtype, out_dtype, rows, cols, path, P, G, retain, _fptr(f)),
            "credit_mlp_features")
     return f
 

@@ -87,8 +87,10 @@ credit_status prepare_kernel(DeviceState &d, const void *fn, bool staged) {
 // ------------------------------------------------------------------ host helpers
 namespace credit {
 
-// AUTO retention policy: tensor memory where it applies.
-bool g_auto_retain_tmem = false;
+// AUTO retention policy: tensor memory where it applies (slices above
+// kTmAutoMinSlice bytes).
+bool g_auto_retain_tmem = true;
+constexpr long long kTmAutoMinSlice = 32768;
 
 int dtype_size(int dt) { return dt == DT_F32 ? 4 : (dt == DT_BF16 ? 2 : 1); }
 
@@ -414,13 +416,15 @@ credit_status credit_device_error(cudaStream_t stream) {
 namespace credit {
 
 // Retention tier asked for by a plan: 0 shared memory, 1 tensor memory,
-// 2 tensor memory where it applies (AUTO; CREDIT_RETAIN=smem|tmem overrides).
+// 2 AUTO (tensor memory where it applies and the slice exceeds
+// kTmAutoMinSlice), 3 tensor memory wherever it applies (CREDIT_RETAIN=tmem;
+// CREDIT_RETAIN=smem gives 0).
 static int retain_request(const credit_plan_t *p) {
     if (p->retain == CREDIT_RETAIN_SMEM) return 0;
     if (p->retain == CREDIT_RETAIN_TMEM) return 1;
     const char *e = std::getenv("CREDIT_RETAIN");
     if (e && std::strcmp(e, "smem") == 0) return 0;
-    if (e && std::strcmp(e, "tmem") == 0) return 2;
+    if (e && std::strcmp(e, "tmem") == 0) return 3;
     return g_auto_retain_tmem ? 2 : 0;
 }
 
@@ -432,9 +436,15 @@ static bool ring_config_for(const DeviceInfo &di, const credit_args *a, int isz,
                             RingCfg *rc) {
     const int tout = a->op == OP_LSE ? DT_F32 : a->out_dtype;
     const bool tm_op = a->op != OP_LSE && !(tout == DT_E4M3 && (a->op == OP_LN || a->op == OP_RMS));
-    const int want = retain_request(p);
+    int want = retain_request(p);
     const bool tuned_smem = p->threads != 0 || p->reducer_threads != 0;
-    if (want != 0 && tm_op && !(want == 2 && tuned_smem) &&
+    if (want == 2) {
+        // AUTO: tensor memory pays off once a slice is large enough that the
+        // shared-memory ring would hold one CTA per SM anyway (> 32 KiB)
+        const long long groups = (a->cols * isz) / 16;
+        if ((groups + P - 1) / P * 16 <= kTmAutoMinSlice || tuned_smem) want = 0;
+    }
+    if (want != 0 && tm_op &&
         (p->threads == 0 || p->threads == kTmThreads) && (p->reducer_threads == 0 || p->reducer_threads == kTmReducers) &&
         ring_config_tm(di, a->cols, isz, P, p->ring_chunks, p->chunk_bytes, affine_arrays_aligned(a), rc))
         return true;

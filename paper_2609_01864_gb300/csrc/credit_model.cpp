@@ -214,6 +214,7 @@ static void baseline_plan(const DeviceInfo &di, int device, int op, long long ro
         p->cluster_size = 1;
         p->ctas_per_row = 1;
         p->smem_bytes = rc.smem;
+        p->retain = CREDIT_RETAIN_SMEM;  // the paper's staging
     } else {
         p->path = CREDIT_PATH_TWO_PASS;
         p->cluster_size = 1;
@@ -282,6 +283,7 @@ bool analytic_plan(const DeviceInfo &di, int device, int op, long long rows, lon
         p->cluster_size = bestP;
         p->ctas_per_row = bestP;
         p->smem_bytes = best_rc.smem;
+        p->retain = CREDIT_RETAIN_SMEM;  // Eq. 7-9 model the shared-memory staging
         p->predicted_us = static_cast<float>(T_B - best);
     }
     if (best_dT) *best_dT = best;

@@ -1,7 +1,8 @@
 """Profiling sweep, learned-model training and pick-accuracy evaluation.
 
-Times every legal candidate plan (one-CTA, cluster P in {2, 4, 8, 16},
-two-pass G in {1, 2, 4, 8} and the split factor) of a seeded set of shapes (rows
+Times every legal candidate plan (one-CTA and cluster P in {2, 4, 8, 16}, each
+with the slice retained in shared memory and, where that applies, in tensor
+memory; two-pass G in {1, 2, 4, 8} and the split factor) of a seeded set of shapes (rows
 2^U(6,16), cols 2^U(10,20), dtype and op uniform, I/O <= a byte cap;
 median of `reps` CUDA-event timings), splits the shapes 80/20, trains the
 latency MLP on the GPU with the library's kernels, and reports, on the
@@ -37,9 +38,10 @@ def candidates(op, rows, cols, dtype, x, y, sc, osc, gamma, beta):
     kw = dict(rows=rows, cols=cols, in_dtype=dtype, out_dtype=C.F32 if op == C.LOGSUMEXP else dtype,
               in_scale=sc, out_scale=osc, gamma=gamma, beta=beta)
     for P in (1, 2, 4, 8, 16):
-        p = C.make_plan(C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P)
-        if C.plan_check(op, x, y, p, **kw) == C.OK:
-            out.append((C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P, P, p))
+        for retain in (C.RETAIN_SMEM, C.RETAIN_TMEM):
+            p = C.make_plan(C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P, retain=retain)
+            if C.plan_check(op, x, y, p, **kw) == C.OK:
+                out.append((C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P, P, retain, p))
     isz = {0: 4, 1: 2, 2: 1}[dtype]
     groups = cols * isz // 16
     Gs = [G for G in (1, 2, 4, 8) if G == 1 or groups // G >= 1024]
@@ -47,7 +49,7 @@ def candidates(op, rows, cols, dtype, x, y, sc, osc, gamma, beta):
     if g_auto > 1 and g_auto not in Gs:
         Gs.append(g_auto)
     for G in Gs:
-        out.append((C.PATH_TWO_PASS, 1, G, C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)))
+        out.append((C.PATH_TWO_PASS, 1, G, C.RETAIN_AUTO, C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)))
     return out, kw
 
 
@@ -104,11 +106,12 @@ def run_sweep(shapes, reps, cap_bytes, log=None):
         cands, kw = candidates(op, rows, cols, dt, x, y, scales[:rows], oscales[:rows],
                                gamma[:cols] if op in (2, 3) else None, beta[:cols] if op == 2 else None)
         times = []
-        for path, P, G, plan in cands:
+        for path, P, G, retain, plan in cands:
             us = time_plan(lambda: C.run_ex(op, x, y, plan=plan, **kw), reps)
-            times.append((path, P, G, us))
-        for path, P, G, us in times:
-            rows_out.append(dict(shape=si, op=op, dtype=dt, rows=rows, cols=cols, path=path, P=P, G=G, us=us))
+            times.append((path, P, G, retain, us))
+        for path, P, G, retain, us in times:
+            rows_out.append(dict(shape=si, op=op, dtype=dt, rows=rows, cols=cols, path=path, P=P, G=G,
+                                 retain=retain, us=us))
         if log and si % 100 == 0:
             print(f"shape {si}/{len(shapes)} {time.time() - t0:.0f}s", file=log, flush=True)
     assert C.device_error() == C.OK
@@ -117,7 +120,8 @@ def run_sweep(shapes, reps, cap_bytes, log=None):
 
 def features_of(r):
     out_dt = C.F32 if r["op"] == C.LOGSUMEXP else r["dtype"]
-    return C.mlp_features(r["op"], r["dtype"], out_dt, r["rows"], r["cols"], r["path"], r["P"], r["G"])
+    return C.mlp_features(r["op"], r["dtype"], out_dt, r["rows"], r["cols"], r["path"], r["P"], r["G"],
+                          r.get("retain", 0))
 
 
 def evaluate(rows, test_shapes):
@@ -149,7 +153,8 @@ def evaluate(rows, test_shapes):
             p = C.plan(r0["op"], r0["rows"], r0["cols"], r0["dtype"])
             os.environ.pop("CREDIT_MODEL", None)
             match = [c for c in cand if c["path"] == p.path and (c["P"] == p.cluster_size if p.path != C.PATH_TWO_PASS
-                                                                  else c["G"] == p.ctas_per_row)]
+                                                                  else c["G"] == p.ctas_per_row)
+                     and (p.path == C.PATH_TWO_PASS or c.get("retain", 0) == p.retain)]
             res[name] += ok(match[0]) if match else 0
         tp = [c for c in cand if c["path"] == C.PATH_TWO_PASS and c["G"] == 1]
         res["always_two_pass"] += ok(tp[0]) if tp else 0
@@ -162,7 +167,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--shapes", type=int, default=2000)
     ap.add_argument("--reps", type=int, default=15)
-    ap.add_argument("--cap-gib", type=float, default=8.0)
+    ap.add_argument("--cap-gib", type=float, default=16.0)
     ap.add_argument("--epoch-grid", type=int, nargs="+", default=[50, 100, 200, 400, 800])
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data"))
     ap.add_argument("--calib", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
@@ -184,9 +189,12 @@ def main(argv=None):
         with open(args.from_csv) as f:
             next(f)
             for line in f:
-                sh, op, dt, r, c, path, P, G, us = line.strip().split(",")
+                v = line.strip().split(",")
+                if len(v) == 9:  # timings from before the retention column: shared-memory staging
+                    v = v[:8] + [str(C.RETAIN_SMEM if int(v[5]) != C.PATH_TWO_PASS else C.RETAIN_AUTO)] + v[8:]
+                sh, op, dt, r, c, path, P, G, retain, us = v
                 rows.append(dict(shape=int(sh), op=int(op), dtype=int(dt), rows=int(r), cols=int(c), path=int(path),
-                                 P=int(P), G=int(G), us=float(us)))
+                                 P=int(P), G=int(G), retain=int(retain), us=float(us)))
         shapes = shapes[:1 + max(r["shape"] for r in rows)]
     else:
         rows = run_sweep(shapes, args.reps, cap, log=sys.stderr)
@@ -219,10 +227,10 @@ def main(argv=None):
     if args.from_csv and os.path.abspath(args.from_csv) == os.path.abspath(csv_out):
         csv_out += ".new"
     with open(csv_out, "w") as f:
-        f.write("shape,op,dtype,rows,cols,path,P,G,us\n")
+        f.write("shape,op,dtype,rows,cols,path,P,G,retain,us\n")
         for r in rows:
             f.write(f"{r['shape']},{r['op']},{r['dtype']},{r['rows']},{r['cols']},{r['path']},{r['P']},{r['G']},"
-                    f"{r['us']:.3f}\n")
+                    f"{r['retain']},{r['us']:.3f}\n")
     summary = {"shapes": len(shapes), "timings": len(rows), "train_shapes": len(train), "test_shapes": n_test,
                "pick_rule": "pick within 5% of the measured best candidate", "pick_accuracy": acc,
                "train_loss_first_last": [float(curve[0]), float(curve[-1])], "sweep_s": round(t_sweep, 1),

@@ -86,7 +86,7 @@ def ragged_widths(n_rows: int, *, seed: int = SEED_RAGGED, lo_log2: float = 10.0
     return w, ops
 
 
-def sweep_shapes(n: int, *, seed: int = SEED_SWEEP, cap_bytes: float = 8 * 2**30,
+def sweep_shapes(n: int, *, seed: int = SEED_SWEEP, cap_bytes: float = 16 * 2**30,
                  rows_log2=(6.0, 16.0), cols_log2=(10.0, 20.0)):
     """List of (op, dtype, rows, cols) with rows*cols*(in+out bytes) <= cap."""
     g = _gen(seed, "cpu")
