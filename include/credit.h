@@ -215,6 +215,23 @@ credit_status credit_run_ex(const credit_args *args, const credit_plan_t *plan,
                             cudaStream_t stream);
 
 /*
+ * credit_run_host -- run one op on HOST buffers and return when the output is
+ * in host memory.  args as credit_run_ex, except that in / out (and in_scale,
+ * out_scale, gamma, beta) are host pointers; pinned memory (cudaHostAlloc /
+ * cudaHostRegister) gets the full link bandwidth, pageable memory works but
+ * copies slower.  The rows stream through three device staging slots in
+ * blocks of about rows / 8 rows (at most 256 MiB per buffer): the copy-in of
+ * block b + 1, the op on block b and the copy-out of block b - 1 overlap on
+ * three CUDA streams of the library.  plan is applied to every block (NULL:
+ * credit_plan's choice for the block shape).  Staging buffers are allocated
+ * on first use per device and kept (grown when needed); one host call runs
+ * per device at a time.  The paper has no counterpart; it is the host-memory
+ * form of the same ops (the end-to-end path).
+ *   returns  credit_run_ex's statuses; CREDIT_ERR_CUDA if a copy failed
+ */
+credit_status credit_run_host(const credit_args *args, const credit_plan_t *plan);
+
+/*
  * credit_plan_check -- CREDIT_OK if `plan` is legal for `args` on the current
  * device (Eq. 3 capacity, cluster size, scheduling), CREDIT_ERR_UNSUPPORTED
  * if not, CREDIT_ERR_INVALID_ARG for bad arguments.  Launches nothing.

@@ -84,6 +84,8 @@ def lib() -> ctypes.CDLL:
             L.credit_plan_ex.argtypes = [i32, i64, i64, i32, i32, ctypes.POINTER(PlanT)]
             L.credit_run_ex.restype = i32
             L.credit_run_ex.argtypes = [ctypes.POINTER(ArgsT), ctypes.POINTER(PlanT), vp]
+            L.credit_run_host.restype = i32
+            L.credit_run_host.argtypes = [ctypes.POINTER(ArgsT), ctypes.POINTER(PlanT)]
             L.credit_run_two_pass_noalloc.restype = i32
             L.credit_run_two_pass_noalloc.argtypes = [ctypes.POINTER(ArgsT), i32, vp]
             L.credit_set_trace.restype = i32
@@ -295,6 +297,16 @@ def run_ex(op: int, x, out, *, plan: PlanT | None = None, stream=None, **kw) -> 
     a = make_args(op, x, out, **kw)
     st = lib().credit_run_ex(ctypes.byref(a), ctypes.byref(plan) if plan is not None else None, _stream(stream))
     _check(st, "credit_run_ex")
+    return st
+
+
+def run_host(op: int, x, out, *, plan: PlanT | None = None, **kw) -> int:
+    """credit_run_host: x / out (and in_scale, out_scale, gamma, beta) are
+    host (CPU) tensors, pinned for full copy bandwidth; returns once out holds
+    the result.  Raises CreditError on a non-OK status."""
+    a = make_args(op, x, out, **kw)
+    st = lib().credit_run_host(ctypes.byref(a), ctypes.byref(plan) if plan is not None else None)
+    _check(st, "credit_run_host")
     return st
 
 

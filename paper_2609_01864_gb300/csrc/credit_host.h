@@ -47,6 +47,7 @@ int affine_arrays_aligned(const credit_args *a);
 extern bool g_auto_retain_tmem;
 credit_status validate_args(const credit_args *a);
 credit_status check_plan(int device, const credit_args *a, const credit_plan_t *p);
+credit_status run_with_plan(int device, const credit_args *a, const credit_plan_t *p, cudaStream_t s);
 credit_status ensure_init(int *device_out, cudaStream_t s);
 
 }  // namespace credit
