@@ -404,9 +404,17 @@ def run_ours(args):
             speed_den += chosen
             hit = chosen <= 1.05 * best_all
             hits += int(hit)
+            # paper-style profitability pair: the analytic model (Eq. 7-9, shared-memory staging) picks the
+            # cluster path iff its best dT > 0; measured: best shared-memory cluster vs best non-DSMEM plan
+            os.environ["CREDIT_MODEL"] = "analytic"
+            ap_ = C.plan(j["op"], ROWS, j["cols"], C.F32)
+            os.environ.pop("CREDIT_MODEL", None)
+            cl = [v for n, v in times.items() if n.startswith("cluster") and not n.endswith("_tm")]
             pick_rows.append({"op": j["name"], "cols": j["cols"], "chosen_ms": chosen,
                               "best": min(times, key=times.get), "best_ms": round(best_all, 4),
                               "best_non_dsmem_ms": round(best_non, 4), "hit": hit,
+                              "analytic_cluster": ap_.path == C.PATH_CLUSTER,
+                              "measured_cluster": bool(cl) and min(cl) < best_non,
                               "candidates": {n: round(v, 4) for n, v in times.items()}})
 
     # ---- end to end through the public API with host buffers
@@ -438,12 +446,30 @@ def run_ours(args):
         "clocks": clk,
         "speedup_vs_best_non_dsmem": round(speed_num / speed_den, 4) if speed_den else None,
         "pick_accuracy": round(hits / len(jobs), 4) if pick_rows else None,
+        "profitability": profitability(pick_rows) if pick_rows else None,
         "pick_rule": "chosen plan within 5% of the fastest measured candidate (median of 5)",
         "per_job": per_job,
         "picks": pick_rows,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def profitability(pick_rows):
+    """Paper-style profitability pairs (Sec. IV): per shape, does the analytic
+    model's sign of dT (cluster picked or not) agree with the measured sign
+    (best shared-memory cluster plan faster than the best non-DSMEM plan)?
+    Plus N*, the smallest width where the cluster path wins, per op, predicted
+    and measured."""
+    agree = sum(r["analytic_cluster"] == r["measured_cluster"] for r in pick_rows)
+    n_star = {}
+    for r in sorted(pick_rows, key=lambda r: r["cols"]):
+        d = n_star.setdefault(r["op"], {"analytic": None, "measured": None})
+        if r["analytic_cluster"] and d["analytic"] is None:
+            d["analytic"] = r["cols"]
+        if r["measured_cluster"] and d["measured"] is None:
+            d["measured"] = r["cols"]
+    return {"pairs": len(pick_rows), "sign_agreement": agree, "n_star": n_star}
 
 
 def run_e2e(C, torch, dev, jobs, shapes, stream, args):
