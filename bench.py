@@ -122,6 +122,8 @@ def algorithmic_bytes(rows, cols, op):
 
 def kernel_name(plan, C, cols=0, isz=4):
     if plan.path in (C.PATH_ONE_CTA, C.PATH_CLUSTER):
+        if plan.path == C.PATH_CLUSTER and plan.fill_share > 0:
+            return "k_ring_tm+fill" if plan.retain == C.RETAIN_TMEM else "k_ring+fill"
         if plan.retain == C.RETAIN_TMEM:
             return "k_ring_tm"
         if plan.retain == C.RETAIN_AUTO:  # the library's AUTO rule for the norms with FP32 output
@@ -172,12 +174,22 @@ def time_events(fn, reps, warm=1):
 
 
 def candidates(C, op, x, y, g, b):
+    import torch
+    sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     out = []
     for P in (1, 2, 4, 8, 16):
+        legal = []
         for retain, tag in ((C.RETAIN_SMEM, ""), (C.RETAIN_TMEM, "_tm")):
             p = C.make_plan(C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P, retain=retain)
             if C.plan_check(op, x, y, p, gamma=g, beta=b) == C.OK:
-                out.append((f"{'one_cta' if P == 1 else 'cluster'}{'' if P == 1 else P}{tag}", p))
+                name = f"{'one_cta' if P == 1 else 'cluster'}{'' if P == 1 else P}{tag}"
+                out.append((name, p))
+                legal.append((name, retain, p))
+        if P > 1 and legal:  # fills of a cluster plan that leaves SMs idle
+            name, retain, p = legal[-1]
+            if sm - P * C.max_clusters(op, x, y, p, gamma=g, beta=b) >= 16:
+                for f in (0.15, 0.2, 0.3, 0.4):
+                    out.append((f"{name}_f{f}", C.make_plan(C.PATH_CLUSTER, P, retain=retain, fill_share=f)))
     for G in (1, 2, 4, 8):
         p = C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)
         out.append((f"two_pass_g{G}", p))
@@ -384,7 +396,7 @@ def run_ours(args):
         ms = statistics.median(per[s][k][0].elapsed_time(per[s][k][1]) for s in range(args.steps))
         per_job.append({"op": j["name"], "cols": j["cols"], "plan": C.PATH_NAMES[j["plan"].path],
                         "P": j["plan"].cluster_size, "G": j["plan"].ctas_per_row, "source": j["plan"].source,
-                        "kernel": j["kernel"],
+                        "kernel": j["kernel"], "fill_share": round(j["plan"].fill_share, 3),
                         "ms": round(ms, 4), "GBps": round(j["bytes"] / ms / 1e6, 1)})
 
     # ---- speedup vs best non-DSMEM path and pick accuracy (every candidate timed)

@@ -151,6 +151,13 @@ credit_status credit_rmsnorm(const void *in, void *out, int64_t rows, int64_t co
  *                 (>= chunks of one slice; 0 = default)
  *   chunk_bytes   staged paths: bytes per chunk (multiple of 16; 0 = default)
  *   retain        staged paths: credit_retain (0 = AUTO)
+ *   fill_share    CLUSTER only.  A cluster of P CTAs is placed inside one GPC, so
+ *                 at P = 8 / 16 only 15 / 7 clusters fit on a GB300 (120 / 112 of
+ *                 152 SMs).  With fill_share = f > 0 the last round(f * rows) rows
+ *                 run on the split two-pass path (fill_g CTAs per row) on a
+ *                 library stream that forks from and joins back into the
+ *                 caller's stream, and fills the SMs the clusters leave idle.
+ *                 The project's addition; the paper runs one path per launch.
  *   smem_bytes    dynamic shared memory per CTA (S_CTA of Eq. 3), output
  *   predicted_us  model latency for the whole call (0 when not modelled)
  *   source        0 analytic model, 1 learned model, 2 forced by caller or
@@ -168,6 +175,9 @@ typedef struct {
     int64_t smem_bytes;
     float predicted_us;
     int32_t source;
+    float fill_share;      /* CLUSTER: share of the rows run by the split two-pass path on the SMs the
+                              clusters leave idle, concurrently (0 = none; at most 0.9) */
+    int32_t fill_g;        /* CTAs per row of that two-pass part (0 = by row width) */
 } credit_plan_t;
 
 /*
@@ -230,6 +240,17 @@ credit_status credit_run_ex(const credit_args *args, const credit_plan_t *plan,
  *   returns  credit_run_ex's statuses; CREDIT_ERR_CUDA if a copy failed
  */
 credit_status credit_run_host(const credit_args *args, const credit_plan_t *plan);
+
+/*
+ * credit_max_clusters -- how many clusters (CTAs for the one-CTA path) of a
+ * staged plan can be resident at once on the current device for these
+ * arguments (cudaOccupancyMaxActiveClusters of the kernel the plan selects,
+ * with its shared-memory request).  0 if the plan is not a legal staged plan
+ * (Eq. 3, scheduling) or not a staged plan at all.  Launches nothing.
+ * P * credit_max_clusters() below the SM count means the cluster path leaves
+ * SMs idle, which fill_share can use.
+ */
+int32_t credit_max_clusters(const credit_args *args, const credit_plan_t *plan);
 
 /*
  * credit_plan_check -- CREDIT_OK if `plan` is legal for `args` on the current
@@ -352,23 +373,25 @@ credit_status credit_load_model(const char *path);
 
 /* ------------------------------------------------------------------ learned model
  * A 3 x 64 ReLU MLP predicting log2 of a candidate plan's latency (us) from
- * 19 features (credit_mlp_features), trained on the GPU by the library's own
+ * 20 features (credit_mlp_features), trained on the GPU by the library's own
  * FP32 kernels (forward, backward, Adam; no tensor cores).  With
  * CREDIT_MODEL=learned, credit_plan picks the legal candidate with the
  * smallest predicted latency; the analytic model stays the fallback.  The
  * paper has no learned model; this is the project's addition.
  */
-#define CREDIT_MLP_FEATURES 19
+#define CREDIT_MLP_FEATURES 20
 int64_t credit_mlp_num_params(void);
-/* Features of candidate (path, P, G, retain) for (op, dtypes, rows, cols) into
- * out[19]: log2 rows, log2 cols, input dtype one-hot, op one-hot, path one-hot
- * (one-CTA, two-pass, cluster), log2 P, log2 G, log2 algorithmic bytes,
- * output bytes per element, log2 input bytes per CTA, log2 CTAs per SM, and
- * 1 when a staged path retains the slice in tensor memory (retain =
- * CREDIT_RETAIN_TMEM; AUTO and SMEM give 0). */
+/* Features of candidate (path, P, G, retain, fill_share) for (op, dtypes, rows,
+ * cols) into out[20]: log2 rows, log2 cols, input dtype one-hot, op one-hot,
+ * path one-hot (one-CTA, two-pass, cluster), log2 P, log2 G, log2 algorithmic
+ * bytes, output bytes per element, log2 input bytes per CTA, log2 CTAs per
+ * SM, 1 when a staged path retains the slice in tensor memory (retain =
+ * CREDIT_RETAIN_TMEM; AUTO and SMEM give 0), and the fill share of a cluster
+ * plan (0 for the other paths).  fill_share outside [0, 1]:
+ * CREDIT_ERR_INVALID_ARG. */
 credit_status credit_mlp_features(int32_t op, int32_t in_dtype, int32_t out_dtype, int64_t rows, int64_t cols,
-                                  int32_t path, int32_t P, int32_t G, int32_t retain, float *out);
-/* Train from scratch on n host samples (X n x 19, y = log2 us): minibatch
+                                  int32_t path, int32_t P, int32_t G, int32_t retain, float fill_share, float *out);
+/* Train from scratch on n host samples (X n x 20, y = log2 us): minibatch
  * Adam on the MSE of standardised targets; He-initialised from `seed`.
  * loss_curve (NULL or `epochs` floats) gets the mean training loss per epoch. */
 credit_status credit_mlp_train(const float *X, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,

@@ -38,7 +38,8 @@ class CreditError(RuntimeError):
 class PlanT(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("cluster_size", ctypes.c_int32), ("ctas_per_row", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("ring_chunks", ctypes.c_int32), ("chunk_bytes", ctypes.c_int32),
-                ("reducer_threads", ctypes.c_int32), ("retain", ctypes.c_int32), ("smem_bytes", ctypes.c_int64), ("predicted_us", ctypes.c_float), ("source", ctypes.c_int32)]
+                ("reducer_threads", ctypes.c_int32), ("retain", ctypes.c_int32), ("smem_bytes", ctypes.c_int64), ("predicted_us", ctypes.c_float), ("source", ctypes.c_int32),
+                ("fill_share", ctypes.c_float), ("fill_g", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,6 +93,8 @@ def lib() -> ctypes.CDLL:
             L.credit_set_trace.argtypes = [vp, i64]
             L.credit_plan_check.restype = i32
             L.credit_plan_check.argtypes = [ctypes.POINTER(ArgsT), ctypes.POINTER(PlanT)]
+            L.credit_max_clusters.restype = i32
+            L.credit_max_clusters.argtypes = [ctypes.POINTER(ArgsT), ctypes.POINTER(PlanT)]
             L.credit_device_error.restype = i32
             L.credit_device_error.argtypes = [vp]
             L.credit_slice_capacity.restype = i64
@@ -159,7 +162,7 @@ def _extra_prototypes(L):
     fp = ctypes.POINTER(ctypes.c_float)
     L.credit_mlp_num_params.restype = i64
     L.credit_mlp_features.restype = i32
-    L.credit_mlp_features.argtypes = [i32, i32, i32, i64, i64, i32, i32, i32, i32, fp]
+    L.credit_mlp_features.argtypes = [i32, i32, i32, i64, i64, i32, i32, i32, i32, ctypes.c_float, fp]
     L.credit_mlp_train.restype = i32
     L.credit_mlp_train.argtypes = [fp, fp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64, fp]
     L.credit_mlp_predict.restype = i32
@@ -242,7 +245,8 @@ def rmsnorm(x, out=None, stream=None):
 
 
 def make_plan(path: int, cluster_size: int = 1, ctas_per_row: int = 1, threads: int = 0, ring_chunks: int = 0,
-              chunk_bytes: int = 0, reducer_threads: int = 0, retain: int = 0) -> PlanT:
+              chunk_bytes: int = 0, reducer_threads: int = 0, retain: int = 0, fill_share: float = 0.0,
+              fill_g: int = 0) -> PlanT:
     p = PlanT()
     p.path = path
     p.cluster_size = cluster_size
@@ -252,6 +256,8 @@ def make_plan(path: int, cluster_size: int = 1, ctas_per_row: int = 1, threads: 
     p.chunk_bytes = chunk_bytes
     p.reducer_threads = reducer_threads
     p.retain = retain
+    p.fill_share = fill_share
+    p.fill_g = fill_g
     return p
 
 
@@ -288,6 +294,12 @@ def plan_check(op: int, x, out, plan: PlanT, **kw) -> int:
     """credit_plan_check: OK if `plan` is legal for these arguments."""
     a = make_args(op, x, out, **kw)
     return lib().credit_plan_check(ctypes.byref(a), ctypes.byref(plan))
+
+
+def max_clusters(op: int, x, out, plan: PlanT, **kw) -> int:
+    """credit_max_clusters: co-resident clusters (CTAs for one-CTA) of a staged plan; 0 if illegal."""
+    a = make_args(op, x, out, **kw)
+    return int(lib().credit_max_clusters(ctypes.byref(a), ctypes.byref(plan)))
 
 
 def run_ex(op: int, x, out, *, plan: PlanT | None = None, stream=None, **kw) -> int:
@@ -395,7 +407,7 @@ class Ragged:
             pass
 
 
-MLP_FEATURES = 19
+MLP_FEATURES = 20
 
 
 def _fptr(a):
@@ -408,10 +420,11 @@ def mlp_num_params() -> int:
     return int(lib().credit_mlp_num_params())
 
 
-def mlp_features(op, in_dtype, out_dtype, rows, cols, path, P, G, retain=0):
+def mlp_features(op, in_dtype, out_dtype, rows, cols, path, P, G, retain=0, fill_share=0.0):
     import numpy as np
     f = np.zeros(MLP_FEATURES, dtype=np.float32)
-    _check(lib().credit_mlp_features(op, in_dtype, out_dtype, rows, cols, path, P, G, retain, _fptr(f)),
+    _check(lib().credit_mlp_features(op, in_dtype, out_dtype, rows, cols, path, P, G, retain, float(fill_share),
+                                     _fptr(f)),
            "credit_mlp_features")
     return f
 

@@ -36,6 +36,8 @@ struct DeviceState {
     DeviceInfo info{};
     float *ws = nullptr;
     unsigned *err = nullptr;
+    cudaStream_t side = nullptr;               // fill work of cluster plans (fill_share > 0)
+    cudaEvent_t fork = nullptr, join = nullptr;
     std::map<const void *, bool> attr_done;
     std::map<std::tuple<const void *, int, int, long long>, int> clusters;  // max active clusters
 };
@@ -386,6 +388,9 @@ credit_status credit_init(int device) {
     if ((e = cudaMalloc(&d.ws, kWorkspaceFloats * sizeof(float))) != cudaSuccess) return cuda_status(e);
     if ((e = cudaMalloc(&d.err, 64)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaMemset(d.err, 0, 64)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaStreamCreateWithFlags(&d.side, cudaStreamNonBlocking)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaEventCreateWithFlags(&d.join, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
     info.ws_floats = kWorkspaceFloats;
     d.info = info;
     d.ready.store(true);
@@ -487,6 +492,10 @@ credit_status check_plan(int device, const credit_args *a, const credit_plan_t *
     const int threads = p->threads;
     if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32)) return CREDIT_ERR_UNSUPPORTED;
     (void)threads;
+    if (!(p->fill_share >= 0.0f && p->fill_share <= kMaxFillShare)) return CREDIT_ERR_UNSUPPORTED;
+    if (p->fill_share > 0.0f && (p->path != CREDIT_PATH_CLUSTER || p->fill_g < 0 || p->fill_g > 4096 ||
+                                 static_cast<size_t>(p->fill_g) * 4 > di->ws_floats))
+        return CREDIT_ERR_UNSUPPORTED;
     switch (p->path) {
     case CREDIT_PATH_ONE_CTA:
     case CREDIT_PATH_CLUSTER: {
@@ -573,6 +582,24 @@ static cudaError_t launch(const void *fn, dim3 grid, dim3 block, size_t smem, in
 
 std::atomic<long long> g_launch_count{0};
 
+// Rows of a cluster plan handed to the fill (the last ones); at least one row
+// stays on the cluster path.
+static long long fill_rows(const credit_plan_t *p, long long rows) {
+    if (p->path != CREDIT_PATH_CLUSTER || !(p->fill_share > 0.0f) || rows < 2) return 0;
+    long long n = static_cast<long long>(static_cast<double>(rows) * p->fill_share + 0.5);
+    if (n > rows - 1) n = rows - 1;
+    return n < 0 ? 0 : n;
+}
+
+// CTAs per row of the fill's two-pass part when the plan leaves it open: one
+// per 512 KiB of row (1..8), so that each CTA's reread slice stays small.
+static int fill_split(long long cols, int isz) {
+    long long g = cols * isz / (512LL << 10);
+    if (g < 1) g = 1;
+    if (g > 8) g = 8;
+    return static_cast<int>(g);
+}
+
 credit_status run_with_plan(int device, const credit_args *a, const credit_plan_t *p, cudaStream_t s) {
     DeviceState &d = g_dev[device];
     const int tin = a->in_dtype;
@@ -602,17 +629,44 @@ credit_status run_with_plan(int device, const credit_args *a, const credit_plan_
                          "affine=%d%s smem=%lld\n",
                          rc.tmem ? "_tm" : "", a->op, P, ncl, maxc, rc.threads, rc.reducers, rc.chunk, rc.ring,
                          rc.affine, rc.affine_resident ? "(resident)" : "", rc.smem);
+        // fill: the last n_fill rows go to the split two-pass path on the side
+        // stream, which forks from s before the cluster launch and joins after
+        const long long n_fill = fill_rows(p, rows);
+        const long long n_cl = rows - n_fill;
+        cudaError_t e;
+        if (n_fill > 0 && (e = cudaEventRecord(d.fork, s)) != cudaSuccess) return cuda_status(e);
         RowArgs r = base;
+        r.rows = n_cl;
         r.chunk_bytes = rc.chunk;
         r.ring = rc.ring;
         r.reducers = rc.reducers;
         r.affine = rc.affine;
         r.affine_resident = rc.affine_resident;
+        const long long ncl_run = n_cl < ncl ? n_cl : ncl;
         void *args[] = {&r};
-        cudaError_t e = launch(fn, dim3(static_cast<unsigned>(P * ncl)), dim3(rc.threads),
-                               static_cast<size_t>(rc.smem), P, s, args);
+        e = launch(fn, dim3(static_cast<unsigned>(P * ncl_run)), dim3(rc.threads), static_cast<size_t>(rc.smem), P,
+                   s, args);
         if (e != cudaSuccess) return cuda_status(e);
         g_launch_count.fetch_add(1);
+        if (n_fill > 0) {
+            if ((e = cudaStreamWaitEvent(d.side, d.fork, 0)) != cudaSuccess) return cuda_status(e);
+            credit_args fa = *a;
+            const long long ld_in = a->ld_in ? a->ld_in : a->cols, ld_out = a->ld_out ? a->ld_out : a->cols;
+            fa.in = static_cast<const unsigned char *>(a->in) + n_cl * ld_in * isz;
+            fa.out = lse ? static_cast<void *>(static_cast<unsigned char *>(a->out) + n_cl * 4)
+                         : static_cast<void *>(static_cast<unsigned char *>(a->out) + n_cl * ld_out * osz);
+            if (a->in_scale) fa.in_scale = a->in_scale + n_cl;
+            if (a->out_scale) fa.out_scale = a->out_scale + n_cl;
+            fa.rows = n_fill;
+            credit_plan_t fp{};
+            fp.path = CREDIT_PATH_TWO_PASS;
+            fp.cluster_size = 1;
+            fp.ctas_per_row = p->fill_g > 0 ? p->fill_g : fill_split(a->cols, isz);
+            const credit_status st2 = run_with_plan(device, &fa, &fp, d.side);
+            if (st2 != CREDIT_OK) return st2;
+            if ((e = cudaEventRecord(d.join, d.side)) != cudaSuccess) return cuda_status(e);
+            if ((e = cudaStreamWaitEvent(s, d.join, 0)) != cudaSuccess) return cuda_status(e);
+        }
         return CREDIT_OK;
     }
 
@@ -708,6 +762,20 @@ credit_status credit_set_trace(void *device_buf, int64_t bytes) {
     g_trace_buf = static_cast<unsigned long long *>(device_buf);
     g_trace_rows = static_cast<int>(bytes / per_row);
     return CREDIT_OK;
+}
+
+int32_t credit_max_clusters(const credit_args *args, const credit_plan_t *plan) {
+    if (!plan || validate_args(args) != CREDIT_OK) return 0;
+    if (plan->path != CREDIT_PATH_ONE_CTA && plan->path != CREDIT_PATH_CLUSTER) return 0;
+    int dev = 0;
+    if (ensure_init(&dev, nullptr) != CREDIT_OK) return 0;
+    if (check_plan(dev, args, plan) != CREDIT_OK) return 0;
+    const DeviceInfo *di = device_info(dev);
+    const int P = plan->path == CREDIT_PATH_ONE_CTA ? 1 : plan->cluster_size;
+    RingCfg rc;
+    if (!ring_config_for(*di, args, dtype_size(args->in_dtype), P, plan, &rc)) return 0;
+    const int tout = args->op == OP_LSE ? DT_F32 : args->out_dtype;
+    return ring_max_clusters(dev, args->op, args->in_dtype, tout, P, rc.threads, rc.smem, rc.tmem != 0);
 }
 
 credit_status credit_plan_check(const credit_args *args, const credit_plan_t *plan) {

@@ -45,6 +45,7 @@ int ring_max_clusters(int device, int op, int tin, int tout, int P, int threads,
 int affine_arrays(const credit_args *a);
 int affine_arrays_aligned(const credit_args *a);
 extern bool g_auto_retain_tmem;
+constexpr float kMaxFillShare = 0.9f;  // largest fill_share a cluster plan may carry
 credit_status validate_args(const credit_args *a);
 credit_status check_plan(int device, const credit_args *a, const credit_plan_t *p);
 credit_status run_with_plan(int device, const credit_args *a, const credit_plan_t *p, cudaStream_t s);

@@ -29,7 +29,11 @@ namespace credit {
 
 namespace {
 
-constexpr int kIn = 19, kH = 64;
+constexpr int kIn = 20, kH = 64;
+// fill candidates of cluster plans that leave SMs idle (share of the rows)
+constexpr float kFillShares[] = {0.15f, 0.2f, 0.3f, 0.4f};
+constexpr int kFillMinIdle = 16;
+constexpr long long kFillMinRows = 64;
 // flat layout: W1 (64x18), b1, W2 (64x64), b2, W3 (64x64), b3, W4 (1x64), b4
 constexpr int kOffW[4] = {0, kH * kIn + kH, kH * kIn + kH + kH * kH + kH, kH * kIn + kH + 2 * (kH * kH + kH)};
 constexpr int kFanIn[4] = {kIn, kH, kH, kH};
@@ -203,7 +207,7 @@ void host_forward(const Model &mdl, const float *xin, float *yout_log2us) {
 // log2 of the algorithmic bytes, output bytes per element, log2 of the input
 // bytes one CTA handles, log2 of the CTAs per SM (152 SMs) the rows need.
 void mlp_features(int op, int tin, int tout, long long rows, long long cols, int path, int P, int G, int retain_tm,
-                  float *f) {
+                  float fill, float *f) {
     std::memset(f, 0, kIn * sizeof(float));
     f[0] = std::log2(static_cast<float>(rows));
     f[1] = std::log2(static_cast<float>(cols));
@@ -220,6 +224,7 @@ void mlp_features(int op, int tin, int tout, long long rows, long long cols, int
     f[16] = static_cast<float>(std::log2(static_cast<double>(cols) * dtype_size(tin) / split + 1.0));
     f[17] = static_cast<float>(std::log2(static_cast<double>(rows) * split / 152.0));
     f[18] = retain_tm ? 1.0f : 0.0f;
+    f[19] = fill;
 }
 
 static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin,
@@ -245,9 +250,9 @@ static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long lon
     }
     float best = 1e30f;
     credit_plan_t bp{};
-    auto consider = [&](int path, int P, int G, long long smem, int retain) {
+    auto consider = [&](int path, int P, int G, long long smem, int retain, float fill) {
         float f[kIn], y;
-        mlp_features(op, tin, tout, rows, cols, path, P, G, retain == CREDIT_RETAIN_TMEM, f);
+        mlp_features(op, tin, tout, rows, cols, path, P, G, retain == CREDIT_RETAIN_TMEM, fill, f);
         host_forward(mdl, f, &y);
         if (y < best) {
             best = y;
@@ -257,6 +262,7 @@ static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long lon
             bp.ctas_per_row = path == CREDIT_PATH_TWO_PASS ? G : P;
             bp.smem_bytes = smem;
             bp.retain = retain;
+            bp.fill_share = fill;
             bp.predicted_us = std::exp2(y);
             bp.source = 1;
         }
@@ -266,21 +272,29 @@ static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long lon
         if (op == 1 && P == 1) continue;
         if (P > 1 && !allow_cluster) continue;
         const int path = P == 1 ? CREDIT_PATH_ONE_CTA : CREDIT_PATH_CLUSTER;
+        // a cluster plan that leaves >= kFillMinIdle SMs idle also comes with a
+        // fill of the last rows by the split two-pass path on those SMs
+        auto with_fills = [&](long long smem, int retain, int maxc) {
+            consider(path, P, P, smem, retain, 0.0f);
+            if (P > 1 && rows >= kFillMinRows && di.sm_count - P * maxc >= kFillMinIdle)
+                for (float f : kFillShares) consider(path, P, P, smem, retain, f);
+        };
         RingCfg rc;
+        int maxc = 0;
         if (ring_config(di, cols, isz, P, 0, 0, 0, 0, 0, &rc) &&
-            ring_max_clusters(device, op, tin, tout, P, rc.threads, rc.smem) > 0)
-            consider(path, P, P, rc.smem, CREDIT_RETAIN_SMEM);
+            (maxc = ring_max_clusters(device, op, tin, tout, P, rc.threads, rc.smem)) > 0)
+            with_fills(rc.smem, CREDIT_RETAIN_SMEM, maxc);
         const bool tm_op = op != 1 && !(tout == 2 && (op == 2 || op == 3));
         if (tm_op && ring_config_tm(di, cols, isz, P, 0, 0, 0, &rc) &&
-            ring_max_clusters(device, op, tin, tout, P, rc.threads, rc.smem, true) > 0)
-            consider(path, P, P, rc.smem, CREDIT_RETAIN_TMEM);
+            (maxc = ring_max_clusters(device, op, tin, tout, P, rc.threads, rc.smem, true)) > 0)
+            with_fills(rc.smem, CREDIT_RETAIN_TMEM, maxc);
     }
     // two-pass: G in {1, 2, 4, 8} with >= 1024 16-byte groups per CTA, and the split rule's G
     const long long groups = cols * isz / 16;
     for (int G : {1, 2, 4, 8})
-        if (G == 1 || groups / G >= 1024) consider(CREDIT_PATH_TWO_PASS, 1, G, 0, CREDIT_RETAIN_AUTO);
+        if (G == 1 || groups / G >= 1024) consider(CREDIT_PATH_TWO_PASS, 1, G, 0, CREDIT_RETAIN_AUTO, 0.0f);
     const int Gs = two_pass_split(di.sm_count, rows, cols, isz);
-    if (Gs > 1 && Gs != 2 && Gs != 4 && Gs != 8) consider(CREDIT_PATH_TWO_PASS, 1, Gs, 0, CREDIT_RETAIN_AUTO);
+    if (Gs > 1 && Gs != 2 && Gs != 4 && Gs != 8) consider(CREDIT_PATH_TWO_PASS, 1, Gs, 0, CREDIT_RETAIN_AUTO, 0.0f);
     *p = bp;
     return true;
 }
@@ -294,12 +308,13 @@ extern "C" {
 int64_t credit_mlp_num_params(void) { return kParams; }
 
 credit_status credit_mlp_features(int32_t op, int32_t in_dtype, int32_t out_dtype, int64_t rows, int64_t cols,
-                                  int32_t path, int32_t P, int32_t G, int32_t retain, float *out) {
+                                  int32_t path, int32_t P, int32_t G, int32_t retain, float fill_share, float *out) {
     if (!out || op < 0 || op > 3 || in_dtype < 0 || in_dtype > 2 || out_dtype < 0 || out_dtype > 2 || rows <= 0 ||
-        cols <= 0 || path < 0 || path > 2 || retain < 0 || retain > 2)
+        cols <= 0 || path < 0 || path > 2 || retain < 0 || retain > 2 || !(fill_share >= 0.0f && fill_share <= 1.0f))
         return CREDIT_ERR_INVALID_ARG;
     mlp_features(op, in_dtype, op == 1 ? 0 : out_dtype, rows, cols, path, P, G,
-                 path != CREDIT_PATH_TWO_PASS && retain == CREDIT_RETAIN_TMEM, out);
+                 path != CREDIT_PATH_TWO_PASS && retain == CREDIT_RETAIN_TMEM,
+                 path == CREDIT_PATH_CLUSTER ? fill_share : 0.0f, out);
     return CREDIT_OK;
 }
 

@@ -2,7 +2,8 @@
 
 Times every legal candidate plan (one-CTA and cluster P in {2, 4, 8, 16}, each
 with the slice retained in shared memory and, where that applies, in tensor
-memory; two-pass G in {1, 2, 4, 8} and the split factor) of a seeded set of shapes (rows
+memory; cluster plans that leave SMs idle also with fill shares 0.15-0.4;
+two-pass G in {1, 2, 4, 8} and the split factor) of a seeded set of shapes (rows
 2^U(6,16), cols 2^U(10,20), dtype and op uniform, I/O <= a byte cap;
 median of `reps` CUDA-event timings), splits the shapes 80/20, trains the
 latency MLP on the GPU with the library's kernels, and reports, on the
@@ -31,17 +32,32 @@ from . import credit as C
 from . import synth
 
 DT_TORCH = {0: torch.float32, 1: torch.bfloat16, 2: torch.float8_e4m3fn}
+# fill candidates of cluster plans that leave at least FILL_MIN_IDLE SMs idle
+# (the library's learned planner offers the same shares)
+FILL_SHARES = (0.15, 0.2, 0.3, 0.4)
+FILL_MIN_IDLE = 16
+FILL_MIN_ROWS = 64
 
 
 def candidates(op, rows, cols, dtype, x, y, sc, osc, gamma, beta):
     out = []
     kw = dict(rows=rows, cols=cols, in_dtype=dtype, out_dtype=C.F32 if op == C.LOGSUMEXP else dtype,
               in_scale=sc, out_scale=osc, gamma=gamma, beta=beta)
+    sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     for P in (1, 2, 4, 8, 16):
+        legal = []
         for retain in (C.RETAIN_SMEM, C.RETAIN_TMEM):
             p = C.make_plan(C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P, retain=retain)
             if C.plan_check(op, x, y, p, **kw) == C.OK:
-                out.append((C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P, P, retain, p))
+                out.append((C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P, P, retain, 0.0, p))
+                legal.append((retain, p))
+        # fills of a cluster plan that leaves SMs idle (the tensor-memory tier when it applies)
+        if P > 1 and legal and rows >= FILL_MIN_ROWS:
+            retain, p = legal[-1]
+            if sm - P * C.max_clusters(op, x, y, p, **kw) >= FILL_MIN_IDLE:
+                for f in FILL_SHARES:
+                    out.append((C.PATH_CLUSTER, P, P, retain, f, C.make_plan(C.PATH_CLUSTER, P, retain=retain,
+                                                                              fill_share=f)))
     isz = {0: 4, 1: 2, 2: 1}[dtype]
     groups = cols * isz // 16
     Gs = [G for G in (1, 2, 4, 8) if G == 1 or groups // G >= 1024]
@@ -49,7 +65,7 @@ def candidates(op, rows, cols, dtype, x, y, sc, osc, gamma, beta):
     if g_auto > 1 and g_auto not in Gs:
         Gs.append(g_auto)
     for G in Gs:
-        out.append((C.PATH_TWO_PASS, 1, G, C.RETAIN_AUTO, C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)))
+        out.append((C.PATH_TWO_PASS, 1, G, C.RETAIN_AUTO, 0.0, C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)))
     return out, kw
 
 
@@ -106,12 +122,12 @@ def run_sweep(shapes, reps, cap_bytes, log=None):
         cands, kw = candidates(op, rows, cols, dt, x, y, scales[:rows], oscales[:rows],
                                gamma[:cols] if op in (2, 3) else None, beta[:cols] if op == 2 else None)
         times = []
-        for path, P, G, retain, plan in cands:
+        for path, P, G, retain, fill, plan in cands:
             us = time_plan(lambda: C.run_ex(op, x, y, plan=plan, **kw), reps)
-            times.append((path, P, G, retain, us))
-        for path, P, G, retain, us in times:
+            times.append((path, P, G, retain, fill, us))
+        for path, P, G, retain, fill, us in times:
             rows_out.append(dict(shape=si, op=op, dtype=dt, rows=rows, cols=cols, path=path, P=P, G=G,
-                                 retain=retain, us=us))
+                                 retain=retain, fill=fill, us=us))
         if log and si % 100 == 0:
             print(f"shape {si}/{len(shapes)} {time.time() - t0:.0f}s", file=log, flush=True)
     assert C.device_error() == C.OK
@@ -121,7 +137,7 @@ def run_sweep(shapes, reps, cap_bytes, log=None):
 def features_of(r):
     out_dt = C.F32 if r["op"] == C.LOGSUMEXP else r["dtype"]
     return C.mlp_features(r["op"], r["dtype"], out_dt, r["rows"], r["cols"], r["path"], r["P"], r["G"],
-                          r.get("retain", 0))
+                          r.get("retain", 0), r.get("fill", 0.0))
 
 
 def evaluate(rows, test_shapes):
@@ -154,7 +170,8 @@ def evaluate(rows, test_shapes):
             os.environ.pop("CREDIT_MODEL", None)
             match = [c for c in cand if c["path"] == p.path and (c["P"] == p.cluster_size if p.path != C.PATH_TWO_PASS
                                                                   else c["G"] == p.ctas_per_row)
-                     and (p.path == C.PATH_TWO_PASS or c.get("retain", 0) == p.retain)]
+                     and (p.path == C.PATH_TWO_PASS or c.get("retain", 0) == p.retain)
+                     and abs(c.get("fill", 0.0) - p.fill_share) < 1e-6]
             res[name] += ok(match[0]) if match else 0
         tp = [c for c in cand if c["path"] == C.PATH_TWO_PASS and c["G"] == 1]
         res["always_two_pass"] += ok(tp[0]) if tp else 0
@@ -192,9 +209,11 @@ def main(argv=None):
                 v = line.strip().split(",")
                 if len(v) == 9:  # timings from before the retention column: shared-memory staging
                     v = v[:8] + [str(C.RETAIN_SMEM if int(v[5]) != C.PATH_TWO_PASS else C.RETAIN_AUTO)] + v[8:]
-                sh, op, dt, r, c, path, P, G, retain, us = v
+                if len(v) == 10:  # before the fill column: no fill
+                    v = v[:9] + ["0"] + v[9:]
+                sh, op, dt, r, c, path, P, G, retain, fill, us = v
                 rows.append(dict(shape=int(sh), op=int(op), dtype=int(dt), rows=int(r), cols=int(c), path=int(path),
-                                 P=int(P), G=int(G), retain=int(retain), us=float(us)))
+                                 P=int(P), G=int(G), retain=int(retain), fill=float(fill), us=float(us)))
         shapes = shapes[:1 + max(r["shape"] for r in rows)]
     else:
         rows = run_sweep(shapes, args.reps, cap, log=sys.stderr)
@@ -227,10 +246,10 @@ def main(argv=None):
     if args.from_csv and os.path.abspath(args.from_csv) == os.path.abspath(csv_out):
         csv_out += ".new"
     with open(csv_out, "w") as f:
-        f.write("shape,op,dtype,rows,cols,path,P,G,retain,us\n")
+        f.write("shape,op,dtype,rows,cols,path,P,G,retain,fill,us\n")
         for r in rows:
             f.write(f"{r['shape']},{r['op']},{r['dtype']},{r['rows']},{r['cols']},{r['path']},{r['P']},{r['G']},"
-                    f"{r['retain']},{r['us']:.3f}\n")
+                    f"{r['retain']},{r['fill']:g},{r['us']:.3f}\n")
     summary = {"shapes": len(shapes), "timings": len(rows), "train_shapes": len(train), "test_shapes": n_test,
                "pick_rule": "pick within 5% of the measured best candidate", "pick_accuracy": acc,
                "train_loss_first_last": [float(curve[0]), float(curve[-1])], "sweep_s": round(t_sweep, 1),

@@ -76,6 +76,6 @@ def test_validation_rejects_bad_calls_without_touching_the_gpu(lib):
 
 
 def test_struct_layouts_match_the_header():
-    assert ctypes.sizeof(C.PlanT) == 48 and C.PlanT.smem_bytes.offset == 32
+    assert ctypes.sizeof(C.PlanT) == 56 and C.PlanT.smem_bytes.offset == 32 and C.PlanT.fill_g.offset == 52
     assert ctypes.sizeof(C.ArgsT) == 104
     assert C.ArgsT.eps.offset == 96 and C.ArgsT.in_scale.offset == 64
