@@ -391,12 +391,22 @@ int64_t credit_mlp_num_params(void);
  * CREDIT_ERR_INVALID_ARG. */
 credit_status credit_mlp_features(int32_t op, int32_t in_dtype, int32_t out_dtype, int64_t rows, int64_t cols,
                                   int32_t path, int32_t P, int32_t G, int32_t retain, float fill_share, float *out);
-/* Train from scratch on n host samples (X n x 20, y = log2 us): minibatch
+/* Train one network from scratch on n host samples (X n x 20, y = log2 us),
+ * replacing the loaded model: minibatch
  * Adam on the MSE of standardised targets; He-initialised from `seed`.
  * loss_curve (NULL or `epochs` floats) gets the mean training loss per epoch. */
 credit_status credit_mlp_train(const float *X, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,
                                uint64_t seed, float *loss_curve);
-/* Batched GPU inference: out[i] = predicted log2 us of feature row i. */
+/* An ensemble: `members` (1..16) networks trained as credit_mlp_train with
+ * seeds seed, seed + 1, ...; replaces the loaded model.  Predictions and the
+ * planner use the mean of the members' log2 latencies.  loss_curve is the
+ * first member's. */
+credit_status credit_mlp_train_ensemble(const float *X, const float *y, int64_t n, int32_t members, int32_t epochs,
+                                        int32_t batch, float lr, uint64_t seed, float *loss_curve);
+/* Members of the loaded model (0: none). */
+int32_t credit_mlp_members(void);
+/* Batched GPU inference: out[i] = predicted log2 us of feature row i (the
+ * members' mean). */
 credit_status credit_mlp_predict(const float *X, int64_t n, float *out);
 /* One GPU forward + backward with explicit parameters on raw inputs: MSE loss
  * and its gradient (host arrays; params and grad have credit_mlp_num_params()

@@ -165,6 +165,10 @@ def _extra_prototypes(L):
     L.credit_mlp_features.argtypes = [i32, i32, i32, i64, i64, i32, i32, i32, i32, ctypes.c_float, fp]
     L.credit_mlp_train.restype = i32
     L.credit_mlp_train.argtypes = [fp, fp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64, fp]
+    L.credit_mlp_train_ensemble.restype = i32
+    L.credit_mlp_train_ensemble.argtypes = [fp, fp, i64, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, fp]
+    L.credit_mlp_members.restype = i32
+    L.credit_mlp_members.argtypes = []
     L.credit_mlp_predict.restype = i32
     L.credit_mlp_predict.argtypes = [fp, i64, fp]
     L.credit_mlp_grad.restype = i32
@@ -437,6 +441,22 @@ def mlp_train(X, y, *, epochs=200, batch=256, lr=2e-3, seed=0):
     _check(lib().credit_mlp_train(_fptr(X), _fptr(y), X.shape[0], epochs, batch, lr, seed, _fptr(curve)),
            "credit_mlp_train")
     return curve
+
+
+def mlp_train_ensemble(X, y, *, members=5, epochs=200, batch=256, lr=2e-3, seed=0):
+    """credit_mlp_train_ensemble: `members` networks (seeds seed, seed+1, ...),
+    predictions averaged; returns the first member's loss curve."""
+    import numpy as np
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    curve = np.zeros(epochs, dtype=np.float32)
+    _check(lib().credit_mlp_train_ensemble(_fptr(X), _fptr(y), X.shape[0], members, epochs, batch, lr, seed,
+                                           _fptr(curve)), "credit_mlp_train_ensemble")
+    return curve
+
+
+def mlp_members() -> int:
+    return int(lib().credit_mlp_members())
 
 
 def mlp_predict(X):

@@ -1,8 +1,11 @@
 // credit_mlp.cu -- learned latency model: a 3 x 64 MLP trained on the GPU
 // with hand-written FP32 kernels (no tensor cores: the matrices are 64 wide).
 //
-// Input: 18 features of one (shape, dtype, op, candidate plan) (see
-// credit_mlp_features).  Output: predicted log2 of the latency in us.
+// Input: kIn features of one (shape, dtype, op, candidate plan) (see
+// credit_mlp_features).  Output: predicted log2 of the latency in us.  An
+// ensemble of independently initialised members predicts the mean of their
+// outputs (lower variance than one network, which matters when candidates
+// differ by a few percent).
 // Training: minibatch Adam on the mean squared error of standardised
 // targets; features and targets are standardised with the training set's
 // mean / standard deviation, kept with the weights.
@@ -34,7 +37,7 @@ constexpr int kIn = 20, kH = 64;
 constexpr float kFillShares[] = {0.15f, 0.2f, 0.3f, 0.4f};
 constexpr int kFillMinIdle = 16;
 constexpr long long kFillMinRows = 64;
-// flat layout: W1 (64x18), b1, W2 (64x64), b2, W3 (64x64), b3, W4 (1x64), b4
+// flat layout: W1 (64 x kIn), b1, W2 (64x64), b2, W3 (64x64), b3, W4 (1x64), b4
 constexpr int kOffW[4] = {0, kH * kIn + kH, kH * kIn + kH + kH * kH + kH, kH * kIn + kH + 2 * (kH * kH + kH)};
 constexpr int kFanIn[4] = {kIn, kH, kH, kH};
 constexpr int kFanOut[4] = {kH, kH, kH, 1};
@@ -46,8 +49,9 @@ struct Model {
     float fmean[kIn], fstd[kIn];     // feature standardisation
     float tmean = 0.0f, tstd = 1.0f;  // target standardisation
 };
-Model g_model;
+std::vector<Model> g_models;  // the ensemble (empty: no learned model)
 std::mutex g_mu;
+constexpr int kMaxMembers = 16;
 
 // ------------------------------------------------------------------ kernels
 // out[s][u] = act(b[u] + sum_k W[u][k] in[s][k]); one thread per (s, u)
@@ -242,18 +246,23 @@ bool learned_plan_no_cluster(const DeviceInfo &di, int device, int op, long long
 
 static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin,
                               int tout, bool allow_cluster, credit_plan_t *p) {
-    Model mdl;
+    std::vector<Model> ens;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_model.loaded) return false;
-        mdl = g_model;
+        if (g_models.empty()) return false;
+        ens = g_models;
     }
     float best = 1e30f;
     credit_plan_t bp{};
     auto consider = [&](int path, int P, int G, long long smem, int retain, float fill) {
-        float f[kIn], y;
+        float f[kIn], y = 0.0f;
         mlp_features(op, tin, tout, rows, cols, path, P, G, retain == CREDIT_RETAIN_TMEM, fill, f);
-        host_forward(mdl, f, &y);
+        for (const Model &m : ens) {
+            float ym;
+            host_forward(m, f, &ym);
+            y += ym;
+        }
+        y /= static_cast<float>(ens.size());
         if (y < best) {
             best = y;
             std::memset(&bp, 0, sizeof(bp));
@@ -347,9 +356,14 @@ credit_status credit_mlp_grad(const float *params, const float *X, const float *
 // Train from scratch: n samples (host X n x 16, targets = log2 us), minibatch
 // Adam.  loss_curve (may be NULL) receives the training MSE (standardised)
 // after each epoch.
-credit_status credit_mlp_train(const float *X, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,
-                               uint64_t seed, float *loss_curve) {
-    if (!X || !y || n < 2 || epochs < 1 || batch < 1) return CREDIT_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace credit {
+namespace {
+// Train one member from scratch (see credit_mlp_train); the model is returned
+// in *out, not installed.
+credit_status train_one(const float *X, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,
+                        uint64_t seed, float *loss_curve, Model *out) {
     Model mdl;
     // standardisation
     for (int k = 0; k < kIn; ++k) {
@@ -424,69 +438,110 @@ credit_status credit_mlp_train(const float *X, const float *y, int64_t n, int32_
     d.release();
     if (e != cudaSuccess) return CREDIT_ERR_CUDA;
     mdl.loaded = true;
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_model = mdl;
+    *out = mdl;
     return CREDIT_OK;
+}
+}  // namespace
+}  // namespace credit
+
+extern "C" {
+
+credit_status credit_mlp_train(const float *X, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,
+                               uint64_t seed, float *loss_curve) {
+    return credit_mlp_train_ensemble(X, y, n, 1, epochs, batch, lr, seed, loss_curve);
+}
+
+credit_status credit_mlp_train_ensemble(const float *X, const float *y, int64_t n, int32_t members, int32_t epochs,
+                                        int32_t batch, float lr, uint64_t seed, float *loss_curve) {
+    if (!X || !y || n < 2 || epochs < 1 || batch < 1 || members < 1 || members > kMaxMembers)
+        return CREDIT_ERR_INVALID_ARG;
+    std::vector<Model> ens(static_cast<size_t>(members));
+    for (int m = 0; m < members; ++m) {
+        const credit_status st = train_one(X, y, n, epochs, batch, lr, seed + static_cast<uint64_t>(m),
+                                           m == 0 ? loss_curve : nullptr, &ens[static_cast<size_t>(m)]);
+        if (st != CREDIT_OK) return st;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_models = ens;
+    return CREDIT_OK;
+}
+
+int32_t credit_mlp_members(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return static_cast<int32_t>(g_models.size());
 }
 
 // Batched inference on the GPU: predicted log2 us for n feature rows.
 credit_status credit_mlp_predict(const float *X, int64_t n, float *out) {
     if (!X || !out || n <= 0 || n > (1 << 22)) return CREDIT_ERR_INVALID_ARG;
-    Model mdl;
+    std::vector<Model> ens;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_model.loaded) return CREDIT_ERR_NOT_INITIALIZED;
-        mdl = g_model;
+        if (g_models.empty()) return CREDIT_ERR_NOT_INITIALIZED;
+        ens = g_models;
     }
-    std::vector<float> Xs(n * kIn);
-    for (int64_t i = 0; i < n; ++i)
-        for (int k = 0; k < kIn; ++k) Xs[i * kIn + k] = (X[i * kIn + k] - mdl.fmean[k]) / mdl.fstd[k];
     Dev d;
     if (!d.alloc(static_cast<int>(n))) {
         d.release();
         return CREDIT_ERR_CUDA;
     }
-    cudaMemcpy(d.p, mdl.p.data(), kParams * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(d.x, Xs.data(), Xs.size() * 4, cudaMemcpyHostToDevice);
-    d.forward(static_cast<int>(n));
-    cudaError_t e = cudaMemcpy(out, d.y, n * 4, cudaMemcpyDeviceToHost);
+    std::vector<float> Xs(n * kIn), ym(n);
+    for (int64_t i = 0; i < n; ++i) out[i] = 0.0f;
+    cudaError_t e = cudaSuccess;
+    for (const Model &mdl : ens) {
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = 0; k < kIn; ++k) Xs[i * kIn + k] = (X[i * kIn + k] - mdl.fmean[k]) / mdl.fstd[k];
+        cudaMemcpy(d.p, mdl.p.data(), kParams * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(d.x, Xs.data(), Xs.size() * 4, cudaMemcpyHostToDevice);
+        d.forward(static_cast<int>(n));
+        if ((e = cudaMemcpy(ym.data(), d.y, n * 4, cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+        for (int64_t i = 0; i < n; ++i) out[i] += ym[i] * mdl.tstd + mdl.tmean;
+    }
     d.release();
     if (e != cudaSuccess) return CREDIT_ERR_CUDA;
-    for (int64_t i = 0; i < n; ++i) out[i] = out[i] * mdl.tstd + mdl.tmean;
+    for (int64_t i = 0; i < n; ++i) out[i] /= static_cast<float>(ens.size());
     return CREDIT_OK;
 }
 
 credit_status credit_mlp_save(const char *path) {
-    Model mdl;
+    std::vector<Model> ens;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_model.loaded) return CREDIT_ERR_NOT_INITIALIZED;
-        mdl = g_model;
+        if (g_models.empty()) return CREDIT_ERR_NOT_INITIALIZED;
+        ens = g_models;
     }
     FILE *f = path ? std::fopen(path, "w") : nullptr;
     if (!f) return CREDIT_ERR_IO;
-    std::fprintf(f, "credit-mlp 1 %d %d %d\n", kIn, kH, kParams);
-    for (int k = 0; k < kIn; ++k) std::fprintf(f, "%.9g %.9g\n", mdl.fmean[k], mdl.fstd[k]);
-    std::fprintf(f, "%.9g %.9g\n", mdl.tmean, mdl.tstd);
-    for (int i = 0; i < kParams; ++i) std::fprintf(f, "%.9g\n", mdl.p[i]);
+    // version 2: the member count, then every member (standardisation, parameters)
+    std::fprintf(f, "credit-mlp 2 %d %d %d %d\n", kIn, kH, kParams, static_cast<int>(ens.size()));
+    for (const Model &mdl : ens) {
+        for (int k = 0; k < kIn; ++k) std::fprintf(f, "%.9g %.9g\n", mdl.fmean[k], mdl.fstd[k]);
+        std::fprintf(f, "%.9g %.9g\n", mdl.tmean, mdl.tstd);
+        for (int i = 0; i < kParams; ++i) std::fprintf(f, "%.9g\n", mdl.p[i]);
+    }
     return std::fclose(f) == 0 ? CREDIT_OK : CREDIT_ERR_IO;
 }
 
+// Reads version 1 (one network) and version 2 (an ensemble).
 credit_status credit_mlp_load(const char *path) {
     FILE *f = path ? std::fopen(path, "r") : nullptr;
     if (!f) return CREDIT_ERR_IO;
-    Model mdl;
-    int a = 0, b = 0, c = 0, v = 0;
-    bool ok = std::fscanf(f, "credit-mlp %d %d %d %d", &v, &a, &b, &c) == 4 && a == kIn && b == kH && c == kParams;
-    for (int k = 0; ok && k < kIn; ++k) ok = std::fscanf(f, "%f %f", &mdl.fmean[k], &mdl.fstd[k]) == 2;
-    if (ok) ok = std::fscanf(f, "%f %f", &mdl.tmean, &mdl.tstd) == 2;
-    mdl.p.resize(kParams);
-    for (int i = 0; ok && i < kParams; ++i) ok = std::fscanf(f, "%f", &mdl.p[i]) == 1;
+    int a = 0, b = 0, c = 0, v = 0, members = 1;
+    bool ok = std::fscanf(f, "credit-mlp %d %d %d %d", &v, &a, &b, &c) == 4 && a == kIn && b == kH && c == kParams &&
+              (v == 1 || v == 2);
+    if (ok && v == 2) ok = std::fscanf(f, "%d", &members) == 1 && members >= 1 && members <= kMaxMembers;
+    std::vector<Model> ens(ok ? static_cast<size_t>(members) : 0);
+    for (Model &mdl : ens) {
+        for (int k = 0; ok && k < kIn; ++k) ok = std::fscanf(f, "%f %f", &mdl.fmean[k], &mdl.fstd[k]) == 2;
+        if (ok) ok = std::fscanf(f, "%f %f", &mdl.tmean, &mdl.tstd) == 2;
+        mdl.p.resize(kParams);
+        for (int i = 0; ok && i < kParams; ++i) ok = std::fscanf(f, "%f", &mdl.p[i]) == 1;
+        mdl.loaded = ok;
+    }
     std::fclose(f);
     if (!ok) return CREDIT_ERR_IO;
-    mdl.loaded = true;
     std::lock_guard<std::mutex> lk(g_mu);
-    g_model = mdl;
+    g_models = ens;
     return CREDIT_OK;
 }
 

@@ -186,6 +186,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=15)
     ap.add_argument("--cap-gib", type=float, default=16.0)
     ap.add_argument("--epoch-grid", type=int, nargs="+", default=[50, 100, 200, 400, 800])
+    ap.add_argument("--members", type=int, default=5, help="ensemble size of the learned model")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data"))
     ap.add_argument("--calib", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
                                                     "gb300.calib"))
@@ -233,11 +234,11 @@ def main(argv=None):
     Xf, yf = xy(fit_set)
     val_acc = {}
     for ep in args.epoch_grid:
-        C.mlp_train(Xf, yf, epochs=ep, batch=256, lr=2e-3, seed=0)
+        C.mlp_train_ensemble(Xf, yf, members=args.members, epochs=ep, batch=256, lr=2e-3, seed=0)
         val_acc[ep] = evaluate(rows, val_set)[0]["learned"]
     epochs = max(args.epoch_grid, key=lambda e: (val_acc[e], -e))
     Xtr, ytr = xy(set(train))
-    curve = C.mlp_train(Xtr, ytr, epochs=epochs, batch=256, lr=2e-3, seed=0)
+    curve = C.mlp_train_ensemble(Xtr, ytr, members=args.members, epochs=epochs, batch=256, lr=2e-3, seed=0)
     t_train = time.time() - t1
     acc, n_test = evaluate(rows, test)
     os.makedirs(args.out, exist_ok=True)
@@ -254,7 +255,8 @@ def main(argv=None):
                "pick_rule": "pick within 5% of the measured best candidate", "pick_accuracy": acc,
                "train_loss_first_last": [float(curve[0]), float(curve[-1])], "sweep_s": round(t_sweep, 1),
                "epochs": epochs, "validation_accuracy_by_epochs": val_acc,
-               "train_s": round(t_train, 1), "reps": args.reps, "cap_gib": args.cap_gib}
+               "train_s": round(t_train, 1), "reps": args.reps, "cap_gib": args.cap_gib,
+               "members": args.members}
     with open(os.path.join(args.out, "sweep_gb300_summary.json"), "w") as f:
         json.dump(summary, f, indent=1)
     print(json.dumps(summary))

@@ -54,3 +54,24 @@ def test_save_and_load_roundtrip(tmp_path):
     C.mlp_load(path)
     b = C.mlp_predict(X[:64])
     assert np.allclose(a, b, rtol=1e-5, atol=1e-5)
+
+
+def test_ensemble_is_the_mean_of_its_members(tmp_path):
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((1024, C.MLP_FEATURES)).astype(np.float32)
+    y = (X[:, 0] - 2 * X[:, 3]).astype(np.float32)
+    members = []
+    for seed in (7, 8, 9):
+        C.mlp_train(X, y, epochs=8, batch=128, seed=seed)
+        members.append(C.mlp_predict(X[:64]))
+    C.mlp_train_ensemble(X, y, members=3, epochs=8, batch=128, seed=7)
+    assert C.mlp_members() == 3
+    ens = C.mlp_predict(X[:64])
+    assert np.allclose(ens, np.mean(members, axis=0), rtol=1e-4, atol=1e-4)
+    path = str(tmp_path / "e.mlp")
+    C.mlp_save(path)
+    C.mlp_train(X, -y, epochs=2, batch=128, seed=1)  # one different network
+    assert C.mlp_members() == 1
+    C.mlp_load(path)
+    assert C.mlp_members() == 3
+    assert np.allclose(C.mlp_predict(X[:64]), ens, rtol=1e-5, atol=1e-5)
