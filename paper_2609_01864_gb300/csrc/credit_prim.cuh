@@ -204,6 +204,16 @@ __device__ __forceinline__ void tm_ld16(uint32_t taddr, uint32_t (&r)[16]) {
                  : "memory");
 }
 
+// Issue-only store.  tcgen05.st reads its source registers when it issues;
+// tm_wait_st() then waits for every store this thread issued (before the
+// TMEM words are handed to another warp).
+__device__ __forceinline__ void tm_st16_issue(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+                 : "memory");
+}
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // ------------------------------------------------------------ math
 // 2^x on the SFU (ex2.approx, subnormal results kept).  exp(x) = 2^(x*log2 e).
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -212,6 +222,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 constexpr float kLog2e = 1.4426950408889634f;
+// 1/x on the SFU (rcp.approx: relative error below 2^-22 for normal x; one
+// instruction, no special-case branch).  The counts it inverts are positive
+// integers below 2^24.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float exp_fast(float x) { return ex2_approx(x * kLog2e); }
 
 // ------------------------------------------------------------ element formats

@@ -344,8 +344,9 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
                         acc.add(f);
                     }
                 }
-                tm_st16(tb + static_cast<uint32_t>(k * kTmColsPerChunk), w);
+                tm_st16_issue(tb + static_cast<uint32_t>(k * kTmColsPerChunk), w);
             }
+            tm_wait_st();  // the row's TMEM stores, complete before the handoff below
             const long long n_head = (c == 0 && tid == 0) ? g.s.h0 : 0;
             const long long n_tail = (c == P - 1 && tid == Tr - 1) ? g.s.t0 : 0;
             for (int e = 0; e < 2; ++e)

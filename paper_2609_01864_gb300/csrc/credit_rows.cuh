@@ -248,8 +248,8 @@ template <> struct Stream<OP_LN> {
     float K = 0.0f, s1 = 0.0f, s2 = 0.0f;
     bool has = false;
     // Chan's merge of (nb, mb, m2b) into this state.  The two quotients use
-    // one correctly rounded reciprocal of the merged count (<= 1.5 ulp each
-    // instead of two IEEE divisions on the reduction's critical path).
+    // one SFU reciprocal of the merged count (a few ulp each instead of two
+    // IEEE divisions on the reduction's critical path).
     __device__ __forceinline__ void merge3(float nb, float mb, float m2b) {
         if (nb == 0.0f) return;
         if (n == 0.0f) {
@@ -259,7 +259,7 @@ template <> struct Stream<OP_LN> {
             return;
         }
         const float nn = n + nb;
-        const float r = __frcp_rn(nn);
+        const float r = rcp_approx(nn);
         const float d = mb - mu;
         const float wb = nb * r;
         mu += d * wb;
@@ -286,7 +286,7 @@ template <> struct Stream<OP_LN> {
     // (n, K, s1, s2) -> (n, mean, M2); call once before merging
     __device__ __forceinline__ void finish() {
         if (n > 0.0f) {
-            const float q = s1 * __frcp_rn(n);
+            const float q = s1 * rcp_approx(n);
             mu = K + q;
             m2 = fmaxf(s2 - s1 * q, 0.0f);
         }
