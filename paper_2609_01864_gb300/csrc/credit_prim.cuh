@@ -61,6 +61,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait for phase `parity` of `bar`.  Returns false (and flags the
 // error word) if the phase did not complete within kWaitLimitNs.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned *err) {
@@ -68,6 +79,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     const unsigned long long t0 = global_timer_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
+            if (err) atomicOr(err, ERR_TMA_TIMEOUT);
+            return false;
+        }
+    }
+}
+// The same wait with acquire semantics at cluster scope: for mbarriers that
+// peers complete with st.async (the exchange), so that the pushed partials
+// are read after the pushes that completed the phase.
+__device__ __forceinline__ bool mbar_wait_bounded_cluster(uint64_t *bar, uint32_t parity, unsigned *err) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    const unsigned long long t0 = global_timer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
         if ((it & 255u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
             if (err) atomicOr(err, ERR_TMA_TIMEOUT);
             return false;
@@ -136,6 +161,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 __device__ __forceinline__ void fence_acq_rel_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+// Release fence at cluster scope restricted to this CTA's shared memory: the
+// thread's earlier shared::cta accesses (and those ordered before them by
+// CTA-scope synchronisation) become ordered before its later release patterns
+// at cluster scope -- here, before the st.async that pushes a partial into a
+// peer, which is what keeps a peer's next push from overtaking this CTA's
+// reads of its own exchange slots.  Far cheaper than fence.acq_rel.cluster,
+// which also drains global-memory operations.
+__device__ __forceinline__ void fence_release_smem_cluster() {
+    asm volatile("fence.release.sync_restrict::shared::cta.cluster;" ::: "memory");
+}
 // Named barrier over the first `nthreads` threads (a multiple of 32).
 __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");

@@ -115,14 +115,14 @@ __device__ __forceinline__ Stats exchange_combine(int op, float2 part, float *sl
                 mine[0] = part.x;
                 mine[1] = part.y;
             } else {
-                fence_acq_rel_cluster();
+                fence_release_smem_cluster();  // this CTA's earlier reads of the slots first
                 st_async_v2f32(mapa_shared(smem_addr(mine), tid), part.x, part.y,
                                mapa_shared(smem_addr(&xbar[par]), tid));
             }
         }
         if (tid == 0) mbar_arrive_expect_tx(&xbar[par], static_cast<uint32_t>((P - 1) * 8));
         __syncthreads();
-        mbar_wait_bounded(&xbar[par], phase, err);
+        mbar_wait_bounded_cluster(&xbar[par], phase, err);
         const float *sl = slots + par * 16 * 4;
         st = op == OP_SOFTMAX ? combine_partials<OP_SOFTMAX>(sl, 4, P, s, V, N, eps)
                               : combine_partials<OP_RMS>(sl, 4, P, s, V, N, eps);

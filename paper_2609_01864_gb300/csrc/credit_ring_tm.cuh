@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
             const int s4 = rr & 3;
             if (lane == 0)
                 mbar_arrive_expect_tx(&xbar[s4], static_cast<uint32_t>((P - 1) * kTmWarps * 16));
-            mbar_wait_bounded(&xbar[s4], static_cast<uint32_t>((rr >> 2) & 1), a.err);
+            mbar_wait_bounded_cluster(&xbar[s4], static_cast<uint32_t>((rr >> 2) & 1), a.err);
             TmPart<OP> t;
             if (lane < ne) t.from(*reinterpret_cast<const float4 *>(slots + (s4 * 16 * kTmWarps + lane) * 4));
 #pragma unroll
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
                 mbar_arrive(&xbar[s4]);
             } else if (lane < P) {
                 const uint32_t d = static_cast<uint32_t>((c + lane) % P);
-                fence_acq_rel_cluster();
+                fence_release_smem_cluster();
                 st_async_v4f32(mapa_shared(smem_addr(ent), d), e, mapa_shared(smem_addr(&xbar[s4]), d));
             }
             j += g.nch;

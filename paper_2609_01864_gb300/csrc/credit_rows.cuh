@@ -495,7 +495,7 @@ __device__ __forceinline__ const float *exchange_push(float p0, float p1, float 
             if (NQ == 2) mine[1] = p1;
         } else {
             // order this CTA's earlier reads of the slots before the peer's next writes
-            fence_acq_rel_cluster();
+            fence_release_smem_cluster();
             const uint32_t raddr = mapa_shared(smem_addr(mine), static_cast<uint32_t>(tid));
             const uint32_t rbar = mapa_shared(smem_addr(bar), static_cast<uint32_t>(tid));
             if (NQ == 2) st_async_v2f32(raddr, p0, p1, rbar);
@@ -504,7 +504,7 @@ __device__ __forceinline__ const float *exchange_push(float p0, float p1, float 
     }
     if (tid == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>((P - 1) * NQ * 4));
     named_bar_sync(1, Tc);
-    mbar_wait_bounded(bar, phase, err);
+    mbar_wait_bounded_cluster(bar, phase, err);
     return slot_ptr(slots, stage, par, 0);
 }
 
