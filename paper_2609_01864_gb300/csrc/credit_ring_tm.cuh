@@ -1,9 +1,10 @@
 // credit_ring_tm.cuh -- the staged path with tensor memory as the retention tier.
 //
 // Same method as k_ring (Eq. 2 slicing, one sweep that reduces a slice while
-// it lands, Eq. 5 push exchange, fixed-order combine, reuse pass from on-chip
-// storage), with the retained slice held in tensor memory (TMEM: 128 lanes x
-// 512 32-bit columns = 256 KiB per SM) instead of the shared-memory ring:
+// it lands, Eq. 5 push exchange, a combine in one fixed order in every CTA,
+// reuse pass from on-chip storage), with the retained slice held in tensor
+// memory (TMEM: 128 lanes x 512 32-bit columns = 256 KiB per SM) instead of
+// the shared-memory ring:
 //
 //   producer (warp 16, lane 0)  streams the slice's chunks into a short
 //            shared-memory ring with cp.async.bulk, as in k_ring; lane 1
@@ -43,8 +44,11 @@
 // Exchange slots and mbarriers are indexed by row % 4: a CTA's reducers reach
 // row r + 4 only after its writers finished row r + 2, which needed every
 // peer's row-(r + 2) partial, which each peer pushed only after its own
-// writers had finished row r and so read its row-r slots.  TMEM buffers are
-// indexed by row % 2 and handed back by the writers (tm_empty).
+// writers had finished row r -- and those waited for the statistics its
+// combiner computed from its row-r slots.  The push is ordered after those
+// reads by a release fence restricted to shared memory at cluster scope; the
+// combiner acquires at cluster scope.  TMEM buffers are indexed by row % 2 and
+// handed back by the writers (tm_empty).
 //
 // One CTA per SM: the kernel allocates all 512 TMEM columns, and the host
 // requests more than half of the SM's shared memory so no second CTA of this
@@ -152,7 +156,6 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
     constexpr int isz = Fmt<TIN>::size, V = Fmt<TIN>::V;
     constexpr int SV = V < 8 ? V : 8;
     constexpr int osz = Fmt<TOUT>::size;
-    constexpr int NQ = (OP == OP_RMS) ? 1 : 2;
     constexpr int Tr = kTmReducers, Tw = kTmWriters, TL = kTmLanes;
 
     const int CH = a.chunk_bytes, K = a.ring, gpc = CH / 16;
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
     __syncthreads();
     tm_fence_after();
     const uint32_t taddr = *tm_base;
-    // this warp's lane quarter (reducer warp q and writer warp 4 + q share it)
+    // this warp's lane quarter (reducer warps q, 4 + q and writer warps 8 + q, 12 + q share it)
     const uint32_t tq = taddr + ((static_cast<uint32_t>(warp & 3) * 32u) << 16);
     if (P > 1) cluster_arrive_release();  // start barrier, split
     bool waited_start = false;
