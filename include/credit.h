@@ -417,14 +417,17 @@ credit_status credit_mlp_save(const char *path);
 credit_status credit_mlp_load(const char *path);
 
 /*
- * credit_set_trace -- phase tracing of the staged (ring) kernel.  While a
- * buffer is set, the first 32 CTAs of every staged launch write global-timer
- * stamps (ns) for their first R = bytes / (32 * 8 * 8) rows into it, as
- * uint64 [cta][row][8]: 0 row start, 1 stage-1 sweep done, 2 CTA reduction
- * done, 3 DSMEM exchange done, 4 reuse pass done, 5 producer issued the row's
- * last chunk (6, 7 unused).  device_buf: caller-owned device memory, 8-byte
- * aligned; NULL turns tracing off.  Not thread-safe against concurrent
- * launches; a debugging aid, off by default.
+ * credit_set_trace -- phase tracing of the staged kernels.  While a buffer is
+ * set, the first 32 CTAs of every staged launch write global-timer stamps (ns)
+ * for their first R = bytes / (32 * 8 * 8) rows into it, as uint64
+ * [cta][row][8].  Shared-memory retention: 0 row start, 1 stage-1 sweep done,
+ * 2 CTA reduction done, 3 DSMEM exchange done, 4 reuse pass done, 5 producer
+ * issued the row's last chunk (6, 7 unused).  Tensor-memory retention:
+ * 0 reducer row start, 5 its TMEM buffer free, 1 sweep done, 2 warp partial
+ * merged and pushed; 6 writer row start, 3 statistics in hand, 4 writes done
+ * (7 unused).  device_buf: caller-owned device memory, 8-byte aligned; NULL
+ * turns tracing off.  Not thread-safe against concurrent launches; a
+ * debugging aid, off by default.
  */
 credit_status credit_set_trace(void *device_buf, int64_t bytes);
 
