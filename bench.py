@@ -229,13 +229,34 @@ def cpu_oracle_sample(seconds: float = 10.0, threads: int = 0):
                       f"{reps} repetitions in {el:.1f} s ({nbytes / 1e9:.2f} GB algorithmic)"}
 
 
+# ---------------------------------------------------------------- ranks (host logic, also run under gloo in tests)
+def dist_env():
+    """(rank, world, local rank) from the launcher's environment (1 process: 0, 1, 0)."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value: float, world: int, device="cpu") -> float:
+    """The largest of the ranks' values (the step time the job is charged)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(step_bytes_per_rank: int, world: int, ms_step: float) -> float:
+    """Whole-job GB/s: every rank processes its own rows (weak scaling)."""
+    return step_bytes_per_rank * world / (ms_step * 1e-3) / 1e9
+
+
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
-    per_step = min(per_step, 10.0)
+    per_step = min(10.0, max(0.05, args.ref_seconds / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         cpu_oracle_sample(seconds=min(2.0, per_step))
     vals = []
@@ -291,9 +312,7 @@ def run_ours(args):
     from paper_2609_01864_gb300 import credit as C
     from paper_2609_01864_gb300 import synth
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
@@ -359,13 +378,9 @@ def run_ours(args):
         dist.barrier()
     launches = C.launch_count() - n0
     clk = clocks.stop()
-    ms_total = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(t_start.elapsed_time(t_end), world, device=dev)
     ms_step = ms_total / args.steps
-    value = step_bytes * world / (ms_step * 1e-3) / 1e9
+    value = job_value(step_bytes, world, ms_step)
     assert C.device_error() == C.OK
 
     # ---- per-kernel launch times (roofline of the dominant kernel)
@@ -404,7 +419,7 @@ def run_ours(args):
     # timed region, before the candidate sweep below)
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(C, torch, dev, jobs, shapes, stream, args)
+        e2e = run_e2e(C, torch, dev, jobs, shapes, stream, args, world)
 
     # ---- speedup vs best non-DSMEM path and pick accuracy (every candidate timed)
     speed_num = speed_den = 0.0
@@ -486,11 +501,14 @@ def profitability(pick_rows):
     return {"pairs": len(pick_rows), "sign_agreement": agree, "n_star": n_star}
 
 
-def run_e2e(C, torch, dev, jobs, shapes, stream, args):
+def run_e2e(C, torch, dev, jobs, shapes, stream, args, world=1):
     """The same step through the public host-buffer call (credit_run_host):
     every op copies its input in from pinned host memory, runs, and copies its
     output back, the library overlapping the copies of consecutive row blocks
-    with the op.  Wall-clock time of whole steps (the call is synchronous)."""
+    with the op.  Wall-clock time of whole steps (the call is synchronous),
+    bracketed by barriers and taken as the max over ranks; the value counts
+    every rank's rows."""
+    import torch.distributed as dist
     host_x, host_g, host_b = {}, {}, {}
     for sh in shapes:
         for src, dst in ((sh["x"], host_x), (sh["g"], host_g), (sh["b"], host_b)):
@@ -513,14 +531,16 @@ def run_e2e(C, torch, dev, jobs, shapes, stream, args):
     steps = max(1, min(args.steps, args.e2e_steps))
     step()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
         step()
     torch.cuda.synchronize()
-    ms = (time.perf_counter() - t0) * 1e3 / steps
+    ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / steps, world, device=dev)
     step_bytes = sum(j["bytes"] for j in jobs)
-    return {"value": round(step_bytes / (ms * 1e-3) / 1e9, 1), "unit": "GB/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3), "steps": steps,
+    return {"value": round(job_value(step_bytes, world, ms), 1), "unit": "GB/s", "h2d_bytes_per_step": h2d * world,
+            "d2h_bytes_per_step": d2h * world, "ms_per_step": round(ms, 3), "steps": steps,
             "api": "credit_run_host (pinned host buffers, library-planned row blocks)"}
 
 
@@ -537,6 +557,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="--impl reference: CPU seconds of the whole run, split over warm-up and timed steps")
     ap.add_argument("--case", default="", help="op:rows:cols:path:P[:retain[:fill_share]] -- one plan, 3 calls (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not args.case:

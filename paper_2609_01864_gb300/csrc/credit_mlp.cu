@@ -209,7 +209,8 @@ void host_forward(const Model &mdl, const float *xin, float *yout_log2us) {
 // Features of one candidate: log2 rows, log2 cols, input dtype one-hot (3),
 // op one-hot (4), path one-hot (one-CTA, two-pass, cluster), log2 P, log2 G,
 // log2 of the algorithmic bytes, output bytes per element, log2 of the input
-// bytes one CTA handles, log2 of the CTAs per SM (152 SMs) the rows need.
+// bytes one CTA handles, log2 of the CTAs per SM (152 SMs) the rows need,
+// tensor-memory retention (0 / 1), and the share of rows given to the fill.
 void mlp_features(int op, int tin, int tout, long long rows, long long cols, int path, int P, int G, int retain_tm,
                   float fill, float *f) {
     std::memset(f, 0, kIn * sizeof(float));

@@ -134,6 +134,39 @@ def run_sweep(shapes, reps, cap_bytes, log=None):
     return rows_out
 
 
+CSV_HEADER = "shape,op,dtype,rows,cols,path,P,G,retain,fill,us"
+
+
+def write_csv(path, rows):
+    """One line per timed candidate (times in microseconds)."""
+    with open(path, "w") as f:
+        f.write(CSV_HEADER + "\n")
+        for r in rows:
+            f.write(f"{r['shape']},{r['op']},{r['dtype']},{r['rows']},{r['cols']},{r['path']},{r['P']},{r['G']},"
+                    f"{r['retain']},{r['fill']:g},{r['us']:.3f}\n")
+
+
+def read_csv(path):
+    """Timings written by write_csv, and the two older forms: 9 columns (no
+    retention column: cluster and one-CTA plans staged in shared memory) and
+    10 columns (no fill column: no fill)."""
+    rows = []
+    with open(path) as f:
+        next(f)
+        for line in f:
+            v = line.strip().split(",")
+            if len(v) == 9:
+                v = v[:8] + [str(C.RETAIN_SMEM if int(v[5]) != C.PATH_TWO_PASS else C.RETAIN_AUTO)] + v[8:]
+            if len(v) == 10:
+                v = v[:9] + ["0"] + v[9:]
+            if len(v) != 11:
+                raise ValueError(f"{path}: bad timing line {line.strip()!r}")
+            sh, op, dt, r, c, path_, P, G, retain, fill, us = v
+            rows.append(dict(shape=int(sh), op=int(op), dtype=int(dt), rows=int(r), cols=int(c), path=int(path_),
+                             P=int(P), G=int(G), retain=int(retain), fill=float(fill), us=float(us)))
+    return rows
+
+
 def features_of(r):
     out_dt = C.F32 if r["op"] == C.LOGSUMEXP else r["dtype"]
     return C.mlp_features(r["op"], r["dtype"], out_dt, r["rows"], r["cols"], r["path"], r["P"], r["G"],
@@ -203,18 +236,7 @@ def main(argv=None):
     shapes = synth.sweep_shapes(args.shapes, cap_bytes=cap)
     t0 = time.time()
     if args.from_csv:
-        rows = []
-        with open(args.from_csv) as f:
-            next(f)
-            for line in f:
-                v = line.strip().split(",")
-                if len(v) == 9:  # timings from before the retention column: shared-memory staging
-                    v = v[:8] + [str(C.RETAIN_SMEM if int(v[5]) != C.PATH_TWO_PASS else C.RETAIN_AUTO)] + v[8:]
-                if len(v) == 10:  # before the fill column: no fill
-                    v = v[:9] + ["0"] + v[9:]
-                sh, op, dt, r, c, path, P, G, retain, fill, us = v
-                rows.append(dict(shape=int(sh), op=int(op), dtype=int(dt), rows=int(r), cols=int(c), path=int(path),
-                                 P=int(P), G=int(G), retain=int(retain), fill=float(fill), us=float(us)))
+        rows = read_csv(args.from_csv)
         shapes = shapes[:1 + max(r["shape"] for r in rows)]
     else:
         rows = run_sweep(shapes, args.reps, cap, log=sys.stderr)
@@ -246,11 +268,7 @@ def main(argv=None):
     csv_out = os.path.join(args.out, "sweep_gb300.csv")
     if args.from_csv and os.path.abspath(args.from_csv) == os.path.abspath(csv_out):
         csv_out += ".new"
-    with open(csv_out, "w") as f:
-        f.write("shape,op,dtype,rows,cols,path,P,G,retain,fill,us\n")
-        for r in rows:
-            f.write(f"{r['shape']},{r['op']},{r['dtype']},{r['rows']},{r['cols']},{r['path']},{r['P']},{r['G']},"
-                    f"{r['retain']},{r['fill']:g},{r['us']:.3f}\n")
+    write_csv(csv_out, rows)
     summary = {"shapes": len(shapes), "timings": len(rows), "train_shapes": len(train), "test_shapes": n_test,
                "pick_rule": "pick within 5% of the measured best candidate", "pick_accuracy": acc,
                "train_loss_first_last": [float(curve[0]), float(curve[-1])], "sweep_s": round(t_sweep, 1),
