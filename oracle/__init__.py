@@ -8,7 +8,9 @@ library: the two share no code and meet only at the seeded input bytes.
 Contents
 --------
 * ``credit_oracle.c`` -- the plain double-precision definitions of softmax,
-  log-sum-exp, LayerNorm and RMSNorm (Eq. 1 of the paper, one row at a time),
+  log-sum-exp, LayerNorm and RMSNorm (Eq. 1 of the paper, one row at a time)
+  and of the input gradients of softmax, LayerNorm and RMSNorm (the backward
+  members of the workload suite, Sec. IV-A),
   exact decoding of BF16 / FP8-E4M3 inputs and round-to-nearest-even encoding
   of BF16 / E4M3 outputs, written from the formats' definitions.
 * ``cost_model`` -- the analytic profitability model (Eq. 3, 4, 6-9).
@@ -77,6 +79,11 @@ def lib() -> ctypes.CDLL:
             L.oracle_run.restype = i32
             L.oracle_run.argtypes = [i32, i32, i32, vp, vp, i64, i64, i64, vp, vp, d,
                                      vp, vp, i64, vp, i32]
+            L.oracle_softmax_bwd_row.argtypes = [vp, vp, i64, vp]
+            L.oracle_layernorm_bwd_row.argtypes = [vp, vp, i64, vp, d, d, vp]
+            L.oracle_rmsnorm_bwd_row.argtypes = [vp, vp, i64, vp, d, vp]
+            L.oracle_run_bwd.restype = i32
+            L.oracle_run_bwd.argtypes = [i32, i32, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp, i32]
             L.oracle_max_threads.restype = i32
             _lib = L
     return _lib
@@ -187,6 +194,61 @@ def run(op: int, in_dtype: int, raw: np.ndarray, rows: int, cols: int, *, out_dt
     if rc != 0:
         raise ValueError("oracle_run rejected its arguments")
     return y64, enc, osc
+
+
+# ---------------------------------------------------------------- input gradients
+def softmax_bwd(y, dy):
+    """dx of softmax given its output y and the upstream gradient dy (rows x cols, FP64)."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    dy = np.ascontiguousarray(dy, dtype=np.float64)
+    dx = np.empty_like(y)
+    for r in range(y.shape[0]):
+        lib().oracle_softmax_bwd_row(_ptr(y[r]), _ptr(dy[r]), y.shape[1], _ptr(dx[r]))
+    return dx
+
+
+def layernorm_bwd(x, dy, mean, rstd, gamma=None):
+    """dx of LayerNorm given its input x, dy and the saved per-row mean / rstd (FP64)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    dy = np.ascontiguousarray(dy, dtype=np.float64)
+    g = None if gamma is None else np.ascontiguousarray(gamma, dtype=np.float64)
+    dx = np.empty_like(x)
+    for r in range(x.shape[0]):
+        lib().oracle_layernorm_bwd_row(_ptr(x[r]), _ptr(dy[r]), x.shape[1], _ptr(g), float(mean[r]),
+                                       float(rstd[r]), _ptr(dx[r]))
+    return dx
+
+
+def rmsnorm_bwd(x, dy, rstd, gamma=None):
+    """dx of RMSNorm given its input x, dy and the saved per-row rstd (FP64)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    dy = np.ascontiguousarray(dy, dtype=np.float64)
+    g = None if gamma is None else np.ascontiguousarray(gamma, dtype=np.float64)
+    dx = np.empty_like(x)
+    for r in range(x.shape[0]):
+        lib().oracle_rmsnorm_bwd_row(_ptr(x[r]), _ptr(dy[r]), x.shape[1], _ptr(g), float(rstd[r]), _ptr(dx[r]))
+    return dx
+
+
+def run_bwd(op: int, dtype: int, a_raw, dy_raw, rows: int, cols: int, *, gamma=None, mean=None, rstd=None,
+            ld: int = 0, want_exact: bool = True, want_encoded: bool = False, nthreads: int = 0):
+    """Batch input gradient.  op is the forward op (SOFTMAX, LAYERNORM, RMSNORM); a_raw is the forward
+    output (softmax) or input (norms), dy_raw the upstream gradient, both stored elements of dtype (F32 /
+    BF16 codes) with row stride ld; gamma, mean, rstd are FP32 arrays.  Returns (dx64 or None, encoded or
+    None)."""
+    a_raw = np.ascontiguousarray(a_raw)
+    dy_raw = np.ascontiguousarray(dy_raw)
+    f32 = lambda v: None if v is None else np.ascontiguousarray(v, dtype=np.float32)  # noqa: E731
+    g, mu, rs = f32(gamma), f32(mean), f32(rstd)
+    dx64 = np.empty((rows, cols), dtype=np.float64) if want_exact else None
+    enc = None
+    if want_encoded:
+        enc = np.empty((rows, ld or cols), dtype={F32: np.float32, BF16: np.uint16}[dtype])
+    rc = lib().oracle_run_bwd(op, dtype, _ptr(a_raw), _ptr(dy_raw), rows, cols, ld, _ptr(g), _ptr(mu), _ptr(rs),
+                              _ptr(dx64), _ptr(enc), nthreads)
+    if rc != 0:
+        raise ValueError("oracle_run_bwd rejected its arguments")
+    return dx64, (None if enc is None else enc[:, :cols])
 
 
 def max_threads() -> int:

@@ -19,6 +19,10 @@
  *             y_i = (x_i - mu) / sqrt(var + eps) * gamma_i + beta_i
  *   rmsnorm   y_i = x_i / sqrt(sum x^2 / N + eps) * gamma_i
  *
+ * and the input gradients of softmax, LayerNorm and RMSNorm (their
+ * vector-Jacobian products with an upstream gradient dy, given the forward's
+ * saved row statistics; see the backward section below).
+ *
  * Sums use Neumaier compensation so that the oracle's own rounding stays far
  * below every tolerance the GPU path is held to.
  *
@@ -191,6 +195,60 @@ void oracle_rmsnorm_row(const double *x, int64_t n, const double *gamma,
 }
 
 /* ------------------------------------------------------------------ */
+/* Input gradients (the backward members of the workload suite,        */
+/* Sec. IV-A): the vector-Jacobian product of each forward op above    */
+/* with the upstream gradient dy, by the chain rule through the row    */
+/* statistics.  With g_i = dy_i * gamma_i (gamma = 1 when absent):      */
+/*   softmax   s = sum_j y_j dy_j,                  dx_i = y_i (dy_i - s) */
+/*             (y is the forward output)                              */
+/*   layernorm xh_i = (x_i - mean) * rstd,                            */
+/*             dx_i = rstd (g_i - sum_j g_j / N - xh_i sum_j g_j xh_j / N) */
+/*   rmsnorm   xh_i = x_i * rstd,                                     */
+/*             dx_i = rstd (g_i - xh_i sum_j g_j xh_j / N)            */
+/* mean and rstd are the forward's saved row statistics (rstd =       */
+/* 1/sqrt(var + eps) and 1/sqrt(sum x^2 / N + eps)); they are taken as */
+/* given, so the result is exact for the statistics the caller holds.  */
+/* The derivation: d mean / d x_k = 1/N, d rstd / d x_k = -rstd^2 xh_k / N */
+/* (layernorm; the mean's own term cancels because sum (x - mean) = 0) */
+/* and -rstd^2 xh_k / N (rmsnorm).                                    */
+/* ------------------------------------------------------------------ */
+
+void oracle_softmax_bwd_row(const double *y, const double *dy, int64_t n, double *dx) {
+    nsum_t S = {0, 0};
+    for (int64_t i = 0; i < n; ++i) nsum_add(&S, y[i] * dy[i]);
+    double s = nsum_get(&S);
+    for (int64_t i = 0; i < n; ++i) dx[i] = y[i] * (dy[i] - s);
+}
+
+void oracle_layernorm_bwd_row(const double *x, const double *dy, int64_t n, const double *gamma,
+                              double mean, double rstd, double *dx) {
+    nsum_t A = {0, 0}, B = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        double g = dy[i] * (gamma ? gamma[i] : 1.0);
+        double xh = (x[i] - mean) * rstd;
+        nsum_add(&A, g);
+        nsum_add(&B, g * xh);
+    }
+    double a = nsum_get(&A) / (double)n, b = nsum_get(&B) / (double)n;
+    for (int64_t i = 0; i < n; ++i) {
+        double g = dy[i] * (gamma ? gamma[i] : 1.0);
+        double xh = (x[i] - mean) * rstd;
+        dx[i] = rstd * (g - a - xh * b);
+    }
+}
+
+void oracle_rmsnorm_bwd_row(const double *x, const double *dy, int64_t n, const double *gamma,
+                            double rstd, double *dx) {
+    nsum_t B = {0, 0};
+    for (int64_t i = 0; i < n; ++i) nsum_add(&B, dy[i] * (gamma ? gamma[i] : 1.0) * x[i] * rstd);
+    double b = nsum_get(&B) / (double)n;
+    for (int64_t i = 0; i < n; ++i) {
+        double g = dy[i] * (gamma ? gamma[i] : 1.0);
+        dx[i] = rstd * (g - x[i] * rstd * b);
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Batch driver: decode -> op -> (exact doubles, encoded output)        */
 /* ------------------------------------------------------------------ */
 
@@ -283,6 +341,67 @@ int oracle_run(int op, int in_dtype, int out_dtype, const void *in,
             }
         }
         free_row(x); free_row(y); free_row(g); free_row(b);
+    }
+    return bad ? -1 : 0;
+}
+
+/*
+ * Backward batch.  op: 0 softmax, 2 layernorm, 3 rmsnorm (the forward op's
+ * code).  a (softmax: the forward output y; norms: the forward input x) and
+ * dy hold rows x cols elements of dtype (F32 or BF16) with row stride ld;
+ * gamma (cols FP32, NULL = 1), mean (rows FP32, layernorm) and rstd (rows
+ * FP32, norms) are decoded exactly.  dx64 (may be NULL) receives the exact
+ * rows*cols result, dx (may be NULL) the result rounded to dtype with row
+ * stride ld.  Returns 0, or -1 on a bad argument.
+ */
+int oracle_run_bwd(int op, int dtype, const void *a, const void *dy, int64_t rows, int64_t cols, int64_t ld,
+                   const float *gamma, const float *mean, const float *rstd, double *dx64, void *dx,
+                   int nthreads) {
+    if (rows < 0 || cols <= 0 || !a || !dy) return -1;
+    if (!(op == OR_SOFTMAX || op == OR_LAYERNORM || op == OR_RMSNORM) || dtype < 0 || dtype > 1) return -1;
+    if (op == OR_LAYERNORM && (!mean || !rstd)) return -1;
+    if (op == OR_RMSNORM && !rstd) return -1;
+    if (ld <= 0) ld = cols;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    int bad = 0;
+#pragma omp parallel
+    {
+        double *x = (double *)malloc_row(cols);
+        double *d = (double *)malloc_row(cols);
+        double *o = (double *)malloc_row(cols);
+        double *g = gamma ? (double *)malloc_row(cols) : NULL;
+        if (!x || !d || !o || (gamma && !g)) {
+#pragma omp atomic write
+            bad = 1;
+        } else {
+            if (g) for (int64_t i = 0; i < cols; ++i) g[i] = (double)gamma[i];
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t r = 0; r < rows; ++r) {
+                const char *ar = (const char *)a + r * ld * dtype_size(dtype);
+                const char *dr = (const char *)dy + r * ld * dtype_size(dtype);
+                for (int64_t i = 0; i < cols; ++i) {
+                    x[i] = decode_one(ar, dtype, i);
+                    d[i] = decode_one(dr, dtype, i);
+                }
+                if (op == OR_SOFTMAX) oracle_softmax_bwd_row(x, d, cols, o);
+                else if (op == OR_LAYERNORM)
+                    oracle_layernorm_bwd_row(x, d, cols, g, (double)mean[r], (double)rstd[r], o);
+                else oracle_rmsnorm_bwd_row(x, d, cols, g, (double)rstd[r], o);
+                if (dx64) memcpy(dx64 + r * cols, o, (size_t)cols * sizeof(double));
+                if (!dx) continue;
+                char *orow = (char *)dx + r * ld * dtype_size(dtype);
+                if (dtype == OR_F32) {
+                    for (int64_t i = 0; i < cols; ++i) ((float *)orow)[i] = (float)o[i];
+                } else {
+                    for (int64_t i = 0; i < cols; ++i) ((uint16_t *)orow)[i] = oracle_double_to_bf16(o[i]);
+                }
+            }
+        }
+        free_row(x); free_row(d); free_row(o); free_row(g);
     }
     return bad ? -1 : 0;
 }
