@@ -259,6 +259,87 @@ int32_t credit_max_clusters(const credit_args *args, const credit_plan_t *plan);
  */
 credit_status credit_plan_check(const credit_args *args, const credit_plan_t *plan);
 
+/* ------------------------------------------------------------------ backward ops
+ * Input gradients of softmax, LayerNorm and RMSNorm: the backward members of
+ * the paper's reduction-reuse workload suite (Sec. IV-A).  Like the forward
+ * ops, each row is reduced to dot-product statistics that are then applied
+ * to every element of the same row; the row now has two arrays (a and dy),
+ * so the global-reread path rereads both (Eq. 4: 5 element accesses instead
+ * of 3) while the staged paths keep both slices in shared memory.  With
+ * g_i = dy_i * gamma_i (gamma = 1 when NULL) and N = cols:
+ *   CREDIT_OP_SOFTMAX_BWD    a = y (softmax output), s = sum_j y_j dy_j,
+ *                            dx_i = y_i (dy_i - s)
+ *   CREDIT_OP_LAYERNORM_BWD  a = x (LayerNorm input), xh_i = (x_i - mean) rstd,
+ *                            dx_i = rstd (g_i - sum_j g_j / N - xh_i sum_j g_j xh_j / N)
+ *   CREDIT_OP_RMSNORM_BWD    a = x (RMSNorm input), xh_i = x_i rstd,
+ *                            dx_i = rstd (g_i - xh_i sum_j g_j xh_j / N)
+ * mean / rstd are the forward's saved row statistics (rstd = 1/sqrt(var +
+ * eps) for LayerNorm, 1/sqrt(sum x^2 / N + eps) for RMSNorm), FP32 per row.
+ * Only dx is computed (the parameter gradients dgamma / dbeta are column
+ * sums over rows, not row ops).  Statistics accumulate in FP32; dx is
+ * rounded to nearest even.
+ */
+typedef enum {
+    CREDIT_OP_SOFTMAX_BWD = 4,
+    CREDIT_OP_LAYERNORM_BWD = 5,
+    CREDIT_OP_RMSNORM_BWD = 6
+} credit_bwd_op;
+
+/*
+ *   op         credit_bwd_op
+ *   dtype      CREDIT_F32 or CREDIT_BF16, for a, dy and dx (FP8: CREDIT_ERR_UNSUPPORTED)
+ *   a, dy, dx  device pointers, rows x cols elements with row stride ld
+ *              elements (0 = cols).  dx may equal a or dy (in place);
+ *              partial overlap is undefined.
+ *   gamma      norms: cols FP32, NULL = 1; ignored by softmax
+ *   mean       LAYERNORM_BWD: rows FP32 (required)
+ *   rstd       LAYERNORM_BWD / RMSNORM_BWD: rows FP32 (required)
+ */
+typedef struct {
+    int32_t op;
+    int32_t dtype;
+    const void *a;
+    const void *dy;
+    void *dx;
+    int64_t rows, cols, ld;
+    const float *gamma;
+    const float *mean;
+    const float *rstd;
+} credit_bwd_args;
+
+/*
+ * credit_run_bwd -- one backward op with a plan (NULL = credit_plan_bwd's
+ * choice).  Plans:
+ *   CLUSTER (P = 2..16) / ONE_CTA (P = 1)  each CTA stages its slice of a and
+ *       of dy with bulk-async copies, pushes its partial sums to every peer
+ *       over DSMEM, and writes its dx segment from shared memory.  ring_chunks
+ *       = row buffers per CTA (0: two when they fit, so that the next row
+ *       loads while this one is processed; 1 or 2 forced).  Needs 16-byte
+ *       aligned rows (a, dy, dx and ld * element size multiples of 16) and
+ *       two slices within the opt-in shared memory; otherwise
+ *       CREDIT_ERR_UNSUPPORTED, with nothing launched.
+ *   TWO_PASS (G = ctas_per_row >= 1)  a statistics sweep over HBM and a
+ *       second sweep that rereads a and dy; G > 1 splits a row over G CTAs
+ *       whose partials go through the device workspace between two launches.
+ *       Any alignment.
+ * fill_share and retain must be 0.  Asynchronous on `stream`; the statuses
+ * of credit_run_ex.
+ */
+credit_status credit_run_bwd(const credit_bwd_args *args, const credit_plan_t *plan, cudaStream_t stream);
+
+/*
+ * credit_plan_bwd -- a plan for (op, rows, cols, dtype) of the backward ops,
+ * assuming 16-byte aligned rows (credit_run_bwd falls back to TWO_PASS for
+ * unaligned rows when planning itself): the fused two-pass path for rows of
+ * at most 16 KiB per array, else the staged path with the smallest cluster
+ * size whose two slices fit double-buffered (then single-buffered), else the
+ * split two-pass path.  source = 3 (built-in rule).
+ */
+credit_status credit_plan_bwd(int32_t op, int64_t rows, int64_t cols, credit_dtype dtype, credit_plan_t *out);
+
+/* CREDIT_OK if `plan` is legal for `args` (see credit_run_bwd), else its error; launches nothing. */
+credit_status credit_bwd_plan_check(const credit_bwd_args *args, const credit_plan_t *plan);
+
 /* ------------------------------------------------------------------ ragged batches
  * Rows of uneven width and mixed op in one persistent cluster launch captured
  * in a CUDA graph.  Each row: elements in_base[in_off .. in_off + cols) ->

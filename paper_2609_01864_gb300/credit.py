@@ -24,6 +24,8 @@ OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_INITIALIZED
 OP_NAMES = {SOFTMAX: "softmax", LOGSUMEXP: "logsumexp", LAYERNORM: "layernorm", RMSNORM: "rmsnorm"}
 PATH_NAMES = {PATH_ONE_CTA: "one_cta", PATH_TWO_PASS: "two_pass", PATH_CLUSTER: "cluster"}
 RETAIN_AUTO, RETAIN_SMEM, RETAIN_TMEM = 0, 1, 2
+SOFTMAX_BWD, LAYERNORM_BWD, RMSNORM_BWD = 4, 5, 6
+OP_NAMES.update({SOFTMAX_BWD: "softmax_bwd", LAYERNORM_BWD: "layernorm_bwd", RMSNORM_BWD: "rmsnorm_bwd"})
 
 TORCH_DTYPE = {F32: torch.float32, BF16: torch.bfloat16, FP8_E4M3: torch.float8_e4m3fn}
 DTYPE_OF = {torch.float32: F32, torch.bfloat16: BF16, torch.float8_e4m3fn: FP8_E4M3}
@@ -54,6 +56,12 @@ class ArgsT(ctypes.Structure):
                 ("ld_out", ctypes.c_int64), ("in_dtype", ctypes.c_int32), ("out_dtype", ctypes.c_int32),
                 ("in_scale", ctypes.c_void_p), ("out_scale", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
                 ("beta", ctypes.c_void_p), ("eps", ctypes.c_float)]
+
+
+class BwdArgsT(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("dtype", ctypes.c_int32), ("a", ctypes.c_void_p), ("dy", ctypes.c_void_p),
+                ("dx", ctypes.c_void_p), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("gamma", ctypes.c_void_p), ("mean", ctypes.c_void_p), ("rstd", ctypes.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -99,6 +107,12 @@ def lib() -> ctypes.CDLL:
             L.credit_device_error.argtypes = [vp]
             L.credit_slice_capacity.restype = i64
             L.credit_slice_capacity.argtypes = [i32]
+            L.credit_run_bwd.restype = i32
+            L.credit_run_bwd.argtypes = [ctypes.POINTER(BwdArgsT), ctypes.POINTER(PlanT), vp]
+            L.credit_plan_bwd.restype = i32
+            L.credit_plan_bwd.argtypes = [i32, i64, i64, i32, ctypes.POINTER(PlanT)]
+            L.credit_bwd_plan_check.restype = i32
+            L.credit_bwd_plan_check.argtypes = [ctypes.POINTER(BwdArgsT), ctypes.POINTER(PlanT)]
             L.credit_launch_count.restype = ctypes.c_longlong
             L.credit_launch_count.argtypes = []
             _extra_prototypes(L)
@@ -331,6 +345,46 @@ def run_two_pass_noalloc(op: int, x, out, ctas_per_row: int, *, stream=None, **k
     library's fixed device scratch (no allocation).  Returns the status."""
     a = make_args(op, x, out, **kw)
     return lib().credit_run_two_pass_noalloc(ctypes.byref(a), int(ctas_per_row), _stream(stream))
+
+
+def make_bwd_args(op: int, a, dy, dx, *, rows: int | None = None, cols: int | None = None, ld: int = 0,
+                  dtype: int | None = None, gamma=None, mean=None, rstd=None) -> BwdArgsT:
+    r = BwdArgsT()
+    r.op = op
+    r.dtype = DTYPE_OF[a.dtype] if dtype is None else dtype
+    r.a, r.dy, r.dx = _ptr(a), _ptr(dy), _ptr(dx)
+    if rows is None or cols is None:
+        rows, cols = a.shape[0], a.shape[-1]
+    r.rows, r.cols, r.ld = rows, cols, ld
+    r.gamma, r.mean, r.rstd = _ptr(gamma), _ptr(mean), _ptr(rstd)
+    return r
+
+
+def run_bwd(op: int, a, dy, dx, *, plan: PlanT | None = None, stream=None, **kw) -> int:
+    """credit_run_bwd: dx of softmax (a = y), LayerNorm or RMSNorm (a = x); keyword arguments as
+    make_bwd_args (gamma, mean, rstd are FP32 tensors).  Raises CreditError on a non-OK status."""
+    r = make_bwd_args(op, a, dy, dx, **kw)
+    st = lib().credit_run_bwd(ctypes.byref(r), ctypes.byref(plan) if plan is not None else None, _stream(stream))
+    _check(st, "credit_run_bwd")
+    return st
+
+
+def run_bwd_status(*args, **kw) -> int:
+    try:
+        return run_bwd(*args, **kw)
+    except CreditError as e:
+        return e.status
+
+
+def plan_bwd(op: int, rows: int, cols: int, dtype: int) -> PlanT:
+    p = PlanT()
+    _check(lib().credit_plan_bwd(op, rows, cols, dtype, ctypes.byref(p)), "credit_plan_bwd")
+    return p
+
+
+def bwd_plan_check(op: int, a, dy, dx, plan: PlanT, **kw) -> int:
+    r = make_bwd_args(op, a, dy, dx, **kw)
+    return lib().credit_bwd_plan_check(ctypes.byref(r), ctypes.byref(plan))
 
 
 def run_ex_status(*args, **kw) -> int:

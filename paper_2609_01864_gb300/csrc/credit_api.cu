@@ -294,11 +294,17 @@ int current_device() {
 // 0 if it cannot be scheduled.  Cached.
 int ring_max_clusters(int device, int op, int tin, int tout, int P, int threads, long long smem, bool tm) {
     if (device < 0 || device >= kMaxDevices) return 0;
-    DeviceState &d = g_dev[device];
     KernelSet ks;
     if (!kernel_set(op, tin, tout, &ks)) return 0;
     const void *fn = tm ? ks.ring_tm : ks.ring;
     if (fn == nullptr) return 0;
+    return staged_max_clusters(device, fn, P, threads, smem, tm);
+}
+
+int staged_max_clusters(int device, const void *fn, int P, int threads, long long smem, bool one_per_sm) {
+    if (device < 0 || device >= kMaxDevices || fn == nullptr) return 0;
+    DeviceState &d = g_dev[device];
+    const bool tm = one_per_sm;
     if (smem > d.info.smem_optin) return 0;
     if (prepare_kernel(d, fn, true) != CREDIT_OK) return 0;
     const auto key = std::make_tuple(fn, P, threads, smem);
@@ -336,6 +342,21 @@ int ring_max_clusters(int device, int op, int tin, int tout, int P, int threads,
     std::lock_guard<std::mutex> lk(d.mu);
     d.clusters[key] = n;
     return n;
+}
+
+credit_status prepare_staged_kernel(int device, const void *fn) {
+    if (device < 0 || device >= kMaxDevices) return CREDIT_ERR_CUDA;
+    return prepare_kernel(g_dev[device], fn, true);
+}
+
+unsigned *device_error_word(int device) {
+    return device < 0 || device >= kMaxDevices ? nullptr : g_dev[device].err;
+}
+
+float *device_workspace(int device, size_t *floats) {
+    if (device < 0 || device >= kMaxDevices) return nullptr;
+    if (floats) *floats = g_dev[device].info.ws_floats;
+    return g_dev[device].ws;
 }
 
 }  // namespace credit
@@ -561,7 +582,7 @@ static RowArgs rows_from(const RowArgs &base, long long r0, long long n, int isz
     return r;
 }
 
-static cudaError_t launch(const void *fn, dim3 grid, dim3 block, size_t smem, int cluster, cudaStream_t s,
+cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, size_t smem, int cluster, cudaStream_t s,
                           void **args) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -578,6 +599,11 @@ static cudaError_t launch(const void *fn, dim3 grid, dim3 block, size_t smem, in
         cfg.numAttrs = 1;
     }
     return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+static cudaError_t launch(const void *fn, dim3 grid, dim3 block, size_t smem, int cluster, cudaStream_t s,
+                          void **args) {
+    return launch_kernel(fn, grid, block, smem, cluster, s, args);
 }
 
 std::atomic<long long> g_launch_count{0};

@@ -1,0 +1,649 @@
+// credit_bwd.cu -- input gradients of softmax, LayerNorm and RMSNorm
+// (the backward members of the reduction-reuse workload suite, Sec. IV-A).
+//
+// Every row has two arrays, a (softmax: the forward output y; norms: the
+// forward input x) and the upstream gradient dy.  With g = dy * gamma:
+//   softmax    S0 = sum y dy                     dx = y (dy - S0)
+//   layernorm  xh = (x - mean) rstd, S0 = sum g, S1 = sum g xh
+//              dx = rstd (g - S0 / N - xh S1 / N)
+//   rmsnorm    xh = x rstd, S1 = sum g xh        dx = rstd (g - xh S1 / N)
+// i.e. one reduction stage (L = 1) of q = 1 or 2 plain sums, then an
+// elementwise pass over the same two arrays (Eq. 1).
+//
+// Paths:
+//   k_bwd_staged   ONE_CTA (P = 1) and CLUSTER (P = 2..16).  A persistent
+//                  cluster walks rows cl, cl + ncl, ...  Each CTA stages its
+//                  slice of a and of dy (16-byte groups group_split(G, c, P)
+//                  .. group_split(G, c + 1, P), Eq. 2) with bulk-async copies
+//                  completed on an mbarrier, sums its partials, pushes them
+//                  to every peer with st.async (completing on the peer's
+//                  exchange mbarrier, Eq. 5-6), combines the P partials in
+//                  the fixed order c = 0..P-1 (identical statistics in every
+//                  CTA), and writes its dx segment from shared memory: one
+//                  HBM read of each array and one write (Eq. 4, b_reread = 0).
+//                  With two row buffers the copies of row r + ncl run while
+//                  row r is reduced and written.  The elements past the last
+//                  full group (N * size not a multiple of 16) are read from
+//                  global memory by the last CTA.
+//   k_bwd_tp_*     TWO_PASS: sums over HBM, then a second sweep that rereads
+//                  both arrays; G CTAs per row exchange partials through the
+//                  device workspace between two launches (G = 1: one fused
+//                  kernel, the reread mostly from L2).  Any alignment.
+//
+// Exchange slots: [parity = row iteration % 2][16 sources][4 floats].  A CTA
+// pushes its partial for iteration t + 2 into parity t % 2 only after its
+// exchange of iteration t + 1 completed, which needed every peer's push of
+// t + 1, which each peer made after its own combine of iteration t had read
+// those slots; the release fence before each push and the cluster-scope
+// acquire of the mbarrier wait carry that order (as in the forward kernels).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "../../include/credit.h"
+#include "credit_host.h"
+#include "credit_rows.cuh"
+
+namespace credit {
+extern std::atomic<long long> g_launch_count;
+
+namespace {
+
+enum BwdOp : int { BOP_SOFTMAX = 4, BOP_LN = 5, BOP_RMS = 6 };
+
+constexpr int kBwdThreads = 512;
+constexpr int kBwdCtrl = 1152;             // control area before the row buffers (bytes)
+constexpr uint32_t kBwdPiece = 32768;      // bytes per bulk copy instruction
+constexpr long long kBwdFusedMaxBytes = 16384;  // planner: fused two-pass up to this many bytes per array row
+
+struct BwdArgs {
+    const unsigned char *a, *dy;
+    unsigned char *dx;
+    long long rows, cols, ld;  // ld in elements (all three arrays)
+    const float *gamma, *mean, *rstd;
+    unsigned *err;
+    float *ws;                 // two-pass partials [row - row0][G][2]
+    int G;                     // two-pass CTAs per row
+    int nbuf;                  // staged: row buffers (1 or 2)
+    int slice_groups;          // staged: 16-byte groups per array slice buffer
+    long long row0;            // first row of this launch
+};
+
+// Per-row constants and the per-element math of each op.
+template <int OP>
+struct BwdRow {
+    float mean = 0.0f, rstd = 1.0f;
+    __device__ __forceinline__ void load(const BwdArgs &p, long long row) {
+        if constexpr (OP == BOP_LN) mean = p.mean[row];
+        if constexpr (OP != BOP_SOFTMAX) rstd = p.rstd[row];
+    }
+    // add element (a, dy, gamma) to the partial sums
+    __device__ __forceinline__ void acc(float a, float d, float gm, float &s0, float &s1) const {
+        if constexpr (OP == BOP_SOFTMAX) {
+            s0 = fmaf(a, d, s0);
+        } else {
+            const float g = d * gm;
+            const float xh = (OP == BOP_LN ? a - mean : a) * rstd;
+            if constexpr (OP == BOP_LN) s0 += g;
+            s1 = fmaf(g, xh, s1);
+        }
+    }
+    // dx of element (a, dy, gamma) given c0 = S0 (softmax) or S0 / N, c1 = S1 / N
+    __device__ __forceinline__ float dx(float a, float d, float gm, float c0, float c1) const {
+        if constexpr (OP == BOP_SOFTMAX) {
+            return a * (d - c0);
+        } else {
+            const float g = d * gm;
+            const float xh = (OP == BOP_LN ? a - mean : a) * rstd;
+            return rstd * (g - c0 - xh * c1);
+        }
+    }
+};
+
+// c0, c1 from the row totals (S0, S1) and N.
+template <int OP>
+__device__ __forceinline__ void row_coeffs(float S0, float S1, long long N, float &c0, float &c1) {
+    const float inv_n = 1.0f / static_cast<float>(N);
+    if constexpr (OP == BOP_SOFTMAX) {
+        c0 = S0;
+        c1 = 0.0f;
+    } else if constexpr (OP == BOP_LN) {
+        c0 = S0 * inv_n;
+        c1 = S1 * inv_n;
+    } else {
+        c0 = 0.0f;
+        c1 = S1 * inv_n;
+    }
+}
+
+// Deterministic block sum of two floats through red (>= 66 floats); every
+// thread returns the totals.  Contains two __syncthreads.
+__device__ __forceinline__ float2 block_sum2(float a, float b, float *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+        red[2 * wid] = a;
+        red[2 * wid + 1] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        float ta = lane < nw ? red[2 * lane] : 0.0f;
+        float tb = lane < nw ? red[2 * lane + 1] : 0.0f;
+        ta = warp_sum(ta);
+        tb = warp_sum(tb);
+        if (lane == 0) {
+            red[64] = ta;
+            red[65] = tb;
+        }
+    }
+    __syncthreads();
+    return make_float2(red[64], red[65]);
+}
+
+// ------------------------------------------------------------------ staged (ONE_CTA / CLUSTER)
+// Shared memory: [0, 16) full[2] mbarriers, [16, 32) xbar[2] mbarriers,
+// [64, 576) reduction scratch, [576, 1088) exchange slots, then nbuf row
+// buffers of (a slice, dy slice), slice_groups * 16 bytes each.
+template <int OP, int DT>
+__global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *xbar = full + 2;
+    float *red = reinterpret_cast<float *>(smem + 64);
+    float *slots = reinterpret_cast<float *>(smem + 576);
+    unsigned char *data = smem + kBwdCtrl;
+    constexpr int isz = Fmt<DT>::size, V = Fmt<DT>::V;
+    constexpr int NQ = (OP == BOP_LN) ? 2 : 1;
+
+    const int P = static_cast<int>(cluster_nctarank());
+    const int c = static_cast<int>(cluster_ctarank());
+    const long long cl = blockIdx.x / P, ncl = gridDim.x / P;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const long long N = p.cols;
+    const long long Gq = N / V;                  // full 16-byte groups of a row
+    const long long tail = N - Gq * V;
+    const long long g_lo = group_split(Gq, c, P), g_hi = group_split(Gq, c + 1, P);
+    const int ng = static_cast<int>(g_hi - g_lo);
+    const size_t arr = static_cast<size_t>(p.slice_groups) * 16;
+    const bool g_vec = p.gamma == nullptr || (reinterpret_cast<uintptr_t>(p.gamma) & 15u) == 0;
+
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&xbar[0], 1);
+        mbar_init(&xbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (P > 1) {  // every peer's exchange barriers exist before the first push
+        cluster_arrive_release();
+        cluster_wait_acquire();
+    }
+
+    // thread 0: stage this CTA's slices of row `row` into buffer b
+    auto issue = [&](long long row, int b) {
+        const size_t off = static_cast<size_t>(row * p.ld + g_lo * V) * isz;
+        unsigned char *da = data + static_cast<size_t>(b) * 2 * arr, *dd = da + arr;
+        const uint32_t bytes = static_cast<uint32_t>(ng) * 16u;
+        mbar_arrive_expect_tx(&full[b], 2 * bytes);
+        for (uint32_t o = 0; o < bytes; o += kBwdPiece) {
+            const uint32_t n = bytes - o < kBwdPiece ? bytes - o : kBwdPiece;
+            bulk_g2s(da + o, p.a + off + o, n, &full[b]);
+            bulk_g2s(dd + o, p.dy + off + o, n, &full[b]);
+        }
+    };
+
+    if (tid == 0 && cl < p.rows) issue(cl, 0);
+    long long it = 0;
+    for (long long row = cl; row < p.rows; row += ncl, ++it) {
+        const int b = p.nbuf == 2 ? static_cast<int>(it & 1) : 0;
+        const uint32_t fpar = p.nbuf == 2 ? static_cast<uint32_t>((it >> 1) & 1) : static_cast<uint32_t>(it & 1);
+        // the next row into the other buffer (read last in the previous iteration, before its final barrier)
+        if (p.nbuf == 2 && tid == 0 && row + ncl < p.rows) {
+            fence_proxy_async_smem();
+            issue(row + ncl, b ^ 1);
+        }
+        BwdRow<OP> R;
+        R.load(p, row);
+        const unsigned char *da = data + static_cast<size_t>(b) * 2 * arr, *dd = da + arr;
+        const size_t row_off = static_cast<size_t>(row * p.ld) * isz;
+        mbar_wait_bounded(&full[b], fpar, p.err);
+
+        float s0 = 0.0f, s1 = 0.0f;
+        for (int k = tid; k < ng; k += T) {
+            float fa[V], fd[V], fg[V];
+            decode_group<DT>(*reinterpret_cast<const uint4 *>(da + 16 * k), fa, 1.0f);
+            decode_group<DT>(*reinterpret_cast<const uint4 *>(dd + 16 * k), fd, 1.0f);
+            load_affine<V>(OP == BOP_SOFTMAX ? nullptr : p.gamma, (g_lo + k) * V, g_vec, 1.0f, fg);
+#pragma unroll
+            for (int v = 0; v < V; ++v) R.acc(fa[v], fd[v], fg[v], s0, s1);
+        }
+        if (c == P - 1) {
+            for (long long t = tid; t < tail; t += T) {
+                const long long i = Gq * V + t;
+                const float gm = (OP != BOP_SOFTMAX && p.gamma) ? p.gamma[i] : 1.0f;
+                R.acc(decode_one<DT>(p.a + row_off + i * isz, 1.0f), decode_one<DT>(p.dy + row_off + i * isz, 1.0f),
+                      gm, s0, s1);
+            }
+        }
+        float2 tot = block_sum2(s0, s1, red);
+        if (P > 1) {
+            const float *sl = exchange_push<NQ>(OP == BOP_RMS ? tot.y : tot.x, tot.y, slots, xbar, 0,
+                                                static_cast<int>(it & 1), static_cast<uint32_t>((it >> 1) & 1), P,
+                                                c, T, p.err);
+            float S0 = 0.0f, S1 = 0.0f;
+            for (int q = 0; q < P; ++q) {  // fixed order: the same totals in every CTA
+                S0 += sl[4 * q];
+                if (NQ == 2) S1 += sl[4 * q + 1];
+            }
+            tot = OP == BOP_RMS ? make_float2(0.0f, S0) : make_float2(S0, S1);
+        }
+        float c0, c1;
+        row_coeffs<OP>(tot.x, tot.y, N, c0, c1);
+        unsigned char *xr = p.dx + row_off + static_cast<size_t>(g_lo * V) * isz;
+        for (int k = tid; k < ng; k += T) {
+            float fa[V], fd[V], fg[V], y[V];
+            decode_group<DT>(*reinterpret_cast<const uint4 *>(da + 16 * k), fa, 1.0f);
+            decode_group<DT>(*reinterpret_cast<const uint4 *>(dd + 16 * k), fd, 1.0f);
+            load_affine<V>(OP == BOP_SOFTMAX ? nullptr : p.gamma, (g_lo + k) * V, g_vec, 1.0f, fg);
+#pragma unroll
+            for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], c0, c1);
+            store_group<DT, V>(xr + 16 * k, y, true);
+        }
+        if (c == P - 1) {
+            for (long long t = tid; t < tail; t += T) {
+                const long long i = Gq * V + t;
+                const float gm = (OP != BOP_SOFTMAX && p.gamma) ? p.gamma[i] : 1.0f;
+                const float v = R.dx(decode_one<DT>(p.a + row_off + i * isz, 1.0f),
+                                     decode_one<DT>(p.dy + row_off + i * isz, 1.0f), gm, c0, c1);
+                store_one<DT>(p.dx + row_off + i * isz, v);
+            }
+        }
+        __syncthreads();  // every read of buffer b is done before it is refilled
+        if (p.nbuf == 1 && tid == 0 && row + ncl < p.rows) {
+            fence_proxy_async_smem();
+            issue(row + ncl, 0);
+        }
+    }
+    if (P > 1) {  // nobody exits while a peer may still push into it
+        cluster_arrive_release();
+        cluster_wait_acquire();
+    }
+}
+
+// ------------------------------------------------------------------ two-pass
+// Units of CTA j of G for one row: 16-byte groups when the row's three
+// arrays are 16-byte aligned (plus the tail elements, by CTA G - 1), single
+// elements otherwise.
+struct BwdSpan {
+    bool vec;
+    long long lo, hi;        // groups (vec) or elements
+    long long t_lo, t_hi;    // tail elements handled here (vec only)
+};
+
+template <int DT>
+__device__ __forceinline__ BwdSpan bwd_span(const BwdArgs &p, long long row, int j, int G) {
+    constexpr int isz = Fmt<DT>::size, V = Fmt<DT>::V;
+    const size_t off = static_cast<size_t>(row * p.ld) * isz;
+    const bool vec = ((reinterpret_cast<uintptr_t>(p.a + off) | reinterpret_cast<uintptr_t>(p.dy + off) |
+                       reinterpret_cast<uintptr_t>(p.dx + off)) & 15u) == 0;
+    BwdSpan s;
+    s.vec = vec;
+    if (vec) {
+        const long long Gq = p.cols / V;
+        s.lo = group_split(Gq, j, G);
+        s.hi = group_split(Gq, j + 1, G);
+        s.t_lo = j == G - 1 ? Gq * V : p.cols;
+        s.t_hi = p.cols;
+    } else {
+        s.lo = group_split(p.cols, j, G);
+        s.hi = group_split(p.cols, j + 1, G);
+        s.t_lo = s.t_hi = 0;
+    }
+    return s;
+}
+
+template <int OP, int DT>
+__device__ __forceinline__ float2 bwd_sums(const BwdArgs &p, long long row, const BwdRow<OP> &R, const BwdSpan &s) {
+    constexpr int isz = Fmt<DT>::size, V = Fmt<DT>::V;
+    const size_t off = static_cast<size_t>(row * p.ld) * isz;
+    const bool g_vec = p.gamma == nullptr || (reinterpret_cast<uintptr_t>(p.gamma) & 15u) == 0;
+    const float *gam = OP == BOP_SOFTMAX ? nullptr : p.gamma;
+    float s0 = 0.0f, s1 = 0.0f;
+    if (s.vec) {
+        for (long long k = s.lo + threadIdx.x; k < s.hi; k += blockDim.x) {
+            float fa[V], fd[V], fg[V];
+            decode_group<DT>(ld_global_v4(p.a + off + 16 * k), fa, 1.0f);
+            decode_group<DT>(ld_global_v4(p.dy + off + 16 * k), fd, 1.0f);
+            load_affine<V>(gam, k * V, g_vec, 1.0f, fg);
+#pragma unroll
+            for (int v = 0; v < V; ++v) R.acc(fa[v], fd[v], fg[v], s0, s1);
+        }
+    }
+    const long long e_lo = s.vec ? s.t_lo : s.lo, e_hi = s.vec ? s.t_hi : s.hi;
+    for (long long i = e_lo + threadIdx.x; i < e_hi; i += blockDim.x)
+        R.acc(decode_one<DT>(p.a + off + i * isz, 1.0f), decode_one<DT>(p.dy + off + i * isz, 1.0f),
+              gam ? gam[i] : 1.0f, s0, s1);
+    return make_float2(s0, s1);
+}
+
+template <int OP, int DT>
+__device__ __forceinline__ void bwd_apply(const BwdArgs &p, long long row, const BwdRow<OP> &R, const BwdSpan &s,
+                                          float c0, float c1) {
+    constexpr int isz = Fmt<DT>::size, V = Fmt<DT>::V;
+    const size_t off = static_cast<size_t>(row * p.ld) * isz;
+    const bool g_vec = p.gamma == nullptr || (reinterpret_cast<uintptr_t>(p.gamma) & 15u) == 0;
+    const float *gam = OP == BOP_SOFTMAX ? nullptr : p.gamma;
+    if (s.vec) {
+        for (long long k = s.lo + threadIdx.x; k < s.hi; k += blockDim.x) {
+            float fa[V], fd[V], fg[V], y[V];
+            decode_group<DT>(ld_global_v4(p.a + off + 16 * k), fa, 1.0f);
+            decode_group<DT>(ld_global_v4(p.dy + off + 16 * k), fd, 1.0f);
+            load_affine<V>(gam, k * V, g_vec, 1.0f, fg);
+#pragma unroll
+            for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], c0, c1);
+            store_group<DT, V>(p.dx + off + 16 * k, y, true);
+        }
+    }
+    const long long e_lo = s.vec ? s.t_lo : s.lo, e_hi = s.vec ? s.t_hi : s.hi;
+    for (long long i = e_lo + threadIdx.x; i < e_hi; i += blockDim.x) {
+        const float v = R.dx(decode_one<DT>(p.a + off + i * isz, 1.0f), decode_one<DT>(p.dy + off + i * isz, 1.0f),
+                             gam ? gam[i] : 1.0f, c0, c1);
+        store_one<DT>(p.dx + off + i * isz, v);
+    }
+}
+
+// G = 1: one CTA per row, both sweeps.
+template <int OP, int DT>
+__global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_fused(const BwdArgs p) {
+    __shared__ float red[128];
+    const long long row = p.row0 + blockIdx.x;
+    BwdRow<OP> R;
+    R.load(p, row);
+    const BwdSpan s = bwd_span<DT>(p, row, 0, 1);
+    const float2 t = bwd_sums<OP, DT>(p, row, R, s);
+    const float2 tot = block_sum2(t.x, t.y, red);
+    float c0, c1;
+    row_coeffs<OP>(tot.x, tot.y, p.cols, c0, c1);
+    bwd_apply<OP, DT>(p, row, R, s, c0, c1);
+}
+
+// G > 1, launch 1: partial sums of CTA j of row lr into ws[lr][j][0..1].
+template <int OP, int DT>
+__global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_stats(const BwdArgs p) {
+    __shared__ float red[128];
+    const int G = p.G, j = blockIdx.x % G;
+    const long long lr = blockIdx.x / G, row = p.row0 + lr;
+    BwdRow<OP> R;
+    R.load(p, row);
+    const BwdSpan s = bwd_span<DT>(p, row, j, G);
+    const float2 t = bwd_sums<OP, DT>(p, row, R, s);
+    const float2 tot = block_sum2(t.x, t.y, red);
+    if (threadIdx.x == 0) {
+        p.ws[(lr * G + j) * 2] = tot.x;
+        p.ws[(lr * G + j) * 2 + 1] = tot.y;
+    }
+}
+
+// G > 1, launch 2: the row totals (partials in the fixed order j = 0..G-1), then dx.
+template <int OP, int DT>
+__global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_apply(const BwdArgs p) {
+    const int G = p.G, j = blockIdx.x % G;
+    const long long lr = blockIdx.x / G, row = p.row0 + lr;
+    BwdRow<OP> R;
+    R.load(p, row);
+    float S0 = 0.0f, S1 = 0.0f;
+    for (int q = 0; q < G; ++q) {
+        S0 += p.ws[(lr * G + q) * 2];
+        S1 += p.ws[(lr * G + q) * 2 + 1];
+    }
+    float c0, c1;
+    row_coeffs<OP>(S0, S1, p.cols, c0, c1);
+    bwd_apply<OP, DT>(p, row, R, bwd_span<DT>(p, row, j, G), c0, c1);
+}
+
+struct BwdKernels {
+    const void *staged, *fused, *stats, *apply;
+};
+
+template <int OP, int DT>
+BwdKernels bwd_kernels_of() {
+    return {reinterpret_cast<const void *>(&k_bwd_staged<OP, DT>), reinterpret_cast<const void *>(&k_bwd_tp_fused<OP, DT>),
+            reinterpret_cast<const void *>(&k_bwd_tp_stats<OP, DT>),
+            reinterpret_cast<const void *>(&k_bwd_tp_apply<OP, DT>)};
+}
+
+bool bwd_kernels(int op, int dt, BwdKernels *k) {
+    switch (op * 4 + dt) {
+    case BOP_SOFTMAX * 4 + DT_F32: *k = bwd_kernels_of<BOP_SOFTMAX, DT_F32>(); return true;
+    case BOP_SOFTMAX * 4 + DT_BF16: *k = bwd_kernels_of<BOP_SOFTMAX, DT_BF16>(); return true;
+    case BOP_LN * 4 + DT_F32: *k = bwd_kernels_of<BOP_LN, DT_F32>(); return true;
+    case BOP_LN * 4 + DT_BF16: *k = bwd_kernels_of<BOP_LN, DT_BF16>(); return true;
+    case BOP_RMS * 4 + DT_F32: *k = bwd_kernels_of<BOP_RMS, DT_F32>(); return true;
+    case BOP_RMS * 4 + DT_BF16: *k = bwd_kernels_of<BOP_RMS, DT_BF16>(); return true;
+    default: return false;
+    }
+}
+
+// ------------------------------------------------------------------ host
+credit_status validate_bwd(const credit_bwd_args *a) {
+    if (a == nullptr) return CREDIT_ERR_INVALID_ARG;
+    if (a->op < BOP_SOFTMAX || a->op > BOP_RMS) return CREDIT_ERR_INVALID_ARG;
+    if (a->dtype == CREDIT_FP8_E4M3) return CREDIT_ERR_UNSUPPORTED;
+    if (a->dtype != CREDIT_F32 && a->dtype != CREDIT_BF16) return CREDIT_ERR_INVALID_ARG;
+    if (a->rows < 0 || a->cols <= 0 || a->ld < 0 || (a->ld != 0 && a->ld < a->cols)) return CREDIT_ERR_INVALID_ARG;
+    if (a->rows == 0) return CREDIT_OK;
+    if (a->a == nullptr || a->dy == nullptr || a->dx == nullptr) return CREDIT_ERR_INVALID_ARG;
+    if (a->op == BOP_LN && (a->mean == nullptr || a->rstd == nullptr)) return CREDIT_ERR_INVALID_ARG;
+    if (a->op == BOP_RMS && a->rstd == nullptr) return CREDIT_ERR_INVALID_ARG;
+    return CREDIT_OK;
+}
+
+bool rows_aligned(const credit_bwd_args *a) {
+    const long long ld = a->ld ? a->ld : a->cols;
+    const int isz = dtype_size(a->dtype);
+    const uintptr_t u = reinterpret_cast<uintptr_t>(a->a) | reinterpret_cast<uintptr_t>(a->dy) |
+                        reinterpret_cast<uintptr_t>(a->dx);
+    return (u & 15u) == 0 && (a->rows <= 1 || (ld * isz) % 16 == 0);
+}
+
+struct BwdCfg {
+    int P, nbuf, slice_groups, threads;
+    long long smem;
+};
+
+// Staged geometry: the largest slice of P CTAs, nbuf buffers of two slices.
+bool bwd_config(const DeviceInfo &di, long long N, int isz, int P, int req_nbuf, BwdCfg *out) {
+    if (P < 1 || P > kMaxCluster || (P & (P - 1)) != 0) return false;
+    const long long Gq = N * isz / 16;
+    const long long per = (Gq + P - 1) / P;  // groups of the largest slice
+    const long long groups = (per + 7) / 8 * 8;  // 128-byte multiples
+    if (groups > (1LL << 24)) return false;
+    for (int nb = 2; nb >= 1; --nb) {
+        if (req_nbuf != 0 && nb != req_nbuf) continue;
+        const long long smem = kBwdCtrl + static_cast<long long>(nb) * 2 * groups * 16;
+        if (smem <= di.smem_optin) {
+            *out = {P, nb, static_cast<int>(groups), kBwdThreads, smem};
+            return true;
+        }
+    }
+    return false;
+}
+
+credit_status check_bwd_plan(int dev, const credit_bwd_args *a, const credit_plan_t *p, BwdCfg *cfg, int *maxc) {
+    if (p->fill_share != 0.0f || p->retain != 0) return CREDIT_ERR_UNSUPPORTED;
+    if (p->threads != 0 && p->threads != kBwdThreads) return CREDIT_ERR_UNSUPPORTED;
+    BwdKernels k;
+    if (!bwd_kernels(a->op, a->dtype, &k)) return CREDIT_ERR_UNSUPPORTED;
+    if (p->path == CREDIT_PATH_TWO_PASS) {
+        if (p->ctas_per_row < 1 || p->ctas_per_row > 4096) return CREDIT_ERR_UNSUPPORTED;
+        return CREDIT_OK;
+    }
+    if (p->path != CREDIT_PATH_ONE_CTA && p->path != CREDIT_PATH_CLUSTER) return CREDIT_ERR_UNSUPPORTED;
+    const int P = p->path == CREDIT_PATH_ONE_CTA ? 1 : p->cluster_size;
+    if (p->path == CREDIT_PATH_CLUSTER && P < 2) return CREDIT_ERR_UNSUPPORTED;
+    if (p->ring_chunks < 0 || p->ring_chunks > 2) return CREDIT_ERR_UNSUPPORTED;
+    if (!rows_aligned(a)) return CREDIT_ERR_UNSUPPORTED;
+    const DeviceInfo *di = device_info(dev);
+    if (di == nullptr || !bwd_config(*di, a->cols, dtype_size(a->dtype), P, p->ring_chunks, cfg))
+        return CREDIT_ERR_UNSUPPORTED;
+    const credit_status st = prepare_staged_kernel(dev, k.staged);
+    if (st != CREDIT_OK) return st;
+    *maxc = staged_max_clusters(dev, k.staged, P, cfg->threads, cfg->smem, false);
+    return *maxc > 0 ? CREDIT_OK : CREDIT_ERR_UNSUPPORTED;
+}
+
+credit_status plan_bwd_for(int dev, int op, long long cols, int dtype, credit_plan_t *out) {
+    std::memset(out, 0, sizeof(*out));
+    out->source = 3;
+    out->threads = kBwdThreads;
+    const int isz = dtype_size(dtype);
+    const DeviceInfo *di = dev >= 0 ? device_info(dev) : nullptr;
+    if (di != nullptr && cols * isz > kBwdFusedMaxBytes) {
+        BwdKernels k;
+        if (!bwd_kernels(op, dtype, &k)) return CREDIT_ERR_UNSUPPORTED;
+        for (int want = 2; want >= 1; --want) {
+            for (int P = 1; P <= kMaxCluster; P *= 2) {
+                BwdCfg cfg;
+                if (!bwd_config(*di, cols, isz, P, want, &cfg)) continue;
+                if (prepare_staged_kernel(dev, k.staged) != CREDIT_OK) continue;
+                if (staged_max_clusters(dev, k.staged, P, cfg.threads, cfg.smem, false) <= 0) continue;
+                out->path = P == 1 ? CREDIT_PATH_ONE_CTA : CREDIT_PATH_CLUSTER;
+                out->cluster_size = P;
+                out->ctas_per_row = P;
+                out->ring_chunks = cfg.nbuf;
+                out->smem_bytes = cfg.smem;
+                return CREDIT_OK;
+            }
+        }
+    }
+    long long g = cols * isz / (256LL << 10);
+    out->path = CREDIT_PATH_TWO_PASS;
+    out->cluster_size = 1;
+    out->ctas_per_row = static_cast<int>(g < 1 ? 1 : (g > 8 ? 8 : g));
+    return CREDIT_OK;
+}
+
+BwdArgs make_bwd_args(const credit_bwd_args *a, unsigned *err, float *ws) {
+    BwdArgs r{};
+    r.a = static_cast<const unsigned char *>(a->a);
+    r.dy = static_cast<const unsigned char *>(a->dy);
+    r.dx = static_cast<unsigned char *>(a->dx);
+    r.rows = a->rows;
+    r.cols = a->cols;
+    r.ld = a->ld ? a->ld : a->cols;
+    r.gamma = a->gamma;
+    r.mean = a->mean;
+    r.rstd = a->rstd;
+    r.err = err;
+    r.ws = ws;
+    return r;
+}
+
+credit_status cuda_st(cudaError_t e) {
+    if (e == cudaSuccess) return CREDIT_OK;
+    if (std::getenv("CREDIT_LOG")) std::fprintf(stderr, "credit: CUDA error %s\n", cudaGetErrorString(e));
+    return CREDIT_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace credit
+
+using namespace credit;
+
+extern "C" {
+
+credit_status credit_plan_bwd(int32_t op, int64_t rows, int64_t cols, credit_dtype dtype, credit_plan_t *out) {
+    if (out == nullptr || op < BOP_SOFTMAX || op > BOP_RMS || rows < 0 || cols <= 0) return CREDIT_ERR_INVALID_ARG;
+    if (dtype != CREDIT_F32 && dtype != CREDIT_BF16) return CREDIT_ERR_UNSUPPORTED;
+    int dev = 0;
+    const credit_status st = ensure_init(&dev, nullptr);
+    if (st != CREDIT_OK) return st;
+    return plan_bwd_for(dev, op, cols, dtype, out);
+}
+
+credit_status credit_bwd_plan_check(const credit_bwd_args *args, const credit_plan_t *plan) {
+    credit_status st = validate_bwd(args);
+    if (st != CREDIT_OK) return st;
+    if (plan == nullptr) return CREDIT_ERR_INVALID_ARG;
+    int dev = 0;
+    if ((st = ensure_init(&dev, nullptr)) != CREDIT_OK) return st;
+    BwdCfg cfg;
+    int maxc = 0;
+    return check_bwd_plan(dev, args, plan, &cfg, &maxc);
+}
+
+credit_status credit_run_bwd(const credit_bwd_args *args, const credit_plan_t *plan, cudaStream_t stream) {
+    credit_status st = validate_bwd(args);
+    if (st != CREDIT_OK) return st;
+    if (args->rows == 0) return CREDIT_OK;
+    int dev = 0;
+    if ((st = ensure_init(&dev, stream)) != CREDIT_OK) return st;
+    credit_plan_t chosen;
+    if (plan) {
+        chosen = *plan;
+    } else {
+        if ((st = plan_bwd_for(dev, args->op, args->cols, args->dtype, &chosen)) != CREDIT_OK) return st;
+        if (chosen.path != CREDIT_PATH_TWO_PASS && !rows_aligned(args)) {  // staged paths need aligned rows
+            chosen.path = CREDIT_PATH_TWO_PASS;
+            chosen.cluster_size = 1;
+            long long g = args->cols * dtype_size(args->dtype) / (256LL << 10);
+            chosen.ctas_per_row = static_cast<int>(g < 1 ? 1 : (g > 8 ? 8 : g));
+            chosen.ring_chunks = 0;
+        }
+    }
+    BwdCfg cfg{};
+    int maxc = 0;
+    if ((st = check_bwd_plan(dev, args, &chosen, &cfg, &maxc)) != CREDIT_OK) return st;
+    BwdKernels k;
+    bwd_kernels(args->op, args->dtype, &k);
+    size_t ws_floats = 0;
+    float *ws = device_workspace(dev, &ws_floats);
+    BwdArgs base = make_bwd_args(args, device_error_word(dev), ws);
+    const long long rows = args->rows;
+    cudaError_t e;
+
+    if (chosen.path != CREDIT_PATH_TWO_PASS) {
+        const long long ncl = rows < maxc ? rows : maxc;
+        BwdArgs r = base;
+        r.nbuf = cfg.nbuf;
+        r.slice_groups = cfg.slice_groups;
+        void *kargs[] = {&r};
+        e = launch_kernel(k.staged, dim3(static_cast<unsigned>(cfg.P * ncl)), dim3(cfg.threads),
+                          static_cast<size_t>(cfg.smem), cfg.P, stream, kargs);
+        if (e != cudaSuccess) return cuda_st(e);
+        g_launch_count.fetch_add(1);
+        return CREDIT_OK;
+    }
+    const int G = chosen.ctas_per_row;
+    const long long cap = G == 1 ? 0x7FFFFFFFLL : static_cast<long long>(ws_floats / (static_cast<size_t>(G) * 2));
+    const long long max_rows = cap < 0x7FFFFFFFLL / G ? cap : 0x7FFFFFFFLL / G;
+    if (max_rows < 1) return CREDIT_ERR_UNSUPPORTED;
+    for (long long r0 = 0; r0 < rows; r0 += max_rows) {
+        const long long n = rows - r0 < max_rows ? rows - r0 : max_rows;
+        BwdArgs r = base;
+        r.row0 = r0;
+        r.G = G;
+        void *kargs[] = {&r};
+        if (G == 1) {
+            e = launch_kernel(k.fused, dim3(static_cast<unsigned>(n)), dim3(kBwdThreads), 0, 1, stream, kargs);
+            if (e != cudaSuccess) return cuda_st(e);
+            g_launch_count.fetch_add(1);
+            continue;
+        }
+        const dim3 grid(static_cast<unsigned>(G * n));
+        e = launch_kernel(k.stats, grid, dim3(kBwdThreads), 0, 1, stream, kargs);
+        if (e != cudaSuccess) return cuda_st(e);
+        g_launch_count.fetch_add(1);
+        e = launch_kernel(k.apply, grid, dim3(kBwdThreads), 0, 1, stream, kargs);
+        if (e != cudaSuccess) return cuda_st(e);
+        g_launch_count.fetch_add(1);
+    }
+    return CREDIT_OK;
+}
+
+}  // extern "C"

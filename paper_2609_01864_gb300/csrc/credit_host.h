@@ -2,6 +2,7 @@
 // translation units (not part of the public C ABI).
 #pragma once
 
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "../../include/credit.h"
@@ -50,5 +51,17 @@ credit_status validate_args(const credit_args *a);
 credit_status check_plan(int device, const credit_args *a, const credit_plan_t *p);
 credit_status run_with_plan(int device, const credit_args *a, const credit_plan_t *p, cudaStream_t s);
 credit_status ensure_init(int *device_out, cudaStream_t s);
+
+// Shared pieces of the per-device state for the other translation units.
+// Max resident clusters (CTAs when P = 1; one_per_sm: only one CTA per SM
+// allowed) of a staged kernel with this launch shape; 0 if it cannot run.
+int staged_max_clusters(int device, const void *fn, int P, int threads, long long smem, bool one_per_sm);
+// Raise the opt-in shared memory and non-portable cluster attributes of fn once.
+credit_status prepare_staged_kernel(int device, const void *fn);
+unsigned *device_error_word(int device);
+float *device_workspace(int device, size_t *floats);
+// Launch fn with a cluster dimension of `cluster` (<= 1: no cluster attribute).
+cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, size_t smem, int cluster, cudaStream_t s,
+                          void **args);
 
 }  // namespace credit

@@ -137,3 +137,70 @@ def check_against_oracle(op, x_cpu, scale, *, out_dtype=None, plan=None, gamma=N
     m = error_metric(op, out_dtype, to64(out), ref, None if osc is None else osc.cpu().numpy())
     assert m <= limit, f"error {m:.3f} x bound (op={op}, in={in_dtype}, out={out_dtype}, plan={plan})"
     return m, out
+
+
+# ---------------------------------------------------------------- backward ops
+BWD_FWD_OP = {C.SOFTMAX_BWD: O.SOFTMAX, C.LAYERNORM_BWD: O.LAYERNORM, C.RMSNORM_BWD: O.RMSNORM}
+
+
+def bwd_inputs(op: int, dtype: int, rows: int, cols: int, *, ld: int = 0, seed: int = 0, device="cpu"):
+    """Tensors (a, dy, gamma, mean, rstd) on `device` for a backward op: a is softmax(N(0, 3^2) logits)
+    or the outlier-laden x of the forward workload, dy ~ N(0, 1), gamma ~ N(1, 0.1); mean / rstd are the
+    FP64 row statistics of the stored a, rounded to FP32 (the forward's saved statistics)."""
+    ld = ld or cols
+    if op == C.SOFTMAX_BWD:
+        logits = synth.normal(rows, cols, std=3.0, seed=seed, device=device).double()
+        a = torch.zeros(rows, ld, dtype=torch.float32, device=device)
+        a[:, :cols] = torch.softmax(logits, dim=1).float()
+        del logits
+    else:
+        a = synth.outliers(rows, ld, seed=seed, device=device)
+    dy = synth.normal(rows, ld, seed=seed + 1, device=device)
+    if dtype == C.BF16:
+        a, dy = synth.to_bf16(a), synth.to_bf16(dy)
+    gamma = synth.gamma_beta(cols, seed=seed + 2, device=device)[0] if op != C.SOFTMAX_BWD else None
+    mean = rstd = None
+    if op != C.SOFTMAX_BWD:
+        a64 = a[:, :cols].double()
+        if op == C.LAYERNORM_BWD:
+            m = a64.mean(dim=1)
+            rstd = (1.0 / torch.sqrt(((a64 - m[:, None]) ** 2).mean(dim=1) + 1e-5)).float()
+            mean = m.float()
+        else:
+            rstd = (1.0 / torch.sqrt((a64 * a64).mean(dim=1) + 1e-6)).float()
+        del a64
+    return a, dy, gamma, mean, rstd
+
+
+def bwd_reference(op, dtype, a, dy, gamma, mean, rstd, rows, cols, ld=0):
+    f = lambda t: None if t is None else t.cpu().numpy()  # noqa: E731
+    dx64, _ = O.run_bwd(BWD_FWD_OP[op], dtype, raw_numpy(a), raw_numpy(dy), rows, cols, ld=ld or cols,
+                        gamma=f(gamma), mean=f(mean), rstd=f(rstd))
+    return dx64
+
+
+def bwd_error(op, dtype, dx, ref, a, dy, gamma, mean, rstd, cols):
+    """Error of dx (rows x cols, FP64) in units of the bound (<= 1.0 passes).
+
+    The bound is 1e-5 of the row's largest term of the formula, S_row, plus one BF16 ulp of the exact
+    value for BF16 output: softmax S = max|y| (max|dy| + sum|y dy|); layernorm S = rstd (max|g| + sum|g|/N
+    + max|xh| sum|g xh|/N); rmsnorm S = rstd (max|g| + max|xh| sum|g xh|/N), g = dy gamma.  FP32 sums of N
+    terms err by a small multiple of 2^-24 times the sum of the terms' magnitudes; dx cancels, so its error
+    is measured against those magnitudes, not against |dx|."""
+    a64, dy64 = to64(a)[:, :cols], to64(dy)[:, :cols]
+    if op == C.SOFTMAX_BWD:
+        S = np.abs(a64).max(axis=1) * (np.abs(dy64).max(axis=1) + np.abs(a64 * dy64).sum(axis=1))
+    else:
+        g = dy64 * (1.0 if gamma is None else gamma.cpu().double().numpy()[None, :])
+        r = rstd.cpu().double().numpy()
+        xh = (a64 - (mean.cpu().double().numpy()[:, None] if op == C.LAYERNORM_BWD else 0.0)) * r[:, None]
+        S = np.abs(g).max(axis=1) + np.abs(xh).max(axis=1) * np.abs(g * xh).sum(axis=1) / cols
+        if op == C.LAYERNORM_BWD:
+            S = S + np.abs(g).sum(axis=1) / cols
+        S = r * S
+    bound = F32_TOL * S[:, None]
+    if dtype == C.BF16:
+        mag = np.abs(ref)
+        ulp = np.where(mag > 0, np.exp2(np.floor(np.log2(np.where(mag > 0, mag, 1.0))) - 7), 2.0 ** -133)
+        bound = bound + ulp
+    return float((np.abs(dx - ref) / bound).max())

@@ -79,3 +79,31 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(C.PlanT) == 56 and C.PlanT.smem_bytes.offset == 32 and C.PlanT.fill_g.offset == 52
     assert ctypes.sizeof(C.ArgsT) == 104
     assert C.ArgsT.eps.offset == 96 and C.ArgsT.in_scale.offset == 64
+
+
+def test_struct_layouts_match_a_c_compiler(tmp_path):
+    """Every ctypes mirror of a header struct has the C compiler's size and field offsets."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    cuda_inc = "/usr/local/cuda/include"
+    if cc is None or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime_api.h")):
+        pytest.skip("no C compiler or CUDA headers")
+    structs = {"credit_plan_t": C.PlanT, "credit_args": C.ArgsT, "credit_bwd_args": C.BwdArgsT}
+    rename = {"in_": "in"}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "credit.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {rename.get(f, f)}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), "-I", cuda_inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        cname, field, val = line.split()
+        py = structs[cname]
+        got = ctypes.sizeof(py) if field == "size" else getattr(py, field).offset
+        assert got == int(val), (cname, field, got, val)
