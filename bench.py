@@ -23,7 +23,8 @@ pick accuracy on these shapes (pick within 5% of the measured best candidate).
 
 --impl reference  times the FP64 CPU oracle (the reference arm of this
            project) on a bounded sample of the same workload.
---case op:rows:cols:path:P  runs one small case a few times (for profilers).
+--case op:rows:cols:path:P  runs one small case a few times (for profilers; op 4-6 are the
+           backward ops).
 """
 from __future__ import annotations
 
@@ -291,6 +292,20 @@ def run_case(spec: str):
     retain = int(v[5]) if len(v) > 5 else 0
     fill = float(v[6]) if len(v) > 6 else 0.0
     C.init(torch.cuda.current_device())
+    if op >= C.SOFTMAX_BWD:  # backward op: a, dy -> dx
+        a = synth.outliers(rows, cols, seed=synth.SEED_DATA, device="cuda")
+        dy = synth.normal(rows, cols, seed=synth.SEED_DATA + 1, device="cuda")
+        dx = torch.empty_like(a)
+        g, _ = synth.gamma_beta(cols, device="cuda")
+        st = torch.ones(rows, device="cuda")
+        kw = {} if op == C.SOFTMAX_BWD else dict(gamma=g, rstd=st, mean=st if op == C.LAYERNORM_BWD else None)
+        plan = None if path < 0 else C.make_plan(path, P, ctas_per_row=P if path == C.PATH_TWO_PASS else 1)
+        for _ in range(3):
+            C.run_bwd(op, a, dy, dx, plan=plan, **kw)
+        torch.cuda.synchronize()
+        assert C.device_error() == C.OK
+        print(json.dumps({"case": spec, "launches": C.launch_count()}))
+        return 0
     x = synth.outliers(rows, cols, seed=synth.SEED_DATA, device="cuda")
     y = torch.empty_like(x)
     g, b = synth.gamma_beta(cols, device="cuda")
@@ -451,6 +466,10 @@ def run_ours(args):
                               "measured_cluster": bool(cl) and min(cl) < best_non,
                               "candidates": {n: round(v, 4) for n, v in times.items()}})
 
+    bwd = None
+    if not args.no_bwd:
+        bwd = run_bwd_bench(C, torch, dev, synth)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_oracle_sample(seconds=args.cpu_seconds)
@@ -479,9 +498,75 @@ def run_ours(args):
         "pick_rule": "chosen plan within 5% of the fastest measured candidate (median of 5)",
         "per_job": per_job,
         "picks": pick_rows,
+        "backward": bwd,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+BWD_WIDTHS = [16384, 65536, 131072, 262144]
+
+
+def run_bwd_bench(C, torch, dev, synth):
+    """The backward ops (dx of softmax, LayerNorm, RMSNorm; FP32, 4096 rows): every candidate plan timed
+    (median of 5, CUDA events), the planner's pick, the best non-DSMEM plan and the speed-up of the pick
+    over it.  Algorithmic bytes: one read of a and of dy, one write of dx (12 B per element)."""
+    peak, peak_kind = measured_peak()
+    out = {"rows": ROWS, "dtype": "f32", "bytes_per_elem": 12, "peak_GBps": peak, "peak_source": peak_kind,
+           "shapes": []}
+    for cols in BWD_WIDTHS:
+        a = synth.outliers(ROWS, cols, seed=synth.SEED_DATA, device=dev)
+        dy = synth.normal(ROWS, cols, seed=synth.SEED_DATA + 1, device=dev)
+        dx = torch.empty_like(a)
+        g, _ = synth.gamma_beta(cols, device=dev)
+        a64 = a.double()
+        mean = a64.mean(dim=1)
+        rstd_ln = (1.0 / torch.sqrt(((a64 - mean[:, None]) ** 2).mean(dim=1) + 1e-5)).float()
+        rstd_rms = (1.0 / torch.sqrt((a64 * a64).mean(dim=1) + 1e-6)).float()
+        mean = mean.float()
+        del a64
+        nbytes = ROWS * cols * 12
+        for op, name, kw in ((C.SOFTMAX_BWD, "softmax_bwd", {}),
+                             (C.LAYERNORM_BWD, "layernorm_bwd", dict(gamma=g, mean=mean, rstd=rstd_ln)),
+                             (C.RMSNORM_BWD, "rmsnorm_bwd", dict(gamma=g, rstd=rstd_rms))):
+            cands = [(f"two_pass_g{G}", C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)) for G in (1, 2, 4, 8)]
+            cands.append(("one_cta", C.make_plan(C.PATH_ONE_CTA)))
+            cands += [(f"cluster{P}", C.make_plan(C.PATH_CLUSTER, P)) for P in (2, 4, 8, 16)]
+            times = {}
+            for cname, p in cands:
+                if C.bwd_plan_check(op, a, dy, dx, p, **kw) != C.OK:
+                    continue
+                ts = time_events(lambda: C.run_bwd(op, a, dy, dx, plan=p, **kw), 5)
+                times[cname] = statistics.median(ts)
+            chosen_plan = C.plan_bwd(op, ROWS, cols, C.F32)
+            chosen = statistics.median(time_events(lambda: C.run_bwd(op, a, dy, dx, **kw), 5))
+            non = {k: v for k, v in times.items() if k.startswith("two_pass")}
+            staged = {k: v for k, v in times.items() if not k.startswith("two_pass")}
+            best_non = min(non.values())
+            pname = (PATH_NAMES_SHORT[chosen_plan.path] +
+                     (str(chosen_plan.cluster_size) if chosen_plan.path == C.PATH_CLUSTER else
+                      (f"_g{chosen_plan.ctas_per_row}" if chosen_plan.path == C.PATH_TWO_PASS else "")))
+            out["shapes"].append({
+                "op": name, "cols": cols, "chosen": pname, "chosen_ms": round(chosen, 4),
+                "chosen_GBps": round(nbytes / chosen / 1e6, 1), "frac": round(nbytes / chosen / 1e6 / peak, 4),
+                "best": min(times, key=times.get), "best_ms": round(min(times.values()), 4),
+                "best_non_dsmem_ms": round(best_non, 4),
+                "best_staged_ms": round(min(staged.values()), 4) if staged else None,
+                "speedup_vs_best_non_dsmem": round(best_non / chosen, 4),
+                "hit": chosen <= 1.05 * min(times.values()),
+                "candidates": {k: round(v, 4) for k, v in sorted(times.items(), key=lambda kv: kv[1])}})
+        del a, dy, dx
+        torch.cuda.empty_cache()
+    assert C.device_error() == C.OK
+    sh = out["shapes"]
+    tot_chosen = sum(r["chosen_ms"] for r in sh)
+    out["GBps"] = round(sum(ROWS * r["cols"] * 12 for r in sh) / tot_chosen / 1e6, 1)
+    out["speedup_vs_best_non_dsmem"] = round(sum(r["best_non_dsmem_ms"] for r in sh) / tot_chosen, 4)
+    out["pick_accuracy"] = round(sum(r["hit"] for r in sh) / len(sh), 4)
+    return out
+
+
+PATH_NAMES_SHORT = {0: "one_cta", 1: "two_pass", 2: "cluster"}
 
 
 def profitability(pick_rows):
@@ -539,9 +624,37 @@ def run_e2e(C, torch, dev, jobs, shapes, stream, args, world=1):
     torch.cuda.synchronize()
     ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / steps, world, device=dev)
     step_bytes = sum(j["bytes"] for j in jobs)
-    return {"value": round(job_value(step_bytes, world, ms), 1), "unit": "GB/s", "h2d_bytes_per_step": h2d * world,
+    value = job_value(step_bytes, world, ms)
+    # the host link's own rates on this machine, for scale: 1 GiB plain copies between the same pinned
+    # buffers and device tensors (the input is copied onto its own device copy, so nothing changes)
+    big_cols = max(host_x, key=lambda c: host_x[c].numel())
+    dj = next(j for j in jobs if j["cols"] == big_cols)
+    n = min(1 << 28, host_x[big_cols].numel())
+    hx, dx = host_x[big_cols].view(-1)[:n], dj["x"].view(-1)[:n]
+    hy, dy = host_y[:n], dj["y"].view(-1)[:n]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def copy_rate(h2d_on, d2h_on, reps=3):
+        def go():
+            if h2d_on:
+                with torch.cuda.stream(s_in):
+                    dx.copy_(hx, non_blocking=True)
+            if d2h_on:
+                with torch.cuda.stream(s_out):
+                    hy.copy_(dy, non_blocking=True)
+        go()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            go()
+        torch.cuda.synchronize()
+        return round((h2d_on + d2h_on) * n * 4 * reps / (time.perf_counter() - t) / 1e9, 1)
+
+    link = {"h2d": copy_rate(True, False), "d2h": copy_rate(False, True), "both": copy_rate(True, True)}
+    return {"value": round(value, 1), "unit": "GB/s", "h2d_bytes_per_step": h2d * world,
             "d2h_bytes_per_step": d2h * world, "ms_per_step": round(ms, 3), "steps": steps,
-            "api": "credit_run_host (pinned host buffers, library-planned row blocks)"}
+            "api": "credit_run_host (pinned host buffers, library-planned row blocks)",
+            "link_gbs": link, "frac_of_link_both": round(value / world / link["both"], 3)}
 
 
 def main():
@@ -555,6 +668,7 @@ def main():
     ap.add_argument("--no-model", action="store_true", help="plan with the built-in heuristic")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-bwd", action="store_true", help="skip the backward-op table")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-seconds", type=float, default=60.0,

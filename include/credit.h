@@ -314,7 +314,8 @@ typedef struct {
  *       of dy with bulk-async copies, pushes its partial sums to every peer
  *       over DSMEM, and writes its dx segment from shared memory.  ring_chunks
  *       = row buffers per CTA (0: two when they fit, so that the next row
- *       loads while this one is processed; 1 or 2 forced).  Needs 16-byte
+ *       loads while this one is processed; 1 or 2 forced).  The norms also
+ *       stage their gamma slice once (when gamma is 16-byte aligned).  Needs 16-byte
  *       aligned rows (a, dy, dx and ld * element size multiples of 16) and
  *       two slices within the opt-in shared memory; otherwise
  *       CREDIT_ERR_UNSUPPORTED, with nothing launched.
@@ -332,8 +333,8 @@ credit_status credit_run_bwd(const credit_bwd_args *args, const credit_plan_t *p
  * assuming 16-byte aligned rows (credit_run_bwd falls back to TWO_PASS for
  * unaligned rows when planning itself): the fused two-pass path for rows of
  * at most 16 KiB per array, else the staged path with the smallest cluster
- * size whose two slices fit double-buffered (then single-buffered), else the
- * split two-pass path.  source = 3 (built-in rule).
+ * size whose slices (two row buffers of a and dy, and gamma for the norms)
+ * fit, else the split two-pass path.  source = 3 (built-in rule).
  */
 credit_status credit_plan_bwd(int32_t op, int64_t rows, int64_t cols, credit_dtype dtype, credit_plan_t *out);
 

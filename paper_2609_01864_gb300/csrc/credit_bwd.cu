@@ -69,6 +69,7 @@ struct BwdArgs {
     int G;                     // two-pass CTAs per row
     int nbuf;                  // staged: row buffers (1 or 2)
     int slice_groups;          // staged: 16-byte groups per array slice buffer
+    int gamma_smem;            // staged: this CTA's gamma slice is staged once in shared memory
     long long row0;            // first row of this launch
 };
 
@@ -146,13 +147,17 @@ __device__ __forceinline__ float2 block_sum2(float a, float b, float *red) {
 
 // ------------------------------------------------------------------ staged (ONE_CTA / CLUSTER)
 // Shared memory: [0, 16) full[2] mbarriers, [16, 32) xbar[2] mbarriers,
-// [64, 576) reduction scratch, [576, 1088) exchange slots, then nbuf row
-// buffers of (a slice, dy slice), slice_groups * 16 bytes each.
+// [32, 40) gbar mbarrier, [64, 576) reduction scratch, [576, 1088) exchange
+// slots, then nbuf row buffers of (a slice, dy slice), slice_groups * 16
+// bytes each, then (gamma_smem) the CTA's FP32 gamma slice, staged once for
+// all rows: gamma is the same for every row, so the loops read it from shared
+// memory instead of issuing an L2 load per element group.
 template <int OP, int DT>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *xbar = full + 2;
+    uint64_t *gbar = full + 4;
     float *red = reinterpret_cast<float *>(smem + 64);
     float *slots = reinterpret_cast<float *>(smem + 576);
     unsigned char *data = smem + kBwdCtrl;
@@ -170,15 +175,28 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
     const int ng = static_cast<int>(g_hi - g_lo);
     const size_t arr = static_cast<size_t>(p.slice_groups) * 16;
     const bool g_vec = p.gamma == nullptr || (reinterpret_cast<uintptr_t>(p.gamma) & 15u) == 0;
+    const bool g_sm = OP != BOP_SOFTMAX && p.gamma_smem;
+    const float *gs = reinterpret_cast<const float *>(data + static_cast<size_t>(p.nbuf) * 2 * arr);
 
     if (tid == 0) {
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
         mbar_init(&xbar[0], 1);
         mbar_init(&xbar[1], 1);
+        mbar_init(gbar, 1);
         fence_mbar_init();
+        if (g_sm) {  // this CTA's gamma slice, once
+            const uint32_t gbytes = static_cast<uint32_t>(ng) * V * 4u;
+            mbar_arrive_expect_tx(gbar, gbytes);
+            for (uint32_t o = 0; o < gbytes; o += kBwdPiece) {
+                const uint32_t n = gbytes - o < kBwdPiece ? gbytes - o : kBwdPiece;
+                bulk_g2s(reinterpret_cast<unsigned char *>(const_cast<float *>(gs)) + o,
+                         reinterpret_cast<const unsigned char *>(p.gamma + g_lo * V) + o, n, gbar);
+            }
+        }
     }
     __syncthreads();
+    if (g_sm) mbar_wait_bounded(gbar, 0, p.err);
     if (P > 1) {  // every peer's exchange barriers exist before the first push
         cluster_arrive_release();
         cluster_wait_acquire();
@@ -218,7 +236,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
             float fa[V], fd[V], fg[V];
             decode_group<DT>(*reinterpret_cast<const uint4 *>(da + 16 * k), fa, 1.0f);
             decode_group<DT>(*reinterpret_cast<const uint4 *>(dd + 16 * k), fd, 1.0f);
-            load_affine<V>(OP == BOP_SOFTMAX ? nullptr : p.gamma, (g_lo + k) * V, g_vec, 1.0f, fg);
+            if (g_sm) load_affine_smem<V>(gs, k * V, 1.0f, fg);
+            else load_affine<V>(OP == BOP_SOFTMAX ? nullptr : p.gamma, (g_lo + k) * V, g_vec, 1.0f, fg);
 #pragma unroll
             for (int v = 0; v < V; ++v) R.acc(fa[v], fd[v], fg[v], s0, s1);
         }
@@ -249,7 +268,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
             float fa[V], fd[V], fg[V], y[V];
             decode_group<DT>(*reinterpret_cast<const uint4 *>(da + 16 * k), fa, 1.0f);
             decode_group<DT>(*reinterpret_cast<const uint4 *>(dd + 16 * k), fd, 1.0f);
-            load_affine<V>(OP == BOP_SOFTMAX ? nullptr : p.gamma, (g_lo + k) * V, g_vec, 1.0f, fg);
+            if (g_sm) load_affine_smem<V>(gs, k * V, 1.0f, fg);
+            else load_affine<V>(OP == BOP_SOFTMAX ? nullptr : p.gamma, (g_lo + k) * V, g_vec, 1.0f, fg);
 #pragma unroll
             for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], c0, c1);
             store_group<DT, V>(xr + 16 * k, y, true);
@@ -452,26 +472,33 @@ bool rows_aligned(const credit_bwd_args *a) {
 }
 
 struct BwdCfg {
-    int P, nbuf, slice_groups, threads;
+    int P, nbuf, slice_groups, threads, gamma_smem;
     long long smem;
 };
 
-// Staged geometry: the largest slice of P CTAs, nbuf buffers of two slices.
-bool bwd_config(const DeviceInfo &di, long long N, int isz, int P, int req_nbuf, BwdCfg *out) {
+// Staged geometry: the largest slice of P CTAs, nbuf buffers of two slices,
+// and (gamma_smem) the FP32 gamma slice (4 / isz times a slice's bytes).
+bool bwd_config(const DeviceInfo &di, long long N, int isz, int P, int req_nbuf, bool gamma_smem, BwdCfg *out) {
     if (P < 1 || P > kMaxCluster || (P & (P - 1)) != 0) return false;
     const long long Gq = N * isz / 16;
     const long long per = (Gq + P - 1) / P;  // groups of the largest slice
     const long long groups = (per + 7) / 8 * 8;  // 128-byte multiples
     if (groups > (1LL << 24)) return false;
+    const long long gbytes = gamma_smem ? groups * 16 * (4 / isz) : 0;
     for (int nb = 2; nb >= 1; --nb) {
         if (req_nbuf != 0 && nb != req_nbuf) continue;
-        const long long smem = kBwdCtrl + static_cast<long long>(nb) * 2 * groups * 16;
+        const long long smem = kBwdCtrl + static_cast<long long>(nb) * 2 * groups * 16 + gbytes;
         if (smem <= di.smem_optin) {
-            *out = {P, nb, static_cast<int>(groups), kBwdThreads, smem};
+            *out = {P, nb, static_cast<int>(groups), kBwdThreads, gamma_smem ? 1 : 0, smem};
             return true;
         }
     }
     return false;
+}
+
+// gamma is staged in shared memory by the norms when present and 16-byte aligned.
+bool stage_gamma(int op, const float *gamma) {
+    return op != BOP_SOFTMAX && gamma != nullptr && (reinterpret_cast<uintptr_t>(gamma) & 15u) == 0;
 }
 
 credit_status check_bwd_plan(int dev, const credit_bwd_args *a, const credit_plan_t *p, BwdCfg *cfg, int *maxc) {
@@ -489,7 +516,8 @@ credit_status check_bwd_plan(int dev, const credit_bwd_args *a, const credit_pla
     if (p->ring_chunks < 0 || p->ring_chunks > 2) return CREDIT_ERR_UNSUPPORTED;
     if (!rows_aligned(a)) return CREDIT_ERR_UNSUPPORTED;
     const DeviceInfo *di = device_info(dev);
-    if (di == nullptr || !bwd_config(*di, a->cols, dtype_size(a->dtype), P, p->ring_chunks, cfg))
+    if (di == nullptr ||
+        !bwd_config(*di, a->cols, dtype_size(a->dtype), P, p->ring_chunks, stage_gamma(a->op, a->gamma), cfg))
         return CREDIT_ERR_UNSUPPORTED;
     const credit_status st = prepare_staged_kernel(dev, k.staged);
     if (st != CREDIT_OK) return st;
@@ -506,19 +534,19 @@ credit_status plan_bwd_for(int dev, int op, long long cols, int dtype, credit_pl
     if (di != nullptr && cols * isz > kBwdFusedMaxBytes) {
         BwdKernels k;
         if (!bwd_kernels(op, dtype, &k)) return CREDIT_ERR_UNSUPPORTED;
-        for (int want = 2; want >= 1; --want) {
-            for (int P = 1; P <= kMaxCluster; P *= 2) {
-                BwdCfg cfg;
-                if (!bwd_config(*di, cols, isz, P, want, &cfg)) continue;
-                if (prepare_staged_kernel(dev, k.staged) != CREDIT_OK) continue;
-                if (staged_max_clusters(dev, k.staged, P, cfg.threads, cfg.smem, false) <= 0) continue;
-                out->path = P == 1 ? CREDIT_PATH_ONE_CTA : CREDIT_PATH_CLUSTER;
-                out->cluster_size = P;
-                out->ctas_per_row = P;
-                out->ring_chunks = cfg.nbuf;
-                out->smem_bytes = cfg.smem;
-                return CREDIT_OK;
-            }
+        // double-buffered staging only: a single buffer leaves the copies of the next row unoverlapped, which
+        // measured no faster than the global-reread path
+        for (int P = 1; P <= kMaxCluster; P *= 2) {
+            BwdCfg cfg;
+            if (!bwd_config(*di, cols, isz, P, 2, op != BOP_SOFTMAX, &cfg)) continue;
+            if (prepare_staged_kernel(dev, k.staged) != CREDIT_OK) continue;
+            if (staged_max_clusters(dev, k.staged, P, cfg.threads, cfg.smem, false) <= 0) continue;
+            out->path = P == 1 ? CREDIT_PATH_ONE_CTA : CREDIT_PATH_CLUSTER;
+            out->cluster_size = P;
+            out->ctas_per_row = P;
+            out->ring_chunks = cfg.nbuf;
+            out->smem_bytes = cfg.smem;
+            return CREDIT_OK;
         }
     }
     long long g = cols * isz / (256LL << 10);
@@ -612,6 +640,7 @@ credit_status credit_run_bwd(const credit_bwd_args *args, const credit_plan_t *p
         BwdArgs r = base;
         r.nbuf = cfg.nbuf;
         r.slice_groups = cfg.slice_groups;
+        r.gamma_smem = cfg.gamma_smem;
         void *kargs[] = {&r};
         e = launch_kernel(k.staged, dim3(static_cast<unsigned>(cfg.P * ncl)), dim3(cfg.threads),
                           static_cast<size_t>(cfg.smem), cfg.P, stream, kargs);

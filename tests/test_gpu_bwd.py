@@ -110,6 +110,18 @@ def test_tiny_rows_and_empty_slices(op, cols):
         check(op, C.F32, 5, cols, pad(cols, C.F32), plan, seed=cols)
 
 
+@pytest.mark.parametrize("dtype", DTYPES, ids=["f32", "bf16"])
+def test_gamma_staged_or_loaded_gives_the_same_bits(dtype):
+    op, rows, cols = C.LAYERNORM_BWD, 200, 30000
+    a, dy, g, m, r = U.bwd_inputs(op, dtype, rows, cols, seed=13)
+    plan = C.make_plan(C.PATH_CLUSTER, 4)
+    staged = run(op, dtype, a, dy, g, m, r, rows, cols, 0, plan)
+    buf = torch.empty(cols + 1, device="cuda")
+    buf[1:] = g.cuda()
+    loaded = run(op, dtype, a, dy, buf[1:], m, r, rows, cols, 0, plan)  # gamma off the 16-byte grid: L2 loads
+    assert torch.equal(staged, loaded)
+
+
 def test_in_place_matches_out_of_place():
     op, dtype, rows, cols = C.RMSNORM_BWD, C.BF16, 64, 65536
     a, dy, g, m, r = U.bwd_inputs(op, dtype, rows, cols, seed=5)
@@ -160,11 +172,13 @@ def test_refusals_launch_nothing():
 def test_planner_choices():
     narrow = C.plan_bwd(C.LAYERNORM_BWD, 4096, 2048, C.F32)
     assert (narrow.path, narrow.ctas_per_row) == (C.PATH_TWO_PASS, 1)
-    for cols in (16384, 65536, 262144):
+    for cols in (16384, 65536, 131072):  # two row buffers of a and dy plus gamma fit at P = 2, 8, 16
         p = C.plan_bwd(C.RMSNORM_BWD, 4096, cols, C.F32)
-        assert p.path in (C.PATH_ONE_CTA, C.PATH_CLUSTER) and p.smem_bytes > 0
+        assert p.path == C.PATH_CLUSTER and p.ring_chunks == 2 and p.smem_bytes > 0
         x = torch.zeros(4, cols, device="cuda")
-        assert C.bwd_plan_check(C.RMSNORM_BWD, x, x, x, p, rstd=torch.ones(4, device="cuda")) == C.OK
+        g = torch.ones(cols, device="cuda")
+        assert C.bwd_plan_check(C.RMSNORM_BWD, x, x, x, p, gamma=g, rstd=torch.ones(4, device="cuda")) == C.OK
+    assert C.plan_bwd(C.RMSNORM_BWD, 4096, 262144, C.F32).path == C.PATH_TWO_PASS  # only a single buffer fits
     wide = C.plan_bwd(C.SOFTMAX_BWD, 64, 1 << 21, C.F32)
     assert wide.path == C.PATH_TWO_PASS and wide.ctas_per_row > 1
 
