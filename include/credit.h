@@ -314,7 +314,8 @@ typedef struct {
  *       of dy with bulk-async copies, pushes its partial sums to every peer
  *       over DSMEM, and writes its dx segment from shared memory.  ring_chunks
  *       = row buffers per CTA (0: two when they fit, so that the next row
- *       loads while this one is processed; 1 or 2 forced).  The norms also
+ *       loads while this one is processed, else one, refilled chunk by chunk
+ *       behind the write pass; 1 or 2 forced).  The norms also
  *       stage their gamma slice once (when gamma is 16-byte aligned).  Needs 16-byte
  *       aligned rows (a, dy, dx and ld * element size multiples of 16) and
  *       two slices within the opt-in shared memory; otherwise

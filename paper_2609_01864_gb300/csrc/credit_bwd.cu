@@ -55,7 +55,8 @@ namespace {
 enum BwdOp : int { BOP_SOFTMAX = 4, BOP_LN = 5, BOP_RMS = 6 };
 
 constexpr int kBwdThreads = 512;
-constexpr int kBwdCtrl = 1152;             // control area before the row buffers (bytes)
+constexpr int kBwdCtrl = 1280;             // control area before the row buffers (bytes)
+constexpr int kBwdMaxChunks = 8;           // chunks (mbarriers) per row buffer
 constexpr uint32_t kBwdPiece = 32768;      // bytes per bulk copy instruction
 constexpr long long kBwdFusedMaxBytes = 16384;  // planner: fused two-pass up to this many bytes per array row
 
@@ -70,6 +71,7 @@ struct BwdArgs {
     int nbuf;                  // staged: row buffers (1 or 2)
     int slice_groups;          // staged: 16-byte groups per array slice buffer
     int gamma_smem;            // staged: this CTA's gamma slice is staged once in shared memory
+    int nch, chunk_groups;     // staged: chunks per slice and 16-byte groups per chunk
     long long row0;            // first row of this launch
 };
 
@@ -146,20 +148,28 @@ __device__ __forceinline__ float2 block_sum2(float a, float b, float *red) {
 }
 
 // ------------------------------------------------------------------ staged (ONE_CTA / CLUSTER)
-// Shared memory: [0, 16) full[2] mbarriers, [16, 32) xbar[2] mbarriers,
-// [32, 40) gbar mbarrier, [64, 576) reduction scratch, [576, 1088) exchange
-// slots, then nbuf row buffers of (a slice, dy slice), slice_groups * 16
-// bytes each, then (gamma_smem) the CTA's FP32 gamma slice, staged once for
-// all rows: gamma is the same for every row, so the loops read it from shared
-// memory instead of issuing an L2 load per element group.
+// Shared memory: [0, 128) full[2][8] mbarriers (row buffer x chunk), [128,
+// 144) xbar[2] mbarriers, [144, 152) gbar mbarrier, [256, 768) reduction
+// scratch, [768, 1280) exchange slots, then nbuf row buffers of (a slice, dy
+// slice), slice_groups * 16 bytes each, then (gamma_smem) the CTA's FP32
+// gamma slice, staged once for all rows: gamma is the same for every row, so
+// the loops read it from shared memory instead of issuing an L2 load per
+// element group.
+//
+// A slice is processed in nch chunks of chunk_groups groups, each with its
+// own mbarrier, so the sweep starts on chunk 0 while later chunks land.  With
+// two row buffers the whole next row is issued into the other buffer when a
+// row starts.  With one buffer (slices too large for two) chunk q of the next
+// row is issued as soon as every thread has written its outputs of chunk q of
+// this row, so the copies of the next row overlap this row's write pass.
 template <int OP, int DT>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *xbar = full + 2;
-    uint64_t *gbar = full + 4;
-    float *red = reinterpret_cast<float *>(smem + 64);
-    float *slots = reinterpret_cast<float *>(smem + 576);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);  // [b * kBwdMaxChunks + q]
+    uint64_t *xbar = full + 2 * kBwdMaxChunks;
+    uint64_t *gbar = xbar + 2;
+    float *red = reinterpret_cast<float *>(smem + 256);
+    float *slots = reinterpret_cast<float *>(smem + 768);
     unsigned char *data = smem + kBwdCtrl;
     constexpr int isz = Fmt<DT>::size, V = Fmt<DT>::V;
     constexpr int NQ = (OP == BOP_LN) ? 2 : 1;
@@ -173,14 +183,14 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
     const long long tail = N - Gq * V;
     const long long g_lo = group_split(Gq, c, P), g_hi = group_split(Gq, c + 1, P);
     const int ng = static_cast<int>(g_hi - g_lo);
+    const int nch = p.nch, cg = p.chunk_groups;
     const size_t arr = static_cast<size_t>(p.slice_groups) * 16;
     const bool g_vec = p.gamma == nullptr || (reinterpret_cast<uintptr_t>(p.gamma) & 15u) == 0;
     const bool g_sm = OP != BOP_SOFTMAX && p.gamma_smem;
     const float *gs = reinterpret_cast<const float *>(data + static_cast<size_t>(p.nbuf) * 2 * arr);
 
     if (tid == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
+        for (int k = 0; k < 2 * kBwdMaxChunks; ++k) mbar_init(&full[k], 1);
         mbar_init(&xbar[0], 1);
         mbar_init(&xbar[1], 1);
         mbar_init(gbar, 1);
@@ -202,44 +212,68 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
         cluster_wait_acquire();
     }
 
-    // thread 0: stage this CTA's slices of row `row` into buffer b
-    auto issue = [&](long long row, int b) {
-        const size_t off = static_cast<size_t>(row * p.ld + g_lo * V) * isz;
-        unsigned char *da = data + static_cast<size_t>(b) * 2 * arr, *dd = da + arr;
-        const uint32_t bytes = static_cast<uint32_t>(ng) * 16u;
-        mbar_arrive_expect_tx(&full[b], 2 * bytes);
+    // groups [k0, k1) of chunk q of this CTA's slice
+    auto chunk_range = [&](int q, int &k0, int &k1) {
+        k0 = q * cg < ng ? q * cg : ng;
+        k1 = (q + 1) * cg < ng ? (q + 1) * cg : ng;
+    };
+    // thread 0: stage chunk q of this CTA's slices of row `row` into buffer b
+    auto issue_chunk = [&](long long row, int b, int q) {
+        int k0, k1;
+        chunk_range(q, k0, k1);
+        const size_t off = static_cast<size_t>(row * p.ld + (g_lo + k0) * V) * isz;
+        unsigned char *da = data + static_cast<size_t>(b) * 2 * arr + static_cast<size_t>(k0) * 16;
+        unsigned char *dd = da + arr;
+        const uint32_t bytes = static_cast<uint32_t>(k1 - k0) * 16u;
+        uint64_t *bar = &full[b * kBwdMaxChunks + q];
+        mbar_arrive_expect_tx(bar, 2 * bytes);
         for (uint32_t o = 0; o < bytes; o += kBwdPiece) {
             const uint32_t n = bytes - o < kBwdPiece ? bytes - o : kBwdPiece;
-            bulk_g2s(da + o, p.a + off + o, n, &full[b]);
-            bulk_g2s(dd + o, p.dy + off + o, n, &full[b]);
+            bulk_g2s(da + o, p.a + off + o, n, bar);
+            bulk_g2s(dd + o, p.dy + off + o, n, bar);
         }
     };
 
-    if (tid == 0 && cl < p.rows) issue(cl, 0);
+    if (tid == 0 && cl < p.rows)
+        for (int q = 0; q < nch; ++q) issue_chunk(cl, 0, q);
     long long it = 0;
     for (long long row = cl; row < p.rows; row += ncl, ++it) {
         const int b = p.nbuf == 2 ? static_cast<int>(it & 1) : 0;
         const uint32_t fpar = p.nbuf == 2 ? static_cast<uint32_t>((it >> 1) & 1) : static_cast<uint32_t>(it & 1);
-        // the next row into the other buffer (read last in the previous iteration, before its final barrier)
-        if (p.nbuf == 2 && tid == 0 && row + ncl < p.rows) {
+        const bool more = row + ncl < p.rows;
+        // two buffers: the whole next row into the other one (read last in the previous iteration, before
+        // that iteration's final barrier)
+        if (p.nbuf == 2 && tid == 0 && more) {
             fence_proxy_async_smem();
-            issue(row + ncl, b ^ 1);
+            for (int q = 0; q < nch; ++q) issue_chunk(row + ncl, b ^ 1, q);
         }
         BwdRow<OP> R;
         R.load(p, row);
         const unsigned char *da = data + static_cast<size_t>(b) * 2 * arr, *dd = da + arr;
         const size_t row_off = static_cast<size_t>(row * p.ld) * isz;
-        mbar_wait_bounded(&full[b], fpar, p.err);
 
         float s0 = 0.0f, s1 = 0.0f;
-        for (int k = tid; k < ng; k += T) {
-            float fa[V], fd[V], fg[V];
-            decode_group<DT>(*reinterpret_cast<const uint4 *>(da + 16 * k), fa, 1.0f);
-            decode_group<DT>(*reinterpret_cast<const uint4 *>(dd + 16 * k), fd, 1.0f);
-            if (g_sm) load_affine_smem<V>(gs, k * V, 1.0f, fg);
-            else load_affine<V>(OP == BOP_SOFTMAX ? nullptr : p.gamma, (g_lo + k) * V, g_vec, 1.0f, fg);
+        auto sweep = [&](int k0, int k1) {
+            for (int k = k0 + tid; k < k1; k += T) {
+                float fa[V], fd[V], fg[V];
+                decode_group<DT>(*reinterpret_cast<const uint4 *>(da + 16 * k), fa, 1.0f);
+                decode_group<DT>(*reinterpret_cast<const uint4 *>(dd + 16 * k), fd, 1.0f);
+                if (g_sm) load_affine_smem<V>(gs, k * V, 1.0f, fg);
+                else load_affine<V>(OP == BOP_SOFTMAX ? nullptr : p.gamma, (g_lo + k) * V, g_vec, 1.0f, fg);
 #pragma unroll
-            for (int v = 0; v < V; ++v) R.acc(fa[v], fd[v], fg[v], s0, s1);
+                for (int v = 0; v < V; ++v) R.acc(fa[v], fd[v], fg[v], s0, s1);
+            }
+        };
+        if (nch == 1) {
+            mbar_wait_bounded(&full[b * kBwdMaxChunks], fpar, p.err);
+            sweep(0, ng);
+        } else {
+            for (int q = 0; q < nch; ++q) {
+                int k0, k1;
+                chunk_range(q, k0, k1);
+                mbar_wait_bounded(&full[b * kBwdMaxChunks + q], fpar, p.err);
+                sweep(k0, k1);
+            }
         }
         if (c == P - 1) {
             for (long long t = tid; t < tail; t += T) {
@@ -263,18 +297,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
         }
         float c0, c1;
         row_coeffs<OP>(tot.x, tot.y, N, c0, c1);
-        unsigned char *xr = p.dx + row_off + static_cast<size_t>(g_lo * V) * isz;
-        for (int k = tid; k < ng; k += T) {
-            float fa[V], fd[V], fg[V], y[V];
-            decode_group<DT>(*reinterpret_cast<const uint4 *>(da + 16 * k), fa, 1.0f);
-            decode_group<DT>(*reinterpret_cast<const uint4 *>(dd + 16 * k), fd, 1.0f);
-            if (g_sm) load_affine_smem<V>(gs, k * V, 1.0f, fg);
-            else load_affine<V>(OP == BOP_SOFTMAX ? nullptr : p.gamma, (g_lo + k) * V, g_vec, 1.0f, fg);
-#pragma unroll
-            for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], c0, c1);
-            store_group<DT, V>(xr + 16 * k, y, true);
-        }
-        if (c == P - 1) {
+        if (c == P - 1) {  // the elements past the last full group, from global memory
             for (long long t = tid; t < tail; t += T) {
                 const long long i = Gq * V + t;
                 const float gm = (OP != BOP_SOFTMAX && p.gamma) ? p.gamma[i] : 1.0f;
@@ -283,10 +306,33 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
                 store_one<DT>(p.dx + row_off + i * isz, v);
             }
         }
-        __syncthreads();  // every read of buffer b is done before it is refilled
-        if (p.nbuf == 1 && tid == 0 && row + ncl < p.rows) {
-            fence_proxy_async_smem();
-            issue(row + ncl, 0);
+        unsigned char *xr = p.dx + row_off + static_cast<size_t>(g_lo * V) * isz;
+        auto write = [&](int k0, int k1) {
+            for (int k = k0 + tid; k < k1; k += T) {
+                float fa[V], fd[V], fg[V], y[V];
+                decode_group<DT>(*reinterpret_cast<const uint4 *>(da + 16 * k), fa, 1.0f);
+                decode_group<DT>(*reinterpret_cast<const uint4 *>(dd + 16 * k), fd, 1.0f);
+                if (g_sm) load_affine_smem<V>(gs, k * V, 1.0f, fg);
+                else load_affine<V>(OP == BOP_SOFTMAX ? nullptr : p.gamma, (g_lo + k) * V, g_vec, 1.0f, fg);
+#pragma unroll
+                for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], c0, c1);
+                store_group<DT, V>(xr + 16 * k, y, true);
+            }
+        };
+        if (p.nbuf == 2) {
+            write(0, ng);
+            __syncthreads();  // every read of buffer b is done before it is refilled
+        } else {
+            for (int q = 0; q < nch; ++q) {
+                int k0, k1;
+                chunk_range(q, k0, k1);
+                write(k0, k1);
+                __syncthreads();  // every read of chunk q is done before it is refilled
+                if (tid == 0 && more) {
+                    fence_proxy_async_smem();
+                    issue_chunk(row + ncl, 0, q);
+                }
+            }
         }
     }
     if (P > 1) {  // nobody exits while a peer may still push into it
@@ -472,7 +518,7 @@ bool rows_aligned(const credit_bwd_args *a) {
 }
 
 struct BwdCfg {
-    int P, nbuf, slice_groups, threads, gamma_smem;
+    int P, nbuf, slice_groups, threads, gamma_smem, nch, chunk_groups;
     long long smem;
 };
 
@@ -489,7 +535,18 @@ bool bwd_config(const DeviceInfo &di, long long N, int isz, int P, int req_nbuf,
         if (req_nbuf != 0 && nb != req_nbuf) continue;
         const long long smem = kBwdCtrl + static_cast<long long>(nb) * 2 * groups * 16 + gbytes;
         if (smem <= di.smem_optin) {
-            *out = {P, nb, static_cast<int>(groups), kBwdThreads, gamma_smem ? 1 : 0, smem};
+            // two buffers: one chunk (the whole next row is in flight anyway).  One buffer: at most
+            // kBwdMaxChunks chunks whose size is a multiple of the thread count, so that every thread sums
+            // the same groups in the same order as with one chunk (the result does not depend on the
+            // buffering)
+            long long cgr = groups > 0 ? groups : 1, nch = 1;
+            if (nb == 1 && groups > kBwdThreads) {
+                const long long per_chunk = (groups + kBwdMaxChunks - 1) / kBwdMaxChunks;
+                cgr = (per_chunk + kBwdThreads - 1) / kBwdThreads * kBwdThreads;
+                nch = (groups + cgr - 1) / cgr;
+            }
+            *out = {P, nb, static_cast<int>(groups), kBwdThreads, gamma_smem ? 1 : 0, static_cast<int>(nch),
+                    static_cast<int>(cgr), smem};
             return true;
         }
     }
@@ -641,6 +698,8 @@ credit_status credit_run_bwd(const credit_bwd_args *args, const credit_plan_t *p
         r.nbuf = cfg.nbuf;
         r.slice_groups = cfg.slice_groups;
         r.gamma_smem = cfg.gamma_smem;
+        r.nch = cfg.nch;
+        r.chunk_groups = cfg.chunk_groups;
         void *kargs[] = {&r};
         e = launch_kernel(k.staged, dim3(static_cast<unsigned>(cfg.P * ncl)), dim3(cfg.threads),
                           static_cast<size_t>(cfg.smem), cfg.P, stream, kargs);

@@ -92,6 +92,13 @@ def test_many_rows_recycle_buffers_and_slots(op):
         check(op, C.F32, 1500, 8195, 8196, plan, seed=11 + P)
 
 
+@pytest.mark.parametrize("op", OPS, ids=["softmax", "layernorm", "rmsnorm"])
+def test_single_buffer_refilled_chunk_by_chunk(op):
+    # 64 KiB slices at P = 16: only one row buffer fits, refilled in 8 chunks behind the write pass
+    check(op, C.F32, 300, 262147, 262148, C.make_plan(C.PATH_CLUSTER, 16), seed=17)
+    check(op, C.BF16, 200, 300007, 300008, C.make_plan(C.PATH_CLUSTER, 16, ring_chunks=1), seed=19)
+
+
 def test_single_and_double_buffering_agree_bitwise():
     op, dtype, rows, cols = C.LAYERNORM_BWD, C.F32, 300, 40000
     a, dy, g, m, r = U.bwd_inputs(op, dtype, rows, cols, seed=3)
