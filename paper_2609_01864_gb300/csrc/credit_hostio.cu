@@ -165,8 +165,11 @@ extern "C" credit_status credit_run_host(const credit_args *args, const credit_p
         const long long n = rows - r0 < br ? rows - r0 : br;
         // copy-in (slot k free once its previous copy-out finished)
         if (b >= kBlocks && (e = cudaStreamWaitEvent(io.s_in, io.out_done[k], 0)) != cudaSuccess) break;
-        e = cudaMemcpy2DAsync(io.in_buf[k], row_in, hin + r0 * ld_in * isz, ld_in * isz, row_in, n,
-                              cudaMemcpyHostToDevice, io.s_in);
+        if (ld_in * isz == row_in)  // contiguous rows: one plain copy
+            e = cudaMemcpyAsync(io.in_buf[k], hin + r0 * row_in, n * row_in, cudaMemcpyHostToDevice, io.s_in);
+        else
+            e = cudaMemcpy2DAsync(io.in_buf[k], row_in, hin + r0 * ld_in * isz, ld_in * isz, row_in, n,
+                                  cudaMemcpyHostToDevice, io.s_in);
         if (e == cudaSuccess && tin == CREDIT_FP8_E4M3)
             e = cudaMemcpyAsync(io.isc[k], args->in_scale + r0, n * 4, cudaMemcpyHostToDevice, io.s_in);
         if (e == cudaSuccess) e = cudaEventRecord(io.in_done[k], io.s_in);
@@ -190,6 +193,8 @@ extern "C" credit_status credit_run_host(const credit_args *args, const credit_p
         if ((e = cudaStreamWaitEvent(io.s_out, io.op_done[k], 0)) != cudaSuccess) break;
         if (lse)
             e = cudaMemcpyAsync(hout + r0 * 4, io.out_buf[k], n * 4, cudaMemcpyDeviceToHost, io.s_out);
+        else if (ld_out * osz == row_out)
+            e = cudaMemcpyAsync(hout + r0 * row_out, io.out_buf[k], n * row_out, cudaMemcpyDeviceToHost, io.s_out);
         else
             e = cudaMemcpy2DAsync(hout + r0 * ld_out * osz, ld_out * osz, io.out_buf[k], row_out, row_out, n,
                                   cudaMemcpyDeviceToHost, io.s_out);
