@@ -37,6 +37,7 @@ _lib = None
 
 F32, BF16, E4M3 = 0, 1, 2
 SOFTMAX, LOGSUMEXP, LAYERNORM, RMSNORM = 0, 1, 2, 3
+SOFTMAX_LOGITS, XENT = 7, 8  # backward ops from logits (run_bwd only)
 DTYPE_SIZE = {F32: 4, BF16: 2, E4M3: 1}
 E4M3_MAX = 448.0
 
@@ -82,6 +83,8 @@ def lib() -> ctypes.CDLL:
             L.oracle_softmax_bwd_row.argtypes = [vp, vp, i64, vp]
             L.oracle_layernorm_bwd_row.argtypes = [vp, vp, i64, vp, d, d, vp]
             L.oracle_rmsnorm_bwd_row.argtypes = [vp, vp, i64, vp, d, vp]
+            L.oracle_softmax_logits_bwd_row.argtypes = [vp, vp, i64, vp]
+            L.oracle_xent_bwd_row.argtypes = [vp, vp, i64, d, vp]
             L.oracle_run_bwd.restype = i32
             L.oracle_run_bwd.argtypes = [i32, i32, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp, i32]
             L.oracle_max_threads.restype = i32
@@ -230,12 +233,33 @@ def rmsnorm_bwd(x, dy, rstd, gamma=None):
     return dx
 
 
+def softmax_logits_bwd(z, dy):
+    """dz of softmax given its logits z (the output is recomputed) and the upstream gradient dy (FP64)."""
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    dy = np.ascontiguousarray(dy, dtype=np.float64)
+    dz = np.empty_like(z)
+    for r in range(z.shape[0]):
+        lib().oracle_softmax_logits_bwd_row(_ptr(z[r]), _ptr(dy[r]), z.shape[1], _ptr(dz[r]))
+    return dz
+
+
+def xent_bwd(z, t, w=None):
+    """dz of the cross entropy -sum t log softmax(z) per row, times the row scale w (None = 1) (FP64)."""
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    dz = np.empty_like(z)
+    for r in range(z.shape[0]):
+        lib().oracle_xent_bwd_row(_ptr(z[r]), _ptr(t[r]), z.shape[1], 1.0 if w is None else float(w[r]), _ptr(dz[r]))
+    return dz
+
+
 def run_bwd(op: int, dtype: int, a_raw, dy_raw, rows: int, cols: int, *, gamma=None, mean=None, rstd=None,
             ld: int = 0, want_exact: bool = True, want_encoded: bool = False, nthreads: int = 0):
-    """Batch input gradient.  op is the forward op (SOFTMAX, LAYERNORM, RMSNORM); a_raw is the forward
-    output (softmax) or input (norms), dy_raw the upstream gradient, both stored elements of dtype (F32 /
-    BF16 codes) with row stride ld; gamma, mean, rstd are FP32 arrays.  Returns (dx64 or None, encoded or
-    None)."""
+    """Batch input gradient.  op is the forward op (SOFTMAX, LAYERNORM, RMSNORM) or SOFTMAX_LOGITS / XENT;
+    a_raw is the forward output (softmax), input (norms) or the logits (SOFTMAX_LOGITS, XENT), dy_raw the
+    upstream gradient (XENT: the target weights), both stored elements of dtype (F32 / BF16 codes) with row
+    stride ld; gamma, mean, rstd (XENT: the per-row upstream scale) are FP32 arrays.  Returns (dx64 or None,
+    encoded or None)."""
     a_raw = np.ascontiguousarray(a_raw)
     dy_raw = np.ascontiguousarray(dy_raw)
     f32 = lambda v: None if v is None else np.ascontiguousarray(v, dtype=np.float32)  # noqa: E731

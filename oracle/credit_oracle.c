@@ -47,6 +47,7 @@
 
 enum { OR_F32 = 0, OR_BF16 = 1, OR_E4M3 = 2 };
 enum { OR_SOFTMAX = 0, OR_LOGSUMEXP = 1, OR_LAYERNORM = 2, OR_RMSNORM = 3 };
+enum { OR_SOFTMAX_LOGITS = 7, OR_XENT = 8 };  /* backward batch only */
 
 /* ------------------------------------------------------------------ */
 /* Compensated (Neumaier) summation                                    */
@@ -248,6 +249,30 @@ void oracle_rmsnorm_bwd_row(const double *x, const double *dy, int64_t n, const 
     }
 }
 
+/* Gradients with respect to the logits z of a softmax (the "softmax-logits */
+/* backward" workload of Sec. IV-A), where y = softmax(z) is recomputed    */
+/* from z rather than read:                                               */
+/*   through the softmax, given dy:   dz_i = y_i (dy_i - sum_j y_j dy_j)   */
+/*   of the cross entropy L = -sum_j t_j log y_j with target weights t    */
+/*   (soft labels), times a per-row upstream scale w:                     */
+/*                                    dz_i = w (y_i sum_j t_j - t_i)      */
+/* (dL/dz_k = -sum_i t_i (delta_ik - y_k)).                               */
+void oracle_softmax_logits_bwd_row(const double *z, const double *dy, int64_t n, double *dz) {
+    double *y = (double *)malloc((size_t)n * sizeof(double));
+    if (!y) { for (int64_t i = 0; i < n; ++i) dz[i] = NAN; return; }
+    oracle_softmax_row(z, n, y);
+    oracle_softmax_bwd_row(y, dy, n, dz);
+    free(y);
+}
+
+void oracle_xent_bwd_row(const double *z, const double *t, int64_t n, double w, double *dz) {
+    oracle_softmax_row(z, n, dz);
+    nsum_t T = {0, 0};
+    for (int64_t i = 0; i < n; ++i) nsum_add(&T, t[i]);
+    double tt = nsum_get(&T);
+    for (int64_t i = 0; i < n; ++i) dz[i] = w * (dz[i] * tt - t[i]);
+}
+
 /* ------------------------------------------------------------------ */
 /* Batch driver: decode -> op -> (exact doubles, encoded output)        */
 /* ------------------------------------------------------------------ */
@@ -347,10 +372,12 @@ int oracle_run(int op, int in_dtype, int out_dtype, const void *in,
 
 /*
  * Backward batch.  op: 0 softmax, 2 layernorm, 3 rmsnorm (the forward op's
- * code).  a (softmax: the forward output y; norms: the forward input x) and
- * dy hold rows x cols elements of dtype (F32 or BF16) with row stride ld;
- * gamma (cols FP32, NULL = 1), mean (rows FP32, layernorm) and rstd (rows
- * FP32, norms) are decoded exactly.  dx64 (may be NULL) receives the exact
+ * code), 7 softmax from logits, 8 cross entropy from logits.  a (softmax:
+ * the forward output y; norms: the forward input x; 7 and 8: the logits z)
+ * and dy (8: the target weights t) hold rows x cols elements of dtype (F32
+ * or BF16) with row stride ld; gamma (cols FP32, NULL = 1), mean (rows FP32,
+ * layernorm) and rstd (rows FP32, norms; for 8 the per-row upstream scale w,
+ * NULL = 1) are decoded exactly.  dx64 (may be NULL) receives the exact
  * rows*cols result, dx (may be NULL) the result rounded to dtype with row
  * stride ld.  Returns 0, or -1 on a bad argument.
  */
@@ -358,7 +385,9 @@ int oracle_run_bwd(int op, int dtype, const void *a, const void *dy, int64_t row
                    const float *gamma, const float *mean, const float *rstd, double *dx64, void *dx,
                    int nthreads) {
     if (rows < 0 || cols <= 0 || !a || !dy) return -1;
-    if (!(op == OR_SOFTMAX || op == OR_LAYERNORM || op == OR_RMSNORM) || dtype < 0 || dtype > 1) return -1;
+    if (!(op == OR_SOFTMAX || op == OR_LAYERNORM || op == OR_RMSNORM || op == OR_SOFTMAX_LOGITS ||
+          op == OR_XENT) || dtype < 0 || dtype > 1)
+        return -1;
     if (op == OR_LAYERNORM && (!mean || !rstd)) return -1;
     if (op == OR_RMSNORM && !rstd) return -1;
     if (ld <= 0) ld = cols;
@@ -388,6 +417,8 @@ int oracle_run_bwd(int op, int dtype, const void *a, const void *dy, int64_t row
                     d[i] = decode_one(dr, dtype, i);
                 }
                 if (op == OR_SOFTMAX) oracle_softmax_bwd_row(x, d, cols, o);
+                else if (op == OR_SOFTMAX_LOGITS) oracle_softmax_logits_bwd_row(x, d, cols, o);
+                else if (op == OR_XENT) oracle_xent_bwd_row(x, d, cols, rstd ? (double)rstd[r] : 1.0, o);
                 else if (op == OR_LAYERNORM)
                     oracle_layernorm_bwd_row(x, d, cols, g, (double)mean[r], (double)rstd[r], o);
                 else oracle_rmsnorm_bwd_row(x, d, cols, g, (double)rstd[r], o);

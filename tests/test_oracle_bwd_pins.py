@@ -238,3 +238,78 @@ def test_batch_driver_rejects_bad_arguments():
         O.run_bwd(O.RMSNORM, O.F32, a, a, 2, 8)                           # no rstd
     with pytest.raises(ValueError):
         O.run_bwd(O.SOFTMAX, O.E4M3, a.view(np.uint8), a.view(np.uint8), 2, 8)
+
+
+# ---------------------------------------------------------------- gradients with respect to the logits
+def _xent_loss(z, t):
+    """-sum_j t_j log softmax(z)_j per row, through the oracle's log-sum-exp: log y_j = z_j - LSE(z)."""
+    return -(t * (z - O.logsumexp(z)[:, None])).sum(axis=1)
+
+
+@pytest.mark.parametrize("n", [2, 7, 33])
+def test_softmax_logits_bwd_matches_finite_differences(n):
+    z, dy, _, _ = _row_case(11, n)
+    dz = O.softmax_logits_bwd(z, dy)
+    fd = _fd_grad(O.softmax, z, dy)
+    assert np.abs(dz - fd).max() <= 1e-8 * max(1.0, np.abs(fd).max())
+    assert np.array_equal(dz, O.softmax_bwd(O.softmax(z), dy))  # the composition it is defined as
+
+
+@pytest.mark.parametrize("n", [2, 7, 33])
+def test_xent_bwd_matches_finite_differences(n):
+    r = _rng(12)
+    z = r.standard_normal((3, n)) * 3.0
+    t = r.uniform(0.0, 1.0, (3, n))            # soft labels that do not sum to one
+    w = np.array([1.0, 0.5, -2.0])
+    dz = O.xent_bwd(z, t, w)
+    h = 1e-5
+    fd = np.empty_like(z)
+    for k in range(n):
+        zp, zm = z.copy(), z.copy()
+        zp[:, k] += h
+        zm[:, k] -= h
+        fd[:, k] = w * (_xent_loss(zp, t) - _xent_loss(zm, t)) / (2 * h)
+    assert np.abs(dz - fd).max() <= 1e-8 * max(1.0, np.abs(fd).max())
+
+
+def test_logits_gradients_against_torch_and_special_cases():
+    r = _rng(13)
+    z = r.standard_normal((4, 200)) * 3.0
+    dy = r.standard_normal((4, 200))
+    t = r.dirichlet(np.ones(200), size=4)        # probability targets
+    w = r.uniform(0.5, 2.0, 4)
+    tz = torch.tensor(z, requires_grad=True)
+    torch.softmax(tz, dim=1).backward(torch.tensor(dy))
+    assert np.allclose(O.softmax_logits_bwd(z, dy), tz.grad.numpy(), rtol=1e-12, atol=1e-15)
+    tz = torch.tensor(z, requires_grad=True)
+    F.cross_entropy(tz, torch.tensor(t), reduction="none").backward(torch.tensor(w))
+    assert np.allclose(O.xent_bwd(z, t, w), tz.grad.numpy(), rtol=1e-12, atol=1e-15)
+    # shift invariance: the gradients sum to zero
+    assert np.abs(O.softmax_logits_bwd(z, dy).sum(axis=1)).max() <= 1e-14
+    assert np.abs(O.xent_bwd(z, t, w).sum(axis=1)).max() <= 1e-14
+    # the target equal to the prediction: no gradient; a one-hot target: y - e_k
+    assert np.abs(O.xent_bwd(z, O.softmax(z))).max() <= 1e-16
+    onehot = np.zeros_like(z)
+    onehot[np.arange(4), [3, 50, 100, 199]] = 1.0
+    assert np.allclose(O.xent_bwd(z, onehot), O.softmax(z) - onehot, rtol=0, atol=1e-16)
+
+
+@pytest.mark.parametrize("dtype", [O.F32, O.BF16])
+def test_batch_driver_logits_ops(dtype):
+    r = _rng(14)
+    rows, cols = 5, 61
+    z = (r.standard_normal((rows, cols)) * 3).astype(np.float32)
+    d = r.uniform(0, 1, (rows, cols)).astype(np.float32)
+    w = r.uniform(0.5, 2, rows).astype(np.float32)
+    if dtype == O.BF16:
+        zr = torch.from_numpy(z).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        dr = torch.from_numpy(d).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        zd, dd = O.bf16_to_double(zr), O.bf16_to_double(dr)
+    else:
+        zr, dr, zd, dd = z, d, z.astype(np.float64), d.astype(np.float64)
+    dx64, _ = O.run_bwd(O.SOFTMAX_LOGITS, dtype, zr, dr, rows, cols)
+    assert np.array_equal(dx64, O.softmax_logits_bwd(zd, dd))
+    dx64, _ = O.run_bwd(O.XENT, dtype, zr, dr, rows, cols, rstd=w)
+    assert np.array_equal(dx64, O.xent_bwd(zd, dd, w.astype(np.float64)))
+    dx64, _ = O.run_bwd(O.XENT, dtype, zr, dr, rows, cols)  # no scale: 1
+    assert np.array_equal(dx64, O.xent_bwd(zd, dd))
