@@ -508,7 +508,8 @@ BWD_WIDTHS = [16384, 65536, 131072, 262144]
 
 
 def run_bwd_bench(C, torch, dev, synth):
-    """The backward ops (dx of softmax, LayerNorm, RMSNorm; FP32, 4096 rows): every candidate plan timed
+    """The backward ops (dx of softmax, LayerNorm, RMSNorm; dz of softmax and of the cross entropy from
+    logits, with the same arrays as logits and as targets; FP32, 4096 rows): every candidate plan timed
     (median of 5, CUDA events), the planner's pick, the best non-DSMEM plan and the speed-up of the pick
     over it.  Algorithmic bytes: one read of a and of dy, one write of dx (12 B per element)."""
     peak, peak_kind = measured_peak()
@@ -528,7 +529,9 @@ def run_bwd_bench(C, torch, dev, synth):
         nbytes = ROWS * cols * 12
         for op, name, kw in ((C.SOFTMAX_BWD, "softmax_bwd", {}),
                              (C.LAYERNORM_BWD, "layernorm_bwd", dict(gamma=g, mean=mean, rstd=rstd_ln)),
-                             (C.RMSNORM_BWD, "rmsnorm_bwd", dict(gamma=g, rstd=rstd_rms))):
+                             (C.RMSNORM_BWD, "rmsnorm_bwd", dict(gamma=g, rstd=rstd_rms)),
+                             (C.SOFTMAX_LOGITS_BWD, "softmax_logits_bwd", {}),
+                             (C.XENT_BWD, "xent_bwd", {})):
             cands = [(f"two_pass_g{G}", C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)) for G in (1, 2, 4, 8)]
             cands.append(("one_cta", C.make_plan(C.PATH_ONE_CTA)))
             cands += [(f"cluster{P}", C.make_plan(C.PATH_CLUSTER, P)) for P in (2, 4, 8, 16)]

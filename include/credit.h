@@ -273,6 +273,13 @@ credit_status credit_plan_check(const credit_args *args, const credit_plan_t *pl
  *                            dx_i = rstd (g_i - sum_j g_j / N - xh_i sum_j g_j xh_j / N)
  *   CREDIT_OP_RMSNORM_BWD    a = x (RMSNorm input), xh_i = x_i rstd,
  *                            dx_i = rstd (g_i - xh_i sum_j g_j xh_j / N)
+ * and two gradients with respect to logits z (the "softmax-logits backward"
+ * workload), where y = softmax(z) is recomputed from z in the same sweep
+ * with online (max, sum exp) statistics instead of being read:
+ *   CREDIT_OP_SOFTMAX_LOGITS_BWD  a = z, dy:  dz_i = y_i (dy_i - sum_j y_j dy_j)
+ *   CREDIT_OP_XENT_BWD       a = z, dy = t (target weights, soft labels),
+ *                            scale = w (per row, NULL = 1): the gradient of
+ *                            w * (-sum_j t_j log y_j), dz_i = w (y_i sum_j t_j - t_i)
  * mean / rstd are the forward's saved row statistics (rstd = 1/sqrt(var +
  * eps) for LayerNorm, 1/sqrt(sum x^2 / N + eps) for RMSNorm), FP32 per row.
  * Only dx is computed (the parameter gradients dgamma / dbeta are column
@@ -282,7 +289,9 @@ credit_status credit_plan_check(const credit_args *args, const credit_plan_t *pl
 typedef enum {
     CREDIT_OP_SOFTMAX_BWD = 4,
     CREDIT_OP_LAYERNORM_BWD = 5,
-    CREDIT_OP_RMSNORM_BWD = 6
+    CREDIT_OP_RMSNORM_BWD = 6,
+    CREDIT_OP_SOFTMAX_LOGITS_BWD = 7,
+    CREDIT_OP_XENT_BWD = 8
 } credit_bwd_op;
 
 /*
@@ -294,6 +303,7 @@ typedef enum {
  *   gamma      norms: cols FP32, NULL = 1; ignored by softmax
  *   mean       LAYERNORM_BWD: rows FP32 (required)
  *   rstd       LAYERNORM_BWD / RMSNORM_BWD: rows FP32 (required)
+ *   scale      XENT_BWD: rows FP32 upstream gradients of the row losses (NULL = 1); ignored otherwise
  */
 typedef struct {
     int32_t op;
@@ -305,6 +315,7 @@ typedef struct {
     const float *gamma;
     const float *mean;
     const float *rstd;
+    const float *scale;
 } credit_bwd_args;
 
 /*

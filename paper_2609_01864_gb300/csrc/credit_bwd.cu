@@ -52,7 +52,9 @@ extern std::atomic<long long> g_launch_count;
 
 namespace {
 
-enum BwdOp : int { BOP_SOFTMAX = 4, BOP_LN = 5, BOP_RMS = 6 };
+enum BwdOp : int { BOP_SOFTMAX = 4, BOP_LN = 5, BOP_RMS = 6, BOP_SMLOGITS = 7, BOP_XENT = 8 };
+template <int OP> constexpr bool kLogits = OP == BOP_SMLOGITS || OP == BOP_XENT;  // online max statistics
+template <int OP> constexpr bool kNorm = OP == BOP_LN || OP == BOP_RMS;          // gamma, saved statistics
 
 constexpr int kBwdThreads = 512;
 constexpr int kBwdCtrl = 1280;             // control area before the row buffers (bytes)
@@ -65,8 +67,9 @@ struct BwdArgs {
     unsigned char *dx;
     long long rows, cols, ld;  // ld in elements (all three arrays)
     const float *gamma, *mean, *rstd;
+    const float *scale;        // cross entropy: per-row upstream scale (null = 1)
     unsigned *err;
-    float *ws;                 // two-pass partials [row - row0][G][2]
+    float *ws;                 // two-pass partials [row - row0][G][2] ([G][4] for the logits ops)
     int G;                     // two-pass CTAs per row
     int nbuf;                  // staged: row buffers (1 or 2)
     int slice_groups;          // staged: 16-byte groups per array slice buffer
@@ -76,12 +79,17 @@ struct BwdArgs {
 };
 
 // Per-row constants and the per-element math of each op.
+struct Coef {
+    float c0, c1, c2;
+};
+
 template <int OP>
 struct BwdRow {
-    float mean = 0.0f, rstd = 1.0f;
+    float mean = 0.0f, rstd = 1.0f, w = 1.0f;
     __device__ __forceinline__ void load(const BwdArgs &p, long long row) {
         if constexpr (OP == BOP_LN) mean = p.mean[row];
-        if constexpr (OP != BOP_SOFTMAX) rstd = p.rstd[row];
+        if constexpr (kNorm<OP>) rstd = p.rstd[row];
+        if constexpr (OP == BOP_XENT) w = p.scale ? p.scale[row] : 1.0f;
     }
     // add element (a, dy, gamma) to the partial sums
     __device__ __forceinline__ void acc(float a, float d, float gm, float &s0, float &s1) const {
@@ -94,32 +102,177 @@ struct BwdRow {
             s1 = fmaf(g, xh, s1);
         }
     }
-    // dx of element (a, dy, gamma) given c0 = S0 (softmax) or S0 / N, c1 = S1 / N
-    __device__ __forceinline__ float dx(float a, float d, float gm, float c0, float c1) const {
+    // dx of element (a, dy, gamma) given the row coefficients: c0 = S0 (softmax) or S0 / N, c1 = S1 / N
+    // (norms); c0 = max, c1 = 1 / S, c2 = T / S (softmax from logits); c0 = max, c1 = T / S (cross entropy)
+    __device__ __forceinline__ float dx(float a, float d, float gm, const Coef &k) const {
         if constexpr (OP == BOP_SOFTMAX) {
-            return a * (d - c0);
+            return a * (d - k.c0);
+        } else if constexpr (OP == BOP_SMLOGITS) {
+            return exp_fast(a - k.c0) * k.c1 * (d - k.c2);
+        } else if constexpr (OP == BOP_XENT) {
+            return w * (exp_fast(a - k.c0) * k.c1 - d);
         } else {
             const float g = d * gm;
             const float xh = (OP == BOP_LN ? a - mean : a) * rstd;
-            return rstd * (g - c0 - xh * c1);
+            return rstd * (g - k.c0 - xh * k.c1);
         }
     }
 };
 
-// c0, c1 from the row totals (S0, S1) and N.
+// Per-thread (and per-CTA) statistics.  Ops 4-6: the plain sums s0, s1.
+// Ops 7-8: an online (max m, S = sum exp(z - m), T) triple, T = sum exp(z -
+// m) dy (softmax from logits) or sum t (cross entropy); the max of each
+// 16-byte group is folded in before its exponentials, as in the forward
+// softmax.  merge() is commutative bit for bit, so a shuffle tree gives the
+// same state in both lanes of every pair.
+template <int OP, bool L = kLogits<OP>>
+struct BwdState;
+
 template <int OP>
-__device__ __forceinline__ void row_coeffs(float S0, float S1, long long N, float &c0, float &c1) {
-    const float inv_n = 1.0f / static_cast<float>(N);
-    if constexpr (OP == BOP_SOFTMAX) {
-        c0 = S0;
-        c1 = 0.0f;
-    } else if constexpr (OP == BOP_LN) {
-        c0 = S0 * inv_n;
-        c1 = S1 * inv_n;
-    } else {
-        c0 = 0.0f;
-        c1 = S1 * inv_n;
+struct BwdState<OP, false> {
+    float s0 = 0.0f, s1 = 0.0f;
+    template <int V>
+    __device__ __forceinline__ void add(const BwdRow<OP> &R, const float (&fa)[V], const float (&fd)[V],
+                                        const float (&fg)[V]) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) R.acc(fa[v], fd[v], fg[v], s0, s1);
     }
+    __device__ __forceinline__ void add1(const BwdRow<OP> &R, float a, float d, float g) { R.acc(a, d, g, s0, s1); }
+};
+
+template <int OP>
+struct BwdState<OP, true> {
+    float m = -INFINITY, S = 0.0f, T = 0.0f;
+    template <int V>
+    __device__ __forceinline__ void add(const BwdRow<OP> &, const float (&fa)[V], const float (&fd)[V],
+                                        const float (&)[V]) {
+        if constexpr (OP == BOP_XENT) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) T += fd[v];
+        }
+        float mv = fa[0];
+#pragma unroll
+        for (int v = 1; v < V; ++v) mv = fmaxf(mv, fa[v]);
+        if (mv == -INFINITY) return;
+        if (mv > m) {
+            const float r = exp_fast(m - mv);
+            S *= r;
+            if constexpr (OP == BOP_SMLOGITS) T *= r;
+            m = mv;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float e = exp_fast(fa[v] - m);
+            S += e;
+            if constexpr (OP == BOP_SMLOGITS) T = fmaf(e, fd[v], T);
+        }
+    }
+    __device__ __forceinline__ void add1(const BwdRow<OP> &R, float a, float d, float g) {
+        const float fa[1] = {a}, fd[1] = {d}, fg[1] = {g};
+        add<1>(R, fa, fd, fg);
+    }
+    __device__ __forceinline__ void merge(float m2, float S2, float T2) {
+        if constexpr (OP == BOP_XENT) T += T2;
+        if (S2 == 0.0f) return;
+        if (S == 0.0f) {
+            m = m2;
+            S = S2;
+            if constexpr (OP == BOP_SMLOGITS) T = T2;
+            return;
+        }
+        const float M = fmaxf(m, m2), ra = exp_fast(m - M), rb = exp_fast(m2 - M);
+        S = S * ra + S2 * rb;
+        if constexpr (OP == BOP_SMLOGITS) T = T * ra + T2 * rb;
+        m = M;
+    }
+};
+
+template <int OP>
+__device__ __forceinline__ Coef logit_coeffs(float M, float S, float T) {
+    const float inv = 1.0f / S;
+    if constexpr (OP == BOP_SMLOGITS) return {M, inv, T * inv};
+    else return {M, T * inv, 0.0f};
+}
+
+// Shuffle-tree merge of the logits state over groups of `width` lanes (a
+// power of two).  The tree is fixed and merge() commutative, so every lane
+// of a group ends with the same state; merging an empty state is exact.
+template <int OP>
+__device__ __forceinline__ void warp_merge_logits(BwdState<OP, true> &st, int width) {
+    for (int o = width >> 1; o > 0; o >>= 1) {
+        const float m2 = __shfl_xor_sync(0xffffffffu, st.m, o);
+        const float S2 = __shfl_xor_sync(0xffffffffu, st.S, o);
+        const float T2 = __shfl_xor_sync(0xffffffffu, st.T, o);
+        st.merge(m2, S2, T2);
+    }
+}
+
+// Deterministic block merge of the logits state through red (>= 67 floats):
+// a shuffle tree per warp, then one over the warps' states in warp 0.  Every
+// thread returns (m, S, T, 0).  Contains two __syncthreads.
+template <int OP>
+__device__ __forceinline__ float4 block_reduce_logits(BwdState<OP, true> st, float *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    warp_merge_logits<OP>(st, 32);
+    if (lane == 0) {
+        red[4 * wid] = st.m;
+        red[4 * wid + 1] = st.S;
+        red[4 * wid + 2] = st.T;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        BwdState<OP, true> t;
+        if (lane < nw) {
+            t.m = red[4 * lane];
+            t.S = red[4 * lane + 1];
+            t.T = red[4 * lane + 2];
+        }
+        warp_merge_logits<OP>(t, 32);
+        if (lane == 0) {
+            red[64] = t.m;
+            red[65] = t.S;
+            red[66] = t.T;
+        }
+    }
+    __syncthreads();
+    return make_float4(red[64], red[65], red[66], 0.0f);
+}
+
+// Push all-gather of one 16-byte partial per CTA (the logits ops' triple),
+// the same protocol as exchange_push: own slot written locally, peers' slots
+// by st.async completing on their exchange mbarrier, after a release fence
+// that orders this CTA's earlier reads of its slots.
+__device__ __forceinline__ const float *exchange_push4(const float4 &v, float *slots, uint64_t *xbar, int par,
+                                                       uint32_t phase, int P, int c, int Tc, unsigned *err) {
+    const int tid = threadIdx.x;
+    float *mine = slot_ptr(slots, 0, par, c);
+    uint64_t *bar = &xbar[par];
+    if (tid < P) {
+        if (tid == c) {
+            mine[0] = v.x;
+            mine[1] = v.y;
+            mine[2] = v.z;
+            mine[3] = v.w;
+        } else {
+            fence_release_smem_cluster();
+            const uint32_t raddr = mapa_shared(smem_addr(mine), static_cast<uint32_t>(tid));
+            const uint32_t rbar = mapa_shared(smem_addr(bar), static_cast<uint32_t>(tid));
+            st_async_v4f32(raddr, v, rbar);
+        }
+    }
+    if (tid == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>((P - 1) * 16));
+    named_bar_sync(1, Tc);
+    mbar_wait_bounded_cluster(bar, phase, err);
+    return slot_ptr(slots, 0, par, 0);
+}
+
+// Coefficients of ops 4-6 from the row totals (S0, S1) and N.
+template <int OP>
+__device__ __forceinline__ Coef row_coeffs(float S0, float S1, long long N) {
+    const float inv_n = 1.0f / static_cast<float>(N);
+    if constexpr (OP == BOP_SOFTMAX) return {S0, 0.0f, 0.0f};
+    else if constexpr (OP == BOP_LN) return {S0 * inv_n, S1 * inv_n, 0.0f};
+    else return {0.0f, S1 * inv_n, 0.0f};
 }
 
 // Deterministic block sum of two floats through red (>= 66 floats); every
@@ -186,7 +339,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
     const int nch = p.nch, cg = p.chunk_groups;
     const size_t arr = static_cast<size_t>(p.slice_groups) * 16;
     const bool g_vec = p.gamma == nullptr || (reinterpret_cast<uintptr_t>(p.gamma) & 15u) == 0;
-    const bool g_sm = OP != BOP_SOFTMAX && p.gamma_smem;
+    const bool g_sm = kNorm<OP> && p.gamma_smem;
     const float *gs = reinterpret_cast<const float *>(data + static_cast<size_t>(p.nbuf) * 2 * arr);
 
     if (tid == 0) {
@@ -252,16 +405,15 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
         const unsigned char *da = data + static_cast<size_t>(b) * 2 * arr, *dd = da + arr;
         const size_t row_off = static_cast<size_t>(row * p.ld) * isz;
 
-        float s0 = 0.0f, s1 = 0.0f;
+        BwdState<OP> st;
         auto sweep = [&](int k0, int k1) {
             for (int k = k0 + tid; k < k1; k += T) {
                 float fa[V], fd[V], fg[V];
                 decode_group<DT>(*reinterpret_cast<const uint4 *>(da + 16 * k), fa, 1.0f);
                 decode_group<DT>(*reinterpret_cast<const uint4 *>(dd + 16 * k), fd, 1.0f);
                 if (g_sm) load_affine_smem<V>(gs, k * V, 1.0f, fg);
-                else load_affine<V>(OP == BOP_SOFTMAX ? nullptr : p.gamma, (g_lo + k) * V, g_vec, 1.0f, fg);
-#pragma unroll
-                for (int v = 0; v < V; ++v) R.acc(fa[v], fd[v], fg[v], s0, s1);
+                else load_affine<V>(kNorm<OP> ? p.gamma : nullptr, (g_lo + k) * V, g_vec, 1.0f, fg);
+                st.template add<V>(R, fa, fd, fg);
             }
         };
         if (nch == 1) {
@@ -278,31 +430,51 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
         if (c == P - 1) {
             for (long long t = tid; t < tail; t += T) {
                 const long long i = Gq * V + t;
-                const float gm = (OP != BOP_SOFTMAX && p.gamma) ? p.gamma[i] : 1.0f;
-                R.acc(decode_one<DT>(p.a + row_off + i * isz, 1.0f), decode_one<DT>(p.dy + row_off + i * isz, 1.0f),
-                      gm, s0, s1);
+                const float gm = (kNorm<OP> && p.gamma) ? p.gamma[i] : 1.0f;
+                st.add1(R, decode_one<DT>(p.a + row_off + i * isz, 1.0f),
+                        decode_one<DT>(p.dy + row_off + i * isz, 1.0f), gm);
             }
         }
-        float2 tot = block_sum2(s0, s1, red);
-        if (P > 1) {
-            const float *sl = exchange_push<NQ>(OP == BOP_RMS ? tot.y : tot.x, tot.y, slots, xbar, 0,
-                                                static_cast<int>(it & 1), static_cast<uint32_t>((it >> 1) & 1), P,
-                                                c, T, p.err);
-            float S0 = 0.0f, S1 = 0.0f;
-            for (int q = 0; q < P; ++q) {  // fixed order: the same totals in every CTA
-                S0 += sl[4 * q];
-                if (NQ == 2) S1 += sl[4 * q + 1];
+        Coef kc;
+        if constexpr (kLogits<OP>) {
+            float4 tot = block_reduce_logits<OP>(st, red);
+            if (P > 1) {
+                const float *sl = exchange_push4(tot, slots, xbar, static_cast<int>(it & 1),
+                                                 static_cast<uint32_t>((it >> 1) & 1), P, c, T, p.err);
+                // the P partials merged by one fixed shuffle tree (lane q holds CTA q's): the same state in
+                // every thread of every CTA of the cluster
+                BwdState<OP> all;
+                const int lane = tid & 31;
+                if (lane < P) {
+                    all.m = sl[4 * lane];
+                    all.S = sl[4 * lane + 1];
+                    all.T = sl[4 * lane + 2];
+                }
+                warp_merge_logits<OP>(all, 32);  // merging an empty state changes nothing
+                tot = make_float4(all.m, all.S, all.T, 0.0f);
             }
-            tot = OP == BOP_RMS ? make_float2(0.0f, S0) : make_float2(S0, S1);
+            kc = logit_coeffs<OP>(tot.x, tot.y, tot.z);
+        } else {
+            float2 tot = block_sum2(st.s0, st.s1, red);
+            if (P > 1) {
+                const float *sl = exchange_push<NQ>(OP == BOP_RMS ? tot.y : tot.x, tot.y, slots, xbar, 0,
+                                                    static_cast<int>(it & 1), static_cast<uint32_t>((it >> 1) & 1),
+                                                    P, c, T, p.err);
+                float S0 = 0.0f, S1 = 0.0f;
+                for (int q = 0; q < P; ++q) {  // fixed order: the same totals in every CTA
+                    S0 += sl[4 * q];
+                    if (NQ == 2) S1 += sl[4 * q + 1];
+                }
+                tot = OP == BOP_RMS ? make_float2(0.0f, S0) : make_float2(S0, S1);
+            }
+            kc = row_coeffs<OP>(tot.x, tot.y, N);
         }
-        float c0, c1;
-        row_coeffs<OP>(tot.x, tot.y, N, c0, c1);
         if (c == P - 1) {  // the elements past the last full group, from global memory
             for (long long t = tid; t < tail; t += T) {
                 const long long i = Gq * V + t;
-                const float gm = (OP != BOP_SOFTMAX && p.gamma) ? p.gamma[i] : 1.0f;
+                const float gm = (kNorm<OP> && p.gamma) ? p.gamma[i] : 1.0f;
                 const float v = R.dx(decode_one<DT>(p.a + row_off + i * isz, 1.0f),
-                                     decode_one<DT>(p.dy + row_off + i * isz, 1.0f), gm, c0, c1);
+                                     decode_one<DT>(p.dy + row_off + i * isz, 1.0f), gm, kc);
                 store_one<DT>(p.dx + row_off + i * isz, v);
             }
         }
@@ -313,9 +485,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
                 decode_group<DT>(*reinterpret_cast<const uint4 *>(da + 16 * k), fa, 1.0f);
                 decode_group<DT>(*reinterpret_cast<const uint4 *>(dd + 16 * k), fd, 1.0f);
                 if (g_sm) load_affine_smem<V>(gs, k * V, 1.0f, fg);
-                else load_affine<V>(OP == BOP_SOFTMAX ? nullptr : p.gamma, (g_lo + k) * V, g_vec, 1.0f, fg);
+                else load_affine<V>(kNorm<OP> ? p.gamma : nullptr, (g_lo + k) * V, g_vec, 1.0f, fg);
 #pragma unroll
-                for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], c0, c1);
+                for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], kc);
                 store_group<DT, V>(xr + 16 * k, y, true);
             }
         };
@@ -374,36 +546,36 @@ __device__ __forceinline__ BwdSpan bwd_span(const BwdArgs &p, long long row, int
 }
 
 template <int OP, int DT>
-__device__ __forceinline__ float2 bwd_sums(const BwdArgs &p, long long row, const BwdRow<OP> &R, const BwdSpan &s) {
+__device__ __forceinline__ BwdState<OP> bwd_sums(const BwdArgs &p, long long row, const BwdRow<OP> &R,
+                                                 const BwdSpan &s) {
     constexpr int isz = Fmt<DT>::size, V = Fmt<DT>::V;
     const size_t off = static_cast<size_t>(row * p.ld) * isz;
     const bool g_vec = p.gamma == nullptr || (reinterpret_cast<uintptr_t>(p.gamma) & 15u) == 0;
-    const float *gam = OP == BOP_SOFTMAX ? nullptr : p.gamma;
-    float s0 = 0.0f, s1 = 0.0f;
+    const float *gam = kNorm<OP> ? p.gamma : nullptr;
+    BwdState<OP> st;
     if (s.vec) {
         for (long long k = s.lo + threadIdx.x; k < s.hi; k += blockDim.x) {
             float fa[V], fd[V], fg[V];
             decode_group<DT>(ld_global_v4(p.a + off + 16 * k), fa, 1.0f);
             decode_group<DT>(ld_global_v4(p.dy + off + 16 * k), fd, 1.0f);
             load_affine<V>(gam, k * V, g_vec, 1.0f, fg);
-#pragma unroll
-            for (int v = 0; v < V; ++v) R.acc(fa[v], fd[v], fg[v], s0, s1);
+            st.template add<V>(R, fa, fd, fg);
         }
     }
     const long long e_lo = s.vec ? s.t_lo : s.lo, e_hi = s.vec ? s.t_hi : s.hi;
     for (long long i = e_lo + threadIdx.x; i < e_hi; i += blockDim.x)
-        R.acc(decode_one<DT>(p.a + off + i * isz, 1.0f), decode_one<DT>(p.dy + off + i * isz, 1.0f),
-              gam ? gam[i] : 1.0f, s0, s1);
-    return make_float2(s0, s1);
+        st.add1(R, decode_one<DT>(p.a + off + i * isz, 1.0f), decode_one<DT>(p.dy + off + i * isz, 1.0f),
+                gam ? gam[i] : 1.0f);
+    return st;
 }
 
 template <int OP, int DT>
 __device__ __forceinline__ void bwd_apply(const BwdArgs &p, long long row, const BwdRow<OP> &R, const BwdSpan &s,
-                                          float c0, float c1) {
+                                          const Coef &kc) {
     constexpr int isz = Fmt<DT>::size, V = Fmt<DT>::V;
     const size_t off = static_cast<size_t>(row * p.ld) * isz;
     const bool g_vec = p.gamma == nullptr || (reinterpret_cast<uintptr_t>(p.gamma) & 15u) == 0;
-    const float *gam = OP == BOP_SOFTMAX ? nullptr : p.gamma;
+    const float *gam = kNorm<OP> ? p.gamma : nullptr;
     if (s.vec) {
         for (long long k = s.lo + threadIdx.x; k < s.hi; k += blockDim.x) {
             float fa[V], fd[V], fg[V], y[V];
@@ -411,14 +583,14 @@ __device__ __forceinline__ void bwd_apply(const BwdArgs &p, long long row, const
             decode_group<DT>(ld_global_v4(p.dy + off + 16 * k), fd, 1.0f);
             load_affine<V>(gam, k * V, g_vec, 1.0f, fg);
 #pragma unroll
-            for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], c0, c1);
+            for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], kc);
             store_group<DT, V>(p.dx + off + 16 * k, y, true);
         }
     }
     const long long e_lo = s.vec ? s.t_lo : s.lo, e_hi = s.vec ? s.t_hi : s.hi;
     for (long long i = e_lo + threadIdx.x; i < e_hi; i += blockDim.x) {
         const float v = R.dx(decode_one<DT>(p.a + off + i * isz, 1.0f), decode_one<DT>(p.dy + off + i * isz, 1.0f),
-                             gam ? gam[i] : 1.0f, c0, c1);
+                             gam ? gam[i] : 1.0f, kc);
         store_one<DT>(p.dx + off + i * isz, v);
     }
 }
@@ -431,14 +603,20 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_fused(const BwdArgs p) {
     BwdRow<OP> R;
     R.load(p, row);
     const BwdSpan s = bwd_span<DT>(p, row, 0, 1);
-    const float2 t = bwd_sums<OP, DT>(p, row, R, s);
-    const float2 tot = block_sum2(t.x, t.y, red);
-    float c0, c1;
-    row_coeffs<OP>(tot.x, tot.y, p.cols, c0, c1);
-    bwd_apply<OP, DT>(p, row, R, s, c0, c1);
+    const BwdState<OP> t = bwd_sums<OP, DT>(p, row, R, s);
+    Coef kc;
+    if constexpr (kLogits<OP>) {
+        const float4 tot = block_reduce_logits<OP>(t, red);
+        kc = logit_coeffs<OP>(tot.x, tot.y, tot.z);
+    } else {
+        const float2 tot = block_sum2(t.s0, t.s1, red);
+        kc = row_coeffs<OP>(tot.x, tot.y, p.cols);
+    }
+    bwd_apply<OP, DT>(p, row, R, s, kc);
 }
 
-// G > 1, launch 1: partial sums of CTA j of row lr into ws[lr][j][0..1].
+// G > 1, launch 1: partial sums of CTA j of row lr into ws[lr][j][0..1] (logits ops: the state into
+// ws[lr][j][0..2] of a 4-float record).
 template <int OP, int DT>
 __global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_stats(const BwdArgs p) {
     __shared__ float red[128];
@@ -447,11 +625,20 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_stats(const BwdArgs p) {
     BwdRow<OP> R;
     R.load(p, row);
     const BwdSpan s = bwd_span<DT>(p, row, j, G);
-    const float2 t = bwd_sums<OP, DT>(p, row, R, s);
-    const float2 tot = block_sum2(t.x, t.y, red);
-    if (threadIdx.x == 0) {
-        p.ws[(lr * G + j) * 2] = tot.x;
-        p.ws[(lr * G + j) * 2 + 1] = tot.y;
+    const BwdState<OP> t = bwd_sums<OP, DT>(p, row, R, s);
+    if constexpr (kLogits<OP>) {
+        const float4 tot = block_reduce_logits<OP>(t, red);
+        if (threadIdx.x == 0) {
+            p.ws[(lr * G + j) * 4] = tot.x;
+            p.ws[(lr * G + j) * 4 + 1] = tot.y;
+            p.ws[(lr * G + j) * 4 + 2] = tot.z;
+        }
+    } else {
+        const float2 tot = block_sum2(t.s0, t.s1, red);
+        if (threadIdx.x == 0) {
+            p.ws[(lr * G + j) * 2] = tot.x;
+            p.ws[(lr * G + j) * 2 + 1] = tot.y;
+        }
     }
 }
 
@@ -462,14 +649,21 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_apply(const BwdArgs p) {
     const long long lr = blockIdx.x / G, row = p.row0 + lr;
     BwdRow<OP> R;
     R.load(p, row);
-    float S0 = 0.0f, S1 = 0.0f;
-    for (int q = 0; q < G; ++q) {
-        S0 += p.ws[(lr * G + q) * 2];
-        S1 += p.ws[(lr * G + q) * 2 + 1];
+    Coef kc;
+    if constexpr (kLogits<OP>) {
+        BwdState<OP> all;
+        for (int q = 0; q < G; ++q)
+            all.merge(p.ws[(lr * G + q) * 4], p.ws[(lr * G + q) * 4 + 1], p.ws[(lr * G + q) * 4 + 2]);
+        kc = logit_coeffs<OP>(all.m, all.S, all.T);
+    } else {
+        float S0 = 0.0f, S1 = 0.0f;
+        for (int q = 0; q < G; ++q) {
+            S0 += p.ws[(lr * G + q) * 2];
+            S1 += p.ws[(lr * G + q) * 2 + 1];
+        }
+        kc = row_coeffs<OP>(S0, S1, p.cols);
     }
-    float c0, c1;
-    row_coeffs<OP>(S0, S1, p.cols, c0, c1);
-    bwd_apply<OP, DT>(p, row, R, bwd_span<DT>(p, row, j, G), c0, c1);
+    bwd_apply<OP, DT>(p, row, R, bwd_span<DT>(p, row, j, G), kc);
 }
 
 struct BwdKernels {
@@ -491,6 +685,10 @@ bool bwd_kernels(int op, int dt, BwdKernels *k) {
     case BOP_LN * 4 + DT_BF16: *k = bwd_kernels_of<BOP_LN, DT_BF16>(); return true;
     case BOP_RMS * 4 + DT_F32: *k = bwd_kernels_of<BOP_RMS, DT_F32>(); return true;
     case BOP_RMS * 4 + DT_BF16: *k = bwd_kernels_of<BOP_RMS, DT_BF16>(); return true;
+    case BOP_SMLOGITS * 4 + DT_F32: *k = bwd_kernels_of<BOP_SMLOGITS, DT_F32>(); return true;
+    case BOP_SMLOGITS * 4 + DT_BF16: *k = bwd_kernels_of<BOP_SMLOGITS, DT_BF16>(); return true;
+    case BOP_XENT * 4 + DT_F32: *k = bwd_kernels_of<BOP_XENT, DT_F32>(); return true;
+    case BOP_XENT * 4 + DT_BF16: *k = bwd_kernels_of<BOP_XENT, DT_BF16>(); return true;
     default: return false;
     }
 }
@@ -498,7 +696,7 @@ bool bwd_kernels(int op, int dt, BwdKernels *k) {
 // ------------------------------------------------------------------ host
 credit_status validate_bwd(const credit_bwd_args *a) {
     if (a == nullptr) return CREDIT_ERR_INVALID_ARG;
-    if (a->op < BOP_SOFTMAX || a->op > BOP_RMS) return CREDIT_ERR_INVALID_ARG;
+    if (a->op < BOP_SOFTMAX || a->op > BOP_XENT) return CREDIT_ERR_INVALID_ARG;
     if (a->dtype == CREDIT_FP8_E4M3) return CREDIT_ERR_UNSUPPORTED;
     if (a->dtype != CREDIT_F32 && a->dtype != CREDIT_BF16) return CREDIT_ERR_INVALID_ARG;
     if (a->rows < 0 || a->cols <= 0 || a->ld < 0 || (a->ld != 0 && a->ld < a->cols)) return CREDIT_ERR_INVALID_ARG;
@@ -555,7 +753,7 @@ bool bwd_config(const DeviceInfo &di, long long N, int isz, int P, int req_nbuf,
 
 // gamma is staged in shared memory by the norms when present and 16-byte aligned.
 bool stage_gamma(int op, const float *gamma) {
-    return op != BOP_SOFTMAX && gamma != nullptr && (reinterpret_cast<uintptr_t>(gamma) & 15u) == 0;
+    return (op == BOP_LN || op == BOP_RMS) && gamma != nullptr && (reinterpret_cast<uintptr_t>(gamma) & 15u) == 0;
 }
 
 credit_status check_bwd_plan(int dev, const credit_bwd_args *a, const credit_plan_t *p, BwdCfg *cfg, int *maxc) {
@@ -591,11 +789,29 @@ credit_status plan_bwd_for(int dev, int op, long long cols, int dtype, credit_pl
     if (di != nullptr && cols * isz > kBwdFusedMaxBytes) {
         BwdKernels k;
         if (!bwd_kernels(op, dtype, &k)) return CREDIT_ERR_UNSUPPORTED;
+        if (op == BOP_SMLOGITS || op == BOP_XENT) {
+            // the logits ops carry a per-row merge of (max, sum, dot) states whose cost grows with P: staged
+            // only while a CTA's slice is at most 64 KiB per array and P <= 4 (measured: P = 4 beats two-pass
+            // at 64K FP32 columns, P = 8 and 16 lose at 128K), either buffering
+            for (int P = 1; P <= 4; P *= 2) {
+                BwdCfg cfg;
+                if (cols * isz > 65536LL * P) continue;
+                if (!bwd_config(*di, cols, isz, P, 0, false, &cfg)) continue;
+                if (prepare_staged_kernel(dev, k.staged) != CREDIT_OK) continue;
+                if (staged_max_clusters(dev, k.staged, P, cfg.threads, cfg.smem, false) <= 0) continue;
+                out->path = P == 1 ? CREDIT_PATH_ONE_CTA : CREDIT_PATH_CLUSTER;
+                out->cluster_size = P;
+                out->ctas_per_row = P;
+                out->ring_chunks = cfg.nbuf;
+                out->smem_bytes = cfg.smem;
+                return CREDIT_OK;
+            }
+        }
         // double-buffered staging only: a single buffer leaves the copies of the next row unoverlapped, which
         // measured no faster than the global-reread path
-        for (int P = 1; P <= kMaxCluster; P *= 2) {
+        for (int P = 1; P <= kMaxCluster && op != BOP_SMLOGITS && op != BOP_XENT; P *= 2) {
             BwdCfg cfg;
-            if (!bwd_config(*di, cols, isz, P, 2, op != BOP_SOFTMAX, &cfg)) continue;
+            if (!bwd_config(*di, cols, isz, P, 2, op == BOP_LN || op == BOP_RMS, &cfg)) continue;
             if (prepare_staged_kernel(dev, k.staged) != CREDIT_OK) continue;
             if (staged_max_clusters(dev, k.staged, P, cfg.threads, cfg.smem, false) <= 0) continue;
             out->path = P == 1 ? CREDIT_PATH_ONE_CTA : CREDIT_PATH_CLUSTER;
@@ -624,6 +840,7 @@ BwdArgs make_bwd_args(const credit_bwd_args *a, unsigned *err, float *ws) {
     r.gamma = a->gamma;
     r.mean = a->mean;
     r.rstd = a->rstd;
+    r.scale = a->scale;
     r.err = err;
     r.ws = ws;
     return r;
@@ -643,7 +860,7 @@ using namespace credit;
 extern "C" {
 
 credit_status credit_plan_bwd(int32_t op, int64_t rows, int64_t cols, credit_dtype dtype, credit_plan_t *out) {
-    if (out == nullptr || op < BOP_SOFTMAX || op > BOP_RMS || rows < 0 || cols <= 0) return CREDIT_ERR_INVALID_ARG;
+    if (out == nullptr || op < BOP_SOFTMAX || op > BOP_XENT || rows < 0 || cols <= 0) return CREDIT_ERR_INVALID_ARG;
     if (dtype != CREDIT_F32 && dtype != CREDIT_BF16) return CREDIT_ERR_UNSUPPORTED;
     int dev = 0;
     const credit_status st = ensure_init(&dev, nullptr);
@@ -708,7 +925,8 @@ credit_status credit_run_bwd(const credit_bwd_args *args, const credit_plan_t *p
         return CREDIT_OK;
     }
     const int G = chosen.ctas_per_row;
-    const long long cap = G == 1 ? 0x7FFFFFFFLL : static_cast<long long>(ws_floats / (static_cast<size_t>(G) * 2));
+    const size_t rec = (args->op == BOP_SMLOGITS || args->op == BOP_XENT) ? 4 : 2;  // floats per partial
+    const long long cap = G == 1 ? 0x7FFFFFFFLL : static_cast<long long>(ws_floats / (static_cast<size_t>(G) * rec));
     const long long max_rows = cap < 0x7FFFFFFFLL / G ? cap : 0x7FFFFFFFLL / G;
     if (max_rows < 1) return CREDIT_ERR_UNSUPPORTED;
     for (long long r0 = 0; r0 < rows; r0 += max_rows) {

@@ -140,14 +140,30 @@ def check_against_oracle(op, x_cpu, scale, *, out_dtype=None, plan=None, gamma=N
 
 
 # ---------------------------------------------------------------- backward ops
-BWD_FWD_OP = {C.SOFTMAX_BWD: O.SOFTMAX, C.LAYERNORM_BWD: O.LAYERNORM, C.RMSNORM_BWD: O.RMSNORM}
+BWD_FWD_OP = {C.SOFTMAX_BWD: O.SOFTMAX, C.LAYERNORM_BWD: O.LAYERNORM, C.RMSNORM_BWD: O.RMSNORM,
+              C.SOFTMAX_LOGITS_BWD: O.SOFTMAX_LOGITS, C.XENT_BWD: O.XENT}
 
 
 def bwd_inputs(op: int, dtype: int, rows: int, cols: int, *, ld: int = 0, seed: int = 0, device="cpu"):
     """Tensors (a, dy, gamma, mean, rstd) on `device` for a backward op: a is softmax(N(0, 3^2) logits)
-    or the outlier-laden x of the forward workload, dy ~ N(0, 1), gamma ~ N(1, 0.1); mean / rstd are the
-    FP64 row statistics of the stored a, rounded to FP32 (the forward's saved statistics)."""
+    (softmax), N(0, 3^2) logits (the logits ops) or the outlier-laden x of the forward workload (norms);
+    dy ~ N(0, 1), for the cross entropy the targets softmax(N(0, 1)); gamma ~ N(1, 0.1); mean / rstd are
+    the FP64 row statistics of the stored a, rounded to FP32 (the forward's saved statistics).  For the
+    cross entropy the last entry is the per-row scale w ~ U(0.5, 2) instead of rstd."""
     ld = ld or cols
+    if op in (C.SOFTMAX_LOGITS_BWD, C.XENT_BWD):
+        a = torch.zeros(rows, ld, dtype=torch.float32, device=device)
+        a[:, :cols] = synth.normal(rows, cols, std=3.0, seed=seed, device=device)
+        if op == C.XENT_BWD:
+            dy = torch.zeros(rows, ld, dtype=torch.float32, device=device)
+            dy[:, :cols] = torch.softmax(synth.normal(rows, cols, seed=seed + 1, device=device).double(), 1).float()
+            w = 0.5 + 1.5 * torch.rand(rows, generator=torch.Generator(device=device).manual_seed(seed + 3),
+                                       device=device)
+        else:
+            dy = synth.normal(rows, ld, seed=seed + 1, device=device)
+        if dtype == C.BF16:
+            a, dy = synth.to_bf16(a), synth.to_bf16(dy)
+        return a, dy, None, None, (w if op == C.XENT_BWD else None)
     if op == C.SOFTMAX_BWD:
         logits = synth.normal(rows, cols, std=3.0, seed=seed, device=device).double()
         a = torch.zeros(rows, ld, dtype=torch.float32, device=device)
@@ -175,7 +191,7 @@ def bwd_inputs(op: int, dtype: int, rows: int, cols: int, *, ld: int = 0, seed: 
 def bwd_reference(op, dtype, a, dy, gamma, mean, rstd, rows, cols, ld=0):
     f = lambda t: None if t is None else t.cpu().numpy()  # noqa: E731
     dx64, _ = O.run_bwd(BWD_FWD_OP[op], dtype, raw_numpy(a), raw_numpy(dy), rows, cols, ld=ld or cols,
-                        gamma=f(gamma), mean=f(mean), rstd=f(rstd))
+                        gamma=f(gamma), mean=f(mean), rstd=f(rstd))  # for the cross entropy rstd is the scale
     return dx64
 
 
@@ -190,6 +206,13 @@ def bwd_error(op, dtype, dx, ref, a, dy, gamma, mean, rstd, cols):
     a64, dy64 = to64(a)[:, :cols], to64(dy)[:, :cols]
     if op == C.SOFTMAX_BWD:
         S = np.abs(a64).max(axis=1) * (np.abs(dy64).max(axis=1) + np.abs(a64 * dy64).sum(axis=1))
+    elif op == C.SOFTMAX_LOGITS_BWD:  # the softmax bound with y recomputed from the logits
+        y = O.softmax(a64)
+        S = np.abs(y).max(axis=1) * (np.abs(dy64).max(axis=1) + np.abs(y * dy64).sum(axis=1))
+    elif op == C.XENT_BWD:  # w (max y |sum t| + max |t|)
+        y = O.softmax(a64)
+        w = np.ones(a64.shape[0]) if rstd is None else rstd.cpu().double().numpy()
+        S = np.abs(w) * (np.abs(y).max(axis=1) * np.abs(dy64.sum(axis=1)) + np.abs(dy64).max(axis=1))
     else:
         g = dy64 * (1.0 if gamma is None else gamma.cpu().double().numpy()[None, :])
         r = rstd.cpu().double().numpy()

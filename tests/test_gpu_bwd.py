@@ -1,5 +1,6 @@
-"""GPU parity of the backward ops (dx of softmax, LayerNorm, RMSNorm) against
-the FP64 oracle, through the C ABI (credit_run_bwd).
+"""GPU parity of the backward ops (dx of softmax, LayerNorm, RMSNorm; dz of
+softmax and of the cross entropy from logits) against the FP64 oracle,
+through the C ABI (credit_run_bwd).
 
 Every path (fused and split two-pass, one-CTA, clusters of 2-16) on rows
 that span several groups per thread and end in a ragged tail; many rows per
@@ -18,7 +19,8 @@ import parity_util as U
 
 pytestmark = pytest.mark.gpu
 
-OPS = [C.SOFTMAX_BWD, C.LAYERNORM_BWD, C.RMSNORM_BWD]
+OPS = [C.SOFTMAX_BWD, C.LAYERNORM_BWD, C.RMSNORM_BWD, C.SOFTMAX_LOGITS_BWD, C.XENT_BWD]
+IDS = ["softmax", "layernorm", "rmsnorm", "softmax_logits", "xent"]
 DTYPES = [C.F32, C.BF16]
 
 
@@ -40,7 +42,11 @@ def run(op, dtype, a, dy, gamma, mean, rstd, rows, cols, ld=0, plan=None, dx=Non
     d = lambda t: None if t is None else t.cuda()  # noqa: E731
     ga, gdy = a.cuda(), dy.cuda()
     out = torch.full_like(ga, float("nan")) if dx is None else dx
-    C.run_bwd(op, ga, gdy, out, plan=plan, rows=rows, cols=cols, ld=ld, gamma=d(gamma), mean=d(mean), rstd=d(rstd))
+    if op == C.XENT_BWD:  # the last input is the per-row scale
+        C.run_bwd(op, ga, gdy, out, plan=plan, rows=rows, cols=cols, ld=ld, scale=d(rstd))
+    else:
+        C.run_bwd(op, ga, gdy, out, plan=plan, rows=rows, cols=cols, ld=ld, gamma=d(gamma), mean=d(mean),
+                  rstd=d(rstd))
     torch.cuda.synchronize()
     assert C.device_error() == C.OK
     return out
@@ -71,20 +77,20 @@ PLANS = {
 
 @pytest.mark.parametrize("plan", list(PLANS))
 @pytest.mark.parametrize("dtype", DTYPES, ids=["f32", "bf16"])
-@pytest.mark.parametrize("op", OPS, ids=["softmax", "layernorm", "rmsnorm"])
+@pytest.mark.parametrize("op", OPS, ids=IDS)
 def test_bwd_matches_oracle(op, dtype, plan):
     p, cols = PLANS[plan]
     check(op, dtype, 37, cols, pad(cols, dtype) + (8 if dtype == C.F32 else 0), p, seed=op + dtype)
 
 
-@pytest.mark.parametrize("op", OPS, ids=["softmax", "layernorm", "rmsnorm"])
+@pytest.mark.parametrize("op", OPS, ids=IDS)
 def test_unaligned_rows_run_two_pass(op):
     # contiguous rows of 4099 FP32: every row after the first starts off the 16-byte grid
     for plan in (None, C.make_plan(C.PATH_TWO_PASS, ctas_per_row=1), C.make_plan(C.PATH_TWO_PASS, ctas_per_row=4)):
         check(op, C.F32, 21, 4099, 0, plan, seed=7)
 
 
-@pytest.mark.parametrize("op", OPS, ids=["softmax", "layernorm", "rmsnorm"])
+@pytest.mark.parametrize("op", OPS, ids=IDS)
 def test_many_rows_recycle_buffers_and_slots(op):
     # far more rows than resident clusters: every row buffer, exchange slot and mbarrier phase is reused
     for P in (1, 4, 16):
@@ -92,7 +98,7 @@ def test_many_rows_recycle_buffers_and_slots(op):
         check(op, C.F32, 1500, 8195, 8196, plan, seed=11 + P)
 
 
-@pytest.mark.parametrize("op", OPS, ids=["softmax", "layernorm", "rmsnorm"])
+@pytest.mark.parametrize("op", OPS, ids=IDS)
 def test_single_buffer_refilled_chunk_by_chunk(op):
     # 64 KiB slices at P = 16: only one row buffer fits, refilled in 8 chunks behind the write pass
     check(op, C.F32, 300, 262147, 262148, C.make_plan(C.PATH_CLUSTER, 16), seed=17)
@@ -111,7 +117,7 @@ def test_single_and_double_buffering_agree_bitwise():
 
 
 @pytest.mark.parametrize("cols", [1, 3, 17, 64])
-@pytest.mark.parametrize("op", OPS, ids=["softmax", "layernorm", "rmsnorm"])
+@pytest.mark.parametrize("op", OPS, ids=IDS)
 def test_tiny_rows_and_empty_slices(op, cols):
     for plan in (C.make_plan(C.PATH_CLUSTER, 16), C.make_plan(C.PATH_ONE_CTA), None):
         check(op, C.F32, 5, cols, pad(cols, C.F32), plan, seed=cols)
