@@ -75,6 +75,36 @@ def test_validation_rejects_bad_calls_without_touching_the_gpu(lib):
     assert lib.credit_plan_ex(0, 4, 16, 0, 0, None) == C.ERR_INVALID_ARG
 
 
+def test_backward_validation_rejects_bad_calls_without_touching_the_gpu(lib):
+    assert lib.credit_run_bwd(None, None, None) == C.ERR_INVALID_ARG
+    r = C.BwdArgsT()
+    r.op, r.dtype, r.a, r.dy, r.dx, r.rows, r.cols = C.SOFTMAX_BWD, C.F32, 0x1000, 0x2000, 0x3000, 4, 16
+    for op in (C.RMSNORM, 9, -1):                                           # not a backward op
+        r.op = op
+        assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_INVALID_ARG
+    r.op, r.dtype = C.SOFTMAX_BWD, C.FP8_E4M3                               # FP8: no backward kernels
+    assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_UNSUPPORTED
+    r.dtype, r.ld = C.F32, 8                                                # ld < cols
+    assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_INVALID_ARG
+    r.ld, r.cols = 0, 0                                                     # cols == 0
+    assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_INVALID_ARG
+    r.cols, r.dx = 16, None                                                 # NULL output
+    assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_INVALID_ARG
+    r.dx, r.op = 0x3000, C.LAYERNORM_BWD                                    # LayerNorm needs mean and rstd
+    assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_INVALID_ARG
+    r.rstd = 0x4000
+    assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_INVALID_ARG
+    r.op, r.rstd = C.RMSNORM_BWD, None                                       # RMSNorm needs rstd
+    assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_INVALID_ARG
+    r.rows = 0                                                              # rows == 0 is a no-op
+    assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.OK
+    p = C.PlanT()
+    assert lib.credit_plan_bwd(C.SOFTMAX, 4, 16, C.F32, ctypes.byref(p)) == C.ERR_INVALID_ARG
+    assert lib.credit_plan_bwd(C.XENT_BWD, 4, 0, C.F32, ctypes.byref(p)) == C.ERR_INVALID_ARG
+    assert lib.credit_plan_bwd(C.XENT_BWD, 4, 16, C.FP8_E4M3, ctypes.byref(p)) == C.ERR_UNSUPPORTED
+    assert lib.credit_plan_bwd(C.XENT_BWD, 4, 16, C.F32, None) == C.ERR_INVALID_ARG
+
+
 def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(C.PlanT) == 56 and C.PlanT.smem_bytes.offset == 32 and C.PlanT.fill_g.offset == 52
     assert ctypes.sizeof(C.ArgsT) == 104
