@@ -85,6 +85,12 @@ def lib() -> ctypes.CDLL:
             L.oracle_rmsnorm_bwd_row.argtypes = [vp, vp, i64, vp, d, vp]
             L.oracle_softmax_logits_bwd_row.argtypes = [vp, vp, i64, vp]
             L.oracle_xent_bwd_row.argtypes = [vp, vp, i64, d, vp]
+            L.oracle_wvar_row.restype = d
+            L.oracle_wvar_row.argtypes = [vp, vp, i64]
+            L.oracle_wvar_bwd_row.argtypes = [vp, vp, i64, d, vp, vp]
+            L.oracle_pearson_row.restype = d
+            L.oracle_pearson_row.argtypes = [vp, vp, i64]
+            L.oracle_pearson_bwd_row.argtypes = [vp, vp, i64, d, vp, vp]
             L.oracle_run_bwd.restype = i32
             L.oracle_run_bwd.argtypes = [i32, i32, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp, i32]
             L.oracle_max_threads.restype = i32
@@ -251,6 +257,42 @@ def xent_bwd(z, t, w=None):
     for r in range(z.shape[0]):
         lib().oracle_xent_bwd_row(_ptr(z[r]), _ptr(t[r]), z.shape[1], 1.0 if w is None else float(w[r]), _ptr(dz[r]))
     return dz
+
+
+def _pair_rows(a, b):
+    return np.ascontiguousarray(a, dtype=np.float64), np.ascontiguousarray(b, dtype=np.float64)
+
+
+def wvar(x, w):
+    """Weighted variance sum w (x - mu)^2 / sum w per row, mu = sum w x / sum w (FP64)."""
+    x, w = _pair_rows(x, w)
+    return np.array([lib().oracle_wvar_row(_ptr(x[r]), _ptr(w[r]), x.shape[1]) for r in range(x.shape[0])])
+
+
+def wvar_bwd(x, w, g=None):
+    """(dx, dw) of the weighted variance times the per-row upstream gradient g (None = 1) (FP64)."""
+    x, w = _pair_rows(x, w)
+    dx, dw = np.empty_like(x), np.empty_like(x)
+    for r in range(x.shape[0]):
+        lib().oracle_wvar_bwd_row(_ptr(x[r]), _ptr(w[r]), x.shape[1], 1.0 if g is None else float(g[r]),
+                                  _ptr(dx[r]), _ptr(dw[r]))
+    return dx, dw
+
+
+def pearson(x, y):
+    """Pearson correlation of x and y per row (FP64)."""
+    x, y = _pair_rows(x, y)
+    return np.array([lib().oracle_pearson_row(_ptr(x[r]), _ptr(y[r]), x.shape[1]) for r in range(x.shape[0])])
+
+
+def pearson_bwd(x, y, g=None):
+    """(dx, dy) of the Pearson correlation times the per-row upstream gradient g (None = 1) (FP64)."""
+    x, y = _pair_rows(x, y)
+    dx, dy = np.empty_like(x), np.empty_like(x)
+    for r in range(x.shape[0]):
+        lib().oracle_pearson_bwd_row(_ptr(x[r]), _ptr(y[r]), x.shape[1], 1.0 if g is None else float(g[r]),
+                                     _ptr(dx[r]), _ptr(dy[r]))
+    return dx, dy
 
 
 def run_bwd(op: int, dtype: int, a_raw, dy_raw, rows: int, cols: int, *, gamma=None, mean=None, rstd=None,

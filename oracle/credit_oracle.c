@@ -273,6 +273,77 @@ void oracle_xent_bwd_row(const double *z, const double *t, int64_t n, double w, 
     for (int64_t i = 0; i < n; ++i) dz[i] = w * (dz[i] * tt - t[i]);
 }
 
+/* Two-input statistics and their gradients (the "weighted-variance      */
+/* backward" and "Pearson-correlation backward" workloads of Sec. IV-A). */
+/* Weighted variance of x with weights w:                                 */
+/*   W = sum w, mu = sum w x / W, v = sum w (x - mu)^2 / W;               */
+/*   given the upstream gradient g of v:                                  */
+/*   dx_i = g 2 w_i (x_i - mu) / W,   dw_i = g ((x_i - mu)^2 - v) / W     */
+/*   (the mean's own terms vanish because sum w (x - mu) = 0).            */
+/* Pearson correlation of x and y with centred sums                       */
+/*   Sxy = sum (x - xb)(y - yb), Sxx = sum (x - xb)^2, Syy likewise:      */
+/*   r = Sxy / sqrt(Sxx Syy);  given the upstream gradient g of r:        */
+/*   dx_i = g ((y_i - yb) / sqrt(Sxx Syy) - r (x_i - xb) / Sxx), dy_i     */
+/*   symmetrically (the means' own terms vanish because the centred       */
+/*   values sum to zero).                                                 */
+double oracle_wvar_row(const double *x, const double *w, int64_t n) {
+    nsum_t W = {0, 0}, A = {0, 0};
+    for (int64_t i = 0; i < n; ++i) { nsum_add(&W, w[i]); nsum_add(&A, w[i] * x[i]); }
+    double ww = nsum_get(&W), mu = nsum_get(&A) / ww;
+    nsum_t V = {0, 0};
+    for (int64_t i = 0; i < n; ++i) { double d = x[i] - mu; nsum_add(&V, w[i] * d * d); }
+    return nsum_get(&V) / ww;
+}
+
+void oracle_wvar_bwd_row(const double *x, const double *w, int64_t n, double g, double *dx, double *dw) {
+    nsum_t W = {0, 0}, A = {0, 0};
+    for (int64_t i = 0; i < n; ++i) { nsum_add(&W, w[i]); nsum_add(&A, w[i] * x[i]); }
+    double ww = nsum_get(&W), mu = nsum_get(&A) / ww;
+    nsum_t V = {0, 0};
+    for (int64_t i = 0; i < n; ++i) { double d = x[i] - mu; nsum_add(&V, w[i] * d * d); }
+    double v = nsum_get(&V) / ww;
+    for (int64_t i = 0; i < n; ++i) {
+        double d = x[i] - mu;
+        dx[i] = g * 2.0 * w[i] * d / ww;
+        dw[i] = g * (d * d - v) / ww;
+    }
+}
+
+static void pearson_sums(const double *x, const double *y, int64_t n, double *xb, double *yb, double *sxx,
+                         double *syy, double *sxy) {
+    nsum_t X = {0, 0}, Y = {0, 0};
+    for (int64_t i = 0; i < n; ++i) { nsum_add(&X, x[i]); nsum_add(&Y, y[i]); }
+    *xb = nsum_get(&X) / (double)n;
+    *yb = nsum_get(&Y) / (double)n;
+    nsum_t A = {0, 0}, B = {0, 0}, C = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        double dxv = x[i] - *xb, dyv = y[i] - *yb;
+        nsum_add(&A, dxv * dxv);
+        nsum_add(&B, dyv * dyv);
+        nsum_add(&C, dxv * dyv);
+    }
+    *sxx = nsum_get(&A);
+    *syy = nsum_get(&B);
+    *sxy = nsum_get(&C);
+}
+
+double oracle_pearson_row(const double *x, const double *y, int64_t n) {
+    double xb, yb, sxx, syy, sxy;
+    pearson_sums(x, y, n, &xb, &yb, &sxx, &syy, &sxy);
+    return sxy / sqrt(sxx * syy);
+}
+
+void oracle_pearson_bwd_row(const double *x, const double *y, int64_t n, double g, double *dx, double *dy) {
+    double xb, yb, sxx, syy, sxy;
+    pearson_sums(x, y, n, &xb, &yb, &sxx, &syy, &sxy);
+    double den = sqrt(sxx * syy), r = sxy / den;
+    for (int64_t i = 0; i < n; ++i) {
+        double cx = x[i] - xb, cy = y[i] - yb;
+        dx[i] = g * (cy / den - r * cx / sxx);
+        dy[i] = g * (cx / den - r * cy / syy);
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Batch driver: decode -> op -> (exact doubles, encoded output)        */
 /* ------------------------------------------------------------------ */
