@@ -280,6 +280,17 @@ credit_status credit_plan_check(const credit_args *args, const credit_plan_t *pl
  *   CREDIT_OP_XENT_BWD       a = z, dy = t (target weights, soft labels),
  *                            scale = w (per row, NULL = 1): the gradient of
  *                            w * (-sum_j t_j log y_j), dz_i = w (y_i sum_j t_j - t_i)
+ * and the gradients of two statistics of a row pair, with scale = g (the
+ * upstream gradient per row, NULL = 1) and a second output dx2 (the
+ * "weighted-variance backward" and "Pearson-correlation backward" workloads):
+ *   CREDIT_OP_WVAR_BWD       a = x, dy = w (weights); v = sum w (x - mu)^2 / W,
+ *                            mu = sum w x / W, W = sum w:
+ *                            dx_i = g 2 w_i (x_i - mu) / W, dx2_i = dw_i = g ((x_i - mu)^2 - v) / W
+ *   CREDIT_OP_PEARSON_BWD    a = x, dy = y; r = Sxy / sqrt(Sxx Syy) (centred sums):
+ *                            dx_i = g ((y_i - yb) / sqrt(Sxx Syy) - r (x_i - xb) / Sxx),
+ *                            dx2_i = dy_i = g ((x_i - xb) / sqrt(Sxx Syy) - r (y_i - yb) / Syy)
+ * (their moments are accumulated about the row's first elements, which keeps
+ * the centred sums accurate for rows far from zero mean)
  * mean / rstd are the forward's saved row statistics (rstd = 1/sqrt(var +
  * eps) for LayerNorm, 1/sqrt(sum x^2 / N + eps) for RMSNorm), FP32 per row.
  * Only dx is computed (the parameter gradients dgamma / dbeta are column
@@ -291,7 +302,9 @@ typedef enum {
     CREDIT_OP_LAYERNORM_BWD = 5,
     CREDIT_OP_RMSNORM_BWD = 6,
     CREDIT_OP_SOFTMAX_LOGITS_BWD = 7,
-    CREDIT_OP_XENT_BWD = 8
+    CREDIT_OP_XENT_BWD = 8,
+    CREDIT_OP_WVAR_BWD = 9,
+    CREDIT_OP_PEARSON_BWD = 10
 } credit_bwd_op;
 
 /*
@@ -303,7 +316,10 @@ typedef enum {
  *   gamma      norms: cols FP32, NULL = 1; ignored by softmax
  *   mean       LAYERNORM_BWD: rows FP32 (required)
  *   rstd       LAYERNORM_BWD / RMSNORM_BWD: rows FP32 (required)
- *   scale      XENT_BWD: rows FP32 upstream gradients of the row losses (NULL = 1); ignored otherwise
+ *   scale      XENT_BWD, WVAR_BWD, PEARSON_BWD: rows FP32 upstream gradients of the row losses or
+ *              statistics (NULL = 1); ignored otherwise
+ *   dx2        WVAR_BWD / PEARSON_BWD: the second gradient (dw or dy), laid out as dx (required); may
+ *              equal dy.  Ignored otherwise.
  */
 typedef struct {
     int32_t op;
@@ -316,6 +332,7 @@ typedef struct {
     const float *mean;
     const float *rstd;
     const float *scale;
+    void *dx2;
 } credit_bwd_args;
 
 /*

@@ -24,9 +24,10 @@ OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_INITIALIZED
 OP_NAMES = {SOFTMAX: "softmax", LOGSUMEXP: "logsumexp", LAYERNORM: "layernorm", RMSNORM: "rmsnorm"}
 PATH_NAMES = {PATH_ONE_CTA: "one_cta", PATH_TWO_PASS: "two_pass", PATH_CLUSTER: "cluster"}
 RETAIN_AUTO, RETAIN_SMEM, RETAIN_TMEM = 0, 1, 2
-SOFTMAX_BWD, LAYERNORM_BWD, RMSNORM_BWD, SOFTMAX_LOGITS_BWD, XENT_BWD = 4, 5, 6, 7, 8
+SOFTMAX_BWD, LAYERNORM_BWD, RMSNORM_BWD, SOFTMAX_LOGITS_BWD, XENT_BWD, WVAR_BWD, PEARSON_BWD = 4, 5, 6, 7, 8, 9, 10
 OP_NAMES.update({SOFTMAX_BWD: "softmax_bwd", LAYERNORM_BWD: "layernorm_bwd", RMSNORM_BWD: "rmsnorm_bwd",
-                 SOFTMAX_LOGITS_BWD: "softmax_logits_bwd", XENT_BWD: "xent_bwd"})
+                 SOFTMAX_LOGITS_BWD: "softmax_logits_bwd", XENT_BWD: "xent_bwd", WVAR_BWD: "wvar_bwd",
+                 PEARSON_BWD: "pearson_bwd"})
 
 TORCH_DTYPE = {F32: torch.float32, BF16: torch.bfloat16, FP8_E4M3: torch.float8_e4m3fn}
 DTYPE_OF = {torch.float32: F32, torch.bfloat16: BF16, torch.float8_e4m3fn: FP8_E4M3}
@@ -63,7 +64,7 @@ class BwdArgsT(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int32), ("dtype", ctypes.c_int32), ("a", ctypes.c_void_p), ("dy", ctypes.c_void_p),
                 ("dx", ctypes.c_void_p), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("ld", ctypes.c_int64),
                 ("gamma", ctypes.c_void_p), ("mean", ctypes.c_void_p), ("rstd", ctypes.c_void_p),
-                ("scale", ctypes.c_void_p)]
+                ("scale", ctypes.c_void_p), ("dx2", ctypes.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -350,7 +351,7 @@ def run_two_pass_noalloc(op: int, x, out, ctas_per_row: int, *, stream=None, **k
 
 
 def make_bwd_args(op: int, a, dy, dx, *, rows: int | None = None, cols: int | None = None, ld: int = 0,
-                  dtype: int | None = None, gamma=None, mean=None, rstd=None, scale=None) -> BwdArgsT:
+                  dtype: int | None = None, gamma=None, mean=None, rstd=None, scale=None, dx2=None) -> BwdArgsT:
     r = BwdArgsT()
     r.op = op
     r.dtype = DTYPE_OF[a.dtype] if dtype is None else dtype
@@ -358,7 +359,7 @@ def make_bwd_args(op: int, a, dy, dx, *, rows: int | None = None, cols: int | No
     if rows is None or cols is None:
         rows, cols = a.shape[0], a.shape[-1]
     r.rows, r.cols, r.ld = rows, cols, ld
-    r.gamma, r.mean, r.rstd, r.scale = _ptr(gamma), _ptr(mean), _ptr(rstd), _ptr(scale)
+    r.gamma, r.mean, r.rstd, r.scale, r.dx2 = _ptr(gamma), _ptr(mean), _ptr(rstd), _ptr(scale), _ptr(dx2)
     return r
 
 

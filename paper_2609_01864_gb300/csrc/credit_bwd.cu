@@ -52,12 +52,17 @@ extern std::atomic<long long> g_launch_count;
 
 namespace {
 
-enum BwdOp : int { BOP_SOFTMAX = 4, BOP_LN = 5, BOP_RMS = 6, BOP_SMLOGITS = 7, BOP_XENT = 8 };
+enum BwdOp : int {
+    BOP_SOFTMAX = 4, BOP_LN = 5, BOP_RMS = 6, BOP_SMLOGITS = 7, BOP_XENT = 8, BOP_WVAR = 9, BOP_PEARSON = 10
+};
 template <int OP> constexpr bool kLogits = OP == BOP_SMLOGITS || OP == BOP_XENT;  // online max statistics
 template <int OP> constexpr bool kNorm = OP == BOP_LN || OP == BOP_RMS;          // gamma, saved statistics
+template <int OP> constexpr bool kPair = OP == BOP_WVAR || OP == BOP_PEARSON;    // two outputs, shifted sums
+template <int OP> constexpr int kKind = kLogits<OP> ? 1 : (kPair<OP> ? 2 : 0);
+template <int OP> constexpr int kPairSums = OP == BOP_WVAR ? 3 : 5;               // sums of the pair ops
 
 constexpr int kBwdThreads = 512;
-constexpr int kBwdCtrl = 1280;             // control area before the row buffers (bytes)
+constexpr int kBwdCtrl = 1792;             // control area before the row buffers (bytes)
 constexpr int kBwdMaxChunks = 8;           // chunks (mbarriers) per row buffer
 constexpr uint32_t kBwdPiece = 32768;      // bytes per bulk copy instruction
 constexpr long long kBwdFusedMaxBytes = 16384;  // planner: fused two-pass up to this many bytes per array row
@@ -65,11 +70,12 @@ constexpr long long kBwdFusedMaxBytes = 16384;  // planner: fused two-pass up to
 struct BwdArgs {
     const unsigned char *a, *dy;
     unsigned char *dx;
-    long long rows, cols, ld;  // ld in elements (all three arrays)
+    unsigned char *dx2;        // pair ops: the second gradient (dw or dy)
+    long long rows, cols, ld;  // ld in elements (all arrays)
     const float *gamma, *mean, *rstd;
     const float *scale;        // cross entropy: per-row upstream scale (null = 1)
     unsigned *err;
-    float *ws;                 // two-pass partials [row - row0][G][2] ([G][4] for the logits ops)
+    float *ws;                 // two-pass partials [row - row0][G][2] ([G][4] logits ops, [G][8] pair ops)
     int G;                     // two-pass CTAs per row
     int nbuf;                  // staged: row buffers (1 or 2)
     int slice_groups;          // staged: 16-byte groups per array slice buffer
@@ -80,16 +86,53 @@ struct BwdArgs {
 
 // Per-row constants and the per-element math of each op.
 struct Coef {
-    float c0, c1, c2;
+    float c0, c1, c2, c3, c4;
 };
 
 template <int OP>
 struct BwdRow {
     float mean = 0.0f, rstd = 1.0f, w = 1.0f;
+    float kx = 0.0f, ky = 0.0f;  // pair ops: the shifts (the row's first elements of a and dy)
     __device__ __forceinline__ void load(const BwdArgs &p, long long row) {
         if constexpr (OP == BOP_LN) mean = p.mean[row];
         if constexpr (kNorm<OP>) rstd = p.rstd[row];
-        if constexpr (OP == BOP_XENT) w = p.scale ? p.scale[row] : 1.0f;
+        if constexpr (OP == BOP_XENT || kPair<OP>) w = p.scale ? p.scale[row] : 1.0f;
+    }
+    template <int DT>
+    __device__ __forceinline__ void load_shifts(const BwdArgs &p, long long row) {
+        if constexpr (kPair<OP>) {
+            const size_t off = static_cast<size_t>(row * p.ld) * Fmt<DT>::size;
+            kx = decode_one<DT>(p.a + off, 1.0f);
+            if constexpr (OP == BOP_PEARSON) ky = decode_one<DT>(p.dy + off, 1.0f);
+        }
+    }
+    // pair ops: add element (a, d) to the shifted sums s[0..kPairSums)
+    __device__ __forceinline__ void acc_pair(float a, float d, float *s) const {
+        if constexpr (OP == BOP_WVAR) {  // d is the weight
+            const float u = a - kx, wu = d * u;
+            s[0] += d;
+            s[1] += wu;
+            s[2] = fmaf(wu, u, s[2]);
+        } else if constexpr (OP == BOP_PEARSON) {
+            const float u = a - kx, v = d - ky;
+            s[0] += u;
+            s[1] += v;
+            s[2] = fmaf(u, u, s[2]);
+            s[3] = fmaf(v, v, s[3]);
+            s[4] = fmaf(u, v, s[4]);
+        }
+    }
+    // pair ops: both gradients of element (a, d)
+    __device__ __forceinline__ void dx_pair(float a, float d, const Coef &k, float &o1, float &o2) const {
+        if constexpr (OP == BOP_WVAR) {  // c0 = mean, c1 = variance, c2 = g / W
+            const float u = a - k.c0;
+            o1 = k.c2 * 2.0f * d * u;
+            o2 = k.c2 * fmaf(u, u, -k.c1);
+        } else {  // c0 = x mean, c1 = y mean, c2 = g / sqrt(Sxx Syy), c3 = g r / Sxx, c4 = g r / Syy
+            const float u = a - k.c0, v = d - k.c1;
+            o1 = k.c2 * v - k.c3 * u;
+            o2 = k.c2 * u - k.c4 * v;
+        }
     }
     // add element (a, dy, gamma) to the partial sums
     __device__ __forceinline__ void acc(float a, float d, float gm, float &s0, float &s1) const {
@@ -125,11 +168,11 @@ struct BwdRow {
 // 16-byte group is folded in before its exponentials, as in the forward
 // softmax.  merge() is commutative bit for bit, so a shuffle tree gives the
 // same state in both lanes of every pair.
-template <int OP, bool L = kLogits<OP>>
+template <int OP, int KIND = kKind<OP>>
 struct BwdState;
 
 template <int OP>
-struct BwdState<OP, false> {
+struct BwdState<OP, 0> {
     float s0 = 0.0f, s1 = 0.0f;
     template <int V>
     __device__ __forceinline__ void add(const BwdRow<OP> &R, const float (&fa)[V], const float (&fd)[V],
@@ -141,7 +184,7 @@ struct BwdState<OP, false> {
 };
 
 template <int OP>
-struct BwdState<OP, true> {
+struct BwdState<OP, 1> {
     float m = -INFINITY, S = 0.0f, T = 0.0f;
     template <int V>
     __device__ __forceinline__ void add(const BwdRow<OP> &, const float (&fa)[V], const float (&fd)[V],
@@ -187,18 +230,98 @@ struct BwdState<OP, true> {
     }
 };
 
+// Pair ops: sums of the row about shifts taken from its first elements
+// (weighted variance: sum w, sum w u, sum w u^2 with u = x - kx; Pearson:
+// sum u, sum v, sum u^2, sum v^2, sum u v with v = y - ky), so that the
+// centred moments lose little to cancellation.  Plain sums: merged by addition.
+template <int OP>
+struct BwdState<OP, 2> {
+    float s[kPairSums<OP>] = {};
+    template <int V>
+    __device__ __forceinline__ void add(const BwdRow<OP> &R, const float (&fa)[V], const float (&fd)[V],
+                                        const float (&)[V]) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) R.acc_pair(fa[v], fd[v], s);
+    }
+    __device__ __forceinline__ void add1(const BwdRow<OP> &R, float a, float d, float) { R.acc_pair(a, d, s); }
+};
+
+// Coefficients of the pair ops from the row totals (see BwdRow::dx_pair).
+template <int OP>
+__device__ __forceinline__ Coef pair_coeffs(const float *t, long long N, const BwdRow<OP> &R) {
+    if constexpr (OP == BOP_WVAR) {
+        const float W = t[0], inv = 1.0f / W, m1 = t[1] * inv;
+        return {R.kx + m1, t[2] * inv - m1 * m1, R.w * inv, 0.0f, 0.0f};
+    } else {
+        const float n = static_cast<float>(N), inv_n = 1.0f / n;
+        const float sxx = t[2] - t[0] * t[0] * inv_n, syy = t[3] - t[1] * t[1] * inv_n;
+        const float sxy = t[4] - t[0] * t[1] * inv_n;
+        const float inv_den = 1.0f / sqrtf(sxx * syy), r = sxy * inv_den;
+        return {R.kx + t[0] * inv_n, R.ky + t[1] * inv_n, R.w * inv_den, R.w * r / sxx, R.w * r / syy};
+    }
+}
+
+// Deterministic block sum of NS floats through red (>= 16 NS + NS floats).
+// Every thread returns the totals in out.  Contains two __syncthreads.
+template <int NS>
+__device__ __forceinline__ void block_sum_n(const float (&v)[NS], float *red, float (&out)[NS]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        const float t = warp_sum(v[j]);
+        if (lane == 0) red[NS * wid + j] = t;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            const float t = warp_sum(lane < nw ? red[NS * lane + j] : 0.0f);
+            if (lane == 0) red[NS * 16 + j] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NS; ++j) out[j] = red[NS * 16 + j];
+}
+
+// Push all-gather of up to 8 floats per CTA: slots of 8 floats, [par][16][8],
+// two 16-byte st.async per peer (the protocol of exchange_push).
+__device__ __forceinline__ const float *exchange_push8(const float (&v)[8], float *slots, uint64_t *xbar, int par,
+                                                       uint32_t phase, int P, int c, int Tc, unsigned *err) {
+    const int tid = threadIdx.x;
+    float *base = slots + par * 16 * 8;
+    float *mine = base + c * 8;
+    uint64_t *bar = &xbar[par];
+    if (tid < P) {
+        if (tid == c) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) mine[j] = v[j];
+        } else {
+            fence_release_smem_cluster();
+            const uint32_t raddr = mapa_shared(smem_addr(mine), static_cast<uint32_t>(tid));
+            const uint32_t rbar = mapa_shared(smem_addr(bar), static_cast<uint32_t>(tid));
+            st_async_v4f32(raddr, make_float4(v[0], v[1], v[2], v[3]), rbar);
+            st_async_v4f32(raddr + 16, make_float4(v[4], v[5], v[6], v[7]), rbar);
+        }
+    }
+    if (tid == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>((P - 1) * 32));
+    named_bar_sync(1, Tc);
+    mbar_wait_bounded_cluster(bar, phase, err);
+    return base;
+}
+
 template <int OP>
 __device__ __forceinline__ Coef logit_coeffs(float M, float S, float T) {
     const float inv = 1.0f / S;
-    if constexpr (OP == BOP_SMLOGITS) return {M, inv, T * inv};
-    else return {M, T * inv, 0.0f};
+    if constexpr (OP == BOP_SMLOGITS) return {M, inv, T * inv, 0.0f, 0.0f};
+    else return {M, T * inv, 0.0f, 0.0f, 0.0f};
 }
 
 // Shuffle-tree merge of the logits state over groups of `width` lanes (a
 // power of two).  The tree is fixed and merge() commutative, so every lane
 // of a group ends with the same state; merging an empty state is exact.
 template <int OP>
-__device__ __forceinline__ void warp_merge_logits(BwdState<OP, true> &st, int width) {
+__device__ __forceinline__ void warp_merge_logits(BwdState<OP, 1> &st, int width) {
     for (int o = width >> 1; o > 0; o >>= 1) {
         const float m2 = __shfl_xor_sync(0xffffffffu, st.m, o);
         const float S2 = __shfl_xor_sync(0xffffffffu, st.S, o);
@@ -211,7 +334,7 @@ __device__ __forceinline__ void warp_merge_logits(BwdState<OP, true> &st, int wi
 // a shuffle tree per warp, then one over the warps' states in warp 0.  Every
 // thread returns (m, S, T, 0).  Contains two __syncthreads.
 template <int OP>
-__device__ __forceinline__ float4 block_reduce_logits(BwdState<OP, true> st, float *red) {
+__device__ __forceinline__ float4 block_reduce_logits(BwdState<OP, 1> st, float *red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     warp_merge_logits<OP>(st, 32);
     if (lane == 0) {
@@ -221,7 +344,7 @@ __device__ __forceinline__ float4 block_reduce_logits(BwdState<OP, true> st, flo
     }
     __syncthreads();
     if (wid == 0) {
-        BwdState<OP, true> t;
+        BwdState<OP, 1> t;
         if (lane < nw) {
             t.m = red[4 * lane];
             t.S = red[4 * lane + 1];
@@ -270,9 +393,9 @@ __device__ __forceinline__ const float *exchange_push4(const float4 &v, float *s
 template <int OP>
 __device__ __forceinline__ Coef row_coeffs(float S0, float S1, long long N) {
     const float inv_n = 1.0f / static_cast<float>(N);
-    if constexpr (OP == BOP_SOFTMAX) return {S0, 0.0f, 0.0f};
-    else if constexpr (OP == BOP_LN) return {S0 * inv_n, S1 * inv_n, 0.0f};
-    else return {0.0f, S1 * inv_n, 0.0f};
+    if constexpr (OP == BOP_SOFTMAX) return {S0, 0.0f, 0.0f, 0.0f, 0.0f};
+    else if constexpr (OP == BOP_LN) return {S0 * inv_n, S1 * inv_n, 0.0f, 0.0f, 0.0f};
+    else return {0.0f, S1 * inv_n, 0.0f, 0.0f, 0.0f};
 }
 
 // Deterministic block sum of two floats through red (>= 66 floats); every
@@ -402,6 +525,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
         }
         BwdRow<OP> R;
         R.load(p, row);
+    R.template load_shifts<DT>(p, row);
+        R.template load_shifts<DT>(p, row);
         const unsigned char *da = data + static_cast<size_t>(b) * 2 * arr, *dd = da + arr;
         const size_t row_off = static_cast<size_t>(row * p.ld) * isz;
 
@@ -436,7 +561,24 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
             }
         }
         Coef kc;
-        if constexpr (kLogits<OP>) {
+        if constexpr (kPair<OP>) {
+            constexpr int NS = kPairSums<OP>;
+            float tot[NS];
+            block_sum_n<NS>(st.s, red, tot);
+            if (P > 1) {
+                float v8[8] = {};
+#pragma unroll
+                for (int j = 0; j < NS; ++j) v8[j] = tot[j];
+                const float *sl = exchange_push8(v8, slots, xbar, static_cast<int>(it & 1),
+                                                 static_cast<uint32_t>((it >> 1) & 1), P, c, T, p.err);
+#pragma unroll
+                for (int j = 0; j < NS; ++j) tot[j] = 0.0f;
+                for (int q = 0; q < P; ++q)  // fixed order: the same totals in every CTA
+#pragma unroll
+                    for (int j = 0; j < NS; ++j) tot[j] += sl[8 * q + j];
+            }
+            kc = pair_coeffs<OP>(tot, N, R);
+        } else if constexpr (kLogits<OP>) {
             float4 tot = block_reduce_logits<OP>(st, red);
             if (P > 1) {
                 const float *sl = exchange_push4(tot, slots, xbar, static_cast<int>(it & 1),
@@ -473,12 +615,20 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
             for (long long t = tid; t < tail; t += T) {
                 const long long i = Gq * V + t;
                 const float gm = (kNorm<OP> && p.gamma) ? p.gamma[i] : 1.0f;
-                const float v = R.dx(decode_one<DT>(p.a + row_off + i * isz, 1.0f),
-                                     decode_one<DT>(p.dy + row_off + i * isz, 1.0f), gm, kc);
-                store_one<DT>(p.dx + row_off + i * isz, v);
+                const float av = decode_one<DT>(p.a + row_off + i * isz, 1.0f);
+                const float dv = decode_one<DT>(p.dy + row_off + i * isz, 1.0f);
+                if constexpr (kPair<OP>) {
+                    float o1, o2;
+                    R.dx_pair(av, dv, kc, o1, o2);
+                    store_one<DT>(p.dx + row_off + i * isz, o1);
+                    store_one<DT>(p.dx2 + row_off + i * isz, o2);
+                } else {
+                    store_one<DT>(p.dx + row_off + i * isz, R.dx(av, dv, gm, kc));
+                }
             }
         }
         unsigned char *xr = p.dx + row_off + static_cast<size_t>(g_lo * V) * isz;
+        unsigned char *xr2 = kPair<OP> ? p.dx2 + row_off + static_cast<size_t>(g_lo * V) * isz : nullptr;
         auto write = [&](int k0, int k1) {
             for (int k = k0 + tid; k < k1; k += T) {
                 float fa[V], fd[V], fg[V], y[V];
@@ -486,9 +636,17 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
                 decode_group<DT>(*reinterpret_cast<const uint4 *>(dd + 16 * k), fd, 1.0f);
                 if (g_sm) load_affine_smem<V>(gs, k * V, 1.0f, fg);
                 else load_affine<V>(kNorm<OP> ? p.gamma : nullptr, (g_lo + k) * V, g_vec, 1.0f, fg);
+                if constexpr (kPair<OP>) {
+                    float y2[V];
 #pragma unroll
-                for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], kc);
-                store_group<DT, V>(xr + 16 * k, y, true);
+                    for (int v = 0; v < V; ++v) R.dx_pair(fa[v], fd[v], kc, y[v], y2[v]);
+                    store_group<DT, V>(xr + 16 * k, y, true);
+                    store_group<DT, V>(xr2 + 16 * k, y2, true);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], kc);
+                    store_group<DT, V>(xr + 16 * k, y, true);
+                }
             }
         };
         if (p.nbuf == 2) {
@@ -528,7 +686,8 @@ __device__ __forceinline__ BwdSpan bwd_span(const BwdArgs &p, long long row, int
     constexpr int isz = Fmt<DT>::size, V = Fmt<DT>::V;
     const size_t off = static_cast<size_t>(row * p.ld) * isz;
     const bool vec = ((reinterpret_cast<uintptr_t>(p.a + off) | reinterpret_cast<uintptr_t>(p.dy + off) |
-                       reinterpret_cast<uintptr_t>(p.dx + off)) & 15u) == 0;
+                       reinterpret_cast<uintptr_t>(p.dx + off) |
+                       (p.dx2 ? reinterpret_cast<uintptr_t>(p.dx2 + off) : 0)) & 15u) == 0;
     BwdSpan s;
     s.vec = vec;
     if (vec) {
@@ -582,16 +741,30 @@ __device__ __forceinline__ void bwd_apply(const BwdArgs &p, long long row, const
             decode_group<DT>(ld_global_v4(p.a + off + 16 * k), fa, 1.0f);
             decode_group<DT>(ld_global_v4(p.dy + off + 16 * k), fd, 1.0f);
             load_affine<V>(gam, k * V, g_vec, 1.0f, fg);
+            if constexpr (kPair<OP>) {
+                float y2[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], kc);
-            store_group<DT, V>(p.dx + off + 16 * k, y, true);
+                for (int v = 0; v < V; ++v) R.dx_pair(fa[v], fd[v], kc, y[v], y2[v]);
+                store_group<DT, V>(p.dx + off + 16 * k, y, true);
+                store_group<DT, V>(p.dx2 + off + 16 * k, y2, true);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) y[v] = R.dx(fa[v], fd[v], fg[v], kc);
+                store_group<DT, V>(p.dx + off + 16 * k, y, true);
+            }
         }
     }
     const long long e_lo = s.vec ? s.t_lo : s.lo, e_hi = s.vec ? s.t_hi : s.hi;
     for (long long i = e_lo + threadIdx.x; i < e_hi; i += blockDim.x) {
-        const float v = R.dx(decode_one<DT>(p.a + off + i * isz, 1.0f), decode_one<DT>(p.dy + off + i * isz, 1.0f),
-                             gam ? gam[i] : 1.0f, kc);
-        store_one<DT>(p.dx + off + i * isz, v);
+        const float av = decode_one<DT>(p.a + off + i * isz, 1.0f), dv = decode_one<DT>(p.dy + off + i * isz, 1.0f);
+        if constexpr (kPair<OP>) {
+            float o1, o2;
+            R.dx_pair(av, dv, kc, o1, o2);
+            store_one<DT>(p.dx + off + i * isz, o1);
+            store_one<DT>(p.dx2 + off + i * isz, o2);
+        } else {
+            store_one<DT>(p.dx + off + i * isz, R.dx(av, dv, gam ? gam[i] : 1.0f, kc));
+        }
     }
 }
 
@@ -602,10 +775,15 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_fused(const BwdArgs p) {
     const long long row = p.row0 + blockIdx.x;
     BwdRow<OP> R;
     R.load(p, row);
+    R.template load_shifts<DT>(p, row);
     const BwdSpan s = bwd_span<DT>(p, row, 0, 1);
     const BwdState<OP> t = bwd_sums<OP, DT>(p, row, R, s);
     Coef kc;
-    if constexpr (kLogits<OP>) {
+    if constexpr (kPair<OP>) {
+        float tot[kPairSums<OP>];
+        block_sum_n<kPairSums<OP>>(t.s, red, tot);
+        kc = pair_coeffs<OP>(tot, p.cols, R);
+    } else if constexpr (kLogits<OP>) {
         const float4 tot = block_reduce_logits<OP>(t, red);
         kc = logit_coeffs<OP>(tot.x, tot.y, tot.z);
     } else {
@@ -616,7 +794,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_fused(const BwdArgs p) {
 }
 
 // G > 1, launch 1: partial sums of CTA j of row lr into ws[lr][j][0..1] (logits ops: the state into
-// ws[lr][j][0..2] of a 4-float record).
+// ws[lr][j][0..2] of a 4-float record; pair ops: the sums into an 8-float record).
 template <int OP, int DT>
 __global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_stats(const BwdArgs p) {
     __shared__ float red[128];
@@ -624,9 +802,17 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_stats(const BwdArgs p) {
     const long long lr = blockIdx.x / G, row = p.row0 + lr;
     BwdRow<OP> R;
     R.load(p, row);
+    R.template load_shifts<DT>(p, row);
     const BwdSpan s = bwd_span<DT>(p, row, j, G);
     const BwdState<OP> t = bwd_sums<OP, DT>(p, row, R, s);
-    if constexpr (kLogits<OP>) {
+    if constexpr (kPair<OP>) {
+        float tot[kPairSums<OP>];
+        block_sum_n<kPairSums<OP>>(t.s, red, tot);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < kPairSums<OP>; ++q) p.ws[(lr * G + j) * 8 + q] = tot[q];
+        }
+    } else if constexpr (kLogits<OP>) {
         const float4 tot = block_reduce_logits<OP>(t, red);
         if (threadIdx.x == 0) {
             p.ws[(lr * G + j) * 4] = tot.x;
@@ -649,8 +835,16 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_apply(const BwdArgs p) {
     const long long lr = blockIdx.x / G, row = p.row0 + lr;
     BwdRow<OP> R;
     R.load(p, row);
+    R.template load_shifts<DT>(p, row);
     Coef kc;
-    if constexpr (kLogits<OP>) {
+    if constexpr (kPair<OP>) {
+        float tot[kPairSums<OP>] = {};
+        for (int q = 0; q < G; ++q) {  // fixed order
+#pragma unroll
+            for (int i = 0; i < kPairSums<OP>; ++i) tot[i] += p.ws[(lr * G + q) * 8 + i];
+        }
+        kc = pair_coeffs<OP>(tot, p.cols, R);
+    } else if constexpr (kLogits<OP>) {
         BwdState<OP> all;
         for (int q = 0; q < G; ++q)
             all.merge(p.ws[(lr * G + q) * 4], p.ws[(lr * G + q) * 4 + 1], p.ws[(lr * G + q) * 4 + 2]);
@@ -689,6 +883,10 @@ bool bwd_kernels(int op, int dt, BwdKernels *k) {
     case BOP_SMLOGITS * 4 + DT_BF16: *k = bwd_kernels_of<BOP_SMLOGITS, DT_BF16>(); return true;
     case BOP_XENT * 4 + DT_F32: *k = bwd_kernels_of<BOP_XENT, DT_F32>(); return true;
     case BOP_XENT * 4 + DT_BF16: *k = bwd_kernels_of<BOP_XENT, DT_BF16>(); return true;
+    case BOP_WVAR * 4 + DT_F32: *k = bwd_kernels_of<BOP_WVAR, DT_F32>(); return true;
+    case BOP_WVAR * 4 + DT_BF16: *k = bwd_kernels_of<BOP_WVAR, DT_BF16>(); return true;
+    case BOP_PEARSON * 4 + DT_F32: *k = bwd_kernels_of<BOP_PEARSON, DT_F32>(); return true;
+    case BOP_PEARSON * 4 + DT_BF16: *k = bwd_kernels_of<BOP_PEARSON, DT_BF16>(); return true;
     default: return false;
     }
 }
@@ -696,7 +894,7 @@ bool bwd_kernels(int op, int dt, BwdKernels *k) {
 // ------------------------------------------------------------------ host
 credit_status validate_bwd(const credit_bwd_args *a) {
     if (a == nullptr) return CREDIT_ERR_INVALID_ARG;
-    if (a->op < BOP_SOFTMAX || a->op > BOP_XENT) return CREDIT_ERR_INVALID_ARG;
+    if (a->op < BOP_SOFTMAX || a->op > BOP_PEARSON) return CREDIT_ERR_INVALID_ARG;
     if (a->dtype == CREDIT_FP8_E4M3) return CREDIT_ERR_UNSUPPORTED;
     if (a->dtype != CREDIT_F32 && a->dtype != CREDIT_BF16) return CREDIT_ERR_INVALID_ARG;
     if (a->rows < 0 || a->cols <= 0 || a->ld < 0 || (a->ld != 0 && a->ld < a->cols)) return CREDIT_ERR_INVALID_ARG;
@@ -704,6 +902,7 @@ credit_status validate_bwd(const credit_bwd_args *a) {
     if (a->a == nullptr || a->dy == nullptr || a->dx == nullptr) return CREDIT_ERR_INVALID_ARG;
     if (a->op == BOP_LN && (a->mean == nullptr || a->rstd == nullptr)) return CREDIT_ERR_INVALID_ARG;
     if (a->op == BOP_RMS && a->rstd == nullptr) return CREDIT_ERR_INVALID_ARG;
+    if ((a->op == BOP_WVAR || a->op == BOP_PEARSON) && a->dx2 == nullptr) return CREDIT_ERR_INVALID_ARG;
     return CREDIT_OK;
 }
 
@@ -711,7 +910,7 @@ bool rows_aligned(const credit_bwd_args *a) {
     const long long ld = a->ld ? a->ld : a->cols;
     const int isz = dtype_size(a->dtype);
     const uintptr_t u = reinterpret_cast<uintptr_t>(a->a) | reinterpret_cast<uintptr_t>(a->dy) |
-                        reinterpret_cast<uintptr_t>(a->dx);
+                        reinterpret_cast<uintptr_t>(a->dx) | reinterpret_cast<uintptr_t>(a->dx2);
     return (u & 15u) == 0 && (a->rows <= 1 || (ld * isz) % 16 == 0);
 }
 
@@ -834,6 +1033,7 @@ BwdArgs make_bwd_args(const credit_bwd_args *a, unsigned *err, float *ws) {
     r.a = static_cast<const unsigned char *>(a->a);
     r.dy = static_cast<const unsigned char *>(a->dy);
     r.dx = static_cast<unsigned char *>(a->dx);
+    r.dx2 = static_cast<unsigned char *>(a->dx2);
     r.rows = a->rows;
     r.cols = a->cols;
     r.ld = a->ld ? a->ld : a->cols;
@@ -860,7 +1060,7 @@ using namespace credit;
 extern "C" {
 
 credit_status credit_plan_bwd(int32_t op, int64_t rows, int64_t cols, credit_dtype dtype, credit_plan_t *out) {
-    if (out == nullptr || op < BOP_SOFTMAX || op > BOP_XENT || rows < 0 || cols <= 0) return CREDIT_ERR_INVALID_ARG;
+    if (out == nullptr || op < BOP_SOFTMAX || op > BOP_PEARSON || rows < 0 || cols <= 0) return CREDIT_ERR_INVALID_ARG;
     if (dtype != CREDIT_F32 && dtype != CREDIT_BF16) return CREDIT_ERR_UNSUPPORTED;
     int dev = 0;
     const credit_status st = ensure_init(&dev, nullptr);
@@ -925,7 +1125,8 @@ credit_status credit_run_bwd(const credit_bwd_args *args, const credit_plan_t *p
         return CREDIT_OK;
     }
     const int G = chosen.ctas_per_row;
-    const size_t rec = (args->op == BOP_SMLOGITS || args->op == BOP_XENT) ? 4 : 2;  // floats per partial
+    const size_t rec = (args->op == BOP_SMLOGITS || args->op == BOP_XENT) ? 4
+                       : (args->op == BOP_WVAR || args->op == BOP_PEARSON) ? 8 : 2;  // floats per partial
     const long long cap = G == 1 ? 0x7FFFFFFFLL : static_cast<long long>(ws_floats / (static_cast<size_t>(G) * rec));
     const long long max_rows = cap < 0x7FFFFFFFLL / G ? cap : 0x7FFFFFFFLL / G;
     if (max_rows < 1) return CREDIT_ERR_UNSUPPORTED;

@@ -227,3 +227,66 @@ def bwd_error(op, dtype, dx, ref, a, dy, gamma, mean, rstd, cols):
         ulp = np.where(mag > 0, np.exp2(np.floor(np.log2(np.where(mag > 0, mag, 1.0))) - 7), 2.0 ** -133)
         bound = bound + ulp
     return float((np.abs(dx - ref) / bound).max())
+
+
+# ---------------------------------------------------------------- two-input statistics (weighted variance, Pearson)
+def pair_inputs(op: int, dtype: int, rows: int, cols: int, *, ld: int = 0, seed: int = 0, device="cpu"):
+    """Tensors (x, d, g): weighted variance x ~ N(3, 2^2) with 1% +-50 outliers and weights d ~ U(0.1, 2);
+    Pearson x with outliers and d = 0.5 x + N(0, 1); per-row upstream gradients g ~ U(0.5, 2)."""
+    ld = ld or cols
+    x = synth.outliers(rows, ld, seed=seed, device=device)
+    gen = torch.Generator(device=device).manual_seed(seed + 7)
+    if op == C.WVAR_BWD:
+        x = 2.0 * x + 3.0
+        d = 0.1 + 1.9 * torch.rand(rows, ld, generator=gen, device=device)
+    else:
+        d = 0.5 * x + synth.normal(rows, ld, seed=seed + 1, device=device)
+    g = 0.5 + 1.5 * torch.rand(rows, generator=gen, device=device)
+    if dtype == C.BF16:
+        x, d = synth.to_bf16(x), synth.to_bf16(d)
+    return x, d, g
+
+
+def pair_reference(op, x, d, g, cols):
+    x64, d64 = to64(x)[:, :cols], to64(d)[:, :cols]
+    gg = g.cpu().double().numpy()
+    return O.wvar_bwd(x64, d64, gg) if op == C.WVAR_BWD else O.pearson_bwd(x64, d64, gg)
+
+
+def pair_error(op, dtype, out1, out2, ref1, ref2, x, d, g, cols):
+    """Largest error of the two gradients in units of their bounds (<= 1.0 passes): 1e-5 of the row's
+    largest term of each formula, times the conditioning kappa of the shifted moments, plus one BF16 ulp
+    of the exact value for BF16.  Weighted variance: dx terms g 2 w (x - mu) / W, dw terms g (x - mu)^2 / W
+    and g v / W; Pearson: g (y - yb) / sqrt(Sxx Syy) and g r (x - xb) / Sxx (dx), symmetrically for dy.
+    The kernels accumulate the second moments about the row's first elements K, so the FP32 error of a
+    centred moment such as Sxx is a small multiple of 2^-24 sum (x - K)^2 = 2^-24 (Sxx + N (xb - K)^2):
+    kappa = sum (x - K)^2 / Sxx (the larger of x and y; weighted for the variance), 1 + chi^2_1 for a
+    typical K and large when K is an outlier of its row."""
+    x64, d64 = to64(x)[:, :cols], to64(d)[:, :cols]
+    gg = np.abs(g.cpu().double().numpy())
+    if op == C.WVAR_BWD:
+        W = d64.sum(axis=1)
+        mu = (d64 * x64).sum(axis=1) / W
+        u = x64 - mu[:, None]
+        v = (d64 * u * u).sum(axis=1) / W
+        uk = x64 - x64[:, :1]
+        kappa = (d64 * uk * uk).sum(axis=1) / (d64 * u * u).sum(axis=1)
+        S1 = gg / W * np.abs(2 * d64 * u).max(axis=1) * kappa
+        S2 = gg / W * ((u * u).max(axis=1) + v) * kappa
+    else:
+        u = x64 - x64.mean(axis=1, keepdims=True)
+        w_ = d64 - d64.mean(axis=1, keepdims=True)
+        sxx, syy = (u * u).sum(axis=1), (w_ * w_).sum(axis=1)
+        kappa = np.maximum(((x64 - x64[:, :1]) ** 2).sum(axis=1) / sxx, ((d64 - d64[:, :1]) ** 2).sum(axis=1) / syy)
+        den = np.sqrt(sxx * syy)
+        r = np.abs((u * w_).sum(axis=1)) / den
+        S1 = gg * (np.abs(w_).max(axis=1) / den + r * np.abs(u).max(axis=1) / sxx) * kappa
+        S2 = gg * (np.abs(u).max(axis=1) / den + r * np.abs(w_).max(axis=1) / syy) * kappa
+    worst = 0.0
+    for out, ref, S in ((out1, ref1, S1), (out2, ref2, S2)):
+        bound = F32_TOL * S[:, None]
+        if dtype == C.BF16:
+            mag = np.abs(ref)
+            bound = bound + np.where(mag > 0, np.exp2(np.floor(np.log2(np.where(mag > 0, mag, 1.0))) - 7), 2.0 ** -133)
+        worst = max(worst, float((np.abs(out - ref) / bound).max()))
+    return worst
