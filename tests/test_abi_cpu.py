@@ -96,7 +96,13 @@ def test_backward_validation_rejects_bad_calls_without_touching_the_gpu(lib):
     assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_INVALID_ARG
     r.op, r.rstd = C.RMSNORM_BWD, None                                       # RMSNorm needs rstd
     assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_INVALID_ARG
-    r.rows = 0                                                              # rows == 0 is a no-op
+    r.op, r.rstd = C.WVAR_BWD, None                                          # two-output ops need dx2
+    assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_INVALID_ARG
+    r.op = C.PEARSON_BWD
+    assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_INVALID_ARG
+    r.op = 11                                                               # past the last backward op
+    assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.ERR_INVALID_ARG
+    r.op, r.rows = C.RMSNORM_BWD, 0                                         # rows == 0 is a no-op
     assert lib.credit_run_bwd(ctypes.byref(r), None, None) == C.OK
     p = C.PlanT()
     assert lib.credit_plan_bwd(C.SOFTMAX, 4, 16, C.F32, ctypes.byref(p)) == C.ERR_INVALID_ARG
