@@ -1,15 +1,26 @@
-// credit_bwd.cu -- input gradients of softmax, LayerNorm and RMSNorm
-// (the backward members of the reduction-reuse workload suite, Sec. IV-A).
+// credit_bwd.cu -- gradients of reduction-reuse row ops (the backward
+// members of the workload suite, Sec. IV-A).
 //
-// Every row has two arrays, a (softmax: the forward output y; norms: the
-// forward input x) and the upstream gradient dy.  With g = dy * gamma:
-//   softmax    S0 = sum y dy                     dx = y (dy - S0)
-//   layernorm  xh = (x - mean) rstd, S0 = sum g, S1 = sum g xh
+// Every row has two arrays, a and dy, and one stage (L = 1) of reductions
+// followed by an elementwise pass over the same two arrays (Eq. 1).  With
+// g = dy * gamma:
+//   softmax    a = y, S0 = sum y dy                       dx = y (dy - S0)
+//   layernorm  a = x, xh = (x - mean) rstd, S0 = sum g, S1 = sum g xh
 //              dx = rstd (g - S0 / N - xh S1 / N)
-//   rmsnorm    xh = x rstd, S1 = sum g xh        dx = rstd (g - xh S1 / N)
-// i.e. one reduction stage (L = 1) of q = 1 or 2 plain sums, then an
-// elementwise pass over the same two arrays (Eq. 1).
-//
+//   rmsnorm    a = x, xh = x rstd, S1 = sum g xh          dx = rstd (g - xh S1 / N)
+// (q = 1 or 2 plain sums); from logits z, with y = softmax(z) recomputed:
+//   softmax    online (m, S = sum e^(z-m), T = sum e^(z-m) dy)
+//              dz = e^(z-m) / S (dy - T / S)
+//   xent       online (m, S), T = sum t (dy holds the targets t)
+//              dz = w (e^(z-m) / S T - t)
+// (q = 3, merged with rescaling); and of two-input statistics, with two
+// outputs dx, dx2 and moments about the row's first elements kx, ky:
+//   wvar       a = x, dy = w: sums of w, w u, w u^2 (u = x - kx)
+//              dx = g 2 w (x - mu) / W, dx2 = g ((x - mu)^2 - v) / W
+//   pearson    a = x, dy = y: sums of u, v, u^2, v^2, u v (v = y - ky)
+//              dx = g ((y - yb) / sqrt(Sxx Syy) - r (x - xb) / Sxx), dx2 symmetric
+// (q = 3 or 5 plain sums).
+
 // Paths:
 //   k_bwd_staged   ONE_CTA (P = 1) and CLUSTER (P = 2..16).  A persistent
 //                  cluster walks rows cl, cl + ncl, ...  Each CTA stages its
@@ -30,7 +41,8 @@
 //                  device workspace between two launches (G = 1: one fused
 //                  kernel, the reread mostly from L2).  Any alignment.
 //
-// Exchange slots: [parity = row iteration % 2][16 sources][4 floats].  A CTA
+// Exchange slots: [parity = row iteration % 2][16 sources][4 floats] ([8
+// floats] for the two-input statistics).  A CTA
 // pushes its partial for iteration t + 2 into parity t % 2 only after its
 // exchange of iteration t + 1 completed, which needed every peer's push of
 // t + 1, which each peer made after its own combine of iteration t had read
