@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
             L.oracle_pearson_row.restype = d
             L.oracle_pearson_row.argtypes = [vp, vp, i64]
             L.oracle_pearson_bwd_row.argtypes = [vp, vp, i64, d, vp, vp]
+            L.oracle_quant_int8_row.restype = ctypes.c_float
+            L.oracle_quant_int8_row.argtypes = [vp, i64, vp]
             L.oracle_run_bwd.restype = i32
             L.oracle_run_bwd.argtypes = [i32, i32, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp, i32]
             L.oracle_max_threads.restype = i32
@@ -315,6 +317,16 @@ def run_bwd(op: int, dtype: int, a_raw, dy_raw, rows: int, cols: int, *, gamma=N
     if rc != 0:
         raise ValueError("oracle_run_bwd rejected its arguments")
     return dx64, (None if enc is None else enc[:, :cols])
+
+
+def quant_int8(x):
+    """Row-wise int8 quantisation of FP32 rows: (codes int8, scales float32)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    q = np.empty(x.shape, dtype=np.int8)
+    s = np.empty(x.shape[0], dtype=np.float32)
+    for r in range(x.shape[0]):
+        s[r] = lib().oracle_quant_int8_row(_ptr(x[r]), x.shape[1], _ptr(q[r]))
+    return q, s
 
 
 def max_threads() -> int:

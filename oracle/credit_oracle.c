@@ -344,6 +344,28 @@ void oracle_pearson_bwd_row(const double *x, const double *y, int64_t n, double 
     }
 }
 
+/* Row-wise int8 quantisation (the "row-wise int8 quantization" workload */
+/* of Sec. IV-A): s = amax_i |x_i| / 127 (1 for an all-zero row) and     */
+/* q_i = the integer nearest to x_i / s (ties to even), clamped to       */
+/* [-127, 127].  The quotients are taken in FP32 as a kernel takes them: */
+/* s = fl32(amax / 127) and fl32(x_i / s), each computed in double and   */
+/* rounded once to FP32, which equals the correctly rounded FP32         */
+/* quotient (53 >= 2 * 24 + 2 bits, so the double rounding is harmless). */
+/* Returns s; q receives the codes.                                      */
+float oracle_quant_int8_row(const float *x, int64_t n, int8_t *q) {
+    double amax = 0.0;
+    for (int64_t i = 0; i < n; ++i) { double a = fabs((double)x[i]); amax = a > amax ? a : amax; }
+    float s = amax > 0.0 ? (float)(amax / 127.0) : 1.0f;
+    for (int64_t i = 0; i < n; ++i) {
+        float r = (float)((double)x[i] / (double)s);
+        double k = nearbyint((double)r);   /* default rounding mode: ties to even */
+        if (k > 127.0) k = 127.0;
+        if (k < -127.0) k = -127.0;
+        q[i] = (int8_t)k;
+    }
+    return s;
+}
+
 /* ------------------------------------------------------------------ */
 /* Batch driver: decode -> op -> (exact doubles, encoded output)        */
 /* ------------------------------------------------------------------ */
