@@ -19,7 +19,10 @@ cpu_baseline  the FP64 oracle on a bounded sample of the same shapes, all
 
 Also reported: speedup of the chosen plans over the best non-DSMEM plan
 (one-CTA staging or two-pass reread) on the same shapes, and the cost model's
-pick accuracy on these shapes (pick within 5% of the measured best candidate).
+pick accuracy on these shapes (pick within 5% of the measured best candidate);
+`backward`: the gradient ops (softmax, LayerNorm, RMSNorm, softmax from
+logits, cross entropy) over 4096 rows x {16K, 64K, 128K, 256K} FP32, every
+candidate plan timed beside the planner's pick (outside the timed step).
 
 --impl reference  times the FP64 CPU oracle (the reference arm of this
            project) on a bounded sample of the same workload.
