@@ -1,6 +1,6 @@
 """Helpers shared by the parity tests: inputs, oracle references, error bounds.
 
-Error bounds (the readings are listed in the design doc):
+Error bounds (readings of the paper's tolerances):
   FP32 output   softmax: max_i |y - y*| / |y*| <= 1e-5
                 logsumexp, layernorm, rmsnorm: max_i |y - y*| / max(|y*|, 1) <= 1e-5
   BF16 output   |y - y*| <= ulp(y*) + e32(y*): one BF16 ulp of y*, ulp =

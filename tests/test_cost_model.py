@@ -71,7 +71,7 @@ def test_remote_store_time_not_multiplied_by_P():
 
 def test_capacity_and_protocol_equations():
     S_max = 232448  # GB300 opt-in shared memory per block
-    # FP32 64K row (256 KiB): illegal on one CTA, legal on two (SURVEY capacity table)
+    # FP32 64K row (256 KiB): illegal on one CTA, legal on two (Eq. 3 capacity)
     assert not CM.capacity_ok(65536, 1, 4, 2304, S_max)
     assert CM.capacity_ok(65536, 2, 4, 2304, S_max)
     # FP32 512K row needs P = 16
