@@ -143,3 +143,27 @@ def test_struct_layouts_match_a_c_compiler(tmp_path):
         py = structs[cname]
         got = ctypes.sizeof(py) if field == "size" else getattr(py, field).offset
         assert got == int(val), (cname, field, got, val)
+
+
+def test_binding_constants_match_the_header_enums():
+    """Every enum value the binding hard-codes is the header's."""
+    text = open(os.path.join(ROOT, "include", "credit.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    vals = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(CREDIT_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    expect = {
+        "CREDIT_F32": C.F32, "CREDIT_BF16": C.BF16, "CREDIT_FP8_E4M3": C.FP8_E4M3,
+        "CREDIT_OP_SOFTMAX": C.SOFTMAX, "CREDIT_OP_LOGSUMEXP": C.LOGSUMEXP, "CREDIT_OP_LAYERNORM": C.LAYERNORM,
+        "CREDIT_OP_RMSNORM": C.RMSNORM, "CREDIT_PATH_AUTO": C.PATH_AUTO, "CREDIT_PATH_ONE_CTA": C.PATH_ONE_CTA,
+        "CREDIT_PATH_TWO_PASS": C.PATH_TWO_PASS, "CREDIT_PATH_CLUSTER": C.PATH_CLUSTER,
+        "CREDIT_RETAIN_AUTO": C.RETAIN_AUTO, "CREDIT_RETAIN_SMEM": C.RETAIN_SMEM, "CREDIT_RETAIN_TMEM": C.RETAIN_TMEM,
+        "CREDIT_OK": C.OK, "CREDIT_ERR_INVALID_ARG": C.ERR_INVALID_ARG, "CREDIT_ERR_UNSUPPORTED": C.ERR_UNSUPPORTED,
+        "CREDIT_ERR_CUDA": C.ERR_CUDA, "CREDIT_ERR_TIMEOUT": C.ERR_TIMEOUT,
+        "CREDIT_ERR_NOT_INITIALIZED": C.ERR_NOT_INITIALIZED, "CREDIT_ERR_CAPTURE": C.ERR_CAPTURE,
+        "CREDIT_ERR_IO": C.ERR_IO, "CREDIT_OP_SOFTMAX_BWD": C.SOFTMAX_BWD,
+        "CREDIT_OP_LAYERNORM_BWD": C.LAYERNORM_BWD, "CREDIT_OP_RMSNORM_BWD": C.RMSNORM_BWD,
+        "CREDIT_OP_SOFTMAX_LOGITS_BWD": C.SOFTMAX_LOGITS_BWD, "CREDIT_OP_XENT_BWD": C.XENT_BWD,
+        "CREDIT_OP_WVAR_BWD": C.WVAR_BWD, "CREDIT_OP_PEARSON_BWD": C.PEARSON_BWD,
+    }
+    for name, v in expect.items():
+        assert vals.get(name) == v, (name, vals.get(name), v)
+    assert C.MLP_FEATURES == int(re.search(r"#define CREDIT_MLP_FEATURES (\d+)", text).group(1))
