@@ -119,3 +119,15 @@ def test_profitability_pairs():
 
 def test_algorithmic_bytes_count_one_read_and_one_write():
     assert bench.algorithmic_bytes(4096, 524288, C.LAYERNORM) == 4096 * 524288 * 4 * 2
+
+
+def test_committed_traffic_record_matches_the_kernel_sources():
+    """profiles/traffic.json is keyed by a hash of the row-kernel sources; the bench reports its DRAM bytes as
+    roofline.traffic only while the hash matches, so an edit to the kernels without a new capture shows here."""
+    import json
+    recs = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["records"]
+    assert recs and all(r["source_sha"] == bench.source_sha() for r in recs)
+    r = recs[0]
+    assert r["dram_bytes"] == r["dram_read"] + r["dram_write"]
+    assert 0.9 < r["dram_bytes"] / r["algorithmic_bytes"] < 1.5
+    assert bench.traffic_record(r["kernel"], r["op"], r["cols"]) is not None
