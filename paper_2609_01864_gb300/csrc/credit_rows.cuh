@@ -75,11 +75,13 @@ struct RowSlice {
     long long g_lo, g_hi;  // this CTA's groups
 };
 
-// floor(G * k / P) for 0 <= k <= P <= 16: 32-bit unsigned arithmetic when the
-// product fits (the common case; exact, so identical to the 64-bit form).
+// floor(G * k / P) for 0 <= k <= P (P = cluster size, or CTAs per row of the
+// split two-pass path, up to 4096): 32-bit unsigned arithmetic when G * P, and
+// so every G * k, fits in 32 bits (the common case; exact, so identical to
+// the 64-bit form), else 64-bit.
 __host__ __device__ __forceinline__ long long group_split(long long G, int k, int P) {
-    if (G <= 0x0FFFFFFFLL) return static_cast<long long>(static_cast<uint32_t>(G) * static_cast<uint32_t>(k) /
-                                                         static_cast<uint32_t>(P));
+    if (static_cast<unsigned long long>(G) * static_cast<unsigned>(P) <= 0xFFFFFFFFull)
+        return static_cast<long long>(static_cast<uint32_t>(G) * static_cast<uint32_t>(k) / static_cast<uint32_t>(P));
     return G * k / P;
 }
 
