@@ -14,12 +14,13 @@
 //   xent       online (m, S), T = sum t (dy holds the targets t)
 //              dz = w (e^(z-m) / S T - t)
 // (q = 3, merged with rescaling); and of two-input statistics, with two
-// outputs dx, dx2 and moments about the row's first elements kx, ky:
-//   wvar       a = x, dy = w: sums of w, w u, w u^2 (u = x - kx)
-//              dx = g 2 w (x - mu) / W, dx2 = g ((x - mu)^2 - v) / W
-//   pearson    a = x, dy = y: sums of u, v, u^2, v^2, u v (v = y - ky)
+// outputs dx, dx2 and centred moments merged with Chan's formulas:
+//   wvar       a = x, dy = w: (W, mu, M2), W = sum w, M2 = sum w (x - mu)^2
+//              dx = g 2 w (x - mu) / W, dx2 = g ((x - mu)^2 - v) / W, v = M2 / W
+//   pearson    a = x, dy = y: (n, xb, yb, Sxx, Syy, Sxy) centred co-moments
 //              dx = g ((y - yb) / sqrt(Sxx Syy) - r (x - xb) / Sxx), dx2 symmetric
-// (q = 3 or 5 plain sums).
+// (q = 3 or 6; each thread first sums about its own first elements, then
+// converts once to the centred state before the merges).
 
 // Paths:
 //   k_bwd_staged   ONE_CTA (P = 1) and CLUSTER (P = 2..16).  A persistent
@@ -71,7 +72,7 @@ template <int OP> constexpr bool kLogits = OP == BOP_SMLOGITS || OP == BOP_XENT;
 template <int OP> constexpr bool kNorm = OP == BOP_LN || OP == BOP_RMS;          // gamma, saved statistics
 template <int OP> constexpr bool kPair = OP == BOP_WVAR || OP == BOP_PEARSON;    // two outputs, shifted sums
 template <int OP> constexpr int kKind = kLogits<OP> ? 1 : (kPair<OP> ? 2 : 0);
-template <int OP> constexpr int kPairSums = OP == BOP_WVAR ? 3 : 5;               // sums of the pair ops
+template <int OP> constexpr int kPairState = OP == BOP_WVAR ? 3 : 6;              // centred state of the pair ops
 
 constexpr int kBwdThreads = 512;
 constexpr int kBwdCtrl = 1792;             // control area before the row buffers (bytes)
@@ -104,35 +105,10 @@ struct Coef {
 template <int OP>
 struct BwdRow {
     float mean = 0.0f, rstd = 1.0f, w = 1.0f;
-    float kx = 0.0f, ky = 0.0f;  // pair ops: the shifts (the row's first elements of a and dy)
     __device__ __forceinline__ void load(const BwdArgs &p, long long row) {
         if constexpr (OP == BOP_LN) mean = p.mean[row];
         if constexpr (kNorm<OP>) rstd = p.rstd[row];
         if constexpr (OP == BOP_XENT || kPair<OP>) w = p.scale ? p.scale[row] : 1.0f;
-    }
-    template <int DT>
-    __device__ __forceinline__ void load_shifts(const BwdArgs &p, long long row) {
-        if constexpr (kPair<OP>) {
-            const size_t off = static_cast<size_t>(row * p.ld) * Fmt<DT>::size;
-            kx = decode_one<DT>(p.a + off, 1.0f);
-            if constexpr (OP == BOP_PEARSON) ky = decode_one<DT>(p.dy + off, 1.0f);
-        }
-    }
-    // pair ops: add element (a, d) to the shifted sums s[0..kPairSums)
-    __device__ __forceinline__ void acc_pair(float a, float d, float *s) const {
-        if constexpr (OP == BOP_WVAR) {  // d is the weight
-            const float u = a - kx, wu = d * u;
-            s[0] += d;
-            s[1] += wu;
-            s[2] = fmaf(wu, u, s[2]);
-        } else if constexpr (OP == BOP_PEARSON) {
-            const float u = a - kx, v = d - ky;
-            s[0] += u;
-            s[1] += v;
-            s[2] = fmaf(u, u, s[2]);
-            s[3] = fmaf(v, v, s[3]);
-            s[4] = fmaf(u, v, s[4]);
-        }
     }
     // pair ops: both gradients of element (a, d)
     __device__ __forceinline__ void dx_pair(float a, float d, const Coef &k, float &o1, float &o2) const {
@@ -242,58 +218,161 @@ struct BwdState<OP, 1> {
     }
 };
 
-// Pair ops: sums of the row about shifts taken from its first elements
-// (weighted variance: sum w, sum w u, sum w u^2 with u = x - kx; Pearson:
-// sum u, sum v, sum u^2, sum v^2, sum u v with v = y - ky), so that the
-// centred moments lose little to cancellation.  Plain sums: merged by addition.
+// Pair ops, centred state c[] (weighted variance: W = sum w, mu, M2 = sum w
+// (x - mu)^2; Pearson: n, xb, yb and the centred co-moments Sxx, Syy, Sxy).
+// c[0] == 0 is the empty state.  Chan's merge of b into a: with n = na + nb
+// and the mean differences d = mean_b - mean_a,
+//   mean += d nb / n,   S += S_b + d d' na nb / n
+// (d' = d of the other variable for the cross moment).  merge(a, b) is the
+// same arithmetic whichever side calls it, so the shuffle trees below give
+// one state in every lane.
+template <int OP>
+__device__ __forceinline__ void pair_merge(float (&a)[kPairState<OP>], const float (&b)[kPairState<OP>]) {
+    constexpr int NS = kPairState<OP>;
+    if (b[0] == 0.0f) return;
+    if (a[0] == 0.0f) {
+#pragma unroll
+        for (int j = 0; j < NS; ++j) a[j] = b[j];
+        return;
+    }
+    const float n = a[0] + b[0];
+    const float wb = b[0] / n, wab = a[0] * wb;  // nb / n and na nb / n
+    if constexpr (OP == BOP_WVAR) {
+        const float d = b[1] - a[1];
+        a[1] = fmaf(d, wb, a[1]);
+        a[2] = a[2] + b[2] + d * d * wab;
+    } else {
+        const float dx = b[1] - a[1], dy = b[2] - a[2];
+        a[1] = fmaf(dx, wb, a[1]);
+        a[2] = fmaf(dy, wb, a[2]);
+        a[3] = a[3] + b[3] + dx * dx * wab;
+        a[4] = a[4] + b[4] + dy * dy * wab;
+        a[5] = a[5] + b[5] + dx * dy * wab;
+    }
+    a[0] = n;
+}
+
+// Pair ops, per thread: sums about the thread's first element of each array
+// (kx, ky), so the second moments lose little to cancellation, converted once
+// by finish() to the centred state (the scheme of the forward LayerNorm
+// statistics).  Weighted variance: W, sum w u, sum w u^2 (u = x - kx);
+// Pearson: n, sum u, sum v, sum u^2, sum v^2, sum u v (v = y - ky).
 template <int OP>
 struct BwdState<OP, 2> {
-    float s[kPairSums<OP>] = {};
+    float n = 0.0f, kx = 0.0f, ky = 0.0f;
+    float s[5] = {};
+    bool has = false;
+    __device__ __forceinline__ void acc(float a, float d) {
+        if (!has) {
+            kx = a;
+            ky = d;
+            has = true;
+        }
+        if constexpr (OP == BOP_WVAR) {  // d is the weight
+            const float u = a - kx, wu = d * u;
+            n += d;
+            s[0] += wu;
+            s[1] = fmaf(wu, u, s[1]);
+        } else {
+            const float u = a - kx, v = d - ky;
+            n += 1.0f;
+            s[0] += u;
+            s[1] += v;
+            s[2] = fmaf(u, u, s[2]);
+            s[3] = fmaf(v, v, s[3]);
+            s[4] = fmaf(u, v, s[4]);
+        }
+    }
     template <int V>
-    __device__ __forceinline__ void add(const BwdRow<OP> &R, const float (&fa)[V], const float (&fd)[V],
+    __device__ __forceinline__ void add(const BwdRow<OP> &, const float (&fa)[V], const float (&fd)[V],
                                         const float (&)[V]) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) R.acc_pair(fa[v], fd[v], s);
+        for (int v = 0; v < V; ++v) acc(fa[v], fd[v]);
     }
-    __device__ __forceinline__ void add1(const BwdRow<OP> &R, float a, float d, float) { R.acc_pair(a, d, s); }
+    __device__ __forceinline__ void add1(const BwdRow<OP> &, float a, float d, float) { acc(a, d); }
+    __device__ __forceinline__ void finish(float (&c)[kPairState<OP>]) const {
+#pragma unroll
+        for (int j = 0; j < kPairState<OP>; ++j) c[j] = 0.0f;
+        if (n == 0.0f) return;
+        if constexpr (OP == BOP_WVAR) {
+            const float q = s[0] / n;
+            c[0] = n;
+            c[1] = kx + q;
+            c[2] = fmaxf(fmaf(-s[0], q, s[1]), 0.0f);
+        } else {
+            const float qx = s[0] / n, qy = s[1] / n;
+            c[0] = n;
+            c[1] = kx + qx;
+            c[2] = ky + qy;
+            c[3] = fmaxf(fmaf(-s[0], qx, s[2]), 0.0f);
+            c[4] = fmaxf(fmaf(-s[1], qy, s[3]), 0.0f);
+            c[5] = fmaf(-s[0], qy, s[4]);
+        }
+    }
 };
 
-// Coefficients of the pair ops from the row totals (see BwdRow::dx_pair).
+// Shuffle-tree merge of a pair state over the 32 lanes of a warp: at every
+// level both partners compute merge(lower lane, upper lane), so all lanes end
+// with the same state.
 template <int OP>
-__device__ __forceinline__ Coef pair_coeffs(const float *t, long long N, const BwdRow<OP> &R) {
-    if constexpr (OP == BOP_WVAR) {
-        const float W = t[0], inv = 1.0f / W, m1 = t[1] * inv;
-        return {R.kx + m1, t[2] * inv - m1 * m1, R.w * inv, 0.0f, 0.0f};
-    } else {
-        const float n = static_cast<float>(N), inv_n = 1.0f / n;
-        const float sxx = t[2] - t[0] * t[0] * inv_n, syy = t[3] - t[1] * t[1] * inv_n;
-        const float sxy = t[4] - t[0] * t[1] * inv_n;
-        const float inv_den = 1.0f / sqrtf(sxx * syy), r = sxy * inv_den;
-        return {R.kx + t[0] * inv_n, R.ky + t[1] * inv_n, R.w * inv_den, R.w * r / sxx, R.w * r / syy};
+__device__ __forceinline__ void warp_merge_pair(float (&c)[kPairState<OP>]) {
+    constexpr int NS = kPairState<OP>;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float oth[NS];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) oth[j] = __shfl_xor_sync(0xffffffffu, c[j], o);
+        if (lane & o) {
+            pair_merge<OP>(oth, c);
+#pragma unroll
+            for (int j = 0; j < NS; ++j) c[j] = oth[j];
+        } else {
+            pair_merge<OP>(c, oth);
+        }
     }
 }
 
-// Deterministic block sum of NS floats through red (>= 16 NS + NS floats).
-// Every thread returns the totals in out.  Contains two __syncthreads.
-template <int NS>
-__device__ __forceinline__ void block_sum_n(const float (&v)[NS], float *red, float (&out)[NS]) {
+// Deterministic block merge of the threads' pair states through red (>= 17 NS
+// floats): a shuffle tree per warp, then one over the warps' states in warp 0.
+// Every thread returns the CTA's state in out.  Contains two __syncthreads.
+template <int OP>
+__device__ __forceinline__ void block_merge_pair(const BwdState<OP, 2> &st, float *red,
+                                                 float (&out)[kPairState<OP>]) {
+    constexpr int NS = kPairState<OP>;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float c[NS];
+    st.finish(c);
+    warp_merge_pair<OP>(c);
+    if (lane == 0) {
 #pragma unroll
-    for (int j = 0; j < NS; ++j) {
-        const float t = warp_sum(v[j]);
-        if (lane == 0) red[NS * wid + j] = t;
+        for (int j = 0; j < NS; ++j) red[NS * wid + j] = c[j];
     }
     __syncthreads();
     if (wid == 0) {
 #pragma unroll
-        for (int j = 0; j < NS; ++j) {
-            const float t = warp_sum(lane < nw ? red[NS * lane + j] : 0.0f);
-            if (lane == 0) red[NS * 16 + j] = t;
+        for (int j = 0; j < NS; ++j) c[j] = lane < nw ? red[NS * lane + j] : 0.0f;
+        warp_merge_pair<OP>(c);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < NS; ++j) red[NS * 16 + j] = c[j];
         }
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < NS; ++j) out[j] = red[NS * 16 + j];
+}
+
+// Coefficients of the pair ops from the row's centred state (see BwdRow::dx_pair).
+template <int OP>
+__device__ __forceinline__ Coef pair_coeffs(const float (&t)[kPairState<OP>], const BwdRow<OP> &R) {
+    if constexpr (OP == BOP_WVAR) {
+        const float inv = 1.0f / t[0];
+        return {t[1], t[2] * inv, R.w * inv, 0.0f, 0.0f};
+    } else {
+        const float inv_den = 1.0f / (sqrtf(t[3]) * sqrtf(t[4])), r = t[5] * inv_den;
+        return {t[1], t[2], R.w * inv_den, R.w * r / t[3], R.w * r / t[4]};
+    }
 }
 
 // Push all-gather of up to 8 floats per CTA: slots of 8 floats, [par][16][8],
@@ -537,8 +616,6 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
         }
         BwdRow<OP> R;
         R.load(p, row);
-    R.template load_shifts<DT>(p, row);
-        R.template load_shifts<DT>(p, row);
         const unsigned char *da = data + static_cast<size_t>(b) * 2 * arr, *dd = da + arr;
         const size_t row_off = static_cast<size_t>(row * p.ld) * isz;
 
@@ -574,9 +651,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
         }
         Coef kc;
         if constexpr (kPair<OP>) {
-            constexpr int NS = kPairSums<OP>;
+            constexpr int NS = kPairState<OP>;
             float tot[NS];
-            block_sum_n<NS>(st.s, red, tot);
+            block_merge_pair<OP>(st, red, tot);
             if (P > 1) {
                 float v8[8] = {};
 #pragma unroll
@@ -585,11 +662,14 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
                                                  static_cast<uint32_t>((it >> 1) & 1), P, c, T, p.err);
 #pragma unroll
                 for (int j = 0; j < NS; ++j) tot[j] = 0.0f;
-                for (int q = 0; q < P; ++q)  // fixed order: the same totals in every CTA
+                for (int q = 0; q < P; ++q) {  // Chan merges in the fixed order c = 0..P-1: one state in every CTA
+                    float cq[NS];
 #pragma unroll
-                    for (int j = 0; j < NS; ++j) tot[j] += sl[8 * q + j];
+                    for (int j = 0; j < NS; ++j) cq[j] = sl[8 * q + j];
+                    pair_merge<OP>(tot, cq);
+                }
             }
-            kc = pair_coeffs<OP>(tot, N, R);
+            kc = pair_coeffs<OP>(tot, R);
         } else if constexpr (kLogits<OP>) {
             float4 tot = block_reduce_logits<OP>(st, red);
             if (P > 1) {
@@ -787,14 +867,13 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_fused(const BwdArgs p) {
     const long long row = p.row0 + blockIdx.x;
     BwdRow<OP> R;
     R.load(p, row);
-    R.template load_shifts<DT>(p, row);
     const BwdSpan s = bwd_span<DT>(p, row, 0, 1);
     const BwdState<OP> t = bwd_sums<OP, DT>(p, row, R, s);
     Coef kc;
     if constexpr (kPair<OP>) {
-        float tot[kPairSums<OP>];
-        block_sum_n<kPairSums<OP>>(t.s, red, tot);
-        kc = pair_coeffs<OP>(tot, p.cols, R);
+        float tot[kPairState<OP>];
+        block_merge_pair<OP>(t, red, tot);
+        kc = pair_coeffs<OP>(tot, R);
     } else if constexpr (kLogits<OP>) {
         const float4 tot = block_reduce_logits<OP>(t, red);
         kc = logit_coeffs<OP>(tot.x, tot.y, tot.z);
@@ -814,15 +893,14 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_stats(const BwdArgs p) {
     const long long lr = blockIdx.x / G, row = p.row0 + lr;
     BwdRow<OP> R;
     R.load(p, row);
-    R.template load_shifts<DT>(p, row);
     const BwdSpan s = bwd_span<DT>(p, row, j, G);
     const BwdState<OP> t = bwd_sums<OP, DT>(p, row, R, s);
     if constexpr (kPair<OP>) {
-        float tot[kPairSums<OP>];
-        block_sum_n<kPairSums<OP>>(t.s, red, tot);
+        float tot[kPairState<OP>];
+        block_merge_pair<OP>(t, red, tot);
         if (threadIdx.x == 0) {
 #pragma unroll
-            for (int q = 0; q < kPairSums<OP>; ++q) p.ws[(lr * G + j) * 8 + q] = tot[q];
+            for (int q = 0; q < kPairState<OP>; ++q) p.ws[(lr * G + j) * 8 + q] = tot[q];
         }
     } else if constexpr (kLogits<OP>) {
         const float4 tot = block_reduce_logits<OP>(t, red);
@@ -847,15 +925,16 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_tp_apply(const BwdArgs p) {
     const long long lr = blockIdx.x / G, row = p.row0 + lr;
     BwdRow<OP> R;
     R.load(p, row);
-    R.template load_shifts<DT>(p, row);
     Coef kc;
     if constexpr (kPair<OP>) {
-        float tot[kPairSums<OP>] = {};
-        for (int q = 0; q < G; ++q) {  // fixed order
+        float tot[kPairState<OP>] = {};
+        for (int q = 0; q < G; ++q) {  // Chan merges in the fixed order j = 0..G-1
+            float cq[kPairState<OP>];
 #pragma unroll
-            for (int i = 0; i < kPairSums<OP>; ++i) tot[i] += p.ws[(lr * G + q) * 8 + i];
+            for (int i = 0; i < kPairState<OP>; ++i) cq[i] = p.ws[(lr * G + q) * 8 + i];
+            pair_merge<OP>(tot, cq);
         }
-        kc = pair_coeffs<OP>(tot, p.cols, R);
+        kc = pair_coeffs<OP>(tot, R);
     } else if constexpr (kLogits<OP>) {
         BwdState<OP> all;
         for (int q = 0; q < G; ++q)
