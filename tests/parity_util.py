@@ -3,12 +3,16 @@
 Error bounds (readings of the paper's tolerances):
   FP32 output   softmax: max_i |y - y*| / |y*| <= 1e-5
                 logsumexp, layernorm, rmsnorm: max_i |y - y*| / max(|y*|, 1) <= 1e-5
-  BF16 output   |y - y*| <= ulp(y*) + e32(y*): one BF16 ulp of y*, ulp =
-                2^(floor(log2|y*|) - 7) (2^-133 below the normal range), on
-                top of the FP32 bound e32 (1e-5 |y*| for softmax, 1e-5
-                max(|y*|, 1) otherwise).  Without e32 the bound cannot be met
-                with FP32 statistics where the normalised output cancels to
-                |y*| << 1 (LayerNorm with beta).
+  BF16 output   |y - y*| <= ulp(y*) + e_terms: one BF16 ulp of y*, ulp =
+                2^(floor(log2|y*|) - 7) (2^-133 below the normal range).
+                softmax, rmsnorm: e_terms = 0 (a product of positive
+                factors: the FP32 result is within a few 2^-24 |y*|, and its
+                rounding to BF16 adds at most half an ulp).
+                layernorm: y* = (x - mu) r g + b can cancel to |y*| << 1, where
+                one BF16 ulp is below the rounding error of any FP32
+                evaluation of the formula; e_terms = 16 * 2^-24 * ((|x - mu|
+                + |mu| + sigma) r |g| + |b|): a few FP32 roundings of each
+                term, the |mu| + sigma part for the FP32 error of the mean.
   FP8 output    |q * s - y*| <= 2^(max(floor(log2(|y*| / s)), -6) - 3) * s, one
                 E4M3 quantum at the scaled value, and s within 1e-5 (relative)
                 of amax|y*| / 448
@@ -64,8 +68,33 @@ def to64(t: torch.Tensor) -> np.ndarray:
     return t.detach().cpu().to(torch.float64).numpy()
 
 
-def error_metric(op: int, out_dtype: int, y: np.ndarray, ref: np.ndarray, out_scale=None) -> float:
-    """Error in units of the bound (<= 1.0 passes)."""
+LN_TERM_ULPS = 16.0
+
+
+def ln_terms(x64: np.ndarray, gamma=None, beta=None, eps=None) -> np.ndarray:
+    """Per-element magnitude (|x - mu| + |mu| + sigma) r |g| + |b| of the LayerNorm formula's terms, from the
+    FP64 row statistics of the decoded input x64 (rows x cols)."""
+    eps = 1e-5 if eps is None or eps < 0 else eps
+    mu = x64.mean(axis=1, keepdims=True)
+    var = ((x64 - mu) ** 2).mean(axis=1, keepdims=True)
+    r = 1.0 / np.sqrt(var + eps)
+    g = np.ones(x64.shape[1]) if gamma is None else np.abs(np.asarray(gamma, dtype=np.float64))
+    b = np.zeros(x64.shape[1]) if beta is None else np.abs(np.asarray(beta, dtype=np.float64))
+    return (np.abs(x64 - mu) + np.abs(mu) + np.sqrt(var)) * r * g[None, :] + b[None, :]
+
+
+def decoded(x_cpu: torch.Tensor, scale=None) -> np.ndarray:
+    """The stored input as exact FP64 values (E4M3 codes times their row scale)."""
+    x = to64(x_cpu)
+    if scale is not None:
+        x = x * np.asarray(scale.cpu(), dtype=np.float64).reshape(-1, 1)
+    return x
+
+
+def error_metric(op: int, out_dtype: int, y: np.ndarray, ref: np.ndarray, out_scale=None, *, x64=None, gamma=None,
+                 beta=None, eps=None) -> float:
+    """Error in units of the bound (<= 1.0 passes).  LayerNorm with BF16 output needs x64 (the decoded input)
+    and its gamma / beta / eps for the term bound."""
     if op == C.LOGSUMEXP or out_dtype == C.F32:
         if op == C.SOFTMAX:
             den = np.abs(ref)
@@ -77,8 +106,12 @@ def error_metric(op: int, out_dtype: int, y: np.ndarray, ref: np.ndarray, out_sc
         a = np.abs(ref)
         e = np.floor(np.log2(np.where(a > 0, a, 1.0)))
         ulp = np.where(a >= 2.0 ** -126, np.exp2(e - 7), 2.0 ** -133)
-        e32 = F32_TOL * (a if op == C.SOFTMAX else np.maximum(a, 1.0))
-        return float(np.max(np.abs(y - ref) / (ulp + e32))) if y.size else 0.0
+        extra = 0.0
+        if op == C.LAYERNORM:
+            if x64 is None:
+                raise ValueError("LayerNorm BF16 bound needs the decoded input")
+            extra = LN_TERM_ULPS * 2.0 ** -24 * ln_terms(x64, gamma, beta, eps)
+        return float(np.max(np.abs(y - ref) / (ulp + extra))) if y.size else 0.0
     # FP8: y holds decoded codes (not yet scaled)
     s = np.asarray(out_scale, dtype=np.float64).reshape(-1, 1)
     t = np.abs(ref) / s
@@ -134,7 +167,9 @@ def check_against_oracle(op, x_cpu, scale, *, out_dtype=None, plan=None, gamma=N
     torch.cuda.synchronize()
     assert C.device_error() == C.OK
     ref = reference(op, in_dtype, x_cpu, scale, gamma, beta, None if eps < 0 else eps)
-    m = error_metric(op, out_dtype, to64(out), ref, None if osc is None else osc.cpu().numpy())
+    m = error_metric(op, out_dtype, to64(out), ref, None if osc is None else osc.cpu().numpy(),
+                     x64=decoded(x_cpu, scale) if op == C.LAYERNORM else None, gamma=gamma, beta=beta,
+                     eps=None if eps < 0 else eps)
     assert m <= limit, f"error {m:.3f} x bound (op={op}, in={in_dtype}, out={out_dtype}, plan={plan})"
     return m, out
 
@@ -255,13 +290,10 @@ def pair_reference(op, x, d, g, cols):
 
 def pair_error(op, dtype, out1, out2, ref1, ref2, x, d, g, cols):
     """Largest error of the two gradients in units of their bounds (<= 1.0 passes): 1e-5 of the row's
-    largest term of each formula, times the conditioning kappa of the shifted moments, plus one BF16 ulp
-    of the exact value for BF16.  Weighted variance: dx terms g 2 w (x - mu) / W, dw terms g (x - mu)^2 / W
-    and g v / W; Pearson: g (y - yb) / sqrt(Sxx Syy) and g r (x - xb) / Sxx (dx), symmetrically for dy.
-    The kernels accumulate the second moments about the row's first elements K, so the FP32 error of a
-    centred moment such as Sxx is a small multiple of 2^-24 sum (x - K)^2 = 2^-24 (Sxx + N (xb - K)^2):
-    kappa = sum (x - K)^2 / Sxx (the larger of x and y; weighted for the variance), 1 + chi^2_1 for a
-    typical K and large when K is an outlier of its row."""
+    largest term of each formula, plus one BF16 ulp of the exact value for BF16.  Weighted variance: dx terms
+    g 2 w (x - mu) / W, dw terms g (x - mu)^2 / W and g v / W; Pearson: g (y - yb) / sqrt(Sxx Syy) and
+    g r (x - xb) / Sxx (dx), symmetrically for dy.  The bound depends only on the exact values of the terms
+    (FP64, from the inputs), not on how a kernel accumulates the moments."""
     x64, d64 = to64(x)[:, :cols], to64(d)[:, :cols]
     gg = np.abs(g.cpu().double().numpy())
     if op == C.WVAR_BWD:
@@ -269,19 +301,16 @@ def pair_error(op, dtype, out1, out2, ref1, ref2, x, d, g, cols):
         mu = (d64 * x64).sum(axis=1) / W
         u = x64 - mu[:, None]
         v = (d64 * u * u).sum(axis=1) / W
-        uk = x64 - x64[:, :1]
-        kappa = (d64 * uk * uk).sum(axis=1) / (d64 * u * u).sum(axis=1)
-        S1 = gg / W * np.abs(2 * d64 * u).max(axis=1) * kappa
-        S2 = gg / W * ((u * u).max(axis=1) + v) * kappa
+        S1 = gg / W * np.abs(2 * d64 * u).max(axis=1)
+        S2 = gg / W * ((u * u).max(axis=1) + v)
     else:
         u = x64 - x64.mean(axis=1, keepdims=True)
         w_ = d64 - d64.mean(axis=1, keepdims=True)
         sxx, syy = (u * u).sum(axis=1), (w_ * w_).sum(axis=1)
-        kappa = np.maximum(((x64 - x64[:, :1]) ** 2).sum(axis=1) / sxx, ((d64 - d64[:, :1]) ** 2).sum(axis=1) / syy)
         den = np.sqrt(sxx * syy)
         r = np.abs((u * w_).sum(axis=1)) / den
-        S1 = gg * (np.abs(w_).max(axis=1) / den + r * np.abs(u).max(axis=1) / sxx) * kappa
-        S2 = gg * (np.abs(u).max(axis=1) / den + r * np.abs(w_).max(axis=1) / syy) * kappa
+        S1 = gg * (np.abs(w_).max(axis=1) / den + r * np.abs(u).max(axis=1) / sxx)
+        S2 = gg * (np.abs(u).max(axis=1) / den + r * np.abs(w_).max(axis=1) / syy)
     worst = 0.0
     for out, ref, S in ((out1, ref1, S1), (out2, ref2, S2)):
         bound = F32_TOL * S[:, None]

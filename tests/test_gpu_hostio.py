@@ -69,7 +69,9 @@ def test_host_buffers_match_oracle_and_device_path(op, dt, plan, cols):
     C.run_host(op, hx, hy, plan=PLANS[plan], in_dtype=tin, out_dtype=tout, in_scale=hs, out_scale=hos, gamma=g,
                beta=b)
     ref = U.reference(op, tin, x, s, g, b)
-    assert U.error_metric(op, tout, U.to64(hy), ref, None if hos is None else hos.numpy()) <= 1.0
+    assert U.error_metric(op, tout, U.to64(hy), ref, None if hos is None else hos.numpy(),
+                          x64=U.decoded(x, s) if op == C.LAYERNORM else None,
+                          gamma=None if g is None else g.cpu(), beta=None if b is None else b.cpu()) <= 1.0
     # the same plan on device buffers gives the same bits
     p = PLANS[plan] if PLANS[plan] is not None else C.plan(op, -(-rows // 8), cols, tin, tout)
     dy, dos = U.run_gpu(op, x, s, out_dtype=tout, plan=p, gamma=g, beta=b)
