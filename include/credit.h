@@ -53,14 +53,25 @@ extern "C" {
 typedef enum {
     CREDIT_F32 = 0,
     CREDIT_BF16 = 1,
-    CREDIT_FP8_E4M3 = 2  /* e4m3 "fn": +-448 max, per-row FP32 scale */
+    CREDIT_FP8_E4M3 = 2,  /* e4m3 "fn": +-448 max, per-row FP32 scale */
+    CREDIT_INT8 = 3       /* output of CREDIT_OP_QUANT_INT8 only: int8 codes, per-row FP32 scale */
 } credit_dtype;
 
 typedef enum {
     CREDIT_OP_SOFTMAX = 0,    /* y_i = exp(x_i - m) / sum_j exp(x_j - m)            */
     CREDIT_OP_LOGSUMEXP = 1,  /* out[r] = m + ln sum_j exp(x_j - m), FP32 per row    */
     CREDIT_OP_LAYERNORM = 2,  /* y_i = (x_i - mu) / sqrt(var + eps) * g_i + b_i      */
-    CREDIT_OP_RMSNORM = 3     /* y_i = x_i / sqrt(mean(x^2) + eps) * g_i             */
+    CREDIT_OP_RMSNORM = 3,    /* y_i = x_i / sqrt(mean(x^2) + eps) * g_i             */
+    /* Row-wise int8 quantisation (the "row-wise int8 quantization" workload of
+     * Sec. IV-A): s = fl32(max_j |x_j| / 127) (1 for an all-zero row) into
+     * out_scale[r]; q_i = clamp(rint(fl32(x_i / s)), -127, 127), ties to even,
+     * both quotients correctly rounded in FP32.  in_dtype FP32 or BF16,
+     * out_dtype CREDIT_INT8, out_scale required; gamma / beta ignored.  A
+     * reduction (amax, q = 1) whose statistic is applied to every element of
+     * the row: 5 bytes per FP32 element when the row is read once, 9 with the
+     * global reread.  Staged (ONE_CTA / CLUSTER, shared-memory retention) and
+     * TWO_PASS plans; the planner uses its built-in rule (source 3). */
+    CREDIT_OP_QUANT_INT8 = 11
 } credit_op;
 
 typedef enum {
@@ -547,21 +558,24 @@ credit_status credit_set_trace(void *device_buf, int64_t bytes);
  * CTAs per row, partials exchanged through device memory between two kernel
  * launches) for callers that cannot allocate device memory: frameworks whose
  * caching allocator owns the device heap and pass a library only finished
- * buffers, or code recording a CUDA graph in global capture mode, where
- * cudaMalloc is a prohibited call.  The paper has no counterpart; it is an
+ * buffers (a cudaMalloc of the library's own would fragment that heap, or
+ * fail once the allocator has reserved it), and embeddings that forbid
+ * allocation after start-up.  The paper has no counterpart; it is an
  * interface variant of the non-DSMEM baseline.
- *   args          as credit_run_ex (caller-owned device buffers)
+ *   args          as credit_run_ex (caller-owned device buffers; FP8 output
+ *                 scales included)
  *   ctas_per_row  CTAs per row, 2..4096; outside that: CREDIT_ERR_UNSUPPORTED
  * Allocates nothing and never calls credit_init(): the partials live in a
  * fixed 4 MiB array in the library's device image (on every GPU that loads
  * the library, until the process exits), 262144 (row, CTA) partial sets, so
  * one launch covers floor(262144 / ctas_per_row) rows and longer calls are
- * split into several launches on `stream`.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  The array keeps the last call's partials; each
- * call writes every partial it reads, so nothing needs clearing.  All calls
- * share the one array: calls that can overlap on the GPU (different streams,
- * no ordering between them) race and corrupt each other's results.
+ * split into several launches on `stream`.  The first call on a device (and
+ * the first after that device's context was reset) looks up the array's
+ * device address with cudaGetSymbolAddress; make that first call before any
+ * stream capture.  The array keeps the last call's partials; each call writes
+ * every partial it reads, so nothing needs clearing.  All calls share the one
+ * array: calls that can overlap on the GPU (different streams, no ordering
+ * between them) race and corrupt each other's results.
  */
 credit_status credit_run_two_pass_noalloc(const credit_args *args, int32_t ctas_per_row,
                                           cudaStream_t stream);

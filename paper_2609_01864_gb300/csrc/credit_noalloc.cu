@@ -5,10 +5,12 @@
 // partials, then a sweep that combines them and writes the output), but it
 // keeps the partials in the fixed-size device array below instead of the
 // workspace that credit_init() allocates.  It exists for callers that cannot
-// allocate device memory: a framework whose caching allocator owns the
-// device heap and hands a library only finished buffers, or code recording a
-// CUDA graph in global capture mode, where cudaMalloc is a prohibited call
-// and would invalidate the capture.  Nothing in this file allocates.
+// allocate device memory: a framework whose caching allocator owns the device
+// heap and hands a library only finished buffers (a cudaMalloc behind its
+// back would fragment that heap or fail once the allocator has reserved it),
+// or an embedding that forbids allocation after start-up.  Nothing in this
+// file allocates.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -39,18 +41,57 @@ static __device__ __align__(256) float g_credit_static_ws[kStaticFloats];
 
 std::mutex g_mu;
 float *g_static_ptr[kMaxDevices] = {};
+unsigned long long g_static_ctx[kMaxDevices] = {};  // context the address belongs to (0: not looked up)
 
-// Device address of the static scratch on `dev` (looked up once per device,
-// with that device current).  nullptr if the lookup fails.
+// Unique ID of the calling thread's current context (0 if it cannot be had).
+// The driver entry points come through the runtime, so the library does not
+// link libcuda itself.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        (void)cudaGetLastError();
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current == nullptr || get_id == nullptr || get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr ||
+        get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the static scratch on `dev`, looked up with that device
+// current: once per device, and again only if the device's context has
+// changed since (cudaDeviceReset destroys the context, and the array gets a
+// new address when the module is loaded into the next one).  nullptr if the
+// lookup fails.  The caller has made `dev` current and initialised its
+// context (cudaSetDevice / a first runtime call).
 float *static_scratch(int dev) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (g_static_ptr[dev] == nullptr) {
+    const unsigned long long ctx = current_context_id();
+    if (g_static_ptr[dev] == nullptr || ctx == 0 || ctx != g_static_ctx[dev]) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_credit_static_ws) != cudaSuccess) {
+        if (cudaGetSymbolAddress(&p, g_credit_static_ws) != cudaSuccess || p == nullptr) {
             (void)cudaGetLastError();
+            g_static_ptr[dev] = nullptr;
+            g_static_ctx[dev] = 0;
             return nullptr;
         }
         g_static_ptr[dev] = static_cast<float *>(p);
+        g_static_ctx[dev] = ctx;
     }
     return g_static_ptr[dev];
 }

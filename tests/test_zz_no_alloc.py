@@ -1,8 +1,8 @@
 """The allocation-free two-pass entry point against the regular one.
 
 credit_run_two_pass_noalloc serves callers that cannot allocate device
-memory (a framework's allocator owns the heap, or a CUDA graph is being
-recorded in global capture mode).  It must give the same results as the
+memory (a framework's caching allocator owns the device heap, or an
+embedding forbids allocation after start-up).  It must give the same results as the
 split-row two-pass plan of credit_run_ex, call after call, even though every
 call reuses one fixed scratch array.  This file is collected last so that a
 failure here cannot hide the other tests' results.
@@ -50,7 +50,31 @@ def test_noalloc_matches_the_workspace_path_twice(op, dt, rows, cols, G):
         torch.cuda.synchronize()
         # same kernels, same partial order: identical to the workspace path
         assert torch.equal(out, ref)
-        assert U.error_metric(op, out_dtype, U.to64(out), y64_ref) <= 1.0
+        assert U.error_metric(op, out_dtype, U.to64(out), y64_ref, x64=U.decoded(x, s) if op == C.LAYERNORM else None,
+                              gamma=g, beta=b) <= 1.0
+
+
+@pytest.mark.parametrize("op", [C.LAYERNORM, C.RMSNORM], ids=["layernorm", "rmsnorm"])
+def test_noalloc_fp8_output_matches_the_workspace_path_twice(op):
+    """FP8-E4M3 output of the norms: the amax stage between the two sweeps and the per-row output scale,
+    written at each launch's row offset (70000 rows at G = 4 take two launches)."""
+    rows, cols, G = 70000, 600, 4
+    x, _ = U.make_input(C.BF16, rows, cols, kind="outliers", seed=11)
+    xd = x.cuda()
+    g, b = synth.gamma_beta(cols, seed=3)
+    kw = dict(gamma=g.cuda(), beta=b.cuda() if op == C.LAYERNORM else None, out_dtype=C.FP8_E4M3)
+    ref = torch.empty(rows, cols, device="cuda", dtype=torch.float8_e4m3fn)
+    ref_s = torch.empty(rows, device="cuda")
+    C.run_ex(op, xd, ref, plan=C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G), out_scale=ref_s, **kw)
+    pick = torch.arange(0, rows, 997)
+    y64_ref = U.reference(op, C.BF16, x[pick], None, g, b if op == C.LAYERNORM else None)
+    for _ in range(2):
+        out = torch.zeros(rows, cols, device="cuda", dtype=torch.float8_e4m3fn)
+        osc = torch.full((rows,), float("nan"), device="cuda")
+        assert C.run_two_pass_noalloc(op, xd, out, G, out_scale=osc, **kw) == C.OK
+        torch.cuda.synchronize()
+        assert torch.equal(out.view(torch.uint8), ref.view(torch.uint8)) and torch.equal(osc, ref_s)
+        assert U.error_metric(op, C.FP8_E4M3, U.to64(out[pick]), y64_ref, osc[pick].cpu().numpy()) <= 1.0
 
 
 def test_noalloc_rejects_out_of_range_split_and_bad_args():
