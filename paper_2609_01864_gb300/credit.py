@@ -17,8 +17,9 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libcredit.so")
 
 # enums of credit.h
-F32, BF16, FP8_E4M3 = 0, 1, 2
+F32, BF16, FP8_E4M3, INT8 = 0, 1, 2, 3
 SOFTMAX, LOGSUMEXP, LAYERNORM, RMSNORM = 0, 1, 2, 3
+QUANT_INT8 = 11
 PATH_AUTO, PATH_ONE_CTA, PATH_TWO_PASS, PATH_CLUSTER = -1, 0, 1, 2
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_INITIALIZED, ERR_CAPTURE, ERR_IO = range(8)
 OP_NAMES = {SOFTMAX: "softmax", LOGSUMEXP: "logsumexp", LAYERNORM: "layernorm", RMSNORM: "rmsnorm"}
@@ -29,8 +30,8 @@ OP_NAMES.update({SOFTMAX_BWD: "softmax_bwd", LAYERNORM_BWD: "layernorm_bwd", RMS
                  SOFTMAX_LOGITS_BWD: "softmax_logits_bwd", XENT_BWD: "xent_bwd", WVAR_BWD: "wvar_bwd",
                  PEARSON_BWD: "pearson_bwd"})
 
-TORCH_DTYPE = {F32: torch.float32, BF16: torch.bfloat16, FP8_E4M3: torch.float8_e4m3fn}
-DTYPE_OF = {torch.float32: F32, torch.bfloat16: BF16, torch.float8_e4m3fn: FP8_E4M3}
+TORCH_DTYPE = {F32: torch.float32, BF16: torch.bfloat16, FP8_E4M3: torch.float8_e4m3fn, INT8: torch.int8}
+DTYPE_OF = {torch.float32: F32, torch.bfloat16: BF16, torch.float8_e4m3fn: FP8_E4M3, torch.int8: INT8}
 
 
 class CreditError(RuntimeError):

@@ -461,7 +461,7 @@ static int retain_request(const credit_plan_t *p) {
 static bool ring_config_for(const DeviceInfo &di, const credit_args *a, int isz, int P, const credit_plan_t *p,
                             RingCfg *rc) {
     const int tout = a->op == OP_LSE ? DT_F32 : a->out_dtype;
-    const bool tm_op = a->op != OP_LSE && !(tout == DT_E4M3 && (a->op == OP_LN || a->op == OP_RMS));
+    const bool tm_op = a->op != OP_LSE && a->op != OP_Q8 && !(tout == DT_E4M3 && (a->op == OP_LN || a->op == OP_RMS));
     int want = retain_request(p);
     const bool tuned_smem = p->threads != 0 || p->reducer_threads != 0;
     if (want == 2) {
@@ -484,8 +484,11 @@ static bool ring_config_for(const DeviceInfo &di, const credit_args *a, int isz,
 
 credit_status validate_args(const credit_args *a) {
     if (!a) return CREDIT_ERR_INVALID_ARG;
-    if (a->op < 0 || a->op > 3) return CREDIT_ERR_INVALID_ARG;
-    if (a->in_dtype < 0 || a->in_dtype > 2 || a->out_dtype < 0 || a->out_dtype > 2) return CREDIT_ERR_INVALID_ARG;
+    const bool q8 = a->op == OP_Q8;
+    if ((a->op < 0 || a->op > 3) && !q8) return CREDIT_ERR_INVALID_ARG;
+    if (a->in_dtype < 0 || a->in_dtype > 2 || a->out_dtype < 0 || a->out_dtype > 3) return CREDIT_ERR_INVALID_ARG;
+    if (q8 != (a->out_dtype == DT_I8)) return CREDIT_ERR_INVALID_ARG;    // int8 codes are the quantiser's output only
+    if (q8 && a->in_dtype == DT_E4M3) return CREDIT_ERR_UNSUPPORTED;     // FP32 / BF16 rows
     if (a->rows < 0 || a->cols <= 0) return CREDIT_ERR_INVALID_ARG;
     if (a->rows == 0) return CREDIT_OK;
     if (!a->in || !a->out) return CREDIT_ERR_INVALID_ARG;
@@ -494,7 +497,7 @@ credit_status validate_args(const credit_args *a) {
     if (ld_in < a->cols || (a->op != OP_LSE && ld_out < a->cols)) return CREDIT_ERR_INVALID_ARG;
     if (a->in_dtype == DT_E4M3 && !a->in_scale) return CREDIT_ERR_INVALID_ARG;
     const int tout = a->op == OP_LSE ? DT_F32 : a->out_dtype;
-    if (a->op != OP_LSE && tout == DT_E4M3 && !a->out_scale) return CREDIT_ERR_INVALID_ARG;
+    if (a->op != OP_LSE && (tout == DT_E4M3 || q8) && !a->out_scale) return CREDIT_ERR_INVALID_ARG;
     const uintptr_t ip = reinterpret_cast<uintptr_t>(a->in), op = reinterpret_cast<uintptr_t>(a->out);
     if (ip % dtype_size(a->in_dtype) || op % dtype_size(tout)) return CREDIT_ERR_INVALID_ARG;
     if ((a->gamma && reinterpret_cast<uintptr_t>(a->gamma) % 4) ||
@@ -553,8 +556,8 @@ static RowArgs make_row_args(const credit_args *a, unsigned *err, float *ws) {
     r.ld_out = a->ld_out ? a->ld_out : a->cols;
     r.in_scale = a->in_scale;
     r.out_scale = a->out_scale;
-    r.gamma = a->gamma;
-    r.beta = a->beta;
+    r.gamma = (a->op == OP_LN || a->op == OP_RMS) ? a->gamma : nullptr;  // the other ops take no affine
+    r.beta = a->op == OP_LN ? a->beta : nullptr;
     const float dflt = a->op == OP_RMS ? 1e-6f : 1e-5f;
     r.eps = a->eps < 0.0f ? dflt : a->eps;
     r.err = err;

@@ -144,7 +144,7 @@ extern "C" credit_status credit_run_host(const credit_args *args, const credit_p
     blk.ld_in = 0;
     blk.ld_out = 0;
     blk.in_scale = tin == CREDIT_FP8_E4M3 ? io.isc[0] : nullptr;
-    blk.out_scale = (!lse && tout == CREDIT_FP8_E4M3) ? io.osc[0] : nullptr;
+    blk.out_scale = (!lse && (tout == CREDIT_FP8_E4M3 || tout == CREDIT_INT8)) ? io.osc[0] : nullptr;
     blk.gamma = d_gamma;
     blk.beta = d_beta;
     credit_plan_t chosen;

@@ -19,7 +19,7 @@ template <int OP, int TIN, int TOUT>
 static void fill_set(KernelSet *ks) {
     ks->ring = reinterpret_cast<const void *>(&k_ring<OP, TIN, TOUT>);
     ks->ring_tm = nullptr;
-    if constexpr (OP != OP_LSE && !(TOUT == DT_E4M3 && (OP == OP_LN || OP == OP_RMS)))
+    if constexpr (OP != OP_LSE && OP != OP_Q8 && !(TOUT == DT_E4M3 && (OP == OP_LN || OP == OP_RMS)))
         ks->ring_tm = reinterpret_cast<const void *>(&k_ring_tm<OP, TIN, TOUT>);
     ks->tp_fused = reinterpret_cast<const void *>(&k_tp_fused<OP, TIN, TOUT>);
     ks->tp_stats = reinterpret_cast<const void *>(&k_tp_stats<OP, TIN>);
@@ -39,6 +39,10 @@ static bool fill_out(int tout, KernelSet *ks) {
         if (tout != DT_F32) return false;
         fill_set<OP, TIN, DT_F32>(ks);
         return true;
+    } else if constexpr (OP == OP_Q8) {  // FP32 / BF16 rows -> int8 codes
+        if (tout != DT_I8 || TIN == DT_E4M3) return false;
+        fill_set<OP, TIN, DT_I8>(ks);
+        return true;
     } else {
         switch (tout) {
         case DT_F32: fill_set<OP, TIN, DT_F32>(ks); return true;
@@ -55,6 +59,7 @@ bool CREDIT_CAT(kernels_tin, CREDIT_TIN)(int op, int tout, KernelSet *ks) {
     case OP_LSE: return fill_out<OP_LSE, CREDIT_TIN>(tout, ks);
     case OP_LN: return fill_out<OP_LN, CREDIT_TIN>(tout, ks);
     case OP_RMS: return fill_out<OP_RMS, CREDIT_TIN>(tout, ks);
+    case OP_Q8: return fill_out<OP_Q8, CREDIT_TIN>(tout, ks);
     default: return false;
     }
 }

@@ -104,8 +104,11 @@ extern "C" {
 
 credit_status credit_plan_ex(credit_op op, int64_t rows, int64_t cols, credit_dtype in_dtype, credit_dtype out_dtype,
                              credit_plan_t *out) {
-    if (!out || op < 0 || op > 3 || in_dtype < 0 || in_dtype > 2 || out_dtype < 0 || out_dtype > 2)
+    const bool q8 = op == CREDIT_OP_QUANT_INT8;
+    if (!out || ((op < 0 || op > 3) && !q8) || in_dtype < 0 || in_dtype > 2 || out_dtype < 0 || out_dtype > 3)
         return CREDIT_ERR_INVALID_ARG;
+    if (q8 != (out_dtype == CREDIT_INT8)) return CREDIT_ERR_INVALID_ARG;
+    if (q8 && in_dtype == CREDIT_FP8_E4M3) return CREDIT_ERR_UNSUPPORTED;
     if (rows < 0 || cols <= 0) return CREDIT_ERR_INVALID_ARG;
     const int tout = op == CREDIT_OP_LOGSUMEXP ? 0 : out_dtype;
     int dev = 0;
@@ -114,7 +117,8 @@ credit_status credit_plan_ex(credit_op op, int64_t rows, int64_t cols, credit_dt
     const DeviceInfo *di = device_info(dev);
     if (!di) return CREDIT_ERR_NOT_INITIALIZED;
     if (env_force(di, out, cols, in_dtype)) return CREDIT_OK;
-    if (model_plan(*di, dev, op, rows, cols, in_dtype, tout, out)) return CREDIT_OK;
+    // the calibration and the learned model cover the four ops of Sec. III-B; the quantiser takes the rule
+    if (!q8 && model_plan(*di, dev, op, rows, cols, in_dtype, tout, out)) return CREDIT_OK;
     heuristic_plan(*di, dev, op, rows, cols, in_dtype, tout, out);
     return CREDIT_OK;
 }

@@ -17,8 +17,8 @@
 
 namespace credit {
 
-enum DType : int { DT_F32 = 0, DT_BF16 = 1, DT_E4M3 = 2 };
-enum Op : int { OP_SOFTMAX = 0, OP_LSE = 1, OP_LN = 2, OP_RMS = 3 };
+enum DType : int { DT_F32 = 0, DT_BF16 = 1, DT_E4M3 = 2, DT_I8 = 3 /* output codes of OP_Q8 only */ };
+enum Op : int { OP_SOFTMAX = 0, OP_LSE = 1, OP_LN = 2, OP_RMS = 3, OP_Q8 = 11 /* row-wise int8 quantisation */ };
 
 // Error-word bits (read back by credit_device_error).
 enum : unsigned { ERR_TMA_TIMEOUT = 1u, ERR_BAD_LAUNCH = 2u };
@@ -258,6 +258,18 @@ template <> struct Fmt<DT_E4M3> {
     static constexpr int size = 1;
     static constexpr int V = 16;
 };
+template <> struct Fmt<DT_I8> {
+    static constexpr int size = 1;
+    static constexpr int V = 16;
+};
+
+// Row-wise int8 code of x with the row scale s (s = amax / 127 in FP32): the
+// correctly rounded FP32 quotient x / s, rounded to the nearest integer with
+// ties to even, clamped to +-127.  Returned as a float holding the integer.
+__device__ __forceinline__ float q8_code(float x, float s) {
+    const float k = rintf(__fdiv_rn(x, s));
+    return fminf(fmaxf(k, -127.0f), 127.0f);
+}
 
 // Decode one 16-byte group (already loaded as uint4) into floats.
 template <int DT>
@@ -311,6 +323,8 @@ __device__ __forceinline__ void store_one(unsigned char *p, float v) {
     } else if constexpr (DT == DT_BF16) {
         __nv_bfloat16 b = __float2bfloat16_rn(v);
         *reinterpret_cast<__nv_bfloat16 *>(p) = b;
+    } else if constexpr (DT == DT_I8) {
+        *reinterpret_cast<signed char *>(p) = static_cast<signed char>(static_cast<int>(v));
     } else {
         *p = static_cast<unsigned char>(__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3));
     }
@@ -328,6 +342,13 @@ __device__ __forceinline__ void pack_words(const float (&y)[V], uint32_t (&w)[(V
             __nv_bfloat162 b = __floats2bfloat162_rn(y[2 * k], y[2 * k + 1]);
             w[k] = *reinterpret_cast<uint32_t *>(&b);
         }
+    } else if constexpr (DT == DT_I8) {  // y holds integers in [-127, 127]
+#pragma unroll
+        for (int k = 0; k < V / 4; ++k)
+            w[k] = (static_cast<uint32_t>(static_cast<int>(y[4 * k])) & 0xFFu) |
+                   ((static_cast<uint32_t>(static_cast<int>(y[4 * k + 1])) & 0xFFu) << 8) |
+                   ((static_cast<uint32_t>(static_cast<int>(y[4 * k + 2])) & 0xFFu) << 16) |
+                   (static_cast<uint32_t>(static_cast<int>(y[4 * k + 3])) << 24);
     } else {
 #pragma unroll
         for (int k = 0; k < V / 4; ++k) {

@@ -11,6 +11,10 @@
 //   FP8 output of layernorm / rmsnorm adds stage 2: q = 1, amax |h(x)|, and
 //   writes codes h(x) * 448 / amax with the row scale amax / 448.  Softmax
 //   needs no extra stage: its amax is 1 / s in closed form.
+//   int8       stage 1: q = 1, amax |x| (merged by max);  s = amax / 127
+//   quantise   (1 for an all-zero row), h(x) = clamp(rint(x / s), +-127)
+//              with both quotients correctly rounded in FP32; the row's
+//              scale s goes to out_scale.
 //
 // Slicing (Eq. 2).  A row is cut on the 16-byte grid of its own address: the
 // elements before the first 16-byte boundary (the "head", < 16 bytes) belong
@@ -143,6 +147,11 @@ __device__ __forceinline__ Stats combine_partials(const float *p, int stride, in
         }
         st.a = mu;
         st.b = rsqrtf(m2 / static_cast<float>(N) + eps);
+    } else if constexpr (OP == OP_Q8) {
+        float am = 0.0f;
+        for (int c = 0; c < P; ++c) am = fmaxf(am, p[c * stride]);
+        st.a = am > 0.0f ? __fdiv_rn(am, 127.0f) : 1.0f;  // the row scale
+        st.b = 0.0f;
     } else {
         float ss = 0.0f;
         for (int c = 0; c < P; ++c) ss += p[c * stride];
@@ -304,6 +313,15 @@ template <> struct Stream<OP_RMS> {
     __device__ __forceinline__ void add1(float x) { ss = fmaf(x, x, ss); }
 };
 
+template <> struct Stream<OP_Q8> {  // amax |x|: exact, so every merge order gives the same value
+    float am = 0.0f;
+    template <int V> __device__ __forceinline__ void add(const float (&f)[V]) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) am = fmaxf(am, fabsf(f[j]));
+    }
+    __device__ __forceinline__ void add1(float x) { am = fmaxf(am, fabsf(x)); }
+};
+
 // ======================================================================
 // Ring kernel: the cluster path (P > 1) and the one-CTA path (P == 1).
 //
@@ -399,6 +417,9 @@ __device__ __forceinline__ float2 block_reduce_stream(Stream<OP> st, float *red,
     if constexpr (OP == OP_RMS) {
         if (bar_id == 0) return make_float2(block_allreduce<false>(st.ss, red), 0.0f);
         return make_float2(cons_allreduce<false>(st.ss, red, Tc), 0.0f);
+    } else if constexpr (OP == OP_Q8) {
+        if (bar_id == 0) return make_float2(block_allreduce<true>(st.am, red), 0.0f);
+        return make_float2(cons_allreduce<true>(st.am, red, Tc), 0.0f);
     } else if constexpr (OP == OP_LN) {
         st.finish();
 #pragma unroll
@@ -761,8 +782,8 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                     cluster_wait_acquire();
                     waited_start = true;
                 }
-                const float *sl = exchange_push<(OP == OP_RMS) ? 1 : 2>(part0, part1, slots, xbar, 0, par, xphase, P,
-                                                                         c, Tr, a.err);
+                const float *sl = exchange_push<(OP == OP_RMS || OP == OP_Q8) ? 1 : 2>(part0, part1, slots, xbar, 0,
+                                                                                        par, xphase, P, c, Tr, a.err);
                 st = combine_partials<OP>(sl, 4, P, g.s, V, N, a.eps);
             } else {
                 const float p1[2] = {part0, part1};
@@ -816,6 +837,9 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
             if constexpr (OP == OP_LSE) {
                 if (c == 0 && tid == 0) reinterpret_cast<float *>(a.out)[row] = st.a + logf(st.b);
             }
+            if constexpr (OP == OP_Q8) {
+                if (c == 0 && tid == 0) a.out_scale[row] = st.a;
+            }
 
             // ---------- publish the row statistics to the writers
             if (tid == 0) {
@@ -859,6 +883,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                 const float smul = (TOUT == DT_E4M3) ? 448.0f : inv;  // softmax: y (or its code) = exp(x - M) * smul
                 auto h = [&](float x, float gm, float bt) -> float {
                     if constexpr (OP == OP_SOFTMAX) return exp_fast(x - st.a) * smul;
+                    else if constexpr (OP == OP_Q8) return q8_code(x, st.a);
                     else return norm_h<OP>(x, st, gm, bt) * qmul;
                 };
                 for (int k = 0; k < g.nch; ++k) {
@@ -885,7 +910,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                                          for (int hv = 0; hv < V; hv += SV) {
                                              float gg[SV], bb[SV], y[SV];
                                              const long long i0 = i_base + (kg + gi) * V + hv;
-                                             if constexpr (OP != OP_SOFTMAX) {
+                                             if constexpr (OP == OP_LN || OP == OP_RMS) {
                                                  if (A > 0) load_affine_smem<SV>(has_g ? ag : nullptr, gi * V + hv, 1.0f, gg);
                                                  else load_affine<SV>(a.gamma, i0, g_vec, 1.0f, gg);
                                              }
@@ -895,7 +920,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                                              }
 #pragma unroll
                                              for (int q = 0; q < SV; ++q)
-                                                 y[q] = h(f[hv + q], OP != OP_SOFTMAX ? gg[q] : 1.0f,
+                                                 y[q] = h(f[hv + q], (OP == OP_LN || OP == OP_RMS) ? gg[q] : 1.0f,
                                                           OP == OP_LN ? bb[q] : 0.0f);
                                              store_group<TOUT, SV>(out_row + i0 * osz, y, out_vec);
                                          }
@@ -912,7 +937,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                 for (int e = 0; e < 2; ++e)
                     for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) {
                         const long long i = e == 0 ? k : g.s.h0 + g.s.G * V + k;
-                        const float gm = (OP != OP_SOFTMAX && a.gamma) ? a.gamma[i] : 1.0f;
+                        const float gm = ((OP == OP_LN || OP == OP_RMS) && a.gamma) ? a.gamma[i] : 1.0f;
                         const float bt = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
                         store_one<TOUT>(out_row + i * osz, h(edge_x(g, e, k), gm, bt));
                     }
@@ -1022,6 +1047,15 @@ __device__ __forceinline__ void apply_sweep(const RowArgs &a, long long row, con
         });
         sweep_edges<TIN>(in_row, s, P, c, in_sc,
                          [&](long long i, float x) { store_one<TOUT>(out_row + i * osz, exp_fast(x - st.a) * mul); });
+    } else if constexpr (OP == OP_Q8) {
+        sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
+            float y[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) y[j] = q8_code(f[j], st.a);
+            store_group<TOUT, V>(out_row + i0 * osz, y, out_vec);
+        });
+        sweep_edges<TIN>(in_row, s, P, c, in_sc,
+                         [&](long long i, float x) { store_one<TOUT>(out_row + i * osz, q8_code(x, st.a)); });
     } else {
         sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
             float gg[V], bb[V], y[V];
@@ -1063,6 +1097,9 @@ __global__ void __launch_bounds__(1024) k_tp_fused(const RowArgs a) {
         }
         if constexpr (TOUT == DT_E4M3 && OP == OP_SOFTMAX) {
             if (threadIdx.x == 0) a.out_scale[row] = (1.0f / st.b) * (1.0f / 448.0f);
+        }
+        if constexpr (OP == OP_Q8) {
+            if (threadIdx.x == 0) a.out_scale[row] = st.a;
         }
         apply_sweep<OP, TIN, TOUT>(a, row, in_row, s, 1, 0, in_sc, st, qmul);
     }
@@ -1128,6 +1165,9 @@ __global__ void __launch_bounds__(1024) k_tp_apply(const RowArgs a) {
     }
     if constexpr (TOUT == DT_E4M3 && OP == OP_SOFTMAX) {
         if (g == 0 && threadIdx.x == 0) a.out_scale[row] = (1.0f / st.b) * (1.0f / 448.0f);
+    }
+    if constexpr (OP == OP_Q8) {
+        if (g == 0 && threadIdx.x == 0) a.out_scale[row] = st.a;
     }
     apply_sweep<OP, TIN, TOUT>(a, row, in_row, s, G, g, in_sc, st, qmul);
 }

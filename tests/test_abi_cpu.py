@@ -67,6 +67,16 @@ def test_validation_rejects_bad_calls_without_touching_the_gpu(lib):
     assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.ERR_INVALID_ARG
     a.in_, a.rows = 0x1000, 0                                              # rows == 0 is a no-op
     assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.OK
+    # int8 quantisation: codes only as its output, with scales, from FP32 / BF16 rows
+    a.rows, a.op, a.in_dtype, a.out_dtype, a.out_scale = 4, C.QUANT_INT8, C.F32, C.F32, 0x3000
+    assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.ERR_INVALID_ARG   # not an int8 output
+    a.op, a.out_dtype = C.SOFTMAX, C.INT8
+    assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.ERR_INVALID_ARG   # int8 output of another op
+    a.op, a.out_scale = C.QUANT_INT8, None
+    assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.ERR_INVALID_ARG   # no scales
+    a.out_scale, a.in_dtype, a.in_scale = 0x3000, C.FP8_E4M3, 0x4000
+    assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.ERR_UNSUPPORTED   # FP8 rows
+    a.in_dtype, a.out_dtype, a.out_scale, a.in_scale = C.F32, C.F32, None, None
     # simple entry points: FP8 needs credit_run_ex (scales)
     assert lib.credit_softmax(0x1000, 0x2000, 4, 16, C.FP8_E4M3, None) == C.ERR_INVALID_ARG
     p = C.PlanT()
@@ -163,6 +173,7 @@ def test_binding_constants_match_the_header_enums():
         "CREDIT_OP_LAYERNORM_BWD": C.LAYERNORM_BWD, "CREDIT_OP_RMSNORM_BWD": C.RMSNORM_BWD,
         "CREDIT_OP_SOFTMAX_LOGITS_BWD": C.SOFTMAX_LOGITS_BWD, "CREDIT_OP_XENT_BWD": C.XENT_BWD,
         "CREDIT_OP_WVAR_BWD": C.WVAR_BWD, "CREDIT_OP_PEARSON_BWD": C.PEARSON_BWD,
+        "CREDIT_INT8": C.INT8, "CREDIT_OP_QUANT_INT8": C.QUANT_INT8,
     }
     for name, v in expect.items():
         assert vals.get(name) == v, (name, vals.get(name), v)
