@@ -69,7 +69,7 @@ typedef enum {
      * out_dtype CREDIT_INT8, out_scale required; gamma / beta ignored.  A
      * reduction (amax, q = 1) whose statistic is applied to every element of
      * the row: 5 bytes per FP32 element when the row is read once, 9 with the
-     * global reread.  Staged (ONE_CTA / CLUSTER, shared-memory retention) and
+     * global reread.  Staged (ONE_CTA / CLUSTER, either retention tier) and
      * TWO_PASS plans; the planner uses its built-in rule (source 3). */
     CREDIT_OP_QUANT_INT8 = 11
 } credit_op;
@@ -85,8 +85,9 @@ typedef enum {
  * reduction and its reuse pass (Sec. III-C, "reuse"; the capacity of Eq. 3).
  *   SMEM  the shared-memory chunk ring (slice <= the opt-in shared memory)
  *   TMEM  tensor memory, two 128-KiB row buffers per SM; shared memory holds
- *         only chunks in flight and gamma / beta.  Softmax, LayerNorm and
- *         RMSNorm (not FP8-output norms, not logsumexp), slice <= 128 KiB of
+ *         only chunks in flight and gamma / beta.  Softmax, LayerNorm,
+ *         RMSNorm and int8 quantisation (not FP8-output norms, not
+ *         logsumexp), slice <= 128 KiB of
  *         input, one CTA per SM.  The project's addition; the paper stages
  *         in shared memory only.
  *   AUTO  TMEM where it applies and a slice exceeds 32 KiB, else SMEM

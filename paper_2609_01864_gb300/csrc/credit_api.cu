@@ -461,7 +461,7 @@ static int retain_request(const credit_plan_t *p) {
 static bool ring_config_for(const DeviceInfo &di, const credit_args *a, int isz, int P, const credit_plan_t *p,
                             RingCfg *rc) {
     const int tout = a->op == OP_LSE ? DT_F32 : a->out_dtype;
-    const bool tm_op = a->op != OP_LSE && a->op != OP_Q8 && !(tout == DT_E4M3 && (a->op == OP_LN || a->op == OP_RMS));
+    const bool tm_op = a->op != OP_LSE && !(tout == DT_E4M3 && (a->op == OP_LN || a->op == OP_RMS));
     int want = retain_request(p);
     const bool tuned_smem = p->threads != 0 || p->reducer_threads != 0;
     if (want == 2) {

@@ -19,7 +19,7 @@ template <int OP, int TIN, int TOUT>
 static void fill_set(KernelSet *ks) {
     ks->ring = reinterpret_cast<const void *>(&k_ring<OP, TIN, TOUT>);
     ks->ring_tm = nullptr;
-    if constexpr (OP != OP_LSE && OP != OP_Q8 && !(TOUT == DT_E4M3 && (OP == OP_LN || OP == OP_RMS)))
+    if constexpr (OP != OP_LSE && !(TOUT == DT_E4M3 && (OP == OP_LN || OP == OP_RMS)))
         ks->ring_tm = reinterpret_cast<const void *>(&k_ring_tm<OP, TIN, TOUT>);
     ks->tp_fused = reinterpret_cast<const void *>(&k_tp_fused<OP, TIN, TOUT>);
     ks->tp_stats = reinterpret_cast<const void *>(&k_tp_stats<OP, TIN>);

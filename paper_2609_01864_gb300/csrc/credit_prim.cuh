@@ -263,11 +263,18 @@ template <> struct Fmt<DT_I8> {
     static constexpr int V = 16;
 };
 
-// Row-wise int8 code of x with the row scale s (s = amax / 127 in FP32): the
-// correctly rounded FP32 quotient x / s, rounded to the nearest integer with
-// ties to even, clamped to +-127.  Returned as a float holding the integer.
-__device__ __forceinline__ float q8_code(float x, float s) {
-    const float k = rintf(__fdiv_rn(x, s));
+// Row-wise int8 code of x with the row scale s (s = amax / 127 in FP32) and
+// inv = the correctly rounded 1 / s: the correctly rounded FP32 quotient
+// x / s, rounded to the nearest integer with ties to even, clamped to +-127;
+// returned as a float holding the integer.  |x / s| <= 127.00001, so
+// t = x * inv is within 3 * 2^-24 * 128 < 2^-15 of the rounded quotient (three
+// roundings, each of relative size <= 2^-24): rint(t) is the same integer
+// unless t lies within 2^-14 of a half-integer, and only then (and for a
+// non-finite t) is the quotient itself computed.
+__device__ __forceinline__ float q8_code(float x, float s, float inv) {
+    const float t = x * inv;
+    float k = rintf(t);
+    if (!(fabsf(fabsf(t - k) - 0.5f) >= 0x1p-14f)) k = rintf(__fdiv_rn(x, s));
     return fminf(fmaxf(k, -127.0f), 127.0f);
 }
 

@@ -111,6 +111,12 @@ template <> struct TmPart<OP_RMS> {
     __device__ __forceinline__ float4 to() const { return make_float4(st.ss, 0.0f, 0.0f, 0.0f); }
     __device__ __forceinline__ void merge(const TmPart &o) { st.ss += o.st.ss; }
 };
+template <> struct TmPart<OP_Q8> {
+    Stream<OP_Q8> st;
+    __device__ __forceinline__ void from(const float4 &e) { st.am = e.x; }
+    __device__ __forceinline__ float4 to() const { return make_float4(st.am, 0.0f, 0.0f, 0.0f); }
+    __device__ __forceinline__ void merge(const TmPart &o) { st.am = fmaxf(st.am, o.st.am); }
+};
 
 // Xor shuffle tree over the warp; both partners of a level merge (lower
 // lane, upper lane) in that order, so every lane ends with the same value.
@@ -122,7 +128,7 @@ __device__ __forceinline__ TmPart<OP> tm_warp_tree(TmPart<OP> t) {
         const float4 e = t.to();
         float4 f = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         f.x = __shfl_xor_sync(0xffffffffu, e.x, o);
-        if constexpr (OP != OP_RMS) f.y = __shfl_xor_sync(0xffffffffu, e.y, o);
+        if constexpr (OP != OP_RMS && OP != OP_Q8) f.y = __shfl_xor_sync(0xffffffffu, e.y, o);
         if constexpr (OP == OP_LN) f.z = __shfl_xor_sync(0xffffffffu, e.z, o);
         TmPart<OP> u;
         u.from(f);
@@ -256,6 +262,10 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
                 } else if constexpr (OP == OP_LN) {
                     st.a = t.st.mu;
                     st.b = rsqrtf(t.st.m2 / static_cast<float>(N) + a.eps);
+                } else if constexpr (OP == OP_Q8) {
+                    st.a = t.st.am > 0.0f ? __fdiv_rn(t.st.am, 127.0f) : 1.0f;  // the row scale
+                    st.b = __frcp_rn(st.a);
+                    if (c == 0) a.out_scale[row] = st.a;
                 } else {
                     st.a = rsqrtf(t.st.ss / static_cast<float>(N) + a.eps);
                     st.b = 0.0f;
@@ -269,28 +279,27 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
     } else if (warp == 16) {
         // ========================================================== producer
         if (lane == 0) {
-            long long j = 0;
+            RingPos rp(K);
             for (long long row = cl; row < a.rows; row += ncl) {
                 const RowGeo g = geo(row);
                 const long long body = g.ng * 16;
                 const unsigned char *src = g.in_row + g.s.h0 * isz + g.s.g_lo * 16;
-                for (long long off = 0; off < body; off += CH, ++j) {
-                    const int slot = static_cast<int>(j % K);
-                    if (j >= K) mbar_wait_bounded(&empty[slot], static_cast<uint32_t>(((j / K) - 1) & 1), a.err);
+                for (long long off = 0; off < body; off += CH, rp.next()) {
+                    const int slot = rp.slot;
+                    if (rp.lap > 0) mbar_wait_bounded(&empty[slot], rp.prev_parity(), a.err);
                     const uint32_t bytes = static_cast<uint32_t>(body - off < CH ? body - off : CH);
                     mbar_arrive_expect_tx(&full[slot], bytes);
                     bulk_g2s(ring + static_cast<size_t>(slot) * CH, src + off, bytes, &full[slot]);
                 }
             }
         } else if (lane == 1 && A > 0) {
-            long long aj = 0;
+            RingPos ap(A);
             for (long long row = cl; row < a.rows && !(a.affine_resident && row > cl); row += ncl) {
                 const RowGeo g = geo(row);
                 const long long i_base = g.s.h0 + g.s.g_lo * V;
-                for (int k = 0; k < g.nch; ++k, ++aj) {
-                    const int slot = static_cast<int>(aj % A);
-                    if (aj >= A && !a.affine_resident)
-                        mbar_wait_bounded(&affine_empty[slot], static_cast<uint32_t>(((aj / A) - 1) & 1), a.err);
+                for (int k = 0; k < g.nch; ++k, ap.next()) {
+                    const int slot = ap.slot;
+                    if (ap.lap > 0 && !a.affine_resident) mbar_wait_bounded(&affine_empty[slot], ap.prev_parity(), a.err);
                     const uint32_t bytes = static_cast<uint32_t>(chunk_groups(g, k)) * V * 4;
                     const long long e0 = i_base + static_cast<long long>(k) * gpc * V;
                     unsigned char *dst = aring + static_cast<size_t>(slot) * aslot;
@@ -306,7 +315,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
         // reducer thread tid owns lane t = tid % 128 and the half tid / 128 of
         // that lane's groups in every chunk: groups t + 128 (4 half + m)
         const int t = tid & (TL - 1), half = tid / TL;
-        long long j = 0;
+        RingPos rp(K);
         int rr = 0;
         for (long long row = cl; row < a.rows; row += ncl, ++rr) {
             const RowGeo g = geo(row);
@@ -319,10 +328,9 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
             if (tid == 0) trace_stamp(a, rr, 5);
             const uint32_t tb = tq + static_cast<uint32_t>(b * kTmBufCols + half * 4 * kTmHalf);
             Stream<OP> acc;
-            for (int k = 0; k < g.nch; ++k) {
-                const long long jk = j + k;
-                const int slot = static_cast<int>(jk % K);
-                mbar_wait_bounded(&full[slot], static_cast<uint32_t>((jk / K) & 1), a.err);
+            for (int k = 0; k < g.nch; ++k, rp.next()) {
+                const int slot = rp.slot;
+                mbar_wait_bounded(&full[slot], rp.parity(), a.err);
                 const unsigned char *cb = ring + static_cast<size_t>(slot) * CH;
                 const int gn = chunk_groups(g, k);
                 const int g0 = t + half * kTmHalf * TL;
@@ -377,13 +385,12 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
                 fence_release_smem_cluster();
                 st_async_v4f32(mapa_shared(smem_addr(ent), d), e, mapa_shared(smem_addr(&xbar[s4]), d));
             }
-            j += g.nch;
         }
     } else {
         // ========================================================== writers
         const int wt = tid - Tr;
         const int twin = wt & (TL - 1), half = wt / TL;  // the lane, and the half of its groups (as the reducers)
-        long long aj_w = 0;
+        RingPos wa(A > 0 ? A : 1);  // streamed gamma / beta slots
         int rr = 0;
         for (long long row = cl; row < a.rows; row += ncl, ++rr) {
             const RowGeo g = geo(row);
@@ -407,18 +414,18 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
             const float smul = (TOUT == DT_E4M3) ? 448.0f : ((OP == OP_SOFTMAX) ? 1.0f / st.b : 0.0f);
             auto h = [&](float x, float gm, float bt) -> float {
                 if constexpr (OP == OP_SOFTMAX) return exp_fast(x - st.a) * smul;
+                else if constexpr (OP == OP_Q8) return q8_code(x, st.a, st.b);
                 else return norm_h<OP>(x, st, gm, bt);
             };
             const uint32_t tb = tq + static_cast<uint32_t>(b * kTmBufCols);
             for (int k = 0; k < g.nch; ++k) {
                 const int gn = chunk_groups(g, k);
                 const long long kg = static_cast<long long>(k) * gpc;
-                const int aslot_k = A > 0 ? (a.affine_resident ? k : static_cast<int>((aj_w + k) % A)) : 0;
+                const int aslot_k = A > 0 ? (a.affine_resident ? k : wa.slot) : 0;
                 const float *ag = reinterpret_cast<const float *>(aring + static_cast<size_t>(aslot_k) * aslot);
                 const float *ab = ag + (has_g ? gpc * V : 0);
                 if (A > 0 && (!a.affine_resident || rr == 0))
-                    mbar_wait_bounded(&affine_full[aslot_k],
-                                      a.affine_resident ? 0u : static_cast<uint32_t>(((aj_w + k) / A) & 1), a.err);
+                    mbar_wait_bounded(&affine_full[aslot_k], a.affine_resident ? 0u : wa.parity(), a.err);
                 uint32_t w[4 * kTmHalf];
                 tm_ld16(tb + static_cast<uint32_t>(k * kTmColsPerChunk + half * 4 * kTmHalf), w);
                 // gamma / beta for the groups of this chunk, batch by batch (L2 loads issued together)
@@ -433,7 +440,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
 #pragma unroll
                         for (int hv = 0; hv < V; hv += SV) {
                             float tg[SV], tbv[SV];
-                            if constexpr (OP != OP_SOFTMAX) {
+                            if constexpr (OP == OP_LN || OP == OP_RMS) {
                                 if (gi < gn) {
                                     if (A > 0) {
                                         load_affine_smem<SV>(has_g ? ag : nullptr, gi * V + hv, 1.0f, tg);
@@ -483,15 +490,15 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
                 if (A > 0 && !a.affine_resident) {
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&affine_empty[aslot_k]);
+                    wa.next();
                 }
             }
-            aj_w += g.nch;
             const long long n_head = (c == 0 && wt == 0) ? g.s.h0 : 0;
             const long long n_tail = (c == P - 1 && wt == Tw - 1) ? g.s.t0 : 0;
             for (int e = 0; e < 2; ++e)
                 for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) {
                     const long long i = e == 0 ? k : g.s.h0 + g.s.G * V + k;
-                    const float gm = (OP != OP_SOFTMAX && a.gamma) ? a.gamma[i] : 1.0f;
+                    const float gm = ((OP == OP_LN || OP == OP_RMS) && a.gamma) ? a.gamma[i] : 1.0f;
                     const float bt = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
                     store_one<TOUT>(out_row + i * osz, h(edge_x(g, e, k), gm, bt));
                 }

@@ -72,6 +72,37 @@ struct RowArgs {
 constexpr int kMaxCluster = 16;
 constexpr int kMaxChunkBytes = 16384;  // default (and largest) staged chunk
 
+// Position of a role in a ring of n slots that it uses in order: the slot of
+// its next use and the number of completed laps (the phase parity an
+// mbarrier of that slot is at).  Kept incrementally, so the per-chunk loops
+// never divide a running 64-bit chunk count by the ring size.
+struct RingPos {
+    int slot = 0, n = 1;
+    uint32_t lap = 0;
+    __device__ __forceinline__ explicit RingPos(int slots) : n(slots) {}
+    __device__ __forceinline__ void next() {
+        if (++slot == n) {
+            slot = 0;
+            ++lap;
+        }
+    }
+    // parity of this lap's phase (a consumer waiting for the slot to fill)
+    __device__ __forceinline__ uint32_t parity() const { return lap & 1u; }
+    // parity of the previous lap's release (a producer reusing the slot)
+    __device__ __forceinline__ uint32_t prev_parity() const { return (lap - 1u) & 1u; }
+    // the position k uses later (k >= 0; one subtraction per lap crossed)
+    __device__ __forceinline__ RingPos at(int k) const {
+        RingPos r(*this);
+        r.slot += k;
+        while (r.slot >= r.n) {
+            r.slot -= r.n;
+            ++r.lap;
+        }
+        return r;
+    }
+    __device__ __forceinline__ void advance(int k) { *this = at(k); }
+};
+
 struct RowSlice {
     long long h0;          // head elements (rank 0)
     long long G;           // full 16-byte groups after the head
@@ -151,7 +182,7 @@ __device__ __forceinline__ Stats combine_partials(const float *p, int stride, in
         float am = 0.0f;
         for (int c = 0; c < P; ++c) am = fmaxf(am, p[c * stride]);
         st.a = am > 0.0f ? __fdiv_rn(am, 127.0f) : 1.0f;  // the row scale
-        st.b = 0.0f;
+        st.b = __frcp_rn(st.a);                              // its correctly rounded reciprocal
     } else {
         float ss = 0.0f;
         for (int c = 0; c < P; ++c) ss += p[c * stride];
@@ -692,8 +723,8 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
         g.in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
         return g;
     };
-    auto chunk_ptr = [&](long long j, int k) -> const unsigned char * {
-        return ring + static_cast<size_t>((j + k) % K) * CH;
+    auto chunk_ptr = [&](const RingPos &rb, int k) -> const unsigned char * {
+        return ring + static_cast<size_t>(rb.at(k).slot) * CH;
     };
     auto chunk_groups = [&](const RowGeo &g, int k) -> int {
         const long long r = g.ng - static_cast<long long>(k) * gpc;
@@ -707,15 +738,15 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
     if (tid >= Tp) {
         // ========================================================== producer
         if (tid == Tp) {
-            long long j = 0;
+            RingPos rp(K);
             int prr = 0;
             for (long long row = cl; row < a.rows; row += ncl) {
                 const RowGeo g = geo(row);
                 const long long body = g.ng * 16;
                 const unsigned char *src = g.in_row + g.s.h0 * isz + g.s.g_lo * 16;
-                for (long long off = 0; off < body; off += CH, ++j) {
-                    const int slot = static_cast<int>(j % K);
-                    if (j >= K) mbar_wait_bounded(&empty[slot], static_cast<uint32_t>(((j / K) - 1) & 1), a.err);
+                for (long long off = 0; off < body; off += CH, rp.next()) {
+                    const int slot = rp.slot;
+                    if (rp.lap > 0) mbar_wait_bounded(&empty[slot], rp.prev_parity(), a.err);
                     const uint32_t bytes = static_cast<uint32_t>(body - off < CH ? body - off : CH);
                     mbar_arrive_expect_tx(&full[slot], bytes);
                     bulk_g2s(ring + static_cast<size_t>(slot) * CH, src + off, bytes, &full[slot]);
@@ -725,14 +756,13 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
         } else if (tid == Tp + 1 && A > 0) {
             // gamma / beta segments of every chunk, in the writers' order
             // (resident: the first row's chunks only, one slot each)
-            long long aj = 0;
+            RingPos ap(A);
             for (long long row = cl; row < a.rows && !(a.affine_resident && row > cl); row += ncl) {
                 const RowGeo g = geo(row);
                 const long long i_base = g.s.h0 + g.s.g_lo * V;
-                for (int k = 0; k < g.nch; ++k, ++aj) {
-                    const int slot = static_cast<int>(aj % A);
-                    if (aj >= A && !a.affine_resident)
-                        mbar_wait_bounded(&affine_empty[slot], static_cast<uint32_t>(((aj / A) - 1) & 1), a.err);
+                for (int k = 0; k < g.nch; ++k, ap.next()) {
+                    const int slot = ap.slot;
+                    if (ap.lap > 0 && !a.affine_resident) mbar_wait_bounded(&affine_empty[slot], ap.prev_parity(), a.err);
                     const uint32_t bytes = static_cast<uint32_t>(chunk_groups(g, k)) * V * 4;
                     const long long e0 = i_base + static_cast<long long>(k) * gpc * V;
                     unsigned char *dst = aring + static_cast<size_t>(slot) * aslot;
@@ -745,7 +775,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
         __syncwarp();
     } else if (tid < Tr) {
         // ========================================================== reducers
-        long long j = 0;
+        RingPos rb(K);  // ring position of the current row's first chunk
         int rr = 0;
         for (long long row = cl; row < a.rows; row += ncl, ++rr) {
             const RowGeo g = geo(row);
@@ -761,9 +791,9 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
             {
                 Stream<OP> acc;
                 for (int k = 0; k < g.nch; ++k) {
-                    const long long jk = j + k;
-                    mbar_wait_bounded(&full[jk % K], static_cast<uint32_t>((jk / K) & 1), a.err);
-                    visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), tid, Tr, g.in_sc,
+                    const RingPos pk = rb.at(k);
+                    mbar_wait_bounded(&full[pk.slot], pk.parity(), a.err);
+                    visit_chunk<TIN>(chunk_ptr(rb, k), chunk_groups(g, k), tid, Tr, g.in_sc,
                                      [&](int, const float(&f)[V]) { acc.add(f); });
                 }
                 for (int e = 0; e < 2; ++e)
@@ -800,7 +830,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                 float am = 0.0f;
                 for (int k = 0; k < g.nch; ++k) {
                     const long long kg = static_cast<long long>(k) * gpc;
-                    visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), tid, Tr, g.in_sc,
+                    visit_chunk<TIN>(chunk_ptr(rb, k), chunk_groups(g, k), tid, Tr, g.in_sc,
                                      [&](int gi, const float(&f)[V]) {
 #pragma unroll
                                          for (int hv = 0; hv < V; hv += SV) {
@@ -849,12 +879,13 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                 pub[par * 8 + 2] = qmul;
                 mbar_arrive(&stats_full[par]);
             }
-            j += g.nch;
+            rb.advance(g.nch);
         }
     } else {
         // ========================================================== writers
         const int wt = tid - Tr;
-        long long j = 0, aj_w = 0;
+        RingPos rb(K);                // ring position of the current row's first chunk
+        RingPos wb(A > 0 ? A : 1);    // affine ring position of its first chunk
         int rr = 0;
         for (long long row = cl; row < a.rows; row += ncl, ++rr) {
             const RowGeo g = geo(row);
@@ -870,7 +901,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
             if constexpr (OP == OP_LSE) {
                 for (int k = 0; k < g.nch; ++k) {
                     __syncwarp();
-                    if ((wt & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
+                    if ((wt & 31) == 0) mbar_arrive(&empty[rb.at(k).slot]);
                 }
             } else {
                 unsigned char *out_row = a.out + row * a.ld_out * osz;
@@ -883,28 +914,28 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                 const float smul = (TOUT == DT_E4M3) ? 448.0f : inv;  // softmax: y (or its code) = exp(x - M) * smul
                 auto h = [&](float x, float gm, float bt) -> float {
                     if constexpr (OP == OP_SOFTMAX) return exp_fast(x - st.a) * smul;
-                    else if constexpr (OP == OP_Q8) return q8_code(x, st.a);
+                    else if constexpr (OP == OP_Q8) return q8_code(x, st.a, st.b);
                     else return norm_h<OP>(x, st, gm, bt) * qmul;
                 };
                 for (int k = 0; k < g.nch; ++k) {
                     const long long kg = static_cast<long long>(k) * gpc;
-                    const int aslot_k = A > 0 ? (a.affine_resident ? k : static_cast<int>((aj_w + k) % A)) : 0;
+                    const int aslot_k = A > 0 ? (a.affine_resident ? k : wb.at(k).slot) : 0;
                     const float *ag = reinterpret_cast<const float *>(aring + static_cast<size_t>(aslot_k) * aslot);
                     const float *ab = ag + (has_g ? gpc * V : 0);
                     if (A > 0 && (!a.affine_resident || rr == 0))
                         mbar_wait_bounded(&affine_full[aslot_k],
-                                          a.affine_resident ? 0u : static_cast<uint32_t>(((aj_w + k) / A) & 1), a.err);
+                                          a.affine_resident ? 0u : wb.at(k).parity(), a.err);
                     if constexpr (OP == OP_LN || OP == OP_RMS) {
                         if (A == 0 && g_vec && b_vec && (has_g || has_b)) {
-                            write_chunk_direct<OP, TIN, TOUT>(chunk_ptr(j, k), chunk_groups(g, k), wt, Tw, g.in_sc,
+                            write_chunk_direct<OP, TIN, TOUT>(chunk_ptr(rb, k), chunk_groups(g, k), wt, Tw, g.in_sc,
                                                               has_g ? a.gamma : nullptr, has_b ? a.beta : nullptr,
                                                               i_base + kg * V, out_row, out_vec, h);
                             __syncwarp();
-                            if ((wt & 31) == 0) mbar_arrive(&empty[(j + k) % K]);
+                            if ((wt & 31) == 0) mbar_arrive(&empty[rb.at(k).slot]);
                             continue;
                         }
                     }
-                    visit_chunk<TIN>(chunk_ptr(j, k), chunk_groups(g, k), wt, Tw, g.in_sc,
+                    visit_chunk<TIN>(chunk_ptr(rb, k), chunk_groups(g, k), wt, Tw, g.in_sc,
                                      [&](int gi, const float(&f)[V]) {
 #pragma unroll
                                          for (int hv = 0; hv < V; hv += SV) {
@@ -927,11 +958,11 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                                      });
                     __syncwarp();
                     if ((wt & 31) == 0) {
-                        mbar_arrive(&empty[(j + k) % K]);
+                        mbar_arrive(&empty[rb.at(k).slot]);
                         if (A > 0 && !a.affine_resident) mbar_arrive(&affine_empty[aslot_k]);
                     }
                 }
-                aj_w += g.nch;
+                wb.advance(g.nch);
                 const long long n_head = (c == 0 && wt == 0) ? g.s.h0 : 0;
                 const long long n_tail = (c == P - 1 && wt == Tw - 1) ? g.s.t0 : 0;
                 for (int e = 0; e < 2; ++e)
@@ -943,7 +974,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                     }
             }
             if (wt == 0) trace_stamp(a, rr, 4);
-            j += g.nch;
+            rb.advance(g.nch);
         }
     }
     if (P > 1) {
@@ -1051,11 +1082,11 @@ __device__ __forceinline__ void apply_sweep(const RowArgs &a, long long row, con
         sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
             float y[V];
 #pragma unroll
-            for (int j = 0; j < V; ++j) y[j] = q8_code(f[j], st.a);
+            for (int j = 0; j < V; ++j) y[j] = q8_code(f[j], st.a, st.b);
             store_group<TOUT, V>(out_row + i0 * osz, y, out_vec);
         });
         sweep_edges<TIN>(in_row, s, P, c, in_sc,
-                         [&](long long i, float x) { store_one<TOUT>(out_row + i * osz, q8_code(x, st.a)); });
+                         [&](long long i, float x) { store_one<TOUT>(out_row + i * osz, q8_code(x, st.a, st.b)); });
     } else {
         sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
             float gg[V], bb[V], y[V];

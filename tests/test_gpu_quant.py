@@ -63,6 +63,9 @@ PLANS = {
     "cluster4": C.make_plan(C.PATH_CLUSTER, 4),
     "cluster8": C.make_plan(C.PATH_CLUSTER, 8),
     "cluster16": C.make_plan(C.PATH_CLUSTER, 16),
+    "one_cta_tm": C.make_plan(C.PATH_ONE_CTA, retain=C.RETAIN_TMEM),
+    "cluster4_tm": C.make_plan(C.PATH_CLUSTER, 4, retain=C.RETAIN_TMEM),
+    "cluster16_tm": C.make_plan(C.PATH_CLUSTER, 16, retain=C.RETAIN_TMEM),
     "two_pass_g1": C.make_plan(C.PATH_TWO_PASS, ctas_per_row=1),
     "two_pass_g3": C.make_plan(C.PATH_TWO_PASS, ctas_per_row=3),
     "auto": None,
@@ -81,13 +84,40 @@ def test_quant_fp32_bit_exact(plan, cols):
         if C.plan_check(C.QUANT_INT8, xd, q0, p, out_dtype=C.INT8, out_scale=s0) != C.OK:
             # only a slice beyond one CTA's shared memory (Eq. 3) may be refused
             P = 1 if p.path == C.PATH_ONE_CTA else p.cluster_size
-            assert -(-cols * 4 // P) > C.slice_capacity(C.F32) * 4 - 4096
+            cap = 131072 if p.retain == C.RETAIN_TMEM else C.slice_capacity(C.F32) * 4 - 4096
+            assert -(-cols * 4 // P) > cap
             return
     q, s = run(xd, p)
     qr, sr = expected(x)
     assert np.array_equal(s.view(np.uint32), sr.view(np.uint32))
     assert np.array_equal(q, qr)
     assert (s[0] == 1.0) and (q[0] == 0).all()
+
+
+@pytest.mark.parametrize("plan", ["one_cta", "cluster4", "cluster4_tm", "two_pass_g1", "two_pass_g3"])
+def test_quant_near_ties_bit_exact(plan):
+    """Values within a few FP32 ulps of s (k + 1/2) for scales that are not powers of two: the codes are
+    decided by the correctly rounded quotient, which a product with the reciprocal can miss by an ulp."""
+    rows, cols = 24, 4096
+    r = np.random.default_rng(7)
+    x = np.zeros((rows, cols), dtype=np.float32)
+    for i in range(rows):
+        amax = np.float32(r.uniform(1.0, 2.0) * 2.0 ** r.integers(-30, 30))
+        s = np.float32(amax / np.float32(127))
+        k = r.integers(-127, 127, cols).astype(np.float32)
+        base = (s.astype(np.float64) * (k + 0.5)).astype(np.float32)
+        m = r.integers(-4, 5, cols)
+        v = base.copy()
+        for step in range(1, 5):  # move m ulps towards +-inf
+            v = np.where(m >= step, np.nextafter(v, np.float32(np.inf)), v)
+            v = np.where(-m >= step, np.nextafter(v, np.float32(-np.inf)), v)
+        v = np.clip(v, -amax, amax)
+        v[0] = amax
+        x[i] = v
+    xt = torch.from_numpy(x)
+    q, sc = run(xt.cuda(), PLANS[plan])
+    qr, sr = expected(xt)
+    assert np.array_equal(sc, sr) and np.array_equal(q, qr)
 
 
 @pytest.mark.parametrize("plan", ["one_cta", "cluster4", "two_pass_g1", "two_pass_g3"])
@@ -110,7 +140,8 @@ def test_quant_bf16_rows_and_unaligned_strides(plan):
 def test_quant_many_rows_recycle_the_staged_buffers():
     x = rows_input(3000, 20000, seed=9)
     qr, sr = expected(x)
-    for p in (C.make_plan(C.PATH_CLUSTER, 4), C.make_plan(C.PATH_CLUSTER, 16), C.make_plan(C.PATH_ONE_CTA)):
+    for p in (C.make_plan(C.PATH_CLUSTER, 4), C.make_plan(C.PATH_CLUSTER, 16), C.make_plan(C.PATH_ONE_CTA),
+              C.make_plan(C.PATH_CLUSTER, 2, retain=C.RETAIN_TMEM), C.make_plan(C.PATH_CLUSTER, 8, retain=C.RETAIN_TMEM)):
         q, s = run(x.cuda(), p)
         assert np.array_equal(q, qr) and np.array_equal(s, sr)
 
