@@ -536,6 +536,11 @@ credit_status credit_mlp_predict(const float *X, int64_t n, float *out);
  * floats).  For checking the kernels. */
 credit_status credit_mlp_grad(const float *params, const float *X, const float *t, int64_t n, float *grad,
                               float *loss);
+/* One Adam step (Kingma & Ba; b1 = 0.9, b2 = 0.999, eps = 1e-8, step = 1, 2,
+ * ...) of the training kernel on host arrays of credit_mlp_num_params()
+ * floats: params, m and v are updated in place from grad.  For checking the
+ * kernel.  CREDIT_ERR_INVALID_ARG for NULL arrays, step < 1 or lr <= 0. */
+credit_status credit_mlp_adam_step(float *params, const float *grad, float *m, float *v, int32_t step, float lr);
 credit_status credit_mlp_save(const char *path);
 credit_status credit_mlp_load(const char *path);
 

@@ -191,6 +191,8 @@ def _extra_prototypes(L):
     L.credit_mlp_predict.argtypes = [fp, i64, fp]
     L.credit_mlp_grad.restype = i32
     L.credit_mlp_grad.argtypes = [fp, fp, fp, i64, fp, fp]
+    L.credit_mlp_adam_step.restype = i32
+    L.credit_mlp_adam_step.argtypes = [fp, fp, fp, fp, i32, ctypes.c_float]
     L.credit_mlp_save.restype = i32
     L.credit_mlp_save.argtypes = [ctypes.c_char_p]
     L.credit_mlp_load.restype = i32
@@ -535,6 +537,18 @@ def mlp_grad(params, X, t):
     _check(lib().credit_mlp_grad(_fptr(params), _fptr(X), _fptr(t), X.shape[0], _fptr(g), _fptr(loss)),
            "credit_mlp_grad")
     return float(loss[0]), g
+
+
+def mlp_adam_step(params, grad, m, v, step: int, lr: float):
+    """One Adam step of the training kernel: returns the new (params, m, v)."""
+    import numpy as np
+    p = np.array(params, dtype=np.float32)
+    mm = np.array(m, dtype=np.float32)
+    vv = np.array(v, dtype=np.float32)
+    g = np.ascontiguousarray(grad, dtype=np.float32)
+    _check(lib().credit_mlp_adam_step(_fptr(p), _fptr(g), _fptr(mm), _fptr(vv), int(step), float(lr)),
+           "credit_mlp_adam_step")
+    return p, mm, vv
 
 
 def mlp_save(path: str):

@@ -165,6 +165,13 @@ struct Dev {
             in = out;
         }
     }
+    // Adam step number `step` (1, 2, ...) on p from g, with the moments m, v
+    void adam(int step, float lr) {
+        const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+        const float c1 = 1.0f - std::pow(b1, static_cast<float>(step));
+        const float c2 = 1.0f - std::pow(b2, static_cast<float>(step));
+        k_adam<<<blocks(kParams, 256), 256>>>(p, g, m, v, kParams, lr, b1, b2, eps, c1, c2);
+    }
     // backward into g (forward must have run on the same batch)
     void backward(int n) {
         k_out_delta<<<blocks(n, 256), 256>>>(y, t, dy, n);
@@ -354,9 +361,26 @@ credit_status credit_mlp_grad(const float *params, const float *X, const float *
     return CREDIT_OK;
 }
 
-// Train from scratch: n samples (host X n x 16, targets = log2 us), minibatch
-// Adam.  loss_curve (may be NULL) receives the training MSE (standardised)
-// after each epoch.
+// One Adam step of the training kernel on host arrays (params, m, v updated
+// in place from grad), for checking the kernel against an FP64 reference.
+credit_status credit_mlp_adam_step(float *params, const float *grad, float *m, float *v, int32_t step, float lr) {
+    if (!params || !grad || !m || !v || step < 1 || !(lr > 0.0f)) return CREDIT_ERR_INVALID_ARG;
+    Dev d;
+    if (!d.alloc(1)) {
+        d.release();
+        return CREDIT_ERR_CUDA;
+    }
+    cudaMemcpy(d.p, params, kParams * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d.g, grad, kParams * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d.m, m, kParams * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d.v, v, kParams * 4, cudaMemcpyHostToDevice);
+    d.adam(step, lr);
+    cudaError_t e = cudaMemcpy(params, d.p, kParams * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(m, d.m, kParams * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(v, d.v, kParams * 4, cudaMemcpyDeviceToHost);
+    d.release();
+    return e == cudaSuccess ? CREDIT_OK : CREDIT_ERR_CUDA;
+}
 }  // extern "C"
 
 namespace credit {
@@ -407,7 +431,6 @@ credit_status train_one(const float *X, const float *y, int64_t n, int32_t epoch
     std::iota(perm.begin(), perm.end(), 0);
     std::vector<float> bx(static_cast<size_t>(B) * kIn), bt(B);
     int step = 0;
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     for (int ep = 0; ep < epochs; ++ep) {
         std::shuffle(perm.begin(), perm.end(), rng);
         double ep_loss = 0.0;
@@ -421,10 +444,7 @@ credit_status train_one(const float *X, const float *y, int64_t n, int32_t epoch
             cudaMemcpy(d.t, bt.data(), bt.size() * 4, cudaMemcpyHostToDevice);
             d.forward(B);
             d.backward(B);
-            ++step;
-            const float c1 = 1.0f - std::pow(b1, static_cast<float>(step));
-            const float c2 = 1.0f - std::pow(b2, static_cast<float>(step));
-            k_adam<<<blocks(kParams, 256), 256>>>(d.p, d.g, d.m, d.v, kParams, lr, b1, b2, eps, c1, c2);
+            d.adam(++step, lr);
             if (loss_curve) {
                 k_sse<<<1, 256>>>(d.y, d.t, B, d.loss);
                 float sse = 0;

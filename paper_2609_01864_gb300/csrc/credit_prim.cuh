@@ -277,6 +277,25 @@ __device__ __forceinline__ float q8_code(float x, float s, float inv) {
     if (!(fabsf(fabsf(t - k) - 0.5f) >= 0x1p-14f)) k = rintf(__fdiv_rn(x, s));
     return fminf(fmaxf(k, -127.0f), 127.0f);
 }
+// The same codes for N elements with one branch: if any product lies within
+// 2^-14 of a half-integer (or is not finite), all N are taken from the exact
+// quotients.
+template <int N>
+__device__ __forceinline__ void q8_codes(const float (&x)[N], float s, float inv, float (&y)[N]) {
+    bool near = false;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        const float t = x[q] * inv;
+        y[q] = rintf(t);
+        near |= !(fabsf(fabsf(t - y[q]) - 0.5f) >= 0x1p-14f);
+    }
+    if (near) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) y[q] = rintf(__fdiv_rn(x[q], s));
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) y[q] = fminf(fmaxf(y[q], -127.0f), 127.0f);
+}
 
 // Decode one 16-byte group (already loaded as uint4) into floats.
 template <int DT>
@@ -349,13 +368,15 @@ __device__ __forceinline__ void pack_words(const float (&y)[V], uint32_t (&w)[(V
             __nv_bfloat162 b = __floats2bfloat162_rn(y[2 * k], y[2 * k + 1]);
             w[k] = *reinterpret_cast<uint32_t *>(&b);
         }
-    } else if constexpr (DT == DT_I8) {  // y holds integers in [-127, 127]
+    } else if constexpr (DT == DT_I8) {  // y holds integers in [-127, 127]: low bytes of their int values
 #pragma unroll
-        for (int k = 0; k < V / 4; ++k)
-            w[k] = (static_cast<uint32_t>(static_cast<int>(y[4 * k])) & 0xFFu) |
-                   ((static_cast<uint32_t>(static_cast<int>(y[4 * k + 1])) & 0xFFu) << 8) |
-                   ((static_cast<uint32_t>(static_cast<int>(y[4 * k + 2])) & 0xFFu) << 16) |
-                   (static_cast<uint32_t>(static_cast<int>(y[4 * k + 3])) << 24);
+        for (int k = 0; k < V / 4; ++k) {
+            const uint32_t b0 = static_cast<uint32_t>(__float2int_rz(y[4 * k]));
+            const uint32_t b1 = static_cast<uint32_t>(__float2int_rz(y[4 * k + 1]));
+            const uint32_t b2 = static_cast<uint32_t>(__float2int_rz(y[4 * k + 2]));
+            const uint32_t b3 = static_cast<uint32_t>(__float2int_rz(y[4 * k + 3]));
+            w[k] = __byte_perm(__byte_perm(b0, b1, 0x0040), __byte_perm(b2, b3, 0x0040), 0x5410);
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < V / 4; ++k) {

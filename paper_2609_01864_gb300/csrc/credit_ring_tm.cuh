@@ -428,6 +428,47 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
                     mbar_wait_bounded(&affine_full[aslot_k], a.affine_resident ? 0u : wa.parity(), a.err);
                 uint32_t w[4 * kTmHalf];
                 tm_ld16(tb + static_cast<uint32_t>(k * kTmColsPerChunk + half * 4 * kTmHalf), w);
+                // Fast path: every one of this thread's kTmHalf groups lies in the chunk (its last one,
+                // twin + (half * kTmHalf + kTmHalf - 1) * TL, is below gn; a chunk can hold fewer than
+                // TL * kTmGroups groups), vector stores, gamma / beta (where the op has them) staged in shared
+                // memory -- no per-group bounds or pointer tests, 32-bit offsets from the chunk's output base.
+                constexpr bool kNormOp = OP == OP_LN || OP == OP_RMS;
+                const bool fast = out_vec && twin + (half * kTmHalf + kTmHalf - 1) * TL < gn &&
+                                  (!kNormOp || (A > 0 && has_g && (OP != OP_LN || has_b)));
+                if (fast) {
+                    unsigned char *oc = out_row + (i_base + kg * V) * osz;
+                    float gg[kTmHalf][kNormOp ? V : 1], bb[kTmHalf][OP == OP_LN ? V : 1];
+                    if constexpr (kNormOp) {
+#pragma unroll
+                        for (int m = 0; m < kTmHalf; ++m) {
+                            const int gi = twin + (half * kTmHalf + m) * TL;
+                            lds_f32<V>(ag + gi * V, gg[m]);
+                            if constexpr (OP == OP_LN) lds_f32<V>(ab + gi * V, bb[m]);
+                        }
+                    }
+#pragma unroll
+                    for (int m = 0; m < kTmHalf; ++m) {
+                        const int gi = twin + (half * kTmHalf + m) * TL;
+                        float f[V];
+                        decode_group<TIN>(make_uint4(w[4 * m], w[4 * m + 1], w[4 * m + 2], w[4 * m + 3]), f, g.in_sc);
+#pragma unroll
+                        for (int hv = 0; hv < V; hv += SV) {
+                            float y[SV];
+                            if constexpr (OP == OP_Q8) {
+                                float xs[SV];
+#pragma unroll
+                                for (int q = 0; q < SV; ++q) xs[q] = f[hv + q];
+                                q8_codes<SV>(xs, st.a, st.b, y);
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < SV; ++q)
+                                    y[q] = h(f[hv + q], kNormOp ? gg[m][kNormOp ? hv + q : 0] : 1.0f,
+                                             OP == OP_LN ? bb[m][OP == OP_LN ? hv + q : 0] : 0.0f);
+                            }
+                            store_group<TOUT, SV>(oc + static_cast<uint32_t>((gi * V + hv) * osz), y, true);
+                        }
+                    }
+                } else {
                 // gamma / beta for the groups of this chunk, batch by batch (L2 loads issued together)
                 constexpr int MB = (V == 4) ? 4 : (V == 8 ? 2 : 1);
 #pragma unroll
@@ -486,6 +527,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
                             store_group<TOUT, SV>(out_row + (i0 + hv) * osz, y, out_vec);
                         }
                     }
+                }
                 }
                 if (A > 0 && !a.affine_resident) {
                     __syncwarp();

@@ -235,6 +235,17 @@ __device__ __forceinline__ void load_affine_smem(const float *p, int off, float 
     }
 }
 
+// N floats from shared memory at p (16-byte aligned), 16 bytes per load.
+template <int N>
+__device__ __forceinline__ void lds_f32(const float *p, float (&v)[N]) {
+    const uint32_t base = smem_addr(p);
+#pragma unroll
+    for (int k = 0; k < N / 4; ++k)
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v[4 * k]), "=f"(v[4 * k + 1]), "=f"(v[4 * k + 2]), "=f"(v[4 * k + 3])
+                     : "r"(base + 16 * k));
+}
+
 __device__ __forceinline__ void copy_raw(unsigned char *dst, const unsigned char *src, int isz) {
     if (isz == 4) *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(src);
     else if (isz == 2) *reinterpret_cast<uint16_t *>(dst) = *reinterpret_cast<const uint16_t *>(src);
@@ -1081,8 +1092,7 @@ __device__ __forceinline__ void apply_sweep(const RowArgs &a, long long row, con
     } else if constexpr (OP == OP_Q8) {
         sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
             float y[V];
-#pragma unroll
-            for (int j = 0; j < V; ++j) y[j] = q8_code(f[j], st.a, st.b);
+            q8_codes<V>(f, st.a, st.b, y);
             store_group<TOUT, V>(out_row + i0 * osz, y, out_vec);
         });
         sweep_edges<TIN>(in_row, s, P, c, in_sc,
