@@ -70,7 +70,8 @@ typedef enum {
      * reduction (amax, q = 1) whose statistic is applied to every element of
      * the row: 5 bytes per FP32 element when the row is read once, 9 with the
      * global reread.  Staged (ONE_CTA / CLUSTER, either retention tier) and
-     * TWO_PASS plans; the planner uses its built-in rule (source 3). */
+     * TWO_PASS plans.  Planner rule (source 3): the smallest cluster whose
+     * slices fit the tensor-memory tier, else two-pass. */
     CREDIT_OP_QUANT_INT8 = 11
 } credit_op;
 

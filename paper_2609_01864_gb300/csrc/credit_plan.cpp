@@ -63,10 +63,34 @@ int two_pass_split(int sm_count, long long rows, long long cols, int isz) {
     return static_cast<int>(G < 1 ? 1 : G);
 }
 
+// Rule for int8 quantisation (measured on GB300, 4096 rows of 16K-256K FP32
+// columns): the smallest cluster whose slices fit the tensor-memory tier
+// (128 KiB); the fewest CTAs per row keeps the most rows in flight and the
+// exchange shortest.  Two-pass when no staged plan fits.
+static bool quant_plan(const DeviceInfo &di, int device, long long rows, long long cols, int tin, credit_plan_t *p) {
+    const int isz = dtype_size(tin);
+    for (int P : {1, 2, 4, 8, 16}) {
+        RingCfg rc;
+        if (!ring_config_tm(di, cols, isz, P, 0, 0, 0, &rc)) continue;
+        if (ring_max_clusters(device, CREDIT_OP_QUANT_INT8, tin, CREDIT_INT8, P, rc.threads, rc.smem, true) <= 0) continue;
+        p->path = P == 1 ? CREDIT_PATH_ONE_CTA : CREDIT_PATH_CLUSTER;
+        p->cluster_size = P;
+        p->ctas_per_row = P;
+        p->retain = CREDIT_RETAIN_TMEM;
+        p->smem_bytes = rc.smem;
+        return true;
+    }
+    p->path = CREDIT_PATH_TWO_PASS;
+    p->cluster_size = 1;
+    p->ctas_per_row = two_pass_split(di.sm_count, rows, cols, isz);
+    return true;
+}
+
 void heuristic_plan(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin, int tout,
                     credit_plan_t *p) {
     std::memset(p, 0, sizeof(*p));
     p->source = 3;
+    if (op == CREDIT_OP_QUANT_INT8 && quant_plan(di, device, rows, cols, tin, p)) return;
     const int isz = dtype_size(tin);
     if (op != 1) {
         // Smallest P whose slice is <= 64 KiB, else the smallest P that fits.

@@ -263,38 +263,45 @@ template <> struct Fmt<DT_I8> {
     static constexpr int V = 16;
 };
 
-// Row-wise int8 code of x with the row scale s (s = amax / 127 in FP32) and
-// inv = the correctly rounded 1 / s: the correctly rounded FP32 quotient
-// x / s, rounded to the nearest integer with ties to even, clamped to +-127;
-// returned as a float holding the integer.  |x / s| <= 127.00001, so
-// t = x * inv is within 3 * 2^-24 * 128 < 2^-15 of the rounded quotient (three
-// roundings, each of relative size <= 2^-24): rint(t) is the same integer
-// unless t lies within 2^-14 of a half-integer, and only then (and for a
-// non-finite t) is the quotient itself computed.
+// Row-wise int8 codes.  With the row scale s = fl(amax / 127) and inv = the
+// correctly rounded 1 / s, the code of x is rint(fl(x / s)) (ties to even),
+// clamped to +-127.  The codes are carried as "biased" floats u = code +
+// kQ8Bias: for an integer |k| < 2^22 the bits of k + 1.5 * 2^23 are
+// 0x4B400000 + k, so the low byte of u's bits is k's two's-complement byte
+// (the packing below reads it directly).  Fast path: t = x * inv is within
+// 3 * 2^-24 * 128 < 2^-15 of fl(x / s) (three roundings of relative size
+// <= 2^-24, |x / s| <= 127.00001 when s is normal), so t + kQ8Bias, rounded
+// to the nearest integer with ties to even, carries the same code unless t
+// lies within 2^-14 of a half-integer; |rint(t)| <= 127 needs no clamp.  Near
+// a half-integer, for a non-finite t, or for a subnormal s (whose rounding
+// can push x / s past 127.5), the exact quotient decides, clamped.
+constexpr float kQ8Bias = 12582912.0f;  // 1.5 * 2^23
+__device__ __forceinline__ float q8_exact(float x, float s) {
+    return fminf(fmaxf(rintf(__fdiv_rn(x, s)), -127.0f), 127.0f) + kQ8Bias;
+}
+__device__ __forceinline__ bool q8_near(float t, float u) {
+    return !(fabsf(fabsf(t - (u - kQ8Bias)) - 0.5f) >= 0x1p-14f);
+}
 __device__ __forceinline__ float q8_code(float x, float s, float inv) {
     const float t = x * inv;
-    float k = rintf(t);
-    if (!(fabsf(fabsf(t - k) - 0.5f) >= 0x1p-14f)) k = rintf(__fdiv_rn(x, s));
-    return fminf(fmaxf(k, -127.0f), 127.0f);
+    const float u = t + kQ8Bias;
+    return (q8_near(t, u) || !(s >= 0x1p-126f)) ? q8_exact(x, s) : u;
 }
-// The same codes for N elements with one branch: if any product lies within
-// 2^-14 of a half-integer (or is not finite), all N are taken from the exact
-// quotients.
+// The same for N elements with one branch: if any of them needs the exact
+// quotient, all N take it.
 template <int N>
 __device__ __forceinline__ void q8_codes(const float (&x)[N], float s, float inv, float (&y)[N]) {
-    bool near = false;
+    bool near = !(s >= 0x1p-126f);
 #pragma unroll
     for (int q = 0; q < N; ++q) {
         const float t = x[q] * inv;
-        y[q] = rintf(t);
-        near |= !(fabsf(fabsf(t - y[q]) - 0.5f) >= 0x1p-14f);
+        y[q] = t + kQ8Bias;
+        near |= q8_near(t, y[q]);
     }
     if (near) {
 #pragma unroll
-        for (int q = 0; q < N; ++q) y[q] = rintf(__fdiv_rn(x[q], s));
+        for (int q = 0; q < N; ++q) y[q] = q8_exact(x[q], s);
     }
-#pragma unroll
-    for (int q = 0; q < N; ++q) y[q] = fminf(fmaxf(y[q], -127.0f), 127.0f);
 }
 
 // Decode one 16-byte group (already loaded as uint4) into floats.
@@ -349,8 +356,8 @@ __device__ __forceinline__ void store_one(unsigned char *p, float v) {
     } else if constexpr (DT == DT_BF16) {
         __nv_bfloat16 b = __float2bfloat16_rn(v);
         *reinterpret_cast<__nv_bfloat16 *>(p) = b;
-    } else if constexpr (DT == DT_I8) {
-        *reinterpret_cast<signed char *>(p) = static_cast<signed char>(static_cast<int>(v));
+    } else if constexpr (DT == DT_I8) {  // v is a biased code (q8_code): its low byte
+        *p = static_cast<unsigned char>(__float_as_uint(v) & 0xFFu);
     } else {
         *p = static_cast<unsigned char>(__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3));
     }
@@ -368,15 +375,12 @@ __device__ __forceinline__ void pack_words(const float (&y)[V], uint32_t (&w)[(V
             __nv_bfloat162 b = __floats2bfloat162_rn(y[2 * k], y[2 * k + 1]);
             w[k] = *reinterpret_cast<uint32_t *>(&b);
         }
-    } else if constexpr (DT == DT_I8) {  // y holds integers in [-127, 127]: low bytes of their int values
+    } else if constexpr (DT == DT_I8) {  // y holds biased codes (q8_code): the low byte of each
 #pragma unroll
-        for (int k = 0; k < V / 4; ++k) {
-            const uint32_t b0 = static_cast<uint32_t>(__float2int_rz(y[4 * k]));
-            const uint32_t b1 = static_cast<uint32_t>(__float2int_rz(y[4 * k + 1]));
-            const uint32_t b2 = static_cast<uint32_t>(__float2int_rz(y[4 * k + 2]));
-            const uint32_t b3 = static_cast<uint32_t>(__float2int_rz(y[4 * k + 3]));
-            w[k] = __byte_perm(__byte_perm(b0, b1, 0x0040), __byte_perm(b2, b3, 0x0040), 0x5410);
-        }
+        for (int k = 0; k < V / 4; ++k)
+            w[k] = __byte_perm(__byte_perm(__float_as_uint(y[4 * k]), __float_as_uint(y[4 * k + 1]), 0x0040),
+                               __byte_perm(__float_as_uint(y[4 * k + 2]), __float_as_uint(y[4 * k + 3]), 0x0040),
+                               0x5410);
     } else {
 #pragma unroll
         for (int k = 0; k < V / 4; ++k) {
