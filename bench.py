@@ -21,13 +21,19 @@ Also reported: speedup of the chosen plans over the best non-DSMEM plan
 (one-CTA staging or two-pass reread) on the same shapes, and the cost model's
 pick accuracy on these shapes (pick within 5% of the measured best candidate);
 `backward`: the gradient ops (softmax, LayerNorm, RMSNorm, softmax from
-logits, cross entropy) over 4096 rows x {16K, 64K, 128K, 256K} FP32, every
-candidate plan timed beside the planner's pick (outside the timed step).
+logits, cross entropy, weighted variance, Pearson correlation) over 4096 rows
+x {16K, 64K, 128K, 256K} FP32; `quant_int8`: row-wise int8 quantisation of
+4096 x {16K, 64K, 256K} FP32 rows; `precision`: softmax and log-sum-exp over
+4096 x {128K, 256K} BF16 / FP8-E4M3 logits N(0, 3^2) with the error of sampled
+rows against the oracle; `ragged`: 20000 BF16 rows of log-uniform width in one
+graph-replayed persistent launch.  In every table each candidate plan is
+timed beside the planner's pick (outside the timed step).  `summary`, last on
+the line, repeats each table's headline figures.
 
 --impl reference  times the FP64 CPU oracle (the reference arm of this
            project) on a bounded sample of the same workload.
---case op:rows:cols:path:P  runs one small case a few times (for profilers; op 4-6 are the
-           backward ops).
+--case op:rows:cols:path:P  runs one small case a few times (for profilers; ops 4-10 are the
+           backward ops, 11 the int8 quantisation).
 """
 from __future__ import annotations
 
@@ -177,21 +183,24 @@ def time_events(fn, reps, warm=1):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def candidates(C, op, x, y, g, b):
+def candidates(C, op, x, y, g=None, b=None, fills=True, **kw):
+    """Every legal plan of one call: one-CTA / cluster P = 2..16 in both retention tiers, fills of cluster
+    plans that leave SMs idle, two-pass G = 1, 2, 4, 8."""
     import torch
     sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    kw = dict(kw, gamma=g, beta=b)
     out = []
     for P in (1, 2, 4, 8, 16):
         legal = []
         for retain, tag in ((C.RETAIN_SMEM, ""), (C.RETAIN_TMEM, "_tm")):
             p = C.make_plan(C.PATH_ONE_CTA if P == 1 else C.PATH_CLUSTER, P, retain=retain)
-            if C.plan_check(op, x, y, p, gamma=g, beta=b) == C.OK:
+            if C.plan_check(op, x, y, p, **kw) == C.OK:
                 name = f"{'one_cta' if P == 1 else 'cluster'}{'' if P == 1 else P}{tag}"
                 out.append((name, p))
                 legal.append((name, retain, p))
-        if P > 1 and legal:  # fills of a cluster plan that leaves SMs idle
+        if fills and P > 1 and legal:  # fills of a cluster plan that leaves SMs idle
             name, retain, p = legal[-1]
-            if sm - P * C.max_clusters(op, x, y, p, gamma=g, beta=b) >= 16:
+            if sm - P * C.max_clusters(op, x, y, p, **kw) >= 16:
                 for f in (0.15, 0.2, 0.3, 0.4):
                     out.append((f"{name}_f{f}", C.make_plan(C.PATH_CLUSTER, P, retain=retain, fill_share=f)))
     for G in (1, 2, 4, 8):
@@ -295,13 +304,20 @@ def run_case(spec: str):
     retain = int(v[5]) if len(v) > 5 else 0
     fill = float(v[6]) if len(v) > 6 else 0.0
     C.init(torch.cuda.current_device())
-    if op >= C.SOFTMAX_BWD:  # backward op: a, dy -> dx
+    if C.SOFTMAX_BWD <= op <= C.PEARSON_BWD:  # backward op: a, dy -> dx (and dx2)
         a = synth.outliers(rows, cols, seed=synth.SEED_DATA, device="cuda")
         dy = synth.normal(rows, cols, seed=synth.SEED_DATA + 1, device="cuda")
         dx = torch.empty_like(a)
         g, _ = synth.gamma_beta(cols, device="cuda")
         st = torch.ones(rows, device="cuda")
-        kw = {} if op == C.SOFTMAX_BWD else dict(gamma=g, rstd=st, mean=st if op == C.LAYERNORM_BWD else None)
+        if op in (C.WVAR_BWD, C.PEARSON_BWD):
+            if op == C.WVAR_BWD:
+                dy = dy.abs() + 0.1  # weights
+            kw = dict(scale=st, dx2=torch.empty_like(a))
+        elif op in (C.LAYERNORM_BWD, C.RMSNORM_BWD):
+            kw = dict(gamma=g, rstd=st, mean=st if op == C.LAYERNORM_BWD else None)
+        else:
+            kw = {}
         plan = None if path < 0 else C.make_plan(path, P, ctas_per_row=P if path == C.PATH_TWO_PASS else 1)
         for _ in range(3):
             C.run_bwd(op, a, dy, dx, plan=plan, **kw)
@@ -310,11 +326,15 @@ def run_case(spec: str):
         print(json.dumps({"case": spec, "launches": C.launch_count()}))
         return 0
     x = synth.outliers(rows, cols, seed=synth.SEED_DATA, device="cuda")
-    y = torch.empty_like(x)
     g, b = synth.gamma_beta(cols, device="cuda")
     plan = None if path < 0 else C.make_plan(path, P, ctas_per_row=P if path == C.PATH_TWO_PASS else 1,
                                              retain=retain, fill_share=fill)
-    kw = dict(gamma=g if op in (C.LAYERNORM, C.RMSNORM) else None, beta=b if op == C.LAYERNORM else None)
+    if op == C.QUANT_INT8:
+        y = torch.empty(rows, cols, dtype=torch.int8, device="cuda")
+        kw = dict(out_dtype=C.INT8, out_scale=torch.empty(rows, device="cuda"))
+    else:
+        y = torch.empty_like(x)
+        kw = dict(gamma=g if op in (C.LAYERNORM, C.RMSNORM) else None, beta=b if op == C.LAYERNORM else None)
     for _ in range(3):
         C.run_ex(op, x, y, plan=plan, **kw)
     torch.cuda.synchronize()
@@ -472,6 +492,9 @@ def run_ours(args):
     bwd = None
     if not args.no_bwd:
         bwd = run_bwd_bench(C, torch, dev, synth)
+    quant = run_quant_bench(C, torch, dev, synth) if not args.no_quant else None
+    prec = run_precision_bench(C, torch, dev, synth) if not args.no_prec else None
+    ragged = run_ragged_bench(C, torch, dev, synth) if not args.no_ragged else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -502,7 +525,26 @@ def run_ours(args):
         "per_job": per_job,
         "picks": pick_rows,
         "backward": bwd,
+        "quant_int8": quant,
+        "precision": prec,
+        "ragged": ragged,
     }
+    # the headline figures of every table, last on the line
+    line["summary"] = {
+        "forward": {"GBps": round(value, 1), "frac": round(value / roofline["peak"], 4),
+                    "dominant_kernel_frac": roofline["frac"],
+                    "speedup_vs_best_non_dsmem": line["speedup_vs_best_non_dsmem"],
+                    "pick_accuracy": line["pick_accuracy"],
+                    "per_job_GBps": {f"{j['op']}_{j['cols']}": j["GBps"] for j in per_job}},
+        "backward": None if bwd is None else {k: bwd[k] for k in ("GBps", "speedup_vs_best_non_dsmem",
+                                                                   "pick_accuracy")},
+        "quant_int8": None if quant is None else {k: quant[k] for k in ("GBps", "speedup_vs_best_non_dsmem",
+                                                                         "pick_accuracy", "sampled_rows_bit_exact")},
+        "precision": None if prec is None else {
+            "GBps": prec["GBps"], "max_err_in_bound_units": prec["max_err_in_bound_units"],
+            "per_shape_GBps": {f"{r['op']}_{r['cols']}": r["chosen_GBps"] for r in prec["shapes"]}},
+        "ragged": None if ragged is None else {k: ragged[k] for k in ("GBps", "frac", "ms", "max_err_in_bound_units")},
+        "e2e_frac_of_link": None if e2e is None else e2e["frac_of_link_both"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -512,12 +554,13 @@ BWD_WIDTHS = [16384, 65536, 131072, 262144]
 
 def run_bwd_bench(C, torch, dev, synth):
     """The backward ops (dx of softmax, LayerNorm, RMSNorm; dz of softmax and of the cross entropy from
-    logits, with the same arrays as logits and as targets; FP32, 4096 rows): every candidate plan timed
-    (median of 5, CUDA events), the planner's pick, the best non-DSMEM plan and the speed-up of the pick
-    over it.  Algorithmic bytes: one read of a and of dy, one write of dx (12 B per element)."""
+    logits, with the same arrays as logits and as targets; the two gradients of the weighted variance and of
+    the Pearson correlation of a row pair; FP32, 4096 rows): every candidate plan timed (median of 5, CUDA
+    events), the planner's pick, the best non-DSMEM plan and the speed-up of the pick over it.  Algorithmic
+    bytes: one read of each input array and one write of each output (12 B per element, 16 for the pair
+    ops)."""
     peak, peak_kind = measured_peak()
-    out = {"rows": ROWS, "dtype": "f32", "bytes_per_elem": 12, "peak_GBps": peak, "peak_source": peak_kind,
-           "shapes": []}
+    out = {"rows": ROWS, "dtype": "f32", "peak_GBps": peak, "peak_source": peak_kind, "shapes": []}
     for cols in BWD_WIDTHS:
         a = synth.outliers(ROWS, cols, seed=synth.SEED_DATA, device=dev)
         dy = synth.normal(ROWS, cols, seed=synth.SEED_DATA + 1, device=dev)
@@ -529,23 +572,33 @@ def run_bwd_bench(C, torch, dev, synth):
         rstd_rms = (1.0 / torch.sqrt((a64 * a64).mean(dim=1) + 1e-6)).float()
         mean = mean.float()
         del a64
-        nbytes = ROWS * cols * 12
-        for op, name, kw in ((C.SOFTMAX_BWD, "softmax_bwd", {}),
-                             (C.LAYERNORM_BWD, "layernorm_bwd", dict(gamma=g, mean=mean, rstd=rstd_ln)),
-                             (C.RMSNORM_BWD, "rmsnorm_bwd", dict(gamma=g, rstd=rstd_rms)),
-                             (C.SOFTMAX_LOGITS_BWD, "softmax_logits_bwd", {}),
-                             (C.XENT_BWD, "xent_bwd", {})):
+        # the pair ops (f3): weighted variance of 2 a + 3 with weights U(0.1, 2); Pearson of a and 0.5 a + dy
+        gen = torch.Generator(device=dev).manual_seed(synth.SEED_DATA + 7)
+        wv_x = 2.0 * a + 3.0
+        wv_w = 0.1 + 1.9 * torch.rand(ROWS, cols, generator=gen, device=dev)
+        pe_y = 0.5 * a + dy
+        g_row = 0.5 + 1.5 * torch.rand(ROWS, generator=gen, device=dev)
+        dx2 = torch.empty_like(a)
+        ops = ((C.SOFTMAX_BWD, "softmax_bwd", a, dy, {}),
+               (C.LAYERNORM_BWD, "layernorm_bwd", a, dy, dict(gamma=g, mean=mean, rstd=rstd_ln)),
+               (C.RMSNORM_BWD, "rmsnorm_bwd", a, dy, dict(gamma=g, rstd=rstd_rms)),
+               (C.SOFTMAX_LOGITS_BWD, "softmax_logits_bwd", a, dy, {}),
+               (C.XENT_BWD, "xent_bwd", a, dy, {}),
+               (C.WVAR_BWD, "wvar_bwd", wv_x, wv_w, dict(scale=g_row, dx2=dx2)),
+               (C.PEARSON_BWD, "pearson_bwd", a, pe_y, dict(scale=g_row, dx2=dx2)))
+        for op, name, a_, dy_, kw in ops:
+            nbytes = ROWS * cols * (16 if op in (C.WVAR_BWD, C.PEARSON_BWD) else 12)
             cands = [(f"two_pass_g{G}", C.make_plan(C.PATH_TWO_PASS, ctas_per_row=G)) for G in (1, 2, 4, 8)]
             cands.append(("one_cta", C.make_plan(C.PATH_ONE_CTA)))
             cands += [(f"cluster{P}", C.make_plan(C.PATH_CLUSTER, P)) for P in (2, 4, 8, 16)]
             times = {}
             for cname, p in cands:
-                if C.bwd_plan_check(op, a, dy, dx, p, **kw) != C.OK:
+                if C.bwd_plan_check(op, a_, dy_, dx, p, **kw) != C.OK:
                     continue
-                ts = time_events(lambda: C.run_bwd(op, a, dy, dx, plan=p, **kw), 5)
+                ts = time_events(lambda: C.run_bwd(op, a_, dy_, dx, plan=p, **kw), 5)
                 times[cname] = statistics.median(ts)
             chosen_plan = C.plan_bwd(op, ROWS, cols, C.F32)
-            chosen = statistics.median(time_events(lambda: C.run_bwd(op, a, dy, dx, **kw), 5))
+            chosen = statistics.median(time_events(lambda: C.run_bwd(op, a_, dy_, dx, **kw), 5))
             non = {k: v for k, v in times.items() if k.startswith("two_pass")}
             staged = {k: v for k, v in times.items() if not k.startswith("two_pass")}
             best_non = min(non.values())
@@ -553,7 +606,8 @@ def run_bwd_bench(C, torch, dev, synth):
                      (str(chosen_plan.cluster_size) if chosen_plan.path == C.PATH_CLUSTER else
                       (f"_g{chosen_plan.ctas_per_row}" if chosen_plan.path == C.PATH_TWO_PASS else "")))
             out["shapes"].append({
-                "op": name, "cols": cols, "chosen": pname, "chosen_ms": round(chosen, 4),
+                "op": name, "cols": cols, "bytes_per_elem": nbytes // (ROWS * cols), "chosen": pname,
+                "chosen_ms": round(chosen, 4),
                 "chosen_GBps": round(nbytes / chosen / 1e6, 1), "frac": round(nbytes / chosen / 1e6 / peak, 4),
                 "best": min(times, key=times.get), "best_ms": round(min(times.values()), 4),
                 "best_non_dsmem_ms": round(best_non, 4),
@@ -561,15 +615,198 @@ def run_bwd_bench(C, torch, dev, synth):
                 "speedup_vs_best_non_dsmem": round(best_non / chosen, 4),
                 "hit": chosen <= 1.05 * min(times.values()),
                 "candidates": {k: round(v, 4) for k, v in sorted(times.items(), key=lambda kv: kv[1])}})
-        del a, dy, dx
+        del a, dy, dx, dx2, wv_x, wv_w, pe_y
         torch.cuda.empty_cache()
     assert C.device_error() == C.OK
     sh = out["shapes"]
     tot_chosen = sum(r["chosen_ms"] for r in sh)
-    out["GBps"] = round(sum(ROWS * r["cols"] * 12 for r in sh) / tot_chosen / 1e6, 1)
+    out["GBps"] = round(sum(ROWS * r["cols"] * r["bytes_per_elem"] for r in sh) / tot_chosen / 1e6, 1)
     out["speedup_vs_best_non_dsmem"] = round(sum(r["best_non_dsmem_ms"] for r in sh) / tot_chosen, 4)
     out["pick_accuracy"] = round(sum(r["hit"] for r in sh) / len(sh), 4)
     return out
+
+
+def plan_name(C, p):
+    """Short name of a plan, as the candidate tables spell it."""
+    if p.path == C.PATH_TWO_PASS:
+        return f"two_pass_g{p.ctas_per_row}"
+    base = "one_cta" if p.path == C.PATH_ONE_CTA else f"cluster{p.cluster_size}"
+    tag = "_tm" if p.retain == C.RETAIN_TMEM else ""
+    return base + tag + (f"_f{round(p.fill_share, 2)}" if p.fill_share > 0 else "")
+
+
+def time_candidates(C, op, x, y, kw, fills=False):
+    """Median of 5 (CUDA events) for every legal plan of one call, and for the planner's own choice."""
+    times = {}
+    for name, p in candidates(C, op, x, y, fills=fills, **kw):
+        times[name] = statistics.median(time_events(lambda: C.run_ex(op, x, y, plan=p, **kw), 5))
+    chosen = statistics.median(time_events(lambda: C.run_ex(op, x, y, **kw), 5))
+    return times, chosen
+
+
+def table_row(name, cols, nbytes, times, chosen, chosen_name, peak):
+    non = {k: v for k, v in times.items() if k.startswith("two_pass") or k.startswith("one_cta")}
+    best = min(times.values())
+    return {"op": name, "cols": cols, "chosen": chosen_name, "chosen_ms": round(chosen, 4),
+            "chosen_GBps": round(nbytes / chosen / 1e6, 1), "frac": round(nbytes / chosen / 1e6 / peak, 4),
+            "best": min(times, key=times.get), "best_ms": round(best, 4),
+            "best_non_dsmem_ms": round(min(non.values()), 4),
+            "speedup_vs_best_non_dsmem": round(min(non.values()) / chosen, 4), "hit": chosen <= 1.05 * best,
+            "candidates": {k: round(v, 4) for k, v in sorted(times.items(), key=lambda kv: kv[1])[:6]}}
+
+
+def table_summary(rows, nbytes_of):
+    tot = sum(r["chosen_ms"] for r in rows)
+    return {"GBps": round(sum(nbytes_of(r) for r in rows) / tot / 1e6, 1),
+            "speedup_vs_best_non_dsmem": round(sum(r["best_non_dsmem_ms"] for r in rows) / tot, 4),
+            "pick_accuracy": round(sum(r["hit"] for r in rows) / len(rows), 4)}
+
+
+QUANT_WIDTHS = [16384, 65536, 262144]
+
+
+def run_quant_bench(C, torch, dev, synth):
+    """Row-wise int8 quantisation (the paper's suite, Sec. IV-A): FP32 rows of config 2's distribution,
+    4096 x {16K, 64K, 256K}; every candidate timed beside the planner's pick; algorithmic bytes 4 in + 1 out
+    per element + 4 per row (the scale).  Codes and scales of sampled rows are checked bit for bit against
+    the oracle."""
+    import numpy as np
+    import oracle as O
+    peak, peak_kind = measured_peak()
+    out = {"rows": ROWS, "in_dtype": "f32", "bytes_per_elem": 5, "peak_GBps": peak, "peak_source": peak_kind,
+           "shapes": []}
+    exact = True
+    for cols in QUANT_WIDTHS:
+        x = synth.outliers(ROWS, cols, seed=synth.SEED_DATA, device=dev)
+        q = torch.empty(ROWS, cols, dtype=torch.int8, device=dev)
+        sc = torch.empty(ROWS, device=dev)
+        kw = dict(out_dtype=C.INT8, out_scale=sc)
+        times, chosen = time_candidates(C, C.QUANT_INT8, x, q, kw)
+        nbytes = ROWS * cols * 5 + ROWS * 4
+        pick = list(range(0, ROWS, ROWS // 8))
+        qr, sr = O.quant_int8(x[pick].cpu().numpy())
+        exact = exact and bool(np.array_equal(q[pick].cpu().numpy(), qr) and np.array_equal(sc[pick].cpu().numpy(), sr))
+        out["shapes"].append(table_row("quant_int8", cols, nbytes, times, chosen,
+                                       plan_name(C, C.plan(C.QUANT_INT8, ROWS, cols, C.F32, C.INT8)), peak))
+        del x, q
+        torch.cuda.empty_cache()
+    assert C.device_error() == C.OK
+    out.update(table_summary(out["shapes"], lambda r: ROWS * r["cols"] * 5 + ROWS * 4))
+    out["sampled_rows_bit_exact"] = exact
+    return out
+
+
+PREC_WIDTHS = [131072, 262144]
+
+
+def output_error(op, out_dt, y, ref, osc=None):
+    """Largest error of sampled outputs in units of the output format's bound: FP32 (logsumexp) |y - y*| /
+    max(|y*|, 1) / 1e-5; BF16 |y - y*| / ulp_bf16(y*); E4M3 |q s - y*| / (one E4M3 quantum at y* / s) s."""
+    import numpy as np
+    a = np.abs(ref)
+    if out_dt == 0:
+        return float(np.max(np.abs(y - ref) / np.maximum(a, 1.0)) / 1e-5)
+    if out_dt == 1:
+        e = np.floor(np.log2(np.where(a > 0, a, 1.0)))
+        ulp = np.where(a >= 2.0 ** -126, np.exp2(e - 7), 2.0 ** -133)
+        return float(np.max(np.abs(y - ref) / ulp))
+    s = np.asarray(osc, dtype=np.float64).reshape(-1, 1)
+    t = a / s
+    e = np.floor(np.log2(np.where(t > 0, t, 2.0 ** -30)))
+    return float(np.max(np.abs(y * s - ref) / (np.exp2(np.maximum(e, -6) - 3) * s)))
+
+
+def run_precision_bench(C, torch, dev, synth):
+    """The precision workload: softmax and log-sum-exp over 4096 x {128K, 256K} logits N(0, 3^2) in BF16 and
+    in FP8-E4M3 with a per-row FP32 scale, FP32 accumulation.  Every candidate timed beside the planner's
+    pick; algorithmic bytes one read and one write (softmax BF16 4 B, FP8 2 B per element + 8 B per row;
+    log-sum-exp BF16 2 B, FP8 1 B per element + 4 or 8 B per row).  Error of 8 sampled rows against the FP64
+    oracle in units of each format's bound (<= 1 passes)."""
+    import numpy as np
+    import oracle as O
+    peak, peak_kind = measured_peak()
+    out = {"rows": ROWS, "logits": "N(0, 3^2)", "peak_GBps": peak, "peak_source": peak_kind, "shapes": []}
+    nb = {}
+    for cols in PREC_WIDTHS:
+        x32 = synth.normal(ROWS, cols, std=3.0, seed=synth.SEED_DATA, device=dev)
+        for dt, dname in ((C.BF16, "bf16"), (C.FP8_E4M3, "fp8")):
+            if dt == C.BF16:
+                x, isc = synth.to_bf16(x32), None
+            else:
+                x, isc = synth.to_e4m3_rowscaled(x32)
+            pick = list(range(0, ROWS, ROWS // 8))
+            raw = x[pick].cpu().contiguous()
+            raw = raw.view(torch.int16).numpy().view(np.uint16) if dt == C.BF16 else raw.view(torch.uint8).numpy()
+            for op, oname in ((C.SOFTMAX, "softmax"), (C.LOGSUMEXP, "logsumexp")):
+                if op == C.LOGSUMEXP:
+                    y = torch.empty(ROWS, device=dev)
+                    osc = None
+                    out_dt = C.F32
+                else:
+                    y = torch.empty(ROWS, cols, dtype=x.dtype, device=dev)
+                    osc = torch.empty(ROWS, device=dev) if dt == C.FP8_E4M3 else None
+                    out_dt = dt
+                kw = dict(in_dtype=dt, out_dtype=out_dt, in_scale=isc, out_scale=osc)
+                times, chosen = time_candidates(C, op, x, y, kw)
+                isz = 2 if dt == C.BF16 else 1
+                per_row = (4 if op == C.LOGSUMEXP else 0) + (4 if dt == C.FP8_E4M3 else 0) + \
+                    (4 if dt == C.FP8_E4M3 and op == C.SOFTMAX else 0)  # LSE out; FP8 in / out scales
+                nbytes = ROWS * cols * (isz if op == C.LOGSUMEXP else 2 * isz) + ROWS * per_row
+                ref, _, _ = O.run(op, dt, raw, len(pick), cols, in_scale=None if isc is None else isc[pick].cpu().numpy())
+                yv = y[pick].double().cpu().numpy() if op == C.LOGSUMEXP else y[pick].float().double().cpu().numpy()
+                err = output_error(op, out_dt, yv, ref, None if osc is None else osc[pick].cpu().numpy())
+                p = C.plan(op, ROWS, cols, dt, out_dt)
+                row = table_row(f"{oname}_{dname}", cols, nbytes, times, chosen, plan_name(C, p), peak)
+                row["max_err_in_bound_units"] = round(err, 4)
+                out["shapes"].append(row)
+                nb[(row["op"], cols)] = nbytes
+                del y
+            del x
+        del x32
+        torch.cuda.empty_cache()
+    assert C.device_error() == C.OK
+    out.update(table_summary(out["shapes"], lambda r: nb[(r["op"], r["cols"])]))
+    out["max_err_in_bound_units"] = {d: max(r["max_err_in_bound_units"] for r in out["shapes"] if r["op"].endswith(d))
+                                     for d in ("bf16", "fp8")}
+    return out
+
+
+def run_ragged_bench(C, torch, dev, synth, reps=10):
+    """The batching workload: 20000 BF16 rows of widths round(2^(10 + 10 u)) (log-uniform in [1K, 1M]),
+    softmax or RMSNorm by a fair coin per row, packed with no alignment padding, run as one persistent launch
+    replayed from a CUDA graph (the library's autotuner picks cluster size, staging and threads).  GB/s at
+    4 B per element (one BF16 read, one BF16 write); 16 sampled rows checked against the FP64 oracle."""
+    import numpy as np
+    import oracle as O
+    peak, peak_kind = measured_peak()
+    widths, ops = synth.ragged_widths(20000)
+    widths, ops = widths.numpy(), ops.numpy()
+    offs = np.concatenate([[0], np.cumsum(widths)[:-1]]).astype(np.int64)
+    total = int(widths.sum())
+    g = torch.Generator(device=dev).manual_seed(synth.SEED_RAGGED)
+    d_in = (torch.randn(total, generator=g, device=dev) * 2.0).to(torch.bfloat16)
+    d_out = torch.empty_like(d_in)
+    rows = [(int(o), int(o), int(w), int(op)) for o, w, op in zip(offs, widths, ops)]
+    t0 = time.perf_counter()
+    R = C.Ragged(rows, C.BF16, d_in, d_out, tune=True)
+    t_create = time.perf_counter() - t0
+    ms = statistics.median(time_events(lambda: R.run(), reps, warm=3))
+    info = R.info()
+    worst = 0.0
+    for i in np.linspace(0, len(rows) - 1, 16).astype(int):
+        o, w, op = int(offs[i]), int(widths[i]), int(ops[i])
+        raw = d_in[o:o + w].cpu().view(torch.int16).numpy().view(np.uint16)
+        ref, _, _ = O.run(op, C.BF16, raw, 1, w)
+        worst = max(worst, output_error(op, C.BF16, d_out[o:o + w].float().double().cpu().numpy().reshape(1, w), ref))
+    assert C.device_error() == C.OK
+    nbytes = total * 4
+    res = {"rows": len(rows), "elements": total, "dtype": "bf16", "ms": round(ms, 4),
+           "GBps": round(nbytes / ms / 1e6, 1), "frac": round(nbytes / ms / 1e6 / peak, 4), "peak_GBps": peak,
+           "peak_source": peak_kind, "create_s": round(t_create, 2), "launch": info,
+           "max_err_in_bound_units": round(worst, 4)}
+    del R, d_in, d_out
+    torch.cuda.empty_cache()
+    return res
 
 
 PATH_NAMES_SHORT = {0: "one_cta", 1: "two_pass", 2: "cluster"}
@@ -675,6 +912,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-bwd", action="store_true", help="skip the backward-op table")
+    ap.add_argument("--no-quant", action="store_true", help="skip the int8 quantisation table")
+    ap.add_argument("--no-prec", action="store_true", help="skip the BF16 / FP8 softmax / log-sum-exp table")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch graph launch")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-seconds", type=float, default=60.0,
