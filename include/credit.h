@@ -376,7 +376,9 @@ credit_status credit_run_bwd(const credit_bwd_args *args, const credit_plan_t *p
  * unaligned rows when planning itself): the fused two-pass path for rows of
  * at most 16 KiB per array, else the staged path with the smallest cluster
  * size whose slices (two row buffers of a and dy, and gamma for the norms)
- * fit, else the split two-pass path.  source = 3 (built-in rule).
+ * fit, else the split two-pass path.  The logits and pair ops, whose per-row
+ * merges grow with the cluster size, are staged only for P <= 4 with slices
+ * of at most 64 KiB per array.  source = 3 (built-in rule).
  */
 credit_status credit_plan_bwd(int32_t op, int64_t rows, int64_t cols, credit_dtype dtype, credit_plan_t *out);
 
@@ -586,6 +588,23 @@ credit_status credit_set_trace(void *device_buf, int64_t bytes);
  */
 credit_status credit_run_two_pass_noalloc(const credit_args *args, int32_t ctas_per_row,
                                           cudaStream_t stream);
+
+/*
+ * credit_set_wait_test -- test only: exercises the bounded-wait error path
+ * without faulting anything.  wait_ns > 0 sets the limit of the staged
+ * reducers' chunk waits (0 restores the default, 2 s).  extra_tx_bytes > 0
+ * (a multiple of 16, at most 1 MiB) makes the shared-memory staged kernel's
+ * first chunk barrier expect that many bytes more than its bulk copy
+ * delivers, so the reducers' wait runs out, sets the device error word and
+ * returns; the kernel then finishes (its output for that call is not
+ * defined) and credit_device_error() reports CREDIT_ERR_TIMEOUT.  Only
+ * accepted for a one-CTA plan on one row of one chunk with shared-memory
+ * retention (the barrier is armed once and never reused, and the one copy
+ * issued completes); any other staged call returns CREDIT_ERR_UNSUPPORTED
+ * while extra_tx_bytes > 0, launching nothing.  Process-wide; not thread-safe
+ * against concurrent calls.  The paper has no counterpart.
+ */
+credit_status credit_set_wait_test(int64_t wait_ns, int32_t extra_tx_bytes);
 
 /*
  * credit_device_error -- synchronise `stream`, then read and clear the

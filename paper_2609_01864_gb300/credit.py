@@ -191,6 +191,8 @@ def _extra_prototypes(L):
     L.credit_mlp_predict.argtypes = [fp, i64, fp]
     L.credit_mlp_grad.restype = i32
     L.credit_mlp_grad.argtypes = [fp, fp, fp, i64, fp, fp]
+    L.credit_set_wait_test.restype = i32
+    L.credit_set_wait_test.argtypes = [i64, i32]
     L.credit_mlp_adam_step.restype = i32
     L.credit_mlp_adam_step.argtypes = [fp, fp, fp, fp, i32, ctypes.c_float]
     L.credit_mlp_save.restype = i32
@@ -557,6 +559,11 @@ def mlp_save(path: str):
 
 def mlp_load(path: str):
     _check(lib().credit_mlp_load(path.encode()), "credit_mlp_load")
+
+
+def set_wait_test(wait_ns: int = 0, extra_tx_bytes: int = 0) -> None:
+    """credit_set_wait_test (test only): short chunk-wait limit and an unsatisfiable first-chunk barrier."""
+    _check(lib().credit_set_wait_test(int(wait_ns), int(extra_tx_bytes)), "credit_set_wait_test")
 
 
 def device_error(stream=None) -> int:

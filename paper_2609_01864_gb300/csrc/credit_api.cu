@@ -545,6 +545,10 @@ credit_status check_plan(int device, const credit_args *a, const credit_plan_t *
 
 static unsigned long long *g_trace_buf = nullptr;
 static int g_trace_rows = 0;
+// credit_set_wait_test (test only): the reducers' chunk-wait limit and the
+// extra bytes the first chunk's barrier expects
+static std::atomic<unsigned long long> g_wait_ns{0};
+static std::atomic<int> g_test_extra_tx{0};
 
 static RowArgs make_row_args(const credit_args *a, unsigned *err, float *ws) {
     RowArgs r;
@@ -571,6 +575,8 @@ static RowArgs make_row_args(const credit_args *a, unsigned *err, float *ws) {
     r.trace = g_trace_buf;
     r.trace_rows = g_trace_rows;
     r.row0 = 0;
+    r.wait_ns = g_wait_ns.load();
+    r.test_extra_tx = 0;
     return r;
 }
 
@@ -664,7 +670,13 @@ credit_status run_with_plan(int device, const credit_args *a, const credit_plan_
         const long long n_cl = rows - n_fill;
         cudaError_t e;
         if (n_fill > 0 && (e = cudaEventRecord(d.fork, s)) != cudaSuccess) return cuda_status(e);
+        const int extra_tx = g_test_extra_tx.load();
+        // the unsatisfiable first-chunk barrier of the wait test: one CTA, one row, one chunk, shared-memory
+        // ring (the barrier is armed once and never reused; the one copy issued completes)
+        if (extra_tx > 0 && (P != 1 || rows != 1 || rc.tmem || rc.nch_max != 1 || fill_rows(p, rows) > 0))
+            return CREDIT_ERR_UNSUPPORTED;
         RowArgs r = base;
+        r.test_extra_tx = extra_tx;
         r.rows = n_cl;
         r.chunk_bytes = rc.chunk;
         r.ring = rc.ring;
@@ -790,6 +802,14 @@ credit_status credit_set_trace(void *device_buf, int64_t bytes) {
     if (reinterpret_cast<uintptr_t>(device_buf) % 8 || bytes < per_row) return CREDIT_ERR_INVALID_ARG;
     g_trace_buf = static_cast<unsigned long long *>(device_buf);
     g_trace_rows = static_cast<int>(bytes / per_row);
+    return CREDIT_OK;
+}
+
+credit_status credit_set_wait_test(int64_t wait_ns, int32_t extra_tx_bytes) {
+    if (wait_ns < 0 || extra_tx_bytes < 0 || extra_tx_bytes % 16 || extra_tx_bytes > (1 << 20))
+        return CREDIT_ERR_INVALID_ARG;
+    g_wait_ns.store(static_cast<unsigned long long>(wait_ns));
+    g_test_extra_tx.store(extra_tx_bytes);
     return CREDIT_OK;
 }
 

@@ -225,7 +225,8 @@ struct BwdState<OP, 1> {
 //   mean += d nb / n,   S += S_b + d d' na nb / n
 // (d' = d of the other variable for the cross moment).  merge(a, b) is the
 // same arithmetic whichever side calls it, so the shuffle trees below give
-// one state in every lane.
+// one state in every lane.  The two weights share one SFU reciprocal of n
+// (relative error below 2^-22, as in the LayerNorm statistics).
 template <int OP>
 __device__ __forceinline__ void pair_merge(float (&a)[kPairState<OP>], const float (&b)[kPairState<OP>]) {
     constexpr int NS = kPairState<OP>;
@@ -236,7 +237,7 @@ __device__ __forceinline__ void pair_merge(float (&a)[kPairState<OP>], const flo
         return;
     }
     const float n = a[0] + b[0];
-    const float wb = b[0] / n, wab = a[0] * wb;  // nb / n and na nb / n
+    const float wb = b[0] * rcp_approx(n), wab = a[0] * wb;  // nb / n and na nb / n
     if constexpr (OP == BOP_WVAR) {
         const float d = b[1] - a[1];
         a[1] = fmaf(d, wb, a[1]);
@@ -294,13 +295,14 @@ struct BwdState<OP, 2> {
 #pragma unroll
         for (int j = 0; j < kPairState<OP>; ++j) c[j] = 0.0f;
         if (n == 0.0f) return;
+        const float r = rcp_approx(n);
         if constexpr (OP == BOP_WVAR) {
-            const float q = s[0] / n;
+            const float q = s[0] * r;
             c[0] = n;
             c[1] = kx + q;
             c[2] = fmaxf(fmaf(-s[0], q, s[1]), 0.0f);
         } else {
-            const float qx = s[0] / n, qy = s[1] / n;
+            const float qx = s[0] * r, qy = s[1] * r;
             c[0] = n;
             c[1] = kx + qx;
             c[2] = ky + qy;
@@ -311,15 +313,14 @@ struct BwdState<OP, 2> {
     }
 };
 
-// Shuffle-tree merge of a pair state over the 32 lanes of a warp: at every
-// level both partners compute merge(lower lane, upper lane), so all lanes end
-// with the same state.
+// Shuffle-tree merge of a pair state over groups of `width` lanes (a power
+// of two, <= 32): at every level both partners compute merge(lower lane,
+// upper lane), so all lanes of a group end with the same state.
 template <int OP>
-__device__ __forceinline__ void warp_merge_pair(float (&c)[kPairState<OP>]) {
+__device__ __forceinline__ void warp_merge_pair(float (&c)[kPairState<OP>], int width = 32) {
     constexpr int NS = kPairState<OP>;
     const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = width >> 1; o > 0; o >>= 1) {
         float oth[NS];
 #pragma unroll
         for (int j = 0; j < NS; ++j) oth[j] = __shfl_xor_sync(0xffffffffu, c[j], o);
@@ -660,14 +661,12 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_bwd_staged(const BwdArgs p) 
                 for (int j = 0; j < NS; ++j) v8[j] = tot[j];
                 const float *sl = exchange_push8(v8, slots, xbar, static_cast<int>(it & 1),
                                                  static_cast<uint32_t>((it >> 1) & 1), P, c, T, p.err);
+                // the P CTA states merged by one fixed shuffle tree within every group of P lanes (lane l
+                // holds CTA l % P's; P is a power of two): the same state in every thread of every CTA
+                const int q = tid & (P - 1);
 #pragma unroll
-                for (int j = 0; j < NS; ++j) tot[j] = 0.0f;
-                for (int q = 0; q < P; ++q) {  // Chan merges in the fixed order c = 0..P-1: one state in every CTA
-                    float cq[NS];
-#pragma unroll
-                    for (int j = 0; j < NS; ++j) cq[j] = sl[8 * q + j];
-                    pair_merge<OP>(tot, cq);
-                }
+                for (int j = 0; j < NS; ++j) tot[j] = sl[8 * q + j];
+                warp_merge_pair<OP>(tot, P);
             }
             kc = pair_coeffs<OP>(tot, R);
         } else if constexpr (kLogits<OP>) {
@@ -1070,6 +1069,8 @@ credit_status check_bwd_plan(int dev, const credit_bwd_args *a, const credit_pla
     return *maxc > 0 ? CREDIT_OK : CREDIT_ERR_UNSUPPORTED;
 }
 
+inline bool kPairOp(int op) { return op == BOP_WVAR || op == BOP_PEARSON; }
+
 credit_status plan_bwd_for(int dev, int op, long long cols, int dtype, credit_plan_t *out) {
     std::memset(out, 0, sizeof(*out));
     out->source = 3;
@@ -1079,10 +1080,12 @@ credit_status plan_bwd_for(int dev, int op, long long cols, int dtype, credit_pl
     if (di != nullptr && cols * isz > kBwdFusedMaxBytes) {
         BwdKernels k;
         if (!bwd_kernels(op, dtype, &k)) return CREDIT_ERR_UNSUPPORTED;
-        if (op == BOP_SMLOGITS || op == BOP_XENT) {
-            // the logits ops carry a per-row merge of (max, sum, dot) states whose cost grows with P: staged
-            // only while a CTA's slice is at most 64 KiB per array and P <= 4 (measured: P = 4 beats two-pass
-            // at 64K FP32 columns, P = 8 and 16 lose at 128K), either buffering
+        const bool merge_heavy = op == BOP_SMLOGITS || op == BOP_XENT || kPairOp(op);
+        if (merge_heavy) {
+            // the logits ops carry a per-row merge of (max, sum, dot) states, the pair ops Chan merges of
+            // centred moments, whose cost and exchange latency grow with P: staged only while a CTA's slice is
+            // at most 64 KiB per array and P <= 4 (measured: P = 4 beats two-pass at 64K FP32 columns, P = 8
+            // and 16 lose at 128K), either buffering
             for (int P = 1; P <= 4; P *= 2) {
                 BwdCfg cfg;
                 if (cols * isz > 65536LL * P) continue;
@@ -1099,7 +1102,7 @@ credit_status plan_bwd_for(int dev, int op, long long cols, int dtype, credit_pl
         }
         // double-buffered staging only: a single buffer leaves the copies of the next row unoverlapped, which
         // measured no faster than the global-reread path
-        for (int P = 1; P <= kMaxCluster && op != BOP_SMLOGITS && op != BOP_XENT; P *= 2) {
+        for (int P = 1; P <= kMaxCluster && !merge_heavy; P *= 2) {
             BwdCfg cfg;
             if (!bwd_config(*di, cols, isz, P, 2, op == BOP_LN || op == BOP_RMS, &cfg)) continue;
             if (prepare_staged_kernel(dev, k.staged) != CREDIT_OK) continue;

@@ -73,13 +73,14 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t pa
     return ok != 0;
 }
 // Bounded wait for phase `parity` of `bar`.  Returns false (and flags the
-// error word) if the phase did not complete within kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned *err) {
+// error word) if the phase did not complete within limit_ns (default 2 s).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned *err,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_timer_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
+        if ((it & 255u) == 0 && global_timer_ns() - t0 > limit_ns) {
             if (err) atomicOr(err, ERR_TMA_TIMEOUT);
             return false;
         }

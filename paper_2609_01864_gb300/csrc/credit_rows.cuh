@@ -67,6 +67,8 @@ struct RowArgs {
     unsigned long long *trace;            // optional phase timestamps (see credit_set_trace)
     int trace_rows;                       // rows recorded per traced CTA
     long long row0;                       // first row of this launch
+    unsigned long long wait_ns;           // limit of the reducers' chunk waits (ns; 0 = kWaitLimitNs)
+    int test_extra_tx;                    // test only: extra bytes the first chunk's barrier expects (0)
 };
 
 constexpr int kMaxCluster = 16;
@@ -759,7 +761,9 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                     const int slot = rp.slot;
                     if (rp.lap > 0) mbar_wait_bounded(&empty[slot], rp.prev_parity(), a.err);
                     const uint32_t bytes = static_cast<uint32_t>(body - off < CH ? body - off : CH);
-                    mbar_arrive_expect_tx(&full[slot], bytes);
+                    // (test_extra_tx: bytes no copy delivers, so this phase cannot complete; the host allows it
+                    // only for one row of one chunk, where the barrier is never reused)
+                    mbar_arrive_expect_tx(&full[slot], bytes + (rp.lap == 0 && slot == 0 ? a.test_extra_tx : 0));
                     bulk_g2s(ring + static_cast<size_t>(slot) * CH, src + off, bytes, &full[slot]);
                 }
                 trace_stamp(a, prr++, 5);
@@ -803,7 +807,7 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                 Stream<OP> acc;
                 for (int k = 0; k < g.nch; ++k) {
                     const RingPos pk = rb.at(k);
-                    mbar_wait_bounded(&full[pk.slot], pk.parity(), a.err);
+                    mbar_wait_bounded(&full[pk.slot], pk.parity(), a.err, a.wait_ns ? a.wait_ns : kWaitLimitNs);
                     visit_chunk<TIN>(chunk_ptr(rb, k), chunk_groups(g, k), tid, Tr, g.in_sc,
                                      [&](int, const float(&f)[V]) { acc.add(f); });
                 }

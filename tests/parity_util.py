@@ -317,5 +317,8 @@ def pair_error(op, dtype, out1, out2, ref1, ref2, x, d, g, cols):
         if dtype == C.BF16:
             mag = np.abs(ref)
             bound = bound + np.where(mag > 0, np.exp2(np.floor(np.log2(np.where(mag > 0, mag, 1.0))) - 7), 2.0 ** -133)
-        worst = max(worst, float((np.abs(out - ref) / bound).max()))
+        e = np.abs(out - ref) / bound
+        if not np.all(np.isfinite(e)):  # a NaN or infinite output fails (max() would skip a NaN)
+            return float("inf")
+        worst = max(worst, float(e.max()))
     return worst

@@ -77,6 +77,10 @@ def test_validation_rejects_bad_calls_without_touching_the_gpu(lib):
     a.out_scale, a.in_dtype, a.in_scale = 0x3000, C.FP8_E4M3, 0x4000
     assert lib.credit_run_ex(ctypes.byref(a), None, None) == C.ERR_UNSUPPORTED   # FP8 rows
     a.in_dtype, a.out_dtype, a.out_scale, a.in_scale = C.F32, C.F32, None, None
+    # the wait-test knob checks its arguments on the host
+    assert lib.credit_set_wait_test(-1, 0) == C.ERR_INVALID_ARG
+    assert lib.credit_set_wait_test(0, 8) == C.ERR_INVALID_ARG
+    assert lib.credit_set_wait_test(0, 0) == C.OK
     # simple entry points: FP8 needs credit_run_ex (scales)
     assert lib.credit_softmax(0x1000, 0x2000, 4, 16, C.FP8_E4M3, None) == C.ERR_INVALID_ARG
     p = C.PlanT()
