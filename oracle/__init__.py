@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
             L.oracle_pearson_row.restype = d
             L.oracle_pearson_row.argtypes = [vp, vp, i64]
             L.oracle_pearson_bwd_row.argtypes = [vp, vp, i64, d, vp, vp]
+            L.oracle_scan_row.argtypes = [vp, i64, vp]
+            L.oracle_stencil_row.argtypes = [vp, i64, vp, i32, vp]
             L.oracle_quant_int8_row.restype = ctypes.c_float
             L.oracle_quant_int8_row.argtypes = [vp, i64, vp]
             L.oracle_run_bwd.restype = i32
@@ -327,6 +329,26 @@ def quant_int8(x):
     for r in range(x.shape[0]):
         s[r] = lib().oracle_quant_int8_row(_ptr(x[r]), x.shape[1], _ptr(q[r]))
     return q, s
+
+
+def scan(x):
+    """Row-wise inclusive prefix sums (FP64) of rows x (rows x cols)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    for r in range(x.shape[0]):
+        lib().oracle_scan_row(_ptr(x[r]), x.shape[1], _ptr(y[r]))
+    return y
+
+
+def stencil(x, w):
+    """Row-wise stencil with weights w (2r + 1 of them, radius r), zero padding at the row ends (FP64)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    y = np.empty_like(x)
+    r = (len(w) - 1) // 2
+    for i in range(x.shape[0]):
+        lib().oracle_stencil_row(_ptr(x[i]), x.shape[1], _ptr(w), r, _ptr(y[i]))
+    return y
 
 
 def max_threads() -> int:

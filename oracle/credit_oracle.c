@@ -367,6 +367,33 @@ float oracle_quant_int8_row(const float *x, int64_t n, int8_t *q) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Negative controls of the screening rule (Sec. III-D; Sec. IV-C): row  */
+/* ops that read and write a row once but lack the reduction-reuse       */
+/* pattern, so the rule rejects the cluster path for them.               */
+/* Row scan (inclusive prefix sum): y_i = sum_{j <= i} x_j, the running  */
+/* sum kept with Neumaier compensation.                                  */
+void oracle_scan_row(const double *x, int64_t n, double *y) {
+    nsum_t S = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        nsum_add(&S, x[i]);
+        y[i] = nsum_get(&S);
+    }
+}
+
+/* Row stencil of radius r: y_i = sum_{k=-r..r} w[k + r] x_{i+k}, with    */
+/* x_j = 0 outside the row (zero padding at both ends).                   */
+void oracle_stencil_row(const double *x, int64_t n, const double *w, int r, double *y) {
+    for (int64_t i = 0; i < n; ++i) {
+        nsum_t S = {0, 0};
+        for (int k = -r; k <= r; ++k) {
+            int64_t j = i + k;
+            if (j >= 0 && j < n) nsum_add(&S, w[k + r] * x[j]);
+        }
+        y[i] = nsum_get(&S);
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Batch driver: decode -> op -> (exact doubles, encoded output)        */
 /* ------------------------------------------------------------------ */
 
