@@ -26,7 +26,8 @@ x {16K, 64K, 128K, 256K} FP32; `quant_int8`: row-wise int8 quantisation of
 4096 x {16K, 64K, 256K} FP32 rows; `precision`: softmax and log-sum-exp over
 4096 x {128K, 256K} BF16 / FP8-E4M3 logits N(0, 3^2) with the error of sampled
 rows against the oracle; `ragged`: 20000 BF16 rows of log-uniform width in one
-graph-replayed persistent launch.  In every table each candidate plan is
+graph-replayed persistent launch; `controls`: the screen's negative controls
+(row scan, row stencil) planned and timed on the global path.  In every table each candidate plan is
 timed beside the planner's pick (outside the timed step).  `summary`, last on
 the line, repeats each table's headline figures.
 
@@ -495,6 +496,7 @@ def run_ours(args):
     quant = run_quant_bench(C, torch, dev, synth) if not args.no_quant else None
     prec = run_precision_bench(C, torch, dev, synth) if not args.no_prec else None
     ragged = run_ragged_bench(C, torch, dev, synth) if not args.no_ragged else None
+    controls = run_controls_bench(C, torch, dev, synth) if not args.no_controls else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -528,6 +530,7 @@ def run_ours(args):
         "quant_int8": quant,
         "precision": prec,
         "ragged": ragged,
+        "controls": controls,
     }
     # the headline figures of every table, last on the line
     line["summary"] = {
@@ -544,6 +547,8 @@ def run_ours(args):
             "GBps": prec["GBps"], "max_err_in_bound_units": prec["max_err_in_bound_units"],
             "per_shape_GBps": {f"{r['op']}_{r['cols']}": r["chosen_GBps"] for r in prec["shapes"]}},
         "ragged": None if ragged is None else {k: ragged[k] for k in ("GBps", "frac", "ms", "max_err_in_bound_units")},
+        "controls": None if controls is None else {
+            "screen": controls["screen"], "GBps": {f"{r['op']}_{r['cols']}": r["GBps"] for r in controls["shapes"]}},
         "e2e_frac_of_link": None if e2e is None else e2e["frac_of_link_both"]}
     print(json.dumps(line), flush=True)
     return 0
@@ -809,6 +814,56 @@ def run_ragged_bench(C, torch, dev, synth, reps=10):
     return res
 
 
+CONTROL_WIDTHS = [65536, 262144]
+SCREEN_NAMES = {0: "candidate", 1: "no_reuse", 2: "ordered", 3: "remote_state"}
+
+
+def run_controls_bench(C, torch, dev, synth):
+    """Negative controls of the structural screen (Sec. III-D, IV-C): the row scan and the 5-point row stencil
+    over 4096 x {64K, 256K} FP32, planned (the screen's verdict, the global-memory path) and timed (median of
+    5, 8 B per element); the selection case by its verdict alone.  The scan's carries are ordered, K = 2(P - 1):
+    its control cost is estimated from the measured work-free control kernel of the cluster launch shape at
+    one exchange stage plus (P - 2) further stages, each priced at the measured difference between the two- and
+    one-stage control kernels; the one-pass scan rereads nothing (T_save = 0), so dT = -T_ctrl < 0 at every P."""
+    out = {"rows": ROWS, "dtype": "f32", "bytes_per_elem": 8, "shapes": [], "screen": {}}
+    peak, peak_kind = measured_peak()
+    for op, name in ((C.SCAN, "scan"), (C.STENCIL, "stencil"), (C.SELECT, "select"), (C.LOGSUMEXP, "logsumexp")):
+        out["screen"][name] = SCREEN_NAMES[C.screen(C.dataflow(op), 16)[0]]
+    w = torch.tensor([0.1, -0.2, 0.4, -0.2, 0.1], device=dev)
+    for cols in CONTROL_WIDTHS:
+        x = synth.outliers(ROWS, cols, seed=synth.SEED_DATA, device=dev)
+        y = torch.empty_like(x)
+        for op, name, kw in ((C.SCAN, "scan", {}), (C.STENCIL, "stencil", dict(weights=w))):
+            plan, verdict = C.plan_control(op, ROWS, cols)
+            ms = statistics.median(time_events(lambda: C.run_control(op, x, y, **kw), 5, warm=2))
+            nbytes = ROWS * cols * 8
+            out["shapes"].append({"op": name, "cols": cols, "verdict": SCREEN_NAMES[verdict],
+                                  "path": "global, one CTA per row" if op == C.SCAN else "global",
+                                  "ms": round(ms, 4), "GBps": round(nbytes / ms / 1e6, 1),
+                                  "frac": round(nbytes / ms / 1e6 / peak, 4)})
+        del x, y
+        torch.cuda.empty_cache()
+    # the scan's ordered-carry control cost, priced from the measured control kernel (FP8 launch shape: the
+    # one- and two-stage control kernels share it)
+    cols = CONTROL_WIDTHS[0]
+    est = []
+    for P in (2, 4, 8, 16):
+        try:
+            t1 = C.control_time(C.SOFTMAX, ROWS, cols, C.FP8_E4M3, P)
+            t2 = C.control_time(C.LAYERNORM, ROWS, cols, C.FP8_E4M3, P)
+            t0 = C.control_time(C.SOFTMAX, ROWS, cols, C.FP8_E4M3, 1)
+        except C.CreditError:
+            continue
+        K = C.screen(C.dataflow(C.SCAN), P)[1]
+        t_ctrl = (t1 - t0) + (K // 2 - 1) * max(0.0, t2 - t1)
+        est.append({"P": P, "K": K, "T_ctrl_us": round(t_ctrl, 2), "stage_us": round(max(0.0, t2 - t1), 2),
+                    "T_save_us": 0.0, "dT_us": round(-t_ctrl, 2)})
+    out["scan_ordered_control"] = {"cols": cols, "per_P": est}
+    out["peak_GBps"], out["peak_source"] = peak, peak_kind
+    assert C.device_error() == C.OK
+    return out
+
+
 PATH_NAMES_SHORT = {0: "one_cta", 1: "two_pass", 2: "cluster"}
 
 
@@ -915,6 +970,7 @@ def main():
     ap.add_argument("--no-quant", action="store_true", help="skip the int8 quantisation table")
     ap.add_argument("--no-prec", action="store_true", help="skip the BF16 / FP8 softmax / log-sum-exp table")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch graph launch")
+    ap.add_argument("--no-controls", action="store_true", help="skip the negative controls (scan, stencil)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-seconds", type=float, default=60.0,

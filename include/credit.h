@@ -589,6 +589,62 @@ credit_status credit_set_trace(void *device_buf, int64_t bytes);
 credit_status credit_run_two_pass_noalloc(const credit_args *args, int32_t ctas_per_row,
                                           cudaStream_t stream);
 
+/* ------------------------------------------------------------------ structural screen and negative controls
+ * Before any clustered variant is generated, the profitability model rejects
+ * three dataflows by construction (Sec. III-D, last paragraph; the negative
+ * controls of Sec. IV-C), because a wider row cannot make them profitable:
+ *   CREDIT_SCREEN_NO_REUSE      no reduction stage whose statistics every
+ *                               element needs, or nothing the global-reread
+ *                               baseline reads twice (b_reread = 0: log-sum-exp,
+ *                               an elementwise op, a stencil)
+ *   CREDIT_SCREEN_ORDERED       the value a CTA applies depends on the CTAs
+ *                               before it in order (a scan's carries): the
+ *                               barrier count K grows with P instead of 2L
+ *   CREDIT_SCREEN_REMOTE_STATE  the CTAs must exchange data that grows with N
+ *                               (selection, top-k, medians), not the compact
+ *                               q_l statistics of Eq. 6
+ * CREDIT_SCREEN_CANDIDATE goes on to the Eq. 7-9 profitability test.
+ */
+typedef enum {
+    CREDIT_OP_SCAN = 12,     /* control: y_i = sum_{j <= i} x_j (inclusive prefix sum per row), FP32 */
+    CREDIT_OP_STENCIL = 13,  /* control: y_i = sum_{k=-r..r} w[k + r] x_{i+k}, zero-padded row ends, FP32 */
+    CREDIT_OP_SELECT = 14    /* control (screen only, no kernel): row-wise selection, e.g. top-k */
+} credit_control_op;
+typedef enum {
+    CREDIT_SCREEN_CANDIDATE = 0,
+    CREDIT_SCREEN_NO_REUSE = 1,
+    CREDIT_SCREEN_ORDERED = 2,
+    CREDIT_SCREEN_REMOTE_STATE = 3
+} credit_screen_verdict;
+typedef struct {
+    int32_t stages;               /* L: reduction stages before the reuse pass (0: none)                 */
+    int32_t ordered;              /* 1: stage results are ordered prefixes over the CTAs of a row        */
+    double q_sum;                 /* statistics each CTA exchanges per row, summed over the stages      */
+    double b_reread;              /* bytes per element the global-reread baseline reads a second time    */
+    double remote_bytes_per_elem; /* data each CTA must exchange per element of its slice (0: compact)   */
+} credit_dataflow;
+/* The dataflow of a forward op (credit_op), CREDIT_OP_QUANT_INT8 or a control
+ * op, for rows of in_dtype.  Pure host code.  CREDIT_ERR_INVALID_ARG for an
+ * unknown op. */
+credit_status credit_dataflow_of(int32_t op, credit_dtype in_dtype, credit_dataflow *out);
+/* The structural screen for cluster size P (1..16): *verdict gets a
+ * credit_screen_verdict, *K (may be NULL) the barrier count per row (2L, or
+ * 2L(P - 1) for ordered stages).  Pure host code. */
+credit_status credit_screen(const credit_dataflow *d, int32_t P, int32_t *verdict, int32_t *K);
+/* Plan of a control op (CREDIT_OP_SCAN / CREDIT_OP_STENCIL): the screen's
+ * verdict in *verdict (may be NULL), and the non-DSMEM global-memory path
+ * (path TWO_PASS: the scan one CTA per row, the stencil a grid over the
+ * row).  source = 3. */
+credit_status credit_plan_control(int32_t op, int64_t rows, int64_t cols, credit_plan_t *out, int32_t *verdict);
+/* Run a control op on FP32 device rows (row strides ld_in / ld_out elements,
+ * 0 = cols): the scan (in == out allowed) with one CTA per row, one read and
+ * one write of every element; the stencil with weights = 2 radius + 1 FP32
+ * values in device memory, radius 0..8, in != out, rows <= 65535.  The sums
+ * accumulate in FP32 (the scan's carry across tiles with Kahan
+ * compensation).  Asynchronous on `stream`. */
+credit_status credit_run_control(int32_t op, const float *in, float *out, int64_t rows, int64_t cols, int64_t ld_in,
+                                 int64_t ld_out, const float *weights, int32_t radius, cudaStream_t stream);
+
 /*
  * credit_set_wait_test -- test only: exercises the bounded-wait error path
  * without faulting anything.  wait_ns > 0 sets the limit of the staged

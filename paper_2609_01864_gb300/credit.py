@@ -20,6 +20,8 @@ LIB_PATH = os.path.join(_PKG, "_build", "libcredit.so")
 F32, BF16, FP8_E4M3, INT8 = 0, 1, 2, 3
 SOFTMAX, LOGSUMEXP, LAYERNORM, RMSNORM = 0, 1, 2, 3
 QUANT_INT8 = 11
+SCAN, STENCIL, SELECT = 12, 13, 14
+SCREEN_CANDIDATE, SCREEN_NO_REUSE, SCREEN_ORDERED, SCREEN_REMOTE_STATE = 0, 1, 2, 3
 PATH_AUTO, PATH_ONE_CTA, PATH_TWO_PASS, PATH_CLUSTER = -1, 0, 1, 2
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_INITIALIZED, ERR_CAPTURE, ERR_IO = range(8)
 OP_NAMES = {SOFTMAX: "softmax", LOGSUMEXP: "logsumexp", LAYERNORM: "layernorm", RMSNORM: "rmsnorm"}
@@ -160,6 +162,11 @@ class ModelInT(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in MODEL_IN_FIELDS] + [("ablation", ctypes.c_int32)]
 
 
+class DataflowT(ctypes.Structure):
+    _fields_ = [("stages", ctypes.c_int32), ("ordered", ctypes.c_int32), ("q_sum", ctypes.c_double),
+                ("b_reread", ctypes.c_double), ("remote_bytes_per_elem", ctypes.c_double)]
+
+
 class ModelOutT(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in MODEL_OUT_FIELDS]
 
@@ -191,6 +198,14 @@ def _extra_prototypes(L):
     L.credit_mlp_predict.argtypes = [fp, i64, fp]
     L.credit_mlp_grad.restype = i32
     L.credit_mlp_grad.argtypes = [fp, fp, fp, i64, fp, fp]
+    L.credit_dataflow_of.restype = i32
+    L.credit_dataflow_of.argtypes = [i32, i32, ctypes.POINTER(DataflowT)]
+    L.credit_screen.restype = i32
+    L.credit_screen.argtypes = [ctypes.POINTER(DataflowT), i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.credit_plan_control.restype = i32
+    L.credit_plan_control.argtypes = [i32, i64, i64, ctypes.POINTER(PlanT), ctypes.POINTER(i32)]
+    L.credit_run_control.restype = i32
+    L.credit_run_control.argtypes = [i32, vp, vp, i64, i64, i64, i64, vp, i32, vp]
     L.credit_set_wait_test.restype = i32
     L.credit_set_wait_test.argtypes = [i64, i32]
     L.credit_mlp_adam_step.restype = i32
@@ -559,6 +574,46 @@ def mlp_save(path: str):
 
 def mlp_load(path: str):
     _check(lib().credit_mlp_load(path.encode()), "credit_mlp_load")
+
+
+def dataflow(op: int, in_dtype: int = F32) -> DataflowT:
+    """credit_dataflow_of: the structural description of an op the screen reads."""
+    d = DataflowT()
+    _check(lib().credit_dataflow_of(op, in_dtype, ctypes.byref(d)), "credit_dataflow_of")
+    return d
+
+
+def screen(d: DataflowT, P: int = 16):
+    """credit_screen: (verdict, K) for cluster size P."""
+    v, k = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().credit_screen(ctypes.byref(d), P, ctypes.byref(v), ctypes.byref(k)), "credit_screen")
+    return v.value, k.value
+
+
+def plan_control(op: int, rows: int, cols: int):
+    """credit_plan_control: (plan, screen verdict) of a control op."""
+    p, v = PlanT(), ctypes.c_int32()
+    _check(lib().credit_plan_control(op, rows, cols, ctypes.byref(p), ctypes.byref(v)), "credit_plan_control")
+    return p, v.value
+
+
+def run_control(op: int, x, out, *, rows=None, cols=None, ld_in=0, ld_out=0, weights=None, stream=None) -> int:
+    """credit_run_control: the scan / stencil control ops on FP32 device rows (weights: FP32 device tensor of
+    2 r + 1 values for the stencil).  Raises CreditError on a non-OK status."""
+    if rows is None or cols is None:
+        rows, cols = x.shape[0], x.shape[-1]
+    radius = 0 if weights is None else (weights.numel() - 1) // 2
+    st = lib().credit_run_control(op, _ptr(x), _ptr(out), rows, cols, ld_in, ld_out, _ptr(weights), radius,
+                                  _stream(stream))
+    _check(st, "credit_run_control")
+    return st
+
+
+def run_control_status(*args, **kw) -> int:
+    try:
+        return run_control(*args, **kw)
+    except CreditError as e:
+        return e.status
 
 
 def set_wait_test(wait_ns: int = 0, extra_tx_bytes: int = 0) -> None:
