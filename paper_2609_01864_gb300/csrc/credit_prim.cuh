@@ -244,6 +244,11 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 __device__ __forceinline__ float exp_fast(float x) { return ex2_approx(x * kLog2e); }
+// exp(x - c / log2 e) as one FMA and one SFU op: 2^(x log2 e - c), with c the
+// caller's log2-domain offset (for a softmax, m log2 e + log2 S).  The offset
+// is rounded once, so the result carries an extra relative error of about
+// 2^-24 |c| ln 2 (1e-6 for |c| < 25).
+__device__ __forceinline__ float exp_off(float x, float c) { return ex2_approx(fmaf(x, kLog2e, -c)); }
 
 // ------------------------------------------------------------ element formats
 template <int DT> struct Fmt;

@@ -412,8 +412,10 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
             const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + g.s.h0) & 15u) == 0);
             const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + g.s.h0) & 15u) == 0);
             const float smul = (TOUT == DT_E4M3) ? 448.0f : ((OP == OP_SOFTMAX) ? 1.0f / st.b : 0.0f);
+            // softmax: y (or its FP8 code) = exp(x - M) * smul as one FMA and one SFU op
+            const float cL = (OP == OP_SOFTMAX) ? fmaf(st.a, kLog2e, -log2f(smul)) : 0.0f;
             auto h = [&](float x, float gm, float bt) -> float {
-                if constexpr (OP == OP_SOFTMAX) return exp_fast(x - st.a) * smul;
+                if constexpr (OP == OP_SOFTMAX) return exp_off(x, cL);
                 else if constexpr (OP == OP_Q8) return q8_code(x, st.a, st.b);
                 else return norm_h<OP>(x, st, gm, bt);
             };

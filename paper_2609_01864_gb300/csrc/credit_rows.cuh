@@ -259,19 +259,27 @@ __device__ __forceinline__ void copy_raw(unsigned char *dst, const unsigned char
 // ======================================================================
 template <int OP> struct Stream;
 
+template <int N>
+__device__ __forceinline__ float max_of(const float (&f)[N]) {
+    float mv = f[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j) mv = fmaxf(mv, f[j]);
+    return mv;
+}
+
 template <> struct Stream<OP_SOFTMAX> {  // online (max, sum exp)
     float m = -INFINITY, s = 0.0f;
+    float mL = INFINITY;                   // m log2 e: each exponential is one FMA and one SFU op
     template <int V> __device__ __forceinline__ void add(const float (&f)[V]) {
-        float mv = f[0];
-#pragma unroll
-        for (int j = 1; j < V; ++j) mv = fmaxf(mv, f[j]);
+        const float mv = max_of(f);
         if (mv == -INFINITY) return;
         if (mv > m) {
             s *= exp_fast(m - mv);
             m = mv;
+            mL = m * kLog2e;
         }
 #pragma unroll
-        for (int j = 0; j < V; ++j) s += exp_fast(f[j] - m);
+        for (int j = 0; j < V; ++j) s += exp_off(f[j], mL);
     }
     __device__ __forceinline__ void add1(float x) {
         float f[1] = {x};
@@ -282,11 +290,13 @@ template <> struct Stream<OP_SOFTMAX> {  // online (max, sum exp)
         if (s == 0.0f) {
             m = m2;
             s = s2;
+            mL = m * kLog2e;
             return;
         }
         const float M = fmaxf(m, m2);
         s = s * exp_fast(m - M) + s2 * exp_fast(m2 - M);
         m = M;
+        mL = m * kLog2e;
     }
     __device__ __forceinline__ float p0() const { return m; }
     __device__ __forceinline__ float p1() const { return s; }
@@ -927,8 +937,9 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                 const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + g.s.h0) & 15u) == 0);
                 const float inv = (OP == OP_SOFTMAX) ? 1.0f / st.b : 0.0f;
                 const float smul = (TOUT == DT_E4M3) ? 448.0f : inv;  // softmax: y (or its code) = exp(x - M) * smul
+                const float cL = (OP == OP_SOFTMAX) ? fmaf(st.a, kLog2e, -log2f(smul)) : 0.0f;  // as one exp_off
                 auto h = [&](float x, float gm, float bt) -> float {
-                    if constexpr (OP == OP_SOFTMAX) return exp_fast(x - st.a) * smul;
+                    if constexpr (OP == OP_SOFTMAX) return exp_off(x, cL);
                     else if constexpr (OP == OP_Q8) return q8_code(x, st.a, st.b);
                     else return norm_h<OP>(x, st, gm, bt) * qmul;
                 };
@@ -1083,16 +1094,17 @@ __device__ __forceinline__ void apply_sweep(const RowArgs &a, long long row, con
     const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + s.h0) & 15u) == 0);
     const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + s.h0) & 15u) == 0);
     if constexpr (OP == OP_SOFTMAX) {
-        const float inv = 1.0f / st.b;
-        const float mul = (TOUT == DT_E4M3) ? 448.0f : inv;
+        // y (or its FP8 code) = exp(x - M) * mul = 2^(x log2 e - (M log2 e - log2 mul)): one FMA, one SFU op
+        const float mul = (TOUT == DT_E4M3) ? 448.0f : 1.0f / st.b;
+        const float cL = fmaf(st.a, kLog2e, -log2f(mul));
         sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
             float y[V];
 #pragma unroll
-            for (int j = 0; j < V; ++j) y[j] = exp_fast(f[j] - st.a) * mul;
+            for (int j = 0; j < V; ++j) y[j] = exp_off(f[j], cL);
             store_group<TOUT, V>(out_row + i0 * osz, y, out_vec);
         });
         sweep_edges<TIN>(in_row, s, P, c, in_sc,
-                         [&](long long i, float x) { store_one<TOUT>(out_row + i * osz, exp_fast(x - st.a) * mul); });
+                         [&](long long i, float x) { store_one<TOUT>(out_row + i * osz, exp_off(x, cL)); });
     } else if constexpr (OP == OP_Q8) {
         sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
             float y[V];
