@@ -312,6 +312,22 @@ static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long lon
         if (G == 1 || groups / G >= 1024) consider(CREDIT_PATH_TWO_PASS, 1, G, 0, CREDIT_RETAIN_AUTO, 0.0f);
     const int Gs = two_pass_split(di.sm_count, rows, cols, isz);
     if (Gs > 1 && Gs != 2 && Gs != 4 && Gs != 8) consider(CREDIT_PATH_TWO_PASS, 1, Gs, 0, CREDIT_RETAIN_AUTO, 0.0f);
+    // predicted latency anchored on the measured baseline: T_B (calibration, Eq. 7) times the model's ratio of
+    // the pick to the baseline plan (the ratio is what the network learns; its per-shape level cancels)
+    credit_plan_t base;
+    double T_B = 0.0;
+    if (baseline_estimate(di, device, op, rows, cols, tin, tout, &base, &T_B) && T_B > 0.0) {
+        float fb[kIn], yb = 0.0f;
+        mlp_features(op, tin, tout, rows, cols, base.path, base.cluster_size, base.ctas_per_row,
+                     base.retain == CREDIT_RETAIN_TMEM, 0.0f, fb);
+        for (const Model &m : ens) {
+            float ym;
+            host_forward(m, fb, &ym);
+            yb += ym;
+        }
+        yb /= static_cast<float>(ens.size());
+        bp.predicted_us = static_cast<float>(T_B * std::exp2(static_cast<double>(best) - yb));
+    }
     *p = bp;
     return true;
 }

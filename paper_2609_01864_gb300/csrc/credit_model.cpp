@@ -222,6 +222,24 @@ static void baseline_plan(const DeviceInfo &di, int device, int op, long long ro
     }
 }
 
+bool baseline_estimate(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin, int tout,
+                       credit_plan_t *base, double *T_B_us) {
+    baseline_plan(di, device, op, rows, cols, tin, tout, base);
+    *T_B_us = 0.0;
+    if (device < 0 || device >= kMaxDev) return false;
+    Calib cal;
+    {
+        std::lock_guard<std::mutex> lk(g_cal_mu);
+        if (!g_cal[device].loaded) return false;
+        cal = g_cal[device];
+    }
+    const Bytes b = static_bytes(op, tin, tout, base->path == CREDIT_PATH_ONE_CTA);
+    const double bw = tb_bytes_per_us(cal, op, tin, rows, cols);
+    if (!(bw > 0)) return false;
+    *T_B_us = static_cast<double>(rows) * cols * b.b_B / bw;
+    return true;
+}
+
 // Score every legal P with Eq. 7-9.  Returns false without calibration.
 bool analytic_plan(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin, int tout,
                    int ablation, credit_plan_t *p, double *best_dT) {
@@ -538,6 +556,10 @@ credit_status credit_calibrate(const char *path, int64_t max_bytes) {
                 }
             }
     finish_calib(di, c);
+    {  // a learned model named by the calibration loaded before stays named by the new one
+        std::lock_guard<std::mutex> lk(g_cal_mu);
+        if (g_cal[dev].loaded) c.mlp_path = g_cal[dev].mlp_path;
+    }
     if (!write_calib(path, c, di)) return CREDIT_ERR_IO;
     std::lock_guard<std::mutex> lk(g_cal_mu);
     g_cal[dev] = c;

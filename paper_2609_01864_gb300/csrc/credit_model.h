@@ -25,6 +25,12 @@ bool learned_plan_no_cluster(const DeviceInfo &di, int device, int op, long long
 
 int two_pass_split(int sm_count, long long rows, long long cols, int isz);
 
+// The selected non-DSMEM baseline plan of a shape (Sec. IV-A) and its time
+// T_B (us) from the loaded calibration (Eq. 7's measured baseline timing,
+// interpolated over the calibration grid).  false (T_B = 0) without one.
+bool baseline_estimate(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin, int tout,
+                       credit_plan_t *base, double *T_B_us);
+
 }  // namespace credit
 
 extern "C" credit_status credit_mlp_load(const char *path);

@@ -224,6 +224,8 @@ def main(argv=None):
     ap.add_argument("--calib", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
                                                     "gb300.calib"))
     ap.add_argument("--from-csv", default="", help="retrain and evaluate from an earlier sweep's timings")
+    ap.add_argument("--target", default="relative", choices=["relative", "absolute"],
+                    help="log2 latency relative to the shape's mean over its candidates, or absolute")
     args = ap.parse_args(argv)
     from . import build as B
     B.build()
@@ -243,9 +245,19 @@ def main(argv=None):
     t_sweep = time.time() - t0
     train, test = synth.split_by_shape(len(shapes))
 
+    # targets: log2 latency, by default relative to the mean over the shape's candidates -- the planner ranks
+    # the candidates of one shape, so the level of a shape carries no information for it, and removing it
+    # leaves the network the within-shape differences to learn (the planner anchors absolute predictions on
+    # the calibration's baseline timing T_B)
+    level = {}
+    for r in rows:
+        level.setdefault(r["shape"], []).append(np.log2(r["us"]))
+    level = {k: float(np.mean(v)) for k, v in level.items()}
+
     def xy(shape_set):
         X = np.stack([features_of(r) for r in rows if r["shape"] in shape_set])
-        y = np.array([np.log2(r["us"]) for r in rows if r["shape"] in shape_set], dtype=np.float32)
+        y = np.array([np.log2(r["us"]) - (level[r["shape"]] if args.target == "relative" else 0.0)
+                      for r in rows if r["shape"] in shape_set], dtype=np.float32)
         return X, y
 
     t1 = time.time()
@@ -274,7 +286,7 @@ def main(argv=None):
                "train_loss_first_last": [float(curve[0]), float(curve[-1])], "sweep_s": round(t_sweep, 1),
                "epochs": epochs, "validation_accuracy_by_epochs": val_acc,
                "train_s": round(t_train, 1), "reps": args.reps, "cap_gib": args.cap_gib,
-               "members": args.members}
+               "members": args.members, "target": args.target}
     with open(os.path.join(args.out, "sweep_gb300_summary.json"), "w") as f:
         json.dump(summary, f, indent=1)
     print(json.dumps(summary))
