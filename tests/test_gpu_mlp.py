@@ -105,7 +105,8 @@ def read_weights(path):
 
 def test_predict_matches_fp64_forward_per_sample():
     """credit_mlp_predict of the committed ensemble, sample by sample, against the FP64 forward of the same
-    weights (features of 300 sweep candidates): relative error <= 1e-5 in log2 latency."""
+    weights (features of 300 sweep candidates): error <= 1e-5 of max(|y*|, 1) in log2 latency (the outputs are
+    latencies relative to a shape's mean, near 0, as LSE outputs can be: the FP32 bound of reading r7)."""
     from paper_2609_01864_gb300 import sweep as S
     path = os.path.join(DATA, "gb300_mlp.txt")
     C.mlp_load(path)
@@ -119,7 +120,7 @@ def test_predict_matches_fp64_forward_per_sample():
         xs = (X.astype(np.float64) - fm) / fs
         ref += OM.forward(p, xs)[0] * ts + tm
     ref /= len(members)
-    assert np.max(np.abs(got - ref) / np.abs(ref)) <= 1e-5
+    assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)) <= 1e-5
 
 
 @pytest.mark.parametrize("step", [1, 7, 1000])
