@@ -156,7 +156,8 @@ credit_status credit_rmsnorm(const void *in, void *out, int64_t rows, int64_t co
  *                 G >= 1 for TWO_PASS (G > 1 uses the workspace)
  *   threads       threads per CTA (multiple of 32; 0 = default).  Staged
  *                 paths: reducer + writer threads + one producer warp
- *                 (96..288); two-pass: 64..1024
+ *                 (96..288); two-pass: 64..1024 (default 512 for FP32 rows,
+ *                 256 for BF16 / FP8 rows)
  *   reducer_threads  staged paths: threads that reduce and exchange (the rest
  *                 of the non-producer threads write); multiple of 32, 0 =
  *                 default (half)

@@ -711,9 +711,11 @@ credit_status run_with_plan(int device, const credit_args *a, const credit_plan_
         return CREDIT_OK;
     }
 
-    // TWO_PASS
+    // TWO_PASS.  Default CTA: 512 threads for FP32 rows, 256 for BF16 / FP8 rows (more CTAs per SM keep
+    // more loads in flight: softmax / log-sum-exp over 4096 x 128K-256K BF16 and FP8 rows measured 6-13%
+    // faster than with 512, 1024 slower still)
     const int G = p->ctas_per_row;
-    const int threads = p->threads ? p->threads : 512;
+    const int threads = p->threads ? p->threads : (isz <= 2 ? 256 : 512);
     if (G == 1) {
         credit_status st = prepare_kernel(d, ks.tp_fused, false);
         if (st != CREDIT_OK) return st;

@@ -224,6 +224,8 @@ def main(argv=None):
     ap.add_argument("--calib", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
                                                     "gb300.calib"))
     ap.add_argument("--from-csv", default="", help="retrain and evaluate from an earlier sweep's timings")
+    ap.add_argument("--extra-shapes", type=int, default=300,
+                    help="training-only shapes from the wide-row corner (rows 2^U(10,14), cols 2^U(14,20))")
     ap.add_argument("--target", default="relative", choices=["relative", "absolute"],
                     help="log2 latency relative to the shape's mean over its candidates, or absolute")
     args = ap.parse_args(argv)
@@ -236,14 +238,19 @@ def main(argv=None):
         print(f"note: {e}", file=sys.stderr)
     cap = int(args.cap_gib * 2 ** 30)
     shapes = synth.sweep_shapes(args.shapes, cap_bytes=cap)
+    # training-only shapes from the wide-row corner (thousands of rows of 16K-1M columns, up to the byte cap),
+    # which the log-uniform draw above reaches rarely: shape ids from len(shapes) on, never in the held-out split
+    extra = synth.sweep_shapes(args.extra_shapes, seed=synth.SEED_SWEEP + 11, cap_bytes=cap,
+                               rows_log2=(10.0, 14.0), cols_log2=(14.0, 20.0)) if args.extra_shapes > 0 else []
     t0 = time.time()
     if args.from_csv:
         rows = read_csv(args.from_csv)
-        shapes = shapes[:1 + max(r["shape"] for r in rows)]
+        rows = [r for r in rows if r["shape"] < len(shapes) + len(extra)]
     else:
-        rows = run_sweep(shapes, args.reps, cap, log=sys.stderr)
+        rows = run_sweep(shapes + extra, args.reps, cap, log=sys.stderr)
     t_sweep = time.time() - t0
     train, test = synth.split_by_shape(len(shapes))
+    extra_ids = list(range(len(shapes), len(shapes) + len(extra)))
 
     # targets: log2 latency, by default relative to the mean over the shape's candidates -- the planner ranks
     # the candidates of one shape, so the level of a shape carries no information for it, and removing it
@@ -264,14 +271,14 @@ def main(argv=None):
     # epochs chosen on a validation split of the training shapes (the held-out
     # test shapes are used once, for the final report)
     fit_idx, val_idx = synth.split_by_shape(len(train), seed=synth.SEED_SWEEP + 7, train_frac=0.85)
-    fit_set, val_set = {train[i] for i in fit_idx}, [train[i] for i in val_idx]
+    fit_set, val_set = {train[i] for i in fit_idx} | set(extra_ids), [train[i] for i in val_idx]
     Xf, yf = xy(fit_set)
     val_acc = {}
     for ep in args.epoch_grid:
         C.mlp_train_ensemble(Xf, yf, members=args.members, epochs=ep, batch=256, lr=2e-3, seed=0)
         val_acc[ep] = evaluate(rows, val_set)[0]["learned"]
     epochs = max(args.epoch_grid, key=lambda e: (val_acc[e], -e))
-    Xtr, ytr = xy(set(train))
+    Xtr, ytr = xy(set(train) | set(extra_ids))
     curve = C.mlp_train_ensemble(Xtr, ytr, members=args.members, epochs=epochs, batch=256, lr=2e-3, seed=0)
     t_train = time.time() - t1
     acc, n_test = evaluate(rows, test)
@@ -282,6 +289,8 @@ def main(argv=None):
         csv_out += ".new"
     write_csv(csv_out, rows)
     summary = {"shapes": len(shapes), "timings": len(rows), "train_shapes": len(train), "test_shapes": n_test,
+               "extra_train_shapes": len(extra),
+               "extra_distribution": "rows 2^U(10,14), cols 2^U(14,20), dtype and op uniform, I/O <= the cap",
                "pick_rule": "pick within 5% of the measured best candidate", "pick_accuracy": acc,
                "train_loss_first_last": [float(curve[0]), float(curve[-1])], "sweep_s": round(t_sweep, 1),
                "epochs": epochs, "validation_accuracy_by_epochs": val_acc,
