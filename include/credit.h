@@ -391,10 +391,14 @@ credit_status credit_bwd_plan_check(const credit_bwd_args *args, const credit_pl
  * in a CUDA graph.  Each row: elements in_base[in_off .. in_off + cols) ->
  * out_base[out_off ..) of the same dtype (offsets in elements; rows may be
  * packed with any alignment); op is CREDIT_OP_SOFTMAX or CREDIT_OP_RMSNORM
- * (gamma = 1, eps = 1e-6).  Narrow rows run one per CTA (one-CTA path), wide
- * rows split over the cluster with the DSMEM exchange (cluster path), rows
- * beyond the staging capacity stream twice within the cluster.  The project's
- * addition; the paper runs one shape per launch.
+ * (gamma = 1, eps = 1e-6).  Each row is staged over the fewest CTAs of the
+ * cluster, w = 1, 2, 4, ... P, whose slices fit the staging capacity; P / w
+ * rows of one width share the cluster in one work item, the w CTAs of a row
+ * exchanging partials over DSMEM (w = 1: the one-CTA path, w = P: the cluster
+ * path).  Rows beyond the capacity at w = P stream twice within the cluster.
+ * Info: narrow_items counts the items of width 1, wide_items those of width
+ * > 1, huge_items the streamed rows.  The project's addition; the paper runs
+ * one shape per launch.
  */
 typedef struct {
     int64_t in_off, out_off, cols;
@@ -500,25 +504,27 @@ credit_status credit_load_model(const char *path);
 
 /* ------------------------------------------------------------------ learned model
  * A 3 x 64 ReLU MLP predicting log2 of a candidate plan's latency (us) from
- * 20 features (credit_mlp_features), trained on the GPU by the library's own
+ * 21 features (credit_mlp_features), trained on the GPU by the library's own
  * FP32 kernels (forward, backward, Adam; no tensor cores).  With
  * CREDIT_MODEL=learned, credit_plan picks the legal candidate with the
  * smallest predicted latency; the analytic model stays the fallback.  The
  * paper has no learned model; this is the project's addition.
  */
-#define CREDIT_MLP_FEATURES 20
+#define CREDIT_MLP_FEATURES 21
 int64_t credit_mlp_num_params(void);
 /* Features of candidate (path, P, G, retain, fill_share) for (op, dtypes, rows,
- * cols) into out[20]: log2 rows, log2 cols, input dtype one-hot, op one-hot,
+ * cols) into out[21]: log2 rows, log2 cols, input dtype one-hot, op one-hot,
  * path one-hot (one-CTA, two-pass, cluster), log2 P, log2 G, log2 algorithmic
  * bytes, output bytes per element, log2 input bytes per CTA, log2 CTAs per
  * SM, 1 when a staged path retains the slice in tensor memory (retain =
- * CREDIT_RETAIN_TMEM; AUTO and SMEM give 0), and the fill share of a cluster
- * plan (0 for the other paths).  fill_share outside [0, 1]:
+ * CREDIT_RETAIN_TMEM; AUTO and SMEM give 0), the fill share of a cluster
+ * plan (0 for the other paths), and 1 when cols * element size is a multiple
+ * of 16 bytes (contiguous rows all start on the 16-byte grid, where the staged
+ * kernels keep gamma / beta in shared memory).  fill_share outside [0, 1]:
  * CREDIT_ERR_INVALID_ARG. */
 credit_status credit_mlp_features(int32_t op, int32_t in_dtype, int32_t out_dtype, int64_t rows, int64_t cols,
                                   int32_t path, int32_t P, int32_t G, int32_t retain, float fill_share, float *out);
-/* Train one network from scratch on n host samples (X n x 20, y = log2 us),
+/* Train one network from scratch on n host samples (X n x 21, y = log2 us),
  * replacing the loaded model: minibatch
  * Adam on the MSE of standardised targets; He-initialised from `seed`.
  * loss_curve (NULL or `epochs` floats) gets the mean training loss per epoch. */

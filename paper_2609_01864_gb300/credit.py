@@ -488,7 +488,7 @@ class Ragged:
             pass
 
 
-MLP_FEATURES = 20
+MLP_FEATURES = 21
 
 
 def _fptr(a):

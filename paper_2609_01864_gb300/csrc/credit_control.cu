@@ -21,8 +21,8 @@
 //                   thread, shuffle scans of the thread and warp totals, and
 //                   a carry across tiles kept with Kahan compensation.
 //   k_ctrl_stencil  row-wise stencil of radius r <= 8 with zero padding at the
-//                   row ends; each thread writes 4 consecutive outputs from
-//                   the 4 + 2r inputs around them.
+//                   row ends; a CTA stages the inputs of 4096 outputs in
+//                   shared memory once and every thread writes 16 of them.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -42,6 +42,7 @@ namespace {
 
 constexpr int kScanThreads = 512;
 constexpr int kStencilThreads = 256;
+constexpr int kStencilTile = 4096;  // outputs per CTA
 constexpr int kMaxRadius = 8;
 
 __device__ __forceinline__ float warp_inclusive_scan(float v) {
@@ -108,35 +109,58 @@ __global__ void __launch_bounds__(kScanThreads) k_ctrl_scan(const float *__restr
     }
 }
 
+// One CTA per tile of kStencilTile outputs of a row: the inputs the tile
+// needs (kStencilTile + 2r, widened to 16-byte address boundaries) are loaded
+// once into shared memory -- every thread issues all of its float4 loads
+// before storing any, so a CTA keeps 16 KiB in flight -- float4 where the
+// whole vector lies inside the row, zero outside it.  Thread t then computes
+// outputs t, t + T, t + 2T, ... of the tile: a warp's shared reads and global
+// stores are consecutive.
 __global__ void __launch_bounds__(kStencilThreads) k_ctrl_stencil(const float *__restrict__ in,
                                                                   float *__restrict__ out, long long cols,
                                                                   long long ld_in, long long ld_out,
                                                                   const float *__restrict__ weights, int r) {
     __shared__ float w[2 * kMaxRadius + 1];
-    if (threadIdx.x < 2 * r + 1) w[threadIdx.x] = weights[threadIdx.x];
-    __syncthreads();
+    __shared__ __align__(16) float tile[kStencilTile + 2 * kMaxRadius + 8];
+    constexpr int kQ = (kStencilTile + 2 * kMaxRadius + 8) / 4 / kStencilThreads + 1;  // float4 loads per thread
+    const int tid = threadIdx.x;
+    if (tid < 2 * r + 1) w[tid] = weights[tid];
     const long long row = blockIdx.y;
     const float *x = in + row * ld_in;
     float *y = out + row * ld_out;
-    const long long i0 = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
-    if (i0 >= cols) return;
-    float win[4 + 2 * kMaxRadius];
-    for (int k = 0; k < 4 + 2 * r; ++k) {
-        const long long j = i0 - r + k;
-        win[k] = (j >= 0 && j < cols) ? __ldg(x + j) : 0.0f;
-    }
-    float o[4];
+    const long long t0 = static_cast<long long>(blockIdx.x) * kStencilTile;
+    const long long need_lo = t0 - r, need_hi = min(t0 + kStencilTile, cols) + r;
+    // first index at or below need_lo whose address is 16-byte aligned (x is 4-byte aligned)
+    const long long lo = need_lo - static_cast<long long>((reinterpret_cast<uintptr_t>(x) / 4 + need_lo) & 3);
+    const int nq = static_cast<int>((need_hi - lo + 3) / 4);
+    float4 v[kQ];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        float acc = 0.0f;
-        for (int k = 0; k <= 2 * r; ++k) acc = fmaf(w[k], win[q + k], acc);
-        o[q] = acc;
+    for (int u = 0; u < kQ; ++u) {
+        const int q = tid + u * kStencilThreads;
+        const long long j = lo + 4LL * q;
+        if (q >= nq) {
+            v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        } else if (j >= 0 && j + 3 < cols) {
+            v[u] = *reinterpret_cast<const float4 *>(x + j);
+        } else {
+            v[u].x = (j >= 0 && j < cols) ? x[j] : 0.0f;
+            v[u].y = (j + 1 >= 0 && j + 1 < cols) ? x[j + 1] : 0.0f;
+            v[u].z = (j + 2 >= 0 && j + 2 < cols) ? x[j + 2] : 0.0f;
+            v[u].w = (j + 3 >= 0 && j + 3 < cols) ? x[j + 3] : 0.0f;
+        }
     }
-    if (i0 + 3 < cols && ((reinterpret_cast<uintptr_t>(y + i0) & 15u) == 0)) {
-        *reinterpret_cast<float4 *>(y + i0) = make_float4(o[0], o[1], o[2], o[3]);
-    } else {
-        for (int q = 0; q < 4; ++q)
-            if (i0 + q < cols) y[i0 + q] = o[q];
+#pragma unroll
+    for (int u = 0; u < kQ; ++u) {
+        const int q = tid + u * kStencilThreads;
+        if (q < nq) *reinterpret_cast<float4 *>(tile + 4 * q) = v[u];
+    }
+    __syncthreads();
+    const int off = static_cast<int>(t0 - r - lo);  // tile index of input t0 - r
+    const int n_out = static_cast<int>(min(static_cast<long long>(kStencilTile), cols - t0));
+    for (int o = tid; o < n_out; o += kStencilThreads) {
+        float acc = 0.0f;
+        for (int m = 0; m <= 2 * r; ++m) acc = fmaf(w[m], tile[off + o + m], acc);
+        y[t0 + o] = acc;
     }
 }
 
@@ -195,8 +219,7 @@ credit_status credit_plan_control(int32_t op, int64_t rows, int64_t cols, credit
     std::memset(out, 0, sizeof(*out));
     out->path = CREDIT_PATH_TWO_PASS;  // the non-DSMEM global-memory path
     out->cluster_size = 1;
-    out->ctas_per_row = op == CREDIT_OP_SCAN ? 1 : static_cast<int32_t>((cols + 4 * kStencilThreads - 1) /
-                                                                        (4 * kStencilThreads));
+    out->ctas_per_row = op == CREDIT_OP_SCAN ? 1 : static_cast<int32_t>((cols + kStencilTile - 1) / kStencilTile);
     out->threads = op == CREDIT_OP_SCAN ? kScanThreads : kStencilThreads;
     out->source = 3;
     if (verdict) *verdict = v;
@@ -221,7 +244,7 @@ credit_status credit_run_control(int32_t op, const float *in, float *out, int64_
         k_ctrl_scan<<<static_cast<unsigned>(rows), kScanThreads, 0, stream>>>(in, out, cols, li, lo);
         e = cudaGetLastError();
     } else {
-        const long long bx = (cols + 4LL * kStencilThreads - 1) / (4LL * kStencilThreads);
+        const long long bx = (cols + kStencilTile - 1) / kStencilTile;
         if (bx > 0x7FFFFFFFLL || rows > 65535) return CREDIT_ERR_UNSUPPORTED;
         k_ctrl_stencil<<<dim3(static_cast<unsigned>(bx), static_cast<unsigned>(rows)), kStencilThreads, 0, stream>>>(
             in, out, cols, li, lo, weights, radius);

@@ -64,4 +64,8 @@ float *device_workspace(int device, size_t *floats);
 cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, size_t smem, int cluster, cudaStream_t s,
                           void **args);
 
+// Generation of the planner's inputs (calibration, learned model): bumped by
+// every change to them, which empties the plan cache of credit_plan_ex.
+void bump_plan_generation();
+
 }  // namespace credit

@@ -32,7 +32,7 @@ namespace credit {
 
 namespace {
 
-constexpr int kIn = 20, kH = 64;
+constexpr int kIn = 21, kH = 64;
 // fill candidates of cluster plans that leave SMs idle (share of the rows)
 constexpr float kFillShares[] = {0.15f, 0.2f, 0.3f, 0.4f};
 constexpr int kFillMinIdle = 16;
@@ -237,6 +237,9 @@ void mlp_features(int op, int tin, int tout, long long rows, long long cols, int
     f[17] = static_cast<float>(std::log2(static_cast<double>(rows) * split / 152.0));
     f[18] = retain_tm ? 1.0f : 0.0f;
     f[19] = fill;
+    // contiguous rows all start on the 16-byte grid: the staged kernels then keep gamma / beta in shared
+    // memory and use whole 16-byte groups from each row's first element
+    f[20] = (cols * dtype_size(tin)) % 16 == 0 ? 1.0f : 0.0f;
 }
 
 static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long long rows, long long cols, int tin,
@@ -498,8 +501,11 @@ credit_status credit_mlp_train_ensemble(const float *X, const float *y, int64_t 
                                            m == 0 ? loss_curve : nullptr, &ens[static_cast<size_t>(m)]);
         if (st != CREDIT_OK) return st;
     }
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_models = ens;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_models = ens;
+    }
+    bump_plan_generation();
     return CREDIT_OK;
 }
 
@@ -577,8 +583,11 @@ credit_status credit_mlp_load(const char *path) {
     }
     std::fclose(f);
     if (!ok) return CREDIT_ERR_IO;
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_models = ens;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_models = ens;
+    }
+    bump_plan_generation();
     return CREDIT_OK;
 }
 

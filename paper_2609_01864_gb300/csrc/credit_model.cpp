@@ -439,6 +439,7 @@ credit_status credit_load_model(const char *path) {
         std::lock_guard<std::mutex> lk(g_cal_mu);
         g_cal[dev] = c;
     }
+    bump_plan_generation();
     if (!c.mlp_path.empty()) {
         std::string p = c.mlp_path;
         if (p[0] != '/') {  // relative to the calibration file
@@ -561,8 +562,11 @@ credit_status credit_calibrate(const char *path, int64_t max_bytes) {
         if (g_cal[dev].loaded) c.mlp_path = g_cal[dev].mlp_path;
     }
     if (!write_calib(path, c, di)) return CREDIT_ERR_IO;
-    std::lock_guard<std::mutex> lk(g_cal_mu);
-    g_cal[dev] = c;
+    {
+        std::lock_guard<std::mutex> lk(g_cal_mu);
+        g_cal[dev] = c;
+    }
+    bump_plan_generation();
     return CREDIT_OK;
 }
 

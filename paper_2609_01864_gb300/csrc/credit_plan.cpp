@@ -6,14 +6,48 @@
 // path.  Without calibration data the built-in heuristic below is used; the
 // analytic model of Eq. 7-9 and the learned model plug in through
 // credit_model.cpp.
+#include <atomic>
 #include <cstdlib>
-#include <initializer_list>
 #include <cstring>
+#include <initializer_list>
+#include <mutex>
+#include <unordered_map>
 
 #include "credit_host.h"
 #include "credit_model.h"
 
 namespace credit {
+
+// Plans chosen by credit_plan_ex, per (device, op, rows, cols, dtypes): the
+// learned planner evaluates every candidate through the network ensemble on
+// the host, which costs more than a short launch, so a call without a plan
+// reuses the choice made for the same shape.  Emptied when the calibration or
+// the model changes; bypassed while CREDIT_FORCE_PATH or CREDIT_MODEL select
+// a planner by environment.
+namespace {
+struct PlanKey {
+    int dev, op, tin, tout;
+    long long rows, cols;
+    bool operator==(const PlanKey &o) const {
+        return dev == o.dev && op == o.op && tin == o.tin && tout == o.tout && rows == o.rows && cols == o.cols;
+    }
+};
+struct PlanKeyHash {
+    size_t operator()(const PlanKey &k) const {
+        uint64_t h = 1469598103934665603ull;
+        const long long v[6] = {k.dev, k.op, k.tin, k.tout, k.rows, k.cols};
+        for (long long x : v) h = (h ^ static_cast<uint64_t>(x)) * 1099511628211ull;
+        return static_cast<size_t>(h);
+    }
+};
+std::mutex g_plan_mu;
+std::unordered_map<PlanKey, credit_plan_t, PlanKeyHash> g_plan_cache;
+std::atomic<unsigned long long> g_plan_gen{0};
+unsigned long long g_cache_gen = 0;
+constexpr size_t kPlanCacheMax = 4096;
+}  // namespace
+
+void bump_plan_generation() { g_plan_gen.fetch_add(1); }
 
 static bool env_force(const DeviceInfo *di, credit_plan_t *p, long long cols, int tin) {
     const char *fp = std::getenv("CREDIT_FORCE_PATH");
@@ -141,9 +175,32 @@ credit_status credit_plan_ex(credit_op op, int64_t rows, int64_t cols, credit_dt
     const DeviceInfo *di = device_info(dev);
     if (!di) return CREDIT_ERR_NOT_INITIALIZED;
     if (env_force(di, out, cols, in_dtype)) return CREDIT_OK;
+    const char *menv = std::getenv("CREDIT_MODEL");
+    const bool cache = !(menv && *menv);
+    const PlanKey key{dev, static_cast<int>(op), static_cast<int>(in_dtype), tout, rows, cols};
+    const unsigned long long gen = g_plan_gen.load();
+    if (cache) {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        if (g_cache_gen != gen) {
+            g_plan_cache.clear();
+            g_cache_gen = gen;
+        }
+        const auto it = g_plan_cache.find(key);
+        if (it != g_plan_cache.end()) {
+            *out = it->second;
+            return CREDIT_OK;
+        }
+    }
     // the calibration and the learned model cover the four ops of Sec. III-B; the quantiser takes the rule
-    if (!q8 && model_plan(*di, dev, op, rows, cols, in_dtype, tout, out)) return CREDIT_OK;
-    heuristic_plan(*di, dev, op, rows, cols, in_dtype, tout, out);
+    if (q8 || !model_plan(*di, dev, op, rows, cols, in_dtype, tout, out))
+        heuristic_plan(*di, dev, op, rows, cols, in_dtype, tout, out);
+    if (cache) {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        if (g_cache_gen == gen) {
+            if (g_plan_cache.size() >= kPlanCacheMax) g_plan_cache.clear();
+            g_plan_cache[key] = *out;
+        }
+    }
     return CREDIT_OK;
 }
 

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 namespace credit {
@@ -234,6 +235,40 @@ __device__ __forceinline__ float ex2_approx(float x) {
     asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// 2^x on the SFU with subnormal results flushed to zero (ex2.approx.ftz: the
+// bare SFU op).  For terms of a softmax sum whose largest term is 1: a flushed
+// term is below 2^-126, so N of them move the sum by less than N 2^-126.
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// 2^x for two halves at once (ex2.approx.f16x2: relative error about 2^-9.9);
+// the FP8 softmax output codes, whose spacing is 2^-3 relative, are decided
+// from it.
+__device__ __forceinline__ __half2 ex2_h2(__half2 x) {
+    uint32_t y;
+    asm("ex2.approx.f16x2 %0, %1;" : "=r"(y) : "r"(*reinterpret_cast<const uint32_t *>(&x)));
+    return *reinterpret_cast<const __half2 *>(&y);
+}
+// Sum of V values (V = 2, 4, 8, 16) as a pairwise tree on packed f32x2 adds.
+template <int V>
+__device__ __forceinline__ float sum_tree(const float (&e)[V]) {
+    if constexpr (V == 1) {
+        return e[0];
+    } else if constexpr (V == 2) {
+        return e[0] + e[1];
+    } else {
+        float h[V / 2];
+#pragma unroll
+        for (int j = 0; j < V / 4; ++j) {
+            const float2 r = __fadd2_rn(make_float2(e[4 * j], e[4 * j + 1]), make_float2(e[4 * j + 2], e[4 * j + 3]));
+            h[2 * j] = r.x;
+            h[2 * j + 1] = r.y;
+        }
+        return sum_tree<V / 2>(h);
+    }
+}
 constexpr float kLog2e = 1.4426950408889634f;
 // 1/x on the SFU (rcp.approx: relative error below 2^-22 for normal x; one
 // instruction, no special-case branch).  The counts it inverts are positive
@@ -244,11 +279,29 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 __device__ __forceinline__ float exp_fast(float x) { return ex2_approx(x * kLog2e); }
-// exp(x - c / log2 e) as one FMA and one SFU op: 2^(x log2 e - c), with c the
-// caller's log2-domain offset (for a softmax, m log2 e + log2 S).  The offset
-// is rounded once, so the result carries an extra relative error of about
-// 2^-24 |c| ln 2 (1e-6 for |c| < 25).
-__device__ __forceinline__ float exp_off(float x, float c) { return ex2_approx(fmaf(x, kLog2e, -c)); }
+// exp(x - m) 2^c as 2^((x - m) log2 e + c): one subtraction, one FMA, one SFU
+// op.  The difference x - m is exact for the terms near the maximum m
+// (Sterbenz), so the error depends on |x - m| (relative 2^-24 |x - m| log2 e
+// ln 2 at most, from rounding the exponent, plus log2 e's own rounding), not on
+// |m|: logits of any magnitude keep the FP32 bound.  c is the caller's
+// log2-domain scale (-log2 S for a softmax, log2 448 for FP8 codes).
+__device__ __forceinline__ float exp_sub(float x, float m, float c) { return ex2_approx(fmaf(x - m, kLog2e, c)); }
+// exp_sub over a group, two elements per packed f32x2 subtraction and FMA.
+template <int V>
+__device__ __forceinline__ void exp_sub_group(const float (&f)[V], float m, float c, float (&y)[V]) {
+    if constexpr (V % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < V; j += 2) {
+            const float2 t = __ffma2_rn(__fadd2_rn(make_float2(f[j], f[j + 1]), make_float2(-m, -m)),
+                                        make_float2(kLog2e, kLog2e), make_float2(c, c));
+            y[j] = ex2_approx(t.x);
+            y[j + 1] = ex2_approx(t.y);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) y[j] = exp_sub(f[j], m, c);
+    }
+}
 
 // ------------------------------------------------------------ element formats
 template <int DT> struct Fmt;

@@ -4,14 +4,20 @@
 //
 // Work items, built on the host from the row list (widest first, dealt
 // round-robin to the persistent clusters):
-//   narrow  up to P rows, one per CTA, each staged whole in its CTA's shared
-//           memory (no exchange; the one-CTA path)
-//   wide    one row split over the P CTAs of the cluster (Eq. 2), each slice
-//           staged once, partials exchanged over DSMEM (Eq. 5), output
-//           written from shared memory (the cluster path)
-//   huge    a row whose slices exceed the staging capacity: each CTA sweeps
-//           its part in HBM, the partials are exchanged, then the part is
-//           read again and written (the two-pass schedule inside a cluster)
+//   staged  P / w rows, each split over w CTAs of the cluster (w = 1, 2, 4,
+//           ..., P: the smallest power of two whose slices fit one CTA's
+//           staging capacity; Eq. 2-3): every slice staged once in shared
+//           memory, the partials of a row exchanged over DSMEM among its w
+//           CTAs (Eq. 5), the output written from shared memory.  w = 1 is
+//           the one-CTA path, w = P the cluster path of one row.
+//   huge    a row whose slices exceed the staging capacity even over all P
+//           CTAs: each CTA sweeps its part in HBM, the partials are exchanged,
+//           then the part is read again and written (the two-pass schedule
+//           inside a cluster)
+// Exchanges among changing subsets of the cluster: a CTA's slots are reused
+// by every item, so each item ends with a split cluster barrier that every
+// CTA executes (arrive once it has read its slots, wait before the next
+// item's pushes); each CTA tracks the phase of its own exchange mbarrier.
 // The op is a per-row field; the element type is a template parameter.
 #include <cuda_runtime.h>
 
@@ -35,7 +41,7 @@ using namespace credit;
 
 namespace {
 
-enum : int { ITEM_NARROW = 0, ITEM_WIDE = 1, ITEM_HUGE = 2 };
+enum : int { ITEM_STAGED = 0, ITEM_HUGE = 2 };
 
 struct RRow {
     long long in_off, out_off, cols;  // elements
@@ -44,8 +50,10 @@ struct RRow {
 };
 struct RItem {
     int kind;
-    int count;      // rows in a narrow item
+    int count;      // staged: rows in the item (<= P / width)
     long long row;  // first row (index into the row table)
+    int width;      // staged: CTAs per row (a power of two <= P); huge: P
+    int pad;
 };
 struct RaggedArgs {
     const unsigned char *in;
@@ -58,7 +66,7 @@ struct RaggedArgs {
     unsigned *err;
 };
 
-constexpr int kRCtrl = 1280;  // [0,128) mbarriers, [128,640) slots [2][16][4], [640,1152) reduction scratch (128 floats)
+constexpr int kRCtrl = 1280;  // [0,128) mbarriers, [128,384) slots [16][4], [640,1152) reduction scratch (128 floats)
 constexpr int kRChunk = 16384;
 
 template <int TIN>
@@ -98,34 +106,37 @@ __device__ __forceinline__ float2 stats_from_smem(int op, const unsigned char *b
     return block_reduce_stream<OP_RMS>(rs, red, 0);
 }
 
-// Exchange (P > 1) with the cluster: every thread returns the combined stats.
+// Exchange among the w CTAs of a row (ranks base .. base + w - 1 of the
+// cluster; this CTA is number cs of them): every thread returns the combined
+// statistics.  Partial of CTA cs lands in slot cs of each of them, pushed
+// with st.async onto the receiver's exchange mbarrier (Eq. 5); xph is this
+// CTA's phase of that mbarrier.  The caller's per-item cluster barrier keeps
+// the next item's pushes behind this combine's reads of the slots.
 template <int TIN>
-__device__ __forceinline__ Stats exchange_combine(int op, float2 part, float *slots, uint64_t *xbar, int &nx, int P,
-                                                  int c, const RowSlice &s, long long N, float eps, unsigned *err) {
+__device__ __forceinline__ Stats exchange_sub(int op, float2 part, float *slots, uint64_t *xbar, uint32_t &xph,
+                                             int base, int w, int cs, const RowSlice &s, long long N, float eps,
+                                             unsigned *err) {
     constexpr int V = Fmt<TIN>::V;
-    const int par = nx & 1;
-    const uint32_t phase = static_cast<uint32_t>((nx >> 1) & 1);
-    ++nx;
     Stats st;
-    if (P > 1) {
+    if (w > 1) {
         const int tid = threadIdx.x;
-        float *mine = slots + (par * 16 + c) * 4;
-        if (tid < P) {
-            if (tid == c) {
+        float *mine = slots + cs * 4;
+        if (tid < w) {
+            if (tid == cs) {
                 mine[0] = part.x;
                 mine[1] = part.y;
             } else {
                 fence_release_smem_cluster();  // this CTA's earlier reads of the slots first
-                st_async_v2f32(mapa_shared(smem_addr(mine), tid), part.x, part.y,
-                               mapa_shared(smem_addr(&xbar[par]), tid));
+                const uint32_t peer = static_cast<uint32_t>(base + tid);
+                st_async_v2f32(mapa_shared(smem_addr(mine), peer), part.x, part.y, mapa_shared(smem_addr(xbar), peer));
             }
         }
-        if (tid == 0) mbar_arrive_expect_tx(&xbar[par], static_cast<uint32_t>((P - 1) * 8));
+        if (tid == 0) mbar_arrive_expect_tx(xbar, static_cast<uint32_t>((w - 1) * 8));
         __syncthreads();
-        mbar_wait_bounded_cluster(&xbar[par], phase, err);
-        const float *sl = slots + par * 16 * 4;
-        st = op == OP_SOFTMAX ? combine_partials<OP_SOFTMAX>(sl, 4, P, s, V, N, eps)
-                              : combine_partials<OP_RMS>(sl, 4, P, s, V, N, eps);
+        mbar_wait_bounded_cluster(xbar, xph, err);
+        xph ^= 1u;
+        st = op == OP_SOFTMAX ? combine_partials<OP_SOFTMAX>(slots, 4, w, s, V, N, eps)
+                              : combine_partials<OP_RMS>(slots, 4, w, s, V, N, eps);
     } else {
         const float p1[2] = {part.x, part.y};
         st = op == OP_SOFTMAX ? combine_partials<OP_SOFTMAX>(p1, 2, 1, s, V, N, eps)
@@ -142,7 +153,7 @@ __device__ __forceinline__ float h_of(int op, float x, const Stats &st, float in
 template <int TIN>
 __global__ void __launch_bounds__(512, 1) k_ragged(const RaggedArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);       // [0..14) chunks, [14..16) exchange
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);       // [0..14) chunks, [14] exchange
     uint64_t *xbar = mbar + 14;
     float *slots = reinterpret_cast<float *>(smem + 128);
     float *red = reinterpret_cast<float *>(smem + 640);
@@ -161,23 +172,26 @@ __global__ void __launch_bounds__(512, 1) k_ragged(const RaggedArgs a) {
         cluster_arrive_release();
         cluster_wait_acquire();  // peers' exchange barriers are initialised
     }
-    uint32_t phase_bits = 0;
-    int nx = 0;
+    uint32_t phase_bits = 0, xph = 0;
+    bool pending = false;  // this CTA has arrived on the per-item cluster barrier and not yet waited
     for (long long it = cl; it < a.n_items; it += ncl) {
         const RItem item = a.items[it];
-        bool active = true;
-        long long ri = item.row;
-        if (item.kind == ITEM_NARROW) {
-            active = c < item.count;
-            ri = item.row + c;
+        if (P > 1 && pending) {  // every CTA has read its slots of the previous item: pushes may follow
+            cluster_wait_acquire();
+            pending = false;
         }
+        const bool huge = item.kind == ITEM_HUGE;
+        const int w = huge ? P : item.width;      // CTAs per row
+        const int sub = c / w, cs = c % w;        // which row of the item, and which slice of it
+        const bool active = huge || sub < item.count;
+        const long long ri = item.row + (huge ? 0 : sub);
         const RRow rw = a.rows[active ? ri : item.row];
         const int op = rw.op;
         const long long N = rw.cols;
         const unsigned char *row = a.in + rw.in_off * isz;
         unsigned char *orow = a.out + rw.out_off * isz;
-        const int Pslice = item.kind == ITEM_NARROW ? 1 : P;
-        const int cslice = item.kind == ITEM_NARROW ? 0 : c;
+        const int Pslice = w;
+        const int cslice = cs;
         const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(row), N, isz, Pslice, cslice);
         const long long ng = s.g_hi - s.g_lo;
         const bool own_head = cslice == 0, own_tail = cslice == Pslice - 1;
@@ -199,13 +213,11 @@ __global__ void __launch_bounds__(512, 1) k_ragged(const RaggedArgs a) {
             if (active)
                 part = stats_from_smem<TIN>(op, buf, ng, s, own_head, own_tail, row, mbar, phase_bits, nch, red,
                                             a.err);
-            Stats st;
-            if (item.kind == ITEM_WIDE) {
-                st = exchange_combine<TIN>(op, part, slots, xbar, nx, P, c, s, N, a.eps, a.err);
-            } else {
-                const float p1[2] = {part.x, part.y};
-                st = op == OP_SOFTMAX ? combine_partials<OP_SOFTMAX>(p1, 2, 1, s, V, N, a.eps)
-                                      : combine_partials<OP_RMS>(p1, 2, 1, s, V, N, a.eps);
+            Stats st{};
+            if (active) st = exchange_sub<TIN>(op, part, slots, xbar, xph, sub * w, w, cs, s, N, a.eps, a.err);
+            if (P > 1) {  // this CTA's slot reads are done
+                cluster_arrive_release();
+                pending = true;
             }
             if (!active) continue;
             const float inv = op == OP_SOFTMAX ? 1.0f / st.b : 0.0f;
@@ -238,7 +250,11 @@ __global__ void __launch_bounds__(512, 1) k_ragged(const RaggedArgs a) {
             });
             const float2 part = op == OP_SOFTMAX ? block_reduce_stream<OP_SOFTMAX>(sm, red, 0)
                                                  : block_reduce_stream<OP_RMS>(rs, red, 0);
-            const Stats st = exchange_combine<TIN>(op, part, slots, xbar, nx, P, c, s, N, a.eps, a.err);
+            const Stats st = exchange_sub<TIN>(op, part, slots, xbar, xph, 0, P, c, s, N, a.eps, a.err);
+            if (P > 1) {
+                cluster_arrive_release();
+                pending = true;
+            }
             const float inv = op == OP_SOFTMAX ? 1.0f / st.b : 0.0f;
             sweep_global<TIN>(row, s, P, c, 1.0f, [&](long long i0, const float(&f)[V]) {
                 float y[V];
@@ -252,6 +268,7 @@ __global__ void __launch_bounds__(512, 1) k_ragged(const RaggedArgs a) {
         }
     }
     if (P > 1) {
+        if (pending) cluster_wait_acquire();
         cluster_arrive_release();  // nobody exits while a peer may still push into it
         cluster_wait_acquire();
     }
@@ -288,33 +305,38 @@ struct credit_ragged {
 
 namespace {
 
-// Items for launch shape (P, cap): rows sorted widest first.
+// Items for launch shape (P, cap): rows sorted widest first; each row gets
+// the smallest power-of-two width w <= P whose slices (plus 32 bytes for an
+// unaligned head and tail) fit cap bytes, consecutive rows of one width share
+// an item (P / w of them), and rows that fit no width are huge.
 void build_items(const std::vector<RRow> &rows, int isz, int P, int cap, std::vector<RItem> &items,
                  std::vector<RRow> &sorted, long long &nn, long long &nw, long long &nh) {
     sorted = rows;
     std::stable_sort(sorted.begin(), sorted.end(), [](const RRow &x, const RRow &y) { return x.cols > y.cols; });
     items.clear();
     nn = nw = nh = 0;
-    const long long per_cta = cap;  // bytes
+    auto width_of = [&](const RRow &r) -> int {
+        const long long groups = r.cols * isz / 16 + 1;
+        for (int w = 1; w <= P; w *= 2)
+            if ((groups + w - 1) / w * 16 + 32 <= cap) return w;
+        return 0;
+    };
     size_t i = 0;
     while (i < sorted.size()) {
-        const long long bytes = sorted[i].cols * isz;
-        if (bytes + 32 <= per_cta && (P == 1 || bytes <= per_cta / 2)) {
-            // narrow: up to P consecutive rows, one per CTA
-            RItem it{ITEM_NARROW, 0, static_cast<long long>(i)};
-            while (i < sorted.size() && it.count < P && sorted[i].cols * isz + 32 <= per_cta) {
-                ++it.count;
-                ++i;
-            }
-            items.push_back(it);
-            ++nn;
-        } else {
-            const long long slice = ((bytes / 16 + P - 1) / P) * 16;
-            RItem it{slice + 32 <= per_cta ? ITEM_WIDE : ITEM_HUGE, 1, static_cast<long long>(i)};
-            items.push_back(it);
-            ++(it.kind == ITEM_WIDE ? nw : nh);
+        const int w = width_of(sorted[i]);
+        if (w == 0) {
+            items.push_back(RItem{ITEM_HUGE, 1, static_cast<long long>(i), P, 0});
+            ++nh;
+            ++i;
+            continue;
+        }
+        RItem it{ITEM_STAGED, 0, static_cast<long long>(i), w, 0};
+        while (i < sorted.size() && it.count < P / w && width_of(sorted[i]) == w) {
+            ++it.count;
             ++i;
         }
+        items.push_back(it);
+        ++(w == 1 ? nn : nw);
     }
 }
 

@@ -412,10 +412,10 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
             const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + g.s.h0) & 15u) == 0);
             const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + g.s.h0) & 15u) == 0);
             const float smul = (TOUT == DT_E4M3) ? 448.0f : ((OP == OP_SOFTMAX) ? 1.0f / st.b : 0.0f);
-            // softmax: y (or its FP8 code) = exp(x - M) * smul as one FMA and one SFU op
-            const float cL = (OP == OP_SOFTMAX) ? fmaf(st.a, kLog2e, -log2f(smul)) : 0.0f;
+            // softmax: y (or its FP8 code) = exp(x - M) * smul = 2^((x - M) log2 e + log2 smul)
+            const float cL = (OP == OP_SOFTMAX) ? log2f(smul) : 0.0f;  // exp_sub's log2-domain scale
             auto h = [&](float x, float gm, float bt) -> float {
-                if constexpr (OP == OP_SOFTMAX) return exp_off(x, cL);
+                if constexpr (OP == OP_SOFTMAX) return exp_sub(x, st.a, cL);
                 else if constexpr (OP == OP_Q8) return q8_code(x, st.a, st.b);
                 else return norm_h<OP>(x, st, gm, bt);
             };

@@ -269,17 +269,61 @@ __device__ __forceinline__ float max_of(const float (&f)[N]) {
 
 template <> struct Stream<OP_SOFTMAX> {  // online (max, sum exp)
     float m = -INFINITY, s = 0.0f;
-    float mL = INFINITY;                   // m log2 e: each exponential is one FMA and one SFU op
+    __device__ __forceinline__ void raise(float mv) {
+        if (mv > m) {
+            s *= ex2_ftz((m - mv) * kLog2e);
+            m = mv;
+        }
+    }
+    // The terms 2^((f - m) log2 e) of a group (the difference first, so the
+    // error does not grow with |m|), two at a time on packed f32x2 ops,
+    // subnormal terms flushed (ex2_ftz), summed as a tree.
     template <int V> __device__ __forceinline__ void add(const float (&f)[V]) {
         const float mv = max_of(f);
         if (mv == -INFINITY) return;
-        if (mv > m) {
-            s *= exp_fast(m - mv);
-            m = mv;
-            mL = m * kLog2e;
-        }
+        raise(mv);
+        if constexpr (V % 4 == 0) {
+            float e[V];
 #pragma unroll
-        for (int j = 0; j < V; ++j) s += exp_off(f[j], mL);
+            for (int j = 0; j < V; j += 2) {
+                const float2 t = __fmul2_rn(__fadd2_rn(make_float2(f[j], f[j + 1]), make_float2(-m, -m)),
+                                            make_float2(kLog2e, kLog2e));
+                e[j] = ex2_ftz(t.x);
+                e[j + 1] = ex2_ftz(t.y);
+            }
+            s += sum_tree<V>(e);
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) s += ex2_ftz((f[j] - m) * kLog2e);
+        }
+    }
+    // One 16-byte group of E4M3 codes q of a row whose elements are x = a q
+    // (a = |in_scale|; a negative scale has been folded into the codes' sign
+    // bits).  The group maximum is taken on the decoded halves (E4M3 is a
+    // subset of FP16, and x is increasing in q); each difference x - m is one
+    // FMA, a q - m rounded once, two codes per packed op.
+    __device__ __forceinline__ void add_e4m3(const uint4 &w, float a) {
+        __half2 h[8];
+        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            __half2_raw r0 = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(u[k] & 0xFFFFu), __NV_E4M3);
+            __half2_raw r1 = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(u[k] >> 16), __NV_E4M3);
+            h[2 * k] = *reinterpret_cast<__half2 *>(&r0);
+            h[2 * k + 1] = *reinterpret_cast<__half2 *>(&r1);
+        }
+        const __half2 mx = __hmax2(__hmax2(__hmax2(h[0], h[1]), __hmax2(h[2], h[3])),
+                                   __hmax2(__hmax2(h[4], h[5]), __hmax2(h[6], h[7])));
+        raise(fmaxf(__low2float(mx), __high2float(mx)) * a);
+        float e[16];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float2 t = __fmul2_rn(__ffma2_rn(__half22float2(h[k]), make_float2(a, a), make_float2(-m, -m)),
+                                        make_float2(kLog2e, kLog2e));
+            e[2 * k] = ex2_ftz(t.x);
+            e[2 * k + 1] = ex2_ftz(t.y);
+        }
+        s += sum_tree<16>(e);
     }
     __device__ __forceinline__ void add1(float x) {
         float f[1] = {x};
@@ -290,13 +334,11 @@ template <> struct Stream<OP_SOFTMAX> {  // online (max, sum exp)
         if (s == 0.0f) {
             m = m2;
             s = s2;
-            mL = m * kLog2e;
             return;
         }
         const float M = fmaxf(m, m2);
-        s = s * exp_fast(m - M) + s2 * exp_fast(m2 - M);
+        s = s * ex2_ftz((m - M) * kLog2e) + s2 * ex2_ftz((m2 - M) * kLog2e);
         m = M;
-        mL = m * kLog2e;
     }
     __device__ __forceinline__ float p0() const { return m; }
     __device__ __forceinline__ float p1() const { return s; }
@@ -937,9 +979,9 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                 const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + g.s.h0) & 15u) == 0);
                 const float inv = (OP == OP_SOFTMAX) ? 1.0f / st.b : 0.0f;
                 const float smul = (TOUT == DT_E4M3) ? 448.0f : inv;  // softmax: y (or its code) = exp(x - M) * smul
-                const float cL = (OP == OP_SOFTMAX) ? fmaf(st.a, kLog2e, -log2f(smul)) : 0.0f;  // as one exp_off
+                const float cL = (OP == OP_SOFTMAX) ? log2f(smul) : 0.0f;  // exp_sub's log2-domain scale
                 auto h = [&](float x, float gm, float bt) -> float {
-                    if constexpr (OP == OP_SOFTMAX) return exp_off(x, cL);
+                    if constexpr (OP == OP_SOFTMAX) return exp_sub(x, st.a, cL);
                     else if constexpr (OP == OP_Q8) return q8_code(x, st.a, st.b);
                     else return norm_h<OP>(x, st, gm, bt) * qmul;
                 };
@@ -1039,6 +1081,35 @@ __device__ __forceinline__ void sweep_global(const unsigned char *in_row, const 
     (void)c;
 }
 
+// sweep_global on the raw 16-byte groups: fn(first element index, group).
+template <int TIN, class F>
+__device__ __forceinline__ void sweep_global_raw(const unsigned char *in_row, const RowSlice &s,
+                                                 F &&fn /* fn(long long elem_index, const uint4 &) */) {
+    constexpr int V = Fmt<TIN>::V, isz = Fmt<TIN>::size;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const unsigned char *body = in_row + s.h0 * isz;
+    constexpr int U = 4;
+    for (long long g0 = s.g_lo + tid; g0 < s.g_hi; g0 += static_cast<long long>(U) * T) {
+        uint4 w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long g = g0 + static_cast<long long>(u) * T;
+            if (g < s.g_hi) w[u] = ld_global_v4(body + g * 16);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long g = g0 + static_cast<long long>(u) * T;
+            if (g < s.g_hi) fn(s.h0 + g * V, w[u]);
+        }
+    }
+}
+
+// Sign bits of 16 E4M3 codes flipped by `neg` (0x80808080 or 0): a row with a
+// negative input scale a becomes the row -q with scale |a|.
+__device__ __forceinline__ uint4 e4m3_fold_sign(uint4 w, uint32_t neg) {
+    return make_uint4(w.x ^ neg, w.y ^ neg, w.z ^ neg, w.w ^ neg);
+}
+
 // Edge elements of this CTA (head by thread 0 of CTA 0, tail by the last
 // thread of CTA P-1).
 template <int TIN, class F>
@@ -1057,7 +1128,13 @@ template <int OP, int TIN>
 __device__ __forceinline__ float2 stats_sweep(const RowArgs &a, const unsigned char *in_row, const RowSlice &s, int P,
                                               int c, float in_sc, float *red) {
     Stream<OP> st;
-    sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long, const float(&f)[Fmt<TIN>::V]) { st.add(f); });
+    if constexpr (TIN == DT_E4M3 && (OP == OP_SOFTMAX || OP == OP_LSE)) {
+        const uint32_t neg = in_sc < 0.0f ? 0x80808080u : 0u;
+        const float a = fabsf(in_sc);
+        sweep_global_raw<TIN>(in_row, s, [&](long long, const uint4 &w) { st.add_e4m3(e4m3_fold_sign(w, neg), a); });
+    } else {
+        sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long, const float(&f)[Fmt<TIN>::V]) { st.add(f); });
+    }
     sweep_edges<TIN>(in_row, s, P, c, in_sc, [&](long long, float x) { st.add1(x); });
     return block_reduce_stream<OP>(st, red, slice_count(s, Fmt<TIN>::V, P, c));
 }
@@ -1093,18 +1170,56 @@ __device__ __forceinline__ void apply_sweep(const RowArgs &a, long long row, con
     const bool out_vec = ((reinterpret_cast<uintptr_t>(out_row) + s.h0 * osz) % vec_bytes) == 0;
     const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + s.h0) & 15u) == 0);
     const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + s.h0) & 15u) == 0);
-    if constexpr (OP == OP_SOFTMAX) {
-        // y (or its FP8 code) = exp(x - M) * mul = 2^(x log2 e - (M log2 e - log2 mul)): one FMA, one SFU op
+    if constexpr (OP == OP_SOFTMAX && TIN == DT_E4M3 && TOUT == DT_E4M3) {
+        // E4M3 codes in and out: code = 448 exp(x - M) = 2^((a q - M) log2 e + log2 448) on the raw input
+        // codes q (sign folded as in the statistics): two packed FMAs per two codes, the exponent rounded
+        // to FP16 and raised by one packed SFU op, converted to two E4M3 codes at once.  The FP16
+        // rounding of the exponent (|t| < 16: error <= 2^-8) and the SFU's 2^-9.9 move a code's value by
+        // under 0.5% relative, a small part of an E4M3 step (2^-3 relative).
+        const float c8 = log2f(448.0f), M = st.a;
+        const uint32_t neg = in_sc < 0.0f ? 0x80808080u : 0u;
+        const float a1 = fabsf(in_sc);
+        sweep_global_raw<TIN>(in_row, s, [&](long long i0, const uint4 &w0) {
+            const uint4 w = e4m3_fold_sign(w0, neg);
+            const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+            uint32_t o[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t code2[2];
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    __half2_raw r = __nv_cvt_fp8x2_to_halfraw2(
+                        static_cast<__nv_fp8x2_storage_t>((u[k] >> (16 * hh)) & 0xFFFFu), __NV_E4M3);
+                    const float2 d = __ffma2_rn(__half22float2(*reinterpret_cast<__half2 *>(&r)),
+                                                make_float2(a1, a1), make_float2(-M, -M));
+                    const float2 t = __ffma2_rn(d, make_float2(kLog2e, kLog2e), make_float2(c8, c8));
+                    const __half2 e = ex2_h2(__float22half2_rn(t));
+                    code2[hh] = __nv_cvt_halfraw2_to_fp8x2(*reinterpret_cast<const __half2_raw *>(&e),
+                                                           __NV_SATFINITE, __NV_E4M3);
+                }
+                o[k] = (code2[0] & 0xFFFFu) | (code2[1] << 16);
+            }
+            unsigned char *p = out_row + i0;
+            if (out_vec) {
+                *reinterpret_cast<uint4 *>(p) = make_uint4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) p[k] = static_cast<unsigned char>(o[k >> 2] >> (8 * (k & 3)));
+            }
+        });
+        sweep_edges<TIN>(in_row, s, P, c, in_sc,
+                         [&](long long i, float x) { store_one<TOUT>(out_row + i, exp_sub(x, M, c8)); });
+    } else if constexpr (OP == OP_SOFTMAX) {
+        // y (or its FP8 code) = exp(x - M) * mul = 2^((x - M) log2 e + log2 mul)
         const float mul = (TOUT == DT_E4M3) ? 448.0f : 1.0f / st.b;
-        const float cL = fmaf(st.a, kLog2e, -log2f(mul));
+        const float cL = log2f(mul);
         sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
             float y[V];
-#pragma unroll
-            for (int j = 0; j < V; ++j) y[j] = exp_off(f[j], cL);
+            exp_sub_group<V>(f, st.a, cL, y);
             store_group<TOUT, V>(out_row + i0 * osz, y, out_vec);
         });
         sweep_edges<TIN>(in_row, s, P, c, in_sc,
-                         [&](long long i, float x) { store_one<TOUT>(out_row + i * osz, exp_off(x, cL)); });
+                         [&](long long i, float x) { store_one<TOUT>(out_row + i * osz, exp_sub(x, st.a, cL)); });
     } else if constexpr (OP == OP_Q8) {
         sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
             float y[V];

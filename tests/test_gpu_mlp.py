@@ -164,10 +164,39 @@ def test_learned_model_beats_the_analytic_model_on_held_out_shapes():
     from paper_2609_01864_gb300 import synth
     C.load_model(os.path.join(DATA, "gb300.calib"))
     rows = S.read_csv(os.path.join(DATA, "sweep_gb300.csv"))
-    n_shapes = 1 + max(r["shape"] for r in rows)
-    _, test = synth.split_by_shape(n_shapes)
-    acc, n = S.evaluate(rows, test)
     summary = json.load(open(os.path.join(DATA, "sweep_gb300_summary.json")))
+    # the split covers the log-uniform shapes only; shape ids from summary["shapes"] on are training-only
+    _, test = synth.split_by_shape(summary["shapes"])
+    acc, n = S.evaluate(rows, test)
     assert n == summary["test_shapes"]
     assert acc["learned"] > acc["analytic"] > 0.0
     assert acc["learned"] == pytest.approx(summary["pick_accuracy"]["learned"], abs=1e-9)
+
+
+def test_plan_cache_repeats_the_choice_and_follows_model_changes(monkeypatch):
+    """A call without a plan reuses the plan chosen for the same shape; loading a calibration or training a
+    model empties the cache, and CREDIT_MODEL bypasses it."""
+    import time
+    calib = os.path.join(DATA, "gb300.calib")
+    C.load_model(calib)
+    shape = (C.LAYERNORM, 4096, 65536, C.F32)
+    p1 = C.plan(*shape)
+    t0 = time.perf_counter()
+    for _ in range(200):
+        p = C.plan(*shape)
+    dt = (time.perf_counter() - t0) / 200
+    assert p.as_dict() == p1.as_dict()
+    assert dt < 50e-6, f"cached plan took {dt * 1e6:.1f} us"
+    monkeypatch.setenv("CREDIT_MODEL", "analytic")
+    pa = C.plan(*shape)
+    assert pa.source != 1  # the analytic model's plan, not the cached learned one
+    monkeypatch.delenv("CREDIT_MODEL")
+    assert C.plan(*shape).as_dict() == p1.as_dict()
+    # a different (tiny, random) model: the next plan is the new model's
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((512, C.MLP_FEATURES)).astype(np.float32)
+    C.mlp_train_ensemble(X, rng.standard_normal(512).astype(np.float32), members=1, epochs=2)
+    p2 = C.plan(*shape)
+    assert p2.source == 1 and p2.as_dict() != p1.as_dict()
+    C.load_model(calib)  # back to the committed model: the first choice again
+    assert C.plan(*shape).as_dict() == p1.as_dict()

@@ -74,6 +74,31 @@ def test_low_precision_paths_match_oracle(op, plan, dt, rows, cols):
     U.check_against_oracle(op, x, s, out_dtype=tout, plan=PLANS[plan], gamma=g, beta=b)
 
 
+@pytest.mark.parametrize("plan", ["one_cta", "cluster4", "two_pass_g1", "two_pass_g5"])
+@pytest.mark.parametrize("op", [C.SOFTMAX, C.LOGSUMEXP])
+@pytest.mark.parametrize("tout", [C.FP8_E4M3, C.F32])
+def test_fp8_rows_with_negative_and_zero_scales(op, plan, tout):
+    """E4M3 rows whose per-row scale is negative (x = scale * code flips the order of the codes), zero
+    (every x is 0: the uniform distribution), tiny or large, with codes spanning the whole E4M3 range
+    (+-448, subnormals, +-0): the softmax statistics and the FP8 output codes against the oracle."""
+    if op == C.LOGSUMEXP:
+        tout = C.F32
+    rows, cols = 12, 20011
+    g = torch.Generator().manual_seed(21)
+    codes = torch.randint(0, 256, (rows, cols), generator=g, dtype=torch.int16)
+    codes = torch.where((codes & 0x7F) == 0x7F, codes - 1, codes).to(torch.uint8)  # no NaN codes
+    codes[:, 0] = 0x7E   # +448
+    codes[:, 1] = 0xFE   # -448
+    codes[:, 2] = 0x01   # smallest subnormal
+    codes[:, 3] = 0x80   # -0
+    x = codes.view(torch.float8_e4m3fn)
+    sc = torch.tensor([-1.0, 0.0, 1e-3, -1e-3, 0.25, -0.25, 0.05, -0.02, 2.0 ** -20, -(2.0 ** -20), 0.01, -0.5],
+                      dtype=torch.float32)
+    if op == C.SOFTMAX and tout == C.F32:
+        sc = sc.clamp(-0.05, 0.05)  # |x - max| <= 45: every probability a normal FP32 number
+    U.check_against_oracle(op, x, sc, out_dtype=tout, plan=PLANS[plan])
+
+
 # --------------------------------------------------------------- config 1
 @pytest.mark.parametrize("plan", ["one_cta", "cluster4"])
 def test_softmax_256x4096_fp32_one_cta_and_cluster4(plan):

@@ -67,6 +67,47 @@ def test_ragged_kinds_match_oracle(force, monkeypatch):
         assert info["items"] == info["narrow_items"] + info["wide_items"] + info["huge_items"]
 
 
+@pytest.mark.parametrize("force", [("16", "2", "256"), ("2", "1", "128"), ("8", "13", "512")],
+                         ids=["p16_small_cap", "p2", "p8"])
+def test_ragged_every_width_class(force, monkeypatch):
+    """Rows sized so that every sub-cluster width w = 1, 2, 4, ..., P occurs, in runs whose lengths are
+    not multiples of P / w (items with idle sub-groups), next to rows that stream (huge)."""
+    monkeypatch.setenv("CREDIT_RAGGED_P", force[0])
+    monkeypatch.setenv("CREDIT_RAGGED_CHUNKS", force[1])
+    monkeypatch.setenv("CREDIT_RAGGED_THREADS", force[2])
+    P, cap = int(force[0]), int(force[1]) * 16384
+    rng = np.random.default_rng(int(force[0]) * 7 + int(force[1]))
+    for dt in (C.BF16, C.F32):
+        isz = 2 if dt == C.BF16 else 4
+        widths = []
+        w = 1
+        while w <= P:  # per class w: more elements than w / 2 CTAs can stage, few enough for w
+            lo = (cap - 32) * (w // 2) // isz + 8 if w > 1 else 1
+            hi = (cap - 48) * w // isz - 16 * w
+            n = int(rng.integers(1, 2 * (P // w) + 2))
+            widths += list(rng.integers(lo, hi, n))
+            w *= 2
+        widths += [cap * P // isz + 1000, cap * P // isz + 12345]  # beyond the cluster's staging: huge
+        widths += [1, 3, 17]
+        widths = np.array(rng.permutation(widths), dtype=np.int64)
+        ops = rng.integers(0, 2, len(widths))
+        ops = np.where(ops == 0, C.SOFTMAX, C.RMSNORM)
+        flat, rows, _ = packed_batch(widths, ops, dt, seed=dt + 5)
+        d_in = flat.cuda()
+        d_out = torch.full_like(d_in, float("nan"))
+        R = C.Ragged(rows, dt, d_in, d_out, tune=False)
+        info = R.info()
+        R.run()
+        torch.cuda.synchronize()
+        assert C.device_error() == C.OK
+        check_rows(flat, d_out, rows, dt, range(len(rows)))
+        assert not torch.isnan(d_out.float()).any()
+        R.close()
+        assert info["cluster_size"] == P
+        assert info["narrow_items"] > 0 and info["huge_items"] > 0
+        assert P == 1 or info["wide_items"] > 0
+
+
 def test_ragged_20000_rows_tuned_sampled_parity():
     widths, ops = synth.ragged_widths(20000, seed=synth.SEED_RAGGED)
     widths, ops = widths.numpy(), ops.numpy()

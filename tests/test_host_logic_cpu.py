@@ -26,7 +26,7 @@ def _lib():
 
 def test_features_of_a_cluster_candidate():
     f = C.mlp_features(C.RMSNORM, C.BF16, C.BF16, 4096, 131072, C.PATH_CLUSTER, 8, 1, C.RETAIN_TMEM, 0.25)
-    assert f.shape == (C.MLP_FEATURES,) == (20,)
+    assert f.shape == (C.MLP_FEATURES,) == (21,)
     assert f[0] == 12 and f[1] == 17
     assert list(f[2:5]) == [0, 1, 0]            # input BF16
     assert list(f[5:9]) == [0, 0, 0, 1]         # RMSNorm
@@ -37,6 +37,7 @@ def test_features_of_a_cluster_candidate():
     assert f[16] == pytest.approx(math.log2(131072 * 2 / 8 + 1))
     assert f[17] == pytest.approx(math.log2(4096 * 8 / 152))
     assert f[18] == 1 and f[19] == pytest.approx(0.25)
+    assert f[20] == 1                           # 131072 BF16 = 16 K groups: every row on the 16-byte grid
 
 
 def test_features_ignore_retention_and_fill_where_they_do_not_apply():
@@ -47,6 +48,9 @@ def test_features_ignore_retention_and_fill_where_they_do_not_apply():
     lse = C.mlp_features(C.LOGSUMEXP, C.FP8_E4M3, C.BF16, 10, 1000, C.PATH_ONE_CTA, 1, 1)
     assert lse[15] == 0                         # one FP32 value per row, counted in the bytes instead
     assert lse[14] == pytest.approx(math.log2(10 * 1000 * 1 + 10 * 4))
+    assert lse[20] == 0                         # 1000 FP8 codes: rows off the 16-byte grid
+    assert C.mlp_features(C.SOFTMAX, C.F32, C.F32, 8, 1002, C.PATH_TWO_PASS, 1, 1)[20] == 0
+    assert C.mlp_features(C.SOFTMAX, C.BF16, C.BF16, 8, 1000, C.PATH_TWO_PASS, 1, 1)[20] == 1
 
 
 @pytest.mark.parametrize("bad", [dict(op=4), dict(rows=0), dict(path=3), dict(retain=3), dict(fill_share=1.5),
