@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <climits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -47,7 +48,8 @@ struct Calib {
     double hbm_gbs = 0.0;
     std::map<int, std::vector<TbCell>> tb;     // key op * 8 + dtype
     std::map<int, std::vector<CtrlCell>> ctrl;  // key dtype
-    std::string mlp_path;
+    std::string mlp_path;   // as written in the file: absolute, or relative to the file's directory
+    std::string mlp_dir;    // the directory of the file it was read from (load time only)
 };
 Calib g_cal[kMaxDev];
 std::mutex g_cal_mu;
@@ -328,6 +330,21 @@ bool model_plan(const DeviceInfo &di, int device, int op, long long rows, long l
 }
 
 // ------------------------------------------------------------------ file I/O
+// "dir/" of "dir/name" ("" for a bare name), an absolute form of a path (the
+// path itself if it cannot be resolved), and whether two directories are one.
+static std::string dir_of(const char *path) {
+    const std::string s(path);
+    const size_t k = s.find_last_of('/');
+    return k == std::string::npos ? std::string() : s.substr(0, k + 1);
+}
+static std::string absolute(const std::string &p) {
+    char buf[PATH_MAX];
+    return realpath(p.c_str(), buf) ? std::string(buf) : p;
+}
+static bool same_dir(const std::string &a, const std::string &b) {
+    return absolute(a.empty() ? "." : a) == absolute(b.empty() ? "." : b);
+}
+
 static bool write_calib(const char *path, const Calib &c, const DeviceInfo &di) {
     FILE *f = std::fopen(path, "w");
     if (!f) return false;
@@ -434,6 +451,7 @@ credit_status credit_load_model(const char *path) {
     if (st != CREDIT_OK) return st;
     Calib c;
     if (!read_calib(path, c)) return CREDIT_ERR_IO;
+    c.mlp_dir = dir_of(path);
     finish_calib(*device_info(dev), c);
     {
         std::lock_guard<std::mutex> lk(g_cal_mu);
@@ -442,11 +460,7 @@ credit_status credit_load_model(const char *path) {
     bump_plan_generation();
     if (!c.mlp_path.empty()) {
         std::string p = c.mlp_path;
-        if (p[0] != '/') {  // relative to the calibration file
-            std::string dir(path);
-            const size_t k = dir.find_last_of('/');
-            p = (k == std::string::npos ? std::string() : dir.substr(0, k + 1)) + p;
-        }
+        if (p[0] != '/') p = dir_of(path) + p;  // relative to the calibration file
         if (credit_mlp_load(p.c_str()) != CREDIT_OK) return CREDIT_ERR_IO;
     }
     return CREDIT_OK;
@@ -557,9 +571,14 @@ credit_status credit_calibrate(const char *path, int64_t max_bytes) {
                 }
             }
     finish_calib(di, c);
-    {  // a learned model named by the calibration loaded before stays named by the new one
+    {  // a learned model named by the calibration loaded before stays named by the new one: by the same
+       // relative name in the same directory, else by its path from the old file's directory
         std::lock_guard<std::mutex> lk(g_cal_mu);
-        if (g_cal[dev].loaded) c.mlp_path = g_cal[dev].mlp_path;
+        if (g_cal[dev].loaded && !g_cal[dev].mlp_path.empty()) {
+            const Calib &o = g_cal[dev];
+            if (o.mlp_path[0] == '/' || same_dir(o.mlp_dir, dir_of(path))) c.mlp_path = o.mlp_path;
+            else c.mlp_path = absolute(o.mlp_dir + o.mlp_path);
+        }
     }
     if (!write_calib(path, c, di)) return CREDIT_ERR_IO;
     {

@@ -130,7 +130,9 @@ extern "C" credit_status credit_run_two_pass_noalloc(const credit_args *a, int32
     const int G = ctas_per_row;
     const long long rows_per_launch = kStaticPairs / G;
     const bool fp8_stage = (a->op == OP_LN || a->op == OP_RMS) && tout == DT_E4M3;
-    const unsigned threads = 512;
+    // the split two-pass path's default CTA size (credit_run_ex with threads = 0): the partials are then
+    // formed over the same thread slices and merged in the same order, so both entries agree bit for bit
+    const unsigned threads = isz <= 2 ? 256 : 512;
 
     RowArgs base{};
     base.in = static_cast<const unsigned char *>(a->in);

@@ -11,13 +11,20 @@
 //           CTAs (Eq. 5), the output written from shared memory.  w = 1 is
 //           the one-CTA path, w = P the cluster path of one row.
 //   huge    a row whose slices exceed the staging capacity even over all P
-//           CTAs: each CTA sweeps its part in HBM, the partials are exchanged,
-//           then the part is read again and written (the two-pass schedule
-//           inside a cluster)
+//           CTAs: each CTA streams its part through the staging buffer as a
+//           ring of bulk-copied chunks, the partials are exchanged, then the
+//           part is written: first the chunks the ring still holds, then the
+//           rest, read again (the two-pass schedule inside a cluster)
+// While a CTA writes a staged item, every chunk slot it has written out takes
+// the same chunk of the CTA's slice of its next item (a bulk copy issued at
+// once), so the loads of item i + 1 overlap the writes of item i; a next item
+// that streams is moved towards L2 instead.
 // Exchanges among changing subsets of the cluster: a CTA's slots are reused
-// by every item, so each item ends with a split cluster barrier that every
-// CTA executes (arrive once it has read its slots, wait before the next
-// item's pushes); each CTA tracks the phase of its own exchange mbarrier.
+// by every item that exchanges (w > 1 or huge), so each such item ends with a
+// split cluster barrier that every CTA executes (arrive once it has read its
+// slots, wait before the next exchanging item's pushes; items of width 1
+// exchange nothing and skip it); each CTA tracks the phase of its own
+// exchange mbarrier.
 // The op is a per-row field; the element type is a template parameter.
 #include <cuda_runtime.h>
 
@@ -90,18 +97,15 @@ __device__ __forceinline__ float2 stats_from_smem(int op, const unsigned char *b
         }
     }
     phase_bits ^= (nch >= 32 ? 0xFFFFFFFFu : ((1u << nch) - 1u));
-    if (own_head && tid == 0)
-        for (long long i = 0; i < s.h0; ++i) {
-            const float x = decode_one<TIN>(row + i * isz, 1.0f);
-            if (op == OP_SOFTMAX) sm.add1(x);
-            else rs.add1(x);
-        }
-    if (own_tail && tid == T - 1)
-        for (long long i = 0; i < s.t0; ++i) {
-            const float x = decode_one<TIN>(row + (s.h0 + s.G * V + i) * isz, 1.0f);
-            if (op == OP_SOFTMAX) sm.add1(x);
-            else rs.add1(x);
-        }
+    // edge elements, one per thread: head element tid, tail element T - 1 - tid
+    for (int e = 0; e < 2; ++e) {
+        const long long i = e == 0 ? ((own_head && tid < s.h0) ? tid : -1)
+                                   : ((own_tail && T - 1 - tid < s.t0) ? s.h0 + s.G * V + (T - 1 - tid) : -1);
+        if (i < 0) continue;
+        const float x = decode_one<TIN>(row + i * isz, 1.0f);
+        if (op == OP_SOFTMAX) sm.add1(x);
+        else rs.add1(x);
+    }
     if (op == OP_SOFTMAX) return block_reduce_stream<OP_SOFTMAX>(sm, red, 0);
     return block_reduce_stream<OP_RMS>(rs, red, 0);
 }
@@ -145,13 +149,127 @@ __device__ __forceinline__ Stats exchange_sub(int op, float2 part, float *slots,
     return st;
 }
 
+// Stream ng 16-byte groups from src (16-byte aligned) through buf as a ring of
+// R chunk slots: thread 0 keeps up to R bulk copies in flight and refills a
+// slot once every thread is done with it; fn(first group, groups, slot) runs
+// on every chunk in order.  The chunk barriers and their phases (phase_bits)
+// are the ones the staged items use.
+template <class F>
+__device__ __forceinline__ void ring_stream(const unsigned char *src, long long ng, unsigned char *buf, int R,
+                                            uint64_t *mbar, uint32_t &phase_bits, unsigned *err, uint64_t policy,
+                                            F &&fn) {
+    const long long body = ng * 16;
+    const long long nch = (body + kRChunk - 1) / kRChunk;
+    auto issue = [&](long long k, int slot) {
+        const long long off = k * kRChunk;
+        const uint32_t bytes = static_cast<uint32_t>(min(static_cast<long long>(kRChunk), body - off));
+        mbar_arrive_expect_tx(&mbar[slot], bytes);
+        bulk_g2s_hint(buf + static_cast<size_t>(slot) * kRChunk, src + off, bytes, &mbar[slot], policy);
+    };
+    if (threadIdx.x == 0)
+        for (int k = 0; k < R && k < nch; ++k) issue(k, k);
+    int slot = 0;
+    for (long long k = 0; k < nch; ++k) {
+        mbar_wait_bounded(&mbar[slot], (phase_bits >> slot) & 1u, err);
+        phase_bits ^= 1u << slot;
+        const long long g0 = k * (kRChunk / 16);
+        fn(g0, static_cast<int>(min(static_cast<long long>(kRChunk / 16), ng - g0)),
+           buf + static_cast<size_t>(slot) * kRChunk);
+        __syncthreads();  // the slot's data has been used by every thread
+        if (threadIdx.x == 0 && k + R < nch) issue(k + R, slot);
+        if (++slot == R) slot = 0;
+    }
+}
+
+// The second pass over a part that ring_stream has just streamed: its last
+// min(R, nch) chunks are still in their slots (chunk k in slot k % R), so
+// they are used first, without a copy, and each slot they free takes one of
+// the chunks that are read again (chunk j into slot (nch + j) % R).
+template <class F>
+__device__ __forceinline__ void ring_stream_again(const unsigned char *src, long long ng, unsigned char *buf, int R,
+                                                  uint64_t *mbar, uint32_t &phase_bits, unsigned *err,
+                                                  uint64_t policy, F &&fn) {
+    const long long body = ng * 16;
+    const long long nch = (body + kRChunk - 1) / kRChunk;
+    const long long kept = min(static_cast<long long>(R), nch), again = nch - kept;
+    auto slot_of = [&](long long k) { return static_cast<int>(k % R); };
+    auto issue = [&](long long j) {
+        const int slot = static_cast<int>((nch + j) % R);
+        const long long off = j * kRChunk;
+        const uint32_t bytes = static_cast<uint32_t>(min(static_cast<long long>(kRChunk), body - off));
+        mbar_arrive_expect_tx(&mbar[slot], bytes);
+        bulk_g2s_hint(buf + static_cast<size_t>(slot) * kRChunk, src + off, bytes, &mbar[slot], policy);
+    };
+    long long next = 0;  // the next chunk to read again
+    for (long long k = nch - kept; k < nch; ++k) {
+        const long long g0 = k * (kRChunk / 16);
+        fn(g0, static_cast<int>(min(static_cast<long long>(kRChunk / 16), ng - g0)),
+           buf + static_cast<size_t>(slot_of(k)) * kRChunk);
+        __syncthreads();
+        if (threadIdx.x == 0 && next < again) issue(next);
+        ++next;
+    }
+    for (long long j = 0; j < again; ++j) {
+        const int slot = static_cast<int>((nch + j) % R);
+        mbar_wait_bounded(&mbar[slot], (phase_bits >> slot) & 1u, err);
+        phase_bits ^= 1u << slot;
+        const long long g0 = j * (kRChunk / 16);
+        fn(g0, static_cast<int>(min(static_cast<long long>(kRChunk / 16), ng - g0)),
+           buf + static_cast<size_t>(slot) * kRChunk);
+        __syncthreads();
+        if (threadIdx.x == 0 && j + R < again) issue(j + R);
+    }
+}
+
 template <int TIN>
 __device__ __forceinline__ float h_of(int op, float x, const Stats &st, float inv) {
     return op == OP_SOFTMAX ? exp_fast(x - st.a) * inv : x * st.a;
 }
 
+// This CTA's slice of a later item, moved from HBM into L2 while the current
+// item is written (at most the staging capacity), so that its bulk copies
+// find it there.
+__device__ __forceinline__ void prefetch_next(const RaggedArgs &a, const RItem &nx, int P, int c, int isz) {
+    const bool huge = nx.kind == ITEM_HUGE;
+    const int w = huge ? P : nx.width;
+    const int sub = c / w, cs = c % w;
+    if (!huge && sub >= nx.count) return;
+    const RRow rw = a.rows[nx.row + (huge ? 0 : sub)];
+    const unsigned char *row = a.in + rw.in_off * isz;
+    const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(row), rw.cols, isz, w, cs);
+    const long long bytes = min((s.g_hi - s.g_lo) * 16, static_cast<long long>(a.cap));
+    if (bytes > 0) bulk_prefetch_l2(row + s.h0 * isz + s.g_lo * 16, static_cast<uint32_t>(bytes));
+}
+
+// Where this CTA's slice of a staged item lies (16-byte aligned start, bytes, chunks); false when the CTA has
+// no row in the item.
+struct SliceSrc {
+    const unsigned char *src;
+    uint32_t body;
+    int nch;
+};
+__device__ __forceinline__ bool staged_slice_of(const RaggedArgs &a, const RItem &it, int c, int isz, SliceSrc &o) {
+    const int w = it.width, sub = c / w, cs = c % w;
+    if (sub >= it.count) return false;
+    const RRow rw = a.rows[it.row + sub];
+    const unsigned char *row = a.in + rw.in_off * isz;
+    const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(row), rw.cols, isz, w, cs);
+    o.src = row + s.h0 * isz + s.g_lo * 16;
+    o.body = static_cast<uint32_t>((s.g_hi - s.g_lo) * 16);
+    o.nch = static_cast<int>((o.body + kRChunk - 1) / kRChunk);
+    return true;
+}
+// A staged slice is read once: its lines go first when L2 needs room, so
+// that a streamed part's lines stay for their second read.
+__device__ __forceinline__ void issue_chunk(unsigned char *buf, const SliceSrc &sl, int k, uint64_t *mbar) {
+    const uint32_t off = static_cast<uint32_t>(k) * kRChunk;
+    const uint32_t bytes = min(static_cast<uint32_t>(kRChunk), sl.body - off);
+    mbar_arrive_expect_tx(&mbar[k], bytes);
+    bulk_g2s_hint(buf + off, sl.src + off, bytes, &mbar[k], l2_evict_first_policy());
+}
+
 template <int TIN>
-__global__ void __launch_bounds__(512, 1) k_ragged(const RaggedArgs a) {
+__global__ void __launch_bounds__(256, 4) k_ragged(const RaggedArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);       // [0..14) chunks, [14] exchange
     uint64_t *xbar = mbar + 14;
@@ -174,14 +292,16 @@ __global__ void __launch_bounds__(512, 1) k_ragged(const RaggedArgs a) {
     }
     uint32_t phase_bits = 0, xph = 0;
     bool pending = false;  // this CTA has arrived on the per-item cluster barrier and not yet waited
+    int pre_issued = 0;    // thread 0: chunks of this item already requested while the previous one was written
     for (long long it = cl; it < a.n_items; it += ncl) {
         const RItem item = a.items[it];
-        if (P > 1 && pending) {  // every CTA has read its slots of the previous item: pushes may follow
+        const bool huge = item.kind == ITEM_HUGE;
+        const int w = huge ? P : item.width;      // CTAs per row
+        const bool xch = P > 1 && (huge || w > 1);  // this item exchanges partials over DSMEM
+        if (xch && pending) {  // every CTA has read its slots of the last exchanging item: pushes may follow
             cluster_wait_acquire();
             pending = false;
         }
-        const bool huge = item.kind == ITEM_HUGE;
-        const int w = huge ? P : item.width;      // CTAs per row
         const int sub = c / w, cs = c % w;        // which row of the item, and which slice of it
         const bool active = huge || sub < item.count;
         const long long ri = item.row + (huge ? 0 : sub);
@@ -199,50 +319,71 @@ __global__ void __launch_bounds__(512, 1) k_ragged(const RaggedArgs a) {
         const bool out_vec = ((reinterpret_cast<uintptr_t>(orow) + s.h0 * isz) & 15u) == 0;
         if (item.kind != ITEM_HUGE) {
             // ---- staged: TMA the slice into shared memory (chunks), reduce, [exchange], write
-            const uint32_t body = static_cast<uint32_t>(ng * 16);
-            const int nch = active ? static_cast<int>((body + kRChunk - 1) / kRChunk) : 0;
+            const SliceSrc cur{row + s.h0 * isz + s.g_lo * 16, static_cast<uint32_t>(ng * 16),
+                               active ? static_cast<int>((ng * 16 + kRChunk - 1) / kRChunk) : 0};
+            const int nch = cur.nch;
             __syncthreads();  // the previous item's reads of buf are done
             if (tid == 0)
-                for (int k = 0; k < nch; ++k) {
-                    const uint32_t off = static_cast<uint32_t>(k) * kRChunk;
-                    const uint32_t bytes = min(static_cast<uint32_t>(kRChunk), body - off);
-                    mbar_arrive_expect_tx(&mbar[k], bytes);
-                    bulk_g2s(buf + off, row + s.h0 * isz + s.g_lo * 16 + off, bytes, &mbar[k]);
-                }
+                for (int k = pre_issued; k < nch; ++k) issue_chunk(buf, cur, k, mbar);
+            pre_issued = 0;
             float2 part = make_float2(op == OP_SOFTMAX ? -INFINITY : 0.0f, 0.0f);
             if (active)
                 part = stats_from_smem<TIN>(op, buf, ng, s, own_head, own_tail, row, mbar, phase_bits, nch, red,
                                             a.err);
             Stats st{};
             if (active) st = exchange_sub<TIN>(op, part, slots, xbar, xph, sub * w, w, cs, s, N, a.eps, a.err);
-            if (P > 1) {  // this CTA's slot reads are done
+            if (xch) {  // this CTA's slot reads are done
                 cluster_arrive_release();
                 pending = true;
             }
+            // the next item: a staged slice is requested chunk by chunk as the slots free up below, a huge
+            // part is moved towards L2
+            SliceSrc nx{};
+            bool pre = false;
+            if (tid == 0 && it + ncl < a.n_items) {
+                const RItem ni = a.items[it + ncl];
+                if (ni.kind == ITEM_STAGED) pre = staged_slice_of(a, ni, c, isz, nx);
+                else prefetch_next(a, ni, P, c, isz);
+            }
             if (!active) continue;
             const float inv = op == OP_SOFTMAX ? 1.0f / st.b : 0.0f;
-            for (long long g = tid; g < ng; g += T) {
-                float f[V], y[V];
-                decode_group<TIN>(*reinterpret_cast<const uint4 *>(buf + g * 16), f, 1.0f);
+            for (int k = 0; k < nch; ++k) {
+                const long long gb = static_cast<long long>(k) * (kRChunk / 16);
+                const long long ge = min(ng, gb + kRChunk / 16);
+                for (long long g = gb + tid; g < ge; g += T) {
+                    float f[V], y[V];
+                    decode_group<TIN>(*reinterpret_cast<const uint4 *>(buf + g * 16), f, 1.0f);
 #pragma unroll
-                for (int q = 0; q < V; ++q) y[q] = h_of<TIN>(op, f[q], st, inv);
-                store_group<TIN, V>(orow + (i_base + g * V) * isz, y, out_vec);
-            }
-            if (own_head && tid == 0)
-                for (long long i = 0; i < s.h0; ++i)
-                    store_one<TIN>(orow + i * isz, h_of<TIN>(op, decode_one<TIN>(row + i * isz, 1.0f), st, inv));
-            if (own_tail && tid == T - 1)
-                for (long long i = 0; i < s.t0; ++i) {
-                    const long long e = s.h0 + s.G * V + i;
-                    store_one<TIN>(orow + e * isz, h_of<TIN>(op, decode_one<TIN>(row + e * isz, 1.0f), st, inv));
+                    for (int q = 0; q < V; ++q) y[q] = h_of<TIN>(op, f[q], st, inv);
+                    store_group<TIN, V>(orow + (i_base + g * V) * isz, y, out_vec);
                 }
+                __syncthreads();  // chunk k of this item is written: its slot takes chunk k of the next
+                if (tid == 0 && pre && k < nx.nch) issue_chunk(buf, nx, k, mbar);
+            }
+            if (tid == 0) pre_issued = pre ? min(nch, nx.nch) : 0;
+            for (int e = 0; e < 2; ++e) {  // edge elements, one per thread
+                const long long i = e == 0 ? ((own_head && tid < s.h0) ? tid : -1)
+                                           : ((own_tail && T - 1 - tid < s.t0) ? s.h0 + s.G * V + (T - 1 - tid) : -1);
+                if (i >= 0)
+                    store_one<TIN>(orow + i * isz, h_of<TIN>(op, decode_one<TIN>(row + i * isz, 1.0f), st, inv));
+            }
         } else {
-            // ---- streaming: sweep HBM, exchange, reread and write
+            // ---- streaming: this CTA's part through the staging buffer as a ring of chunks (many bulk copies in
+            // flight), exchange, then the part again (mostly from L2: the cluster read it moments before) and write
             Stream<OP_SOFTMAX> sm;
             Stream<OP_RMS> rs;
-            sweep_global<TIN>(row, s, P, c, 1.0f, [&](long long, const float(&f)[V]) {
-                if (op == OP_SOFTMAX) sm.add(f);
-                else rs.add(f);
+            const unsigned char *src = row + s.h0 * isz + s.g_lo * 16;
+            const int R = min(a.cap / kRChunk, 14);
+            __syncthreads();  // the previous item's reads of buf are done
+            // first pass: keep the lines in L2 for the second
+            ring_stream(src, ng, buf, R, mbar, phase_bits, a.err, l2_evict_last_policy(),
+                        [&](long long, int gn, const unsigned char *cb) {
+                for (int g = tid; g < gn; g += T) {
+                    float f[V];
+                    decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, 1.0f);
+                    if (op == OP_SOFTMAX) sm.add(f);
+                    else rs.add(f);
+                }
             });
             sweep_edges<TIN>(row, s, P, c, 1.0f, [&](long long, float x) {
                 if (op == OP_SOFTMAX) sm.add1(x);
@@ -251,16 +392,20 @@ __global__ void __launch_bounds__(512, 1) k_ragged(const RaggedArgs a) {
             const float2 part = op == OP_SOFTMAX ? block_reduce_stream<OP_SOFTMAX>(sm, red, 0)
                                                  : block_reduce_stream<OP_RMS>(rs, red, 0);
             const Stats st = exchange_sub<TIN>(op, part, slots, xbar, xph, 0, P, c, s, N, a.eps, a.err);
-            if (P > 1) {
+            if (xch) {
                 cluster_arrive_release();
                 pending = true;
             }
             const float inv = op == OP_SOFTMAX ? 1.0f / st.b : 0.0f;
-            sweep_global<TIN>(row, s, P, c, 1.0f, [&](long long i0, const float(&f)[V]) {
-                float y[V];
+            ring_stream_again(src, ng, buf, R, mbar, phase_bits, a.err, l2_evict_first_policy(),
+                              [&](long long g0, int gn, const unsigned char *cb) {
+                for (int g = tid; g < gn; g += T) {
+                    float f[V], y[V];
+                    decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, 1.0f);
 #pragma unroll
-                for (int q = 0; q < V; ++q) y[q] = h_of<TIN>(op, f[q], st, inv);
-                store_group<TIN, V>(orow + i0 * isz, y, out_vec);
+                    for (int q = 0; q < V; ++q) y[q] = h_of<TIN>(op, f[q], st, inv);
+                    store_group<TIN, V>(orow + (i_base + (g0 + g) * V) * isz, y, out_vec);
+                }
             });
             sweep_edges<TIN>(row, s, P, c, 1.0f, [&](long long i, float x) {
                 store_one<TIN>(orow + i * isz, h_of<TIN>(op, x, st, inv));
@@ -470,17 +615,17 @@ credit_status credit_ragged_create(const credit_ragged_row *host_rows, int64_t n
     cudaMemset(h->d_err, 0, 16);
     // autotune: cluster size x staging capacity x threads, timed on this batch
     const int Ps[3] = {4, 8, 16};
-    const int caps[2] = {6 * kRChunk, 13 * kRChunk};
-    const int thr[2] = {256, 512};
+    const int caps[4] = {3 * kRChunk, 4 * kRChunk, 6 * kRChunk, 13 * kRChunk};  // 4, 3, 2, 1 CTAs per SM
+    const int thr[2] = {128, 256};  // the kernel is built for up to 256 threads, 4 CTAs per SM (64 registers)
     float best = 1e30f;
-    int bP = 16, bcap = caps[1], bthr = 512;
+    int bP = 16, bcap = caps[3], bthr = 256;
     if (!tune) {  // fixed launch shape (CREDIT_RAGGED_P / _CHUNKS / _THREADS override the defaults)
         const char *eP = std::getenv("CREDIT_RAGGED_P"), *eC = std::getenv("CREDIT_RAGGED_CHUNKS");
         const char *eT = std::getenv("CREDIT_RAGGED_THREADS");
         if (eP) bP = std::atoi(eP);
         if (eC) bcap = std::atoi(eC) * kRChunk;
         if (eT) bthr = std::atoi(eT);
-        if (bP < 1 || bP > 16 || bcap < kRChunk || bcap > 13 * kRChunk || bthr < 64 || bthr > 512 || bthr % 32) {
+        if (bP < 1 || bP > 16 || bcap < kRChunk || bcap > 13 * kRChunk || bthr < 64 || bthr > 256 || bthr % 32) {
             credit_ragged_destroy(h);
             return CREDIT_ERR_INVALID_ARG;
         }

@@ -358,10 +358,9 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
                 tm_st16_issue(tb + static_cast<uint32_t>(k * kTmColsPerChunk), w);
             }
             tm_wait_st();  // the row's TMEM stores, complete before the handoff below
-            const long long n_head = (c == 0 && tid == 0) ? g.s.h0 : 0;
-            const long long n_tail = (c == P - 1 && tid == Tr - 1) ? g.s.t0 : 0;
-            for (int e = 0; e < 2; ++e)
-                for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) acc.add1(edge_x(g, e, k));
+            // edge elements, one per reducer thread (head element tid, tail element Tr - 1 - tid)
+            if (c == 0 && tid < g.s.h0) acc.add1(edge_x(g, 0, tid));
+            if (c == P - 1 && Tr - 1 - tid < g.s.t0) acc.add1(edge_x(g, 1, Tr - 1 - tid));
             if (tid == 0) trace_stamp(a, rr, 1);
             // ---------- warp partial, pushed to every CTA of the cluster (Eq. 5)
             if constexpr (OP == OP_LN) acc.finish();
@@ -537,15 +536,16 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
                     wa.next();
                 }
             }
-            const long long n_head = (c == 0 && wt == 0) ? g.s.h0 : 0;
-            const long long n_tail = (c == P - 1 && wt == Tw - 1) ? g.s.t0 : 0;
-            for (int e = 0; e < 2; ++e)
-                for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) {
-                    const long long i = e == 0 ? k : g.s.h0 + g.s.G * V + k;
-                    const float gm = ((OP == OP_LN || OP == OP_RMS) && a.gamma) ? a.gamma[i] : 1.0f;
-                    const float bt = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
-                    store_one<TOUT>(out_row + i * osz, h(edge_x(g, e, k), gm, bt));
-                }
+            // edge elements, one per writer thread (head element wt, tail element Tw - 1 - wt)
+            for (int e = 0; e < 2; ++e) {
+                const long long k = e == 0 ? ((c == 0 && wt < g.s.h0) ? wt : -1)
+                                           : ((c == P - 1 && Tw - 1 - wt < g.s.t0) ? Tw - 1 - wt : -1);
+                if (k < 0) continue;
+                const long long i = e == 0 ? k : g.s.h0 + g.s.G * V + k;
+                const float gm = ((OP == OP_LN || OP == OP_RMS) && a.gamma) ? a.gamma[i] : 1.0f;
+                const float bt = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
+                store_one<TOUT>(out_row + i * osz, h(edge_x(g, e, k), gm, bt));
+            }
             tm_fence_before();  // this warp's TMEM loads, before handing the buffer back
             __syncwarp();
             if (lane == 0) mbar_arrive(&tm_empty[b]);

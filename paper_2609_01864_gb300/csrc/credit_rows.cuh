@@ -846,8 +846,10 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
         int rr = 0;
         for (long long row = cl; row < a.rows; row += ncl, ++rr) {
             const RowGeo g = geo(row);
-            const long long n_head = (c == 0 && tid == 0) ? g.s.h0 : 0;
-            const long long n_tail = (c == P - 1 && tid == Tr - 1) ? g.s.t0 : 0;
+            // edge elements spread one per thread (a row has fewer than 16 of each): head element tid,
+            // tail element Tr - 1 - tid; -1 where this thread has none
+            const long long k_head = (c == 0 && tid < g.s.h0) ? tid : -1;
+            const long long k_tail = (c == P - 1 && Tr - 1 - tid < g.s.t0) ? Tr - 1 - tid : -1;
             const int par = rr & 1;
             const uint32_t xphase = static_cast<uint32_t>((rr >> 1) & 1);
             if (tid == 0) trace_stamp(a, rr, 0);
@@ -863,8 +865,8 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                     visit_chunk<TIN>(chunk_ptr(rb, k), chunk_groups(g, k), tid, Tr, g.in_sc,
                                      [&](int, const float(&f)[V]) { acc.add(f); });
                 }
-                for (int e = 0; e < 2; ++e)
-                    for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) acc.add1(edge_x(g, e, k));
+                if (k_head >= 0) acc.add1(edge_x(g, 0, k_head));
+                if (k_tail >= 0) acc.add1(edge_x(g, 1, k_tail));
                 if (tid == 0) trace_stamp(a, rr, 1);
                 const float2 part = block_reduce_stream<OP>(acc, red, n_c, 1, Tr);
                 part0 = part.x;
@@ -912,13 +914,14 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                                          }
                                      });
                 }
-                for (int e = 0; e < 2; ++e)
-                    for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) {
-                        const long long i = e == 0 ? k : g.s.h0 + g.s.G * V + k;
-                        const float gg = a.gamma ? a.gamma[i] : 1.0f;
-                        const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
-                        am = fmaxf(am, fabsf(norm_h<OP>(edge_x(g, e, k), st, gg, bb)));
-                    }
+                for (int e = 0; e < 2; ++e) {
+                    const long long k = e == 0 ? k_head : k_tail;
+                    if (k < 0) continue;
+                    const long long i = e == 0 ? k : g.s.h0 + g.s.G * V + k;
+                    const float gg = a.gamma ? a.gamma[i] : 1.0f;
+                    const float bb = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
+                    am = fmaxf(am, fabsf(norm_h<OP>(edge_x(g, e, k), st, gg, bb)));
+                }
                 am = cons_allreduce<true>(am, red, Tr);
                 if (P > 1) {
                     const float *sl = exchange_push<1>(am, 0.0f, slots, xbar, 1, par, xphase, P, c, Tr, a.err);
@@ -1031,15 +1034,16 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                     }
                 }
                 wb.advance(g.nch);
-                const long long n_head = (c == 0 && wt == 0) ? g.s.h0 : 0;
-                const long long n_tail = (c == P - 1 && wt == Tw - 1) ? g.s.t0 : 0;
-                for (int e = 0; e < 2; ++e)
-                    for (long long k = 0; k < (e == 0 ? n_head : n_tail); ++k) {
-                        const long long i = e == 0 ? k : g.s.h0 + g.s.G * V + k;
-                        const float gm = ((OP == OP_LN || OP == OP_RMS) && a.gamma) ? a.gamma[i] : 1.0f;
-                        const float bt = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
-                        store_one<TOUT>(out_row + i * osz, h(edge_x(g, e, k), gm, bt));
-                    }
+                // edge elements, one per writer thread (head element wt, tail element Tw - 1 - wt)
+                for (int e = 0; e < 2; ++e) {
+                    const long long k = e == 0 ? ((c == 0 && wt < g.s.h0) ? wt : -1)
+                                               : ((c == P - 1 && Tw - 1 - wt < g.s.t0) ? Tw - 1 - wt : -1);
+                    if (k < 0) continue;
+                    const long long i = e == 0 ? k : g.s.h0 + g.s.G * V + k;
+                    const float gm = ((OP == OP_LN || OP == OP_RMS) && a.gamma) ? a.gamma[i] : 1.0f;
+                    const float bt = (OP == OP_LN && a.beta) ? a.beta[i] : 0.0f;
+                    store_one<TOUT>(out_row + i * osz, h(edge_x(g, e, k), gm, bt));
+                }
             }
             if (wt == 0) trace_stamp(a, rr, 4);
             rb.advance(g.nch);
@@ -1110,17 +1114,18 @@ __device__ __forceinline__ uint4 e4m3_fold_sign(uint4 w, uint32_t neg) {
     return make_uint4(w.x ^ neg, w.y ^ neg, w.z ^ neg, w.w ^ neg);
 }
 
-// Edge elements of this CTA (head by thread 0 of CTA 0, tail by the last
-// thread of CTA P-1).
+// Edge elements of this CTA, one per thread (a row has fewer than 16 head and
+// 16 tail elements): head element t by thread t of CTA 0, tail element k by
+// thread T - 1 - k of CTA P-1, so their loads are in flight together.
 template <int TIN, class F>
 __device__ __forceinline__ void sweep_edges(const unsigned char *in_row, const RowSlice &s, int P, int c, float in_sc,
                                             F &&fn /* fn(long long i, float x) */) {
     constexpr int V = Fmt<TIN>::V, isz = Fmt<TIN>::size;
-    if (c == 0 && threadIdx.x == 0)
-        for (long long k = 0; k < s.h0; ++k) fn(k, decode_one<TIN>(in_row + k * isz, in_sc));
-    if (c == P - 1 && threadIdx.x == blockDim.x - 1) {
-        const long long t = s.h0 + s.G * V;
-        for (long long k = 0; k < s.t0; ++k) fn(t + k, decode_one<TIN>(in_row + (t + k) * isz, in_sc));
+    const long long t = threadIdx.x, kt = static_cast<long long>(blockDim.x) - 1 - t;
+    if (c == 0 && t < s.h0) fn(t, decode_one<TIN>(in_row + t * isz, in_sc));
+    if (c == P - 1 && kt < s.t0) {
+        const long long i = s.h0 + s.G * V + kt;
+        fn(i, decode_one<TIN>(in_row + i * isz, in_sc));
     }
 }
 

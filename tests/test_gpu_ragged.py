@@ -43,7 +43,7 @@ def check_rows(flat_in, flat_out_dev, rows, dtype, pick):
         assert U.error_metric(op, dtype, y, ref) <= 1.0, (i, w, op)
 
 
-@pytest.mark.parametrize("force", [("16", "13", "512"), ("4", "2", "256"), ("8", "6", "256")],
+@pytest.mark.parametrize("force", [("16", "13", "256"), ("4", "2", "128"), ("8", "6", "256")],
                          ids=["wide", "huge", "mixed"])
 def test_ragged_kinds_match_oracle(force, monkeypatch):
     monkeypatch.setenv("CREDIT_RAGGED_P", force[0])
@@ -67,7 +67,7 @@ def test_ragged_kinds_match_oracle(force, monkeypatch):
         assert info["items"] == info["narrow_items"] + info["wide_items"] + info["huge_items"]
 
 
-@pytest.mark.parametrize("force", [("16", "2", "256"), ("2", "1", "128"), ("8", "13", "512")],
+@pytest.mark.parametrize("force", [("16", "2", "256"), ("2", "1", "128"), ("8", "13", "256")],
                          ids=["p16_small_cap", "p2", "p8"])
 def test_ragged_every_width_class(force, monkeypatch):
     """Rows sized so that every sub-cluster width w = 1, 2, 4, ..., P occurs, in runs whose lengths are
