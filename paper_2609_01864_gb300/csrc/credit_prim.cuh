@@ -508,6 +508,19 @@ __device__ __forceinline__ uint4 ld_global_v4(const void *p) {
                  : "l"(p));
     return v;
 }
+// 16-byte load / store with an L2 cache policy (l2_evict_last_policy, ...).
+__device__ __forceinline__ uint4 ld_global_v4_hint(const void *p, uint64_t policy) {
+    uint4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(policy));
+    return v;
+}
+__device__ __forceinline__ void st_global_v4_hint(void *p, const uint4 &v, uint64_t policy) {
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w), "l"(policy)
+                 : "memory");
+}
 __device__ __forceinline__ uint4 ld_global_stream_v4(const void *p) {
     uint4 v;
     asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"

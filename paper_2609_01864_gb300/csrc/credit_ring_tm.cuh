@@ -348,13 +348,10 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[slot]);
 #pragma unroll
-                for (int m = 0; m < kTmHalf; ++m) {
-                    if (g0 + m * TL < gn) {
-                        float f[V];
-                        decode_group<TIN>(make_uint4(w[4 * m], w[4 * m + 1], w[4 * m + 2], w[4 * m + 3]), f, g.in_sc);
-                        acc.add(f);
-                    }
-                }
+                for (int m = 0; m < kTmHalf; ++m)
+                    if (g0 + m * TL < gn)
+                        stream_add_group<OP, TIN>(acc, make_uint4(w[4 * m], w[4 * m + 1], w[4 * m + 2], w[4 * m + 3]),
+                                                  g.in_sc);
                 tm_st16_issue(tb + static_cast<uint32_t>(k * kTmColsPerChunk), w);
             }
             tm_wait_st();  // the row's TMEM stores, complete before the handoff below
@@ -447,6 +444,21 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
                             if constexpr (OP == OP_LN) lds_f32<V>(ab + gi * V, bb[m]);
                         }
                     }
+                    // E4M3 softmax codes from the raw input codes (softmax_e4m3_codes) with 16-byte stores,
+                    // where the output groups start on the 16-byte grid (out_vec checks 8 bytes here)
+                    constexpr bool kRaw8 = OP == OP_SOFTMAX && TIN == DT_E4M3 && TOUT == DT_E4M3;
+                    const bool raw8 = kRaw8 && ((reinterpret_cast<uintptr_t>(out_row) + g.s.h0) & 15u) == 0;
+                    if (raw8) {
+                        const uint32_t neg = e4m3_sign_mask(g.in_sc);
+                        const float a1 = fabsf(g.in_sc);
+#pragma unroll
+                        for (int m = 0; m < kTmHalf; ++m) {
+                            const int gi = twin + (half * kTmHalf + m) * TL;
+                            *reinterpret_cast<uint4 *>(oc + static_cast<uint32_t>(gi * V)) = softmax_e4m3_codes(
+                                e4m3_fold_sign(make_uint4(w[4 * m], w[4 * m + 1], w[4 * m + 2], w[4 * m + 3]), neg),
+                                a1, st.a);
+                        }
+                    } else {
 #pragma unroll
                     for (int m = 0; m < kTmHalf; ++m) {
                         const int gi = twin + (half * kTmHalf + m) * TL;
@@ -468,6 +480,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
                             }
                             store_group<TOUT, SV>(oc + static_cast<uint32_t>((gi * V + hv) * osz), y, true);
                         }
+                    }
                     }
                 } else {
                 // gamma / beta for the groups of this chunk, batch by batch (L2 loads issued together)

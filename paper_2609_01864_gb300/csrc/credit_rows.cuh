@@ -345,6 +345,54 @@ template <> struct Stream<OP_SOFTMAX> {  // online (max, sum exp)
 };
 template <> struct Stream<OP_LSE> : Stream<OP_SOFTMAX> {};
 
+// Sign bits of 16 E4M3 codes flipped by `neg` (0x80808080 or 0): a row with a
+// negative input scale a becomes the row -q with scale |a|.
+__device__ __forceinline__ uint4 e4m3_fold_sign(uint4 w, uint32_t neg) {
+    return make_uint4(w.x ^ neg, w.y ^ neg, w.z ^ neg, w.w ^ neg);
+}
+__device__ __forceinline__ uint32_t e4m3_sign_mask(float in_sc) { return in_sc < 0.0f ? 0x80808080u : 0u; }
+
+// One 16-byte group of a row into the op's statistics: E4M3 softmax / log-sum-exp rows on the raw codes
+// (Stream::add_e4m3), everything else decoded first.
+template <int OP, int TIN>
+__device__ __forceinline__ void stream_add_group(Stream<OP> &acc, const uint4 &w, float in_sc) {
+    if constexpr (TIN == DT_E4M3 && (OP == OP_SOFTMAX || OP == OP_LSE)) {
+        acc.add_e4m3(e4m3_fold_sign(w, e4m3_sign_mask(in_sc)), fabsf(in_sc));
+    } else {
+        float f[Fmt<TIN>::V];
+        decode_group<TIN>(w, f, in_sc);
+        acc.add(f);
+    }
+}
+
+// Softmax output codes of one 16-byte group of E4M3 input codes q (sign folded, x = a q): code =
+// 448 exp(x - M) = 2^((a q - M) log2 e + log2 448), two codes per packed op -- the exponent from two
+// packed FMAs, rounded to FP16, raised by the packed FP16 SFU op and converted to two E4M3 codes at
+// once.  The FP16 rounding of the exponent (|t| < 16: error <= 2^-8) and the SFU's 2^-9.9 move a code's
+// value by under 0.5% relative, a small part of an E4M3 step (2^-3 relative).
+__device__ __forceinline__ uint4 softmax_e4m3_codes(const uint4 &w, float a, float M) {
+    const float c8 = 8.807354922057604f;  // log2 448
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+    uint32_t o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t code2[2];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            __half2_raw r =
+                __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>((u[k] >> (16 * hh)) & 0xFFFFu), __NV_E4M3);
+            const float2 d = __ffma2_rn(__half22float2(*reinterpret_cast<__half2 *>(&r)), make_float2(a, a),
+                                        make_float2(-M, -M));
+            const float2 t = __ffma2_rn(d, make_float2(kLog2e, kLog2e), make_float2(c8, c8));
+            const __half2 e = ex2_h2(__float22half2_rn(t));
+            code2[hh] = __nv_cvt_halfraw2_to_fp8x2(*reinterpret_cast<const __half2_raw *>(&e), __NV_SATFINITE,
+                                                   __NV_E4M3);
+        }
+        o[k] = (code2[0] & 0xFFFFu) | (code2[1] << 16);
+    }
+    return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
 // LayerNorm statistics in one sweep: each thread accumulates sums about a
 // shift K (its first element), s1 = sum (x - K), s2 = sum (x - K)^2, and
 // converts them once to (n, mean, M2) = (n, K + s1/n, s2 - s1^2/n) before the
@@ -652,6 +700,21 @@ __device__ __forceinline__ void visit_chunk(const unsigned char *cb, int gn, int
     }
 }
 
+// visit_chunk on the raw 16-byte groups: fn(group index, group).
+template <class F>
+__device__ __forceinline__ void visit_chunk_raw(const unsigned char *cb, int gn, int tid, int Tc, F &&fn) {
+    constexpr int U = 4;
+    int g = tid;
+    for (; g + (U - 1) * Tc < gn; g += U * Tc) {
+        uint4 w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) w[u] = *reinterpret_cast<const uint4 *>(cb + (g + u * Tc) * 16);
+#pragma unroll
+        for (int u = 0; u < U; ++u) fn(g + u * Tc, w[u]);
+    }
+    for (; g < gn; g += Tc) fn(g, *reinterpret_cast<const uint4 *>(cb + g * 16));
+}
+
 // Reuse pass of the norms over one staged chunk with gamma / beta read from
 // global memory (L2): for each batch of U groups every gamma / beta load is
 // issued before the batch's shared-memory reads and stores, so their latency
@@ -862,8 +925,8 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                 for (int k = 0; k < g.nch; ++k) {
                     const RingPos pk = rb.at(k);
                     mbar_wait_bounded(&full[pk.slot], pk.parity(), a.err, a.wait_ns ? a.wait_ns : kWaitLimitNs);
-                    visit_chunk<TIN>(chunk_ptr(rb, k), chunk_groups(g, k), tid, Tr, g.in_sc,
-                                     [&](int, const float(&f)[V]) { acc.add(f); });
+                    visit_chunk_raw(chunk_ptr(rb, k), chunk_groups(g, k), tid, Tr,
+                                    [&](int, const uint4 &w) { stream_add_group<OP, TIN>(acc, w, g.in_sc); });
                 }
                 if (k_head >= 0) acc.add1(edge_x(g, 0, k_head));
                 if (k_tail >= 0) acc.add1(edge_x(g, 1, k_tail));
@@ -1006,6 +1069,21 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
                             continue;
                         }
                     }
+                    if constexpr (OP == OP_SOFTMAX && TIN == DT_E4M3 && TOUT == DT_E4M3) {
+                        // raw codes in and out (softmax_e4m3_codes), 16-byte stores: only where the output
+                        // groups start on the 16-byte grid (out_vec checks 8 bytes for this format)
+                        if (((reinterpret_cast<uintptr_t>(out_row) + g.s.h0) & 15u) == 0) {
+                            const uint32_t neg = e4m3_sign_mask(g.in_sc);
+                            const float a1 = fabsf(g.in_sc);
+                            visit_chunk_raw(chunk_ptr(rb, k), chunk_groups(g, k), wt, Tw, [&](int gi, const uint4 &w) {
+                                *reinterpret_cast<uint4 *>(out_row + i_base + (kg + gi) * V) =
+                                    softmax_e4m3_codes(e4m3_fold_sign(w, neg), a1, st.a);
+                            });
+                            __syncwarp();
+                            if ((wt & 31) == 0) mbar_arrive(&empty[rb.at(k).slot]);
+                            continue;
+                        }
+                    }
                     visit_chunk<TIN>(chunk_ptr(rb, k), chunk_groups(g, k), wt, Tw, g.in_sc,
                                      [&](int gi, const float(&f)[V]) {
 #pragma unroll
@@ -1057,19 +1135,34 @@ __global__ void __launch_bounds__(288, 3) k_ring(const RowArgs a) {
 }
 
 // Visit this CTA's part of a row in global memory, 4 groups in flight per thread.
-template <int TIN, class F>
+// L2 treatment of a sweep's loads: 0 default, 1 keep (the row is read again
+// soon), 2 evict first (last read).
+template <int L2H>
+__device__ __forceinline__ uint64_t sweep_policy() {
+    if constexpr (L2H == 1) return l2_evict_last_policy();
+    else if constexpr (L2H == 2) return l2_evict_first_policy();
+    else return 0;
+}
+template <int L2H>
+__device__ __forceinline__ uint4 sweep_load(const unsigned char *p, uint64_t pol) {
+    if constexpr (L2H == 0) return ld_global_v4(p);
+    else return ld_global_v4_hint(p, pol);
+}
+
+template <int TIN, int L2H = 0, class F>
 __device__ __forceinline__ void sweep_global(const unsigned char *in_row, const RowSlice &s, int P, int c,
                                              float in_sc, F &&fn /* fn(long long elem_index, float(&)[V]) */) {
     constexpr int V = Fmt<TIN>::V, isz = Fmt<TIN>::size;
     const int tid = threadIdx.x, T = blockDim.x;
     const unsigned char *body = in_row + s.h0 * isz;
+    const uint64_t pol = sweep_policy<L2H>();
     constexpr int U = 4;  // 16-byte loads in flight per thread (8 spills at 64 registers and measures slower)
     for (long long g0 = s.g_lo + tid; g0 < s.g_hi; g0 += static_cast<long long>(U) * T) {
         uint4 w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const long long g = g0 + static_cast<long long>(u) * T;
-            if (g < s.g_hi) w[u] = ld_global_v4(body + g * 16);
+            if (g < s.g_hi) w[u] = sweep_load<L2H>(body + g * 16, pol);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -1086,19 +1179,20 @@ __device__ __forceinline__ void sweep_global(const unsigned char *in_row, const 
 }
 
 // sweep_global on the raw 16-byte groups: fn(first element index, group).
-template <int TIN, class F>
+template <int TIN, int L2H = 0, class F>
 __device__ __forceinline__ void sweep_global_raw(const unsigned char *in_row, const RowSlice &s,
                                                  F &&fn /* fn(long long elem_index, const uint4 &) */) {
     constexpr int V = Fmt<TIN>::V, isz = Fmt<TIN>::size;
     const int tid = threadIdx.x, T = blockDim.x;
     const unsigned char *body = in_row + s.h0 * isz;
+    const uint64_t pol = sweep_policy<L2H>();
     constexpr int U = 4;
     for (long long g0 = s.g_lo + tid; g0 < s.g_hi; g0 += static_cast<long long>(U) * T) {
         uint4 w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const long long g = g0 + static_cast<long long>(u) * T;
-            if (g < s.g_hi) w[u] = ld_global_v4(body + g * 16);
+            if (g < s.g_hi) w[u] = sweep_load<L2H>(body + g * 16, pol);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -1106,12 +1200,6 @@ __device__ __forceinline__ void sweep_global_raw(const unsigned char *in_row, co
             if (g < s.g_hi) fn(s.h0 + g * V, w[u]);
         }
     }
-}
-
-// Sign bits of 16 E4M3 codes flipped by `neg` (0x80808080 or 0): a row with a
-// negative input scale a becomes the row -q with scale |a|.
-__device__ __forceinline__ uint4 e4m3_fold_sign(uint4 w, uint32_t neg) {
-    return make_uint4(w.x ^ neg, w.y ^ neg, w.z ^ neg, w.w ^ neg);
 }
 
 // Edge elements of this CTA, one per thread (a row has fewer than 16 head and
@@ -1129,29 +1217,23 @@ __device__ __forceinline__ void sweep_edges(const unsigned char *in_row, const R
     }
 }
 
-template <int OP, int TIN>
+template <int OP, int TIN, int L2H = 0>
 __device__ __forceinline__ float2 stats_sweep(const RowArgs &a, const unsigned char *in_row, const RowSlice &s, int P,
                                               int c, float in_sc, float *red) {
     Stream<OP> st;
-    if constexpr (TIN == DT_E4M3 && (OP == OP_SOFTMAX || OP == OP_LSE)) {
-        const uint32_t neg = in_sc < 0.0f ? 0x80808080u : 0u;
-        const float a = fabsf(in_sc);
-        sweep_global_raw<TIN>(in_row, s, [&](long long, const uint4 &w) { st.add_e4m3(e4m3_fold_sign(w, neg), a); });
-    } else {
-        sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long, const float(&f)[Fmt<TIN>::V]) { st.add(f); });
-    }
+    sweep_global_raw<TIN, L2H>(in_row, s, [&](long long, const uint4 &w) { stream_add_group<OP, TIN>(st, w, in_sc); });
     sweep_edges<TIN>(in_row, s, P, c, in_sc, [&](long long, float x) { st.add1(x); });
     return block_reduce_stream<OP>(st, red, slice_count(s, Fmt<TIN>::V, P, c));
 }
 
-template <int OP, int TIN>
+template <int OP, int TIN, int L2H = 0>
 __device__ __forceinline__ float amax_sweep(const RowArgs &a, const unsigned char *in_row, const RowSlice &s, int P,
                                             int c, float in_sc, const Stats &st, float *red) {
     constexpr int V = Fmt<TIN>::V;
     const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + s.h0) & 15u) == 0);
     const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + s.h0) & 15u) == 0);
     float am = 0.0f;
-    sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
+    sweep_global<TIN, L2H>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
         float gg[V], bb[V];
         load_affine<V>(a.gamma, i0, g_vec, 1.0f, gg);
         load_affine<V>(a.beta, i0, b_vec, 0.0f, bb);
@@ -1165,7 +1247,7 @@ __device__ __forceinline__ float amax_sweep(const RowArgs &a, const unsigned cha
     return block_allreduce<true>(am, red);
 }
 
-template <int OP, int TIN, int TOUT>
+template <int OP, int TIN, int TOUT, int L2H = 0>
 __device__ __forceinline__ void apply_sweep(const RowArgs &a, long long row, const unsigned char *in_row,
                                             const RowSlice &s, int P, int c, float in_sc, const Stats &st,
                                             float qmul) {
@@ -1176,40 +1258,19 @@ __device__ __forceinline__ void apply_sweep(const RowArgs &a, long long row, con
     const bool g_vec = a.gamma == nullptr || ((reinterpret_cast<uintptr_t>(a.gamma + s.h0) & 15u) == 0);
     const bool b_vec = a.beta == nullptr || ((reinterpret_cast<uintptr_t>(a.beta + s.h0) & 15u) == 0);
     if constexpr (OP == OP_SOFTMAX && TIN == DT_E4M3 && TOUT == DT_E4M3) {
-        // E4M3 codes in and out: code = 448 exp(x - M) = 2^((a q - M) log2 e + log2 448) on the raw input
-        // codes q (sign folded as in the statistics): two packed FMAs per two codes, the exponent rounded
-        // to FP16 and raised by one packed SFU op, converted to two E4M3 codes at once.  The FP16
-        // rounding of the exponent (|t| < 16: error <= 2^-8) and the SFU's 2^-9.9 move a code's value by
-        // under 0.5% relative, a small part of an E4M3 step (2^-3 relative).
-        const float c8 = log2f(448.0f), M = st.a;
-        const uint32_t neg = in_sc < 0.0f ? 0x80808080u : 0u;
-        const float a1 = fabsf(in_sc);
-        sweep_global_raw<TIN>(in_row, s, [&](long long i0, const uint4 &w0) {
-            const uint4 w = e4m3_fold_sign(w0, neg);
-            const uint32_t u[4] = {w.x, w.y, w.z, w.w};
-            uint32_t o[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                uint32_t code2[2];
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    __half2_raw r = __nv_cvt_fp8x2_to_halfraw2(
-                        static_cast<__nv_fp8x2_storage_t>((u[k] >> (16 * hh)) & 0xFFFFu), __NV_E4M3);
-                    const float2 d = __ffma2_rn(__half22float2(*reinterpret_cast<__half2 *>(&r)),
-                                                make_float2(a1, a1), make_float2(-M, -M));
-                    const float2 t = __ffma2_rn(d, make_float2(kLog2e, kLog2e), make_float2(c8, c8));
-                    const __half2 e = ex2_h2(__float22half2_rn(t));
-                    code2[hh] = __nv_cvt_halfraw2_to_fp8x2(*reinterpret_cast<const __half2_raw *>(&e),
-                                                           __NV_SATFINITE, __NV_E4M3);
-                }
-                o[k] = (code2[0] & 0xFFFFu) | (code2[1] << 16);
-            }
+        // E4M3 codes in and out, from the raw input codes (softmax_e4m3_codes)
+        const float M = st.a, a1 = fabsf(in_sc), c8 = log2f(448.0f);
+        const uint32_t neg = e4m3_sign_mask(in_sc);
+        sweep_global_raw<TIN, L2H>(in_row, s, [&](long long i0, const uint4 &w0) {
+            const uint4 o = softmax_e4m3_codes(e4m3_fold_sign(w0, neg), a1, M);
             unsigned char *p = out_row + i0;
             if (out_vec) {
-                *reinterpret_cast<uint4 *>(p) = make_uint4(o[0], o[1], o[2], o[3]);
+                if constexpr (L2H == 0) *reinterpret_cast<uint4 *>(p) = o;
+                else st_global_v4_hint(p, o, l2_evict_first_policy());
             } else {
+                const uint32_t ow[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
-                for (int k = 0; k < 16; ++k) p[k] = static_cast<unsigned char>(o[k >> 2] >> (8 * (k & 3)));
+                for (int k = 0; k < 16; ++k) p[k] = static_cast<unsigned char>(ow[k >> 2] >> (8 * (k & 3)));
             }
         });
         sweep_edges<TIN>(in_row, s, P, c, in_sc,
@@ -1218,7 +1279,7 @@ __device__ __forceinline__ void apply_sweep(const RowArgs &a, long long row, con
         // y (or its FP8 code) = exp(x - M) * mul = 2^((x - M) log2 e + log2 mul)
         const float mul = (TOUT == DT_E4M3) ? 448.0f : 1.0f / st.b;
         const float cL = log2f(mul);
-        sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
+        sweep_global<TIN, L2H>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
             float y[V];
             exp_sub_group<V>(f, st.a, cL, y);
             store_group<TOUT, V>(out_row + i0 * osz, y, out_vec);
@@ -1226,7 +1287,7 @@ __device__ __forceinline__ void apply_sweep(const RowArgs &a, long long row, con
         sweep_edges<TIN>(in_row, s, P, c, in_sc,
                          [&](long long i, float x) { store_one<TOUT>(out_row + i * osz, exp_sub(x, st.a, cL)); });
     } else if constexpr (OP == OP_Q8) {
-        sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
+        sweep_global<TIN, L2H>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
             float y[V];
             q8_codes<V>(f, st.a, st.b, y);
             store_group<TOUT, V>(out_row + i0 * osz, y, out_vec);
@@ -1234,7 +1295,7 @@ __device__ __forceinline__ void apply_sweep(const RowArgs &a, long long row, con
         sweep_edges<TIN>(in_row, s, P, c, in_sc,
                          [&](long long i, float x) { store_one<TOUT>(out_row + i * osz, q8_code(x, st.a, st.b)); });
     } else {
-        sweep_global<TIN>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
+        sweep_global<TIN, L2H>(in_row, s, P, c, in_sc, [&](long long i0, const float(&f)[V]) {
             float gg[V], bb[V], y[V];
             load_affine<V>(a.gamma, i0, g_vec, 1.0f, gg);
             if constexpr (OP == OP_LN) load_affine<V>(a.beta, i0, b_vec, 0.0f, bb);
@@ -1260,7 +1321,9 @@ __global__ void __launch_bounds__(1024) k_tp_fused(const RowArgs a) {
     const unsigned char *in_row = a.in + row * a.ld_in * isz;
     const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), a.cols, isz, 1, 0);
     const float in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
-    const float2 p = stats_sweep<OP, TIN>(a, in_row, s, 1, 0, in_sc, red);
+    // the row is read again by this CTA right after (not for log-sum-exp): its lines are kept in L2 on the
+    // first read and go first on the second
+    const float2 p = stats_sweep<OP, TIN, OP == OP_LSE ? 0 : 1>(a, in_row, s, 1, 0, in_sc, red);
     const float pp[2] = {p.x, p.y};
     const Stats st = combine_partials<OP>(pp, 2, 1, s, V, a.cols, a.eps);
     if constexpr (OP == OP_LSE) {
@@ -1268,7 +1331,7 @@ __global__ void __launch_bounds__(1024) k_tp_fused(const RowArgs a) {
     } else {
         float qmul = 1.0f;
         if constexpr (TOUT == DT_E4M3 && (OP == OP_LN || OP == OP_RMS)) {
-            const float am = amax_sweep<OP, TIN>(a, in_row, s, 1, 0, in_sc, st, red);
+            const float am = amax_sweep<OP, TIN, 1>(a, in_row, s, 1, 0, in_sc, st, red);
             qmul = am > 0.0f ? 448.0f / am : 1.0f;
             if (threadIdx.x == 0) a.out_scale[row] = am > 0.0f ? am / 448.0f : 1.0f;
         }
@@ -1278,7 +1341,7 @@ __global__ void __launch_bounds__(1024) k_tp_fused(const RowArgs a) {
         if constexpr (OP == OP_Q8) {
             if (threadIdx.x == 0) a.out_scale[row] = st.a;
         }
-        apply_sweep<OP, TIN, TOUT>(a, row, in_row, s, 1, 0, in_sc, st, qmul);
+        apply_sweep<OP, TIN, TOUT, 2>(a, row, in_row, s, 1, 0, in_sc, st, qmul);
     }
 }
 
