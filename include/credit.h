@@ -410,9 +410,11 @@ typedef struct {
     int32_t cluster_size, threads, staging_bytes, clusters;
     int64_t items, narrow_items, wide_items, huge_items;
     float tuned_us;  /* autotuner's best time for the batch (0 if not tuned) */
+    int32_t vector_groups;  /* vector width: 16-byte groups a thread reads per step (1 or 2) */
 } credit_ragged_info_t;
 /* Build the work list, autotune (tune != 0: cluster size 4/8/16 x staging
- * capacity x threads, each timed on this batch -- this launches the kernel
+ * capacity (48 KiB to 208 KiB) x threads (128, 256) x vector width (1 or 2
+ * groups), each timed on this batch -- this launches the kernel
  * and writes out_base), and capture the chosen launch in a CUDA graph.
  * Allocates the device work list; in_base / out_base must stay valid while
  * the handle is used.  BF16 and FP32 only (FP8 rows would need scales). */

@@ -149,7 +149,8 @@ class RaggedRowT(ctypes.Structure):
 class RaggedInfoT(ctypes.Structure):
     _fields_ = [("cluster_size", ctypes.c_int32), ("threads", ctypes.c_int32), ("staging_bytes", ctypes.c_int32),
                 ("clusters", ctypes.c_int32), ("items", ctypes.c_int64), ("narrow_items", ctypes.c_int64),
-                ("wide_items", ctypes.c_int64), ("huge_items", ctypes.c_int64), ("tuned_us", ctypes.c_float)]
+                ("wide_items", ctypes.c_int64), ("huge_items", ctypes.c_int64), ("tuned_us", ctypes.c_float),
+                ("vector_groups", ctypes.c_int32)]
 
 
 MODEL_IN_FIELDS = ["M", "N", "P", "T_B_us", "T_ctrl_us", "b_B", "b_reread", "b_keep", "b_in", "s_bytes", "q_sum",

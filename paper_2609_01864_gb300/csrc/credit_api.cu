@@ -92,7 +92,6 @@ namespace credit {
 // AUTO retention policy: tensor memory where it applies (slices above
 // kTmAutoMinSlice bytes).
 bool g_auto_retain_tmem = true;
-constexpr long long kTmAutoMinSlice = 32768;
 
 int dtype_size(int dt) { return dt == DT_F32 ? 4 : (dt == DT_BF16 ? 2 : 1); }
 

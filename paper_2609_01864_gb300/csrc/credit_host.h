@@ -39,6 +39,10 @@ struct RingCfg {
 // nab: gamma/beta arrays streamed through the affine ring (0, 1 or 2).
 bool ring_config(const DeviceInfo &di, long long N, int isz, int P, int req_ring, int req_chunk, int req_threads,
                  int req_reducers, int nab, RingCfg *out);
+// Slices above this many bytes are retained in tensor memory when a plan
+// leaves the tier to the library (AUTO): below it the shared-memory ring fits
+// several CTAs per SM.
+constexpr long long kTmAutoMinSlice = 32768;
 // Tensor-memory retention geometry (k_ring_tm); false where it does not apply.
 bool ring_config_tm(const DeviceInfo &di, long long N, int isz, int P, int req_ring, int req_chunk, int nab,
                     RingCfg *out);

@@ -263,11 +263,25 @@ bool analytic_plan(const DeviceInfo &di, int device, int op, long long rows, lon
     double best = 0.0;
     int bestP = 0;
     RingCfg best_rc{};
+    // the retention tier of each P follows the library's AUTO rule: tensor memory for slices above
+    // kTmAutoMinSlice where the op has a reuse pass that tier supports (its own Eq. 3 capacity and
+    // occupancy), else the shared-memory ring the paper's model describes
+    const int isz = dtype_size(tin);
+    const bool tm_op = op != 1 && !(tout == 2 && (op == 2 || op == 3));
+    bool best_tm = false;
     for (int k = 0; k < 4 && T_B > 0; ++k) {
         const int P = kPs[k];
         RingCfg rc;
-        if (!ring_config(di, cols, dtype_size(tin), P, 0, 0, 0, 0, 0, &rc)) continue;  // Eq. 3
-        const int A = ring_max_clusters(device, op, tin, tout, P, rc.threads, rc.smem);
+        int A = 0;
+        bool tm = false;
+        const long long slice = (cols * isz / 16 + P - 1) / P * 16;
+        if (tm_op && slice > kTmAutoMinSlice && ring_config_tm(di, cols, isz, P, 0, 0, 0, &rc) &&
+            (A = ring_max_clusters(device, op, tin, tout, P, rc.threads, rc.smem, true)) > 0) {
+            tm = true;
+        } else {
+            if (!ring_config(di, cols, isz, P, 0, 0, 0, 0, 0, &rc)) continue;  // Eq. 3
+            A = ring_max_clusters(device, op, tin, tout, P, rc.threads, rc.smem);
+        }
         if (A <= 0) continue;
         credit_model_inputs in{};
         in.M = static_cast<double>(rows);
@@ -296,6 +310,7 @@ bool analytic_plan(const DeviceInfo &di, int device, int op, long long rows, lon
             best = t.dT_us;
             bestP = P;
             best_rc = rc;
+            best_tm = tm;
         }
     }
     if (bestP > 0) {
@@ -303,7 +318,7 @@ bool analytic_plan(const DeviceInfo &di, int device, int op, long long rows, lon
         p->cluster_size = bestP;
         p->ctas_per_row = bestP;
         p->smem_bytes = best_rc.smem;
-        p->retain = CREDIT_RETAIN_SMEM;  // Eq. 7-9 model the shared-memory staging
+        p->retain = best_tm ? CREDIT_RETAIN_TMEM : CREDIT_RETAIN_SMEM;
         p->predicted_us = static_cast<float>(T_B - best);
     }
     if (best_dT) *best_dT = best;

@@ -76,7 +76,24 @@ struct RaggedArgs {
 constexpr int kRCtrl = 1280;  // [0,128) mbarriers, [128,384) slots [16][4], [640,1152) reduction scratch (128 floats)
 constexpr int kRChunk = 16384;
 
-template <int TIN>
+// Groups gb .. ge - 1 of a staged buffer, VW per thread per step (the
+// vector width the autotuner picks: VW independent 16-byte reads in flight
+// before any is used): fn(group, its 16 bytes).
+template <int VW, class F>
+__device__ __forceinline__ void for_groups(const unsigned char *base, long long gb, long long ge, int tid, int T,
+                                           F &&fn) {
+    for (long long g = gb + tid; g < ge; g += static_cast<long long>(VW) * T) {
+        uint4 w[VW];
+#pragma unroll
+        for (int u = 0; u < VW; ++u)
+            if (g + static_cast<long long>(u) * T < ge) w[u] = *reinterpret_cast<const uint4 *>(base + (g + u * T) * 16);
+#pragma unroll
+        for (int u = 0; u < VW; ++u)
+            if (g + static_cast<long long>(u) * T < ge) fn(g + static_cast<long long>(u) * T, w[u]);
+    }
+}
+
+template <int TIN, int VW>
 __device__ __forceinline__ float2 stats_from_smem(int op, const unsigned char *buf, long long ng, const RowSlice &s,
                                                   bool own_head, bool own_tail, const unsigned char *row,
                                                   uint64_t *mbar, uint32_t &phase_bits, int nch, float *red,
@@ -89,12 +106,12 @@ __device__ __forceinline__ float2 stats_from_smem(int op, const unsigned char *b
         mbar_wait_bounded(&mbar[k], (phase_bits >> k) & 1u, err);
         const long long gb = static_cast<long long>(k) * (kRChunk / 16);
         const long long ge = min(ng, gb + kRChunk / 16);
-        for (long long g = gb + tid; g < ge; g += T) {
+        for_groups<VW>(buf, gb, ge, tid, T, [&](long long, const uint4 &w) {
             float f[V];
-            decode_group<TIN>(*reinterpret_cast<const uint4 *>(buf + g * 16), f, 1.0f);
+            decode_group<TIN>(w, f, 1.0f);
             if (op == OP_SOFTMAX) sm.add(f);
             else rs.add(f);
-        }
+        });
     }
     phase_bits ^= (nch >= 32 ? 0xFFFFFFFFu : ((1u << nch) - 1u));
     // edge elements, one per thread: head element tid, tail element T - 1 - tid
@@ -268,8 +285,11 @@ __device__ __forceinline__ void issue_chunk(unsigned char *buf, const SliceSrc &
     bulk_g2s_hint(buf + off, sl.src + off, bytes, &mbar[k], l2_evict_first_policy());
 }
 
-template <int TIN>
-__global__ void __launch_bounds__(256, 4) k_ragged(const RaggedArgs a) {
+// VW = 1 fits 64 registers (4 CTAs of 256 threads per SM); VW = 2 keeps two
+// groups' registers live and is built for 2 CTAs per SM: the autotuner
+// weighs the wider steps against the occupancy they cost.
+template <int TIN, int VW>
+__global__ void __launch_bounds__(256, VW == 2 ? 2 : 4) k_ragged(const RaggedArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);       // [0..14) chunks, [14] exchange
     uint64_t *xbar = mbar + 14;
@@ -328,7 +348,7 @@ __global__ void __launch_bounds__(256, 4) k_ragged(const RaggedArgs a) {
             pre_issued = 0;
             float2 part = make_float2(op == OP_SOFTMAX ? -INFINITY : 0.0f, 0.0f);
             if (active)
-                part = stats_from_smem<TIN>(op, buf, ng, s, own_head, own_tail, row, mbar, phase_bits, nch, red,
+                part = stats_from_smem<TIN, VW>(op, buf, ng, s, own_head, own_tail, row, mbar, phase_bits, nch, red,
                                             a.err);
             Stats st{};
             if (active) st = exchange_sub<TIN>(op, part, slots, xbar, xph, sub * w, w, cs, s, N, a.eps, a.err);
@@ -350,13 +370,13 @@ __global__ void __launch_bounds__(256, 4) k_ragged(const RaggedArgs a) {
             for (int k = 0; k < nch; ++k) {
                 const long long gb = static_cast<long long>(k) * (kRChunk / 16);
                 const long long ge = min(ng, gb + kRChunk / 16);
-                for (long long g = gb + tid; g < ge; g += T) {
+                for_groups<VW>(buf, gb, ge, tid, T, [&](long long g, const uint4 &w) {
                     float f[V], y[V];
-                    decode_group<TIN>(*reinterpret_cast<const uint4 *>(buf + g * 16), f, 1.0f);
+                    decode_group<TIN>(w, f, 1.0f);
 #pragma unroll
                     for (int q = 0; q < V; ++q) y[q] = h_of<TIN>(op, f[q], st, inv);
                     store_group<TIN, V>(orow + (i_base + g * V) * isz, y, out_vec);
-                }
+                });
                 __syncthreads();  // chunk k of this item is written: its slot takes chunk k of the next
                 if (tid == 0 && pre && k < nx.nch) issue_chunk(buf, nx, k, mbar);
             }
@@ -378,12 +398,12 @@ __global__ void __launch_bounds__(256, 4) k_ragged(const RaggedArgs a) {
             // first pass: keep the lines in L2 for the second
             ring_stream(src, ng, buf, R, mbar, phase_bits, a.err, l2_evict_last_policy(),
                         [&](long long, int gn, const unsigned char *cb) {
-                for (int g = tid; g < gn; g += T) {
+                for_groups<VW>(cb, 0, gn, tid, T, [&](long long, const uint4 &w) {
                     float f[V];
-                    decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, 1.0f);
+                    decode_group<TIN>(w, f, 1.0f);
                     if (op == OP_SOFTMAX) sm.add(f);
                     else rs.add(f);
-                }
+                });
             });
             sweep_edges<TIN>(row, s, P, c, 1.0f, [&](long long, float x) {
                 if (op == OP_SOFTMAX) sm.add1(x);
@@ -399,13 +419,13 @@ __global__ void __launch_bounds__(256, 4) k_ragged(const RaggedArgs a) {
             const float inv = op == OP_SOFTMAX ? 1.0f / st.b : 0.0f;
             ring_stream_again(src, ng, buf, R, mbar, phase_bits, a.err, l2_evict_first_policy(),
                               [&](long long g0, int gn, const unsigned char *cb) {
-                for (int g = tid; g < gn; g += T) {
+                for_groups<VW>(cb, 0, gn, tid, T, [&](long long g, const uint4 &w) {
                     float f[V], y[V];
-                    decode_group<TIN>(*reinterpret_cast<const uint4 *>(cb + g * 16), f, 1.0f);
+                    decode_group<TIN>(w, f, 1.0f);
 #pragma unroll
                     for (int q = 0; q < V; ++q) y[q] = h_of<TIN>(op, f[q], st, inv);
                     store_group<TIN, V>(orow + (i_base + (g0 + g) * V) * isz, y, out_vec);
-                }
+                });
             });
             sweep_edges<TIN>(row, s, P, c, 1.0f, [&](long long i, float x) {
                 store_one<TIN>(orow + i * isz, h_of<TIN>(op, x, st, inv));
@@ -419,12 +439,13 @@ __global__ void __launch_bounds__(256, 4) k_ragged(const RaggedArgs a) {
     }
 }
 
-const void *ragged_kernel(int dt) {
-    switch (dt) {
-    case DT_F32: return reinterpret_cast<const void *>(&k_ragged<DT_F32>);
-    case DT_BF16: return reinterpret_cast<const void *>(&k_ragged<DT_BF16>);
-    default: return reinterpret_cast<const void *>(&k_ragged<DT_E4M3>);
-    }
+// FP32 and BF16 rows (the ragged entry refuses FP8), vector width 1 or 2 groups.
+const void *ragged_kernel(int dt, int vw) {
+    if (dt == DT_F32)
+        return vw == 2 ? reinterpret_cast<const void *>(&k_ragged<DT_F32, 2>)
+                       : reinterpret_cast<const void *>(&k_ragged<DT_F32, 1>);
+    return vw == 2 ? reinterpret_cast<const void *>(&k_ragged<DT_BF16, 2>)
+                   : reinterpret_cast<const void *>(&k_ragged<DT_BF16, 1>);
 }
 
 }  // namespace
@@ -437,7 +458,7 @@ struct credit_ragged {
     const unsigned char *in = nullptr;
     unsigned char *out = nullptr;
     // chosen launch
-    int P = 0, threads = 0, cap = 0, clusters = 0;
+    int P = 0, threads = 0, cap = 0, clusters = 0, vw = 1;
     long long n_items = 0, n_narrow = 0, n_wide = 0, n_huge = 0;
     RRow *d_rows = nullptr;
     RItem *d_items = nullptr;
@@ -485,7 +506,7 @@ void build_items(const std::vector<RRow> &rows, int isz, int P, int cap, std::ve
     }
 }
 
-credit_status upload_and_launch_config(credit_ragged *h, int P, int threads, int cap, bool capture,
+credit_status upload_and_launch_config(credit_ragged *h, int P, int threads, int cap, int vw, bool capture,
                                        float *us_out) {
     const int isz = dtype_size(h->dtype);
     const DeviceInfo *di = device_info(h->device);
@@ -495,7 +516,7 @@ credit_status upload_and_launch_config(credit_ragged *h, int P, int threads, int
     build_items(h->rows, isz, P, cap, items, sorted, nn, nw, nh);
     const long long smem = kRCtrl + cap;
     if (smem > di->smem_optin) return CREDIT_ERR_UNSUPPORTED;
-    const void *fn = ragged_kernel(h->dtype);
+    const void *fn = ragged_kernel(h->dtype, vw);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(di->smem_optin));
     cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     int maxc = 0;
@@ -542,6 +563,7 @@ credit_status upload_and_launch_config(credit_ragged *h, int P, int threads, int
         h->graph = g;
         if (cudaGraphInstantiate(&h->exec, g, 0) != cudaSuccess) return CREDIT_ERR_CUDA;
         h->P = P;
+        h->vw = vw;
         h->threads = threads;
         h->cap = cap;
         h->clusters = static_cast<int>(ncl);
@@ -613,41 +635,46 @@ credit_status credit_ragged_create(const credit_ragged_row *host_rows, int64_t n
         return CREDIT_ERR_CUDA;
     }
     cudaMemset(h->d_err, 0, 16);
-    // autotune: cluster size x staging capacity x threads, timed on this batch
+    // autotune: cluster size x staging capacity x threads x vector width, timed on this batch
     const int Ps[3] = {4, 8, 16};
+    const int vws[2] = {1, 2};  // 16-byte groups each thread reads before using them
     const int caps[4] = {3 * kRChunk, 4 * kRChunk, 6 * kRChunk, 13 * kRChunk};  // 4, 3, 2, 1 CTAs per SM
     const int thr[2] = {128, 256};  // the kernel is built for up to 256 threads, 4 CTAs per SM (64 registers)
     float best = 1e30f;
-    int bP = 16, bcap = caps[3], bthr = 256;
-    if (!tune) {  // fixed launch shape (CREDIT_RAGGED_P / _CHUNKS / _THREADS override the defaults)
+    int bP = 16, bcap = caps[3], bthr = 256, bvw = 1;
+    if (!tune) {  // fixed launch shape (CREDIT_RAGGED_P / _CHUNKS / _THREADS / _VW override the defaults)
         const char *eP = std::getenv("CREDIT_RAGGED_P"), *eC = std::getenv("CREDIT_RAGGED_CHUNKS");
-        const char *eT = std::getenv("CREDIT_RAGGED_THREADS");
+        const char *eT = std::getenv("CREDIT_RAGGED_THREADS"), *eV = std::getenv("CREDIT_RAGGED_VW");
         if (eP) bP = std::atoi(eP);
         if (eC) bcap = std::atoi(eC) * kRChunk;
         if (eT) bthr = std::atoi(eT);
-        if (bP < 1 || bP > 16 || bcap < kRChunk || bcap > 13 * kRChunk || bthr < 64 || bthr > 256 || bthr % 32) {
+        if (eV) bvw = std::atoi(eV);
+        if (bP < 1 || bP > 16 || bcap < kRChunk || bcap > 13 * kRChunk || bthr < 64 || bthr > 256 || bthr % 32 ||
+            (bvw != 1 && bvw != 2)) {
             credit_ragged_destroy(h);
             return CREDIT_ERR_INVALID_ARG;
         }
     } else {
         for (int P : Ps)
             for (int cap : caps)
-                for (int t : thr) {
-                    float us = 0;
-                    if (upload_and_launch_config(h, P, t, cap, false, &us) == CREDIT_OK && us < best) {
-                        best = us;
-                        bP = P;
-                        bcap = cap;
-                        bthr = t;
+                for (int t : thr)
+                    for (int vw : vws) {
+                        float us = 0;
+                        if (upload_and_launch_config(h, P, t, cap, vw, false, &us) == CREDIT_OK && us < best) {
+                            best = us;
+                            bP = P;
+                            bcap = cap;
+                            bthr = t;
+                            bvw = vw;
+                        }
                     }
-                }
         if (best >= 1e30f) {
             credit_ragged_destroy(h);
             return CREDIT_ERR_UNSUPPORTED;
         }
     }
     h->tuned_us = tune ? best : 0.0f;
-    st = upload_and_launch_config(h, bP, bthr, bcap, true, nullptr);
+    st = upload_and_launch_config(h, bP, bthr, bcap, bvw, true, nullptr);
     if (st != CREDIT_OK) {
         credit_ragged_destroy(h);
         return st;
@@ -675,6 +702,7 @@ credit_status credit_ragged_info(const credit_ragged *h, credit_ragged_info_t *o
     out->wide_items = h->n_wide;
     out->huge_items = h->n_huge;
     out->tuned_us = h->tuned_us;
+    out->vector_groups = h->vw;
     return CREDIT_OK;
 }
 

@@ -213,6 +213,28 @@ def evaluate(rows, test_shapes):
     return {k: v / max(1, n) for k, v in res.items()}, n
 
 
+def eval_only(args) -> int:
+    """Pick accuracies of the loaded learned model and of the analytic / ablation planners on the held-out
+    split of the committed sweep, written back into the summary (the planners can change after a sweep)."""
+    from . import build as B
+    B.build()
+    C.init()
+    C.load_model(args.calib)
+    path = os.path.join(args.out, "sweep_gb300_summary.json")
+    with open(path) as f:
+        summary = json.load(f)
+    rows = read_csv(os.path.join(args.out, "sweep_gb300.csv"))
+    _, test = synth.split_by_shape(summary["shapes"])
+    acc, n = evaluate(rows, test)
+    if n != summary["test_shapes"]:
+        raise SystemExit(f"held-out shapes {n} != {summary['test_shapes']} in the summary")
+    summary["pick_accuracy"] = acc
+    with open(path, "w") as f:
+        json.dump(summary, f, indent=1)
+    print(json.dumps({"pick_accuracy": acc, "test_shapes": n}))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--shapes", type=int, default=2000)
@@ -225,10 +247,19 @@ def main(argv=None):
                                                     "gb300.calib"))
     ap.add_argument("--from-csv", default="", help="retrain and evaluate from an earlier sweep's timings")
     ap.add_argument("--extra-shapes", type=int, default=300,
-                    help="training-only shapes from the wide-row corner (rows 2^U(10,14), cols 2^U(14,20))")
+                    help="training-only shapes from the wide-row corner (rows 2^U(10,14), cols 2^U(14,20)); every "
+                         "second one with cols a multiple of 16")
+    ap.add_argument("--reuse-csv", default="",
+                    help="take the timings of shapes identical to an earlier sweep's (same id, op, dtype, rows, "
+                         "cols) from its CSV and time only the others (the kernels must be the same)")
     ap.add_argument("--target", default="relative", choices=["relative", "absolute"],
                     help="log2 latency relative to the shape's mean over its candidates, or absolute")
+    ap.add_argument("--eval-only", action="store_true",
+                    help="no sweep, no training: evaluate the committed model and the planner rules on the held-out "
+                         "shapes of the committed timings and update the summary's pick accuracies")
     args = ap.parse_args(argv)
+    if args.eval_only:
+        return eval_only(args)
     from . import build as B
     B.build()
     C.init()
@@ -241,11 +272,25 @@ def main(argv=None):
     # training-only shapes from the wide-row corner (thousands of rows of 16K-1M columns, up to the byte cap),
     # which the log-uniform draw above reaches rarely: shape ids from len(shapes) on, never in the held-out split
     extra = synth.sweep_shapes(args.extra_shapes, seed=synth.SEED_SWEEP + 11, cap_bytes=cap,
-                               rows_log2=(10.0, 14.0), cols_log2=(14.0, 20.0)) if args.extra_shapes > 0 else []
+                               rows_log2=(10.0, 14.0), cols_log2=(14.0, 20.0),
+                               align_every=2) if args.extra_shapes > 0 else []
     t0 = time.time()
     if args.from_csv:
         rows = read_csv(args.from_csv)
         rows = [r for r in rows if r["shape"] < len(shapes) + len(extra)]
+    elif args.reuse_csv:
+        allshapes = shapes + extra
+        old = {}
+        for r in read_csv(args.reuse_csv):
+            old.setdefault(r["shape"], []).append(r)
+        keep = {i for i, (op, dt, nr, nc) in enumerate(allshapes)
+                if i in old and all((r["op"], r["dtype"], r["rows"], r["cols"]) == (op, dt, nr, nc) for r in old[i])}
+        todo = [i for i in range(len(allshapes)) if i not in keep]
+        print(f"reusing {len(keep)} shapes, timing {len(todo)}", file=sys.stderr)
+        new_rows = run_sweep([allshapes[i] for i in todo], args.reps, cap, log=sys.stderr)
+        for r in new_rows:
+            r["shape"] = todo[r["shape"]]
+        rows = [r for i in sorted(keep) for r in old[i]] + new_rows
     else:
         rows = run_sweep(shapes + extra, args.reps, cap, log=sys.stderr)
     t_sweep = time.time() - t0

@@ -67,14 +67,17 @@ def test_ragged_kinds_match_oracle(force, monkeypatch):
         assert info["items"] == info["narrow_items"] + info["wide_items"] + info["huge_items"]
 
 
-@pytest.mark.parametrize("force", [("16", "2", "256"), ("2", "1", "128"), ("8", "13", "256")],
-                         ids=["p16_small_cap", "p2", "p8"])
+@pytest.mark.parametrize("force", [("16", "2", "256", "1"), ("2", "1", "128", "2"), ("8", "13", "256", "1"),
+                                   ("8", "3", "256", "2")],
+                         ids=["p16_small_cap", "p2_vw2", "p8", "p8_vw2"])
 def test_ragged_every_width_class(force, monkeypatch):
     """Rows sized so that every sub-cluster width w = 1, 2, 4, ..., P occurs, in runs whose lengths are
-    not multiples of P / w (items with idle sub-groups), next to rows that stream (huge)."""
+    not multiples of P / w (items with idle sub-groups), next to rows that stream (huge); both vector
+    widths."""
     monkeypatch.setenv("CREDIT_RAGGED_P", force[0])
     monkeypatch.setenv("CREDIT_RAGGED_CHUNKS", force[1])
     monkeypatch.setenv("CREDIT_RAGGED_THREADS", force[2])
+    monkeypatch.setenv("CREDIT_RAGGED_VW", force[3])
     P, cap = int(force[0]), int(force[1]) * 16384
     rng = np.random.default_rng(int(force[0]) * 7 + int(force[1]))
     for dt in (C.BF16, C.F32):
@@ -103,7 +106,7 @@ def test_ragged_every_width_class(force, monkeypatch):
         check_rows(flat, d_out, rows, dt, range(len(rows)))
         assert not torch.isnan(d_out.float()).any()
         R.close()
-        assert info["cluster_size"] == P
+        assert info["cluster_size"] == P and info["vector_groups"] == int(force[3])
         assert info["narrow_items"] > 0 and info["huge_items"] > 0
         assert P == 1 or info["wide_items"] > 0
 
