@@ -247,8 +247,8 @@ def main(argv=None):
                                                     "gb300.calib"))
     ap.add_argument("--from-csv", default="", help="retrain and evaluate from an earlier sweep's timings")
     ap.add_argument("--extra-shapes", type=int, default=300,
-                    help="training-only shapes from the wide-row corner (rows 2^U(10,14), cols 2^U(14,20)); every "
-                         "second one with cols a multiple of 16")
+                    help="training-only shapes from the wide-row corner (rows 2^U(10,14), cols 2^U(14,20)); cols "
+                         "as drawn, rounded to a power of two, rounded down to a multiple of 16, in turn")
     ap.add_argument("--reuse-csv", default="",
                     help="take the timings of shapes identical to an earlier sweep's (same id, op, dtype, rows, "
                          "cols) from its CSV and time only the others (the kernels must be the same)")
@@ -273,7 +273,7 @@ def main(argv=None):
     # which the log-uniform draw above reaches rarely: shape ids from len(shapes) on, never in the held-out split
     extra = synth.sweep_shapes(args.extra_shapes, seed=synth.SEED_SWEEP + 11, cap_bytes=cap,
                                rows_log2=(10.0, 14.0), cols_log2=(14.0, 20.0),
-                               align_every=2) if args.extra_shapes > 0 else []
+                               col_modes=("any", "pow2", "align16")) if args.extra_shapes > 0 else []
     t0 = time.time()
     if args.from_csv:
         rows = read_csv(args.from_csv)
@@ -335,7 +335,8 @@ def main(argv=None):
     write_csv(csv_out, rows)
     summary = {"shapes": len(shapes), "timings": len(rows), "train_shapes": len(train), "test_shapes": n_test,
                "extra_train_shapes": len(extra),
-               "extra_distribution": "rows 2^U(10,14), cols 2^U(14,20), dtype and op uniform, I/O <= the cap",
+               "extra_distribution": "rows 2^U(10,14), cols 2^U(14,20) as drawn / nearest power of two / down to a "
+                                     "multiple of 16 in turn, dtype and op uniform, I/O <= the cap",
                "pick_rule": "pick within 5% of the measured best candidate", "pick_accuracy": acc,
                "train_loss_first_last": [float(curve[0]), float(curve[-1])], "sweep_s": round(t_sweep, 1),
                "epochs": epochs, "validation_accuracy_by_epochs": val_acc,

@@ -87,10 +87,11 @@ def ragged_widths(n_rows: int, *, seed: int = SEED_RAGGED, lo_log2: float = 10.0
 
 
 def sweep_shapes(n: int, *, seed: int = SEED_SWEEP, cap_bytes: float = 16 * 2**30,
-                 rows_log2=(6.0, 16.0), cols_log2=(10.0, 20.0), align_every: int = 0):
-    """List of (op, dtype, rows, cols) with rows*cols*(in+out bytes) <= cap.  With align_every = k > 0,
-    every k-th shape's cols are rounded down to a multiple of 16 (contiguous rows then start on the
-    16-byte grid for every dtype)."""
+                 rows_log2=(6.0, 16.0), cols_log2=(10.0, 20.0), col_modes=("any",)):
+    """List of (op, dtype, rows, cols) with rows*cols*(in+out bytes) <= cap.  Shape i takes its cols as
+    drawn when col_modes[i % len(col_modes)] is "any", rounded down to a multiple of 16 for "align16"
+    (contiguous rows then start on the 16-byte grid for every dtype), and rounded to the nearest power of
+    two for "pow2" (down if that breaks the byte cap)."""
     g = _gen(seed, "cpu")
     size = {0: 4, 1: 2, 2: 1}
     out = []
@@ -104,8 +105,14 @@ def sweep_shapes(n: int, *, seed: int = SEED_SWEEP, cap_bytes: float = 16 * 2**3
         nbytes = rows * cols * size[dtype] + (rows * 4 if op == 1 else rows * cols * ob)
         if nbytes > cap_bytes:
             continue
-        if align_every > 0 and len(out) % align_every == align_every - 1:
+        mode = col_modes[len(out) % len(col_modes)]
+        if mode == "align16":
             cols = max(16, cols // 16 * 16)
+        elif mode == "pow2":
+            c2 = 1 << int(round(math.log2(cols)))
+            if c2 > cols and rows * c2 * size[dtype] + (rows * 4 if op == 1 else rows * c2 * ob) > cap_bytes:
+                c2 //= 2
+            cols = c2
         out.append((op, dtype, rows, cols))
     return out
 
