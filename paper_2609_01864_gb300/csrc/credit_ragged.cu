@@ -201,7 +201,9 @@ __device__ __forceinline__ void ring_stream(const unsigned char *src, long long 
 // The second pass over a part that ring_stream has just streamed: its last
 // min(R, nch) chunks are still in their slots (chunk k in slot k % R), so
 // they are used first, without a copy, and each slot they free takes one of
-// the chunks that are read again (chunk j into slot (nch + j) % R).
+// the chunks that are read again.  Those go newest first (chunk again - 1
+// down to 0, the i-th into slot (nch + i) % R): the most recently read lines
+// are the likeliest to be still in L2.
 template <class F>
 __device__ __forceinline__ void ring_stream_again(const unsigned char *src, long long ng, unsigned char *buf, int R,
                                                   uint64_t *mbar, uint32_t &phase_bits, unsigned *err,
@@ -210,9 +212,9 @@ __device__ __forceinline__ void ring_stream_again(const unsigned char *src, long
     const long long nch = (body + kRChunk - 1) / kRChunk;
     const long long kept = min(static_cast<long long>(R), nch), again = nch - kept;
     auto slot_of = [&](long long k) { return static_cast<int>(k % R); };
-    auto issue = [&](long long j) {
-        const int slot = static_cast<int>((nch + j) % R);
-        const long long off = j * kRChunk;
+    auto issue = [&](long long i) {  // the i-th chunk read again: chunk again - 1 - i
+        const int slot = static_cast<int>((nch + i) % R);
+        const long long off = (again - 1 - i) * kRChunk;
         const uint32_t bytes = static_cast<uint32_t>(min(static_cast<long long>(kRChunk), body - off));
         mbar_arrive_expect_tx(&mbar[slot], bytes);
         bulk_g2s_hint(buf + static_cast<size_t>(slot) * kRChunk, src + off, bytes, &mbar[slot], policy);
@@ -226,15 +228,15 @@ __device__ __forceinline__ void ring_stream_again(const unsigned char *src, long
         if (threadIdx.x == 0 && next < again) issue(next);
         ++next;
     }
-    for (long long j = 0; j < again; ++j) {
-        const int slot = static_cast<int>((nch + j) % R);
+    for (long long i = 0; i < again; ++i) {
+        const int slot = static_cast<int>((nch + i) % R);
         mbar_wait_bounded(&mbar[slot], (phase_bits >> slot) & 1u, err);
         phase_bits ^= 1u << slot;
-        const long long g0 = j * (kRChunk / 16);
+        const long long g0 = (again - 1 - i) * (kRChunk / 16);
         fn(g0, static_cast<int>(min(static_cast<long long>(kRChunk / 16), ng - g0)),
            buf + static_cast<size_t>(slot) * kRChunk);
         __syncthreads();
-        if (threadIdx.x == 0 && j + R < again) issue(j + R);
+        if (threadIdx.x == 0 && i + R < again) issue(i + R);
     }
 }
 
