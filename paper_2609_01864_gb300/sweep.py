@@ -213,6 +213,18 @@ def evaluate(rows, test_shapes):
     return {k: v / max(1, n) for k, v in res.items()}, n
 
 
+def reusable_timings(old_rows, shapes):
+    """Timings of an earlier sweep that still describe shape i of `shapes` (every row recorded for id i has the
+    same op, dtype, rows and cols), and the ids that must be timed again (sorted)."""
+    old = {}
+    for r in old_rows:
+        old.setdefault(r["shape"], []).append(r)
+    keep = [i for i, (op, dt, nr, nc) in enumerate(shapes)
+            if i in old and all((r["op"], r["dtype"], r["rows"], r["cols"]) == (op, dt, nr, nc) for r in old[i])]
+    kept_ids = set(keep)
+    return [r for i in keep for r in old[i]], [i for i in range(len(shapes)) if i not in kept_ids]
+
+
 def eval_only(args) -> int:
     """Pick accuracies of the loaded learned model and of the analytic / ablation planners on the held-out
     split of the committed sweep, written back into the summary (the planners can change after a sweep)."""
@@ -280,17 +292,12 @@ def main(argv=None):
         rows = [r for r in rows if r["shape"] < len(shapes) + len(extra)]
     elif args.reuse_csv:
         allshapes = shapes + extra
-        old = {}
-        for r in read_csv(args.reuse_csv):
-            old.setdefault(r["shape"], []).append(r)
-        keep = {i for i, (op, dt, nr, nc) in enumerate(allshapes)
-                if i in old and all((r["op"], r["dtype"], r["rows"], r["cols"]) == (op, dt, nr, nc) for r in old[i])}
-        todo = [i for i in range(len(allshapes)) if i not in keep]
-        print(f"reusing {len(keep)} shapes, timing {len(todo)}", file=sys.stderr)
+        kept, todo = reusable_timings(read_csv(args.reuse_csv), allshapes)
+        print(f"reusing {len(allshapes) - len(todo)} shapes, timing {len(todo)}", file=sys.stderr)
         new_rows = run_sweep([allshapes[i] for i in todo], args.reps, cap, log=sys.stderr)
         for r in new_rows:
             r["shape"] = todo[r["shape"]]
-        rows = [r for i in sorted(keep) for r in old[i]] + new_rows
+        rows = kept + new_rows
     else:
         rows = run_sweep(shapes + extra, args.reps, cap, log=sys.stderr)
     t_sweep = time.time() - t0

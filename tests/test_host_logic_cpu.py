@@ -146,3 +146,35 @@ def test_traffic_record_is_used_only_for_the_kernel_source_it_was_taken_on(tmp_p
     r["source_sha"] = "older-sources"
     (prof / "traffic.json").write_text(json.dumps({"records": [r]}))
     assert bench.traffic_record(r["kernel"], r["op"], r["cols"]) is None
+
+
+def test_sweep_shape_width_modes():
+    """The training-only wide-corner shapes cycle through drawn widths, the nearest power of two and widths
+    rounded down to a multiple of 16; the draw itself (op, dtype, rows) is unchanged by the mode."""
+    from paper_2609_01864_gb300 import synth
+    kw = dict(seed=17, rows_log2=(10.0, 14.0), cols_log2=(14.0, 20.0))
+    plain = synth.sweep_shapes(90, **kw)
+    moded = synth.sweep_shapes(90, col_modes=("any", "pow2", "align16"), **kw)
+    for i, (a, b) in enumerate(zip(plain, moded)):
+        assert a[:3] == b[:3]
+        cols = b[3]
+        if i % 3 == 0:
+            assert cols == a[3]
+        elif i % 3 == 1:
+            assert cols & (cols - 1) == 0 and a[3] / 2 <= cols <= 2 * a[3]
+        else:
+            assert cols % 16 == 0 and a[3] - 16 < cols <= a[3]
+    assert synth.sweep_shapes(50) == synth.sweep_shapes(50, col_modes=("any",))
+
+
+def test_sweep_reuses_only_identical_shapes():
+    """--reuse-csv keeps an earlier sweep's timings for a shape id only where every recorded row matches the
+    shape now drawn at that id, and times the rest (including ids the earlier sweep never had)."""
+    def row(i, op, dt, r, c, us):
+        return dict(shape=i, op=op, dtype=dt, rows=r, cols=c, path=1, P=1, G=1, retain=0, fill=0.0, us=us)
+    old = [row(0, 0, 0, 64, 1024, 1.0), row(0, 0, 0, 64, 1024, 2.0), row(1, 2, 1, 128, 4096, 3.0),
+           row(2, 3, 2, 256, 8192, 4.0)]
+    shapes = [(0, 0, 64, 1024), (2, 1, 128, 4000), (3, 2, 256, 8192), (1, 0, 512, 2048)]
+    kept, todo = S.reusable_timings(old, shapes)
+    assert [r["us"] for r in kept] == [1.0, 2.0, 4.0]
+    assert todo == [1, 3]
