@@ -261,6 +261,23 @@ def max_over_ranks(value: float, world: int, device="cpu") -> float:
     return float(t.item())
 
 
+def ragged_shard(widths, world: int, rank: int):
+    """Rows [lo, hi) of this rank's share of a ragged batch: the row list is cut where the running element
+    count crosses k / world of the total (byte-balanced prefix sums; every share is contiguous and the shares
+    differ by less than one row's bytes)."""
+    import numpy as np
+    ends = np.cumsum(np.asarray(widths, dtype=np.int64))
+    total = int(ends[-1]) if len(ends) else 0
+
+    def cut(k):
+        if k <= 0:
+            return 0
+        if k >= world:
+            return len(ends)
+        return int(np.searchsorted(ends, total * k / world, side="right"))
+    return cut(rank), cut(rank + 1)
+
+
 def job_value(step_bytes_per_rank: int, world: int, ms_step: float) -> float:
     """Whole-job GB/s: every rank processes its own rows (weak scaling)."""
     return step_bytes_per_rank * world / (ms_step * 1e-3) / 1e9
@@ -464,7 +481,7 @@ def run_ours(args):
     speed_num = speed_den = 0.0
     hits = 0
     pick_rows = []
-    if not args.no_picks:
+    if not args.no_picks and world == 1:  # candidate tables time one GPU's kernels
         for k, j in enumerate(jobs):
             times = {}
             for name, p in candidates(C, j["op"], j["x"], j["y"], j["kw"]["gamma"], j["kw"]["beta"]):
@@ -490,13 +507,15 @@ def run_ours(args):
                               "measured_cluster": bool(cl) and min(cl) < best_non,
                               "candidates": {n: round(v, 4) for n, v in times.items()}})
 
+    # the secondary tables time one GPU's kernels: at N = 1 only; the ragged batch is sharded across ranks
+    single = world == 1
     bwd = None
-    if not args.no_bwd:
+    if not args.no_bwd and single:
         bwd = run_bwd_bench(C, torch, dev, synth)
-    quant = run_quant_bench(C, torch, dev, synth) if not args.no_quant else None
-    prec = run_precision_bench(C, torch, dev, synth) if not args.no_prec else None
-    ragged = run_ragged_bench(C, torch, dev, synth) if not args.no_ragged else None
-    controls = run_controls_bench(C, torch, dev, synth) if not args.no_controls else None
+    quant = run_quant_bench(C, torch, dev, synth) if not args.no_quant and single else None
+    prec = run_precision_bench(C, torch, dev, synth) if not args.no_prec and single else None
+    ragged = run_ragged_bench(C, torch, dev, synth, world=world, rank=rank) if not args.no_ragged else None
+    controls = run_controls_bench(C, torch, dev, synth) if not args.no_controls and single else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -776,19 +795,23 @@ def run_precision_bench(C, torch, dev, synth):
     return out
 
 
-def run_ragged_bench(C, torch, dev, synth, reps=10):
+def run_ragged_bench(C, torch, dev, synth, reps=10, world=1, rank=0):
     """The batching workload: 20000 BF16 rows of widths round(2^(10 + 10 u)) (log-uniform in [1K, 1M]),
     softmax or RMSNorm by a fair coin per row, packed with no alignment padding, run as one persistent launch
-    replayed from a CUDA graph (the library's autotuner picks cluster size, staging and threads).  GB/s at
-    4 B per element (one BF16 read, one BF16 write); 16 sampled rows checked against the FP64 oracle."""
+    replayed from a CUDA graph (the library's autotuner picks cluster size, staging, threads and vector
+    width).  GB/s at 4 B per element (one BF16 read, one BF16 write); 16 sampled rows checked against the
+    FP64 oracle.  Under several ranks each runs its byte-balanced contiguous share of the rows
+    (ragged_shard) and the batch time is the slowest rank's."""
     import numpy as np
     import oracle as O
     peak, peak_kind = measured_peak()
-    widths, ops = synth.ragged_widths(20000)
-    widths, ops = widths.numpy(), ops.numpy()
+    widths_all, ops_all = synth.ragged_widths(20000)
+    widths_all, ops_all = widths_all.numpy(), ops_all.numpy()
+    lo, hi = ragged_shard(widths_all, world, rank)
+    widths, ops = widths_all[lo:hi], ops_all[lo:hi]
     offs = np.concatenate([[0], np.cumsum(widths)[:-1]]).astype(np.int64)
     total = int(widths.sum())
-    g = torch.Generator(device=dev).manual_seed(synth.SEED_RAGGED)
+    g = torch.Generator(device=dev).manual_seed(synth.SEED_RAGGED + rank)
     d_in = (torch.randn(total, generator=g, device=dev) * 2.0).to(torch.bfloat16)
     d_out = torch.empty_like(d_in)
     rows = [(int(o), int(o), int(w), int(op)) for o, w, op in zip(offs, widths, ops)]
@@ -796,6 +819,8 @@ def run_ragged_bench(C, torch, dev, synth, reps=10):
     R = C.Ragged(rows, C.BF16, d_in, d_out, tune=True)
     t_create = time.perf_counter() - t0
     ms = statistics.median(time_events(lambda: R.run(), reps, warm=3))
+    if world > 1:
+        ms = max_over_ranks(ms, world, device=dev)
     info = R.info()
     worst = 0.0
     for i in np.linspace(0, len(rows) - 1, 16).astype(int):
@@ -804,8 +829,9 @@ def run_ragged_bench(C, torch, dev, synth, reps=10):
         ref, _, _ = O.run(op, C.BF16, raw, 1, w)
         worst = max(worst, output_error(op, C.BF16, d_out[o:o + w].float().double().cpu().numpy().reshape(1, w), ref))
     assert C.device_error() == C.OK
+    total = int(widths_all.sum())  # the whole batch, over all ranks
     nbytes = total * 4
-    res = {"rows": len(rows), "elements": total, "dtype": "bf16", "ms": round(ms, 4),
+    res = {"rows": len(widths_all), "elements": total, "dtype": "bf16", "ms": round(ms, 4), "ranks": world,
            "GBps": round(nbytes / ms / 1e6, 1), "frac": round(nbytes / ms / 1e6 / peak, 4), "peak_GBps": peak,
            "peak_source": peak_kind, "create_s": round(t_create, 2), "launch": info,
            "max_err_in_bound_units": round(worst, 4)}

@@ -87,3 +87,20 @@ def test_reference_arm_under_torchrun_prints_once():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 2 and d["warmup"] == 1
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_ragged_shards_are_contiguous_and_byte_balanced(world):
+    """SURVEY-style partitioning of a ragged batch over ranks: contiguous row blocks cut on the prefix sum of
+    bytes; the shares tile the row list and differ by less than the widest row."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2609_01864_gb300 import synth
+    widths, _ = synth.ragged_widths(20000)
+    widths = widths.numpy()
+    cuts = [bench.ragged_shard(widths, world, r) for r in range(world)]
+    assert cuts[0][0] == 0 and cuts[-1][1] == len(widths)
+    assert all(cuts[r][1] == cuts[r + 1][0] for r in range(world - 1))
+    share = [int(widths[lo:hi].sum()) for lo, hi in cuts]
+    assert max(share) - min(share) <= 2 * int(widths.max())
+    assert sum(share) == int(widths.sum())
