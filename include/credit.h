@@ -246,7 +246,10 @@ credit_status credit_run_ex(const credit_args *args, const credit_plan_t *plan,
  * copies slower.  The rows stream through three device staging slots in
  * blocks of about rows / 8 rows (at most 256 MiB per buffer): the copy-in of
  * block b + 1, the op on block b and the copy-out of block b - 1 overlap on
- * three CUDA streams of the library.  plan is applied to every block (NULL:
+ * three CUDA streams of the library.  Row blocks of pinned buffers (the
+ * first and last byte of the rows' range page-locked) are moved by a copy
+ * kernel of the library that loads and stores host memory directly; pageable
+ * ones by cudaMemcpy(2D)Async; scales and gamma / beta always by the latter.  plan is applied to every block (NULL:
  * credit_plan's choice for the block shape).  Staging buffers are allocated
  * on first use per device and kept (grown when needed); one host call runs
  * per device at a time.  The paper has no counterpart; it is the host-memory
