@@ -313,17 +313,26 @@ __device__ __forceinline__ float exp_fast(float x) { return ex2_approx(x * kLog2
 // ln 2 at most, from rounding the exponent, plus log2 e's own rounding), not on
 // |m|: logits of any magnitude keep the FP32 bound.  c is the caller's
 // log2-domain scale (-log2 S for a softmax, log2 448 for FP8 codes).
-__device__ __forceinline__ float exp_sub(float x, float m, float c) { return ex2_approx(fmaf(x - m, kLog2e, c)); }
+// The power is taken as 2^-24 * ex2.ftz(t + 24): every FP32 result down to the
+// smallest subnormal (t >= -149) comes from a normal SFU result, and the
+// multiply by 2^-24 is exact for normal results and rounds subnormal ones
+// correctly (the bare flush-to-zero SFU op plus one multiply).
+constexpr float kExpLift = 24.0f, kExpDrop = 5.9604644775390625e-8f;  // the lift 24 and 2^-24
+__device__ __forceinline__ float exp_sub(float x, float m, float c) {
+    return ex2_ftz(fmaf(x - m, kLog2e, c + kExpLift)) * kExpDrop;
+}
 // exp_sub over a group, two elements per packed f32x2 subtraction and FMA.
 template <int V>
 __device__ __forceinline__ void exp_sub_group(const float (&f)[V], float m, float c, float (&y)[V]) {
     if constexpr (V % 2 == 0) {
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
+            const float cl = c + kExpLift;
             const float2 t = __ffma2_rn(__fadd2_rn(make_float2(f[j], f[j + 1]), make_float2(-m, -m)),
-                                        make_float2(kLog2e, kLog2e), make_float2(c, c));
-            y[j] = ex2_approx(t.x);
-            y[j + 1] = ex2_approx(t.y);
+                                        make_float2(kLog2e, kLog2e), make_float2(cl, cl));
+            const float2 e = __fmul2_rn(make_float2(ex2_ftz(t.x), ex2_ftz(t.y)), make_float2(kExpDrop, kExpDrop));
+            y[j] = e.x;
+            y[j + 1] = e.y;
         }
     } else {
 #pragma unroll
