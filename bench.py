@@ -343,11 +343,24 @@ def run_case(spec: str):
         assert C.device_error() == C.OK
         print(json.dumps({"case": spec, "launches": C.launch_count()}))
         return 0
+    dtype = v[7] if len(v) > 7 else "f32"
     x = synth.outliers(rows, cols, seed=synth.SEED_DATA, device="cuda")
     g, b = synth.gamma_beta(cols, device="cuda")
     plan = None if path < 0 else C.make_plan(path, P, ctas_per_row=P if path == C.PATH_TWO_PASS else 1,
                                              retain=retain, fill_share=fill)
-    if op == C.QUANT_INT8:
+    if dtype == "e4m3":  # config-3 logits N(0, 3^2) as per-row scaled E4M3 codes
+        x, isc = synth.to_e4m3_rowscaled(3.0 * synth.normal(rows, cols, seed=synth.SEED_DATA, device="cuda"))
+        if op == C.LOGSUMEXP:
+            y = torch.empty(rows, device="cuda")
+            kw = dict(in_scale=isc)
+        else:
+            y = torch.empty_like(x)
+            kw = dict(in_scale=isc, out_dtype=C.FP8_E4M3, out_scale=torch.empty(rows, device="cuda"))
+    elif dtype == "bf16":
+        x = x.to(torch.bfloat16)
+        y = torch.empty(rows, device="cuda") if op == C.LOGSUMEXP else torch.empty_like(x)
+        kw = {}
+    elif op == C.QUANT_INT8:
         y = torch.empty(rows, cols, dtype=torch.int8, device="cuda")
         kw = dict(out_dtype=C.INT8, out_scale=torch.empty(rows, device="cuda"))
     else:
@@ -1001,7 +1014,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-seconds", type=float, default=60.0,
                     help="--impl reference: CPU seconds of the whole run, split over warm-up and timed steps")
-    ap.add_argument("--case", default="", help="op:rows:cols:path:P[:retain[:fill_share]] -- one plan, 3 calls (for ncu)")
+    ap.add_argument("--case", default="", help="op:rows:cols:path:P[:retain[:fill_share[:f32|bf16|e4m3]]] -- one plan, 3 calls (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not args.case:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

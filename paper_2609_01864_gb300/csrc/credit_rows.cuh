@@ -1311,6 +1311,196 @@ __device__ __forceinline__ void apply_sweep(const RowArgs &a, long long row, con
 }
 
 // ----------------------------------------------------------------------
+// E4M3 softmax / log-sum-exp rows through per-row code tables (one CTA per
+// row).  A row of E4M3 codes b with scale a takes at most 256 values
+// x(b) = a value(b), so a statistics term exp(x - m) for a fixed m, and an
+// FP8 softmax output code, depend on the input code alone: the CTA evaluates
+// them once per code into a shared-memory table, and every element costs one
+// table lookup instead of a decode, an FMA chain and an SFU exponential.
+// The table keeps 32 copies of each entry, (b, lane) at b * 32 + lane, so the
+// 32 lookups of a warp hit 32 different banks whatever the codes are.
+// ----------------------------------------------------------------------
+constexpr int kLutLanes = 32;
+constexpr int kLutEntries = 256 * kLutLanes;
+// The terms are first taken about m0 = |a| 448, which bounds every finite x
+// of the row.  Their sum S0 = sum exp(x - m0) is kept when S0 >= 2^-8: then
+// each term that matters has |x - m0| < (8 + log2 cols) ln 2, so the relative
+// error of a term (from rounding x - m0 and the exponent) stays a few 1e-7
+// times that, a few 1e-6 at most.  A row whose largest value lies further
+// below m0 is summed again about its own maximum.
+constexpr float kLutMinSum = 0.00390625f;  // 2^-8
+
+__device__ __forceinline__ float e4m3_value(uint32_t b) {
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw(static_cast<__nv_fp8_storage_t>(b & 0xFFu), __NV_E4M3)));
+}
+
+// Fill a table: the 32 copies of entry b = val(b).  Warp w evaluates the codes
+// 32 k + lane of the blocks k = w, w + warps, ...; each value then goes to its
+// 32 copies by a shuffle and 16-byte stores (8 lanes per entry).
+template <class F>
+__device__ __forceinline__ void lut_fill(uint32_t *tab, F &&val) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int blk = threadIdx.x >> 5; blk < 8; blk += nw) {
+        const uint32_t mine = val(static_cast<uint32_t>(blk * 32 + lane));
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r = 4 * k + (lane >> 3);
+            const uint32_t v = __shfl_sync(0xffffffffu, mine, r);
+            reinterpret_cast<uint4 *>(tab + (blk * 32 + r) * kLutLanes)[lane & 7] = make_uint4(v, v, v, v);
+        }
+    }
+}
+
+// Maximum of 16 sign-folded E4M3 codes, on FP16 halves (E4M3 is a subset of FP16).
+__device__ __forceinline__ __half2 e4m3_group_hmax(const uint4 &w) {
+    __half2 h[8];
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        __half2_raw r0 = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(u[k] & 0xFFFFu), __NV_E4M3);
+        __half2_raw r1 = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(u[k] >> 16), __NV_E4M3);
+        h[2 * k] = *reinterpret_cast<__half2 *>(&r0);
+        h[2 * k + 1] = *reinterpret_cast<__half2 *>(&r1);
+    }
+    return __hmax2(__hmax2(__hmax2(h[0], h[1]), __hmax2(h[2], h[3])), __hmax2(__hmax2(h[4], h[5]), __hmax2(h[6], h[7])));
+}
+
+// Entry of code byte i of u in this lane's copy of a table (base: the table's shared-memory address + 4 lane):
+// the byte moved down by one permute, the address by one shift-add, one 32-bit shared load.
+template <int I>
+__device__ __forceinline__ uint32_t lut_ld(uint32_t base, uint32_t u) {
+    const uint32_t b = __byte_perm(u, 0u, 0x4440u | I);
+    uint32_t v;
+    asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(base + (b << 7)));
+    return v;
+}
+__device__ __forceinline__ uint32_t lut_base(const uint32_t *tab) {
+    return smem_addr(tab) + 4u * (threadIdx.x & 31);
+}
+
+// Sum of the table entries of this thread's codes (16 lookups per group, summed as a tree); with MAXT also
+// the running maximum of the sign-folded codes (neg: e4m3_sign_mask of the row scale).
+template <bool MAXT, int L2H>
+__device__ __forceinline__ float lut_sum_sweep(const unsigned char *in_row, const RowSlice &s, const uint32_t *tab,
+                                               uint32_t neg, __half2 &hm) {
+    const uint32_t base = lut_base(tab);
+    float sum = 0.0f;
+    sweep_global_raw<DT_E4M3, L2H>(in_row, s, [&](long long, const uint4 &w) {
+        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+        float e[16];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            e[4 * k] = __uint_as_float(lut_ld<0>(base, u[k]));
+            e[4 * k + 1] = __uint_as_float(lut_ld<1>(base, u[k]));
+            e[4 * k + 2] = __uint_as_float(lut_ld<2>(base, u[k]));
+            e[4 * k + 3] = __uint_as_float(lut_ld<3>(base, u[k]));
+        }
+        sum += sum_tree<16>(e);
+        if constexpr (MAXT) hm = __hmax2(hm, e4m3_group_hmax(e4m3_fold_sign(w, neg)));
+    });
+    return sum;
+}
+
+// The statistics table about m: entry b = 2^((a value(b) - m) log2 e), flushed below 2^-126 (a flushed
+// term is < 2^-126 m-relative, as in the online form), the difference rounded once.
+__device__ __forceinline__ void lut_fill_terms(uint32_t *tab, float in_sc, float m) {
+    lut_fill(tab, [&](uint32_t b) { return __float_as_uint(ex2_ftz(fmaf(e4m3_value(b), in_sc, -m) * kLog2e)); });
+}
+
+// sum exp(x - m) over the row: table about m, one sweep, the edge elements directly, block sum.
+template <int L2H>
+__device__ __forceinline__ float lut_row_sum(const unsigned char *in_row, const RowSlice &s, float in_sc, float m,
+                                             uint32_t *tab, float *red) {
+    __syncthreads();  // the previous table's lookups are done
+    lut_fill_terms(tab, in_sc, m);
+    __syncthreads();
+    __half2 hm;
+    float sum = lut_sum_sweep<false, L2H>(in_row, s, tab, 0u, hm);
+    sweep_edges<DT_E4M3>(in_row, s, 1, 0, in_sc, [&](long long, float x) { sum += ex2_ftz((x - m) * kLog2e); });
+    return block_allreduce<false>(sum, red);
+}
+
+// The row maximum x of this thread's codes and edges, from the folded-code maximum hm.
+__device__ __forceinline__ float lut_thread_max(__half2 hm, float a1, float xm) {
+    const float q = fmaxf(__low2float(hm), __high2float(hm));
+    return fmaxf(q == -INFINITY ? -INFINITY : q * a1, xm);
+}
+
+template <int OP, int TOUT>
+__device__ __forceinline__ void tp_fused_e4m3(const RowArgs &a, long long row, const unsigned char *in_row,
+                                              const RowSlice &s, float in_sc, float *red) {
+    __shared__ __align__(16) uint32_t tab[kLutEntries];
+    const float a1 = fabsf(in_sc), m0 = a1 * 448.0f;
+    const uint32_t neg = e4m3_sign_mask(in_sc);
+    const __half2 hneg = __half2half2(__ushort_as_half(0xFC00u));  // -inf
+    // sweep 1: terms about m0 (and, for softmax, the row maximum); the row is kept in L2 for the next sweep
+    lut_fill_terms(tab, in_sc, m0);
+    __syncthreads();
+    __half2 hm = hneg;
+    float sum = lut_sum_sweep<OP == OP_SOFTMAX, OP == OP_SOFTMAX ? 1 : 0>(in_row, s, tab, neg, hm);
+    float xm = -INFINITY;
+    sweep_edges<DT_E4M3>(in_row, s, 1, 0, in_sc, [&](long long, float x) {
+        sum += ex2_ftz((x - m0) * kLog2e);
+        xm = fmaxf(xm, x);
+    });
+    const float S0 = block_allreduce<false>(sum, red);
+    if constexpr (OP == OP_LSE) {
+        float lse = m0 + logf(S0);
+        if (!(S0 >= kLutMinSum)) {
+            // the row's maximum lies far below m0: find it, then sum about it
+            hm = hneg;
+            sweep_global_raw<DT_E4M3, 1>(in_row, s, [&](long long, const uint4 &w) {
+                hm = __hmax2(hm, e4m3_group_hmax(e4m3_fold_sign(w, neg)));
+            });
+            const float M = block_allreduce<true>(lut_thread_max(hm, a1, xm), red);
+            lse = M + logf(lut_row_sum<0>(in_row, s, in_sc, M, tab, red));
+        }
+        if (threadIdx.x == 0) reinterpret_cast<float *>(a.out)[row] = lse;
+    } else {
+        const float M = block_allreduce<true>(lut_thread_max(hm, a1, xm), red);
+        float S;
+        if (S0 >= kLutMinSum) S = M == m0 ? S0 : S0 * ex2_ftz((m0 - M) * kLog2e);
+        else S = lut_row_sum<1>(in_row, s, in_sc, M, tab, red);
+        if constexpr (TOUT == DT_E4M3) {
+            if (threadIdx.x == 0) a.out_scale[row] = (1.0f / S) * (1.0f / 448.0f);
+            // sweep 2: output code of input code b = E4M3(448 exp(x(b) - M)), evaluated once per code in FP32
+            const float c8 = log2f(448.0f);
+            __syncthreads();
+            lut_fill(tab, [&](uint32_t b) {
+                const float d = fmaf(e4m3_value(b), in_sc, -M);
+                return static_cast<uint32_t>(__nv_cvt_float_to_fp8(ex2_ftz(fmaf(d, kLog2e, c8 + kExpLift)) * kExpDrop,
+                                                                   __NV_SATFINITE, __NV_E4M3));
+            });
+            __syncthreads();
+            unsigned char *out_row = a.out + row * a.ld_out;
+            const bool out_vec = ((reinterpret_cast<uintptr_t>(out_row) + s.h0) & 15u) == 0;
+            const uint32_t base = lut_base(tab);
+            const uint64_t pol = l2_evict_first_policy();
+            sweep_global_raw<DT_E4M3, 2>(in_row, s, [&](long long i0, const uint4 &w) {
+                const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+                uint32_t o[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    o[k] = __byte_perm(__byte_perm(lut_ld<0>(base, u[k]), lut_ld<1>(base, u[k]), 0x0040),
+                                       __byte_perm(lut_ld<2>(base, u[k]), lut_ld<3>(base, u[k]), 0x0040), 0x5410);
+                unsigned char *p = out_row + i0;
+                if (out_vec) {
+                    st_global_v4_hint(p, make_uint4(o[0], o[1], o[2], o[3]), pol);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) p[k] = static_cast<unsigned char>(o[k >> 2] >> (8 * (k & 3)));
+                }
+            });
+            sweep_edges<DT_E4M3>(in_row, s, 1, 0, in_sc,
+                                 [&](long long i, float x) { store_one<DT_E4M3>(out_row + i, exp_sub(x, M, c8)); });
+        } else {
+            const Stats st{M, S};
+            apply_sweep<OP, DT_E4M3, TOUT, 2>(a, row, in_row, s, 1, 0, in_sc, st, 1.0f);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------
 // Two-pass path, one CTA per row (single launch, the row is read twice).
 // ----------------------------------------------------------------------
 template <int OP, int TIN, int TOUT>
@@ -1321,6 +1511,10 @@ __global__ void __launch_bounds__(1024) k_tp_fused(const RowArgs a) {
     const unsigned char *in_row = a.in + row * a.ld_in * isz;
     const RowSlice s = make_slice(reinterpret_cast<uintptr_t>(in_row), a.cols, isz, 1, 0);
     const float in_sc = (TIN == DT_E4M3) ? a.in_scale[row] : 1.0f;
+    if constexpr (TIN == DT_E4M3 && (OP == OP_SOFTMAX || OP == OP_LSE)) {
+        tp_fused_e4m3<OP, TOUT>(a, row, in_row, s, in_sc, red);
+        return;
+    }
     // the row is read again by this CTA right after (not for log-sum-exp): its lines are kept in L2 on the
     // first read and go first on the second
     const float2 p = stats_sweep<OP, TIN, OP == OP_LSE ? 0 : 1>(a, in_row, s, 1, 0, in_sc, red);

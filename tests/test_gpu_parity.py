@@ -99,6 +99,33 @@ def test_fp8_rows_with_negative_and_zero_scales(op, plan, tout):
     U.check_against_oracle(op, x, sc, out_dtype=tout, plan=PLANS[plan])
 
 
+@pytest.mark.parametrize("plan", ["one_cta", "cluster4", "two_pass_g1", "two_pass_g5"])
+@pytest.mark.parametrize("op,tout", [(C.SOFTMAX, C.FP8_E4M3), (C.SOFTMAX, C.F32), (C.LOGSUMEXP, C.F32)])
+def test_fp8_rows_whose_maximum_lies_below_the_scale_bound(op, tout, plan):
+    """E4M3 rows whose codes do not reach +-448 in the direction of their scale, so the row maximum lies below
+    |scale| * 448: far below (every term about that bound underflows; sign folded or not; a constant row) and
+    a little below (the terms about the bound are kept and rescaled to the row maximum).  Row lengths off the
+    16-byte grid give head and tail elements."""
+    rows, cols = 8, 20011
+    spec = [  # (lowest code, highest code, scale)
+        (0x80, 0xFE, 0.1),     # values -448..-0: x in [-44.8, 0]
+        (0x00, 0x60, 0.05),    # 0..32: max 1.6 against the bound 22.4
+        (0x00, 0x70, 0.01),    # 0..128: max 1.28 against 4.48
+        (0x00, 0x7E, -0.1),    # 0..448 with a negative scale: x in [-44.8, 0]
+        (0x80, 0xFE, -0.002),  # -448..-0 with a negative scale: the maximum is the bound
+        (0x38, 0x48, 0.5),     # 1..4: x in [0.5, 2] against 224
+        (0x40, 0x40, 0.3),     # one code: the uniform distribution
+        (0x00, 0x68, 0.02),    # 0..64: max 1.28 against 8.96
+    ]
+    g = torch.Generator().manual_seed(33)
+    codes = torch.empty(rows, cols, dtype=torch.uint8)
+    for r, (lo, hi, _) in enumerate(spec):
+        codes[r] = torch.randint(lo, hi + 1, (cols,), generator=g, dtype=torch.int16).to(torch.uint8)
+    x = codes.view(torch.float8_e4m3fn)
+    sc = torch.tensor([s for _, _, s in spec], dtype=torch.float32)
+    U.check_against_oracle(op, x, sc, out_dtype=tout, plan=PLANS[plan])
+
+
 # --------------------------------------------------------------- config 1
 @pytest.mark.parametrize("plan", ["one_cta", "cluster4"])
 def test_softmax_256x4096_fp32_one_cta_and_cluster4(plan):
