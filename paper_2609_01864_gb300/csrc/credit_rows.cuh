@@ -44,6 +44,8 @@
 //                kernel ever waits on another CTA.
 #pragma once
 
+#include <type_traits>
+
 #include "credit_prim.cuh"
 
 namespace credit {
@@ -1365,7 +1367,7 @@ __device__ __forceinline__ __half2 e4m3_group_hmax(const uint4 &w) {
     return __hmax2(__hmax2(__hmax2(h[0], h[1]), __hmax2(h[2], h[3])), __hmax2(__hmax2(h[4], h[5]), __hmax2(h[6], h[7])));
 }
 
-// Entry of code byte i of u in this lane's copy of a table (base: the table's shared-memory address + 4 lane):
+// Entry of code byte I of u in this lane's copy of a table (base: the table's shared-memory address + 4 lane):
 // the byte moved down by one permute, the address by one shift-add, one 32-bit shared load.
 template <int I>
 __device__ __forceinline__ uint32_t lut_ld(uint32_t base, uint32_t u) {
@@ -1374,15 +1376,25 @@ __device__ __forceinline__ uint32_t lut_ld(uint32_t base, uint32_t u) {
     asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(base + (b << 7)));
     return v;
 }
-__device__ __forceinline__ uint32_t lut_base(const uint32_t *tab) {
-    return smem_addr(tab) + 4u * (threadIdx.x & 31);
+__device__ __forceinline__ uint32_t lut_base(const uint32_t *tab) { return smem_addr(tab) + 4u * (threadIdx.x & 31); }
+
+template <int V>
+__device__ __forceinline__ float max_tree(const float (&e)[V]) {
+    if constexpr (V == 1) {
+        return e[0];
+    } else {
+        float h[V / 2];
+#pragma unroll
+        for (int j = 0; j < V / 2; ++j) h[j] = fmaxf(e[2 * j], e[2 * j + 1]);
+        return max_tree<V / 2>(h);
+    }
 }
 
 // Sum of the table entries of this thread's codes (16 lookups per group, summed as a tree); with MAXT also
-// the running maximum of the sign-folded codes (neg: e4m3_sign_mask of the row scale).
+// their running maximum (the entries increase with x).
 template <bool MAXT, int L2H>
 __device__ __forceinline__ float lut_sum_sweep(const unsigned char *in_row, const RowSlice &s, const uint32_t *tab,
-                                               uint32_t neg, __half2 &hm) {
+                                               float &tmax) {
     const uint32_t base = lut_base(tab);
     float sum = 0.0f;
     sweep_global_raw<DT_E4M3, L2H>(in_row, s, [&](long long, const uint4 &w) {
@@ -1396,7 +1408,7 @@ __device__ __forceinline__ float lut_sum_sweep(const unsigned char *in_row, cons
             e[4 * k + 3] = __uint_as_float(lut_ld<3>(base, u[k]));
         }
         sum += sum_tree<16>(e);
-        if constexpr (MAXT) hm = __hmax2(hm, e4m3_group_hmax(e4m3_fold_sign(w, neg)));
+        if constexpr (MAXT) tmax = fmaxf(tmax, max_tree<16>(e));
     });
     return sum;
 }
@@ -1414,30 +1426,35 @@ __device__ __forceinline__ float lut_row_sum(const unsigned char *in_row, const 
     __syncthreads();  // the previous table's lookups are done
     lut_fill_terms(tab, in_sc, m);
     __syncthreads();
-    __half2 hm;
-    float sum = lut_sum_sweep<false, L2H>(in_row, s, tab, 0u, hm);
+    float tmax = 0.0f;
+    float sum = lut_sum_sweep<false, L2H>(in_row, s, tab, tmax);
     sweep_edges<DT_E4M3>(in_row, s, 1, 0, in_sc, [&](long long, float x) { sum += ex2_ftz((x - m) * kLog2e); });
     return block_allreduce<false>(sum, red);
 }
 
-// The row maximum x of this thread's codes and edges, from the folded-code maximum hm.
-__device__ __forceinline__ float lut_thread_max(__half2 hm, float a1, float xm) {
+// The row maximum of x: the sign-folded codes' maximum on FP16 halves, scaled, and the edge elements'
+// maximum xm of this thread.
+__device__ __forceinline__ float lut_row_max(const unsigned char *in_row, const RowSlice &s, float in_sc, float xm,
+                                             float *red) {
+    const uint32_t neg = e4m3_sign_mask(in_sc);
+    __half2 hm = __half2half2(__ushort_as_half(0xFC00u));  // -inf
+    sweep_global_raw<DT_E4M3, 1>(in_row, s, [&](long long, const uint4 &w) {
+        hm = __hmax2(hm, e4m3_group_hmax(e4m3_fold_sign(w, neg)));
+    });
     const float q = fmaxf(__low2float(hm), __high2float(hm));
-    return fmaxf(q == -INFINITY ? -INFINITY : q * a1, xm);
+    return block_allreduce<true>(fmaxf(q == -INFINITY ? -INFINITY : q * fabsf(in_sc), xm), red);
 }
 
 template <int OP, int TOUT>
 __device__ __forceinline__ void tp_fused_e4m3(const RowArgs &a, long long row, const unsigned char *in_row,
                                               const RowSlice &s, float in_sc, float *red) {
     __shared__ __align__(16) uint32_t tab[kLutEntries];
-    const float a1 = fabsf(in_sc), m0 = a1 * 448.0f;
-    const uint32_t neg = e4m3_sign_mask(in_sc);
-    const __half2 hneg = __half2half2(__ushort_as_half(0xFC00u));  // -inf
-    // sweep 1: terms about m0 (and, for softmax, the row maximum); the row is kept in L2 for the next sweep
+    const float m0 = fabsf(in_sc) * 448.0f;
+    // sweep 1: terms about m0 (and, for softmax, their maximum); the row is kept in L2 for the next sweep
     lut_fill_terms(tab, in_sc, m0);
     __syncthreads();
-    __half2 hm = hneg;
-    float sum = lut_sum_sweep<OP == OP_SOFTMAX, OP == OP_SOFTMAX ? 1 : 0>(in_row, s, tab, neg, hm);
+    float tmax = 0.0f;
+    float sum = lut_sum_sweep<OP == OP_SOFTMAX, OP == OP_SOFTMAX ? 1 : 0>(in_row, s, tab, tmax);
     float xm = -INFINITY;
     sweep_edges<DT_E4M3>(in_row, s, 1, 0, in_sc, [&](long long, float x) {
         sum += ex2_ftz((x - m0) * kLog2e);
@@ -1448,24 +1465,30 @@ __device__ __forceinline__ void tp_fused_e4m3(const RowArgs &a, long long row, c
         float lse = m0 + logf(S0);
         if (!(S0 >= kLutMinSum)) {
             // the row's maximum lies far below m0: find it, then sum about it
-            hm = hneg;
-            sweep_global_raw<DT_E4M3, 1>(in_row, s, [&](long long, const uint4 &w) {
-                hm = __hmax2(hm, e4m3_group_hmax(e4m3_fold_sign(w, neg)));
-            });
-            const float M = block_allreduce<true>(lut_thread_max(hm, a1, xm), red);
+            const float M = lut_row_max(in_row, s, in_sc, xm, red);
             lse = M + logf(lut_row_sum<0>(in_row, s, in_sc, M, tab, red));
         }
         if (threadIdx.x == 0) reinterpret_cast<float *>(a.out)[row] = lse;
     } else {
-        const float M = block_allreduce<true>(lut_thread_max(hm, a1, xm), red);
-        float S;
-        if (S0 >= kLutMinSum) S = M == m0 ? S0 : S0 * ex2_ftz((m0 - M) * kLog2e);
-        else S = lut_row_sum<1>(in_row, s, in_sc, M, tab, red);
+        float M, S;
+        if (S0 >= kLutMinSum) {
+            // the row maximum from the largest entry met: the largest value among the codes with that entry
+            // (a code not in the row can share it only if its value is within ~1e-6 of the maximum)
+            const float Tm = block_allreduce<true>(tmax, red);
+            float cand = xm;
+            for (int b = threadIdx.x; b < 256; b += blockDim.x)
+                if (__uint_as_float(tab[b * kLutLanes]) == Tm) cand = fmaxf(cand, e4m3_value(b) * in_sc);
+            M = block_allreduce<true>(cand, red);
+            S = M == m0 ? S0 : S0 * ex2_ftz((m0 - M) * kLog2e);
+        } else {
+            M = lut_row_max(in_row, s, in_sc, xm, red);
+            S = lut_row_sum<1>(in_row, s, in_sc, M, tab, red);
+        }
         if constexpr (TOUT == DT_E4M3) {
             if (threadIdx.x == 0) a.out_scale[row] = (1.0f / S) * (1.0f / 448.0f);
             // sweep 2: output code of input code b = E4M3(448 exp(x(b) - M)), evaluated once per code in FP32
             const float c8 = log2f(448.0f);
-            __syncthreads();
+            __syncthreads();  // the statistics table's last reads (the maximum's codes) are done
             lut_fill(tab, [&](uint32_t b) {
                 const float d = fmaf(e4m3_value(b), in_sc, -M);
                 return static_cast<uint32_t>(__nv_cvt_float_to_fp8(ex2_ftz(fmaf(d, kLog2e, c8 + kExpLift)) * kExpDrop,
@@ -1476,21 +1499,26 @@ __device__ __forceinline__ void tp_fused_e4m3(const RowArgs &a, long long row, c
             const bool out_vec = ((reinterpret_cast<uintptr_t>(out_row) + s.h0) & 15u) == 0;
             const uint32_t base = lut_base(tab);
             const uint64_t pol = l2_evict_first_policy();
-            sweep_global_raw<DT_E4M3, 2>(in_row, s, [&](long long i0, const uint4 &w) {
-                const uint32_t u[4] = {w.x, w.y, w.z, w.w};
-                uint32_t o[4];
+            // one sweep per store form, so the loop body holds only the stores it executes
+            auto sweep = [&](auto vec) {
+                sweep_global_raw<DT_E4M3, 2>(in_row, s, [&](long long i0, const uint4 &w) {
+                    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+                    uint32_t o[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    o[k] = __byte_perm(__byte_perm(lut_ld<0>(base, u[k]), lut_ld<1>(base, u[k]), 0x0040),
-                                       __byte_perm(lut_ld<2>(base, u[k]), lut_ld<3>(base, u[k]), 0x0040), 0x5410);
-                unsigned char *p = out_row + i0;
-                if (out_vec) {
-                    st_global_v4_hint(p, make_uint4(o[0], o[1], o[2], o[3]), pol);
-                } else {
+                    for (int k = 0; k < 4; ++k)
+                        o[k] = __byte_perm(__byte_perm(lut_ld<0>(base, u[k]), lut_ld<1>(base, u[k]), 0x0040),
+                                           __byte_perm(lut_ld<2>(base, u[k]), lut_ld<3>(base, u[k]), 0x0040), 0x5410);
+                    unsigned char *p = out_row + i0;
+                    if constexpr (decltype(vec)::value) {
+                        st_global_v4_hint(p, make_uint4(o[0], o[1], o[2], o[3]), pol);
+                    } else {
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) p[k] = static_cast<unsigned char>(o[k >> 2] >> (8 * (k & 3)));
-                }
-            });
+                        for (int k = 0; k < 16; ++k) p[k] = static_cast<unsigned char>(o[k >> 2] >> (8 * (k & 3)));
+                    }
+                });
+            };
+            if (out_vec) sweep(std::true_type{});
+            else sweep(std::false_type{});
             sweep_edges<DT_E4M3>(in_row, s, 1, 0, in_sc,
                                  [&](long long i, float x) { store_one<DT_E4M3>(out_row + i, exp_sub(x, M, c8)); });
         } else {
