@@ -35,6 +35,9 @@ namespace {
 constexpr int kIn = 21, kH = 64;
 // fill candidates of cluster plans that leave SMs idle (share of the rows)
 constexpr float kFillShares[] = {0.15f, 0.2f, 0.3f, 0.4f};
+// Predictions closer than this (log2 of the latency ratio, 0.7%) are below the ensemble's resolution: among
+// them the planner takes a plan without a fill (one launch instead of three, no shared-HBM contention).
+constexpr float kFillTieLog2 = 0.01f;
 constexpr int kFillMinIdle = 16;
 constexpr long long kFillMinRows = 64;
 // flat layout: W1 (64 x kIn), b1, W2 (64x64), b2, W3 (64x64), b3, W4 (1x64), b4
@@ -263,8 +266,7 @@ static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long lon
         if (g_models.empty()) return false;
         ens = g_models;
     }
-    float best = 1e30f;
-    credit_plan_t bp{};
+    std::vector<std::pair<float, credit_plan_t>> cands;  // (mean predicted log2 latency, plan), in order
     auto consider = [&](int path, int P, int G, long long smem, int retain, float fill) {
         float f[kIn], y = 0.0f;
         mlp_features(op, tin, tout, rows, cols, path, P, G, retain == CREDIT_RETAIN_TMEM, fill, f);
@@ -274,18 +276,16 @@ static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long lon
             y += ym;
         }
         y /= static_cast<float>(ens.size());
-        if (y < best) {
-            best = y;
-            std::memset(&bp, 0, sizeof(bp));
-            bp.path = path;
-            bp.cluster_size = path == CREDIT_PATH_TWO_PASS ? 1 : P;
-            bp.ctas_per_row = path == CREDIT_PATH_TWO_PASS ? G : P;
-            bp.smem_bytes = smem;
-            bp.retain = retain;
-            bp.fill_share = fill;
-            bp.predicted_us = std::exp2(y);
-            bp.source = 1;
-        }
+        credit_plan_t c{};
+        c.path = path;
+        c.cluster_size = path == CREDIT_PATH_TWO_PASS ? 1 : P;
+        c.ctas_per_row = path == CREDIT_PATH_TWO_PASS ? G : P;
+        c.smem_bytes = smem;
+        c.retain = retain;
+        c.fill_share = fill;
+        c.predicted_us = std::exp2(y);
+        c.source = 1;
+        cands.emplace_back(y, c);
     };
     const int isz = dtype_size(tin);
     for (int P : {1, 2, 4, 8, 16}) {
@@ -315,6 +315,21 @@ static bool learned_plan_impl(const DeviceInfo &di, int device, int op, long lon
         if (G == 1 || groups / G >= 1024) consider(CREDIT_PATH_TWO_PASS, 1, G, 0, CREDIT_RETAIN_AUTO, 0.0f);
     const int Gs = two_pass_split(di.sm_count, rows, cols, isz);
     if (Gs > 1 && Gs != 2 && Gs != 4 && Gs != 8) consider(CREDIT_PATH_TWO_PASS, 1, Gs, 0, CREDIT_RETAIN_AUTO, 0.0f);
+    if (cands.empty()) return false;
+    float best = 1e30f;
+    for (const auto &c : cands) best = std::min(best, c.first);
+    // the lowest prediction; within kFillTieLog2 of it, the lowest one without a fill
+    int pick = -1, pick_nofill = -1;
+    for (int i = 0; i < static_cast<int>(cands.size()); ++i) {
+        const float y = cands[i].first;
+        if (pick < 0 && y == best) pick = i;
+        if (cands[i].second.fill_share == 0.0f && y <= best + kFillTieLog2 &&
+            (pick_nofill < 0 || y < cands[pick_nofill].first))
+            pick_nofill = i;
+    }
+    if (pick_nofill >= 0) pick = pick_nofill;
+    best = cands[pick].first;
+    credit_plan_t bp = cands[pick].second;
     // predicted latency anchored on the measured baseline: T_B (calibration, Eq. 7) times the model's ratio of
     // the pick to the baseline plan (the ratio is what the network learns; its per-shape level cancels)
     credit_plan_t base;

@@ -173,6 +173,17 @@ def features_of(r):
                           r.get("retain", 0), r.get("fill", 0.0))
 
 
+FILL_TIE_LOG2 = 0.01  # the learned planner's tie-break (kFillTieLog2 in csrc/credit_mlp.cu)
+
+
+def learned_pick(cand):
+    """The learned planner's choice among a shape's measured candidates: the lowest prediction or, within
+    FILL_TIE_LOG2 of it, the lowest one without a fill."""
+    lo = min(c["pred_log2us"] for c in cand)
+    nofill = [c for c in cand if c.get("fill", 0.0) == 0.0 and c["pred_log2us"] <= lo + FILL_TIE_LOG2]
+    return min(nofill or cand, key=lambda c: c["pred_log2us"])
+
+
 def evaluate(rows, test_shapes):
     by_shape = {}
     for r in rows:
@@ -194,7 +205,7 @@ def evaluate(rows, test_shapes):
         n += 1
         best = min(c["us"] for c in cand)
         ok = lambda c: c["us"] <= 1.05 * best  # noqa: E731
-        learned = min(cand, key=lambda c: c["pred_log2us"])
+        learned = learned_pick(cand)
         res["learned"] += ok(learned)
         r0 = cand[0]
         for name, env in (("analytic", "analytic"), ("ablation", "ablation")):
