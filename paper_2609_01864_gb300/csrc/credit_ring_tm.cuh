@@ -472,6 +472,11 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ring_tm(const RowArgs a) {
 #pragma unroll
                                 for (int q = 0; q < SV; ++q) xs[q] = f[hv + q];
                                 q8_codes<SV>(xs, st.a, st.b, y);
+                            } else if constexpr (OP == OP_SOFTMAX) {  // h on element pairs (the same bits as h)
+                                float xs[SV];
+#pragma unroll
+                                for (int q = 0; q < SV; ++q) xs[q] = f[hv + q];
+                                exp_sub_group<SV>(xs, st.a, cL, y);
                             } else {
 #pragma unroll
                                 for (int q = 0; q < SV; ++q)

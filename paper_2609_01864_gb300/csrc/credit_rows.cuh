@@ -261,12 +261,18 @@ __device__ __forceinline__ void copy_raw(unsigned char *dst, const unsigned char
 // ======================================================================
 template <int OP> struct Stream;
 
+// Maximum of N values as a tree (dependency depth log2 N; the same value as any order).
 template <int N>
 __device__ __forceinline__ float max_of(const float (&f)[N]) {
-    float mv = f[0];
+    if constexpr (N == 1) {
+        return f[0];
+    } else {
+        float h[(N + 1) / 2];
 #pragma unroll
-    for (int j = 1; j < N; ++j) mv = fmaxf(mv, f[j]);
-    return mv;
+        for (int j = 0; j < N / 2; ++j) h[j] = fmaxf(f[2 * j], f[2 * j + 1]);
+        if constexpr (N % 2 == 1) h[N / 2] = f[N - 1];
+        return max_of(h);
+    }
 }
 
 template <> struct Stream<OP_SOFTMAX> {  // online (max, sum exp)
@@ -1378,18 +1384,6 @@ __device__ __forceinline__ uint32_t lut_ld(uint32_t base, uint32_t u) {
 }
 __device__ __forceinline__ uint32_t lut_base(const uint32_t *tab) { return smem_addr(tab) + 4u * (threadIdx.x & 31); }
 
-template <int V>
-__device__ __forceinline__ float max_tree(const float (&e)[V]) {
-    if constexpr (V == 1) {
-        return e[0];
-    } else {
-        float h[V / 2];
-#pragma unroll
-        for (int j = 0; j < V / 2; ++j) h[j] = fmaxf(e[2 * j], e[2 * j + 1]);
-        return max_tree<V / 2>(h);
-    }
-}
-
 // Sum of the table entries of this thread's codes (16 lookups per group, summed as a tree); with MAXT also
 // their running maximum (the entries increase with x).
 template <bool MAXT, int L2H>
@@ -1408,7 +1402,7 @@ __device__ __forceinline__ float lut_sum_sweep(const unsigned char *in_row, cons
             e[4 * k + 3] = __uint_as_float(lut_ld<3>(base, u[k]));
         }
         sum += sum_tree<16>(e);
-        if constexpr (MAXT) tmax = fmaxf(tmax, max_tree<16>(e));
+        if constexpr (MAXT) tmax = fmaxf(tmax, max_of(e));
     });
     return sum;
 }
