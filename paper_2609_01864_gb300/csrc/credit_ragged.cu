@@ -244,6 +244,29 @@ template <int TIN>
 __device__ __forceinline__ float h_of(int op, float x, const Stats &st, float inv) {
     return op == OP_SOFTMAX ? exp_fast(x - st.a) * inv : x * st.a;
 }
+// h_of over one decoded group, two elements per packed f32x2 subtraction and multiply (the same bits as
+// h_of element by element), the op tested once per group.
+template <int V>
+__device__ __forceinline__ void h_group(int op, const float (&f)[V], const Stats &st, float inv, float (&y)[V]) {
+    static_assert(V % 2 == 0, "groups hold an even number of elements");
+    if (op == OP_SOFTMAX) {
+#pragma unroll
+        for (int j = 0; j < V; j += 2) {
+            const float2 t = __fmul2_rn(__fadd2_rn(make_float2(f[j], f[j + 1]), make_float2(-st.a, -st.a)),
+                                        make_float2(kLog2e, kLog2e));
+            const float2 e = __fmul2_rn(make_float2(ex2_approx(t.x), ex2_approx(t.y)), make_float2(inv, inv));
+            y[j] = e.x;
+            y[j + 1] = e.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; j += 2) {
+            const float2 e = __fmul2_rn(make_float2(f[j], f[j + 1]), make_float2(st.a, st.a));
+            y[j] = e.x;
+            y[j + 1] = e.y;
+        }
+    }
+}
 
 // This CTA's slice of a later item, moved from HBM into L2 while the current
 // item is written (at most the staging capacity), so that its bulk copies
@@ -375,8 +398,7 @@ __global__ void __launch_bounds__(256, VW == 2 ? 2 : 4) k_ragged(const RaggedArg
                 for_groups<VW>(buf, gb, ge, tid, T, [&](long long g, const uint4 &w) {
                     float f[V], y[V];
                     decode_group<TIN>(w, f, 1.0f);
-#pragma unroll
-                    for (int q = 0; q < V; ++q) y[q] = h_of<TIN>(op, f[q], st, inv);
+                    h_group<V>(op, f, st, inv, y);
                     store_group<TIN, V>(orow + (i_base + g * V) * isz, y, out_vec);
                 });
                 __syncthreads();  // chunk k of this item is written: its slot takes chunk k of the next
@@ -424,8 +446,7 @@ __global__ void __launch_bounds__(256, VW == 2 ? 2 : 4) k_ragged(const RaggedArg
                 for_groups<VW>(cb, 0, gn, tid, T, [&](long long g, const uint4 &w) {
                     float f[V], y[V];
                     decode_group<TIN>(w, f, 1.0f);
-#pragma unroll
-                    for (int q = 0; q < V; ++q) y[q] = h_of<TIN>(op, f[q], st, inv);
+                    h_group<V>(op, f, st, inv, y);
                     store_group<TIN, V>(orow + (i_base + (g0 + g) * V) * isz, y, out_vec);
                 });
             });
