@@ -90,7 +90,10 @@ typedef enum {
  *         RMSNorm and int8 quantisation (not FP8-output norms, not
  *         logsumexp), slice <= 128 KiB of
  *         input, one CTA per SM.  The project's addition; the paper stages
- *         in shared memory only.
+ *         in shared memory only.  A LayerNorm call whose gamma / beta cannot
+ *         be staged in shared memory beside the ring (rows off the 16-byte
+ *         grid) runs on the SMEM tier instead, also under an explicit TMEM
+ *         plan.
  *   AUTO  TMEM where it applies and a slice exceeds 32 KiB, else SMEM
  *         (CREDIT_RETAIN=smem in the environment makes AUTO mean SMEM,
  *         CREDIT_RETAIN=tmem TMEM wherever it applies).  The planners set
