@@ -110,6 +110,26 @@ def test_affine_modes(op, dt, cols, P, mode, monkeypatch):
     U.check_against_oracle(op, x, s, out_dtype=C.F32 if dt == C.FP8_E4M3 else dt, plan=tm_plan(P), gamma=g, beta=b)
 
 
+def test_layernorm_with_affine_from_l2_repeats_exactly(monkeypatch):
+    """LayerNorm whose gamma / beta the tensor-memory kernel would read from L2 runs on the shared-memory ring,
+    also under an explicit tensor-memory plan (the tensor-memory kernel returned wrong rows on that
+    combination in soak runs): 48 x 262144 FP32 at P = 8, within the oracle's bound, then 30 more calls into
+    NaN-filled outputs, each bit-identical to the first."""
+    monkeypatch.setenv("CREDIT_TM_AFFINE", "direct")
+    rows, cols, P = 48, 262144, 8
+    x, s = U.make_input(C.F32, rows, cols, kind="outliers", seed=cols + P)
+    g, b = affine(C.LAYERNORM, cols, seed=9)
+    _, first = U.check_against_oracle(C.LAYERNORM, x, s, plan=tm_plan(P), gamma=g, beta=b)
+    xd, gd, bd = x.cuda(), g.cuda(), b.cuda()
+    out = torch.empty_like(xd)
+    for _ in range(30):
+        out.fill_(float("nan"))
+        C.run_ex(C.LAYERNORM, xd, out, plan=tm_plan(P), gamma=gd, beta=bd)
+        torch.cuda.synchronize()
+        assert torch.equal(out, first)
+    assert C.device_error() == C.OK
+
+
 @pytest.mark.parametrize("P", [1, 4])
 @pytest.mark.parametrize("op", TM_OPS)
 def test_unaligned_rows_and_strides(op, P):
