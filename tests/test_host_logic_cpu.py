@@ -178,3 +178,24 @@ def test_sweep_reuses_only_identical_shapes():
     kept, todo = S.reusable_timings(old, shapes)
     assert [r["us"] for r in kept] == [1.0, 2.0, 4.0]
     assert todo == [1, 3]
+
+
+def test_learned_pick_prefers_a_plan_without_fill_only_within_the_tie_margin():
+    """The learned planner's choice as the sweep scores it: the lowest prediction, except that within
+    FILL_TIE_LOG2 of it the lowest prediction without a fill wins (two-pass and one-CTA plans count as
+    plans without a fill); ties at equal predictions keep the first candidate."""
+    def cand(name, pred, fill=0.0):
+        return dict(name=name, pred_log2us=pred, fill=fill)
+    eps = S.FILL_TIE_LOG2
+    # a fill ahead by less than the margin: the plain cluster plan
+    c = [cand("c16_f0.15", 1.000, 0.15), cand("c16", 1.000 + 0.4 * eps), cand("tp4", 1.5)]
+    assert S.learned_pick(c)["name"] == "c16"
+    # a fill ahead by more than the margin: the fill
+    c = [cand("c16_f0.15", 1.000, 0.15), cand("c16", 1.000 + 2.0 * eps), cand("tp4", 1.5)]
+    assert S.learned_pick(c)["name"] == "c16_f0.15"
+    # only fills near the minimum: the lowest of them
+    c = [cand("c8_f0.2", 2.0, 0.2), cand("c8_f0.15", 1.99, 0.15), cand("tp1", 3.0)]
+    assert S.learned_pick(c)["name"] == "c8_f0.15"
+    # among plans without a fill inside the margin, the lowest; equal predictions keep the first
+    c = [cand("c4", 1.004), cand("c2", 1.002), cand("c2b", 1.002), cand("c8_f0.3", 1.0, 0.3)]
+    assert S.learned_pick(c)["name"] == "c2"
